@@ -1,0 +1,308 @@
+"""FP64 oracle of the indexing path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
+import this module.  It shares no code with the CUDA path (``paper_2111_07347_gb300``)
+and imports nothing from it; the seeded generators in
+``paper_2111_07347_gb300.synth`` feed both sides.
+
+Steps, in the paper's order (Section 2.2):
+
+* ``prepare_library``  -- template spots to the polar grid: radius and angle rounded
+  to the nearest pixel (Section 2.2, "rounded to the nearest integer"), spots beyond
+  the grid dropped, spots landing on one pixel merged by summing intensity (the
+  rendered template image of Eq. 1), mirror templates made by reflecting spots across
+  y = 0 (Section 2.2 / Fig. 2 caption), optional unit intensities (Section 4.3),
+  template norms sqrt(sum T^2) (Eq. 1 denominator) and azimuthal sums (Section 2.2,
+  pre-filter).
+* ``polar``            -- gamma/subtract then bilinear polar resampling (C loops).
+* ``scores``           -- per template maximum of Eq. 1 over all azimuthal shifts with
+  wraparound and the lowest shift attaining it (C loops).
+* ``prefilter``        -- azimuthally integrated image and templates correlated by one
+  matrix-vector product; the best fraction kept (Section 2.2, Fig. 3).
+* ``top_n``            -- templates ranked by their best Q (Section 2.2: "sorted and
+  the top N best matching templates can be queried").
+* ``dense_scores`` / ``dft_scores`` -- Q(k, s) for every shift written as the dense
+  circulant contraction and as its angular-DFT factorisation (Section 2.2, the
+  complexity discussion naming the FFT cross-correlation alternative), both in FP64.
+
+Ties: a relative window of 1e-12 decides equality; among equals the lowest shift and
+the lowest template index win.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+TIE_REL = 1e-12
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def build(force: bool = False) -> str:
+    """Compile tm_oracle.c into liboracle.so beside it (gcc, -O2, OpenMP, no fast-math)."""
+    src = os.path.join(_HERE, "tm_oracle.c")
+    out = os.path.join(_HERE, "liboracle.so")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                               "-o", out + ".tmp", src, "-lm"])
+        os.replace(out + ".tmp", out)
+    return out
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, i32, d = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.oracle_polar.argtypes = [P, i32, i64, i32, i32, P, d, d, d, d, i32, i32, d, P]
+        lib.oracle_scores.argtypes = [P, i64, i32, i32, P, P, P, P, P, i64, P, P, P]
+        lib.oracle_scores_full.argtypes = [P, i64, i32, i32, P, P, P, P, P, i64, P]
+        lib.oracle_num_threads.restype = i32
+        _LIB = lib
+    return _LIB
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_lib().oracle_num_threads())
+
+
+# ----------------------------------------------------------------------------------
+# Library preparation (Section 2.1 template lists -> polar grid of Section 2.2)
+# ----------------------------------------------------------------------------------
+
+class Library:
+    """Rounded, merged templates on the polar grid (expanded: mirrors at k >= K0)."""
+
+    def __init__(self, off, ri, ti, inten, K0, mirror, n_r, n_theta, dr):
+        self.off, self.ri, self.ti, self.I = off, ri, ti, inten
+        self.K0, self.mirror = K0, mirror
+        self.K = off.shape[0] - 1
+        self.n_r, self.n_theta, self.dr = n_r, n_theta, dr
+        self.norm = np.array([math.sqrt(float(np.sum(inten[off[k]:off[k + 1]] ** 2)))
+                              for k in range(self.K)], dtype=np.float64)
+        self.radial = np.zeros((self.K, n_r), dtype=np.float64)
+        for k in range(self.K):
+            for i in range(off[k], off[k + 1]):
+                self.radial[k, ri[i]] += inten[i]
+
+    def dense(self, k: int) -> np.ndarray:
+        """Template k rendered as a dense polar image T[r, theta]."""
+        T = np.zeros((self.n_r, self.n_theta))
+        for i in range(self.off[k], self.off[k + 1]):
+            T[self.ri[i], self.ti[i]] += self.I[i]
+        return T
+
+
+def round_spot(r_px: float, theta: float, n_theta: int, dr: float):
+    """Nearest polar pixel of a spot: r_i = floor(r/dr + 1/2), t_i = floor(u + 1/2) mod
+    n_theta with u = theta' / (2 pi / n_theta) and theta' = theta reduced to [0, 2 pi)."""
+    th = math.fmod(theta, 2.0 * math.pi)
+    if th < 0.0:
+        th += 2.0 * math.pi
+    step = 2.0 * math.pi / n_theta
+    t = int(math.floor(th / step + 0.5)) % n_theta
+    r = int(math.floor(r_px / dr + 0.5))
+    return r, t
+
+
+def prepare_library(ts, n_r: int, n_theta: int, dr: float = 1.0, mirror: bool | None = None,
+                    unit_intensity: bool = False) -> Library:
+    """Template set -> Library on the (n_r, n_theta, dr) grid.
+
+    Spots given as (kx, ky) are converted with r = hypot(x, y), theta = atan2(y, x) after
+    scaling to pixels; a mirror copy reflects y -> -y (theta -> -theta) before rounding.
+    With ``unit_intensity`` every input spot gets intensity 1 before merging."""
+    mirror = ts.mirror if mirror is None else mirror
+    K0 = ts.n_templates
+    copies = (False, True) if mirror else (False,)
+    off = [0]
+    ri_all, ti_all, I_all = [], [], []
+    for m in copies:
+        for k in range(K0):
+            merged = {}
+            order = []
+            for i in range(int(ts.offsets[k]), int(ts.offsets[k + 1])):
+                a, b = float(ts.a[i]), float(ts.b[i])
+                if ts.coords == "xy":
+                    x, y = a * ts.px_per_unit, b * ts.px_per_unit
+                    if m:
+                        y = -y
+                    r_px, th = math.hypot(x, y), math.atan2(y, x)
+                else:
+                    r_px, th = a, (-b if m else b)
+                r, t = round_spot(r_px, th, n_theta, dr)
+                if r < 0 or r >= n_r:
+                    continue
+                w = 1.0 if unit_intensity else float(ts.intensity[i])
+                if (r, t) not in merged:
+                    merged[(r, t)] = 0.0
+                    order.append((r, t))
+                merged[(r, t)] += w
+            for key in order:
+                ri_all.append(key[0]); ti_all.append(key[1]); I_all.append(merged[key])
+            off.append(len(ri_all))
+    return Library(np.asarray(off, dtype=np.int64), np.asarray(ri_all, dtype=np.int32),
+                   np.asarray(ti_all, dtype=np.int32), np.asarray(I_all, dtype=np.float64),
+                   K0, mirror, n_r, n_theta, dr)
+
+
+# ----------------------------------------------------------------------------------
+# Pattern side
+# ----------------------------------------------------------------------------------
+
+def polar(frames: np.ndarray, n_r: int, n_theta: int, dr: float = 1.0, gamma: float = 0.5,
+          subtract: float = 0.0, centre=None, centres: np.ndarray | None = None) -> np.ndarray:
+    """Gamma/subtract then bilinear polar resampling: [n][H][W] -> [n][n_r][n_theta] FP64.
+    Default centre ((W-1)/2, (H-1)/2); ``centres`` [n][2] overrides per pattern."""
+    frames = np.ascontiguousarray(frames)
+    if frames.dtype == np.uint16:
+        dt = 0
+    elif frames.dtype == np.float32:
+        dt = 1
+    else:
+        raise TypeError("frames must be uint16 or float32")
+    n, H, W = frames.shape
+    cx, cy = ((W - 1) / 2.0, (H - 1) / 2.0) if centre is None else centre
+    out = np.empty((n, n_r, n_theta), dtype=np.float64)
+    c = None if centres is None else np.ascontiguousarray(centres, dtype=np.float64)
+    _lib().oracle_polar(_ptr(frames), dt, n, H, W, _ptr(c), float(cx), float(cy), float(gamma),
+                        float(subtract), n_r, n_theta, float(dr), _ptr(out))
+    return out
+
+
+def scores(P: np.ndarray, lib: Library, active: np.ndarray | None = None):
+    """Per (pattern, template): max over shifts of Eq. 1 and the lowest shift attaining it."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    n = P.shape[0]
+    q = np.empty((n, lib.K), dtype=np.float64)
+    s = np.empty((n, lib.K), dtype=np.int32)
+    act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+    _lib().oracle_scores(_ptr(P), n, lib.n_r, lib.n_theta, _ptr(lib.off), _ptr(lib.ri),
+                         _ptr(lib.ti), _ptr(lib.I), _ptr(lib.norm), lib.K, _ptr(act),
+                         _ptr(q), _ptr(s))
+    return q, s
+
+
+def scores_full(P: np.ndarray, lib: Library) -> np.ndarray:
+    """Q for every (pattern, template, shift): [n][K][n_theta]."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    n = P.shape[0]
+    q = np.empty((n, lib.K, lib.n_theta), dtype=np.float64)
+    _lib().oracle_scores_full(_ptr(P), n, lib.n_r, lib.n_theta, _ptr(lib.off), _ptr(lib.ri),
+                              _ptr(lib.ti), _ptr(lib.I), _ptr(lib.norm), lib.K, _ptr(q))
+    return q
+
+
+def radial_profile(P: np.ndarray) -> np.ndarray:
+    """Azimuthal integral of each polar image: [n][n_r]."""
+    return P.sum(axis=2)
+
+
+def keep_count(fraction: float, K: int) -> int:
+    """Number of templates the pre-filter keeps: ceil(fraction * K), all when fraction >= 1."""
+    if fraction >= 1.0:
+        return K
+    return max(1, int(math.ceil(fraction * K)))
+
+
+def prefilter(P: np.ndarray, lib: Library, fraction: float):
+    """Cosine correlation of azimuthal sums; keep the ceil(fraction K) best templates per
+    pattern, ties to the lower index.  Returns (active [n][K] bool, score [n][K])."""
+    RP = radial_profile(P)
+    RT = lib.radial
+    num = RP @ RT.T
+    nP = np.sqrt(np.sum(RP * RP, axis=1))
+    nT = np.sqrt(np.sum(RT * RT, axis=1))
+    den = nP[:, None] * nT[None, :]
+    sc = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+    n, K = sc.shape
+    keep = keep_count(fraction, K)
+    active = np.zeros((n, K), dtype=bool)
+    ks = np.arange(K)
+    for p in range(n):
+        order = np.lexsort((ks, -sc[p]))
+        active[p, order[:keep]] = True
+    return active, sc
+
+
+def top_n(q_best: np.ndarray, s_best: np.ndarray, N: int, active: np.ndarray | None = None):
+    """Greedy top-N per pattern: repeatedly take the best remaining Q and, among the
+    entries within the relative tie window of it, the lowest template index.
+    Returns (template [n][N] int64, shift [n][N], score [n][N]); missing rows: -1, -1, -inf."""
+    n, K = q_best.shape
+    tk = np.full((n, N), -1, dtype=np.int64)
+    ts = np.full((n, N), -1, dtype=np.int64)
+    tq = np.full((n, N), -np.inf)
+    for p in range(n):
+        q = q_best[p].copy()
+        if active is not None:
+            q[~active[p]] = -np.inf
+        for j in range(N):
+            best = np.max(q)
+            if best == -np.inf:
+                break
+            thr = best - TIE_REL * abs(best)
+            k = int(np.flatnonzero(q >= thr)[0])
+            tk[p, j], ts[p, j], tq[p, j] = k, s_best[p, k], best
+            q[k] = -np.inf
+    return tk, ts, tq
+
+
+def index(frames: np.ndarray, lib: Library, gamma: float = 0.5, subtract: float = 0.0,
+          prefilter_fraction: float = 1.0, N: int = 5, centre=None):
+    """The whole path for a batch of frames; returns a dict of FP64 results."""
+    P = polar(frames, lib.n_r, lib.n_theta, lib.dr, gamma, subtract, centre)
+    active = None
+    if prefilter_fraction < 1.0:
+        active, _ = prefilter(P, lib, prefilter_fraction)
+    q, s = scores(P, lib, active)
+    tk, tsh, tq = top_n(q, s, N, active)
+    return dict(polar=P, q_best=q, s_best=s, active=active, template=tk, shift=tsh, score=tq,
+                angle_deg=np.where(tsh >= 0, tsh * (360.0 / lib.n_theta), np.nan),
+                mirror=np.where(tk >= 0, tk >= lib.K0 if lib.mirror else False, False))
+
+
+# ----------------------------------------------------------------------------------
+# Dense forms of the same correlation (the contraction the tensor-core path computes)
+# ----------------------------------------------------------------------------------
+
+def dense_scores(P: np.ndarray, lib: Library) -> np.ndarray:
+    """C[k, s] = sum_{r,theta} T_k[r, theta] P[r, (theta + s) mod n_theta] with every
+    template rendered dense, for one polar image P [n_r][n_theta]; returns Q[k][s]."""
+    n_theta = lib.n_theta
+    nP = math.sqrt(float(np.sum(P * P)))
+    out = np.zeros((lib.K, n_theta))
+    # circulant stack: Pc[s] = P rolled so Pc[s][r, theta] = P[r, (theta + s) mod n_theta]
+    Pc = np.stack([np.roll(P, -s, axis=1) for s in range(n_theta)])          # [s][r][theta]
+    flat = Pc.reshape(n_theta, -1)
+    for k in range(lib.K):
+        T = lib.dense(k).reshape(-1)
+        d = nP * lib.norm[k]
+        out[k] = (flat @ T) / d if d > 0 else 0.0
+    return out
+
+
+def dft_scores(P: np.ndarray, lib: Library) -> np.ndarray:
+    """The same Q[k][s] through the angular DFT: with X^[r, m] = sum_theta X[r, theta]
+    e^{-2 pi i m theta / n}, C[k, s] = (1/n) sum_m e^{+2 pi i m s / n} sum_r
+    conj(T^_k[r, m]) P^[r, m] (correlation theorem along theta, then a sum over r)."""
+    n_theta = lib.n_theta
+    nP = math.sqrt(float(np.sum(P * P)))
+    Ph = np.fft.fft(P, axis=1)
+    out = np.zeros((lib.K, n_theta))
+    for k in range(lib.K):
+        Th = np.fft.fft(lib.dense(k), axis=1)
+        G = np.sum(np.conj(Th) * Ph, axis=0)                   # [m]
+        C = np.fft.ifft(G).real
+        d = nP * lib.norm[k]
+        out[k] = C / d if d > 0 else 0.0
+    return out

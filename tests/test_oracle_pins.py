@@ -1,0 +1,284 @@
+"""Pins for the FP64 oracle: closed forms, invariants, brute force and the paper's worked
+example.  None of these compares the oracle with itself; each would fail on a plausible
+mistake (dropped term, wrong sign or index, swapped axes, wrong tie rule)."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2111_07347_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_lib(rng, K=6, n_r=12, n_theta=24, spots=(2, 5), mirror=False):
+    ts = synth.random_templates(rng, K, spots=spots, r_range=(1.0, n_r - 1.5))
+    ts.mirror = mirror
+    return ts, O.prepare_library(ts, n_r, n_theta, 1.0, mirror=mirror)
+
+
+# ------------------------------------------------------------------ Eq. 1 itself
+
+def test_brute_force_tiny_all_shifts():
+    """Q(k, s) from the dense template image and np.roll, written out per (k, s), equals the
+    oracle's sparse loop; argmax / lowest-shift / lowest-template rules hold."""
+    rng = np.random.default_rng(7)
+    n_r, n_theta = 8, 8
+    ts = synth.random_templates(rng, 3, spots=(1, 4), r_range=(0.0, 7.4))
+    lib = O.prepare_library(ts, n_r, n_theta)
+    P = rng.random((2, n_r, n_theta))
+    full = O.scores_full(P, lib)
+    for p in range(2):
+        nP = math.sqrt(sum(P[p, j, k] ** 2 for j in range(n_r) for k in range(n_theta)))
+        for k in range(lib.K):
+            T = np.zeros((n_r, n_theta))
+            for i in range(lib.off[k], lib.off[k + 1]):
+                T[lib.ri[i], lib.ti[i]] += lib.I[i]
+            nT = math.sqrt(float((T * T).sum()))
+            for s in range(n_theta):
+                num = 0.0
+                for j, t in itertools.product(range(n_r), range(n_theta)):
+                    num += T[j, t] * P[p, j, (t + s) % n_theta]
+                assert abs(full[p, k, s] - num / (nP * nT)) < 1e-12
+    q, sb = O.scores(P, lib)
+    for p in range(2):
+        for k in range(lib.K):
+            assert q[p, k] == pytest.approx(full[p, k].max(), abs=1e-15)
+            assert sb[p, k] == int(np.argmax(full[p, k]))
+
+
+def test_q_equals_one_for_rolled_template():
+    """Cauchy-Schwarz: Q <= 1 with equality iff P is proportional to the template image
+    shifted by m columns; the oracle must return (k, m) with Q = 1."""
+    rng = np.random.default_rng(11)
+    ts, lib = _small_lib(rng, K=8, n_r=16, n_theta=36, spots=(3, 7))
+    for k, m in [(0, 0), (3, 5), (7, 35)]:
+        T = lib.dense(k)
+        P = 2.5 * np.roll(T, m, axis=1)[None]          # P[r, t + m] = T[r, t]
+        q, s = O.scores(P, lib)
+        assert abs(q[0, k] - 1.0) < 1e-12
+        assert s[0, k] == m
+        assert np.all(q[0] <= 1.0 + 1e-12)
+        tk, tsh, tq = O.top_n(q, s, 3)
+        assert tk[0, 0] == k and tsh[0, 0] == m
+
+
+def test_q_bound_and_sign():
+    rng = np.random.default_rng(3)
+    ts, lib = _small_lib(rng, K=10, n_r=10, n_theta=20)
+    P = rng.normal(size=(4, 10, 20))
+    q, _ = O.scores(P, lib)
+    assert np.all(q <= 1 + 1e-12) and np.all(q >= -1 - 1e-12)
+    q2, _ = O.scores(-P, lib)
+    full = O.scores_full(P, lib)
+    assert np.allclose(q2, -full.min(axis=2), atol=1e-14)
+
+
+def test_linearity_gamma_one():
+    """With gamma = 1 and no subtraction, scaling the frame leaves Q unchanged."""
+    ts, scan, prm = synth.tiny_workload(n_side=2)
+    lib = O.prepare_library(ts, 60, 180)
+    P1 = O.polar(scan.frames, 60, 180, gamma=1.0)
+    P2 = O.polar(scan.frames * np.float32(3.0), 60, 180, gamma=1.0)
+    q1, s1 = O.scores(P1, lib)
+    q2, s2 = O.scores(P2, lib)
+    assert np.allclose(q1, q2, rtol=1e-12, atol=1e-14)
+    assert np.array_equal(s1, s2)
+
+
+# ------------------------------------------------------------------ polar transform
+
+def test_polar_constant_and_gamma_subtract():
+    f = np.full((1, 32, 32), 9.0, dtype=np.float32)
+    P = O.polar(f, 14, 40, gamma=1.0)
+    assert np.allclose(P, 9.0, atol=1e-12)
+    P = O.polar(f, 14, 40, gamma=0.5, subtract=0.25)
+    assert np.allclose(P, 3.0 - 0.25, atol=1e-12)
+
+
+def test_polar_linear_ramp_is_exact():
+    """Bilinear interpolation reproduces a linear function: P(r, theta) =
+    a (cx + r cos theta) + b (cy + r sin theta) + d  (x = column, y = row)."""
+    H, W = 40, 48
+    a, b, d = 0.75, -1.25, 100.0
+    yy, xx = np.mgrid[0:H, 0:W]
+    f = (a * xx + b * yy + d).astype(np.float32)[None]
+    n_r, n_theta = 18, 72
+    P = O.polar(f, n_r, n_theta, gamma=1.0)
+    cx, cy = (W - 1) / 2, (H - 1) / 2
+    for j in range(n_r):
+        for k in range(n_theta):
+            th = 2 * math.pi * k / n_theta
+            want = a * (cx + j * math.cos(th)) + b * (cy + j * math.sin(th)) + d
+            assert abs(P[0, j, k] - want) < 1e-9
+
+
+def test_polar_centre_and_gamma_order():
+    """r = 0 samples the centre: with the default centre ((W-1)/2, (H-1)/2) it is the mean of
+    the four central pixels after gamma (gamma first, then resampling)."""
+    f = np.zeros((1, 6, 6), dtype=np.float32)
+    f[0, 2, 2], f[0, 2, 3], f[0, 3, 2], f[0, 3, 3] = 1.0, 4.0, 9.0, 16.0
+    P = O.polar(f, 2, 12, gamma=0.5)
+    assert np.allclose(P[0, 0], (1 + 2 + 3 + 4) / 4.0, atol=1e-12)
+
+
+def test_polar_zero_outside_frame():
+    f = np.ones((1, 8, 8), dtype=np.float32)
+    P = O.polar(f, 5, 4, gamma=1.0)       # r = 4, theta = 0: x = 7.5 -> half the taps outside
+    assert abs(P[0, 4, 0] - 0.5) < 1e-12
+    assert abs(P[0, 4, 2] - 0.5) < 1e-12  # theta = pi: x = -0.5
+
+
+def test_rotation_equivariance_rot90():
+    """np.rot90 with the default centre rolls the polar image by n_theta/4 columns, so the
+    best template and its Q are unchanged and the shift moves by -n_theta/4."""
+    ts, scan, prm = synth.tiny_workload(n_side=3)
+    lib = O.prepare_library(ts, 60, 180)
+    f = scan.frames
+    fr = np.ascontiguousarray(np.rot90(f, k=1, axes=(1, 2)))
+    P, Pr = O.polar(f, 60, 180), O.polar(fr, 60, 180)
+    assert np.allclose(Pr, np.roll(P, -45, axis=2), atol=1e-9)
+    q, s = O.scores(P, lib)
+    qr, sr = O.scores(Pr, lib)
+    assert np.allclose(q, qr, rtol=1e-10, atol=1e-13)
+    b = np.argmax(q, axis=1)
+    br = np.argmax(qr, axis=1)
+    assert np.array_equal(b, br)
+    rows = np.arange(len(b))
+    assert np.array_equal(sr[rows, br], (s[rows, b] - 45) % 180)
+
+
+def test_mirror_flip_equivariance():
+    """A vertical flip (y -> H-1-y) reflects the pattern across y = 0, so template k scores on
+    the flipped frame what its mirror k +- K0 scores on the original, at shift -s."""
+    rng = synth.make_rng(0)
+    ts = synth.random_templates(rng, 40)
+    ts.mirror = True
+    scan = synth.render_scan(rng, ts, 6, 128, 128, n_theta=180, dtype=np.float32)
+    lib = O.prepare_library(ts, 60, 180, mirror=True)
+    K0 = lib.K0
+    f = scan.frames
+    ff = np.ascontiguousarray(f[:, ::-1, :])
+    q, s = O.scores(O.polar(f, 60, 180), lib)
+    qf, sf = O.scores(O.polar(ff, 60, 180), lib)
+    perm = np.concatenate([np.arange(K0, 2 * K0), np.arange(K0)])
+    assert np.allclose(qf, q[:, perm], rtol=1e-9, atol=1e-12)
+    b = np.argmax(q, axis=1)
+    bf = np.argmax(qf, axis=1)
+    assert np.array_equal(bf, perm[b])
+    rows = np.arange(len(b))
+    assert np.array_equal(sf[rows, bf], (-s[rows, b]) % 180)
+
+
+# ------------------------------------------------------------------ library preparation
+
+def test_round_spot_rules():
+    assert O.round_spot(2.5, 0.0, 360, 1.0) == (3, 0)       # half-way rounds up
+    assert O.round_spot(2.49, 0.0, 360, 1.0) == (2, 0)
+    assert O.round_spot(5.0, math.pi, 180, 1.0) == (5, 90)
+    assert O.round_spot(5.0, -1e-9, 360, 1.0) == (5, 0)     # wraps to [0, 2pi) then rounds to 360 -> 0
+    assert O.round_spot(5.0, -math.pi / 2, 4, 1.0) == (5, 3)
+    assert O.round_spot(7.0, 0.0, 8, 2.0) == (4, 0)          # dr = 2 px
+
+
+def test_golden_angle_step():
+    """Section 2.2 worked example: a polar image 360 pixels wide gives a 1 degree in-plane step."""
+    rows = [ln.split("#")[0].split() for ln in open(os.path.join(GOLDEN, "angle_step.txt"))]
+    rows = [r for r in rows if r]
+    for n_theta, step_deg in rows:
+        n_theta, step_deg = int(n_theta), float(step_deg)
+        # a template spot at angle step_deg degrees rounds to column 1
+        assert O.round_spot(10.0, math.radians(step_deg), n_theta, 1.0) == (10, 1)
+        ts = synth.TemplateSet(np.array([0, 1]), np.array([10.0]), np.array([0.0]), np.array([1.0]))
+        lib = O.prepare_library(ts, 12, n_theta)
+        P = np.roll(lib.dense(0), 1, axis=1)[None]
+        tk, tsh, tq = O.top_n(*O.scores(P, lib), 1)
+        assert tsh[0, 0] * 360.0 / n_theta == pytest.approx(step_deg)
+
+
+def test_prepare_merge_drop_mirror_unit():
+    ts = synth.TemplateSet(
+        offsets=np.array([0, 4]),
+        a=np.array([0.10, 0.101, 0.05, 2.0]),        # 1/A; px_per_unit 100 -> 10, 10.1, 5, 200 px
+        b=np.array([0.0, 0.0, 0.05, 0.0]),
+        intensity=np.array([2.0, 3.0, 5.0, 7.0]),
+        coords="xy", px_per_unit=100.0, mirror=True)
+    lib = O.prepare_library(ts, 64, 360)
+    assert lib.K == 2 and lib.K0 == 1
+    sp0 = sorted(zip(lib.ri[:lib.off[1]], lib.ti[:lib.off[1]], lib.I[:lib.off[1]]))
+    # first two spots merge at (10, 0); (5, 5) at 45 deg -> (7, 45); 200 px dropped
+    assert sp0 == [(7, 45, 5.0), (10, 0, 5.0)]
+    sp1 = sorted(zip(lib.ri[lib.off[1]:], lib.ti[lib.off[1]:], lib.I[lib.off[1]:]))
+    assert sp1 == [(7, 315, 5.0), (10, 0, 5.0)]            # mirror: ky -> -ky
+    assert lib.norm[0] == pytest.approx(math.sqrt(50.0))
+    assert lib.radial[0, 10] == 5.0 and lib.radial[0, 7] == 5.0
+    libu = O.prepare_library(ts, 64, 360, unit_intensity=True)
+    sp = sorted(zip(libu.ri[:libu.off[1]], libu.ti[:libu.off[1]], libu.I[:libu.off[1]]))
+    assert sp == [(7, 45, 1.0), (10, 0, 2.0)]
+
+
+# ------------------------------------------------------------------ pre-filter and top-N
+
+def test_prefilter_identity_and_cosine():
+    rng = np.random.default_rng(5)
+    ts, lib = _small_lib(rng, K=9, n_r=10, n_theta=20, mirror=True)
+    P = rng.random((3, 10, 20))
+    act, sc = O.prefilter(P, lib, 1.0)
+    assert act.all()
+    # a polar image whose azimuthal sum equals R_T[k] scores cosine 1 for k (and its mirror)
+    k = 4
+    Pk = np.repeat((lib.radial[k] / 20.0)[:, None], 20, axis=1)[None]
+    act, sc = O.prefilter(Pk, lib, 0.1)
+    assert sc[0, k] == pytest.approx(1.0, abs=1e-12)
+    assert sc[0, k + lib.K0] == sc[0, k]
+    assert act.sum() == O.keep_count(0.1, lib.K) == 2
+    assert act[0, k] and act[0, k + lib.K0]
+    act, _ = O.prefilter(Pk, lib, 0.05)                   # keep 1: tie -> lower index
+    assert act[0, k] and not act[0, k + lib.K0]
+
+
+def test_top_n_order_ties_and_padding():
+    q = np.array([[0.5, 0.9, 0.9, 0.1, 0.9 * (1 + 1e-13)]])
+    s = np.array([[1, 2, 3, 4, 5]], dtype=np.int32)
+    tk, tsh, tq = O.top_n(q, s, 4)
+    assert list(tk[0]) == [1, 2, 4, 0]                     # ties within 1e-12 -> lower index
+    act = np.array([[True, False, False, True, False]])
+    tk, tsh, tq = O.top_n(q, s, 4, act)
+    assert list(tk[0]) == [0, 3, -1, -1] and np.isneginf(tq[0, 2])
+
+
+def test_shift_tie_lowest():
+    """A template invariant under a half turn ties at s and s + n_theta/2: lowest wins."""
+    ts = synth.TemplateSet(np.array([0, 2]), np.array([5.0, 5.0]), np.array([0.3, 0.3 + math.pi]),
+                           np.array([1.0, 1.0]))
+    lib = O.prepare_library(ts, 8, 36)
+    P = np.roll(lib.dense(0), 25, axis=1)[None]
+    q, s = O.scores(P, lib)
+    assert s[0, 0] == 25 - 18 and abs(q[0, 0] - 1) < 1e-12
+
+
+# ------------------------------------------------------------------ dense forms
+
+def test_dense_and_dft_equal_sparse():
+    rng = np.random.default_rng(9)
+    ts, lib = _small_lib(rng, K=5, n_r=12, n_theta=30, spots=(2, 8))
+    P = rng.random((1, 12, 30))
+    full = O.scores_full(P, lib)[0]
+    assert np.allclose(O.dense_scores(P[0], lib), full, atol=1e-12)
+    assert np.allclose(O.dft_scores(P[0], lib), full, atol=1e-12)
+
+
+# ------------------------------------------------------------------ ground truth (informative)
+
+def test_tiny_workload_recovers_truth():
+    ts, scan, prm = synth.tiny_workload()
+    lib = O.prepare_library(ts, 60, 180)
+    r = O.index(scan.frames, lib, N=5)
+    assert np.mean(r["template"][:, 0] == scan.template) > 0.95
+    ex = scan.exact
+    m = np.round(scan.angle[ex] / (2 * math.pi / 180)).astype(int) % 180
+    err = np.abs(((r["shift"][ex, 0] - m) + 90) % 180 - 90)
+    assert np.mean(err <= 1) > 0.95
