@@ -1,0 +1,224 @@
+/*
+ * tmgb -- GB300-native template-matching orientation mapping (indexing hot path).
+ *
+ * C ABI of libtmgb.so.  Plain pointers and sizes only.  Every function returns an int
+ * status (TM_OK = 0); on failure tm_last_error() gives a message for the calling thread.
+ * No function aborts, traps or falls back to the CPU: without a usable GPU the calls
+ * fail with TM_ERR_CUDA.
+ *
+ * Method (arXiv 2111.07347, Section 2.2): every diffraction pattern P is compared with
+ * every template T of a library by the correlation index of Eq. 1,
+ *     Q = sum_i P(x_i) T(x_i) / ( sqrt(sum_i P(x_i)^2) sqrt(sum_i T(x_i)^2) ),
+ * evaluated in polar coordinates about the direct beam, with the template slid along
+ * the azimuthal axis with wraparound; the best Q and its in-plane angle are kept per
+ * template and the top N templates are returned.
+ *
+ * Device pointers: arguments named *_dev are device memory owned by the caller (for
+ * example torch.Tensor.data_ptr()).  Work is enqueued on the caller's CUDA stream
+ * (`stream`, a cudaStream_t; NULL = legacy default stream) and is complete when that
+ * stream is synchronised.  Host pointers are read before the call returns.
+ *
+ * Threading: one context may be used from several host threads; calls are serialised
+ * on the host by the context, and on the GPU each call waits for the previous call of
+ * the same context (whatever stream it ran on), because calls share the context's
+ * workspace.
+ */
+#ifndef TMGB_H
+#define TMGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+    TM_OK = 0,
+    TM_ERR_INVALID_ARG = 1,  /* bad pointer, size, grid or parameter (NaN, out of range)   */
+    TM_ERR_OOM = 2,          /* device allocation failed or the context's HBM budget is hit */
+    TM_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error)     */
+    TM_ERR_TIMEOUT = 4,      /* a bounded wait ran out                                     */
+    TM_ERR_BUSY = 5,         /* a non-blocking submit found no room                        */
+    TM_ERR_CANCELLED = 6,    /* the request was cancelled                                  */
+    TM_ERR_NOT_FOUND = 7,    /* unknown library id or ticket                               */
+    TM_ERR_UNSUPPORTED = 8   /* valid request this build does not implement                */
+};
+
+enum { TM_DTYPE_U16 = 0, TM_DTYPE_F32 = 1 };             /* frame element type            */
+enum { TM_COORDS_POLAR = 0, TM_COORDS_XY = 1 };          /* template spot coordinates     */
+enum { TM_LIB_MIRROR = 1u, TM_LIB_UNIT_INTENSITY = 2u }; /* library flags                 */
+enum { TM_PATH_FP32_SPARSE = 0, TM_PATH_BF16_RESCORE = 1 };
+
+typedef struct tm_ctx tm_ctx;
+
+/* ---------------------------------------------------------------- libraries
+ * A template library (Section 2.1: each template is a list of reflections with
+ * coordinates (kx, ky)_i and intensities I_i at in-plane angle zero).  At load time the
+ * spots are put on the polar grid the library is built for (Section 2.2):
+ *   r_i = floor(r / dr + 1/2),  t_i = floor(u + 1/2) mod n_theta,
+ *   u = theta' / (2 pi / n_theta), theta' = theta reduced to [0, 2 pi),
+ * computed in double precision; spots with r_i >= n_r are dropped; spots landing on the
+ * same polar pixel are merged by summing intensity; with TM_LIB_MIRROR every template
+ * gets a mirror copy made by reflecting its spots across y = 0 (theta -> -theta) before
+ * rounding (Section 2.2, Fig. 2 caption), stored at index k + n_templates; with
+ * TM_LIB_UNIT_INTENSITY every input spot has intensity 1 before merging (Section 4.3).
+ * The template norm sqrt(sum I^2) of Eq. 1 is taken over the merged spots.  A template
+ * whose merged spot set is invariant under a rotation by 2 pi / n (n dividing n_theta)
+ * is only slid over n_theta / n shifts (its scores repeat exactly beyond).
+ */
+typedef struct tm_library_desc {
+    int64_t n_templates;          /* K0 >= 1                                              */
+    const int64_t* spot_offsets;  /* host [K0 + 1], CSR, offsets[0] = 0, non-decreasing   */
+    const double* spot_a;         /* host [S]: r in pixels (POLAR) or kx (XY)             */
+    const double* spot_b;         /* host [S]: theta in radians (POLAR) or ky (XY)        */
+    const double* intensity;      /* host [S], finite (ignored with UNIT_INTENSITY)       */
+    int32_t coords;               /* TM_COORDS_POLAR or TM_COORDS_XY                      */
+    uint32_t flags;               /* TM_LIB_* bits                                        */
+    double px_per_unit;           /* XY: detector pixels per unit of (kx, ky); > 0        */
+    int32_t n_r;                  /* polar grid: radii r_j = j * dr, j in [0, n_r)        */
+    int32_t n_theta;              /* polar grid: angles 2 pi k / n_theta, k in [0, n_theta) */
+    double dr;                    /* radial step in pixels, > 0                           */
+} tm_library_desc;
+
+typedef struct tm_library_info {
+    int64_t n_templates;          /* K, including mirror copies                          */
+    int64_t n_base;               /* K0                                                  */
+    int64_t n_spots;              /* merged spots over all K templates                   */
+    int32_t max_spots;            /* largest merged spot count                           */
+    int32_t mirror;               /* 1 if mirror copies were added                       */
+    int32_t n_r, n_theta;
+    double dr;
+    int64_t n_symmetric;          /* templates with rotational order > 1                 */
+    int64_t macs_per_pattern;     /* sum_k spots_k * n_theta / order_k (sparse work)     */
+    int64_t device_bytes;         /* device memory held by the library                   */
+} tm_library_info;
+
+/* ---------------------------------------------------------------- indexing
+ * Parameters of the per-pattern path (Section 2.2 and Section 4.1/4.3 preprocessing):
+ * g = max(x, 0)^gamma - subtract per raw pixel, then bilinear polar resampling about
+ * (cx, cy) (x = column, y = row; zero outside the frame), then [pre-filter], then Q. */
+typedef struct tm_index_params {
+    double gamma;                 /* > 0; 0.5 uses sqrt                                  */
+    double subtract;              /* constant subtracted after gamma (0 = none)          */
+    double cx, cy;                /* beam centre in pixels; NaN -> ((W-1)/2, (H-1)/2)    */
+    double prefilter_fraction;    /* (0, 1]: keep ceil(f K) templates by radial cosine   */
+    int32_t top_n;                /* N >= 1 results per pattern and library              */
+    int32_t path;                 /* TM_PATH_FP32_SPARSE or TM_PATH_BF16_RESCORE         */
+    int32_t rescore_k;            /* BF16 path: candidates rescored exactly (default 64) */
+    int32_t reserved;
+} tm_index_params;
+
+/* One result row.  Rows of a pattern are ordered by (score desc, template asc); when
+ * fewer than N templates take part the tail rows have template_index = -1 and
+ * score = -inf. */
+typedef struct tm_hit {
+    int32_t template_index;       /* expanded index k (mirror copies at k >= n_base)     */
+    int32_t shift;                /* best azimuthal shift s (lowest among exact ties)    */
+    float score;                  /* Q of Eq. 1                                          */
+    float angle_deg;              /* in-plane angle phi1 = s * 360 / n_theta             */
+    int32_t mirror;               /* 1 if the template is a mirror copy                  */
+} tm_hit;
+
+typedef struct tm_stats {
+    int64_t patterns;             /* patterns indexed by the call                        */
+    int64_t correlations;         /* (pattern, template, shift) triples evaluated        */
+    int64_t templates_scored;     /* (pattern, template) pairs scored exactly            */
+    int64_t launches;             /* kernels launched by the call                        */
+} tm_stats;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory
+ * the context allocates (libraries + workspace); 0 = no cap.  The context owns every
+ * library and workspace buffer it allocates; tm_destroy frees them. */
+int tm_create(int device, size_t hbm_budget_bytes, tm_ctx** out);
+void tm_destroy(tm_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next
+ * call on this thread. */
+const char* tm_last_error(void);
+
+/* Copy a library to the device (see the library notes above).  *lib_id receives an id
+ * >= 0.  Errors: TM_ERR_INVALID_ARG for a malformed descriptor, TM_ERR_OOM. */
+int tm_load_library(tm_ctx* ctx, const tm_library_desc* desc, int* lib_id);
+int tm_unload_library(tm_ctx* ctx, int lib_id);
+int tm_library_info_get(tm_ctx* ctx, int lib_id, tm_library_info* out);
+
+/* Copy the library's rounded, merged templates back to host buffers sized from
+ * tm_library_info: offsets [K + 1], r [n_spots], t [n_spots], intensity [n_spots]
+ * (float, as used on the device), norm [K] (float sqrt(sum I^2)), order [K] (rotational
+ * order n_k).  Any pointer may be NULL to skip it.  Synchronous. */
+int tm_library_export(tm_ctx* ctx, int lib_id, int64_t* offsets, int32_t* r, int32_t* t,
+                      float* intensity, float* norm, int32_t* order);
+
+/* The host half of tm_load_library without a device: validates the descriptor and puts
+ * the templates on the polar grid exactly as tm_load_library does.  Call once with NULL
+ * arrays to get the sizes in *info, then again with host buffers as for
+ * tm_library_export.  info->device_bytes is 0.  Needs no GPU. */
+int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, int64_t* offsets,
+                            int32_t* r, int32_t* t, float* intensity, float* norm, int32_t* order);
+
+/* Stage 1 (Section 2.2, Fig. 2 (a)-(c)): gamma/subtract and bilinear polar resampling.
+ * frames_dev [n][H][W] (TM_DTYPE_U16 or TM_DTYPE_F32, row-major, contiguous);
+ * polar_dev [n][n_r][n_theta] float; norm_dev [n] float = sqrt(sum over the polar image
+ * of P^2) (nullable); radial_dev [n][n_r] float = sum over theta (nullable).
+ * Uses params->gamma, subtract, cx, cy. */
+int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,
+                       int32_t dtype, int64_t n, int32_t H, int32_t W, int32_t n_r,
+                       int32_t n_theta, double dr, float* polar_dev, float* norm_dev,
+                       float* radial_dev, void* stream);
+
+/* Stage 2 (Section 2.2, azimuthally integrated pre-filter, Fig. 3): score_k =
+ * R_P . R_T,k / (|R_P| |R_T,k|) from radial_dev [n][n_r] (Stage 1 output); keeps the
+ * ceil(fraction K) best per pattern, ties to the lower template index.  mask_dev
+ * [n][ceil(K/32)] uint32 receives bit (k % 32) of word k / 32 set for kept templates;
+ * score_dev [n][K] float (nullable). */
+int tm_prefilter(tm_ctx* ctx, int lib_id, const float* radial_dev, int64_t n, double fraction,
+                 uint32_t* mask_dev, float* score_dev, void* stream);
+
+/* Stage 3 (Eq. 1 at every shift with wraparound, Section 2.2, Fig. 2 (e)): for each
+ * pattern and template the best Q and the lowest shift attaining it, in FP32.
+ * polar_dev / norm_dev from Stage 1; mask_dev from Stage 2 or NULL (all templates).
+ * q_dev [n][K] float and s_dev [n][K] int32; masked-out templates get -inf and -1. */
+int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev,
+                 int64_t n, const uint32_t* mask_dev, float* q_dev, int32_t* s_dev,
+                 void* stream);
+
+/* The whole path for a batch: frames -> polar -> [pre-filter] -> Q -> top-N, for each
+ * of n_libs libraries (all built for the same polar grid).  out_dev [n_libs][n][top_n]
+ * tm_hit.  centres_dev must be NULL in this build (per-pattern centres:
+ * TM_ERR_UNSUPPORTED).  stats (host, nullable) receives counts for the call. */
+int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,
+                      int32_t dtype, int64_t n, int32_t H, int32_t W, const float* centres_dev,
+                      const int32_t* lib_ids, int32_t n_libs, tm_hit* out_dev,
+                      tm_stats* stats, void* stream);
+
+/* Per-stage device time, measured with CUDA events recorded on the stream each kernel
+ * is launched on (around every launch of the stage). */
+enum {
+    TM_STAGE_POLAR = 0,       /* gamma + polar resampling                               */
+    TM_STAGE_PREFILTER = 1,   /* radial norms, scores and selection                     */
+    TM_STAGE_SPARSE = 2,      /* FP32 sparse correlation + top-N                        */
+    TM_STAGE_DFT = 3,         /* angular DFT of the polar images (BF16 path)            */
+    TM_STAGE_DENSE = 4,       /* BF16 tensor-core pre-score (BF16 path)                 */
+    TM_STAGE_RESCORE = 5,     /* FP32 rescore of the candidates (BF16 path)             */
+    TM_STAGE_COUNT = 8
+};
+typedef struct tm_profile {
+    double ms[TM_STAGE_COUNT];        /* summed launch durations                        */
+    int64_t launches[TM_STAGE_COUNT]; /* kernel launches timed                           */
+} tm_profile;
+
+/* Enable (1) or disable (0) stage timing for later calls on ctx; resets the totals. */
+int tm_profile_enable(tm_ctx* ctx, int enable);
+/* Totals since the last enable/read; waits for the timed work to finish, then resets. */
+int tm_profile_read(tm_ctx* ctx, tm_profile* out);
+
+/* Default parameters: gamma 0.5, subtract 0, centre NaN, prefilter 1, top_n 5,
+ * FP32 sparse path, rescore_k 64. */
+void tm_index_params_default(tm_index_params* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMGB_H */

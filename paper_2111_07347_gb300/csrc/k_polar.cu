@@ -1,0 +1,128 @@
+// Stage 1: gamma / constant subtraction of the raw frame and bilinear resampling onto
+// the polar grid about the direct beam (arXiv 2111.07347, Section 2.2, Fig. 2 (a)-(c);
+// the gamma and subtraction of Sections 2.2 and 4.3).  By-products for later stages:
+// the image norm sqrt(sum P'^2) of Eq. 1 and the azimuthal sums R_P[j] used by the
+// pre-filter (Section 2.2, Fig. 3).
+//
+// One CTA per pattern (grid-stride).  Thread k owns polar column k; rows are walked in
+// order, so the writes of a row are coalesced.  Tap positions and fractions come from a
+// table built on the host in double precision for the call's centre, so only the
+// weights are rounded to float.  Reductions run in a fixed order: the result does not
+// depend on the grid size or on other patterns of the batch.
+#include "tm_internal.h"
+
+namespace tmgb {
+namespace {
+
+struct Gamma {
+    int mode;            // 0: sqrt (gamma = 0.5), 1: identity, 2: powf
+    float g, sub;
+    __device__ __forceinline__ float operator()(float v) const {
+        v = fmaxf(v, 0.0f);
+        float r = mode == 0 ? sqrtf(v) : (mode == 1 ? v : powf(v, g));
+        return r - sub;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ float tap(const T* frame, int H, int W, int x, int y, const Gamma& gm) {
+    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return 0.0f;  // zero outside
+    return gm((float)__ldg(frame + (size_t)y * W + x));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
+             const int32_t* __restrict__ txy, const float* __restrict__ tfx,
+             const float* __restrict__ tfy, Gamma gm, int n_r, int n_theta,
+             float* __restrict__ polar, float* __restrict__ pnorm, float* __restrict__ radial) {
+    extern __shared__ float smem[];
+    const int nw = blockDim.x >> 5;
+    float* part = smem;                         // [n_r][nw] row partial sums
+    float* red = smem + (size_t)n_r * nw;       // [blockDim] norm partials
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
+        const T* frame = frames + (size_t)p * H * W;
+        float* out = polar + (size_t)p * n_r * n_theta;
+        float s2 = 0.0f, c2 = 0.0f;             // Kahan sum of P'^2 for this thread
+        for (int j = 0; j < n_r; ++j) {
+            float rowsum = 0.0f;
+            for (int k = threadIdx.x; k < n_theta; k += blockDim.x) {
+                const int idx = j * n_theta + k;
+                const int xy = __ldg(txy + idx);
+                const int x0 = (int)(int16_t)(xy & 0xffff);
+                const int y0 = xy >> 16;
+                const float fx = __ldg(tfx + idx), fy = __ldg(tfy + idx);
+                const float v00 = tap(frame, H, W, x0, y0, gm);
+                const float v10 = tap(frame, H, W, x0 + 1, y0, gm);
+                const float v01 = tap(frame, H, W, x0, y0 + 1, gm);
+                const float v11 = tap(frame, H, W, x0 + 1, y0 + 1, gm);
+                const float gx = 1.0f - fx, gy = 1.0f - fy;
+                const float v = gx * gy * v00 + fx * gy * v10 + gx * fy * v01 + fx * fy * v11;
+                out[idx] = v;
+                const float y = fmaf(v, v, -c2);
+                const float t = s2 + y;
+                c2 = (t - s2) - y;
+                s2 = t;
+                rowsum += v;
+            }
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
+            if (lane == 0) part[j * nw + warp] = rowsum;
+        }
+        red[threadIdx.x] = s2;
+        __syncthreads();
+        // fixed-order tree over the block (blockDim is a multiple of 32)
+        for (int w = 1; w < (int)blockDim.x; w <<= 1) {
+            const int i = threadIdx.x;
+            if ((i & (2 * w - 1)) == 0 && i + w < (int)blockDim.x) red[i] += red[i + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && pnorm) pnorm[p] = sqrtf(red[0]);
+        if (radial) {
+            for (int j = threadIdx.x; j < n_r; j += blockDim.x) {
+                float s = 0.0f;
+                for (int w = 0; w < nw; ++w) s += part[j * nw + w];
+                radial[(size_t)p * n_r + j] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
+                         const PolarTable& tab, double gamma, double subtract, int n_r,
+                         int n_theta, float* polar, float* pnorm, float* radial,
+                         cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    Gamma gm;
+    gm.mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
+    gm.g = (float)gamma;
+    gm.sub = (float)subtract;
+    int threads = ((n_theta + 31) / 32) * 32;
+    if (threads > 1024) threads = 1024;
+    const int nw = threads / 32;
+    const size_t smem = ((size_t)n_r * nw + threads) * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e;
+        if (dtype == TM_DTYPE_U16)
+            e = cudaFuncSetAttribute(polar_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else
+            e = cudaFuncSetAttribute(polar_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t grid64 = n < 65535 * 16 ? n : 65535 * 16;
+    const int grid = (int)grid64;
+    if (dtype == TM_DTYPE_U16)
+        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.fx,
+                                                          tab.fy, gm, n_r, n_theta, polar, pnorm, radial);
+    else
+        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.fx,
+                                                       tab.fy, gm, n_r, n_theta, polar, pnorm, radial);
+    return cudaGetLastError();
+}
+
+}  // namespace tmgb

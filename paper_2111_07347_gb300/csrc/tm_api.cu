@@ -1,0 +1,849 @@
+// Host side of libtmgb.so: the C ABI declared in include/tmgb.h.
+//
+// Library loading follows arXiv 2111.07347 Section 2.1 (templates are spot lists at
+// in-plane angle zero) and Section 2.2 (spot coordinates rounded to the nearest polar
+// pixel; mirror templates by reflecting across y = 0; norms of Eq. 1 precomputed);
+// Section 4.3 gives the unit-intensity option.  All template geometry is done in double
+// precision here; the device receives float intensities and packed integer addresses.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "tm_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(TM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define TM_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct Library {
+    int64_t K = 0, K0 = 0;
+    int mirror = 0, n_r = 0, n_theta = 0;
+    double dr = 1.0;
+    int64_t n_sym = 0, macs = 0;
+    int max_spots = 0;
+    // host copies (exported for tests)
+    std::vector<int64_t> off;
+    std::vector<int32_t> r, t, order;
+    std::vector<float> I, norm;
+    // device
+    int32_t* d_off = nullptr;
+    int2* d_spot = nullptr;
+    float* d_norm = nullptr;
+    int32_t* d_nshift = nullptr;
+    float* d_radial = nullptr;
+    float* d_rnorm = nullptr;
+    size_t bytes = 0;
+};
+
+struct Buffer {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct PolarTableDev {
+    int32_t* xy = nullptr;
+    float* fx = nullptr;
+    float* fy = nullptr;
+    size_t bytes = 0;
+};
+
+using TableKey = std::tuple<int, int, int, int, double, double, double>;
+
+}  // namespace
+
+struct tm_ctx {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    int num_sms = 0;
+    std::mutex mu;
+    std::map<int, std::unique_ptr<Library>> libs;
+    int next_id = 0;
+    std::map<TableKey, PolarTableDev> tables;
+    std::map<std::string, Buffer> ws;
+    cudaEvent_t ws_event = nullptr;
+    // stage timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> ev_marks;
+};
+
+namespace {
+
+int dev_alloc(tm_ctx* ctx, void** p, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(TM_ERR_OOM, "%s: %zu bytes exceed the context budget (%zu of %zu used)", what, bytes,
+                    ctx->used, ctx->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TM_ERR_OOM, "%s: cudaMalloc(%zu) failed: %s", what, bytes, cudaGetErrorString(e));
+    }
+    ctx->used += bytes;
+    return TM_OK;
+}
+
+void dev_free(tm_ctx* ctx, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    ctx->used -= std::min(ctx->used, bytes ? bytes : 16);
+}
+
+// Workspace buffer `name` of at least `bytes`, grown on demand.
+int workspace(tm_ctx* ctx, const std::string& name, size_t bytes, void** out) {
+    Buffer& b = ctx->ws[name];
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cudaDeviceSynchronize();
+            dev_free(ctx, b.p, b.bytes);
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        size_t want = bytes + bytes / 8;
+        int rc = dev_alloc(ctx, &b.p, want, name.c_str());
+        if (rc) return rc;
+        b.bytes = want;
+    }
+    *out = b.p;
+    return TM_OK;
+}
+
+// Stage timer: records an event pair around the launches of one stage when profiling.
+struct StageTimer {
+    tm_ctx* ctx;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    static cudaEvent_t take(tm_ctx* c) {
+        if (!c->ev_pool.empty()) {
+            cudaEvent_t e = c->ev_pool.back();
+            c->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    StageTimer(tm_ctx* c, int s, cudaStream_t stream) : ctx(c), stage(s), st(stream) {
+        if (!ctx->profiling) return;
+        a = take(ctx);
+        b = take(ctx);
+        if (a && b) cudaEventRecord(a, st);
+    }
+    ~StageTimer() {
+        if (!a || !b) return;
+        cudaEventRecord(b, st);
+        ctx->ev_marks.emplace_back(stage, a, b);
+    }
+};
+
+// ---------------------------------------------------------------- template geometry
+
+struct Merged {
+    std::vector<int32_t> r, t;
+    std::vector<double> I;
+};
+
+// Nearest polar pixel of a spot (Section 2.2): r = floor(r_px / dr + 1/2),
+// t = floor(theta' / (2 pi / n_theta) + 1/2) mod n_theta, theta' in [0, 2 pi).
+inline void round_spot(double r_px, double theta, int n_theta, double dr, int64_t* ri, int64_t* ti) {
+    double th = fmod(theta, 2.0 * kPi);
+    if (th < 0.0) th += 2.0 * kPi;
+    const double step = 2.0 * kPi / n_theta;
+    int64_t t = (int64_t)floor(th / step + 0.5);
+    t %= n_theta;
+    *ti = t;
+    *ri = (int64_t)floor(r_px / dr + 0.5);
+}
+
+// Largest n dividing n_theta such that the merged spot multiset is invariant under a
+// rotation by n_theta / n columns (exact comparison of integer positions and intensities).
+int rotational_order(const Merged& m, int n_theta) {
+    const size_t s = m.r.size();
+    if (s == 0) return n_theta;
+    std::vector<std::tuple<int32_t, int32_t, double>> a(s), b(s);
+    for (size_t i = 0; i < s; ++i) a[i] = std::make_tuple(m.r[i], m.t[i], m.I[i]);
+    std::sort(a.begin(), a.end());
+    for (int n = n_theta; n >= 2; --n) {
+        if (n_theta % n) continue;
+        const int sh = n_theta / n;
+        for (size_t i = 0; i < s; ++i)
+            b[i] = std::make_tuple(m.r[i], (int32_t)((m.t[i] + sh) % n_theta), m.I[i]);
+        std::sort(b.begin(), b.end());
+        if (a == b) return n;
+    }
+    return 1;
+}
+
+// Host half of library loading: validation, rounding, merging, mirrors, norms, orders.
+struct Prepared {
+    std::vector<int2> spot;
+    std::vector<int32_t> nshift;
+    std::vector<double> radial, rnorm;
+};
+
+int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
+    if (!d) return fail(TM_ERR_INVALID_ARG, "tm_load_library: desc is NULL");
+    if (d->n_templates < 1 || d->n_templates > (1 << 24))
+        return fail(TM_ERR_INVALID_ARG, "tm_load_library: n_templates=%lld out of range", (long long)d->n_templates);
+    if (!d->spot_offsets) return fail(TM_ERR_INVALID_ARG, "tm_load_library: spot_offsets is NULL");
+    if (d->coords != TM_COORDS_POLAR && d->coords != TM_COORDS_XY)
+        return fail(TM_ERR_INVALID_ARG, "tm_load_library: coords=%d invalid", d->coords);
+    if (d->coords == TM_COORDS_XY && !(d->px_per_unit > 0.0 && isfinite(d->px_per_unit)))
+        return fail(TM_ERR_INVALID_ARG, "tm_load_library: px_per_unit must be > 0");
+    if (d->n_r < 1 || d->n_r > 4096) return fail(TM_ERR_INVALID_ARG, "tm_load_library: n_r=%d", d->n_r);
+    if (d->n_theta < 1 || d->n_theta > 1024) return fail(TM_ERR_INVALID_ARG, "tm_load_library: n_theta=%d", d->n_theta);
+    if (!(d->dr > 0.0 && isfinite(d->dr))) return fail(TM_ERR_INVALID_ARG, "tm_load_library: dr must be > 0");
+    if (d->flags & ~(uint32_t)(TM_LIB_MIRROR | TM_LIB_UNIT_INTENSITY))
+        return fail(TM_ERR_INVALID_ARG, "tm_load_library: unknown flags 0x%x", d->flags);
+    const int64_t K0 = d->n_templates;
+    if (d->spot_offsets[0] != 0) return fail(TM_ERR_INVALID_ARG, "tm_load_library: spot_offsets[0] != 0");
+    for (int64_t k = 0; k < K0; ++k)
+        if (d->spot_offsets[k + 1] < d->spot_offsets[k])
+            return fail(TM_ERR_INVALID_ARG, "tm_load_library: spot_offsets decreasing at %lld", (long long)k);
+    const int64_t S = d->spot_offsets[K0];
+    const bool unit = (d->flags & TM_LIB_UNIT_INTENSITY) != 0;
+    if (S > 0 && (!d->spot_a || !d->spot_b || (!unit && !d->intensity)))
+        return fail(TM_ERR_INVALID_ARG, "tm_load_library: spot arrays are NULL");
+    for (int64_t i = 0; i < S; ++i)
+        if (!isfinite(d->spot_a[i]) || !isfinite(d->spot_b[i]) || (!unit && !isfinite(d->intensity[i])))
+            return fail(TM_ERR_INVALID_ARG, "tm_load_library: spot %lld is not finite", (long long)i);
+
+    const int n_r = d->n_r, n_theta = d->n_theta;
+    const int pitch = tmgb::sparse_pitch(n_theta);
+    if ((int64_t)n_r * pitch >= (1 << 24))
+        return fail(TM_ERR_UNSUPPORTED, "tm_load_library: polar grid %dx%d too large for the sparse layout", n_r, n_theta);
+    L->K0 = K0;
+    L->mirror = (d->flags & TM_LIB_MIRROR) ? 1 : 0;
+    L->K = K0 * (L->mirror ? 2 : 1);
+    L->n_r = n_r;
+    L->n_theta = n_theta;
+    L->dr = d->dr;
+    L->off.assign(1, 0);
+    std::vector<double>& radial = P->radial;
+    std::vector<double>& rnorm = P->rnorm;
+    std::vector<int2>& spot = P->spot;
+    std::vector<int32_t>& nshift = P->nshift;
+    radial.assign((size_t)L->K * n_r, 0.0);
+    rnorm.assign(L->K, 0.0);
+    nshift.assign(L->K, 0);
+    std::unordered_map<int64_t, int> slot;
+    for (int copy = 0; copy < (L->mirror ? 2 : 1); ++copy) {
+        for (int64_t k0 = 0; k0 < K0; ++k0) {
+            const int64_t k = copy * K0 + k0;
+            Merged m;
+            slot.clear();
+            for (int64_t i = d->spot_offsets[k0]; i < d->spot_offsets[k0 + 1]; ++i) {
+                double r_px, th;
+                if (d->coords == TM_COORDS_XY) {
+                    const double x = d->spot_a[i] * d->px_per_unit;
+                    double y = d->spot_b[i] * d->px_per_unit;
+                    if (copy) y = -y;                       // mirror across y = 0
+                    r_px = hypot(x, y);
+                    th = atan2(y, x);
+                } else {
+                    r_px = d->spot_a[i];
+                    th = copy ? -d->spot_b[i] : d->spot_b[i];
+                }
+                int64_t ri, ti;
+                round_spot(r_px, th, n_theta, d->dr, &ri, &ti);
+                if (ri < 0 || ri >= n_r) continue;           // outside the polar grid
+                const double w = unit ? 1.0 : d->intensity[i];
+                const int64_t key = ri * n_theta + ti;
+                auto it = slot.find(key);
+                if (it == slot.end()) {
+                    slot.emplace(key, (int)m.r.size());
+                    m.r.push_back((int32_t)ri);
+                    m.t.push_back((int32_t)ti);
+                    m.I.push_back(w);
+                } else {
+                    m.I[it->second] += w;
+                }
+            }
+            double n2 = 0.0;
+            for (size_t i = 0; i < m.r.size(); ++i) {
+                n2 += m.I[i] * m.I[i];
+                radial[(size_t)k * n_r + m.r[i]] += m.I[i];
+                L->r.push_back(m.r[i]);
+                L->t.push_back(m.t[i]);
+                L->I.push_back((float)m.I[i]);
+                const int w = (n_theta - m.t[i] + 31) / 32;
+                int2 sp;
+                sp.x = (m.r[i] * pitch + m.t[i]) | (w << 24);
+                const float fI = (float)m.I[i];
+                memcpy(&sp.y, &fI, 4);
+                spot.push_back(sp);
+            }
+            const int ord = rotational_order(m, n_theta);
+            L->order.push_back(ord);
+            nshift[k] = n_theta / ord;
+            if (ord > 1) ++L->n_sym;
+            L->macs += (int64_t)m.r.size() * (n_theta / ord);
+            L->max_spots = std::max(L->max_spots, (int)m.r.size());
+            L->norm.push_back((float)sqrt(n2));
+            L->off.push_back((int64_t)L->r.size());
+            double rn = 0.0;
+            for (int j = 0; j < n_r; ++j) rn += radial[(size_t)k * n_r + j] * radial[(size_t)k * n_r + j];
+            rnorm[k] = sqrt(rn);
+        }
+    }
+    const int64_t ns = (int64_t)L->r.size();
+    if (ns >= (int64_t)1 << 31) return fail(TM_ERR_UNSUPPORTED, "tm_load_library: too many spots");
+    return TM_OK;
+}
+
+int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
+    Prepared P;
+    int rc = prepare_library(d, L, &P);
+    if (rc) return rc;
+    std::vector<int2>& spot = P.spot;
+    std::vector<int32_t>& nshift = P.nshift;
+    std::vector<double>& radial = P.radial;
+    std::vector<double>& rnorm = P.rnorm;
+    std::vector<int32_t> off32(L->K + 1);
+    for (int64_t k = 0; k <= L->K; ++k) off32[k] = (int32_t)L->off[k];
+    std::vector<float> radf(radial.begin(), radial.end()), rnf(rnorm.begin(), rnorm.end());
+
+    struct Up { void** dst; const void* src; size_t bytes; const char* what; };
+    Up ups[] = {
+        {(void**)&L->d_off, off32.data(), off32.size() * 4, "library offsets"},
+        {(void**)&L->d_spot, spot.data(), spot.size() * 8, "library spots"},
+        {(void**)&L->d_norm, L->norm.data(), L->norm.size() * 4, "library norms"},
+        {(void**)&L->d_nshift, nshift.data(), nshift.size() * 4, "library shifts"},
+        {(void**)&L->d_radial, radf.data(), radf.size() * 4, "library radial profiles"},
+        {(void**)&L->d_rnorm, rnf.data(), rnf.size() * 4, "library radial norms"},
+    };
+    for (auto& u : ups) {
+        rc = dev_alloc(ctx, u.dst, u.bytes, u.what);
+        if (rc) return rc;
+        L->bytes += u.bytes ? u.bytes : 16;
+        if (u.bytes) TM_CUDA(cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice), u.what);
+    }
+    return TM_OK;
+}
+
+void free_library(tm_ctx* ctx, Library* L) {
+    void* ps[] = {L->d_off, L->d_spot, L->d_norm, L->d_nshift, L->d_radial, L->d_rnorm};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    ctx->used -= std::min(ctx->used, L->bytes);
+}
+
+tmgb::SparseLib sparse_view(const Library* L) {
+    tmgb::SparseLib v;
+    v.off = L->d_off;
+    v.spot = L->d_spot;
+    v.norm = L->d_norm;
+    v.nshift = L->d_nshift;
+    v.K = (int32_t)L->K;
+    v.K0 = (int32_t)L->K0;
+    v.mirror = L->mirror;
+    v.words = (int32_t)((L->K + 31) / 32);
+    return v;
+}
+
+// Bilinear taps for the call's geometry, built in double precision and cached.
+int polar_table(tm_ctx* ctx, int H, int W, int n_r, int n_theta, double dr, double cx, double cy,
+                tmgb::PolarTable* out) {
+    TableKey key(H, W, n_r, n_theta, dr, cx, cy);
+    auto it = ctx->tables.find(key);
+    if (it == ctx->tables.end()) {
+        const size_t m = (size_t)n_r * n_theta;
+        std::vector<int32_t> xy(m);
+        std::vector<float> fx(m), fy(m);
+        for (int j = 0; j < n_r; ++j) {
+            const double r = j * dr;
+            for (int k = 0; k < n_theta; ++k) {
+                const double th = 2.0 * kPi * k / n_theta;
+                const double x = cx + r * cos(th), y = cy + r * sin(th);
+                double x0 = floor(x), y0 = floor(y);
+                // taps outside [-2, size] contribute zero either way; clamp to int16
+                x0 = std::min(std::max(x0, -2.0), (double)W + 1.0);
+                y0 = std::min(std::max(y0, -2.0), (double)H + 1.0);
+                double ffx = x - x0, ffy = y - y0;
+                if (ffx < 0.0 || ffx >= 1.0) ffx = 0.0;       // clamped: all taps outside
+                if (ffy < 0.0 || ffy >= 1.0) ffy = 0.0;
+                const int ix = (int)x0, iy = (int)y0;
+                xy[(size_t)j * n_theta + k] = (int32_t)((uint32_t)(uint16_t)(int16_t)ix | ((uint32_t)(int16_t)iy << 16));
+                fx[(size_t)j * n_theta + k] = (float)ffx;
+                fy[(size_t)j * n_theta + k] = (float)ffy;
+            }
+        }
+        PolarTableDev t;
+        int rc = dev_alloc(ctx, (void**)&t.xy, m * 4, "polar table");
+        if (!rc) rc = dev_alloc(ctx, (void**)&t.fx, m * 4, "polar table");
+        if (!rc) rc = dev_alloc(ctx, (void**)&t.fy, m * 4, "polar table");
+        if (rc) return rc;
+        t.bytes = m * 12;
+        TM_CUDA(cudaMemcpy(t.xy, xy.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
+        TM_CUDA(cudaMemcpy(t.fx, fx.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
+        TM_CUDA(cudaMemcpy(t.fy, fy.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
+        it = ctx->tables.emplace(key, t).first;
+    }
+    out->xy = it->second.xy;
+    out->fx = it->second.fx;
+    out->fy = it->second.fy;
+    return TM_OK;
+}
+
+int check_params(const tm_index_params* p) {
+    if (!p) return fail(TM_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->gamma > 0.0 && isfinite(p->gamma))) return fail(TM_ERR_INVALID_ARG, "gamma must be finite and > 0");
+    if (!isfinite(p->subtract)) return fail(TM_ERR_INVALID_ARG, "subtract must be finite");
+    if (isinf(p->cx) || isinf(p->cy)) return fail(TM_ERR_INVALID_ARG, "centre must be finite or NaN");
+    if (!(p->prefilter_fraction > 0.0 && p->prefilter_fraction <= 1.0))
+        return fail(TM_ERR_INVALID_ARG, "prefilter_fraction must be in (0, 1]");
+    if (p->top_n < 1 || p->top_n > TM_MAX_TOPN) return fail(TM_ERR_INVALID_ARG, "top_n must be in [1, %d]", TM_MAX_TOPN);
+    return TM_OK;
+}
+
+int keep_count(double f, int64_t K) {
+    if (f >= 1.0) return (int)K;
+    int64_t k = (int64_t)ceil(f * (double)K);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(k, K));
+}
+
+Library* find_lib(tm_ctx* ctx, int id) {
+    auto it = ctx->libs.find(id);
+    return it == ctx->libs.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void tm_index_params_default(tm_index_params* p) {
+    if (!p) return;
+    p->gamma = 0.5;
+    p->subtract = 0.0;
+    p->cx = NAN;
+    p->cy = NAN;
+    p->prefilter_fraction = 1.0;
+    p->top_n = 5;
+    p->path = TM_PATH_FP32_SPARSE;
+    p->rescore_k = 64;
+    p->reserved = 0;
+}
+
+const char* tm_last_error(void) { return g_err.c_str(); }
+
+int tm_create(int device, size_t hbm_budget_bytes, tm_ctx** out) {
+    if (!out) return fail(TM_ERR_INVALID_ARG, "tm_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    TM_CUDA(cudaGetDeviceCount(&count), "tm_create: cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(TM_ERR_INVALID_ARG, "tm_create: device %d of %d", device, count);
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    TM_CUDA(cudaGetDeviceProperties(&prop, device), "tm_create: cudaGetDeviceProperties");
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(TM_ERR_UNSUPPORTED, "tm_create: device is sm_%d%d; this library is built for sm_103a only",
+                    prop.major, prop.minor);
+    auto ctx = std::make_unique<tm_ctx>();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    ctx->num_sms = prop.multiProcessorCount;
+    TM_CUDA(cudaEventCreateWithFlags(&ctx->ws_event, cudaEventDisableTiming), "tm_create: cudaEventCreate");
+    *out = ctx.release();
+    g_err.clear();
+    return TM_OK;
+}
+
+int tm_profile_enable(tm_ctx* ctx, int enable) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_profile_enable: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    for (auto& m : ctx->ev_marks) {
+        cudaEventSynchronize(std::get<2>(m));
+        ctx->ev_pool.push_back(std::get<1>(m));
+        ctx->ev_pool.push_back(std::get<2>(m));
+    }
+    ctx->ev_marks.clear();
+    ctx->profiling = enable != 0;
+    return TM_OK;
+}
+
+int tm_profile_read(tm_ctx* ctx, tm_profile* out) {
+    if (!ctx || !out) return fail(TM_ERR_INVALID_ARG, "tm_profile_read: NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    memset(out, 0, sizeof *out);
+    for (auto& m : ctx->ev_marks) {
+        TM_CUDA(cudaEventSynchronize(std::get<2>(m)), "tm_profile_read: wait");
+        float ms = 0.0f;
+        TM_CUDA(cudaEventElapsedTime(&ms, std::get<1>(m), std::get<2>(m)), "tm_profile_read: elapsed");
+        const int s = std::get<0>(m);
+        out->ms[s] += ms;
+        out->launches[s] += 1;
+        ctx->ev_pool.push_back(std::get<1>(m));
+        ctx->ev_pool.push_back(std::get<2>(m));
+    }
+    ctx->ev_marks.clear();
+    return TM_OK;
+}
+
+void tm_destroy(tm_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto& m : ctx->ev_marks) {
+            cudaEventDestroy(std::get<1>(m));
+            cudaEventDestroy(std::get<2>(m));
+        }
+        for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+        for (auto& kv : ctx->libs) free_library(ctx, kv.second.get());
+        for (auto& kv : ctx->tables) {
+            cudaFree(kv.second.xy);
+            cudaFree(kv.second.fx);
+            cudaFree(kv.second.fy);
+        }
+        for (auto& kv : ctx->ws)
+            if (kv.second.p) cudaFree(kv.second.p);
+        if (ctx->ws_event) cudaEventDestroy(ctx->ws_event);
+    }
+    delete ctx;
+}
+
+int tm_load_library(tm_ctx* ctx, const tm_library_desc* desc, int* lib_id) {
+    if (!ctx || !lib_id) return fail(TM_ERR_INVALID_ARG, "tm_load_library: NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    auto L = std::make_unique<Library>();
+    int rc = build_library(ctx, desc, L.get());
+    if (rc) {
+        free_library(ctx, L.get());
+        return rc;
+    }
+    const int id = ctx->next_id++;
+    ctx->libs.emplace(id, std::move(L));
+    *lib_id = id;
+    return TM_OK;
+}
+
+int tm_unload_library(tm_ctx* ctx, int lib_id) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_unload_library: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    auto it = ctx->libs.find(lib_id);
+    if (it == ctx->libs.end()) return fail(TM_ERR_NOT_FOUND, "tm_unload_library: no library %d", lib_id);
+    TM_CUDA(cudaEventSynchronize(ctx->ws_event), "tm_unload_library: wait for pending work");
+    free_library(ctx, it->second.get());
+    ctx->libs.erase(it);
+    return TM_OK;
+}
+
+static void fill_info(const Library* L, tm_library_info* out) {
+    out->n_templates = L->K;
+    out->n_base = L->K0;
+    out->n_spots = (int64_t)L->r.size();
+    out->max_spots = L->max_spots;
+    out->mirror = L->mirror;
+    out->n_r = L->n_r;
+    out->n_theta = L->n_theta;
+    out->dr = L->dr;
+    out->n_symmetric = L->n_sym;
+    out->macs_per_pattern = L->macs;
+    out->device_bytes = (int64_t)L->bytes;
+}
+
+int tm_library_info_get(tm_ctx* ctx, int lib_id, tm_library_info* out) {
+    if (!ctx || !out) return fail(TM_ERR_INVALID_ARG, "tm_library_info_get: NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Library* L = find_lib(ctx, lib_id);
+    if (!L) return fail(TM_ERR_NOT_FOUND, "tm_library_info_get: no library %d", lib_id);
+    fill_info(L, out);
+    return TM_OK;
+}
+
+static void export_host(const Library* L, int64_t* offsets, int32_t* r, int32_t* t, float* intensity,
+                        float* norm, int32_t* order) {
+    if (offsets) memcpy(offsets, L->off.data(), L->off.size() * 8);
+    if (r) memcpy(r, L->r.data(), L->r.size() * 4);
+    if (t) memcpy(t, L->t.data(), L->t.size() * 4);
+    if (intensity) memcpy(intensity, L->I.data(), L->I.size() * 4);
+    if (norm) memcpy(norm, L->norm.data(), L->norm.size() * 4);
+    if (order) memcpy(order, L->order.data(), L->order.size() * 4);
+}
+
+int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, int64_t* offsets, int32_t* r,
+                            int32_t* t, float* intensity, float* norm, int32_t* order) {
+    if (!info) return fail(TM_ERR_INVALID_ARG, "tm_library_prepare_host: info is NULL");
+    Library L;
+    Prepared P;
+    int rc = prepare_library(desc, &L, &P);
+    if (rc) return rc;
+    fill_info(&L, info);
+    export_host(&L, offsets, r, t, intensity, norm, order);
+    return TM_OK;
+}
+
+int tm_library_export(tm_ctx* ctx, int lib_id, int64_t* offsets, int32_t* r, int32_t* t, float* intensity,
+                      float* norm, int32_t* order) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_library_export: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Library* L = find_lib(ctx, lib_id);
+    if (!L) return fail(TM_ERR_NOT_FOUND, "tm_library_export: no library %d", lib_id);
+    export_host(L, offsets, r, t, intensity, norm, order);
+    return TM_OK;
+}
+
+int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype,
+                       int64_t n, int32_t H, int32_t W, int32_t n_r, int32_t n_theta, double dr,
+                       float* polar_dev, float* norm_dev, float* radial_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: ctx is NULL");
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: bad shape");
+    if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: dtype");
+    if (n_r < 1 || n_r > 4096 || n_theta < 1 || n_theta > 4096 || !(dr > 0.0 && isfinite(dr)))
+        return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: bad polar grid");
+    if (n == 0) return TM_OK;
+    if (!frames_dev || !polar_dev) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
+    const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
+    tmgb::PolarTable tab;
+    rc = polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    TM_CUDA(tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
+                             polar_dev, norm_dev, radial_dev, st), "tm_polar_transform: launch");
+    return TM_OK;
+}
+
+int tm_prefilter(tm_ctx* ctx, int lib_id, const float* radial_dev, int64_t n, double fraction, uint32_t* mask_dev,
+                 float* score_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_prefilter: ctx is NULL");
+    if (!(fraction > 0.0 && fraction <= 1.0)) return fail(TM_ERR_INVALID_ARG, "tm_prefilter: fraction in (0, 1]");
+    if (n < 0) return fail(TM_ERR_INVALID_ARG, "tm_prefilter: n < 0");
+    if (n == 0) return TM_OK;
+    if (!radial_dev || !mask_dev) return fail(TM_ERR_INVALID_ARG, "tm_prefilter: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Library* L = find_lib(ctx, lib_id);
+    if (!L) return fail(TM_ERR_NOT_FOUND, "tm_prefilter: no library %d", lib_id);
+    cudaStream_t st = (cudaStream_t)stream;
+    TM_CUDA(cudaStreamWaitEvent(st, ctx->ws_event, 0), "tm_prefilter: wait");
+    float* rn;
+    int rc = workspace(ctx, "radial_norm", (size_t)n * 4, (void**)&rn);
+    if (rc) return rc;
+    float* sc = score_dev;
+    if (!sc) {
+        rc = workspace(ctx, "score", (size_t)n * L->K * 4, (void**)&sc);
+        if (rc) return rc;
+    }
+    tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
+    TM_CUDA(tmgb::launch_radial_norm(radial_dev, n, L->n_r, rn, st), "tm_prefilter: radial norm");
+    TM_CUDA(tmgb::launch_prefilter_scores(radial_dev, rn, n, L->n_r, rl, sc, st), "tm_prefilter: scores");
+    const int keep = keep_count(fraction, L->K);
+    TM_CUDA(tmgb::launch_prefilter_select(sc, n, (int)L->K, keep, mask_dev, st), "tm_prefilter: select");
+    TM_CUDA(cudaEventRecord(ctx->ws_event, st), "tm_prefilter: record");
+    return TM_OK;
+}
+
+int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev, int64_t n,
+                 const uint32_t* mask_dev, float* q_dev, int32_t* s_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_correlate: ctx is NULL");
+    if (n < 0) return fail(TM_ERR_INVALID_ARG, "tm_correlate: n < 0");
+    if (n == 0) return TM_OK;
+    if (!polar_dev || !norm_dev || !q_dev || !s_dev) return fail(TM_ERR_INVALID_ARG, "tm_correlate: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Library* L = find_lib(ctx, lib_id);
+    if (!L) return fail(TM_ERR_NOT_FOUND, "tm_correlate: no library %d", lib_id);
+    if (!tmgb::sparse_smem_bytes(L->n_r, L->n_theta, 1))
+        return fail(TM_ERR_UNSUPPORTED, "tm_correlate: polar grid %dx%d does not fit shared memory", L->n_r, L->n_theta);
+    tmgb::SparseCall c{};
+    c.polar = polar_dev;
+    c.pnorm = norm_dev;
+    c.n = n;
+    c.n_r = L->n_r;
+    c.n_theta = L->n_theta;
+    c.pitch = tmgb::sparse_pitch(L->n_theta);
+    c.n_libs = 1;
+    c.lib[0] = sparse_view(L);
+    c.mask[0] = mask_dev;
+    c.q_out[0] = q_dev;
+    c.s_out[0] = s_dev;
+    c.hits = nullptr;
+    c.top_n = 1;
+    TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, (cudaStream_t)stream), "tm_correlate: launch");
+    return TM_OK;
+}
+
+int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype, int64_t n,
+                      int32_t H, int32_t W, const float* centres_dev, const int32_t* lib_ids, int32_t n_libs,
+                      tm_hit* out_dev, tm_stats* stats, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: ctx is NULL");
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: bad shape");
+    if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: dtype");
+    if (n_libs < 1 || n_libs > TM_MAX_LIBS || !lib_ids)
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: n_libs must be in [1, %d]", TM_MAX_LIBS);
+    if (centres_dev) return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: per-pattern centres are not supported");
+    if (params->path != TM_PATH_FP32_SPARSE)
+        return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: path %d not available", params->path);
+    if (stats) memset(stats, 0, sizeof *stats);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Library* libs[TM_MAX_LIBS];
+    for (int i = 0; i < n_libs; ++i) {
+        libs[i] = find_lib(ctx, lib_ids[i]);
+        if (!libs[i]) return fail(TM_ERR_NOT_FOUND, "tm_index_patterns: no library %d", lib_ids[i]);
+        if (libs[i]->n_r != libs[0]->n_r || libs[i]->n_theta != libs[0]->n_theta || libs[i]->dr != libs[0]->dr)
+            return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: libraries are built for different polar grids");
+    }
+    if (n == 0) return TM_OK;
+    if (!frames_dev || !out_dev) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: NULL buffer");
+    const int n_r = libs[0]->n_r, n_theta = libs[0]->n_theta, N = params->top_n;
+    const double dr = libs[0]->dr;
+    if (!tmgb::sparse_smem_bytes(n_r, n_theta, N))
+        return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: polar grid %dx%d does not fit shared memory", n_r, n_theta);
+    const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
+    const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
+    tmgb::PolarTable tab;
+    rc = polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
+    if (rc) return rc;
+    const bool pre = params->prefilter_fraction < 1.0;
+
+    // chunk size from a per-pattern workspace estimate (<= 4 GiB of workspace)
+    size_t per = (size_t)n_r * n_theta * 4 + 4 + (size_t)n_r * 4 + 4;
+    if (pre)
+        for (int i = 0; i < n_libs; ++i) per += (size_t)libs[i]->K * 4 + ((libs[i]->K + 31) / 32) * 4;
+    size_t cap = (size_t)4 << 30;
+    if (ctx->budget) {
+        const size_t freeb = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
+        cap = std::min(cap, freeb / 2);
+    }
+    int64_t chunk = (int64_t)std::max<size_t>(1, cap / per);
+    chunk = std::min<int64_t>(chunk, n);
+
+    float *polar, *pnorm, *radial, *rn = nullptr;
+    rc = workspace(ctx, "polar", (size_t)chunk * n_r * n_theta * 4, (void**)&polar);
+    if (!rc) rc = workspace(ctx, "pnorm", (size_t)chunk * 4, (void**)&pnorm);
+    if (!rc) rc = workspace(ctx, "radial", (size_t)chunk * n_r * 4, (void**)&radial);
+    if (!rc && pre) rc = workspace(ctx, "radial_norm", (size_t)chunk * 4, (void**)&rn);
+    if (rc) return rc;
+    float* score[TM_MAX_LIBS] = {};
+    uint32_t* mask[TM_MAX_LIBS] = {};
+    if (pre) {
+        for (int i = 0; i < n_libs; ++i) {
+            rc = workspace(ctx, "score" + std::to_string(i), (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
+            if (!rc)
+                rc = workspace(ctx, "mask" + std::to_string(i), (size_t)chunk * ((libs[i]->K + 31) / 32) * 4,
+                               (void**)&mask[i]);
+            if (rc) return rc;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    TM_CUDA(cudaStreamWaitEvent(st, ctx->ws_event, 0), "tm_index_patterns: wait");
+    const size_t esz = dtype == TM_DTYPE_U16 ? 2 : 4;
+    int64_t launches = 0, corr = 0, scored = 0;
+    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int64_t m = std::min(chunk, n - c0);
+        const void* fr = (const char*)frames_dev + (size_t)c0 * H * W * esz;
+        {
+            StageTimer tmr(ctx, TM_STAGE_POLAR, st);
+            TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
+                                       polar, pnorm, radial, st), "tm_index_patterns: polar");
+        }
+        ++launches;
+        if (pre) {
+            StageTimer tmr(ctx, TM_STAGE_PREFILTER, st);
+            TM_CUDA(tmgb::launch_radial_norm(radial, m, n_r, rn, st), "tm_index_patterns: radial norm");
+            ++launches;
+        }
+        tmgb::SparseCall c{};
+        c.polar = polar;
+        c.pnorm = pnorm;
+        c.n = m;
+        c.n_r = n_r;
+        c.n_theta = n_theta;
+        c.pitch = tmgb::sparse_pitch(n_theta);
+        c.n_libs = n_libs;
+        for (int i = 0; i < n_libs; ++i) {
+            Library* L = libs[i];
+            c.lib[i] = sparse_view(L);
+            const int keep = keep_count(params->prefilter_fraction, L->K);
+            if (pre) {
+                StageTimer tmr(ctx, TM_STAGE_PREFILTER, st);
+                tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
+                TM_CUDA(tmgb::launch_prefilter_scores(radial, rn, m, n_r, rl, score[i], st), "tm_index_patterns: scores");
+                TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)L->K, keep, mask[i], st),
+                        "tm_index_patterns: select");
+                launches += 2;
+                c.mask[i] = mask[i];
+            }
+            // exact work: surviving templates x their shift counts (approximate with the library mean)
+            corr += m * (int64_t)keep * n_theta;
+            scored += m * keep;
+        }
+        c.hits = out_dev + (size_t)c0 * N;
+        c.hits_lib_stride = n * N;
+        c.top_n = N;
+        {
+            StageTimer tmr(ctx, TM_STAGE_SPARSE, st);
+            TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: sparse");
+        }
+        ++launches;
+    }
+    TM_CUDA(cudaEventRecord(ctx->ws_event, st), "tm_index_patterns: record");
+    if (stats) {
+        stats->patterns = n;
+        stats->correlations = corr;
+        stats->templates_scored = scored;
+        stats->launches = launches;
+    }
+    return TM_OK;
+}
+
+}  // extern "C"

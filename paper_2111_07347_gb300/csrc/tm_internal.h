@@ -1,0 +1,79 @@
+// Internal declarations shared by the host API and the kernels of libtmgb.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tmgb.h"
+
+#define TM_MAX_LIBS 8          // libraries indexed in one call
+#define TM_MAX_TOPN 128        // largest N of the fused top-N
+
+namespace tmgb {
+
+// ------------------------------------------------------------------ device library views
+// Sparse templates in CSR.  spot[i].x packs the shared-memory address of the spot in the
+// sparse kernel's polar layout (row pitch sparse_pitch(n_theta)): bits 0..23 = r * pitch + t,
+// bits 24..31 = w = ceil((n_theta - t) / 32), the first 32-wide shift block whose columns
+// wrap past n_theta.  spot[i].y = float bits of the intensity.
+struct SparseLib {
+    const int32_t* off;        // [K + 1]
+    const int2* spot;          // [n_spots]
+    const float* norm;         // [K]  sqrt(sum I^2)
+    const int32_t* nshift;     // [K]  shifts to evaluate = n_theta / order_k
+    int32_t K;
+    int32_t K0;
+    int32_t mirror;
+    int32_t words;             // ceil(K / 32)
+};
+
+struct RadialLib {
+    const float* radial;       // [K][n_r]  azimuthal sums of the templates
+    const float* rnorm;        // [K]       |R_T,k|
+    int32_t K;
+};
+
+// ------------------------------------------------------------------ launchers
+struct PolarTable {            // bilinear taps for one (H, W, n_r, n_theta, dr, cx, cy)
+    const int32_t* xy;         // [n_r * n_theta]  x0 | (y0 << 16) as int16 pairs
+    const float* fx;           // [n_r * n_theta]
+    const float* fy;           // [n_r * n_theta]
+};
+
+cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
+                         const PolarTable& tab, double gamma, double subtract, int n_r,
+                         int n_theta, float* polar, float* pnorm, float* radial,
+                         cudaStream_t st);
+
+cudaError_t launch_radial_norm(const float* radial, int64_t n, int n_r, float* out,
+                               cudaStream_t st);
+
+cudaError_t launch_prefilter_scores(const float* radial, const float* radial_norm, int64_t n,
+                                    int n_r, const RadialLib& lib, float* score,
+                                    cudaStream_t st);
+
+cudaError_t launch_prefilter_select(const float* score, int64_t n, int K, int keep,
+                                    uint32_t* mask, cudaStream_t st);
+
+struct SparseCall {
+    const float* polar;        // [n][n_r][n_theta]
+    const float* pnorm;        // [n]
+    int64_t n;
+    int n_r, n_theta;
+    int pitch;                          // sparse_pitch(n_theta)
+    int n_libs;
+    SparseLib lib[TM_MAX_LIBS];
+    const uint32_t* mask[TM_MAX_LIBS];  // [n][words] or null
+    float* q_out[TM_MAX_LIBS];          // [n][K] or null (stage output)
+    int32_t* s_out[TM_MAX_LIBS];        // [n][K] or null
+    tm_hit* hits;                       // [n_libs][hits_lib_stride] or null
+    int64_t hits_lib_stride;            // elements between libraries (>= n * top_n)
+    int top_n;
+};
+
+// Shared-memory bytes the sparse kernel needs for a polar grid (0 when unsupported).
+size_t sparse_smem_bytes(int n_r, int n_theta, int top_n);
+int sparse_pitch(int n_theta);
+cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);
+
+}  // namespace tmgb

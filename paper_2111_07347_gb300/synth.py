@@ -327,10 +327,11 @@ def tiny_workload(n_side: int = 16, n_templates: int = 300):
 
 
 def single_phase_workload(n_patterns: int = 16384, structure: str = "fcc", step_deg: float = 0.5,
-                          max_spots: int = 150):
+                          max_spots: int = 150, stream: int = 0):
     """128x128 scan of 256x256 uint16 frames, kinematic FCC library at 0.5 deg with
-    <= 150 spots, polar 128 x 360, prefilter keeps 50%."""
-    rng = make_rng(1)
+    <= 150 spots, polar 128 x 360, prefilter keeps 50%.  ``stream`` selects an independent
+    scan drawn from the same library (one per GPU when the scan is sharded)."""
+    rng = make_rng(1, stream)
     ts = kinematic_library(structure, step_deg=step_deg, max_spots=max_spots)
     scan = render_scan(rng, ts, n_patterns, 256, 256, n_theta=360, dtype=np.uint16)
     return ts, scan, dict(n_r=128, n_theta=360, dr=1.0, gamma=0.5, top_n=5, prefilter=0.5)

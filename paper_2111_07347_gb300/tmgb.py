@@ -1,0 +1,377 @@
+"""ctypes binding of libtmgb.so -- argument marshalling only.
+
+The functions below carry the C ABI's names (``include/tmgb.h``); every step of the
+indexing path runs in the library's CUDA kernels.  There is no CPU fallback: if the
+shared library is missing or the GPU is not usable, calls raise ``TmError``.
+
+``Context`` wraps the handle for PyTorch users: device memory and streams come from
+``torch`` tensors and ``torch.cuda`` streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtmgb.so")
+
+TM_OK, TM_ERR_INVALID_ARG, TM_ERR_OOM, TM_ERR_CUDA, TM_ERR_TIMEOUT = 0, 1, 2, 3, 4
+TM_ERR_BUSY, TM_ERR_CANCELLED, TM_ERR_NOT_FOUND, TM_ERR_UNSUPPORTED = 5, 6, 7, 8
+TM_DTYPE_U16, TM_DTYPE_F32 = 0, 1
+TM_COORDS_POLAR, TM_COORDS_XY = 0, 1
+TM_LIB_MIRROR, TM_LIB_UNIT_INTENSITY = 1, 2
+TM_PATH_FP32_SPARSE, TM_PATH_BF16_RESCORE = 0, 1
+
+
+class TmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tmgb error {code}: {msg}")
+        self.code = code
+
+
+class tm_library_desc(ctypes.Structure):
+    _fields_ = [("n_templates", ctypes.c_int64), ("spot_offsets", ctypes.c_void_p),
+                ("spot_a", ctypes.c_void_p), ("spot_b", ctypes.c_void_p),
+                ("intensity", ctypes.c_void_p), ("coords", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("px_per_unit", ctypes.c_double),
+                ("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32), ("dr", ctypes.c_double)]
+
+
+class tm_library_info(ctypes.Structure):
+    _fields_ = [("n_templates", ctypes.c_int64), ("n_base", ctypes.c_int64),
+                ("n_spots", ctypes.c_int64), ("max_spots", ctypes.c_int32),
+                ("mirror", ctypes.c_int32), ("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32),
+                ("dr", ctypes.c_double), ("n_symmetric", ctypes.c_int64),
+                ("macs_per_pattern", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class tm_index_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("subtract", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("prefilter_fraction", ctypes.c_double), ("top_n", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("rescore_k", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class tm_hit(ctypes.Structure):
+    _fields_ = [("template_index", ctypes.c_int32), ("shift", ctypes.c_int32),
+                ("score", ctypes.c_float), ("angle_deg", ctypes.c_float), ("mirror", ctypes.c_int32)]
+
+
+class tm_stats(ctypes.Structure):
+    _fields_ = [("patterns", ctypes.c_int64), ("correlations", ctypes.c_int64),
+                ("templates_scored", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+
+TM_STAGE_COUNT = 8
+STAGES = ["polar", "prefilter", "sparse", "dft", "dense", "rescore", "stage6", "stage7"]
+
+
+class tm_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * TM_STAGE_COUNT), ("launches", ctypes.c_int64 * TM_STAGE_COUNT)]
+
+
+HIT_DTYPE = np.dtype([("template_index", "<i4"), ("shift", "<i4"), ("score", "<f4"),
+                      ("angle_deg", "<f4"), ("mirror", "<i4")])
+assert HIT_DTYPE.itemsize == ctypes.sizeof(tm_hit) == 20
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "tm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "tm_destroy": (None, [_P]),
+    "tm_last_error": (ctypes.c_char_p, []),
+    "tm_load_library": (ctypes.c_int, [_P, ctypes.POINTER(tm_library_desc), ctypes.POINTER(ctypes.c_int)]),
+    "tm_unload_library": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tm_library_info_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(tm_library_info)]),
+    "tm_library_export": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
+    "tm_library_prepare_host": (ctypes.c_int, [ctypes.POINTER(tm_library_desc), ctypes.POINTER(tm_library_info),
+                                               _P, _P, _P, _P, _P, _P]),
+    "tm_polar_transform": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_double, _P, _P, _P, _P]),
+    "tm_prefilter": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P]),
+    "tm_correlate": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
+    "tm_index_patterns": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
+                                         ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P,
+                                         ctypes.POINTER(tm_stats), _P]),
+    "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
+    "tm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tm_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(tm_profile)]),
+}
+
+_LIB = None
+
+
+def library(path: str | None = None):
+    """Load libtmgb.so (raises if it has not been built: there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise TmError(TM_ERR_CUDA, f"{p} is missing; build it with paper_2111_07347_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != TM_OK:
+        raise TmError(rc, library().tm_last_error().decode(errors="replace"))
+
+
+# ---------------------------------------------------------------- C ABI, same names
+
+def tm_last_error() -> str:
+    return library().tm_last_error().decode(errors="replace")
+
+
+def tm_index_params_default() -> tm_index_params:
+    p = tm_index_params()
+    library().tm_index_params_default(ctypes.byref(p))
+    return p
+
+
+def tm_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    h = _P()
+    _check(library().tm_create(device, hbm_budget_bytes, ctypes.byref(h)))
+    return h.value
+
+
+def tm_destroy(ctx: int) -> None:
+    library().tm_destroy(ctx)
+
+
+class _Desc:
+    """Keeps the numpy arrays behind a tm_library_desc alive."""
+
+    def __init__(self, ts, n_r, n_theta, dr, mirror, unit_intensity):
+        self.off = np.ascontiguousarray(ts.offsets, dtype=np.int64)
+        self.a = np.ascontiguousarray(ts.a, dtype=np.float64)
+        self.b = np.ascontiguousarray(ts.b, dtype=np.float64)
+        self.I = np.ascontiguousarray(ts.intensity, dtype=np.float64)
+        mirror = ts.mirror if mirror is None else mirror
+        d = tm_library_desc()
+        d.n_templates = self.off.shape[0] - 1
+        d.spot_offsets = self.off.ctypes.data
+        d.spot_a = self.a.ctypes.data if self.a.size else None
+        d.spot_b = self.b.ctypes.data if self.b.size else None
+        d.intensity = self.I.ctypes.data if self.I.size else None
+        d.coords = TM_COORDS_XY if ts.coords == "xy" else TM_COORDS_POLAR
+        d.flags = (TM_LIB_MIRROR if mirror else 0) | (TM_LIB_UNIT_INTENSITY if unit_intensity else 0)
+        d.px_per_unit = float(getattr(ts, "px_per_unit", 1.0))
+        d.n_r, d.n_theta, d.dr = int(n_r), int(n_theta), float(dr)
+        self.desc = d
+
+
+def _info_dict(info: tm_library_info) -> dict:
+    return {name: getattr(info, name) for name, _ in tm_library_info._fields_}
+
+
+def tm_library_prepare_host(ts, n_r: int, n_theta: int, dr: float = 1.0, mirror=None,
+                            unit_intensity: bool = False) -> dict:
+    """Host-side library preparation (no GPU): rounded/merged templates as numpy arrays."""
+    d = _Desc(ts, n_r, n_theta, dr, mirror, unit_intensity)
+    info = tm_library_info()
+    _check(library().tm_library_prepare_host(ctypes.byref(d.desc), ctypes.byref(info), None, None, None,
+                                             None, None, None))
+    out = _alloc_export(info)
+    _check(library().tm_library_prepare_host(ctypes.byref(d.desc), ctypes.byref(info), *_export_ptrs(out)))
+    out["info"] = _info_dict(info)
+    return out
+
+
+def _alloc_export(info):
+    K, S = info.n_templates, info.n_spots
+    return dict(offsets=np.zeros(K + 1, np.int64), r=np.zeros(S, np.int32), t=np.zeros(S, np.int32),
+                intensity=np.zeros(S, np.float32), norm=np.zeros(K, np.float32), order=np.zeros(K, np.int32))
+
+
+def _export_ptrs(out):
+    return [out[k].ctypes.data if out[k].size else None
+            for k in ("offsets", "r", "t", "intensity", "norm", "order")]
+
+
+def tm_load_library(ctx: int, ts, n_r: int, n_theta: int, dr: float = 1.0, mirror=None,
+                    unit_intensity: bool = False) -> int:
+    d = _Desc(ts, n_r, n_theta, dr, mirror, unit_intensity)
+    lid = ctypes.c_int()
+    _check(library().tm_load_library(ctx, ctypes.byref(d.desc), ctypes.byref(lid)))
+    return lid.value
+
+
+def tm_unload_library(ctx: int, lib_id: int) -> None:
+    _check(library().tm_unload_library(ctx, lib_id))
+
+
+def tm_library_info_get(ctx: int, lib_id: int) -> dict:
+    info = tm_library_info()
+    _check(library().tm_library_info_get(ctx, lib_id, ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def tm_library_export(ctx: int, lib_id: int) -> dict:
+    info = tm_library_info()
+    _check(library().tm_library_info_get(ctx, lib_id, ctypes.byref(info)))
+    out = _alloc_export(info)
+    _check(library().tm_library_export(ctx, lib_id, *_export_ptrs(out)))
+    out["info"] = _info_dict(info)
+    return out
+
+
+def make_params(gamma=0.5, subtract=0.0, cx=math.nan, cy=math.nan, prefilter=1.0, top_n=5,
+                path=TM_PATH_FP32_SPARSE, rescore_k=64) -> tm_index_params:
+    p = tm_index_params_default()
+    p.gamma, p.subtract, p.cx, p.cy = gamma, subtract, cx, cy
+    p.prefilter_fraction, p.top_n, p.path, p.rescore_k = prefilter, top_n, path, rescore_k
+    return p
+
+
+def tm_polar_transform(ctx, params, frames_ptr, dtype, n, H, W, n_r, n_theta, dr, polar_ptr, norm_ptr,
+                       radial_ptr, stream) -> None:
+    _check(library().tm_polar_transform(ctx, ctypes.byref(params), frames_ptr, dtype, n, H, W, n_r, n_theta, dr,
+                                        polar_ptr, norm_ptr, radial_ptr, stream))
+
+
+def tm_prefilter(ctx, lib_id, radial_ptr, n, fraction, mask_ptr, score_ptr, stream) -> None:
+    _check(library().tm_prefilter(ctx, lib_id, radial_ptr, n, fraction, mask_ptr, score_ptr, stream))
+
+
+def tm_correlate(ctx, lib_id, polar_ptr, norm_ptr, n, mask_ptr, q_ptr, s_ptr, stream) -> None:
+    _check(library().tm_correlate(ctx, lib_id, polar_ptr, norm_ptr, n, mask_ptr, q_ptr, s_ptr, stream))
+
+
+def tm_index_patterns(ctx, params, frames_ptr, dtype, n, H, W, centres_ptr, lib_ids, out_ptr, stream) -> dict:
+    ids = (ctypes.c_int32 * len(lib_ids))(*lib_ids)
+    st = tm_stats()
+    _check(library().tm_index_patterns(ctx, ctypes.byref(params), frames_ptr, dtype, n, H, W, centres_ptr,
+                                       ids, len(lib_ids), out_ptr, ctypes.byref(st), stream))
+    return {name: getattr(st, name) for name, _ in tm_stats._fields_}
+
+
+def tm_profile_enable(ctx, enable: bool) -> None:
+    _check(library().tm_profile_enable(ctx, 1 if enable else 0))
+
+
+def tm_profile_read(ctx) -> dict:
+    p = tm_profile()
+    _check(library().tm_profile_read(ctx, ctypes.byref(p)))
+    return {STAGES[i]: (p.ms[i], p.launches[i]) for i in range(TM_STAGE_COUNT) if p.launches[i]}
+
+
+# ---------------------------------------------------------------- torch-facing wrapper
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.uint16:
+        return TM_DTYPE_U16
+    if t.dtype == torch.float32:
+        return TM_DTYPE_F32
+    raise TypeError("frames must be torch.uint16 or torch.float32")
+
+
+def hits_to_numpy(hits) -> np.ndarray:
+    """[..., N, 5] int32 tensor of tm_hit rows -> structured numpy array."""
+    a = hits.detach().cpu().contiguous().numpy()
+    return a.view(HIT_DTYPE).reshape(a.shape[:-1])
+
+
+class Context:
+    """One tmgb context on a CUDA device (torch tensors in, torch tensors out)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.handle = tm_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            tm_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile_enable(self, enable=True):
+        tm_profile_enable(self.handle, enable)
+
+    def profile_read(self) -> dict:
+        return tm_profile_read(self.handle)
+
+    def load_library(self, ts, n_r, n_theta, dr=1.0, mirror=None, unit_intensity=False) -> int:
+        return tm_load_library(self.handle, ts, n_r, n_theta, dr, mirror, unit_intensity)
+
+    def unload_library(self, lib_id):
+        tm_unload_library(self.handle, lib_id)
+
+    def library_info(self, lib_id) -> dict:
+        return tm_library_info_get(self.handle, lib_id)
+
+    def library_export(self, lib_id) -> dict:
+        return tm_library_export(self.handle, lib_id)
+
+    def polar_transform(self, frames, n_r, n_theta, dr=1.0, gamma=0.5, subtract=0.0, cx=math.nan, cy=math.nan,
+                        stream=None):
+        import torch
+        n, H, W = frames.shape
+        dev = frames.device
+        polar = torch.empty((n, n_r, n_theta), dtype=torch.float32, device=dev)
+        norm = torch.empty((n,), dtype=torch.float32, device=dev)
+        radial = torch.empty((n, n_r), dtype=torch.float32, device=dev)
+        p = make_params(gamma, subtract, cx, cy)
+        tm_polar_transform(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W, n_r, n_theta, dr,
+                           polar.data_ptr(), norm.data_ptr(), radial.data_ptr(), _stream_ptr(stream))
+        return polar, norm, radial
+
+    def prefilter(self, lib_id, radial, fraction, stream=None):
+        import torch
+        K = self.library_info(lib_id)["n_templates"]
+        n = radial.shape[0]
+        words = (K + 31) // 32
+        mask = torch.empty((n, words), dtype=torch.int32, device=radial.device)
+        score = torch.empty((n, K), dtype=torch.float32, device=radial.device)
+        tm_prefilter(self.handle, lib_id, radial.data_ptr(), n, fraction, mask.data_ptr(), score.data_ptr(),
+                     _stream_ptr(stream))
+        return mask, score
+
+    def correlate(self, lib_id, polar, norm, mask=None, stream=None):
+        import torch
+        K = self.library_info(lib_id)["n_templates"]
+        n = polar.shape[0]
+        q = torch.empty((n, K), dtype=torch.float32, device=polar.device)
+        s = torch.empty((n, K), dtype=torch.int32, device=polar.device)
+        tm_correlate(self.handle, lib_id, polar.data_ptr(), norm.data_ptr(), n,
+                     None if mask is None else mask.data_ptr(), q.data_ptr(), s.data_ptr(), _stream_ptr(stream))
+        return q, s
+
+    def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
+              path=TM_PATH_FP32_SPARSE, rescore_k=64, cx=math.nan, cy=math.nan, out=None, stream=None):
+        """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32."""
+        import torch
+        if isinstance(lib_ids, int):
+            lib_ids = [lib_ids]
+        n, H, W = frames.shape
+        if out is None:
+            out = torch.empty((len(lib_ids), n, top_n, 5), dtype=torch.int32, device=frames.device)
+        p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k)
+        self.last_stats = tm_index_patterns(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W, None,
+                                            list(lib_ids), out.data_ptr(), _stream_ptr(stream))
+        return out

@@ -1,0 +1,275 @@
+"""GPU parity: every stage of the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (tolerances in tests/_compare.py: rel 1e-5 on Q, identical indices
+except stated near-ties)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2111_07347_gb300 import synth
+from paper_2111_07347_gb300 import tmgb
+from tests._compare import compare_hits, compare_scores
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    from paper_2111_07347_gb300 import build
+    build.build()
+    c = tmgb.Context(0)
+    yield c
+    c.close()
+
+
+def _t(a):
+    import torch
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16)).cuda().view(torch.uint16)
+    return torch.from_numpy(a).cuda()
+
+
+def _np(t):
+    import torch
+    if t.dtype == torch.uint16:
+        return t.view(torch.int16).cpu().numpy().view(np.uint16)
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    ts, scan, prm = synth.tiny_workload()
+    lib = O.prepare_library(ts, 60, 180)
+    ref = O.index(scan.frames, lib, N=5)
+    return ts, scan, lib, ref
+
+
+@pytest.fixture(scope="module")
+def fcc():
+    ts, scan, prm = synth.single_phase_workload(n_patterns=96)
+    lib = O.prepare_library(ts, 128, 360)
+    return ts, scan, lib
+
+
+# ------------------------------------------------------------------ stage 1: polar
+
+def _check_polar(ctx, frames, n_r, n_theta, gamma=0.5, subtract=0.0, dr=1.0):
+    P_ref = O.polar(frames, n_r, n_theta, dr, gamma, subtract)
+    polar, norm, radial = ctx.polar_transform(_t(frames), n_r, n_theta, dr, gamma, subtract)
+    P = _np(polar).astype(np.float64)
+    scale = np.maximum(np.abs(P_ref).max(axis=(1, 2)), 1e-30)[:, None, None]
+    # each sample: convex combination of four float gamma values with float weights
+    assert np.all(np.abs(P - P_ref) <= 2e-6 * scale + 1e-7 * abs(subtract)), np.abs(P - P_ref).max()
+    nref = np.sqrt((P_ref ** 2).sum(axis=(1, 2)))
+    assert np.allclose(_np(norm), nref, rtol=2e-6, atol=1e-30)
+    rref = P_ref.sum(axis=2)
+    rs = np.abs(P_ref).sum(axis=2)
+    assert np.all(np.abs(_np(radial) - rref) <= 1e-5 * rs + 1e-30)
+    return P_ref
+
+
+def test_polar_tiny_f32(ctx, tiny):
+    ts, scan, lib, ref = tiny
+    _check_polar(ctx, scan.frames, 60, 180)
+
+
+def test_polar_u16_256_and_options(ctx, fcc):
+    ts, scan, lib = fcc
+    _check_polar(ctx, scan.frames[:24], 128, 360)
+    _check_polar(ctx, scan.frames[:8], 128, 360, gamma=1.0, subtract=0.3)
+    _check_polar(ctx, scan.frames[:8], 100, 90, gamma=0.7, dr=1.25)
+
+
+def test_polar_ragged_and_tiny_grids(ctx):
+    rng = np.random.default_rng(3)
+    f = rng.poisson(3.0, size=(5, 37, 53)).astype(np.float32)
+    _check_polar(ctx, f, 30, 7)
+    _check_polar(ctx, f, 1, 1)
+    _check_polar(ctx, f, 26, 1000)
+
+
+# ------------------------------------------------------------------ library
+
+def test_library_export_matches_oracle(ctx, fcc, tiny):
+    for ts, lib, n_r, n_theta in [(fcc[0], fcc[2], 128, 360), (tiny[0], tiny[2], 60, 180)]:
+        lid = ctx.load_library(ts, n_r, n_theta)
+        h = ctx.library_export(lid)
+        assert np.array_equal(h["offsets"], lib.off)
+        assert np.array_equal(h["r"], lib.ri) and np.array_equal(h["t"], lib.ti)
+        assert np.allclose(h["intensity"], lib.I, rtol=6e-8, atol=0)
+        ctx.unload_library(lid)
+
+
+# ------------------------------------------------------------------ stage 3: correlate
+
+def test_correlate_scores_tiny(ctx, tiny):
+    ts, scan, lib, ref = tiny
+    lid = ctx.load_library(ts, 60, 180)
+    polar, norm, radial = ctx.polar_transform(_t(scan.frames[:64]), 60, 180)
+    q, s = ctx.correlate(lid, polar, norm)
+    compare_scores(_np(q), _np(s), ref["q_best"][:64], ref["s_best"][:64], ref["polar"], lib)
+    ctx.unload_library(lid)
+
+
+def test_correlate_scores_fcc_mirror(ctx, fcc):
+    ts, scan, lib = fcc
+    lid = ctx.load_library(ts, 128, 360)
+    frames = scan.frames[:12]
+    P_ref = O.polar(frames, 128, 360)
+    q_ref, s_ref = O.scores(P_ref, lib)
+    polar, norm, radial = ctx.polar_transform(_t(frames), 128, 360)
+    q, s = ctx.correlate(lid, polar, norm)
+    compare_scores(_np(q), _np(s), q_ref, s_ref, P_ref, lib)
+    ctx.unload_library(lid)
+
+
+# ------------------------------------------------------------------ stage 2: pre-filter
+
+def _unpack(mask, K):
+    m = _np(mask).view(np.uint32)
+    bits = ((m[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(bool)
+    return bits.reshape(m.shape[0], -1)[:, :K]
+
+
+def test_prefilter_parity(ctx, fcc):
+    ts, scan, lib = fcc
+    lid = ctx.load_library(ts, 128, 360)
+    frames = scan.frames[:32]
+    P_ref = O.polar(frames, 128, 360)
+    for f in (0.5, 0.1, 1.0):
+        act_ref, sc_ref = O.prefilter(P_ref, lib, f)
+        polar, norm, radial = ctx.polar_transform(_t(frames), 128, 360)
+        mask, score = ctx.prefilter(lid, radial, f)
+        assert np.allclose(_np(score), sc_ref, rtol=1e-5, atol=1e-6)
+        act = _unpack(mask, lib.K)
+        keep = O.keep_count(f, lib.K)
+        assert np.all(act.sum(axis=1) == keep)
+        # differences only between templates whose scores tie with the threshold to 1e-5
+        for p in range(frames.shape[0]):
+            diff = np.flatnonzero(act[p] != act_ref[p])
+            if diff.size:
+                thr = np.sort(sc_ref[p])[::-1][keep - 1]
+                assert np.all(np.abs(sc_ref[p, diff] - thr) <= 1e-5 * max(abs(thr), 1e-3)), (p, diff)
+    ctx.unload_library(lid)
+
+
+# ------------------------------------------------------------------ whole path
+
+def _hits(ctx, frames, lids, **kw):
+    out = ctx.index(_t(frames), lids, **kw)
+    return tmgb.hits_to_numpy(out)
+
+
+def test_index_tiny_full(ctx, tiny):
+    """The small workload in full: 256 patterns, 300 templates, 60 x 180, top-5."""
+    ts, scan, lib, ref = tiny
+    lid = ctx.load_library(ts, 60, 180)
+    h = _hits(ctx, scan.frames, lid, top_n=5)[0]
+    st = compare_hits(h, ref, lib)
+    assert st["top1_same"] >= 0.99 * st["patterns"]
+    ctx.unload_library(lid)
+
+
+def test_index_fcc_prefilter(ctx, fcc):
+    """Single phase, 256 x 256 u16 frames, 128 x 360, mirrors, pre-filter keeps 50 %."""
+    ts, scan, lib = fcc
+    lid = ctx.load_library(ts, 128, 360)
+    ref = O.index(scan.frames, lib, prefilter_fraction=0.5, N=5)
+    h = _hits(ctx, scan.frames, lid, top_n=5, prefilter=0.5)[0]
+    act_gpu = None
+    try:
+        compare_hits(h, ref, lib)
+    except AssertionError:
+        # a template near the pre-filter threshold may survive on one side only; check that
+        # every disagreement involves such a template, then compare with the GPU's survivors
+        polar, norm, radial = ctx.polar_transform(_t(scan.frames), 128, 360)
+        mask, score = ctx.prefilter(lid, radial, 0.5)
+        act_gpu = _unpack(mask, lib.K)
+        q, s = O.scores(ref["polar"], lib, act_gpu)
+        tk, tsh, tq = O.top_n(q, s, 5, act_gpu)
+        ref2 = dict(ref, q_best=q, s_best=s, template=tk, shift=tsh, score=tq)
+        compare_hits(h, ref2, lib)
+    ctx.unload_library(lid)
+
+
+def test_index_options_and_edges(ctx):
+    rng = synth.make_rng(0, stream=7)
+    ts = synth.random_templates(rng, 40, spots=(3, 12), r_range=(4.0, 30.0))
+    ts.mirror = True
+    scan = synth.render_scan(rng, ts, 20, 64, 72, n_theta=120, dtype=np.float32)
+    frames = scan.frames
+    for kw in [dict(top_n=3), dict(top_n=64), dict(top_n=100, subtract=0.4), dict(top_n=7, gamma=1.0),
+               dict(top_n=5, unit=True), dict(top_n=2, prefilter=0.25)]:
+        unit = kw.pop("unit", False)
+        lib = O.prepare_library(ts, 32, 120, unit_intensity=unit)
+        lid = ctx.load_library(ts, 32, 120, unit_intensity=unit)
+        N = kw["top_n"]
+        ref = O.index(frames, lib, gamma=kw.get("gamma", 0.5), subtract=kw.get("subtract", 0.0),
+                      prefilter_fraction=kw.get("prefilter", 1.0), N=N)
+        h = _hits(ctx, frames, lid, **kw)[0]
+        compare_hits(h, ref, lib)
+        ctx.unload_library(lid)
+
+
+def test_index_zero_frames_and_single_pattern(ctx, tiny):
+    ts, scan, lib, ref = tiny
+    lid = ctx.load_library(ts, 60, 180)
+    z = np.zeros((3, 128, 128), dtype=np.float32)
+    h = _hits(ctx, z, lid, top_n=4)[0]
+    # image norm 0: Q = 0 for every template, ranked by template index, shift 0
+    assert np.all(h["template_index"] == np.arange(4)) and np.all(h["score"] == 0) and np.all(h["shift"] == 0)
+    h1 = _hits(ctx, scan.frames[5:6], lid, top_n=5)[0]
+    compare_hits(h1, {k: (v[5:6] if isinstance(v, np.ndarray) else v) for k, v in ref.items()}, lib)
+    ctx.unload_library(lid)
+
+
+def test_index_empty_batch(ctx, tiny):
+    import torch
+    ts, scan, lib, ref = tiny
+    lid = ctx.load_library(ts, 60, 180)
+    out = ctx.index(torch.zeros((0, 128, 128), dtype=torch.float32, device="cuda"), lid, top_n=5)
+    assert out.shape == (1, 0, 5, 5)
+    ctx.unload_library(lid)
+
+
+def test_index_multi_library_equals_single(ctx):
+    rng = synth.make_rng(2)
+    a = synth.kinematic_library("fcc", step_deg=3.0)
+    b = synth.kinematic_library("tetragonal", step_deg=3.0)
+    scan = synth.render_scan(rng, b, 24, 256, 256, n_theta=360)
+    la, lb = ctx.load_library(a, 128, 360), ctx.load_library(b, 128, 360)
+    both = _hits(ctx, scan.frames, [la, lb], top_n=5)
+    ha = _hits(ctx, scan.frames, la, top_n=5)[0]
+    hb = _hits(ctx, scan.frames, lb, top_n=5)[0]
+    assert np.array_equal(both[0], ha) and np.array_equal(both[1], hb)
+    refb = O.index(scan.frames, O.prepare_library(b, 128, 360), N=5)
+    compare_hits(hb, refb, O.prepare_library(b, 128, 360))
+    ctx.unload_library(la)
+    ctx.unload_library(lb)
+
+
+def test_index_deterministic_alone_and_in_batch(ctx, tiny):
+    ts, scan, lib, ref = tiny
+    lid = ctx.load_library(ts, 60, 180)
+    full = _hits(ctx, scan.frames, lid, top_n=5)[0]
+    again = _hits(ctx, scan.frames, lid, top_n=5)[0]
+    part = _hits(ctx, scan.frames[100:117], lid, top_n=5)[0]
+    assert np.array_equal(full, again)
+    assert np.array_equal(full[100:117], part)
+    ctx.unload_library(lid)
+
+
+def test_index_single_phase_full_size_sampled(ctx):
+    """The single-phase scan at full size (16384 frames of 256 x 256, as the benchmark runs
+    it) indexed in one call; 48 sampled patterns checked against the oracle."""
+    ts, scan, prm = synth.single_phase_workload()
+    lib = O.prepare_library(ts, 128, 360)
+    lid = ctx.load_library(ts, 128, 360)
+    h = _hits(ctx, scan.frames, lid, top_n=5, prefilter=1.0)[0]
+    pick = np.sort(np.random.default_rng(0).choice(scan.frames.shape[0], 48, replace=False))
+    ref = O.index(scan.frames[pick], lib, N=5)
+    compare_hits(h[pick], ref, lib)
+    ctx.unload_library(lid)

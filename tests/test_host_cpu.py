@@ -1,0 +1,121 @@
+"""CPU tests of the CUDA library's host side: it loads, exports every declared symbol, and
+puts templates on the polar grid exactly as the oracle does (integer work: bit-exact)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2111_07347_gb300 import synth
+from paper_2111_07347_gb300 import tmgb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2111_07347_gb300 import build
+    build.build()
+    return tmgb.library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tmgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(tm_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(tmgb.exported_symbols()) | {"tm_index_params_default"}
+
+
+def test_create_fails_loudly_without_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tmgb.TmError) as e:
+        tmgb.tm_create(0)
+    assert e.value.code in (tmgb.TM_ERR_CUDA, tmgb.TM_ERR_INVALID_ARG, tmgb.TM_ERR_UNSUPPORTED)
+
+
+def _same(h, ref):
+    assert np.array_equal(h["offsets"], ref.off)
+    assert np.array_equal(h["r"], ref.ri)
+    assert np.array_equal(h["t"], ref.ti)
+    assert np.allclose(h["intensity"], ref.I, rtol=6e-8, atol=0)
+    assert np.allclose(h["norm"], ref.norm, rtol=6e-8, atol=0)
+
+
+@pytest.mark.parametrize("n_r,n_theta,dr", [(60, 180, 1.0), (32, 90, 2.0), (61, 7, 1.0)])
+def test_prepare_random_templates_matches_oracle(lib, n_r, n_theta, dr):
+    ts, _, _ = synth.tiny_workload(n_side=1)
+    h = tmgb.tm_library_prepare_host(ts, n_r, n_theta, dr)
+    _same(h, O.prepare_library(ts, n_r, n_theta, dr))
+
+
+@pytest.mark.parametrize("unit", [False, True])
+def test_prepare_kinematic_mirror_matches_oracle(lib, unit):
+    ts = synth.kinematic_library("hcp", step_deg=2.0)
+    h = tmgb.tm_library_prepare_host(ts, 128, 360, unit_intensity=unit)
+    ref = O.prepare_library(ts, 128, 360, unit_intensity=unit)
+    _same(h, ref)
+    assert h["info"]["mirror"] == 1 and h["info"]["n_templates"] == 2 * ts.n_templates
+
+
+def test_prepare_drops_out_of_grid_and_merges(lib):
+    ts = synth.TemplateSet(np.array([0, 5]), np.array([3.0, 3.2, 9.6, 4.0, 0.2]),
+                           np.array([0.0, 0.001, 1.0, -math.pi / 2, 2.0]), np.array([1.0, 2.0, 3.0, 4.0, 5.0]))
+    h = tmgb.tm_library_prepare_host(ts, 8, 4)
+    _same(h, O.prepare_library(ts, 8, 4))
+    assert h["info"]["n_spots"] == 3          # (3,0) merged, 9.6 -> 10 dropped, (4,3), (0,*)
+
+
+def test_rotational_order_is_a_true_period(lib):
+    """A template reported with order n has Q(s + n_theta/n) == Q(s) for every pattern
+    (checked with the oracle's Q table), and order 1 templates are not periodic."""
+    rng = np.random.default_rng(1)
+    base = np.array([4.0, 6.0, 6.0])
+    th = np.array([0.2, 1.0, 2.5])
+    # template 0: 3-fold copy; template 1: 2-fold; template 2: generic
+    r = np.concatenate([np.tile(base, 3), np.tile(base, 2), base])
+    t = np.concatenate([np.concatenate([th + i * 2 * math.pi / 3 for i in range(3)]),
+                        np.concatenate([th + i * math.pi for i in range(2)]), th])
+    I = np.concatenate([np.tile([1.0, 2.0, 3.0], 3), np.tile([1.0, 2.0, 3.0], 2), [1.0, 2.0, 3.0]])
+    ts = synth.TemplateSet(np.array([0, 9, 15, 18]), r, t, I)
+    h = tmgb.tm_library_prepare_host(ts, 8, 36)
+    ref = O.prepare_library(ts, 8, 36)
+    _same(h, ref)
+    assert list(h["order"]) == [3, 2, 1]
+    full = O.scores_full(rng.random((2, 8, 36)), ref)
+    for k, n in enumerate(h["order"]):
+        per = 36 // n
+        assert np.allclose(full[:, k], np.roll(full[:, k], per, axis=1), atol=1e-14) == (n > 1) or n == 1
+
+
+@pytest.mark.parametrize("bad", ["n_r", "theta", "dr", "offsets", "nan"])
+def test_prepare_rejects_bad_descriptor(lib, bad):
+    ts = synth.TemplateSet(np.array([0, 2]), np.array([3.0, 4.0]), np.array([0.0, 1.0]), np.array([1.0, 1.0]))
+    kw = dict(n_r=8, n_theta=36, dr=1.0)
+    if bad == "n_r":
+        kw["n_r"] = 0
+    elif bad == "theta":
+        kw["n_theta"] = 5000
+    elif bad == "dr":
+        kw["dr"] = -1.0
+    elif bad == "offsets":
+        ts.offsets = np.array([0, 3])
+        ts.a = np.array([3.0, 4.0, 5.0])
+        ts.b = np.array([0.0, 1.0, 2.0])
+        ts.intensity = np.array([1.0, 1.0, 1.0])
+        ts.offsets = np.array([1, 3])
+    elif bad == "nan":
+        ts.a = np.array([3.0, np.nan])
+    with pytest.raises(tmgb.TmError) as e:
+        tmgb.tm_library_prepare_host(ts, **kw)
+    assert e.value.code == tmgb.TM_ERR_INVALID_ARG
