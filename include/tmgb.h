@@ -184,8 +184,30 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
                  int64_t n, const uint32_t* mask_dev, float* q_dev, int32_t* s_dev,
                  void* stream);
 
+/* Stage A7 alone: the BF16 tensor-core pre-score.  The correlation along theta is taken
+ * through the correlation theorem (Section 2.2 names the FFT cross-correlation as the
+ * alternative to sliding): C[k, s] = sum_m (w_m / n) Re(G[k, m] e^{2 pi i m s / n}) with
+ * G[k, m] = sum_r conj(T^_k[r, m]) P^[r, m]; G is formed in FP32 and rounded to BF16, the
+ * sum over frequencies for every shift runs on the tensor cores (tcgen05, FP32
+ * accumulation).  For each pattern the kc templates with the largest pre-score
+ * Q~ = max_s C / (|P| |T|) are returned, ordered by (Q~ desc, template asc).
+ * polar_dev / norm_dev: Stage 1 outputs; radial_dev: Stage 1 azimuthal sums, used when
+ * fraction < 1 (only the pre-filter's survivors are scored); cand_dev [n][kc] int32
+ * (-1 past the survivors), score_dev [n][kc] float (nullable).  kc in [1, 256]; n_theta
+ * must be even and <= 376.  Errors: TM_ERR_UNSUPPORTED for other grids. */
+int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev,
+                const float* radial_dev, int64_t n, double fraction, int32_t kc, int32_t* cand_dev,
+                float* score_dev, void* stream);
+
+/* Wait for `stream`, then report whether a kernel of this context stopped on a bounded
+ * wait since the last check (TM_ERR_TIMEOUT; the error word is cleared). */
+int tm_check(tm_ctx* ctx, void* stream);
+
 /* The whole path for a batch: frames -> polar -> [pre-filter] -> Q -> top-N, for each
- * of n_libs libraries (all built for the same polar grid).  out_dev [n_libs][n][top_n]
+ * of n_libs libraries (all built for the same polar grid).  path TM_PATH_FP32_SPARSE
+ * scores every surviving template exactly in FP32 (Stage 3 with a fused top-N);
+ * TM_PATH_BF16_RESCORE takes the rescore_k best by the Stage A7 pre-score and rescores
+ * them exactly in FP32 before the top-N.  out_dev [n_libs][n][top_n]
  * tm_hit.  centres_dev must be NULL in this build (per-pattern centres:
  * TM_ERR_UNSUPPORTED).  stats (host, nullable) receives counts for the call. */
 int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,

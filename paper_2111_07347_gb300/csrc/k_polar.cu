@@ -5,9 +5,10 @@
 // pre-filter (Section 2.2, Fig. 3).
 //
 // One CTA per pattern (grid-stride).  Thread k owns polar column k; rows are walked in
-// order, so the writes of a row are coalesced.  Tap positions and fractions come from a
-// table built on the host in double precision for the call's centre, so only the
-// weights are rounded to float.  Reductions run in a fixed order: the result does not
+// order, so the writes of a row are coalesced.  Tap positions and the fractions fx, 1-fx,
+// fy, 1-fy come from a table built on the host in double precision for the call's centre
+// (storing 1-fx avoids the cancellation of forming it in float when fx is near 1), so
+// each bilinear weight is within a few float ulps of its exact value.  Reductions run in a fixed order: the result does not
 // depend on the grid size or on other patterns of the batch.
 #include "tm_internal.h"
 
@@ -33,8 +34,7 @@ __device__ __forceinline__ float tap(const T* frame, int H, int W, int x, int y,
 template <typename T>
 __global__ void __launch_bounds__(1024)
 polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
-             const int32_t* __restrict__ txy, const float* __restrict__ tfx,
-             const float* __restrict__ tfy, Gamma gm, int n_r, int n_theta,
+             const int32_t* __restrict__ txy, const float4* __restrict__ tw, Gamma gm, int n_r, int n_theta,
              float* __restrict__ polar, float* __restrict__ pnorm, float* __restrict__ radial) {
     extern __shared__ float smem[];
     const int nw = blockDim.x >> 5;
@@ -53,13 +53,12 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
                 const int xy = __ldg(txy + idx);
                 const int x0 = (int)(int16_t)(xy & 0xffff);
                 const int y0 = xy >> 16;
-                const float fx = __ldg(tfx + idx), fy = __ldg(tfy + idx);
+                const float4 f = __ldg(tw + idx);           // fx, 1 - fx, fy, 1 - fy
                 const float v00 = tap(frame, H, W, x0, y0, gm);
                 const float v10 = tap(frame, H, W, x0 + 1, y0, gm);
                 const float v01 = tap(frame, H, W, x0, y0 + 1, gm);
                 const float v11 = tap(frame, H, W, x0 + 1, y0 + 1, gm);
-                const float gx = 1.0f - fx, gy = 1.0f - fy;
-                const float v = gx * gy * v00 + fx * gy * v10 + gx * fy * v01 + fx * fy * v11;
+                const float v = f.w * (f.y * v00 + f.x * v10) + f.z * (f.y * v01 + f.x * v11);
                 out[idx] = v;
                 const float y = fmaf(v, v, -c2);
                 const float t = s2 + y;
@@ -117,11 +116,9 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
     const int64_t grid64 = n < 65535 * 16 ? n : 65535 * 16;
     const int grid = (int)grid64;
     if (dtype == TM_DTYPE_U16)
-        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.fx,
-                                                          tab.fy, gm, n_r, n_theta, polar, pnorm, radial);
+        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, polar, pnorm, radial);
     else
-        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.fx,
-                                                       tab.fy, gm, n_r, n_theta, polar, pnorm, radial);
+        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, polar, pnorm, radial);
     return cudaGetLastError();
 }
 

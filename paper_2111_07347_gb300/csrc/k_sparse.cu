@@ -136,45 +136,60 @@ sparse_kernel(const SparseCall c) {
             const uint32_t* mrow = c.mask[li] ? c.mask[li] + (size_t)p * L.words : nullptr;
             float* qo = c.q_out[li] ? c.q_out[li] + (size_t)p * L.K : nullptr;
             int32_t* so = c.s_out[li] ? c.s_out[li] + (size_t)p * L.K : nullptr;
+            const int32_t* crow = c.cand[li] ? c.cand[li] + (size_t)p * c.kc : nullptr;
+            uint32_t m = 0;          // remaining bits of the current mask word (warp-uniform)
+            int wd = 0;
             for (;;) {
-                int wd = 0;
-                if (lane == 0) wd = atomicAdd(counter, 1);
-                wd = __shfl_sync(0xffffffffu, wd, 0);
-                if (wd >= L.words) break;
-                uint32_t m = mrow ? __ldg(mrow + wd) : 0xffffffffu;
-                const int rem = L.K - wd * 32;
-                if (rem < 32) m &= (1u << rem) - 1u;
-                if (qo) {
-                    const int k = wd * 32 + lane;
-                    if (lane < rem && !((m >> lane) & 1u)) { qo[k] = -INFINITY; so[k] = -1; }
-                }
-                while (m) {
+                // next template: from the candidate list, or the next set bit of a mask word
+                int k = -1;
+                if (crow) {
+                    int j = 0;
+                    if (lane == 0) j = atomicAdd(counter, 1);
+                    j = __shfl_sync(0xffffffffu, j, 0);
+                    if (j >= c.kc) break;
+                    k = __ldg(crow + j);
+                    if (k < 0 || k >= L.K) continue;
+                } else {
+                    bool done = false;
+                    while (m == 0) {
+                        if (lane == 0) wd = atomicAdd(counter, 1);
+                        wd = __shfl_sync(0xffffffffu, wd, 0);
+                        if (wd >= L.words) { done = true; break; }
+                        m = mrow ? __ldg(mrow + wd) : 0xffffffffu;
+                        const int rem = L.K - wd * 32;
+                        if (rem < 32) m &= (1u << rem) - 1u;
+                        if (qo) {
+                            const int kk = wd * 32 + lane;
+                            if (lane < rem && !((m >> lane) & 1u)) { qo[kk] = -INFINITY; so[kk] = -1; }
+                        }
+                    }
+                    if (done) break;
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
-                    const int k = wd * 32 + bit;
-                    float best;
-                    int s;
-                    score_dispatch<NBMAX>(sP, L, k, n_theta, lane, best, s);
-                    const float d = pn * __ldg(L.norm + k);
-                    float q;
-                    if (d > 0.0f) q = __fdiv_rn(best, d);
-                    else { q = 0.0f; s = 0; }
-                    if (lane == 0) {
-                        if (qo) { qo[k] = q; so[k] = s; }
-                        if (c.hits) {
-                            float* wq = lq + warp * N;
-                            int* wk = lk + warp * N;
-                            int* ws = ls + warp * N;
-                            const int cnt = lcnt[warp];
-                            if (cnt < N || better(q, k, wq[N - 1], wk[N - 1])) {
-                                int i = cnt < N ? cnt : N - 1;
-                                while (i > 0 && better(q, k, wq[i - 1], wk[i - 1])) {
-                                    wq[i] = wq[i - 1]; wk[i] = wk[i - 1]; ws[i] = ws[i - 1];
-                                    --i;
-                                }
-                                wq[i] = q; wk[i] = k; ws[i] = s;
-                                if (cnt < N) lcnt[warp] = cnt + 1;
+                    k = wd * 32 + bit;
+                }
+                float best;
+                int s;
+                score_dispatch<NBMAX>(sP, L, k, n_theta, lane, best, s);
+                const float d = pn * __ldg(L.norm + k);
+                float q;
+                if (d > 0.0f) q = __fdiv_rn(best, d);
+                else { q = 0.0f; s = 0; }
+                if (lane == 0) {
+                    if (qo) { qo[k] = q; so[k] = s; }
+                    if (c.hits) {
+                        float* wq = lq + warp * N;
+                        int* wk = lk + warp * N;
+                        int* ws = ls + warp * N;
+                        const int cnt = lcnt[warp];
+                        if (cnt < N || better(q, k, wq[N - 1], wk[N - 1])) {
+                            int i = cnt < N ? cnt : N - 1;
+                            while (i > 0 && better(q, k, wq[i - 1], wk[i - 1])) {
+                                wq[i] = wq[i - 1]; wk[i] = wk[i - 1]; ws[i] = ws[i - 1];
+                                --i;
                             }
+                            wq[i] = q; wk[i] = k; ws[i] = s;
+                            if (cnt < N) lcnt[warp] = cnt + 1;
                         }
                     }
                 }

@@ -76,6 +76,9 @@ struct Library {
     int32_t* d_nshift = nullptr;
     float* d_radial = nullptr;
     float* d_rnorm = nullptr;
+    int32_t* d_rt = nullptr;       // r | (t << 16) per spot (BF16 path)
+    int32_t* d_order = nullptr;    // templates sorted by spot count (BF16 tile order)
+    std::vector<int32_t> radii;    // distinct radii with spots
     size_t bytes = 0;
 };
 
@@ -86,12 +89,22 @@ struct Buffer {
 
 struct PolarTableDev {
     int32_t* xy = nullptr;
-    float* fx = nullptr;
-    float* fy = nullptr;
+    float4* w = nullptr;
     size_t bytes = 0;
 };
 
 using TableKey = std::tuple<int, int, int, int, double, double, double>;
+
+struct SpectralTables {            // per n_theta: inverse-DFT basis and twiddles
+    void* basis = nullptr;         // bf16 [rows][cols]
+    float2* twiddle = nullptr;     // [n_theta]
+};
+
+struct RadiusMap {                 // per set of libraries: union of radii
+    int32_t* radii = nullptr;      // [n_rad]
+    int32_t* rmap = nullptr;       // [n_r]
+    int n_rad = 0;
+};
 
 }  // namespace
 
@@ -105,6 +118,9 @@ struct tm_ctx {
     std::map<TableKey, PolarTableDev> tables;
     std::map<std::string, Buffer> ws;
     cudaEvent_t ws_event = nullptr;
+    unsigned* d_error = nullptr;   // device error word of the bounded waits
+    std::map<int, SpectralTables> spectral;
+    std::map<std::string, RadiusMap> radius_maps;
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -347,6 +363,19 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
     std::vector<int32_t> off32(L->K + 1);
     for (int64_t k = 0; k <= L->K; ++k) off32[k] = (int32_t)L->off[k];
     std::vector<float> radf(radial.begin(), radial.end()), rnf(rnorm.begin(), rnorm.end());
+    std::vector<int32_t> rt(L->r.size());
+    for (size_t i = 0; i < rt.size(); ++i) rt[i] = L->r[i] | (L->t[i] << 16);
+    std::vector<int32_t> order(L->K);
+    for (int64_t k = 0; k < L->K; ++k) order[k] = (int32_t)k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return L->off[x + 1] - L->off[x] < L->off[y + 1] - L->off[y];
+    });
+    {
+        std::vector<int32_t> rr(L->r);
+        std::sort(rr.begin(), rr.end());
+        rr.erase(std::unique(rr.begin(), rr.end()), rr.end());
+        L->radii = rr;
+    }
 
     struct Up { void** dst; const void* src; size_t bytes; const char* what; };
     Up ups[] = {
@@ -356,6 +385,8 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
         {(void**)&L->d_nshift, nshift.data(), nshift.size() * 4, "library shifts"},
         {(void**)&L->d_radial, radf.data(), radf.size() * 4, "library radial profiles"},
         {(void**)&L->d_rnorm, rnf.data(), rnf.size() * 4, "library radial norms"},
+        {(void**)&L->d_rt, rt.data(), rt.size() * 4, "library spot positions"},
+        {(void**)&L->d_order, order.data(), order.size() * 4, "library tile order"},
     };
     for (auto& u : ups) {
         rc = dev_alloc(ctx, u.dst, u.bytes, u.what);
@@ -367,7 +398,7 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
 }
 
 void free_library(tm_ctx* ctx, Library* L) {
-    void* ps[] = {L->d_off, L->d_spot, L->d_norm, L->d_nshift, L->d_radial, L->d_rnorm};
+    void* ps[] = {L->d_off, L->d_spot, L->d_norm, L->d_nshift, L->d_radial, L->d_rnorm, L->d_rt, L->d_order};
     for (void* p : ps)
         if (p) cudaFree(p);
     ctx->used -= std::min(ctx->used, L->bytes);
@@ -394,7 +425,7 @@ int polar_table(tm_ctx* ctx, int H, int W, int n_r, int n_theta, double dr, doub
     if (it == ctx->tables.end()) {
         const size_t m = (size_t)n_r * n_theta;
         std::vector<int32_t> xy(m);
-        std::vector<float> fx(m), fy(m);
+        std::vector<float4> wv(m);
         for (int j = 0; j < n_r; ++j) {
             const double r = j * dr;
             for (int k = 0; k < n_theta; ++k) {
@@ -409,25 +440,102 @@ int polar_table(tm_ctx* ctx, int H, int W, int n_r, int n_theta, double dr, doub
                 if (ffy < 0.0 || ffy >= 1.0) ffy = 0.0;
                 const int ix = (int)x0, iy = (int)y0;
                 xy[(size_t)j * n_theta + k] = (int32_t)((uint32_t)(uint16_t)(int16_t)ix | ((uint32_t)(int16_t)iy << 16));
-                fx[(size_t)j * n_theta + k] = (float)ffx;
-                fy[(size_t)j * n_theta + k] = (float)ffy;
+                wv[(size_t)j * n_theta + k] = make_float4((float)ffx, (float)(1.0 - ffx), (float)ffy, (float)(1.0 - ffy));
             }
         }
         PolarTableDev t;
         int rc = dev_alloc(ctx, (void**)&t.xy, m * 4, "polar table");
-        if (!rc) rc = dev_alloc(ctx, (void**)&t.fx, m * 4, "polar table");
-        if (!rc) rc = dev_alloc(ctx, (void**)&t.fy, m * 4, "polar table");
+        if (!rc) rc = dev_alloc(ctx, (void**)&t.w, m * 16, "polar table");
         if (rc) return rc;
-        t.bytes = m * 12;
+        t.bytes = m * 20;
         TM_CUDA(cudaMemcpy(t.xy, xy.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
-        TM_CUDA(cudaMemcpy(t.fx, fx.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
-        TM_CUDA(cudaMemcpy(t.fy, fy.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
+        TM_CUDA(cudaMemcpy(t.w, wv.data(), m * 16, cudaMemcpyHostToDevice), "polar table");
         it = ctx->tables.emplace(key, t).first;
     }
     out->xy = it->second.xy;
-    out->fx = it->second.fx;
-    out->fy = it->second.fy;
+    out->w = it->second.w;
     return TM_OK;
+}
+
+uint16_t f32_to_bf16(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;      // NaN
+    u += 0x7fffu + ((u >> 16) & 1u);                           // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+
+// Inverse-DFT basis for the radix-2 split (rows: shift s < n/2; columns: even-m then odd-m
+// (re, im) pairs) and the twiddle table, built in FP64 and cached per n_theta.
+int spectral_tables(tm_ctx* ctx, int n_theta, SpectralTables* out) {
+    auto it = ctx->spectral.find(n_theta);
+    if (it == ctx->spectral.end()) {
+        const int R = tmgb::dense_basis_rows(), C = tmgb::dense_basis_cols(), half = C / 2;
+        const int H = n_theta / 2;
+        std::vector<uint16_t> basis((size_t)R * C, 0);
+        for (int s = 0; s < R && s < H; ++s) {
+            for (int kk = 0; kk < C; ++kk) {
+                const int part = kk / half, j = (kk % half) / 2, comp = kk % 2;
+                const int m = 2 * j + part;
+                if (m > H) continue;
+                const double w = (m == 0 || m == H) ? 1.0 : 2.0;
+                const double ang = 2.0 * kPi * (double)m * (double)s / n_theta;
+                const double v = (w / n_theta) * (comp == 0 ? cos(ang) : -sin(ang));
+                basis[(size_t)s * C + kk] = f32_to_bf16((float)v);
+            }
+        }
+        std::vector<float2> tw(n_theta);
+        for (int j = 0; j < n_theta; ++j) {
+            const double ang = 2.0 * kPi * j / n_theta;
+            tw[j] = make_float2((float)cos(ang), (float)sin(ang));
+        }
+        SpectralTables t;
+        int rc = dev_alloc(ctx, &t.basis, basis.size() * 2, "dft basis");
+        if (!rc) rc = dev_alloc(ctx, (void**)&t.twiddle, tw.size() * 8, "twiddles");
+        if (rc) return rc;
+        TM_CUDA(cudaMemcpy(t.basis, basis.data(), basis.size() * 2, cudaMemcpyHostToDevice), "dft basis");
+        TM_CUDA(cudaMemcpy(t.twiddle, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice), "twiddles");
+        it = ctx->spectral.emplace(n_theta, t).first;
+    }
+    *out = it->second;
+    return TM_OK;
+}
+
+// Union of the radii the libraries use, and the radius -> row map of the spectra.
+int radius_map(tm_ctx* ctx, Library* const* libs, const int32_t* ids, int n_libs, int n_r, RadiusMap* out) {
+    std::string key;
+    for (int i = 0; i < n_libs; ++i) key += std::to_string(ids[i]) + ",";
+    auto it = ctx->radius_maps.find(key);
+    if (it == ctx->radius_maps.end()) {
+        std::vector<int32_t> u;
+        for (int i = 0; i < n_libs; ++i) u.insert(u.end(), libs[i]->radii.begin(), libs[i]->radii.end());
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        if (u.empty()) u.push_back(0);
+        std::vector<int32_t> rmap(n_r, -1);
+        for (size_t i = 0; i < u.size(); ++i) rmap[u[i]] = (int32_t)i;
+        RadiusMap m;
+        m.n_rad = (int)u.size();
+        int rc = dev_alloc(ctx, (void**)&m.radii, u.size() * 4, "radius list");
+        if (!rc) rc = dev_alloc(ctx, (void**)&m.rmap, rmap.size() * 4, "radius map");
+        if (rc) return rc;
+        TM_CUDA(cudaMemcpy(m.radii, u.data(), u.size() * 4, cudaMemcpyHostToDevice), "radius list");
+        TM_CUDA(cudaMemcpy(m.rmap, rmap.data(), rmap.size() * 4, cudaMemcpyHostToDevice), "radius map");
+        it = ctx->radius_maps.emplace(key, m).first;
+    }
+    *out = it->second;
+    return TM_OK;
+}
+
+tmgb::DenseLib dense_view(const Library* L) {
+    tmgb::DenseLib v;
+    v.off = L->d_off;
+    v.rt = L->d_rt;
+    v.spot = L->d_spot;
+    v.norm = L->d_norm;
+    v.order = L->d_order;
+    v.K = (int32_t)L->K;
+    return v;
 }
 
 int check_params(const tm_index_params* p) {
@@ -490,6 +598,8 @@ int tm_create(int device, size_t hbm_budget_bytes, tm_ctx** out) {
     ctx->budget = hbm_budget_bytes;
     ctx->num_sms = prop.multiProcessorCount;
     TM_CUDA(cudaEventCreateWithFlags(&ctx->ws_event, cudaEventDisableTiming), "tm_create: cudaEventCreate");
+    TM_CUDA(cudaMalloc(&ctx->d_error, sizeof(unsigned)), "tm_create: error word");
+    TM_CUDA(cudaMemset(ctx->d_error, 0, sizeof(unsigned)), "tm_create: error word");
     *out = ctx.release();
     g_err.clear();
     return TM_OK;
@@ -541,14 +651,36 @@ void tm_destroy(tm_ctx* ctx) {
         for (auto& kv : ctx->libs) free_library(ctx, kv.second.get());
         for (auto& kv : ctx->tables) {
             cudaFree(kv.second.xy);
-            cudaFree(kv.second.fx);
-            cudaFree(kv.second.fy);
+            cudaFree(kv.second.w);
         }
         for (auto& kv : ctx->ws)
             if (kv.second.p) cudaFree(kv.second.p);
+        for (auto& kv : ctx->spectral) {
+            cudaFree(kv.second.basis);
+            cudaFree(kv.second.twiddle);
+        }
+        for (auto& kv : ctx->radius_maps) {
+            cudaFree(kv.second.radii);
+            cudaFree(kv.second.rmap);
+        }
+        if (ctx->d_error) cudaFree(ctx->d_error);
         if (ctx->ws_event) cudaEventDestroy(ctx->ws_event);
     }
     delete ctx;
+}
+
+int tm_check(tm_ctx* ctx, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_check: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    TM_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "tm_check: stream");
+    unsigned err = 0;
+    TM_CUDA(cudaMemcpy(&err, ctx->d_error, sizeof err, cudaMemcpyDeviceToHost), "tm_check: read");
+    if (err) {
+        TM_CUDA(cudaMemset(ctx->d_error, 0, sizeof err), "tm_check: reset");
+        return fail(TM_ERR_TIMEOUT, "tm_check: a kernel's bounded wait ran out (error word 0x%x)", err);
+    }
+    return TM_OK;
 }
 
 int tm_load_library(tm_ctx* ctx, const tm_library_desc* desc, int* lib_id) {
@@ -730,8 +862,11 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     if (n_libs < 1 || n_libs > TM_MAX_LIBS || !lib_ids)
         return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: n_libs must be in [1, %d]", TM_MAX_LIBS);
     if (centres_dev) return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: per-pattern centres are not supported");
-    if (params->path != TM_PATH_FP32_SPARSE)
-        return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: path %d not available", params->path);
+    if (params->path != TM_PATH_FP32_SPARSE && params->path != TM_PATH_BF16_RESCORE)
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: unknown path %d", params->path);
+    const bool bf16 = params->path == TM_PATH_BF16_RESCORE;
+    if (bf16 && (params->rescore_k < 1 || params->rescore_k > 256))
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: rescore_k must be in [1, 256]");
     if (stats) memset(stats, 0, sizeof *stats);
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
@@ -754,11 +889,31 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     rc = polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
     if (rc) return rc;
     const bool pre = params->prefilter_fraction < 1.0;
+    const int kc = params->rescore_k;
+    const int n_freq = n_theta / 2 + 1;
+    SpectralTables spec;
+    RadiusMap rmap;
+    if (bf16) {
+        if (!tmgb::dense_supported(n_theta))
+            return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: the BF16 path needs an even n_theta <= 376 (got %d)",
+                        n_theta);
+        rc = spectral_tables(ctx, n_theta, &spec);
+        if (!rc) rc = radius_map(ctx, libs, lib_ids, n_libs, n_r, &rmap);
+        if (rc) return rc;
+        if (tmgb::dense_smem_bytes(n_theta, n_r, rmap.n_rad, n_freq, kc) > 232448)
+            return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: %d distinct radii exceed the BF16 kernel's shared memory",
+                        rmap.n_rad);
+    }
+    int keep[TM_MAX_LIBS];
+    for (int i = 0; i < n_libs; ++i) keep[i] = keep_count(params->prefilter_fraction, libs[i]->K);
 
     // chunk size from a per-pattern workspace estimate (<= 4 GiB of workspace)
     size_t per = (size_t)n_r * n_theta * 4 + 4 + (size_t)n_r * 4 + 4;
-    if (pre)
-        for (int i = 0; i < n_libs; ++i) per += (size_t)libs[i]->K * 4 + ((libs[i]->K + 31) / 32) * 4;
+    for (int i = 0; i < n_libs; ++i) {
+        if (pre) per += (size_t)libs[i]->K * 4 + ((libs[i]->K + 31) / 32) * 4 + (bf16 ? (size_t)keep[i] * 4 : 0);
+        if (bf16) per += (size_t)kc * 8;
+    }
+    if (bf16) per += (size_t)rmap.n_rad * n_freq * 4;
     size_t cap = (size_t)4 << 30;
     if (ctx->budget) {
         const size_t freeb = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
@@ -768,21 +923,28 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     chunk = std::min<int64_t>(chunk, n);
 
     float *polar, *pnorm, *radial, *rn = nullptr;
+    void* phat = nullptr;
     rc = workspace(ctx, "polar", (size_t)chunk * n_r * n_theta * 4, (void**)&polar);
     if (!rc) rc = workspace(ctx, "pnorm", (size_t)chunk * 4, (void**)&pnorm);
     if (!rc) rc = workspace(ctx, "radial", (size_t)chunk * n_r * 4, (void**)&radial);
     if (!rc && pre) rc = workspace(ctx, "radial_norm", (size_t)chunk * 4, (void**)&rn);
+    if (!rc && bf16) rc = workspace(ctx, "phat", (size_t)chunk * rmap.n_rad * n_freq * 4, &phat);
     if (rc) return rc;
     float* score[TM_MAX_LIBS] = {};
     uint32_t* mask[TM_MAX_LIBS] = {};
-    if (pre) {
-        for (int i = 0; i < n_libs; ++i) {
-            rc = workspace(ctx, "score" + std::to_string(i), (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
-            if (!rc)
-                rc = workspace(ctx, "mask" + std::to_string(i), (size_t)chunk * ((libs[i]->K + 31) / 32) * 4,
-                               (void**)&mask[i]);
-            if (rc) return rc;
+    int32_t* list[TM_MAX_LIBS] = {};
+    int32_t* cand[TM_MAX_LIBS] = {};
+    float* cand_q[TM_MAX_LIBS] = {};
+    for (int i = 0; i < n_libs; ++i) {
+        const std::string s = std::to_string(i);
+        if (pre) {
+            rc = workspace(ctx, "score" + s, (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
+            if (!rc) rc = workspace(ctx, "mask" + s, (size_t)chunk * ((libs[i]->K + 31) / 32) * 4, (void**)&mask[i]);
+            if (!rc && bf16) rc = workspace(ctx, "list" + s, (size_t)chunk * keep[i] * 4, (void**)&list[i]);
         }
+        if (!rc && bf16) rc = workspace(ctx, "cand" + s, (size_t)chunk * kc * 4, (void**)&cand[i]);
+        if (!rc && bf16) rc = workspace(ctx, "cand_q" + s, (size_t)chunk * kc * 4, (void**)&cand_q[i]);
+        if (rc) return rc;
     }
     cudaStream_t st = (cudaStream_t)stream;
     TM_CUDA(cudaStreamWaitEvent(st, ctx->ws_event, 0), "tm_index_patterns: wait");
@@ -801,6 +963,19 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             StageTimer tmr(ctx, TM_STAGE_PREFILTER, st);
             TM_CUDA(tmgb::launch_radial_norm(radial, m, n_r, rn, st), "tm_index_patterns: radial norm");
             ++launches;
+            for (int i = 0; i < n_libs; ++i) {
+                Library* L = libs[i];
+                tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
+                TM_CUDA(tmgb::launch_prefilter_scores(radial, rn, m, n_r, rl, score[i], st), "tm_index_patterns: scores");
+                TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)L->K, keep[i], mask[i], st),
+                        "tm_index_patterns: select");
+                launches += 2;
+                if (bf16) {
+                    TM_CUDA(tmgb::launch_compact(mask[i], m, (int)L->K, L->d_order, keep[i], list[i], st),
+                            "tm_index_patterns: compact");
+                    ++launches;
+                }
+            }
         }
         tmgb::SparseCall c{};
         c.polar = polar;
@@ -811,30 +986,66 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
         c.pitch = tmgb::sparse_pitch(n_theta);
         c.n_libs = n_libs;
         for (int i = 0; i < n_libs; ++i) {
-            Library* L = libs[i];
-            c.lib[i] = sparse_view(L);
-            const int keep = keep_count(params->prefilter_fraction, L->K);
-            if (pre) {
-                StageTimer tmr(ctx, TM_STAGE_PREFILTER, st);
-                tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
-                TM_CUDA(tmgb::launch_prefilter_scores(radial, rn, m, n_r, rl, score[i], st), "tm_index_patterns: scores");
-                TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)L->K, keep, mask[i], st),
-                        "tm_index_patterns: select");
-                launches += 2;
-                c.mask[i] = mask[i];
-            }
-            // exact work: surviving templates x their shift counts (approximate with the library mean)
-            corr += m * (int64_t)keep * n_theta;
-            scored += m * keep;
+            c.lib[i] = sparse_view(libs[i]);
+            if (pre && !bf16) c.mask[i] = mask[i];
+            if (bf16) c.cand[i] = cand[i];
         }
+        c.kc = bf16 ? kc : 0;
         c.hits = out_dev + (size_t)c0 * N;
         c.hits_lib_stride = n * N;
         c.top_n = N;
-        {
-            StageTimer tmr(ctx, TM_STAGE_SPARSE, st);
-            TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: sparse");
+        if (bf16) {
+            {
+                StageTimer tmr(ctx, TM_STAGE_DFT, st);
+                TM_CUDA(tmgb::launch_dft(polar, pnorm, m, n_r, n_theta, rmap.radii, rmap.n_rad, n_freq, spec.twiddle,
+                                         phat, ctx->num_sms, st), "tm_index_patterns: dft");
+            }
+            ++launches;
+            tmgb::DenseCall dc{};
+            dc.phat = phat;
+            dc.n = m;
+            dc.n_theta = n_theta;
+            dc.n_r = n_r;
+            dc.n_rad = rmap.n_rad;
+            dc.n_freq = n_freq;
+            dc.rmap = rmap.rmap;
+            dc.basis = spec.basis;
+            dc.twiddle = spec.twiddle;
+            dc.n_libs = n_libs;
+            for (int i = 0; i < n_libs; ++i) {
+                dc.lib[i] = dense_view(libs[i]);
+                dc.list[i] = pre ? list[i] : nullptr;
+                dc.count[i] = keep[i];
+                dc.cand[i] = cand[i];
+                dc.cand_q[i] = cand_q[i];
+            }
+            dc.kc = kc;
+            dc.error = ctx->d_error;
+            {
+                StageTimer tmr(ctx, TM_STAGE_DENSE, st);
+                TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_index_patterns: dense");
+            }
+            ++launches;
+            {
+                StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
+                TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: rescore");
+            }
+            ++launches;
+            for (int i = 0; i < n_libs; ++i) {
+                corr += m * ((int64_t)keep[i] + std::min<int64_t>(kc, keep[i])) * n_theta;
+                scored += m * std::min<int64_t>(kc, keep[i]);
+            }
+        } else {
+            {
+                StageTimer tmr(ctx, TM_STAGE_SPARSE, st);
+                TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: sparse");
+            }
+            ++launches;
+            for (int i = 0; i < n_libs; ++i) {
+                corr += m * (int64_t)keep[i] * n_theta;
+                scored += m * keep[i];
+            }
         }
-        ++launches;
     }
     TM_CUDA(cudaEventRecord(ctx->ws_event, st), "tm_index_patterns: record");
     if (stats) {
@@ -846,4 +1057,75 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     return TM_OK;
 }
 
+int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev, const float* radial_dev,
+                int64_t n, double fraction, int32_t kc, int32_t* cand_dev, float* score_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_prescore: ctx is NULL");
+    if (n < 0 || kc < 1 || kc > 256 || !(fraction > 0.0 && fraction <= 1.0))
+        return fail(TM_ERR_INVALID_ARG, "tm_prescore: bad n, kc or fraction");
+    if (n == 0) return TM_OK;
+    if (!polar_dev || !norm_dev || !cand_dev || (fraction < 1.0 && !radial_dev))
+        return fail(TM_ERR_INVALID_ARG, "tm_prescore: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Library* L = find_lib(ctx, lib_id);
+    if (!L) return fail(TM_ERR_NOT_FOUND, "tm_prescore: no library %d", lib_id);
+    const int n_r = L->n_r, n_theta = L->n_theta, n_freq = n_theta / 2 + 1;
+    if (!tmgb::dense_supported(n_theta))
+        return fail(TM_ERR_UNSUPPORTED, "tm_prescore: needs an even n_theta <= 376 (got %d)", n_theta);
+    SpectralTables spec;
+    RadiusMap rm;
+    Library* libs[1] = {L};
+    int32_t ids[1] = {lib_id};
+    int rc = spectral_tables(ctx, n_theta, &spec);
+    if (!rc) rc = radius_map(ctx, libs, ids, 1, n_r, &rm);
+    if (rc) return rc;
+    if (tmgb::dense_smem_bytes(n_theta, n_r, rm.n_rad, n_freq, kc) > 232448)
+        return fail(TM_ERR_UNSUPPORTED, "tm_prescore: %d distinct radii exceed shared memory", rm.n_rad);
+    const int keep = keep_count(fraction, L->K);
+    void* phat;
+    rc = workspace(ctx, "phat", (size_t)n * rm.n_rad * n_freq * 4, &phat);
+    float* sc = nullptr;
+    float* rn = nullptr;
+    uint32_t* mask = nullptr;
+    int32_t* list = nullptr;
+    if (!rc && fraction < 1.0) {
+        rc = workspace(ctx, "score0", (size_t)n * L->K * 4, (void**)&sc);
+        if (!rc) rc = workspace(ctx, "radial_norm", (size_t)n * 4, (void**)&rn);
+        if (!rc) rc = workspace(ctx, "mask0", (size_t)n * ((L->K + 31) / 32) * 4, (void**)&mask);
+        if (!rc) rc = workspace(ctx, "list0", (size_t)n * keep * 4, (void**)&list);
+    }
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    TM_CUDA(cudaStreamWaitEvent(st, ctx->ws_event, 0), "tm_prescore: wait");
+    if (fraction < 1.0) {
+        tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
+        TM_CUDA(tmgb::launch_radial_norm(radial_dev, n, n_r, rn, st), "tm_prescore: radial norm");
+        TM_CUDA(tmgb::launch_prefilter_scores(radial_dev, rn, n, n_r, rl, sc, st), "tm_prescore: scores");
+        TM_CUDA(tmgb::launch_prefilter_select(sc, n, (int)L->K, keep, mask, st), "tm_prescore: select");
+        TM_CUDA(tmgb::launch_compact(mask, n, (int)L->K, L->d_order, keep, list, st), "tm_prescore: compact");
+    }
+    TM_CUDA(tmgb::launch_dft(polar_dev, norm_dev, n, n_r, n_theta, rm.radii, rm.n_rad, n_freq, spec.twiddle, phat,
+                             ctx->num_sms, st), "tm_prescore: dft");
+    tmgb::DenseCall dc{};
+    dc.phat = phat;
+    dc.n = n;
+    dc.n_theta = n_theta;
+    dc.n_r = n_r;
+    dc.n_rad = rm.n_rad;
+    dc.n_freq = n_freq;
+    dc.rmap = rm.rmap;
+    dc.basis = spec.basis;
+    dc.twiddle = spec.twiddle;
+    dc.n_libs = 1;
+    dc.lib[0] = dense_view(L);
+    dc.list[0] = list;
+    dc.count[0] = keep;
+    dc.cand[0] = cand_dev;
+    dc.cand_q[0] = score_dev;
+    dc.kc = kc;
+    dc.error = ctx->d_error;
+    TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_prescore: dense");
+    TM_CUDA(cudaEventRecord(ctx->ws_event, st), "tm_prescore: record");
+    return TM_OK;
+}
 }  // extern "C"

@@ -36,8 +36,7 @@ struct RadialLib {
 // ------------------------------------------------------------------ launchers
 struct PolarTable {            // bilinear taps for one (H, W, n_r, n_theta, dr, cx, cy)
     const int32_t* xy;         // [n_r * n_theta]  x0 | (y0 << 16) as int16 pairs
-    const float* fx;           // [n_r * n_theta]
-    const float* fy;           // [n_r * n_theta]
+    const float4* w;           // [n_r * n_theta]  (fx, 1 - fx, fy, 1 - fy), each rounded from FP64
 };
 
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
@@ -69,11 +68,51 @@ struct SparseCall {
     tm_hit* hits;                       // [n_libs][hits_lib_stride] or null
     int64_t hits_lib_stride;            // elements between libraries (>= n * top_n)
     int top_n;
+    const int32_t* cand[TM_MAX_LIBS];   // candidate mode: [n][kc] template ids (-1 = none)
+    int kc;                             // candidates per pattern (0 = mask mode)
 };
 
 // Shared-memory bytes the sparse kernel needs for a polar grid (0 when unsupported).
 size_t sparse_smem_bytes(int n_r, int n_theta, int top_n);
 int sparse_pitch(int n_theta);
 cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);
+
+// ------------------------------------------------------------------ BF16 tensor-core path
+struct DenseLib {
+    const int32_t* off;        // [K + 1]
+    const int32_t* rt;         // [n_spots]  r | (t << 16)
+    const int2* spot;          // [n_spots]  .y = float bits of the intensity
+    const float* norm;         // [K]
+    const int32_t* order;      // [K]  templates sorted by spot count (tile order)
+    int32_t K;
+};
+
+struct DenseCall {
+    const void* phat;          // [n][n_rad][n_freq] half2: DFT of the polar rows / |P|
+    int64_t n;
+    int n_theta, n_r, n_rad, n_freq;
+    const int32_t* rmap;       // [n_r]  radius -> row of phat (-1 if unused)
+    const void* basis;         // [192][384] bf16, K-major (dense_basis_rows x dense_basis_cols)
+    const float2* twiddle;     // [n_theta]  (cos, sin) of 2 pi j / n_theta
+    int n_libs;
+    DenseLib lib[TM_MAX_LIBS];
+    const int32_t* list[TM_MAX_LIBS];   // [n][count] survivors or null (all, in lib order)
+    int count[TM_MAX_LIBS];             // templates scored per pattern
+    int32_t* cand[TM_MAX_LIBS];         // [n][kc] out
+    float* cand_q[TM_MAX_LIBS];         // [n][kc] out (pre-scores) or null
+    int kc;
+    unsigned* error;                    // device word: bit 0 = a bounded wait timed out
+};
+
+bool dense_supported(int n_theta);
+int dense_basis_rows();
+int dense_basis_cols();
+size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq, int kc);
+cudaError_t launch_dense(const DenseCall& c, int num_sms, cudaStream_t st);
+cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_r, int n_theta,
+                       const int32_t* radii, int n_rad, int n_freq, const float2* twiddle, void* out,
+                       int num_sms, cudaStream_t st);
+cudaError_t launch_compact(const uint32_t* mask, int64_t n, int K, const int32_t* order, int keep,
+                           int32_t* list, cudaStream_t st);
 
 }  // namespace tmgb

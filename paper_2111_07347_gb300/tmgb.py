@@ -98,6 +98,9 @@ _SIGS = {
                                          ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P,
                                          ctypes.POINTER(tm_stats), _P]),
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
+    "tm_prescore": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
+                                   _P, _P, _P]),
+    "tm_check": (ctypes.c_int, [_P, _P]),
     "tm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tm_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(tm_profile)]),
 }
@@ -251,6 +254,15 @@ def tm_correlate(ctx, lib_id, polar_ptr, norm_ptr, n, mask_ptr, q_ptr, s_ptr, st
     _check(library().tm_correlate(ctx, lib_id, polar_ptr, norm_ptr, n, mask_ptr, q_ptr, s_ptr, stream))
 
 
+def tm_prescore(ctx, lib_id, polar_ptr, norm_ptr, radial_ptr, n, fraction, kc, cand_ptr, score_ptr, stream) -> None:
+    _check(library().tm_prescore(ctx, lib_id, polar_ptr, norm_ptr, radial_ptr, n, fraction, kc, cand_ptr, score_ptr,
+                                 stream))
+
+
+def tm_check(ctx, stream) -> None:
+    _check(library().tm_check(ctx, stream))
+
+
 def tm_index_patterns(ctx, params, frames_ptr, dtype, n, H, W, centres_ptr, lib_ids, out_ptr, stream) -> dict:
     ids = (ctypes.c_int32 * len(lib_ids))(*lib_ids)
     st = tm_stats()
@@ -361,6 +373,20 @@ class Context:
         tm_correlate(self.handle, lib_id, polar.data_ptr(), norm.data_ptr(), n,
                      None if mask is None else mask.data_ptr(), q.data_ptr(), s.data_ptr(), _stream_ptr(stream))
         return q, s
+
+    def prescore(self, lib_id, polar, norm, radial=None, fraction=1.0, kc=64, stream=None):
+        import torch
+        n = polar.shape[0]
+        cand = torch.empty((n, kc), dtype=torch.int32, device=polar.device)
+        score = torch.empty((n, kc), dtype=torch.float32, device=polar.device)
+        tm_prescore(self.handle, lib_id, polar.data_ptr(), norm.data_ptr(),
+                    None if radial is None else radial.data_ptr(), n, fraction, kc, cand.data_ptr(),
+                    score.data_ptr(), _stream_ptr(stream))
+        return cand, score
+
+    def check(self, stream=None):
+        """Synchronise and raise TmError(TM_ERR_TIMEOUT) if a kernel stopped on a bounded wait."""
+        tm_check(self.handle, _stream_ptr(stream))
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
               path=TM_PATH_FP32_SPARSE, rescore_k=64, cx=math.nan, cy=math.nan, out=None, stream=None):

@@ -60,14 +60,20 @@ def _check_polar(ctx, frames, n_r, n_theta, gamma=0.5, subtract=0.0, dr=1.0):
     P_ref = O.polar(frames, n_r, n_theta, dr, gamma, subtract)
     polar, norm, radial = ctx.polar_transform(_t(frames), n_r, n_theta, dr, gamma, subtract)
     P = _np(polar).astype(np.float64)
-    scale = np.maximum(np.abs(P_ref).max(axis=(1, 2)), 1e-30)[:, None, None]
-    # each sample: convex combination of four float gamma values with float weights
-    assert np.all(np.abs(P - P_ref) <= 2e-6 * scale + 1e-7 * abs(subtract)), np.abs(P - P_ref).max()
+    # each sample is a convex combination of four float gamma values (correctly rounded
+    # sqrt / powf) with weights within a few ulps: error <= 8 ulp of the largest tap; the
+    # per-pattern maximum bounds every tap
+    scale = np.maximum(np.abs(P_ref).max(axis=(1, 2)), 1e-30)[:, None, None] + abs(subtract)
+    err = np.abs(P - P_ref)
+    assert np.all(err <= 1e-6 * scale), (err.max(), np.unravel_index(np.argmax(err / scale), err.shape))
     nref = np.sqrt((P_ref ** 2).sum(axis=(1, 2)))
     assert np.allclose(_np(norm), nref, rtol=2e-6, atol=1e-30)
     rref = P_ref.sum(axis=2)
     rs = np.abs(P_ref).sum(axis=2)
-    assert np.all(np.abs(_np(radial) - rref) <= 1e-5 * rs + 1e-30)
+    # row sums: the per-sample bound summed over the row plus float summation of n_theta terms
+    rerr = np.abs(_np(radial) - rref)
+    rtol = 1e-6 * scale[:, :, 0] * n_theta + 1e-6 * rs
+    assert np.all(rerr <= rtol), (rerr.max(), np.unravel_index(np.argmax(rerr / rtol), rerr.shape))
     return P_ref
 
 
@@ -174,24 +180,37 @@ def test_index_tiny_full(ctx, tiny):
 
 
 def test_index_fcc_prefilter(ctx, fcc):
-    """Single phase, 256 x 256 u16 frames, 128 x 360, mirrors, pre-filter keeps 50 %."""
+    """Single phase, 256 x 256 u16 frames, 128 x 360, mirrors, pre-filter keeps 50 %.
+
+    Templates whose FP64 pre-filter score lies within 1e-5 of the keep threshold may
+    survive on one side only.  Where such a template would enter the oracle's top-N over
+    the survivors plus those templates, the expected answer is not unique and the GPU's
+    rows are checked for validity instead (every template eligible, every score equal to
+    the oracle's Q for it); elsewhere the rows must match the oracle exactly."""
     ts, scan, lib = fcc
     lid = ctx.load_library(ts, 128, 360)
-    ref = O.index(scan.frames, lib, prefilter_fraction=0.5, N=5)
-    h = _hits(ctx, scan.frames, lid, top_n=5, prefilter=0.5)[0]
-    act_gpu = None
-    try:
-        compare_hits(h, ref, lib)
-    except AssertionError:
-        # a template near the pre-filter threshold may survive on one side only; check that
-        # every disagreement involves such a template, then compare with the GPU's survivors
-        polar, norm, radial = ctx.polar_transform(_t(scan.frames), 128, 360)
-        mask, score = ctx.prefilter(lid, radial, 0.5)
-        act_gpu = _unpack(mask, lib.K)
-        q, s = O.scores(ref["polar"], lib, act_gpu)
-        tk, tsh, tq = O.top_n(q, s, 5, act_gpu)
-        ref2 = dict(ref, q_best=q, s_best=s, template=tk, shift=tsh, score=tq)
-        compare_hits(h, ref2, lib)
+    N = 5
+    ref = O.index(scan.frames, lib, prefilter_fraction=0.5, N=N)
+    q_all, s_all = O.scores(ref["polar"], lib)
+    _, sc = O.prefilter(ref["polar"], lib, 0.5)
+    keep = O.keep_count(0.5, lib.K)
+    h = _hits(ctx, scan.frames, lid, top_n=N, prefilter=0.5)[0]
+    exact = []
+    for p in range(scan.frames.shape[0]):
+        thr = np.sort(sc[p])[::-1][keep - 1]
+        amb = np.abs(sc[p] - thr) <= 1e-5 * max(abs(thr), 1e-3)
+        elig = ref["active"][p] | amb
+        tk, _, _ = O.top_n(q_all[p:p + 1], s_all[p:p + 1], N + 1, elig[None])
+        if not np.any(amb[tk[0][tk[0] >= 0]]):
+            exact.append(p)
+            continue
+        q_top = q_all[p][elig].max()
+        for j in range(N):
+            k = int(h["template_index"][p, j])
+            assert k >= 0 and elig[k], (p, j, k)
+            assert abs(h["score"][p, j] - q_all[p, k]) <= 1e-5 * max(abs(q_all[p, k]), 1e-3 * abs(q_top))
+    assert len(exact) >= 0.9 * scan.frames.shape[0]
+    compare_hits(h, ref, lib, patterns=exact)
     ctx.unload_library(lid)
 
 
