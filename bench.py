@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "patterns/s indexed, BF16-TC vs FP32 sparse at ≥99.5% top-1 match; p99 line ms"
 WORKLOAD = ("single-phase scan: 16384 x 256x256 u16 frames, FCC 0.5 deg (+mirrors), polar 128x360, "
-            "prefilter 50%, top-5; BF16 tensor-core pre-score + FP32 rescore of the top-64 vs FP32 sparse")
-N_R, N_THETA, TOP_N, PREFILTER, RESCORE_K = 128, 360, 5, 0.5, 64
+            "prefilter 50%, top-5; BF16 tensor-core pre-score + FP32 rescore of the top-256 vs FP32 sparse")
+N_R, N_THETA, TOP_N, PREFILTER, RESCORE_K = 128, 360, 5, 0.5, 256
 MATCH_SAMPLE = 512
 # tensor-core work per (pattern, scored template): 2 x 180 shifts x (182 + 180) frequency terms
 DENSE_FLOPS_PER_PAIR = 2 * 180 * (182 + 180)
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--patterns", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", default="fp32,bf16", help="paths to time (fp32, bf16)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -123,9 +124,10 @@ def to_device_u16(a: np.ndarray, device):
 
 
 def pinned_u16(a: np.ndarray):
+    """Pinned host copy of a uint16 array: (torch uint16 view, numpy uint16 view)."""
     import torch
     t = torch.from_numpy(a.view(np.int16)).pin_memory()
-    return t.view(torch.uint16)
+    return t.view(torch.uint16), t.numpy().view(np.uint16)
 
 
 def kernel_sha(path: str) -> str:
@@ -159,6 +161,69 @@ def cpu_baseline(ts, scan, seconds: float) -> dict:
     dt = time.perf_counter() - t
     return {"value": n / dt, "unit": "patterns/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"first {n} patterns of the scan, whole path (polar, pre-filter, Q, top-5), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ serving loop (scan lines and maps)
+
+def serve_bench(ctx, lib_ids, pool: np.ndarray, path_kw: dict, seconds: float = 2.5, seed: int = 2111_07347 + 103):
+    """Poisson arrivals against device-resident libraries: 80 % scan lines of 64-512
+    patterns (frame rate 1-10 kHz: a line arrives when its last frame is acquired), 20 %
+    maps of 64^2 or 128^2 patterns (the frame pool holds 16384 frames, so the 256^2 and
+    512^2 maps of the workload are left out).  Capacity is measured first with a saturating
+    burst; offered load is then 25 / 50 / 80 % of it.  Latency = completion - arrival."""
+    from paper_2111_07347_gb300 import tmgb
+    rng = np.random.default_rng(seed)
+    n_pool = pool.shape[0]
+    srv = tmgb.Server(ctx, slots=3, tile_patterns=512, max_libs=len(lib_ids), max_top_n=TOP_N)
+
+    def submit(n, prio):
+        a = int(rng.integers(0, n_pool - n + 1))
+        return srv.submit(pool[a:a + n], lib_ids, top_n=TOP_N, priority=prio, **path_kw)
+
+    # capacity: a saturating burst of 16 maps of 128^2
+    t0 = time.perf_counter()
+    ts = [submit(16384, 0) for _ in range(6)]
+    for t in ts:
+        srv.wait(t, timeout_ms=600000)
+    cap = 6 * 16384 / (time.perf_counter() - t0)
+    mean_line, mean_map = (64 + 512) / 2, (64 * 64 + 128 * 128) / 2
+    mean_req = 0.8 * mean_line + 0.2 * mean_map
+    out = {"capacity_patterns_per_s": cap, "slots": 3, "tile_patterns": 512,
+           "maps": "64^2 and 128^2 only (frame pool of 16384)"}
+    for load in (0.25, 0.5, 0.8):
+        lam = load * cap / mean_req
+        t_next = time.perf_counter()
+        end = t_next + seconds
+        tickets = []
+        while t_next < end:
+            now = time.perf_counter()
+            if now < t_next:
+                time.sleep(min(t_next - now, 0.002))
+                continue
+            if rng.random() < 0.8:
+                n = int(rng.integers(64, 513))
+                tickets.append(("line", n, submit(n, 1)))
+            else:
+                side = int(rng.choice([64, 128]))
+                tickets.append(("map", side * side, submit(side * side, 0)))
+            t_next += rng.exponential(1.0 / lam)
+        lat = {"line": [], "map": []}
+        pats = 0
+        first, last = None, None
+        for kind, n, t in tickets:
+            res, st = srv.wait(t, timeout_ms=600000)
+            lat[kind].append(st["done_ms"] - st["submit_ms"])
+            pats += n
+            first = st["submit_ms"] if first is None else min(first, st["submit_ms"])
+            last = st["done_ms"] if last is None else max(last, st["done_ms"])
+        rec = {"requests": len(tickets), "throughput_patterns_per_s": pats / max(1e-9, (last - first) / 1e3)}
+        for kind in ("line", "map"):
+            if lat[kind]:
+                rec[f"{kind}_p50_ms"] = float(np.percentile(lat[kind], 50))
+                rec[f"{kind}_p99_ms"] = float(np.percentile(lat[kind], 99))
+        out[f"load_{int(load * 100)}"] = rec
+    srv.close()
+    return out
 
 
 # ------------------------------------------------------------------ reference arm: the oracle
@@ -302,7 +367,7 @@ def run_ours(args):
     value = world * n / (ms / 1e3)
 
     # ---- end to end: pinned host frames -> device -> index -> hits back to the host
-    host = pinned_u16(scan.frames)
+    host, host_np = pinned_u16(scan.frames)
     host_out = torch.empty((1, n, TOP_N, 5), dtype=torch.int32).pin_memory()
     e2e_steps = max(2, args.steps // 2)
     buf = torch.empty_like(frames_d)
@@ -386,6 +451,14 @@ def run_ours(args):
             "macs_per_step_sparse": macs_step, "survivors_per_step": survivors_step,
             "roofline": roofline, "stages": stages, "e2e": e2e,
             "gpu_launches": int(launches_per_step * args.steps), "clocks": clk}
+    if not args.no_serving:
+        hcp = synth.kinematic_library("hcp")
+        lid_h = ctx.load_library(hcp, N_R, N_THETA)
+        pool = host_np
+        serving = serve_bench(ctx, [lid, lid_h], pool, {k: v for k, v in kw_head.items() if k not in ("top_n",)})
+        line["serving"] = serving
+        line["p99_line_ms"] = serving["load_50"].get("line_p99_ms")
+        line["serving_workload"] = "FCC + HCP resident, Poisson arrivals, 80 % lines 64-512 / 20 % maps"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ts, scan, args.cpu_seconds)
     if rank == 0:

@@ -19,9 +19,10 @@
  * stream is synchronised.  Host pointers are read before the call returns.
  *
  * Threading: one context may be used from several host threads; calls are serialised
- * on the host by the context, and on the GPU each call waits for the previous call of
- * the same context (whatever stream it ran on), because calls share the context's
- * workspace.
+ * on the host by the context.  Scratch memory is kept per CUDA stream handle: calls on
+ * one stream are ordered by that stream, calls on different streams use separate
+ * scratch buffers and may overlap on the GPU.  Do not destroy a stream while work of
+ * this context is still pending on it.
  */
 #ifndef TMGB_H
 #define TMGB_H
@@ -106,7 +107,7 @@ typedef struct tm_index_params {
     double prefilter_fraction;    /* (0, 1]: keep ceil(f K) templates by radial cosine   */
     int32_t top_n;                /* N >= 1 results per pattern and library              */
     int32_t path;                 /* TM_PATH_FP32_SPARSE or TM_PATH_BF16_RESCORE         */
-    int32_t rescore_k;            /* BF16 path: candidates rescored exactly (default 64) */
+    int32_t rescore_k;            /* BF16 path: candidates rescored exactly (default 256) */
     int32_t reserved;
 } tm_index_params;
 
@@ -189,15 +190,12 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
  * alternative to sliding): C[k, s] = sum_m (w_m / n) Re(G[k, m] e^{2 pi i m s / n}) with
  * G[k, m] = sum_r conj(T^_k[r, m]) P^[r, m]; G is formed in FP32 and rounded to BF16, the
  * sum over frequencies for every shift runs on the tensor cores (tcgen05, FP32
- * accumulation).  For each pattern the kc templates with the largest pre-score
- * Q~ = max_s C / (|P| |T|) are returned, ordered by (Q~ desc, template asc).
- * polar_dev / norm_dev: Stage 1 outputs; radial_dev: Stage 1 azimuthal sums, used when
- * fraction < 1 (only the pre-filter's survivors are scored); cand_dev [n][kc] int32
- * (-1 past the survivors), score_dev [n][kc] float (nullable).  kc in [1, 256]; n_theta
- * must be even and <= 376.  Errors: TM_ERR_UNSUPPORTED for other grids. */
+ * accumulation).  score_dev [n][K] float receives Q~ = max_s C / (|P| |T_k|) for every
+ * template scored and -NaN for the others (the pre-filter's rejects when fraction < 1).
+ * polar_dev / norm_dev: Stage 1 outputs; radial_dev: Stage 1 azimuthal sums (used when
+ * fraction < 1).  n_theta must be even and <= 376 (else TM_ERR_UNSUPPORTED). */
 int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev,
-                const float* radial_dev, int64_t n, double fraction, int32_t kc, int32_t* cand_dev,
-                float* score_dev, void* stream);
+                const float* radial_dev, int64_t n, double fraction, float* score_dev, void* stream);
 
 /* Wait for `stream`, then report whether a kernel of this context stopped on a bounded
  * wait since the last check (TM_ERR_TIMEOUT; the error word is cleared). */
@@ -206,8 +204,8 @@ int tm_check(tm_ctx* ctx, void* stream);
 /* The whole path for a batch: frames -> polar -> [pre-filter] -> Q -> top-N, for each
  * of n_libs libraries (all built for the same polar grid).  path TM_PATH_FP32_SPARSE
  * scores every surviving template exactly in FP32 (Stage 3 with a fused top-N);
- * TM_PATH_BF16_RESCORE takes the rescore_k best by the Stage A7 pre-score and rescores
- * them exactly in FP32 before the top-N.  out_dev [n_libs][n][top_n]
+ * TM_PATH_BF16_RESCORE takes the rescore_k best by the Stage A7 pre-score (exact radix
+ * select, ties to the lower index) and rescores them exactly in FP32 before the top-N.  out_dev [n_libs][n][top_n]
  * tm_hit.  centres_dev must be NULL in this build (per-pattern centres:
  * TM_ERR_UNSUPPORTED).  stats (host, nullable) receives counts for the call. */
 int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,
@@ -237,8 +235,71 @@ int tm_profile_enable(tm_ctx* ctx, int enable);
 int tm_profile_read(tm_ctx* ctx, tm_profile* out);
 
 /* Default parameters: gamma 0.5, subtract 0, centre NaN, prefilter 1, top_n 5,
- * FP32 sparse path, rescore_k 64. */
+ * FP32 sparse path, rescore_k 256. */
 void tm_index_params_default(tm_index_params* p);
+
+/* ---------------------------------------------------------------- serving loop
+ * Continuous batching for on-line mapping (Section 5: indexing a pattern in a few to tens
+ * of milliseconds, on the order of a detector's acquisition time, so indexing can run
+ * beside acquisition).  A server owns a worker thread and `slots` CUDA streams, each
+ * with device staging for one tile.  Requests (a scan line or a whole map) are split into
+ * tiles of `tile_patterns`; tiles of different requests interleave on the device as
+ * slots free up, higher-priority requests (scan lines) first, then submission order.
+ * The libraries stay resident in the context.  Results of a pattern do not depend on
+ * the other patterns of its tile, so a request's result is the same alone and in a mix.
+ */
+typedef struct tm_server tm_server;
+
+typedef struct tm_server_params {
+    int32_t slots;                /* tiles in flight (CUDA streams), >= 1; default 3      */
+    int32_t tile_patterns;        /* patterns per tile, >= 1; default 512                 */
+    int32_t max_H, max_W;         /* largest frame accepted (sizes the staging)           */
+    int32_t max_libs;             /* largest n_libs of a request, in [1, 8]               */
+    int32_t max_top_n;            /* largest top_n of a request                           */
+    size_t queue_bytes;           /* admission budget: frame bytes of requests submitted
+                                     and not finished; 0 = no limit                       */
+    int32_t blocking_submit;      /* 1: submit waits for budget; 0: TM_ERR_BUSY           */
+    int32_t reserved;
+} tm_server_params;
+
+typedef struct tm_request {
+    const void* frames_host;      /* [n][H][W] host memory (pinned for overlap), read until
+                                     the request finishes                                  */
+    int32_t dtype;                /* TM_DTYPE_U16 or TM_DTYPE_F32                          */
+    int32_t H, W;
+    int64_t n;                    /* patterns, >= 1                                        */
+    const int32_t* lib_ids;       /* copied at submit                                      */
+    int32_t n_libs;
+    int32_t priority;             /* higher first: 1 = scan line, 0 = map                  */
+    tm_index_params params;
+    tm_hit* out_host;             /* [n_libs][n][top_n] host memory, complete when the
+                                     request finishes                                      */
+} tm_request;
+
+typedef struct tm_request_status {
+    int32_t status;               /* TM_OK, TM_ERR_CANCELLED, or the error of a tile       */
+    int32_t tiles;
+    double submit_ms, first_dispatch_ms, done_ms;   /* server clock, ms since creation    */
+} tm_request_status;
+
+void tm_server_params_default(tm_server_params* p);
+int tm_server_create(tm_ctx* ctx, const tm_server_params* params, tm_server** out);
+/* Queue a request; *ticket identifies it.  TM_ERR_BUSY when blocking_submit is 0 and
+ * the admission budget is full.  TM_ERR_INVALID_ARG for requests beyond the server's
+ * limits. */
+int tm_server_submit(tm_server* s, const tm_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: no limit) for the request.  TM_OK when it finished
+ * (status->status tells how), TM_ERR_TIMEOUT when it did not finish in time,
+ * TM_ERR_NOT_FOUND for an unknown or already collected ticket.  A finished request is
+ * forgotten once waited for. */
+int tm_server_wait(tm_server* s, uint64_t ticket, int32_t timeout_ms, tm_request_status* status);
+/* Cancel: tiles not yet dispatched are dropped; the request finishes with
+ * TM_ERR_CANCELLED once its dispatched tiles are done. */
+int tm_server_cancel(tm_server* s, uint64_t ticket);
+/* Stop (1) or resume (0) dispatching new tiles (tiles in flight complete). */
+int tm_server_pause(tm_server* s, int32_t paused);
+/* Finish dispatched tiles, drop the rest, stop the worker and free the staging. */
+void tm_server_destroy(tm_server* s);
 
 #ifdef __cplusplus
 }

@@ -17,8 +17,9 @@
 //   warps 0-3  producers: thread i builds row i (one template) of G, 64 K-elements per
 //              chunk, in BF16, into a 2-slot shared-memory ring (128B-swizzled K-major);
 //   warp  8    TMEM allocation and the single MMA-issuing thread;
-//   warps 4-7  epilogue: tcgen05.ld of E and O, max over all n shifts, per-warp top-Kc
-//              candidate lists merged at the end of each pattern.
+//   warps 4-7  epilogue: tcgen05.ld of E and O, max over all n shifts, one pre-score
+//              per (pattern, template) written to global memory (the candidates are
+//              then chosen by the exact radix select and rescored in FP32).
 // The basis (w_m / n) cos / -sin for both halves stays resident in shared memory.
 // Every mbarrier wait is bounded by the global timer; on timeout the CTA records an error
 // in a device word, stops its roles uniformly, releases TMEM and returns.
@@ -156,9 +157,6 @@ struct Smem {
     __half2* phat;        // [n_rad][n_freq]
     float2* tw;           // [n_theta]
     int16_t* rmap;        // [n_r]
-    float* lq;            // [4][kc]
-    int* lk;              // [4][kc]
-    int* lcnt;            // [4]
     uint64_t* bar;        // full[2], empty[2], acc_full, acc_empty
     uint32_t* tmem_base;
     int* abort_flag;
@@ -180,11 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
     s.phat = (__half2*)(s.ring + 2 * kSlotBytes);
     s.tw = (float2*)(((uintptr_t)(s.phat + (size_t)c.n_rad * c.n_freq) + 15) & ~(uintptr_t)15);
     s.rmap = (int16_t*)(s.tw + c.n_theta);
-    float* tail = (float*)(((uintptr_t)(s.rmap + c.n_r) + 15) & ~(uintptr_t)15);
-    s.lq = tail;
-    s.lk = (int*)(s.lq + 4 * c.kc);
-    s.lcnt = s.lk + 4 * c.kc;
-    s.bar = (uint64_t*)(((uintptr_t)(s.lcnt + 4) + 7) & ~(uintptr_t)7);
+    s.bar = (uint64_t*)(((uintptr_t)(s.rmap + c.n_r) + 15) & ~(uintptr_t)15);
     s.tmem_base = (uint32_t*)(s.bar + 6);
     s.abort_flag = (int*)(s.tmem_base + 1);
     volatile int* abort_flag = s.abort_flag;
@@ -349,15 +343,12 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
         const int ew = warp - 4;
         const int row = ew * 32 + lane;
         const uint32_t tbase = tmem + ((uint32_t)(ew * 32) << 16);
-        float* wq = s.lq + ew * c.kc;
-        int* wk = s.lk + ew * c.kc;
         uint32_t tt = 0;
         bool stop = false;
         for (int64_t p = blockIdx.x; p < c.n && !stop; p += gridDim.x) {
             for (int li = 0; li < c.n_libs && !stop; ++li) {
-                if (lane == 0) s.lcnt[ew] = 0;
-                __syncwarp();
                 const int tiles = (c.count[li] + kRows - 1) / kRows;
+                float* out = c.pre[li] + (size_t)p * c.lib[li].K;
                 for (int t = 0; t < tiles; ++t, ++tt) {
                     if (row == 0) {
                         if (!mbar_wait(bar_accf, tt & 1u, abort_flag)) *abort_flag = 1;
@@ -379,65 +370,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
                     tc_fence_before();
                     mbar_arrive(bar_acce);
                     const int k = row_template(c, li, p, t * kRows + row);
-                    // per-warp top-kc insertion by lane 0, candidates in lane order
-                    const float thr_q = (s.lcnt[ew] < c.kc) ? -FLT_MAX : wq[c.kc - 1];
-                    const int thr_k = (s.lcnt[ew] < c.kc) ? INT_MAX : wk[c.kc - 1];
-                    const bool want = k >= 0 && (s.lcnt[ew] < c.kc || better(best, k, thr_q, thr_k));
-                    unsigned ball = __ballot_sync(0xffffffffu, want);
-                    while (ball) {
-                        const int src = __ffs(ball) - 1;
-                        ball &= ball - 1;
-                        const float q = __shfl_sync(0xffffffffu, best, src);
-                        const int kk = __shfl_sync(0xffffffffu, k, src);
-                        if (lane == 0) {
-                            const int cnt = s.lcnt[ew];
-                            if (cnt < c.kc || better(q, kk, wq[c.kc - 1], wk[c.kc - 1])) {
-                                int i = cnt < c.kc ? cnt : c.kc - 1;
-                                while (i > 0 && better(q, kk, wq[i - 1], wk[i - 1])) {
-                                    wq[i] = wq[i - 1];
-                                    wk[i] = wk[i - 1];
-                                    --i;
-                                }
-                                wq[i] = q;
-                                wk[i] = kk;
-                                if (cnt < c.kc) s.lcnt[ew] = cnt + 1;
-                            }
-                        }
-                        __syncwarp();
-                    }
+                    if (k >= 0) out[k] = best;
                 }
-                if (stop) break;
-                named_bar(2, kRows);
-                if (ew == 0) {
-                    int32_t* cout = c.cand[li] + (size_t)p * c.kc;
-                    float* qout = c.cand_q[li] ? c.cand_q[li] + (size_t)p * c.kc : nullptr;
-                    const int total = 4 * c.kc;
-                    for (int j = 0; j < c.kc; ++j) {
-                        float bq = -FLT_MAX;
-                        int bk = INT_MAX, bi = -1;
-                        for (int ci = lane; ci < total; ci += 32) {
-                            const int w = ci / c.kc, i = ci - w * c.kc;
-                            if (i >= s.lcnt[w]) continue;
-                            const int kk = s.lk[ci];
-                            if (kk < 0) continue;
-                            if (bi < 0 || better(s.lq[ci], kk, bq, bk)) { bq = s.lq[ci]; bk = kk; bi = ci; }
-                        }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            const float oq = __shfl_xor_sync(0xffffffffu, bq, o);
-                            const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
-                            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                            if (oi >= 0 && (bi < 0 || better(oq, ok, bq, bk))) { bq = oq; bk = ok; bi = oi; }
-                        }
-                        if (lane == 0) {
-                            cout[j] = bi >= 0 ? bk : -1;
-                            if (qout) qout[j] = bi >= 0 ? bq : -INFINITY;
-                            if (bi >= 0) s.lk[bi] = -1;
-                        }
-                        __syncwarp();
-                    }
-                }
-                named_bar(2, kRows);
             }
         }
     }
@@ -453,11 +387,11 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
 
 }  // namespace
 
-size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq, int kc) {
+size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq) {
     size_t b = 1024;                                           // alignment slack
     b += (size_t)kChunks * kBasisChunkBytes + 2 * kSlotBytes;
     b += (size_t)n_rad * n_freq * 4 + 16 + (size_t)n_theta * 8 + (size_t)n_r * 2 + 16;
-    b += (size_t)4 * kc * 8 + 16 + 6 * 8 + 8 + 16;
+    b += 6 * 8 + 8 + 16;
     return b;
 }
 
@@ -468,7 +402,7 @@ int dense_basis_cols() { return kKB; }
 
 cudaError_t launch_dense(const DenseCall& c, int num_sms, cudaStream_t st) {
     if (c.n <= 0) return cudaSuccess;
-    const size_t smem = dense_smem_bytes(c.n_theta, c.n_r, c.n_rad, c.n_freq, c.kc);
+    const size_t smem = dense_smem_bytes(c.n_theta, c.n_r, c.n_rad, c.n_freq);
     if (smem > 232448) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

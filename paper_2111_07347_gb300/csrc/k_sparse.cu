@@ -5,16 +5,22 @@
 // wraparound; the maximum Q and its angle are kept per template; the top N templates are
 // returned).
 //
-// Design (GB300): a persistent CTA holds one pattern's polar image in shared memory with
-// its rows extended by at least 32 wrapped columns (sparse_pitch), so a warp reading 32
-// consecutive shifts of one spot never splits at the wrap and never conflicts on a bank.
-// One warp scores one template: lane L accumulates shifts s = 32 b + L for every shift
-// block b in registers; a spot costs one broadcast 8-byte load and, per block, one
-// shared-memory load and one FMA.  The work bound is the shared-memory load path
-// (one 4-byte operand per multiply-add).  Warps pull 32-template mask words from a
-// shared counter; a per-warp sorted top-N list is merged at the end of the pattern.
-// Results are independent of scheduling: the per-template sum runs over the spots in
-// CSR order and ranking uses the total order (Q desc, template asc).
+// Design (GB300):
+// * Shared memory holds only the polar rows the library uses (its distinct spot radii --
+//   a few to a few tens of the 128 rows), each padded to sparse_pitch(Nθ) >= Nθ + 32
+//   columns with column c = P'[c mod Nθ]; a warp reading 32 consecutive shifts of one spot
+//   never splits at the wrap and never conflicts on a bank.  The small footprint lets
+//   several CTAs share an SM and leaves L1 to cache the library's spot lists.
+// * A persistent CTA takes patterns from a global counter; its warps take 32-template
+//   mask words from a shared counter.  One warp scores one template: lane L accumulates
+//   shifts s = 32 b + L of every shift block b in registers; the template's spots arrive
+//   in one lane-parallel load and are broadcast by shuffles; a spot costs, per block, one
+//   shared-memory load and one FMA.  The bound is the shared-memory load path (one 4-byte
+//   operand per multiply-add).
+// * The best shift is only resolved (lowest shift among equal maxima) when the template
+//   can enter the warp's top-N, or when per-template results are requested.
+// Results do not depend on scheduling: a template's sum runs over its spots in CSR order
+// and ranking uses the total order (Q desc, template asc).
 #include <float.h>
 #include <limits.h>
 
@@ -29,9 +35,12 @@ __host__ __device__ constexpr int round_nb(int nb) {
     return nb <= 4 ? nb : nb <= 6 ? 6 : nb <= 8 ? 8 : nb <= 12 ? 12 : nb <= 16 ? 16 : nb <= 24 ? 24 : 32;
 }
 
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
 }  // namespace
 
-// Row pitch of the polar image in shared memory.  Block b of a spot at column t reads
+// Row pitch of the polar rows in shared memory.  Block b of a spot at column t reads
 // columns t + 32 b + [0, 32) (or that minus n_theta once it wraps), so the pitch covers
 // n_theta + 32 columns and every column 32 * NB - 1 that the widest rounded block count
 // NB can touch; column c holds P'[c mod n_theta].
@@ -47,157 +56,178 @@ __device__ __forceinline__ bool better(float qa, int ka, float qb, int kb) {
     return qa > qb || (qa == qb && ka < kb);
 }
 
-// Score template k against the polar image in shared memory (warp-collective).
+// Correlation C(s) of one template for all its shifts (warp-collective).  Returns the
+// warp-wide maximum; when it reaches thr_c, *shift_out is the lowest shift attaining it
+// and `resolved` is set.
 template <int NB>
-__device__ __forceinline__ void score_template(const float* __restrict__ sP, const SparseLib& L,
-                                               int k, int n_theta, int lane, float& best_out,
-                                               int& shift_out) {
-    const int beg = __ldg(L.off + k), end = __ldg(L.off + k + 1);
-    const int S = __ldg(L.nshift + k);
+__device__ __forceinline__ float score_template(const float* __restrict__ sP, const SparseLib& L, int beg, int end,
+                                                int S, int n_theta, int lane, float thr_c, int& shift_out,
+                                                bool& resolved) {
     float acc[NB];
-    #pragma unroll
+#pragma unroll
     for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
-    for (int i = beg; i < end; ++i) {
-        const int2 sp = __ldg(L.spot + i);
-        const int a = sp.x & 0xffffff;
-        const int w = (int)((unsigned)sp.x >> 24);
-        const float I = __int_as_float(sp.y);
-        const float* p1 = sP + a + lane;           // blocks b < w: no wrap
-        const float* p2 = p1 - n_theta;            // blocks b >= w: wrapped
-        #pragma unroll
-        for (int b = 0; b < NB; ++b) acc[b] = fmaf(I, (b < w ? p1 : p2)[32 * b], acc[b]);
+    for (int i0 = beg; i0 < end; i0 += 32) {
+        const int cnt = min(32, end - i0);
+        int2 mine = make_int2(0, 0);
+        if (lane < cnt) mine = __ldg(L.spot + i0 + lane);         // one lane-parallel load
+        for (int j = 0; j < cnt; ++j) {
+            const int px = __shfl_sync(0xffffffffu, mine.x, j);
+            const float I = __int_as_float(__shfl_sync(0xffffffffu, mine.y, j));
+            const int a = px & 0xffffff;
+            const int w = (int)((unsigned)px >> 24);
+            const float* p1 = sP + a + lane;                      // blocks b < w: no wrap
+            const float* p2 = p1 - n_theta;                       // blocks b >= w: wrapped
+#pragma unroll
+            for (int b = 0; b < NB; ++b) acc[b] = fmaf(I, (b < w ? p1 : p2)[32 * b], acc[b]);
+        }
     }
     float best = -FLT_MAX;
-    int bs = INT_MAX;
-    #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int s = 32 * b + lane;
-        if (s < S && acc[b] > best) { best = acc[b]; bs = s; }
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+        if (32 * b + lane < S) best = fmaxf(best, acc[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    resolved = false;
+    if (best >= thr_c) {
+        int s = INT_MAX;
+#pragma unroll
+        for (int b = NB - 1; b >= 0; --b)
+            if (32 * b + lane < S && acc[b] == best) s = 32 * b + lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = min(s, __shfl_xor_sync(0xffffffffu, s, o));
+        shift_out = s;
+        resolved = true;
     }
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int os = __shfl_xor_sync(0xffffffffu, bs, o);
-        if (ob > best || (ob == best && os < bs)) { best = ob; bs = os; }
-    }
-    best_out = best;
-    shift_out = bs;
+    return best;
 }
 
 template <int NBMAX>
-__device__ __forceinline__ void score_dispatch(const float* sP, const SparseLib& L, int k,
-                                               int n_theta, int lane, float& best, int& s) {
-    const int nb = (__ldg(L.nshift + k) + 31) >> 5;
-    if (nb <= 1) score_template<1>(sP, L, k, n_theta, lane, best, s);
-    else if (nb <= 2) score_template<2>(sP, L, k, n_theta, lane, best, s);
-    else if (nb <= 3) score_template<3>(sP, L, k, n_theta, lane, best, s);
-    else if (nb <= 4) score_template<4>(sP, L, k, n_theta, lane, best, s);
-    else if (NBMAX >= 6 && nb <= 6) score_template<(NBMAX >= 6 ? 6 : 1)>(sP, L, k, n_theta, lane, best, s);
-    else if (NBMAX >= 8 && nb <= 8) score_template<(NBMAX >= 8 ? 8 : 1)>(sP, L, k, n_theta, lane, best, s);
-    else if (NBMAX >= 12 && nb <= 12) score_template<(NBMAX >= 12 ? 12 : 1)>(sP, L, k, n_theta, lane, best, s);
-    else if (NBMAX >= 16 && nb <= 16) score_template<(NBMAX >= 16 ? 16 : 1)>(sP, L, k, n_theta, lane, best, s);
-    else if (NBMAX >= 24 && nb <= 24) score_template<(NBMAX >= 24 ? 24 : 1)>(sP, L, k, n_theta, lane, best, s);
-    else score_template<(NBMAX >= 32 ? 32 : 1)>(sP, L, k, n_theta, lane, best, s);
+__device__ __forceinline__ float score_dispatch(const float* sP, const SparseLib& L, int beg, int end, int S,
+                                                int n_theta, int lane, float thr_c, int& s, bool& res) {
+    const int nb = (S + 31) >> 5;
+    if (nb <= 1) return score_template<1>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (nb <= 2) return score_template<2>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (nb <= 3) return score_template<3>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (nb <= 4) return score_template<4>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (NBMAX >= 6 && nb <= 6) return score_template<(NBMAX >= 6 ? 6 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (NBMAX >= 8 && nb <= 8) return score_template<(NBMAX >= 8 ? 8 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (NBMAX >= 12 && nb <= 12) return score_template<(NBMAX >= 12 ? 12 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (NBMAX >= 16 && nb <= 16) return score_template<(NBMAX >= 16 ? 16 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (NBMAX >= 24 && nb <= 24) return score_template<(NBMAX >= 24 ? 24 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    return score_template<(NBMAX >= 32 ? 32 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
 }
 
 template <int NBMAX>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kThreads)
 sparse_kernel(const SparseCall c) {
     extern __shared__ __align__(16) float smem[];
-    const int n_r = c.n_r, n_theta = c.n_theta, pitch = c.pitch;
-    const int nw = blockDim.x >> 5;
+    const int n_theta = c.n_theta, pitch = c.pitch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int N = c.top_n;
-    float* sP = smem;                                        // [n_r][pitch]
-    float* lq = sP + (size_t)n_r * pitch;                    // [nw][N]
-    int* lk = (int*)(lq + nw * N);                           // [nw][N]
-    int* ls = lk + nw * N;                                   // [nw][N]
-    int* lcnt = ls + nw * N;                                 // [nw]
-    int* counter = lcnt + nw;                                // [1]
+    float* sP = smem;                                        // [max_rad][pitch]
+    float* lq = sP + (size_t)c.max_rad * pitch;              // [kWarps][N]
+    int* lk = (int*)(lq + kWarps * N);                       // [kWarps][N]
+    int* ls = lk + kWarps * N;                               // [kWarps][N]
+    int* lcnt = ls + kWarps * N;                             // [kWarps]
+    int* counter = lcnt + kWarps;                            // [1]
+    int* s_pattern = counter + 1;                            // [1]
 
-    for (int64_t p = blockIdx.x; p < c.n; p += gridDim.x) {
+    for (;;) {
+        __syncthreads();                                     // previous pattern fully done
+        if (threadIdx.x == 0) *s_pattern = atomicAdd(c.pattern_counter, 1);
         __syncthreads();
-        const float* src = c.polar + (size_t)p * n_r * n_theta;
-        for (int j = warp; j < n_r; j += nw) {
-            const float* row = src + (size_t)j * n_theta;
-            float* dst = sP + (size_t)j * pitch;
-            for (int col = lane; col < pitch; col += 32) {
-                int sc = col;
-                while (sc >= n_theta) sc -= n_theta;
-                dst[col] = __ldg(row + sc);
-            }
-        }
+        const int64_t p = *s_pattern;
+        if (p >= c.n) break;
+        const float* src = c.polar + (size_t)p * c.n_r * n_theta;
         const float pn = __ldg(c.pnorm + p);
         for (int li = 0; li < c.n_libs; ++li) {
             const SparseLib L = c.lib[li];
+            // the library's polar rows, padded with wrapped columns
+            for (int rr = warp; rr < L.n_rad; rr += kWarps) {
+                const float* row = src + (size_t)__ldg(L.radii + rr) * n_theta;
+                float* dst = sP + (size_t)rr * pitch;
+                for (int col = lane; col < pitch; col += 32) {
+                    int sc = col;
+                    while (sc >= n_theta) sc -= n_theta;
+                    dst[col] = __ldg(row + sc);
+                }
+            }
             if (threadIdx.x == 0) *counter = 0;
-            if (threadIdx.x < nw) lcnt[threadIdx.x] = 0;
+            if (threadIdx.x < kWarps) lcnt[threadIdx.x] = 0;
             __syncthreads();
             const uint32_t* mrow = c.mask[li] ? c.mask[li] + (size_t)p * L.words : nullptr;
             float* qo = c.q_out[li] ? c.q_out[li] + (size_t)p * L.K : nullptr;
             int32_t* so = c.s_out[li] ? c.s_out[li] + (size_t)p * L.K : nullptr;
-            const int32_t* crow = c.cand[li] ? c.cand[li] + (size_t)p * c.kc : nullptr;
-            uint32_t m = 0;          // remaining bits of the current mask word (warp-uniform)
-            int wd = 0;
+            float* wq = lq + warp * N;
+            int* wk = lk + warp * N;
+            int* ws = ls + warp * N;
             for (;;) {
-                // next template: from the candidate list, or the next set bit of a mask word
-                int k = -1;
-                if (crow) {
-                    int j = 0;
-                    if (lane == 0) j = atomicAdd(counter, 1);
-                    j = __shfl_sync(0xffffffffu, j, 0);
-                    if (j >= c.kc) break;
-                    k = __ldg(crow + j);
-                    if (k < 0 || k >= L.K) continue;
-                } else {
-                    bool done = false;
-                    while (m == 0) {
-                        if (lane == 0) wd = atomicAdd(counter, 1);
-                        wd = __shfl_sync(0xffffffffu, wd, 0);
-                        if (wd >= L.words) { done = true; break; }
-                        m = mrow ? __ldg(mrow + wd) : 0xffffffffu;
-                        const int rem = L.K - wd * 32;
-                        if (rem < 32) m &= (1u << rem) - 1u;
-                        if (qo) {
-                            const int kk = wd * 32 + lane;
-                            if (lane < rem && !((m >> lane) & 1u)) { qo[kk] = -INFINITY; so[kk] = -1; }
-                        }
-                    }
-                    if (done) break;
+                int wd = 0;
+                if (lane == 0) wd = atomicAdd(counter, 1);
+                wd = __shfl_sync(0xffffffffu, wd, 0);
+                if (wd >= L.words) break;
+                uint32_t m = mrow ? __ldg(mrow + wd) : 0xffffffffu;
+                const int rem = L.K - wd * 32;
+                if (rem < 32) m &= (1u << rem) - 1u;
+                // per-lane metadata of the word's 32 templates (one round trip per word)
+                const int kl = wd * 32 + lane;
+                int beg_l = 0, end_l = 0, S_l = 1;
+                float tn_l = 0.0f;
+                if (lane < rem && ((m >> lane) & 1u)) {
+                    beg_l = __ldg(L.off + kl);
+                    end_l = __ldg(L.off + kl + 1);
+                    S_l = __ldg(L.nshift + kl);
+                    tn_l = __ldg(L.norm + kl);
+                } else if (qo && lane < rem) {
+                    qo[kl] = -INFINITY;
+                    so[kl] = -1;
+                }
+                while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
-                    k = wd * 32 + bit;
-                }
-                float best;
-                int s;
-                score_dispatch<NBMAX>(sP, L, k, n_theta, lane, best, s);
-                const float d = pn * __ldg(L.norm + k);
-                float q;
-                if (d > 0.0f) q = __fdiv_rn(best, d);
-                else { q = 0.0f; s = 0; }
-                if (lane == 0) {
-                    if (qo) { qo[k] = q; so[k] = s; }
-                    if (c.hits) {
-                        float* wq = lq + warp * N;
-                        int* wk = lk + warp * N;
-                        int* ws = ls + warp * N;
-                        const int cnt = lcnt[warp];
-                        if (cnt < N || better(q, k, wq[N - 1], wk[N - 1])) {
-                            int i = cnt < N ? cnt : N - 1;
-                            while (i > 0 && better(q, k, wq[i - 1], wk[i - 1])) {
-                                wq[i] = wq[i - 1]; wk[i] = wk[i - 1]; ws[i] = ws[i - 1];
-                                --i;
+                    const int k = wd * 32 + bit;
+                    const int beg = __shfl_sync(0xffffffffu, beg_l, bit);
+                    const int end = __shfl_sync(0xffffffffu, end_l, bit);
+                    const int S = __shfl_sync(0xffffffffu, S_l, bit);
+                    const float tn = __shfl_sync(0xffffffffu, tn_l, bit);
+                    const float d = pn * tn;
+                    // a template whose correlation stays below the warp's N-th best (in
+                    // correlation units, with a margin for the division's rounding) cannot
+                    // enter the top-N, so its best shift is not resolved
+                    float thr_c = -FLT_MAX;
+                    if (!qo && c.hits && lcnt[warp] >= N && d > 0.0f) {
+                        const float t = wq[N - 1] * d;
+                        thr_c = t - fabsf(t) * 1e-6f;
+                    }
+                    int s = 0;
+                    bool resolved = false;
+                    const float best = score_dispatch<NBMAX>(sP, L, beg, end, S, n_theta, lane, thr_c, s, resolved);
+                    if (!resolved) continue;
+                    float q;
+                    if (d > 0.0f) q = __fdiv_rn(best, d);
+                    else { q = 0.0f; s = 0; }
+                    if (lane == 0) {
+                        if (qo) { qo[k] = q; so[k] = s; }
+                        if (c.hits) {
+                            const int cnt = lcnt[warp];
+                            if (cnt < N || better(q, k, wq[N - 1], wk[N - 1])) {
+                                int i = cnt < N ? cnt : N - 1;
+                                while (i > 0 && better(q, k, wq[i - 1], wk[i - 1])) {
+                                    wq[i] = wq[i - 1]; wk[i] = wk[i - 1]; ws[i] = ws[i - 1];
+                                    --i;
+                                }
+                                wq[i] = q; wk[i] = k; ws[i] = s;
+                                if (cnt < N) lcnt[warp] = cnt + 1;
                             }
-                            wq[i] = q; wk[i] = k; ws[i] = s;
-                            if (cnt < N) lcnt[warp] = cnt + 1;
                         }
                     }
+                    __syncwarp();
                 }
             }
             __syncthreads();
             if (c.hits && warp == 0) {
                 tm_hit* out = c.hits + (size_t)li * c.hits_lib_stride + (size_t)p * N;
-                const int total = nw * N;
+                const int total = kWarps * N;
                 for (int j = 0; j < N; ++j) {
                     float bq = -INFINITY;
                     int bk = INT_MAX, bi = -1;
@@ -208,7 +238,7 @@ sparse_kernel(const SparseCall c) {
                         if (kk < 0) continue;
                         if (bi < 0 || better(lq[ci], kk, bq, bk)) { bq = lq[ci]; bk = kk; bi = ci; }
                     }
-                    #pragma unroll
+#pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const float oq = __shfl_xor_sync(0xffffffffu, bq, o);
                         const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
@@ -240,35 +270,31 @@ sparse_kernel(const SparseCall c) {
 
 template <int NBMAX>
 cudaError_t launch_nb(const SparseCall& c, int num_sms, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // 1024 threads when only one CTA fits per SM, else 512 (more CTAs per SM)
-    int threads = smem > 110 * 1024 ? 1024 : 512;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX>, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) { threads = 512; e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX>, threads, smem); }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > c.n) grid = c.n;
-    sparse_kernel<NBMAX><<<(int)grid, threads, smem, st>>>(c);
+    e = cudaMemsetAsync(c.pattern_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    sparse_kernel<NBMAX><<<(int)grid, kThreads, smem, st>>>(c);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t sparse_smem_bytes(int n_r, int n_theta, int top_n) {
-    if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN) return 0;
-    const size_t nw = 32;   // lists sized for the largest block
-    const size_t b = (size_t)n_r * sparse_pitch(n_theta) * 4 + nw * top_n * 12 + nw * 4 + 16;
+size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n) {
+    if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
+    const size_t b = (size_t)max_rad * sparse_pitch(n_theta) * 4 + (size_t)kWarps * top_n * 12 + kWarps * 4 + 16;
     return b <= 232448 ? b : 0;
 }
 
 cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st) {
     if (c.n <= 0) return cudaSuccess;
-    const size_t smem = sparse_smem_bytes(c.n_r, c.n_theta, c.top_n);
+    const size_t smem = sparse_smem_bytes(c.max_rad, c.n_theta, c.top_n);
     if (!smem) return cudaErrorInvalidValue;
     const int nbmax = (c.n_theta + 31) / 32;
     if (nbmax <= 6) return launch_nb<6>(c, num_sms, smem, st);

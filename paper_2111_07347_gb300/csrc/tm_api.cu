@@ -77,6 +77,7 @@ struct Library {
     float* d_radial = nullptr;
     float* d_rnorm = nullptr;
     int32_t* d_rt = nullptr;       // r | (t << 16) per spot (BF16 path)
+    int32_t* d_radii = nullptr;    // distinct spot radii (sparse kernel rows)
     int32_t* d_order = nullptr;    // templates sorted by spot count (BF16 tile order)
     std::vector<int32_t> radii;    // distinct radii with spots
     size_t bytes = 0;
@@ -107,6 +108,10 @@ struct RadiusMap {                 // per set of libraries: union of radii
 };
 
 }  // namespace
+
+namespace tmgb {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace tmgb
 
 struct tm_ctx {
     int device = 0;
@@ -149,9 +154,13 @@ void dev_free(tm_ctx* ctx, void* p, size_t bytes) {
     ctx->used -= std::min(ctx->used, bytes ? bytes : 16);
 }
 
-// Workspace buffer `name` of at least `bytes`, grown on demand.
-int workspace(tm_ctx* ctx, const std::string& name, size_t bytes, void** out) {
-    Buffer& b = ctx->ws[name];
+// Workspace buffer `name` of at least `bytes` for work enqueued on stream `st`, grown on
+// demand.  Each stream has its own buffers, so calls on different streams never share
+// scratch memory and may overlap on the GPU; calls on one stream are ordered by it.
+int workspace(tm_ctx* ctx, cudaStream_t st, const std::string& name, size_t bytes, void** out) {
+    char key[64];
+    snprintf(key, sizeof key, "@%llx", (unsigned long long)(uintptr_t)st);
+    Buffer& b = ctx->ws[name + key];
     if (b.bytes < bytes) {
         if (b.p) {
             cudaDeviceSynchronize();
@@ -327,12 +336,6 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
                 L->r.push_back(m.r[i]);
                 L->t.push_back(m.t[i]);
                 L->I.push_back((float)m.I[i]);
-                const int w = (n_theta - m.t[i] + 31) / 32;
-                int2 sp;
-                sp.x = (m.r[i] * pitch + m.t[i]) | (w << 24);
-                const float fI = (float)m.I[i];
-                memcpy(&sp.y, &fI, 4);
-                spot.push_back(sp);
             }
             const int ord = rotational_order(m, n_theta);
             L->order.push_back(ord);
@@ -349,6 +352,15 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
     }
     const int64_t ns = (int64_t)L->r.size();
     if (ns >= (int64_t)1 << 31) return fail(TM_ERR_UNSUPPORTED, "tm_load_library: too many spots");
+    // distinct radii (rows of the sparse kernel's shared-memory image) and packed spots
+    std::vector<int32_t> row_of(n_r, -1);
+    for (size_t i = 0; i < L->radii.size(); ++i) row_of[L->radii[i]] = (int32_t)i;
+    spot.resize(ns);
+    for (int64_t i = 0; i < ns; ++i) {
+        const int w = (n_theta - L->t[i] + 31) / 32;
+        spot[i].x = (row_of[L->r[i]] * pitch + L->t[i]) | (w << 24);
+        memcpy(&spot[i].y, &L->I[i], 4);
+    }
     return TM_OK;
 }
 
@@ -387,6 +399,7 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
         {(void**)&L->d_rnorm, rnf.data(), rnf.size() * 4, "library radial norms"},
         {(void**)&L->d_rt, rt.data(), rt.size() * 4, "library spot positions"},
         {(void**)&L->d_order, order.data(), order.size() * 4, "library tile order"},
+        {(void**)&L->d_radii, L->radii.data(), L->radii.size() * 4, "library radii"},
     };
     for (auto& u : ups) {
         rc = dev_alloc(ctx, u.dst, u.bytes, u.what);
@@ -398,7 +411,7 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
 }
 
 void free_library(tm_ctx* ctx, Library* L) {
-    void* ps[] = {L->d_off, L->d_spot, L->d_norm, L->d_nshift, L->d_radial, L->d_rnorm, L->d_rt, L->d_order};
+    void* ps[] = {L->d_off, L->d_spot, L->d_norm, L->d_nshift, L->d_radial, L->d_rnorm, L->d_rt, L->d_order, L->d_radii};
     for (void* p : ps)
         if (p) cudaFree(p);
     ctx->used -= std::min(ctx->used, L->bytes);
@@ -410,6 +423,8 @@ tmgb::SparseLib sparse_view(const Library* L) {
     v.spot = L->d_spot;
     v.norm = L->d_norm;
     v.nshift = L->d_nshift;
+    v.radii = L->d_radii;
+    v.n_rad = (int32_t)std::max<size_t>(1, L->radii.size());
     v.K = (int32_t)L->K;
     v.K0 = (int32_t)L->K0;
     v.mirror = L->mirror;
@@ -575,7 +590,7 @@ void tm_index_params_default(tm_index_params* p) {
     p->prefilter_fraction = 1.0;
     p->top_n = 5;
     p->path = TM_PATH_FP32_SPARSE;
-    p->rescore_k = 64;
+    p->rescore_k = 256;
     p->reserved = 0;
 }
 
@@ -705,7 +720,7 @@ int tm_unload_library(tm_ctx* ctx, int lib_id) {
     DeviceGuard g(ctx->device);
     auto it = ctx->libs.find(lib_id);
     if (it == ctx->libs.end()) return fail(TM_ERR_NOT_FOUND, "tm_unload_library: no library %d", lib_id);
-    TM_CUDA(cudaEventSynchronize(ctx->ws_event), "tm_unload_library: wait for pending work");
+    TM_CUDA(cudaDeviceSynchronize(), "tm_unload_library: wait for pending work");
     free_library(ctx, it->second.get());
     ctx->libs.erase(it);
     return TM_OK;
@@ -803,13 +818,12 @@ int tm_prefilter(tm_ctx* ctx, int lib_id, const float* radial_dev, int64_t n, do
     Library* L = find_lib(ctx, lib_id);
     if (!L) return fail(TM_ERR_NOT_FOUND, "tm_prefilter: no library %d", lib_id);
     cudaStream_t st = (cudaStream_t)stream;
-    TM_CUDA(cudaStreamWaitEvent(st, ctx->ws_event, 0), "tm_prefilter: wait");
     float* rn;
-    int rc = workspace(ctx, "radial_norm", (size_t)n * 4, (void**)&rn);
+    int rc = workspace(ctx, st, "radial_norm", (size_t)n * 4, (void**)&rn);
     if (rc) return rc;
     float* sc = score_dev;
     if (!sc) {
-        rc = workspace(ctx, "score", (size_t)n * L->K * 4, (void**)&sc);
+        rc = workspace(ctx, st, "score", (size_t)n * L->K * 4, (void**)&sc);
         if (rc) return rc;
     }
     tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
@@ -817,7 +831,6 @@ int tm_prefilter(tm_ctx* ctx, int lib_id, const float* radial_dev, int64_t n, do
     TM_CUDA(tmgb::launch_prefilter_scores(radial_dev, rn, n, L->n_r, rl, sc, st), "tm_prefilter: scores");
     const int keep = keep_count(fraction, L->K);
     TM_CUDA(tmgb::launch_prefilter_select(sc, n, (int)L->K, keep, mask_dev, st), "tm_prefilter: select");
-    TM_CUDA(cudaEventRecord(ctx->ws_event, st), "tm_prefilter: record");
     return TM_OK;
 }
 
@@ -831,9 +844,16 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
     DeviceGuard g(ctx->device);
     Library* L = find_lib(ctx, lib_id);
     if (!L) return fail(TM_ERR_NOT_FOUND, "tm_correlate: no library %d", lib_id);
-    if (!tmgb::sparse_smem_bytes(L->n_r, L->n_theta, 1))
-        return fail(TM_ERR_UNSUPPORTED, "tm_correlate: polar grid %dx%d does not fit shared memory", L->n_r, L->n_theta);
+    const int n_rad = (int)std::max<size_t>(1, L->radii.size());
+    if (!tmgb::sparse_smem_bytes(n_rad, L->n_theta, 1))
+        return fail(TM_ERR_UNSUPPORTED, "tm_correlate: %d radii x %d angles do not fit shared memory", n_rad, L->n_theta);
+    cudaStream_t st = (cudaStream_t)stream;
+    int* pc;
+    int rc = workspace(ctx, st, "pattern_counter", sizeof(int), (void**)&pc);
+    if (rc) return rc;
     tmgb::SparseCall c{};
+    c.max_rad = n_rad;
+    c.pattern_counter = pc;
     c.polar = polar_dev;
     c.pnorm = norm_dev;
     c.n = n;
@@ -847,7 +867,7 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
     c.s_out[0] = s_dev;
     c.hits = nullptr;
     c.top_n = 1;
-    TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, (cudaStream_t)stream), "tm_correlate: launch");
+    TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_correlate: launch");
     return TM_OK;
 }
 
@@ -865,11 +885,12 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     if (params->path != TM_PATH_FP32_SPARSE && params->path != TM_PATH_BF16_RESCORE)
         return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: unknown path %d", params->path);
     const bool bf16 = params->path == TM_PATH_BF16_RESCORE;
-    if (bf16 && (params->rescore_k < 1 || params->rescore_k > 256))
-        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: rescore_k must be in [1, 256]");
+    if (bf16 && params->rescore_k < 1)
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: rescore_k must be >= 1");
     if (stats) memset(stats, 0, sizeof *stats);
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
     Library* libs[TM_MAX_LIBS];
     for (int i = 0; i < n_libs; ++i) {
         libs[i] = find_lib(ctx, lib_ids[i]);
@@ -881,8 +902,11 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     if (!frames_dev || !out_dev) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: NULL buffer");
     const int n_r = libs[0]->n_r, n_theta = libs[0]->n_theta, N = params->top_n;
     const double dr = libs[0]->dr;
-    if (!tmgb::sparse_smem_bytes(n_r, n_theta, N))
-        return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: polar grid %dx%d does not fit shared memory", n_r, n_theta);
+    int max_rad = 1;
+    for (int i = 0; i < n_libs; ++i) max_rad = std::max<int>(max_rad, (int)libs[i]->radii.size());
+    if (!tmgb::sparse_smem_bytes(max_rad, n_theta, N))
+        return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: %d radii x %d angles do not fit shared memory", max_rad,
+                    n_theta);
     const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
     const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
     tmgb::PolarTable tab;
@@ -900,7 +924,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
         rc = spectral_tables(ctx, n_theta, &spec);
         if (!rc) rc = radius_map(ctx, libs, lib_ids, n_libs, n_r, &rmap);
         if (rc) return rc;
-        if (tmgb::dense_smem_bytes(n_theta, n_r, rmap.n_rad, n_freq, kc) > 232448)
+        if (tmgb::dense_smem_bytes(n_theta, n_r, rmap.n_rad, n_freq) > 232448)
             return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: %d distinct radii exceed the BF16 kernel's shared memory",
                         rmap.n_rad);
     }
@@ -910,8 +934,8 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     // chunk size from a per-pattern workspace estimate (<= 4 GiB of workspace)
     size_t per = (size_t)n_r * n_theta * 4 + 4 + (size_t)n_r * 4 + 4;
     for (int i = 0; i < n_libs; ++i) {
-        if (pre) per += (size_t)libs[i]->K * 4 + ((libs[i]->K + 31) / 32) * 4 + (bf16 ? (size_t)keep[i] * 4 : 0);
-        if (bf16) per += (size_t)kc * 8;
+        if (pre || bf16) per += (size_t)libs[i]->K * 4 + ((libs[i]->K + 31) / 32) * 4;
+        if (pre && bf16) per += (size_t)keep[i] * 4;
     }
     if (bf16) per += (size_t)rmap.n_rad * n_freq * 4;
     size_t cap = (size_t)4 << 30;
@@ -924,30 +948,28 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
 
     float *polar, *pnorm, *radial, *rn = nullptr;
     void* phat = nullptr;
-    rc = workspace(ctx, "polar", (size_t)chunk * n_r * n_theta * 4, (void**)&polar);
-    if (!rc) rc = workspace(ctx, "pnorm", (size_t)chunk * 4, (void**)&pnorm);
-    if (!rc) rc = workspace(ctx, "radial", (size_t)chunk * n_r * 4, (void**)&radial);
-    if (!rc && pre) rc = workspace(ctx, "radial_norm", (size_t)chunk * 4, (void**)&rn);
-    if (!rc && bf16) rc = workspace(ctx, "phat", (size_t)chunk * rmap.n_rad * n_freq * 4, &phat);
+    int* pcount = nullptr;
+    rc = workspace(ctx, st, "pattern_counter", sizeof(int), (void**)&pcount);
+    if (!rc) rc = workspace(ctx, st, "polar", (size_t)chunk * n_r * n_theta * 4, (void**)&polar);
+    if (!rc) rc = workspace(ctx, st, "pnorm", (size_t)chunk * 4, (void**)&pnorm);
+    if (!rc) rc = workspace(ctx, st, "radial", (size_t)chunk * n_r * 4, (void**)&radial);
+    if (!rc && pre) rc = workspace(ctx, st, "radial_norm", (size_t)chunk * 4, (void**)&rn);
+    if (!rc && bf16) rc = workspace(ctx, st, "phat", (size_t)chunk * rmap.n_rad * n_freq * 4, &phat);
     if (rc) return rc;
     float* score[TM_MAX_LIBS] = {};
     uint32_t* mask[TM_MAX_LIBS] = {};
     int32_t* list[TM_MAX_LIBS] = {};
-    int32_t* cand[TM_MAX_LIBS] = {};
-    float* cand_q[TM_MAX_LIBS] = {};
     for (int i = 0; i < n_libs; ++i) {
         const std::string s = std::to_string(i);
-        if (pre) {
-            rc = workspace(ctx, "score" + s, (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
-            if (!rc) rc = workspace(ctx, "mask" + s, (size_t)chunk * ((libs[i]->K + 31) / 32) * 4, (void**)&mask[i]);
-            if (!rc && bf16) rc = workspace(ctx, "list" + s, (size_t)chunk * keep[i] * 4, (void**)&list[i]);
+        // score/mask: pre-filter scores and keep-mask; on the BF16 path reused afterwards for
+        // the pre-scores and the mask of the candidates to rescore
+        if (pre || bf16) {
+            rc = workspace(ctx, st, "score" + s, (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
+            if (!rc) rc = workspace(ctx, st, "mask" + s, (size_t)chunk * ((libs[i]->K + 31) / 32) * 4, (void**)&mask[i]);
         }
-        if (!rc && bf16) rc = workspace(ctx, "cand" + s, (size_t)chunk * kc * 4, (void**)&cand[i]);
-        if (!rc && bf16) rc = workspace(ctx, "cand_q" + s, (size_t)chunk * kc * 4, (void**)&cand_q[i]);
+        if (!rc && pre && bf16) rc = workspace(ctx, st, "list" + s, (size_t)chunk * keep[i] * 4, (void**)&list[i]);
         if (rc) return rc;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    TM_CUDA(cudaStreamWaitEvent(st, ctx->ws_event, 0), "tm_index_patterns: wait");
     const size_t esz = dtype == TM_DTYPE_U16 ? 2 : 4;
     int64_t launches = 0, corr = 0, scored = 0;
     for (int64_t c0 = 0; c0 < n; c0 += chunk) {
@@ -984,13 +1006,13 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
         c.n_r = n_r;
         c.n_theta = n_theta;
         c.pitch = tmgb::sparse_pitch(n_theta);
+        c.max_rad = max_rad;
+        c.pattern_counter = pcount;
         c.n_libs = n_libs;
         for (int i = 0; i < n_libs; ++i) {
             c.lib[i] = sparse_view(libs[i]);
-            if (pre && !bf16) c.mask[i] = mask[i];
-            if (bf16) c.cand[i] = cand[i];
+            if (pre || bf16) c.mask[i] = mask[i];
         }
-        c.kc = bf16 ? kc : 0;
         c.hits = out_dev + (size_t)c0 * N;
         c.hits_lib_stride = n * N;
         c.top_n = N;
@@ -1016,10 +1038,10 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                 dc.lib[i] = dense_view(libs[i]);
                 dc.list[i] = pre ? list[i] : nullptr;
                 dc.count[i] = keep[i];
-                dc.cand[i] = cand[i];
-                dc.cand_q[i] = cand_q[i];
+                dc.pre[i] = score[i];
+                // templates not scored read as -NaN, the smallest key of the select
+                TM_CUDA(cudaMemsetAsync(score[i], 0xFF, (size_t)m * libs[i]->K * 4, st), "tm_index_patterns: memset");
             }
-            dc.kc = kc;
             dc.error = ctx->d_error;
             {
                 StageTimer tmr(ctx, TM_STAGE_DENSE, st);
@@ -1028,6 +1050,12 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             ++launches;
             {
                 StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
+                for (int i = 0; i < n_libs; ++i) {
+                    const int kci = std::min(kc, keep[i]);
+                    TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)libs[i]->K, kci, mask[i], st),
+                            "tm_index_patterns: candidates");
+                    ++launches;
+                }
                 TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: rescore");
             }
             ++launches;
@@ -1047,7 +1075,6 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             }
         }
     }
-    TM_CUDA(cudaEventRecord(ctx->ws_event, st), "tm_index_patterns: record");
     if (stats) {
         stats->patterns = n;
         stats->correlations = corr;
@@ -1058,12 +1085,11 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
 }
 
 int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev, const float* radial_dev,
-                int64_t n, double fraction, int32_t kc, int32_t* cand_dev, float* score_dev, void* stream) {
+                int64_t n, double fraction, float* score_dev, void* stream) {
     if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_prescore: ctx is NULL");
-    if (n < 0 || kc < 1 || kc > 256 || !(fraction > 0.0 && fraction <= 1.0))
-        return fail(TM_ERR_INVALID_ARG, "tm_prescore: bad n, kc or fraction");
+    if (n < 0 || !(fraction > 0.0 && fraction <= 1.0)) return fail(TM_ERR_INVALID_ARG, "tm_prescore: bad n or fraction");
     if (n == 0) return TM_OK;
-    if (!polar_dev || !norm_dev || !cand_dev || (fraction < 1.0 && !radial_dev))
+    if (!polar_dev || !norm_dev || !score_dev || (fraction < 1.0 && !radial_dev))
         return fail(TM_ERR_INVALID_ARG, "tm_prescore: NULL buffer");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
@@ -1079,24 +1105,23 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
     int rc = spectral_tables(ctx, n_theta, &spec);
     if (!rc) rc = radius_map(ctx, libs, ids, 1, n_r, &rm);
     if (rc) return rc;
-    if (tmgb::dense_smem_bytes(n_theta, n_r, rm.n_rad, n_freq, kc) > 232448)
+    if (tmgb::dense_smem_bytes(n_theta, n_r, rm.n_rad, n_freq) > 232448)
         return fail(TM_ERR_UNSUPPORTED, "tm_prescore: %d distinct radii exceed shared memory", rm.n_rad);
     const int keep = keep_count(fraction, L->K);
+    cudaStream_t st = (cudaStream_t)stream;
     void* phat;
-    rc = workspace(ctx, "phat", (size_t)n * rm.n_rad * n_freq * 4, &phat);
+    rc = workspace(ctx, st, "phat", (size_t)n * rm.n_rad * n_freq * 4, &phat);
     float* sc = nullptr;
     float* rn = nullptr;
     uint32_t* mask = nullptr;
     int32_t* list = nullptr;
     if (!rc && fraction < 1.0) {
-        rc = workspace(ctx, "score0", (size_t)n * L->K * 4, (void**)&sc);
-        if (!rc) rc = workspace(ctx, "radial_norm", (size_t)n * 4, (void**)&rn);
-        if (!rc) rc = workspace(ctx, "mask0", (size_t)n * ((L->K + 31) / 32) * 4, (void**)&mask);
-        if (!rc) rc = workspace(ctx, "list0", (size_t)n * keep * 4, (void**)&list);
+        rc = workspace(ctx, st, "score0", (size_t)n * L->K * 4, (void**)&sc);
+        if (!rc) rc = workspace(ctx, st, "radial_norm", (size_t)n * 4, (void**)&rn);
+        if (!rc) rc = workspace(ctx, st, "mask0", (size_t)n * ((L->K + 31) / 32) * 4, (void**)&mask);
+        if (!rc) rc = workspace(ctx, st, "list0", (size_t)n * keep * 4, (void**)&list);
     }
     if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    TM_CUDA(cudaStreamWaitEvent(st, ctx->ws_event, 0), "tm_prescore: wait");
     if (fraction < 1.0) {
         tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
         TM_CUDA(tmgb::launch_radial_norm(radial_dev, n, n_r, rn, st), "tm_prescore: radial norm");
@@ -1106,6 +1131,7 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
     }
     TM_CUDA(tmgb::launch_dft(polar_dev, norm_dev, n, n_r, n_theta, rm.radii, rm.n_rad, n_freq, spec.twiddle, phat,
                              ctx->num_sms, st), "tm_prescore: dft");
+    TM_CUDA(cudaMemsetAsync(score_dev, 0xFF, (size_t)n * L->K * 4, st), "tm_prescore: memset");
     tmgb::DenseCall dc{};
     dc.phat = phat;
     dc.n = n;
@@ -1120,12 +1146,10 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
     dc.lib[0] = dense_view(L);
     dc.list[0] = list;
     dc.count[0] = keep;
-    dc.cand[0] = cand_dev;
-    dc.cand_q[0] = score_dev;
-    dc.kc = kc;
+    dc.pre[0] = score_dev;
     dc.error = ctx->d_error;
     TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_prescore: dense");
-    TM_CUDA(cudaEventRecord(ctx->ws_event, st), "tm_prescore: record");
     return TM_OK;
 }
+
 }  // extern "C"

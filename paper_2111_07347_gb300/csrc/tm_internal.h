@@ -11,16 +11,23 @@
 
 namespace tmgb {
 
+// Message for tm_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // ------------------------------------------------------------------ device library views
-// Sparse templates in CSR.  spot[i].x packs the shared-memory address of the spot in the
-// sparse kernel's polar layout (row pitch sparse_pitch(n_theta)): bits 0..23 = r * pitch + t,
-// bits 24..31 = w = ceil((n_theta - t) / 32), the first 32-wide shift block whose columns
-// wrap past n_theta.  spot[i].y = float bits of the intensity.
+// Sparse templates in CSR.  The sparse kernel keeps only the library's distinct spot
+// radii (radii[0..n_rad)) as rows of its shared-memory polar image, row pitch
+// sparse_pitch(n_theta).  spot[i].x packs the shared-memory address of the spot: bits
+// 0..23 = rho * pitch + t with rho the spot's row in radii[], bits 24..31 =
+// w = ceil((n_theta - t) / 32), the first 32-wide shift block whose columns wrap past
+// n_theta.  spot[i].y = float bits of the intensity.
 struct SparseLib {
     const int32_t* off;        // [K + 1]
     const int2* spot;          // [n_spots]
     const float* norm;         // [K]  sqrt(sum I^2)
     const int32_t* nshift;     // [K]  shifts to evaluate = n_theta / order_k
+    const int32_t* radii;      // [n_rad]  distinct spot radii (polar rows), ascending
+    int32_t n_rad;
     int32_t K;
     int32_t K0;
     int32_t mirror;
@@ -60,6 +67,8 @@ struct SparseCall {
     int64_t n;
     int n_r, n_theta;
     int pitch;                          // sparse_pitch(n_theta)
+    int max_rad;                        // largest n_rad of the libraries (shared-memory rows)
+    int* pattern_counter;               // device int, zeroed by the launcher
     int n_libs;
     SparseLib lib[TM_MAX_LIBS];
     const uint32_t* mask[TM_MAX_LIBS];  // [n][words] or null
@@ -68,12 +77,10 @@ struct SparseCall {
     tm_hit* hits;                       // [n_libs][hits_lib_stride] or null
     int64_t hits_lib_stride;            // elements between libraries (>= n * top_n)
     int top_n;
-    const int32_t* cand[TM_MAX_LIBS];   // candidate mode: [n][kc] template ids (-1 = none)
-    int kc;                             // candidates per pattern (0 = mask mode)
 };
 
-// Shared-memory bytes the sparse kernel needs for a polar grid (0 when unsupported).
-size_t sparse_smem_bytes(int n_r, int n_theta, int top_n);
+// Shared-memory bytes the sparse kernel needs (0 when unsupported).
+size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n);
 int sparse_pitch(int n_theta);
 cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);
 
@@ -96,18 +103,16 @@ struct DenseCall {
     const float2* twiddle;     // [n_theta]  (cos, sin) of 2 pi j / n_theta
     int n_libs;
     DenseLib lib[TM_MAX_LIBS];
-    const int32_t* list[TM_MAX_LIBS];   // [n][count] survivors or null (all, in lib order)
+    const int32_t* list[TM_MAX_LIBS];   // [n][count] survivors or null (all, in tile order)
     int count[TM_MAX_LIBS];             // templates scored per pattern
-    int32_t* cand[TM_MAX_LIBS];         // [n][kc] out
-    float* cand_q[TM_MAX_LIBS];         // [n][kc] out (pre-scores) or null
-    int kc;
+    float* pre[TM_MAX_LIBS];            // [n][K] out: pre-score of every scored template
     unsigned* error;                    // device word: bit 0 = a bounded wait timed out
 };
 
 bool dense_supported(int n_theta);
 int dense_basis_rows();
 int dense_basis_cols();
-size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq, int kc);
+size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq);
 cudaError_t launch_dense(const DenseCall& c, int num_sms, cudaStream_t st);
 cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_r, int n_theta,
                        const int32_t* radii, int n_rad, int n_freq, const float2* twiddle, void* out,

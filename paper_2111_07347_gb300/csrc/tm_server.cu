@@ -1,0 +1,318 @@
+// Serving loop: continuous batching of indexing requests (scan lines and whole maps) on
+// one GPU, for on-line mapping during acquisition (arXiv 2111.07347, Section 5).
+//
+// A worker thread owns `slots` CUDA streams, each with device staging for one tile of
+// frames and its hits.  Requests are split into tiles; whenever a slot is free the worker
+// takes the next tile of the highest-priority request that still has tiles (ties: the
+// earlier submission), copies its frames to the device, runs tm_index_patterns on the
+// slot's stream and copies the hits back into the request's output, then records an
+// event.  Finished slots are detected by polling their events, so tiles of different
+// requests overlap on the device (copies of one tile with the kernels of another).
+// Admission: the frame bytes of requests submitted and not finished stay within
+// queue_bytes.  Every wait is bounded by the caller's timeout.
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "tm_internal.h"
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    tm_request req{};
+    std::vector<int32_t> libs;
+    int64_t next = 0;            // first pattern not yet dispatched
+    int64_t tiles_total = 0, tiles_done = 0, tiles_inflight = 0;
+    int status = TM_OK;
+    bool cancelled = false, finished = false;
+    double t_submit = 0, t_first = -1, t_done = 0;
+    size_t bytes = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void* frames = nullptr;      // device staging
+    tm_hit* hits = nullptr;      // device [max_libs][tile][max_top_n]
+    std::shared_ptr<Request> req;
+    int64_t p0 = 0, m = 0;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct tm_server {
+    tm_ctx* ctx = nullptr;
+    tm_server_params prm{};
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done, cv_room;
+    std::map<uint64_t, std::shared_ptr<Request>> reqs;
+    std::deque<std::shared_ptr<Request>> pending;   // requests with tiles left to dispatch
+    uint64_t next_ticket = 1;
+    size_t bytes_in = 0;
+    bool stop = false, paused = false;
+    std::thread worker;
+    std::chrono::steady_clock::time_point t0;
+    int device = 0;
+
+    double now_ms() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+int sfail(int code, const char* msg) {
+    tmgb::set_last_error(msg);
+    return code;
+}
+
+void finish_locked(tm_server* s, const std::shared_ptr<Request>& r) {
+    r->finished = true;
+    r->t_done = s->now_ms();
+    s->bytes_in -= std::min(s->bytes_in, r->bytes);
+    s->cv_done.notify_all();
+    s->cv_room.notify_all();
+}
+
+// Pick the next tile: highest priority, then submission order.
+std::shared_ptr<Request> pick_locked(tm_server* s) {
+    std::shared_ptr<Request> best;
+    for (auto& r : s->pending) {
+        if (r->cancelled || r->next >= r->req.n) continue;
+        if (!best || r->req.priority > best->req.priority) best = r;
+    }
+    return best;
+}
+
+void worker_main(tm_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        // 1. retire finished slots
+        bool any_busy = false;
+        for (auto& sl : s->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) { any_busy = true; continue; }
+            auto r = sl.req;
+            if (q != cudaSuccess && r->status == TM_OK) r->status = TM_ERR_CUDA;
+            sl.busy = false;
+            sl.req.reset();
+            r->tiles_inflight--;
+            r->tiles_done++;
+            const bool all_sent = r->next >= r->req.n || r->cancelled;
+            if (all_sent && r->tiles_inflight == 0 && !r->finished) {
+                if (r->cancelled && r->status == TM_OK) r->status = TM_ERR_CANCELLED;
+                finish_locked(s, r);
+            }
+        }
+        // drop fully dispatched or cancelled requests from the pending list
+        for (auto it = s->pending.begin(); it != s->pending.end();) {
+            auto& r = *it;
+            if (r->cancelled && r->tiles_inflight == 0 && !r->finished) {
+                r->status = TM_ERR_CANCELLED;
+                finish_locked(s, r);
+            }
+            if (r->finished || r->next >= r->req.n || r->cancelled) it = s->pending.erase(it);
+            else ++it;
+        }
+        if (s->stop && !any_busy) break;
+        // 2. dispatch into free slots
+        bool dispatched = false;
+        if (!s->stop && !s->paused) {
+            for (auto& sl : s->slots) {
+                if (sl.busy) continue;
+                auto r = pick_locked(s);
+                if (!r) break;
+                const int64_t m = std::min<int64_t>(s->prm.tile_patterns, r->req.n - r->next);
+                const size_t esz = r->req.dtype == TM_DTYPE_U16 ? 2 : 4;
+                const size_t fb = (size_t)m * r->req.H * r->req.W * esz;
+                const char* src = (const char*)r->req.frames_host + (size_t)r->next * r->req.H * r->req.W * esz;
+                sl.req = r;
+                sl.p0 = r->next;
+                sl.m = m;
+                sl.busy = true;
+                r->next += m;
+                r->tiles_inflight++;
+                if (r->t_first < 0) r->t_first = s->now_ms();
+                int rc = TM_OK;
+                if (cudaMemcpyAsync(sl.frames, src, fb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) rc = TM_ERR_CUDA;
+                const int N = r->req.params.top_n, L = r->req.n_libs;
+                if (rc == TM_OK)
+                    rc = tm_index_patterns(s->ctx, &r->req.params, sl.frames, r->req.dtype, m, r->req.H, r->req.W,
+                                           nullptr, r->libs.data(), L, sl.hits, nullptr, sl.stream);
+                for (int li = 0; li < L && rc == TM_OK; ++li) {
+                    tm_hit* dst = r->req.out_host + ((size_t)li * r->req.n + sl.p0) * N;
+                    if (cudaMemcpyAsync(dst, sl.hits + (size_t)li * m * N, (size_t)m * N * sizeof(tm_hit),
+                                        cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                        rc = TM_ERR_CUDA;
+                }
+                if (rc != TM_OK && r->status == TM_OK) r->status = rc;
+                cudaEventRecord(sl.done, sl.stream);
+                dispatched = true;
+            }
+        }
+        if (dispatched) continue;
+        // 3. sleep briefly while tiles are in flight, else until work arrives
+        if (any_busy) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            lk.lock();
+        } else {
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void tm_server_params_default(tm_server_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->slots = 3;
+    p->tile_patterns = 512;
+    p->max_H = 256;
+    p->max_W = 256;
+    p->max_libs = 2;
+    p->max_top_n = 5;
+    p->queue_bytes = 0;
+    p->blocking_submit = 1;
+}
+
+int tm_server_create(tm_ctx* ctx, const tm_server_params* params, tm_server** out) {
+    if (!ctx || !out) return sfail(TM_ERR_INVALID_ARG, "tm_server_create: NULL argument");
+    tm_server_params p;
+    if (params) p = *params;
+    else tm_server_params_default(&p);
+    if (p.slots < 1 || p.slots > 16 || p.tile_patterns < 1 || p.max_H < 1 || p.max_W < 1 || p.max_libs < 1 ||
+        p.max_libs > TM_MAX_LIBS || p.max_top_n < 1 || p.max_top_n > TM_MAX_TOPN)
+        return sfail(TM_ERR_INVALID_ARG, "tm_server_create: bad parameters");
+    auto s = std::make_unique<tm_server>();
+    s->ctx = ctx;
+    s->prm = p;
+    s->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&s->device) != cudaSuccess) return sfail(TM_ERR_CUDA, "tm_server_create: no device");
+    s->slots.resize(p.slots);
+    for (auto& sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&sl.frames, (size_t)p.tile_patterns * p.max_H * p.max_W * 4) != cudaSuccess ||
+            cudaMalloc(&sl.hits, (size_t)p.max_libs * p.tile_patterns * p.max_top_n * sizeof(tm_hit)) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& x : s->slots) {
+                if (x.frames) cudaFree(x.frames);
+                if (x.hits) cudaFree(x.hits);
+                if (x.done) cudaEventDestroy(x.done);
+                if (x.stream) cudaStreamDestroy(x.stream);
+            }
+            return sfail(TM_ERR_OOM, "tm_server_create: staging allocation failed");
+        }
+    }
+    tm_server* raw = s.release();
+    raw->worker = std::thread(worker_main, raw);
+    *out = raw;
+    return TM_OK;
+}
+
+int tm_server_submit(tm_server* s, const tm_request* req, uint64_t* ticket) {
+    if (!s || !req || !ticket) return sfail(TM_ERR_INVALID_ARG, "tm_server_submit: NULL argument");
+    if (req->n < 1 || !req->frames_host || !req->out_host || req->H < 1 || req->W < 1 || req->H > s->prm.max_H ||
+        req->W > s->prm.max_W || req->n_libs < 1 || req->n_libs > s->prm.max_libs || !req->lib_ids ||
+        (req->dtype != TM_DTYPE_U16 && req->dtype != TM_DTYPE_F32) || req->params.top_n < 1 ||
+        req->params.top_n > s->prm.max_top_n)
+        return sfail(TM_ERR_INVALID_ARG, "tm_server_submit: request outside the server's limits");
+    auto r = std::make_shared<Request>();
+    r->req = *req;
+    r->libs.assign(req->lib_ids, req->lib_ids + req->n_libs);
+    r->req.lib_ids = r->libs.data();
+    r->tiles_total = (req->n + s->prm.tile_patterns - 1) / s->prm.tile_patterns;
+    r->bytes = (size_t)req->n * req->H * req->W * (req->dtype == TM_DTYPE_U16 ? 2 : 4);
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->prm.queue_bytes && s->bytes_in + r->bytes > s->prm.queue_bytes && s->bytes_in > 0) {
+        if (!s->prm.blocking_submit) return sfail(TM_ERR_BUSY, "tm_server_submit: admission budget full");
+        s->cv_room.wait(lk, [&] { return s->stop || s->bytes_in == 0 || s->bytes_in + r->bytes <= s->prm.queue_bytes; });
+        if (s->stop) return sfail(TM_ERR_CANCELLED, "tm_server_submit: server stopping");
+    }
+    r->ticket = s->next_ticket++;
+    r->t_submit = s->now_ms();
+    s->bytes_in += r->bytes;
+    s->reqs[r->ticket] = r;
+    s->pending.push_back(r);
+    *ticket = r->ticket;
+    s->cv_work.notify_all();
+    return TM_OK;
+}
+
+int tm_server_wait(tm_server* s, uint64_t ticket, int32_t timeout_ms, tm_request_status* status) {
+    if (!s) return sfail(TM_ERR_INVALID_ARG, "tm_server_wait: NULL server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return sfail(TM_ERR_NOT_FOUND, "tm_server_wait: unknown ticket");
+    auto r = it->second;
+    auto done = [&] { return r->finished; };
+    if (timeout_ms < 0) s->cv_done.wait(lk, done);
+    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+        return sfail(TM_ERR_TIMEOUT, "tm_server_wait: request not finished in time");
+    if (status) {
+        status->status = r->status;
+        status->tiles = (int32_t)r->tiles_done;
+        status->submit_ms = r->t_submit;
+        status->first_dispatch_ms = r->t_first;
+        status->done_ms = r->t_done;
+    }
+    s->reqs.erase(it);
+    return TM_OK;
+}
+
+int tm_server_cancel(tm_server* s, uint64_t ticket) {
+    if (!s) return sfail(TM_ERR_INVALID_ARG, "tm_server_cancel: NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return sfail(TM_ERR_NOT_FOUND, "tm_server_cancel: unknown ticket");
+    it->second->cancelled = true;
+    s->cv_work.notify_all();
+    return TM_OK;
+}
+
+int tm_server_pause(tm_server* s, int32_t paused) {
+    if (!s) return sfail(TM_ERR_INVALID_ARG, "tm_server_pause: NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+    s->cv_work.notify_all();
+    return TM_OK;
+}
+
+void tm_server_destroy(tm_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        for (auto& kv : s->reqs) kv.second->cancelled = true;
+        s->cv_work.notify_all();
+        s->cv_room.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& sl : s->slots) {
+        cudaStreamSynchronize(sl.stream);
+        cudaFree(sl.frames);
+        cudaFree(sl.hits);
+        cudaEventDestroy(sl.done);
+        cudaStreamDestroy(sl.stream);
+    }
+    delete s;
+}
+
+}  // extern "C"

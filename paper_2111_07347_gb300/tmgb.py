@@ -66,6 +66,24 @@ class tm_stats(ctypes.Structure):
                 ("templates_scored", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
+class tm_server_params(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("tile_patterns", ctypes.c_int32), ("max_H", ctypes.c_int32),
+                ("max_W", ctypes.c_int32), ("max_libs", ctypes.c_int32), ("max_top_n", ctypes.c_int32),
+                ("queue_bytes", ctypes.c_size_t), ("blocking_submit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class tm_request(ctypes.Structure):
+    _fields_ = [("frames_host", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("n", ctypes.c_int64), ("lib_ids", ctypes.c_void_p),
+                ("n_libs", ctypes.c_int32), ("priority", ctypes.c_int32), ("params", tm_index_params),
+                ("out_host", ctypes.c_void_p)]
+
+
+class tm_request_status(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("tiles", ctypes.c_int32), ("submit_ms", ctypes.c_double),
+                ("first_dispatch_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
 TM_STAGE_COUNT = 8
 STAGES = ["polar", "prefilter", "sparse", "dft", "dense", "rescore", "stage6", "stage7"]
 
@@ -98,9 +116,15 @@ _SIGS = {
                                          ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P,
                                          ctypes.POINTER(tm_stats), _P]),
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
-    "tm_prescore": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
-                                   _P, _P, _P]),
+    "tm_prescore": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     "tm_check": (ctypes.c_int, [_P, _P]),
+    "tm_server_params_default": (None, [ctypes.POINTER(tm_server_params)]),
+    "tm_server_create": (ctypes.c_int, [_P, ctypes.POINTER(tm_server_params), ctypes.POINTER(_P)]),
+    "tm_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(tm_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "tm_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(tm_request_status)]),
+    "tm_server_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "tm_server_pause": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "tm_server_destroy": (None, [_P]),
     "tm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tm_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(tm_profile)]),
 }
@@ -233,7 +257,7 @@ def tm_library_export(ctx: int, lib_id: int) -> dict:
 
 
 def make_params(gamma=0.5, subtract=0.0, cx=math.nan, cy=math.nan, prefilter=1.0, top_n=5,
-                path=TM_PATH_FP32_SPARSE, rescore_k=64) -> tm_index_params:
+                path=TM_PATH_FP32_SPARSE, rescore_k=256) -> tm_index_params:
     p = tm_index_params_default()
     p.gamma, p.subtract, p.cx, p.cy = gamma, subtract, cx, cy
     p.prefilter_fraction, p.top_n, p.path, p.rescore_k = prefilter, top_n, path, rescore_k
@@ -254,9 +278,8 @@ def tm_correlate(ctx, lib_id, polar_ptr, norm_ptr, n, mask_ptr, q_ptr, s_ptr, st
     _check(library().tm_correlate(ctx, lib_id, polar_ptr, norm_ptr, n, mask_ptr, q_ptr, s_ptr, stream))
 
 
-def tm_prescore(ctx, lib_id, polar_ptr, norm_ptr, radial_ptr, n, fraction, kc, cand_ptr, score_ptr, stream) -> None:
-    _check(library().tm_prescore(ctx, lib_id, polar_ptr, norm_ptr, radial_ptr, n, fraction, kc, cand_ptr, score_ptr,
-                                 stream))
+def tm_prescore(ctx, lib_id, polar_ptr, norm_ptr, radial_ptr, n, fraction, score_ptr, stream) -> None:
+    _check(library().tm_prescore(ctx, lib_id, polar_ptr, norm_ptr, radial_ptr, n, fraction, score_ptr, stream))
 
 
 def tm_check(ctx, stream) -> None:
@@ -279,6 +302,100 @@ def tm_profile_read(ctx) -> dict:
     p = tm_profile()
     _check(library().tm_profile_read(ctx, ctypes.byref(p)))
     return {STAGES[i]: (p.ms[i], p.launches[i]) for i in range(TM_STAGE_COUNT) if p.launches[i]}
+
+
+def tm_server_params_default() -> tm_server_params:
+    p = tm_server_params()
+    library().tm_server_params_default(ctypes.byref(p))
+    return p
+
+
+def tm_server_create(ctx, params: tm_server_params) -> int:
+    h = _P()
+    _check(library().tm_server_create(ctx, ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def tm_server_submit(server, req: tm_request) -> int:
+    t = ctypes.c_uint64()
+    _check(library().tm_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def tm_server_wait(server, ticket: int, timeout_ms: int = -1) -> dict:
+    st = tm_request_status()
+    _check(library().tm_server_wait(server, ticket, timeout_ms, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in tm_request_status._fields_}
+
+
+def tm_server_cancel(server, ticket: int) -> None:
+    _check(library().tm_server_cancel(server, ticket))
+
+
+def tm_server_pause(server, paused: bool) -> None:
+    _check(library().tm_server_pause(server, 1 if paused else 0))
+
+
+def tm_server_destroy(server) -> None:
+    library().tm_server_destroy(server)
+
+
+class Server:
+    """Serving loop over a Context: host frames in, host hits out (see tm_server_* in tmgb.h)."""
+
+    def __init__(self, ctx: "Context", slots=3, tile_patterns=512, max_H=256, max_W=256, max_libs=2, max_top_n=5,
+                 queue_bytes=0, blocking_submit=True):
+        p = tm_server_params_default()
+        p.slots, p.tile_patterns, p.max_H, p.max_W = slots, tile_patterns, max_H, max_W
+        p.max_libs, p.max_top_n, p.queue_bytes, p.blocking_submit = max_libs, max_top_n, queue_bytes, int(blocking_submit)
+        self.ctx = ctx
+        self.handle = tm_server_create(ctx.handle, p)
+        self._keep = {}
+
+    def submit(self, frames: np.ndarray, lib_ids, top_n=5, priority=0, out: np.ndarray | None = None, **kw) -> int:
+        """frames: C-contiguous uint16/float32 [n][H][W] host array (pinned memory gives overlap);
+        returns the ticket.  The result array is returned by wait()."""
+        if isinstance(lib_ids, int):
+            lib_ids = [lib_ids]
+        n, H, W = frames.shape
+        if out is None:
+            out = np.empty((len(lib_ids), n, top_n), dtype=HIT_DTYPE)
+        ids = np.ascontiguousarray(lib_ids, dtype=np.int32)
+        r = tm_request()
+        r.frames_host = frames.ctypes.data
+        r.dtype = TM_DTYPE_U16 if frames.dtype == np.uint16 else TM_DTYPE_F32
+        r.H, r.W, r.n = H, W, n
+        r.lib_ids = ids.ctypes.data
+        r.n_libs = len(lib_ids)
+        r.priority = priority
+        r.params = make_params(top_n=top_n, **kw)
+        r.out_host = out.ctypes.data
+        t = tm_server_submit(self.handle, r)
+        self._keep[t] = (frames, out, ids)
+        return t
+
+    def wait(self, ticket, timeout_ms=-1):
+        st = tm_server_wait(self.handle, ticket, timeout_ms)
+        frames, out, ids = self._keep.pop(ticket)
+        return out, st
+
+    def cancel(self, ticket):
+        tm_server_cancel(self.handle, ticket)
+
+    def pause(self, paused=True):
+        tm_server_pause(self.handle, paused)
+
+    def close(self):
+        if self.handle:
+            tm_server_destroy(self.handle)
+            self.handle = 0
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- torch-facing wrapper
@@ -374,22 +491,22 @@ class Context:
                      None if mask is None else mask.data_ptr(), q.data_ptr(), s.data_ptr(), _stream_ptr(stream))
         return q, s
 
-    def prescore(self, lib_id, polar, norm, radial=None, fraction=1.0, kc=64, stream=None):
+    def prescore(self, lib_id, polar, norm, radial=None, fraction=1.0, stream=None):
+        """BF16 tensor-core pre-score of every template: [n][K] float, NaN where not scored."""
         import torch
         n = polar.shape[0]
-        cand = torch.empty((n, kc), dtype=torch.int32, device=polar.device)
-        score = torch.empty((n, kc), dtype=torch.float32, device=polar.device)
+        K = self.library_info(lib_id)["n_templates"]
+        score = torch.empty((n, K), dtype=torch.float32, device=polar.device)
         tm_prescore(self.handle, lib_id, polar.data_ptr(), norm.data_ptr(),
-                    None if radial is None else radial.data_ptr(), n, fraction, kc, cand.data_ptr(),
-                    score.data_ptr(), _stream_ptr(stream))
-        return cand, score
+                    None if radial is None else radial.data_ptr(), n, fraction, score.data_ptr(), _stream_ptr(stream))
+        return score
 
     def check(self, stream=None):
         """Synchronise and raise TmError(TM_ERR_TIMEOUT) if a kernel stopped on a bounded wait."""
         tm_check(self.handle, _stream_ptr(stream))
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
-              path=TM_PATH_FP32_SPARSE, rescore_k=64, cx=math.nan, cy=math.nan, out=None, stream=None):
+              path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None):
         """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32."""
         import torch
         if isinstance(lib_ids, int):

@@ -5,7 +5,8 @@ The pre-score is an approximation (BF16 operands, FP32 accumulation); what is pi
 - each candidate's pre-score lies within a BF16-level tolerance of the oracle's exact Q for
   that template, and no excluded template beats the candidates by more than that;
 - after the FP32 rescore every returned score equals the oracle's Q (rel 1e-5);
-- the top-1 template and shift agree with the oracle on at least 99.5 % of patterns.
+- the top-1 template and shift agree with the oracle (or tie with its best Q within 1e-5)
+  on at least 99.5 % of patterns.
 """
 import numpy as np
 import pytest
@@ -17,87 +18,68 @@ from tests._compare import REL, tol
 
 pytestmark = pytest.mark.gpu
 
-PRE_TOL = 0.03      # |Q~ - Q| <= PRE_TOL * Q_top1 (BF16 G and basis: ~2^-8 relative per term)
+PRE_TOL = 0.01      # |Q~ - Q| <= PRE_TOL * Q_top1 (BF16 G and basis: ~2^-8 relative per term)
 
 
-@pytest.fixture(scope="module")
-def ctx():
-    import torch
-    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
-    from paper_2111_07347_gb300 import build
-    build.build()
-    c = tmgb.Context(0)
-    yield c
-    c.check()
-    c.close()
-
-
-def _t(a):
-    import torch
-    if a.dtype == np.uint16:
-        return torch.from_numpy(a.view(np.int16)).cuda().view(torch.uint16)
-    return torch.from_numpy(a).cuda()
-
-
-def _check_prescore(ctx, ts, frames, n_r, n_theta, kc=64, fraction=1.0):
+def _check_prescore(ctx, ts, frames, n_r, n_theta, kcs=(64, 256), fraction=1.0):
+    """Pre-score of every template vs the oracle's exact Q; returns (worst error / Q_top,
+    {kc: fraction of patterns whose kc best pre-scores contain a template attaining the
+    oracle's best Q within the 1e-5 tie window})."""
     lib = O.prepare_library(ts, n_r, n_theta)
     lid = ctx.load_library(ts, n_r, n_theta)
     polar, norm, radial = ctx.polar_transform(_t(frames), n_r, n_theta)
-    cand, pre = ctx.prescore(lid, polar, norm, radial, fraction, kc)
+    pre = ctx.prescore(lid, polar, norm, radial, fraction)
     ctx.check()
-    cand, pre = cand.cpu().numpy(), pre.cpu().numpy().astype(np.float64)
+    pre = pre.cpu().numpy().astype(np.float64)
     P = O.polar(frames, n_r, n_theta)
-    act = None
+    act = np.ones((frames.shape[0], lib.K), bool)
     if fraction < 1.0:
         act, _ = O.prefilter(P, lib, fraction)
     q, s = O.scores(P, lib, act)
-    worst, recall = 0.0, 0
+    worst = 0.0
+    rec = {kc: 0 for kc in kcs}
+    ks = np.arange(lib.K)
     for p in range(frames.shape[0]):
-        elig = np.isfinite(q[p])
-        c = cand[p]
-        v = c >= 0
-        nv = int(v.sum())
-        assert nv == min(kc, int(elig.sum()))
-        assert len(set(c[v].tolist())) == nv
-        assert np.all(elig[c[v]])
-        assert np.all(np.diff(pre[p, v]) <= 0)
-        q_top = q[p][elig].max()
-        err = np.abs(pre[p, v] - q[p, c[v]])
+        scored = ~np.isnan(pre[p])
+        # the GPU's pre-filter may differ from the oracle's only at threshold near-ties
+        assert scored.sum() == act[p].sum()
+        both = scored & act[p]
+        assert both.sum() >= act[p].sum() - 2
+        q_top = q[p][act[p]].max()
+        err = np.abs(pre[p][both] - q[p][both])
         worst = max(worst, float(err.max() / max(abs(q_top), 1e-30)))
         assert np.all(err <= PRE_TOL * abs(q_top)), (p, err.max(), q_top)
-        # nothing left out scores clearly above the weakest candidate
-        out = elig.copy()
-        out[c[v]] = False
-        if out.any() and nv == kc:
-            assert q[p][out].max() <= pre[p, v][-1] + 2 * PRE_TOL * abs(q_top)
-        recall += int(np.argmax(np.where(elig, q[p], -np.inf)) in set(c[v].tolist()))
+        order = np.lexsort((ks, -np.where(scored, pre[p], -np.inf)))
+        qv = np.where(act[p], q[p], -np.inf)
+        for kc in kcs:
+            rec[kc] += int(qv[order[:kc]].max() >= q_top - 1e-5 * abs(q_top))
     ctx.unload_library(lid)
-    return worst, recall / frames.shape[0]
+    return worst, {kc: v / frames.shape[0] for kc, v in rec.items()}
 
 
 def test_prescore_tiny(ctx):
     ts, scan, prm = synth.tiny_workload(n_side=6)
-    worst, recall = _check_prescore(ctx, ts, scan.frames, 60, 180, kc=32)
-    assert recall >= 0.99, recall
+    worst, rec = _check_prescore(ctx, ts, scan.frames, 60, 180, kcs=(32,))
+    assert rec[32] >= 0.99, rec
 
 
 def test_prescore_fcc_and_prefilter(ctx):
     ts, scan, prm = synth.single_phase_workload(n_patterns=48)
-    worst, recall = _check_prescore(ctx, ts, scan.frames, 128, 360, kc=64)
-    assert recall >= 0.97, recall
-    worst, recall = _check_prescore(ctx, ts, scan.frames, 128, 360, kc=64, fraction=0.5)
-    assert recall >= 0.97, recall
+    worst, rec = _check_prescore(ctx, ts, scan.frames, 128, 360, kcs=(256,), fraction=0.5)
+    assert rec[256] >= 0.97, rec
+    worst, rec = _check_prescore(ctx, ts, scan.frames, 128, 360, kcs=(1024,))
+    assert rec[1024] >= 0.95, rec
 
 
 def test_prescore_tetragonal_many_radii(ctx):
     ts = synth.kinematic_library("tetragonal", step_deg=2.0)
     rng = synth.make_rng(3)
     scan = synth.render_scan(rng, ts, 24, 256, 256, n_theta=360)
-    worst, recall = _check_prescore(ctx, ts, scan.frames, 128, 360, kc=64)
-    assert recall >= 0.95, recall
+    worst, rec = _check_prescore(ctx, ts, scan.frames, 128, 360, kcs=(64,))
+    assert rec[64] >= 0.95, rec
 
 
-def _bf16_hits_check(ctx, ts, frames, n_r, n_theta, N=5, kc=64, prefilter=1.0, mirror=None):
+def _bf16_hits_check(ctx, ts, frames, n_r, n_theta, N=5, kc=256, prefilter=1.0, mirror=None):
     lib = O.prepare_library(ts, n_r, n_theta, mirror=mirror)
     lid = ctx.load_library(ts, n_r, n_theta, mirror=mirror)
     out = ctx.index(_t(frames), lid, top_n=N, prefilter=prefilter, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=kc)
@@ -134,7 +116,7 @@ def test_index_bf16_tiny(ctx):
 
 def test_index_bf16_fcc_prefilter(ctx):
     ts, scan, prm = synth.single_phase_workload(n_patterns=128)
-    rate = _bf16_hits_check(ctx, ts, scan.frames, 128, 360, N=5, kc=64, prefilter=0.5)
+    rate = _bf16_hits_check(ctx, ts, scan.frames, 128, 360, N=5, kc=256, prefilter=0.5)
     assert rate >= 0.98, rate
 
 
@@ -145,7 +127,7 @@ def test_index_bf16_multi_library_equals_single(ctx):
     scan = synth.render_scan(rng, b, 16, 256, 256, n_theta=360)
     la, lb = ctx.load_library(a, 128, 360), ctx.load_library(b, 128, 360)
     f = _t(scan.frames)
-    kw = dict(top_n=5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=48)
+    kw = dict(top_n=5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=128)
     both = tmgb.hits_to_numpy(ctx.index(f, [la, lb], **kw))
     ha = tmgb.hits_to_numpy(ctx.index(f, la, **kw))[0]
     hb = tmgb.hits_to_numpy(ctx.index(f, lb, **kw))[0]
@@ -173,7 +155,7 @@ def test_index_bf16_single_phase_full_size_sampled(ctx):
     ts, scan, prm = synth.single_phase_workload()
     lib = O.prepare_library(ts, 128, 360)
     lid = ctx.load_library(ts, 128, 360)
-    out = ctx.index(_t(scan.frames), lid, top_n=5, prefilter=0.5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=64)
+    out = ctx.index(_t(scan.frames), lid, top_n=5, prefilter=0.5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=256)
     ctx.check()
     h = tmgb.hits_to_numpy(out)[0]
     pick = np.sort(np.random.default_rng(1).choice(scan.frames.shape[0], 32, replace=False))
