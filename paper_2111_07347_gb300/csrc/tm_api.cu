@@ -577,6 +577,23 @@ Library* find_lib(tm_ctx* ctx, int id) {
 
 }  // namespace
 
+namespace tmgb {
+int library_view(tm_ctx* ctx, int lib_id, int* device, int* num_sms, SparseLib* view, int* n_r, int* n_theta,
+                 double* dr) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "library_view: ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Library* L = find_lib(ctx, lib_id);
+    if (!L) return fail(TM_ERR_NOT_FOUND, "no library %d", lib_id);
+    *device = ctx->device;
+    *num_sms = ctx->num_sms;
+    *view = sparse_view(L);
+    *n_r = L->n_r;
+    *n_theta = L->n_theta;
+    *dr = L->dr;
+    return TM_OK;
+}
+}  // namespace tmgb
+
 // ====================================================================== C ABI
 
 extern "C" {

@@ -14,6 +14,7 @@ namespace tmgb {
 // Message for tm_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
+
 // ------------------------------------------------------------------ device library views
 // Sparse templates in CSR.  The sparse kernel keeps only the library's distinct spot
 // radii (radii[0..n_rad)) as rows of its shared-memory polar image, row pitch
@@ -119,5 +120,10 @@ cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_
                        int num_sms, cudaStream_t st);
 cudaError_t launch_compact(const uint32_t* mask, int64_t n, int K, const int32_t* order, int keep,
                            int32_t* list, cudaStream_t st);
+
+// Read-only view of a loaded library for entry points defined outside the host API file:
+// device, SM count, the sparse view and the library's polar grid.  Returns a TM_* status.
+int library_view(tm_ctx* ctx, int lib_id, int* device, int* num_sms, SparseLib* view, int* n_r,
+                 int* n_theta, double* dr);
 
 }  // namespace tmgb
