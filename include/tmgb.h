@@ -108,8 +108,17 @@ typedef struct tm_index_params {
     int32_t top_n;                /* N >= 1 results per pattern and library              */
     int32_t path;                 /* TM_PATH_FP32_SPARSE or TM_PATH_BF16_RESCORE         */
     int32_t rescore_k;            /* BF16 path: candidates rescored exactly (default 256) */
-    int32_t reserved;
+    int32_t reserved;             /* TM_INDEX_* flags                                     */
 } tm_index_params;
+
+/* tm_index_params.reserved flag: replay the call as a CUDA graph.  The first call with a
+ * given set of arguments (pointers, sizes, parameters, libraries, stream) runs normally,
+ * the second is captured into a graph on the caller's stream and launched, later identical
+ * calls launch the graph.  Needs a created stream (not the legacy default stream, where
+ * the call simply runs normally); a graph is rebuilt when the context's scratch buffers
+ * were reallocated, and dropped when a library is unloaded.  Not used while stage timing
+ * is on. */
+#define TM_INDEX_GRAPH 1
 
 /* One result row.  Rows of a pattern are ordered by (score desc, template asc); when
  * fewer than N templates take part the tail rows have template_index = -1 and
@@ -196,6 +205,16 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
  * fraction < 1).  n_theta must be even and <= 376 (else TM_ERR_UNSUPPORTED). */
 int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev,
                 const float* radial_dev, int64_t n, double fraction, float* score_dev, void* stream);
+
+/* Autotune the FP32 sparse kernel for a set of libraries: time its block sizes (128,
+ * 256, 512 threads; 256 is the default) on the first min(n, 2048) frames with these
+ * parameters, keep the fastest for later calls on libraries of the same shapes (template
+ * count, spot count, radii, n_theta) and top_n, and, when the environment variable
+ * TMGB_TUNE_CACHE names a file, append "key threads ms" to it; contexts created later read
+ * that file back.  Synchronous.  *best_threads (nullable) receives the choice. */
+int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype,
+                int64_t n, int32_t H, int32_t W, const int32_t* lib_ids, int32_t n_libs,
+                int32_t* best_threads, void* stream);
 
 /* Wait for `stream`, then report whether a kernel of this context stopped on a bounded
  * wait since the last check (TM_ERR_TIMEOUT; the error word is cleared). */

@@ -35,40 +35,62 @@ template <typename T>
 __global__ void __launch_bounds__(1024)
 polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
              const int32_t* __restrict__ txy, const float4* __restrict__ tw, Gamma gm, int n_r, int n_theta,
-             float* __restrict__ polar, float* __restrict__ pnorm, float* __restrict__ radial) {
+             const uint8_t* __restrict__ keep_row, float* __restrict__ polar, float* __restrict__ pnorm,
+             float* __restrict__ radial) {
     extern __shared__ float smem[];
     const int nw = blockDim.x >> 5;
     float* part = smem;                         // [n_r][nw] row partial sums
     float* red = smem + (size_t)n_r * nw;       // [blockDim] norm partials
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int U = 4;                        // rows in flight per thread
 
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
         const T* frame = frames + (size_t)p * H * W;
         float* out = polar + (size_t)p * n_r * n_theta;
         float s2 = 0.0f, c2 = 0.0f;             // Kahan sum of P'^2 for this thread
-        for (int j = 0; j < n_r; ++j) {
-            float rowsum = 0.0f;
+        for (int j0 = 0; j0 < n_r; j0 += U) {
+            float rowsum[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) rowsum[u] = 0.0f;
             for (int k = threadIdx.x; k < n_theta; k += blockDim.x) {
-                const int idx = j * n_theta + k;
-                const int xy = __ldg(txy + idx);
-                const int x0 = (int)(int16_t)(xy & 0xffff);
-                const int y0 = xy >> 16;
-                const float4 f = __ldg(tw + idx);           // fx, 1 - fx, fy, 1 - fy
-                const float v00 = tap(frame, H, W, x0, y0, gm);
-                const float v10 = tap(frame, H, W, x0 + 1, y0, gm);
-                const float v01 = tap(frame, H, W, x0, y0 + 1, gm);
-                const float v11 = tap(frame, H, W, x0 + 1, y0 + 1, gm);
-                const float v = f.w * (f.y * v00 + f.x * v10) + f.z * (f.y * v01 + f.x * v11);
-                out[idx] = v;
-                const float y = fmaf(v, v, -c2);
-                const float t = s2 + y;
-                c2 = (t - s2) - y;
-                s2 = t;
-                rowsum += v;
+                float v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u;
+                    v[u] = 0.0f;
+                    if (j < n_r) {
+                        const int idx = j * n_theta + k;
+                        const int xy = __ldg(txy + idx);
+                        const int x0 = (int)(int16_t)(xy & 0xffff);
+                        const int y0 = xy >> 16;
+                        const float4 f = __ldg(tw + idx);           // fx, 1 - fx, fy, 1 - fy
+                        const float v00 = tap(frame, H, W, x0, y0, gm);
+                        const float v10 = tap(frame, H, W, x0 + 1, y0, gm);
+                        const float v01 = tap(frame, H, W, x0, y0 + 1, gm);
+                        const float v11 = tap(frame, H, W, x0 + 1, y0 + 1, gm);
+                        v[u] = f.w * (f.y * v00 + f.x * v10) + f.z * (f.y * v01 + f.x * v11);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + u;
+                    if (j < n_r) {
+                        if (!keep_row || keep_row[j]) out[j * n_theta + k] = v[u];
+                        const float y = fmaf(v[u], v[u], -c2);
+                        const float t = s2 + y;
+                        c2 = (t - s2) - y;
+                        s2 = t;
+                        rowsum[u] += v[u];
+                    }
+                }
             }
-            #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
-            if (lane == 0) part[j * nw + warp] = rowsum;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float r = rowsum[u];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+                if (lane == 0 && j0 + u < n_r) part[(j0 + u) * nw + warp] = r;
+            }
         }
         red[threadIdx.x] = s2;
         __syncthreads();
@@ -95,7 +117,7 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st) {
+                         cudaStream_t st, const uint8_t* keep_row) {
     if (n <= 0) return cudaSuccess;
     Gamma gm;
     gm.mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
@@ -116,9 +138,9 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
     const int64_t grid64 = n < 65535 * 16 ? n : 65535 * 16;
     const int grid = (int)grid64;
     if (dtype == TM_DTYPE_U16)
-        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, polar, pnorm, radial);
+        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial);
     else
-        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, polar, pnorm, radial);
+        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial);
     return cudaGetLastError();
 }
 

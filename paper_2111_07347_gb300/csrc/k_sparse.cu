@@ -35,8 +35,8 @@ __host__ __device__ constexpr int round_nb(int nb) {
     return nb <= 4 ? nb : nb <= 6 ? 6 : nb <= 8 ? 8 : nb <= 12 ? 12 : nb <= 16 ? 16 : nb <= 24 ? 24 : 32;
 }
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kMaxThreads = 512;            // block sizes: 128, 256 (default) or 512
+constexpr int kMaxWarps = kMaxThreads / 32;
 
 }  // namespace
 
@@ -118,11 +118,12 @@ __device__ __forceinline__ float score_dispatch(const float* sP, const SparseLib
 }
 
 template <int NBMAX>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kMaxThreads)
 sparse_kernel(const SparseCall c) {
     extern __shared__ __align__(16) float smem[];
     const int n_theta = c.n_theta, pitch = c.pitch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kWarps = blockDim.x >> 5;
     const int N = c.top_n;
     float* sP = smem;                                        // [max_rad][pitch]
     float* lq = sP + (size_t)c.max_rad * pitch;              // [kWarps][N]
@@ -270,17 +271,18 @@ sparse_kernel(const SparseCall c) {
 
 template <int NBMAX>
 cudaError_t launch_nb(const SparseCall& c, int num_sms, size_t smem, cudaStream_t st) {
+    const int threads = (c.threads == 128 || c.threads == 512) ? c.threads : 256;
     cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX>, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > c.n) grid = c.n;
     e = cudaMemsetAsync(c.pattern_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    sparse_kernel<NBMAX><<<(int)grid, kThreads, smem, st>>>(c);
+    sparse_kernel<NBMAX><<<(int)grid, threads, smem, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -288,7 +290,7 @@ cudaError_t launch_nb(const SparseCall& c, int num_sms, size_t smem, cudaStream_
 
 size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n) {
     if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
-    const size_t b = (size_t)max_rad * sparse_pitch(n_theta) * 4 + (size_t)kWarps * top_n * 12 + kWarps * 4 + 16;
+    const size_t b = (size_t)max_rad * sparse_pitch(n_theta) * 4 + (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16;
     return b <= 232448 ? b : 0;
 }
 

@@ -104,6 +104,7 @@ struct SpectralTables {            // per n_theta: inverse-DFT basis and twiddle
 struct RadiusMap {                 // per set of libraries: union of radii
     int32_t* radii = nullptr;      // [n_rad]
     int32_t* rmap = nullptr;       // [n_r]
+    uint8_t* keep_row = nullptr;   // [n_r]  1 for the polar rows later stages read
     int n_rad = 0;
 };
 
@@ -126,6 +127,20 @@ struct tm_ctx {
     unsigned* d_error = nullptr;   // device error word of the bounded waits
     std::map<int, SpectralTables> spectral;
     std::map<std::string, RadiusMap> radius_maps;
+    // CUDA graphs of whole-path calls (TM_INDEX_GRAPH)
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        uint64_t ws_gen = 0;
+        bool seen = false;
+        int64_t launches = 0, corr = 0, scored = 0;
+    };
+    std::map<std::string, GraphEntry> graphs;
+    uint64_t ws_gen = 1;           // bumped whenever a workspace buffer is reallocated
+    bool capturing = false;
+    // autotuned sparse-kernel block size per library signature (tm_autotune)
+    std::map<std::string, int> tuned;
+    int tune_override = 0;
+    std::string tune_file;
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -162,6 +177,8 @@ int workspace(tm_ctx* ctx, cudaStream_t st, const std::string& name, size_t byte
     snprintf(key, sizeof key, "@%llx", (unsigned long long)(uintptr_t)st);
     Buffer& b = ctx->ws[name + key];
     if (b.bytes < bytes) {
+        if (ctx->capturing) return fail(TM_ERR_CUDA, "workspace growth during graph capture");
+        ctx->ws_gen++;
         if (b.p) {
             cudaDeviceSynchronize();
             dev_free(ctx, b.p, b.bytes);
@@ -194,7 +211,7 @@ struct StageTimer {
         return e;
     }
     StageTimer(tm_ctx* c, int s, cudaStream_t stream) : ctx(c), stage(s), st(stream) {
-        if (!ctx->profiling) return;
+        if (!ctx->profiling || ctx->capturing) return;
         a = take(ctx);
         b = take(ctx);
         if (a && b) cudaEventRecord(a, st);
@@ -529,17 +546,32 @@ int radius_map(tm_ctx* ctx, Library* const* libs, const int32_t* ids, int n_libs
         if (u.empty()) u.push_back(0);
         std::vector<int32_t> rmap(n_r, -1);
         for (size_t i = 0; i < u.size(); ++i) rmap[u[i]] = (int32_t)i;
+        std::vector<uint8_t> keep(n_r, 0);
+        for (int32_t r : u) keep[r] = 1;
         RadiusMap m;
         m.n_rad = (int)u.size();
         int rc = dev_alloc(ctx, (void**)&m.radii, u.size() * 4, "radius list");
         if (!rc) rc = dev_alloc(ctx, (void**)&m.rmap, rmap.size() * 4, "radius map");
+        if (!rc) rc = dev_alloc(ctx, (void**)&m.keep_row, keep.size(), "row mask");
         if (rc) return rc;
         TM_CUDA(cudaMemcpy(m.radii, u.data(), u.size() * 4, cudaMemcpyHostToDevice), "radius list");
         TM_CUDA(cudaMemcpy(m.rmap, rmap.data(), rmap.size() * 4, cudaMemcpyHostToDevice), "radius map");
+        TM_CUDA(cudaMemcpy(m.keep_row, keep.data(), keep.size(), cudaMemcpyHostToDevice), "row mask");
         it = ctx->radius_maps.emplace(key, m).first;
     }
     *out = it->second;
     return TM_OK;
+}
+
+// Signature of a set of libraries for the autotuner: shapes, not ids, so that a tuning
+// cache written by one process applies in the next.
+std::string tune_key(Library* const* libs, int n_libs, int top_n) {
+    std::string k = "sparse";
+    for (int i = 0; i < n_libs; ++i) {
+        k += "|" + std::to_string(libs[i]->K) + "/" + std::to_string(libs[i]->r.size()) + "/" +
+             std::to_string(libs[i]->radii.size()) + "/" + std::to_string(libs[i]->n_theta);
+    }
+    return k + "|N" + std::to_string(top_n);
 }
 
 tmgb::DenseLib dense_view(const Library* L) {
@@ -631,6 +663,16 @@ int tm_create(int device, size_t hbm_budget_bytes, tm_ctx** out) {
     ctx->num_sms = prop.multiProcessorCount;
     TM_CUDA(cudaEventCreateWithFlags(&ctx->ws_event, cudaEventDisableTiming), "tm_create: cudaEventCreate");
     TM_CUDA(cudaMalloc(&ctx->d_error, sizeof(unsigned)), "tm_create: error word");
+    if (const char* f = getenv("TMGB_TUNE_CACHE")) {
+        ctx->tune_file = f;
+        if (FILE* fh = fopen(f, "r")) {
+            char key[512];
+            int threads = 0;
+            double ms = 0;
+            while (fscanf(fh, "%511s %d %lf", key, &threads, &ms) == 3) ctx->tuned[key] = threads;
+            fclose(fh);
+        }
+    }
     TM_CUDA(cudaMemset(ctx->d_error, 0, sizeof(unsigned)), "tm_create: error word");
     *out = ctx.release();
     g_err.clear();
@@ -694,8 +736,11 @@ void tm_destroy(tm_ctx* ctx) {
         for (auto& kv : ctx->radius_maps) {
             cudaFree(kv.second.radii);
             cudaFree(kv.second.rmap);
+            cudaFree(kv.second.keep_row);
         }
         if (ctx->d_error) cudaFree(ctx->d_error);
+        for (auto& kv : ctx->graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (ctx->ws_event) cudaEventDestroy(ctx->ws_event);
     }
     delete ctx;
@@ -738,6 +783,9 @@ int tm_unload_library(tm_ctx* ctx, int lib_id) {
     auto it = ctx->libs.find(lib_id);
     if (it == ctx->libs.end()) return fail(TM_ERR_NOT_FOUND, "tm_unload_library: no library %d", lib_id);
     TM_CUDA(cudaDeviceSynchronize(), "tm_unload_library: wait for pending work");
+    for (auto& kv : ctx->graphs)                       // graphs may reference the library
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graphs.clear();
     free_library(ctx, it->second.get());
     ctx->libs.erase(it);
     return TM_OK;
@@ -934,12 +982,13 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     const int n_freq = n_theta / 2 + 1;
     SpectralTables spec;
     RadiusMap rmap;
+    rc = radius_map(ctx, libs, lib_ids, n_libs, n_r, &rmap);
+    if (rc) return rc;
     if (bf16) {
         if (!tmgb::dense_supported(n_theta))
             return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: the BF16 path needs an even n_theta <= 376 (got %d)",
                         n_theta);
         rc = spectral_tables(ctx, n_theta, &spec);
-        if (!rc) rc = radius_map(ctx, libs, lib_ids, n_libs, n_r, &rmap);
         if (rc) return rc;
         if (tmgb::dense_smem_bytes(n_theta, n_r, rmap.n_rad, n_freq) > 232448)
             return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: %d distinct radii exceed the BF16 kernel's shared memory",
@@ -988,116 +1037,243 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
         if (rc) return rc;
     }
     const size_t esz = dtype == TM_DTYPE_U16 ? 2 : 4;
+    int sparse_threads = ctx->tune_override;
+    if (!sparse_threads) {
+        auto tt = ctx->tuned.find(tune_key(libs, n_libs, N));
+        if (tt != ctx->tuned.end()) sparse_threads = tt->second;
+    }
     int64_t launches = 0, corr = 0, scored = 0;
-    for (int64_t c0 = 0; c0 < n; c0 += chunk) {
-        const int64_t m = std::min(chunk, n - c0);
-        const void* fr = (const char*)frames_dev + (size_t)c0 * H * W * esz;
-        {
-            StageTimer tmr(ctx, TM_STAGE_POLAR, st);
-            TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                                       polar, pnorm, radial, st), "tm_index_patterns: polar");
-        }
-        ++launches;
-        if (pre) {
-            StageTimer tmr(ctx, TM_STAGE_PREFILTER, st);
-            TM_CUDA(tmgb::launch_radial_norm(radial, m, n_r, rn, st), "tm_index_patterns: radial norm");
-            ++launches;
-            for (int i = 0; i < n_libs; ++i) {
-                Library* L = libs[i];
-                tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
-                TM_CUDA(tmgb::launch_prefilter_scores(radial, rn, m, n_r, rl, score[i], st), "tm_index_patterns: scores");
-                TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)L->K, keep[i], mask[i], st),
-                        "tm_index_patterns: select");
-                launches += 2;
-                if (bf16) {
-                    TM_CUDA(tmgb::launch_compact(mask[i], m, (int)L->K, L->d_order, keep[i], list[i], st),
-                            "tm_index_patterns: compact");
-                    ++launches;
-                }
-            }
-        }
-        tmgb::SparseCall c{};
-        c.polar = polar;
-        c.pnorm = pnorm;
-        c.n = m;
-        c.n_r = n_r;
-        c.n_theta = n_theta;
-        c.pitch = tmgb::sparse_pitch(n_theta);
-        c.max_rad = max_rad;
-        c.pattern_counter = pcount;
-        c.n_libs = n_libs;
-        for (int i = 0; i < n_libs; ++i) {
-            c.lib[i] = sparse_view(libs[i]);
-            if (pre || bf16) c.mask[i] = mask[i];
-        }
-        c.hits = out_dev + (size_t)c0 * N;
-        c.hits_lib_stride = n * N;
-        c.top_n = N;
-        if (bf16) {
+    auto enqueue = [&]() -> int {
+        for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+            const int64_t m = std::min(chunk, n - c0);
+            const void* fr = (const char*)frames_dev + (size_t)c0 * H * W * esz;
             {
-                StageTimer tmr(ctx, TM_STAGE_DFT, st);
-                TM_CUDA(tmgb::launch_dft(polar, pnorm, m, n_r, n_theta, rmap.radii, rmap.n_rad, n_freq, spec.twiddle,
-                                         phat, ctx->num_sms, st), "tm_index_patterns: dft");
+                StageTimer tmr(ctx, TM_STAGE_POLAR, st);
+                TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
+                                           polar, pnorm, radial, st, rmap.keep_row), "tm_index_patterns: polar");
             }
             ++launches;
-            tmgb::DenseCall dc{};
-            dc.phat = phat;
-            dc.n = m;
-            dc.n_theta = n_theta;
-            dc.n_r = n_r;
-            dc.n_rad = rmap.n_rad;
-            dc.n_freq = n_freq;
-            dc.rmap = rmap.rmap;
-            dc.basis = spec.basis;
-            dc.twiddle = spec.twiddle;
-            dc.n_libs = n_libs;
-            for (int i = 0; i < n_libs; ++i) {
-                dc.lib[i] = dense_view(libs[i]);
-                dc.list[i] = pre ? list[i] : nullptr;
-                dc.count[i] = keep[i];
-                dc.pre[i] = score[i];
-                // templates not scored read as -NaN, the smallest key of the select
-                TM_CUDA(cudaMemsetAsync(score[i], 0xFF, (size_t)m * libs[i]->K * 4, st), "tm_index_patterns: memset");
-            }
-            dc.error = ctx->d_error;
-            {
-                StageTimer tmr(ctx, TM_STAGE_DENSE, st);
-                TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_index_patterns: dense");
-            }
-            ++launches;
-            {
-                StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
+            if (pre) {
+                StageTimer tmr(ctx, TM_STAGE_PREFILTER, st);
+                TM_CUDA(tmgb::launch_radial_norm(radial, m, n_r, rn, st), "tm_index_patterns: radial norm");
+                ++launches;
                 for (int i = 0; i < n_libs; ++i) {
-                    const int kci = std::min(kc, keep[i]);
-                    TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)libs[i]->K, kci, mask[i], st),
-                            "tm_index_patterns: candidates");
-                    ++launches;
+                    Library* L = libs[i];
+                    tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
+                    TM_CUDA(tmgb::launch_prefilter_scores(radial, rn, m, n_r, rl, score[i], st), "tm_index_patterns: scores");
+                    TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)L->K, keep[i], mask[i], st),
+                            "tm_index_patterns: select");
+                    launches += 2;
+                    if (bf16) {
+                        TM_CUDA(tmgb::launch_compact(mask[i], m, (int)L->K, L->d_order, keep[i], list[i], st),
+                                "tm_index_patterns: compact");
+                        ++launches;
+                    }
                 }
-                TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: rescore");
             }
-            ++launches;
+            tmgb::SparseCall c{};
+            c.polar = polar;
+            c.pnorm = pnorm;
+            c.n = m;
+            c.n_r = n_r;
+            c.n_theta = n_theta;
+            c.pitch = tmgb::sparse_pitch(n_theta);
+            c.max_rad = max_rad;
+            c.pattern_counter = pcount;
+            c.n_libs = n_libs;
             for (int i = 0; i < n_libs; ++i) {
-                corr += m * ((int64_t)keep[i] + std::min<int64_t>(kc, keep[i])) * n_theta;
-                scored += m * std::min<int64_t>(kc, keep[i]);
+                c.lib[i] = sparse_view(libs[i]);
+                if (pre || bf16) c.mask[i] = mask[i];
             }
-        } else {
-            {
-                StageTimer tmr(ctx, TM_STAGE_SPARSE, st);
-                TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: sparse");
+            c.hits = out_dev + (size_t)c0 * N;
+            c.hits_lib_stride = n * N;
+            c.top_n = N;
+            if (bf16) {
+                {
+                    StageTimer tmr(ctx, TM_STAGE_DFT, st);
+                    TM_CUDA(tmgb::launch_dft(polar, pnorm, m, n_r, n_theta, rmap.radii, rmap.n_rad, n_freq, spec.twiddle,
+                                             phat, ctx->num_sms, st), "tm_index_patterns: dft");
+                }
+                ++launches;
+                tmgb::DenseCall dc{};
+                dc.phat = phat;
+                dc.n = m;
+                dc.n_theta = n_theta;
+                dc.n_r = n_r;
+                dc.n_rad = rmap.n_rad;
+                dc.n_freq = n_freq;
+                dc.rmap = rmap.rmap;
+                dc.basis = spec.basis;
+                dc.twiddle = spec.twiddle;
+                dc.n_libs = n_libs;
+                for (int i = 0; i < n_libs; ++i) {
+                    dc.lib[i] = dense_view(libs[i]);
+                    dc.list[i] = pre ? list[i] : nullptr;
+                    dc.count[i] = keep[i];
+                    dc.pre[i] = score[i];
+                    // templates not scored read as -NaN, the smallest key of the select
+                    TM_CUDA(cudaMemsetAsync(score[i], 0xFF, (size_t)m * libs[i]->K * 4, st), "tm_index_patterns: memset");
+                }
+                dc.error = ctx->d_error;
+                {
+                    StageTimer tmr(ctx, TM_STAGE_DENSE, st);
+                    TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_index_patterns: dense");
+                }
+                ++launches;
+                {
+                    StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
+                    for (int i = 0; i < n_libs; ++i) {
+                        const int kci = std::min(kc, keep[i]);
+                        TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)libs[i]->K, kci, mask[i], st),
+                                "tm_index_patterns: candidates");
+                        ++launches;
+                    }
+                    TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: rescore");
+                }
+                ++launches;
+                for (int i = 0; i < n_libs; ++i) {
+                    corr += m * ((int64_t)keep[i] + std::min<int64_t>(kc, keep[i])) * n_theta;
+                    scored += m * std::min<int64_t>(kc, keep[i]);
+                }
+            } else {
+                {
+                    StageTimer tmr(ctx, TM_STAGE_SPARSE, st);
+                    TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: sparse");
+                }
+                ++launches;
+                for (int i = 0; i < n_libs; ++i) {
+                    corr += m * (int64_t)keep[i] * n_theta;
+                    scored += m * keep[i];
+                }
             }
-            ++launches;
-            for (int i = 0; i < n_libs; ++i) {
-                corr += m * (int64_t)keep[i] * n_theta;
-                scored += m * keep[i];
+        }
+        return TM_OK;
+    };
+    auto report = [&]() {
+        if (stats) {
+            stats->patterns = n;
+            stats->correlations = corr;
+            stats->templates_scored = scored;
+            stats->launches = launches;
+        }
+    };
+    // CUDA graph: the second identical call on a created stream is captured, later ones replay
+    if ((params->reserved & TM_INDEX_GRAPH) && st != nullptr && !ctx->profiling) {
+        char key[512];
+        int off = snprintf(key, sizeof key, "%p|%p|%p|%d|%lld|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|", st,
+                           frames_dev, (void*)out_dev, dtype, (long long)n, H, W, params->gamma, params->subtract,
+                           params->cx, params->cy, params->prefilter_fraction, params->top_n, params->path,
+                           params->rescore_k);
+        for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);
+        tm_ctx::GraphEntry& ge = ctx->graphs[key];
+        if (ge.exec && ge.ws_gen == ctx->ws_gen) {
+            TM_CUDA(cudaGraphLaunch(ge.exec, st), "tm_index_patterns: graph launch");
+            launches = ge.launches;
+            corr = ge.corr;
+            scored = ge.scored;
+            report();
+            return TM_OK;
+        }
+        if (ge.seen) {
+            if (ge.exec) {
+                cudaGraphExecDestroy(ge.exec);
+                ge.exec = nullptr;
+            }
+            TM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "tm_index_patterns: begin capture");
+            ctx->capturing = true;
+            const int rc2 = enqueue();
+            ctx->capturing = false;
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (rc2 || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc2 ? rc2 : cuda_fail(e, "tm_index_patterns: end capture");
+            }
+            const cudaError_t e2 = cudaGraphInstantiate(&ge.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e2 != cudaSuccess) {
+                ge.exec = nullptr;
+                return cuda_fail(e2, "tm_index_patterns: graph instantiate");
+            }
+            ge.ws_gen = ctx->ws_gen;
+            ge.launches = launches;
+            ge.corr = corr;
+            ge.scored = scored;
+            TM_CUDA(cudaGraphLaunch(ge.exec, st), "tm_index_patterns: graph launch");
+            report();
+            return TM_OK;
+        }
+        ge.seen = true;
+    }
+    rc = enqueue();
+    if (rc) return rc;
+    report();
+    return TM_OK;
+}
+
+int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype, int64_t n,
+                int32_t H, int32_t W, const int32_t* lib_ids, int32_t n_libs, int32_t* best_threads, void* stream) {
+    if (!ctx || !params || !lib_ids || n_libs < 1 || n_libs > TM_MAX_LIBS || n < 1)
+        return fail(TM_ERR_INVALID_ARG, "tm_autotune: bad arguments");
+    std::string key;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        Library* libs[TM_MAX_LIBS];
+        for (int i = 0; i < n_libs; ++i) {
+            libs[i] = find_lib(ctx, lib_ids[i]);
+            if (!libs[i]) return fail(TM_ERR_NOT_FOUND, "tm_autotune: no library %d", lib_ids[i]);
+        }
+        key = tune_key(libs, n_libs, params->top_n);
+    }
+    const int64_t m = std::min<int64_t>(n, 2048);
+    const int64_t N = params->top_n;
+    tm_hit* out = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard g(ctx->device);
+        int rc = workspace(ctx, (cudaStream_t)stream, "tune_out", (size_t)n_libs * m * N * sizeof(tm_hit), (void**)&out);
+        if (rc) return rc;
+    }
+    tm_index_params p = *params;
+    p.path = TM_PATH_FP32_SPARSE;
+    p.reserved = 0;
+    const int cand[3] = {128, 256, 512};
+    int best = 256;
+    double best_ms = 1e30;
+    for (int t : cand) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->tune_override = t;
+        }
+        int rc = tm_index_patterns(ctx, &p, frames_dev, dtype, m, H, W, nullptr, lib_ids, n_libs, out, nullptr, stream);
+        if (!rc) rc = tm_profile_enable(ctx, 1);
+        for (int r = 0; r < 3 && !rc; ++r)
+            rc = tm_index_patterns(ctx, &p, frames_dev, dtype, m, H, W, nullptr, lib_ids, n_libs, out, nullptr, stream);
+        tm_profile prof;
+        if (!rc) rc = tm_profile_read(ctx, &prof);
+        tm_profile_enable(ctx, 0);
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->tune_override = 0;
+        }
+        if (rc) return rc;
+        const double ms = prof.ms[TM_STAGE_SPARSE];
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tuned[key] = best;
+        if (!ctx->tune_file.empty()) {
+            if (FILE* fh = fopen(ctx->tune_file.c_str(), "a")) {
+                fprintf(fh, "%s %d %.6f\n", key.c_str(), best, best_ms / 3.0);
+                fclose(fh);
             }
         }
     }
-    if (stats) {
-        stats->patterns = n;
-        stats->correlations = corr;
-        stats->templates_scored = scored;
-        stats->launches = launches;
-    }
+    if (best_threads) *best_threads = best;
     return TM_OK;
 }
 

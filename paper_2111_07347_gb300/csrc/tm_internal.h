@@ -47,10 +47,12 @@ struct PolarTable {            // bilinear taps for one (H, W, n_r, n_theta, dr,
     const float4* w;           // [n_r * n_theta]  (fx, 1 - fx, fy, 1 - fy), each rounded from FP64
 };
 
+// keep_row [n_r] (nullable): rows whose polar values are stored; the norm and the row
+// sums always cover every row.
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st);
+                         cudaStream_t st, const uint8_t* keep_row = nullptr);
 
 cudaError_t launch_radial_norm(const float* radial, int64_t n, int n_r, float* out,
                                cudaStream_t st);
@@ -78,6 +80,7 @@ struct SparseCall {
     tm_hit* hits;                       // [n_libs][hits_lib_stride] or null
     int64_t hits_lib_stride;            // elements between libraries (>= n * top_n)
     int top_n;
+    int threads;                        // block size: 128, 256 or 512 (0 = 256)
 };
 
 // Shared-memory bytes the sparse kernel needs (0 when unsupported).

@@ -24,6 +24,7 @@ TM_DTYPE_U16, TM_DTYPE_F32 = 0, 1
 TM_COORDS_POLAR, TM_COORDS_XY = 0, 1
 TM_LIB_MIRROR, TM_LIB_UNIT_INTENSITY = 1, 2
 TM_PATH_FP32_SPARSE, TM_PATH_BF16_RESCORE = 0, 1
+TM_INDEX_GRAPH = 1
 
 
 class TmError(RuntimeError):
@@ -118,6 +119,9 @@ _SIGS = {
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
     "tm_prescore": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     "tm_check": (ctypes.c_int, [_P, _P]),
+    "tm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
+                                   ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                   _P]),
     "tm_server_params_default": (None, [ctypes.POINTER(tm_server_params)]),
     "tm_server_create": (ctypes.c_int, [_P, ctypes.POINTER(tm_server_params), ctypes.POINTER(_P)]),
     "tm_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(tm_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -284,6 +288,14 @@ def tm_prescore(ctx, lib_id, polar_ptr, norm_ptr, radial_ptr, n, fraction, score
 
 def tm_check(ctx, stream) -> None:
     _check(library().tm_check(ctx, stream))
+
+
+def tm_autotune(ctx, params, frames_ptr, dtype, n, H, W, lib_ids, stream) -> int:
+    ids = (ctypes.c_int32 * len(lib_ids))(*lib_ids)
+    best = ctypes.c_int32()
+    _check(library().tm_autotune(ctx, ctypes.byref(params), frames_ptr, dtype, n, H, W, ids, len(lib_ids),
+                                 ctypes.byref(best), stream))
+    return best.value
 
 
 def tm_index_patterns(ctx, params, frames_ptr, dtype, n, H, W, centres_ptr, lib_ids, out_ptr, stream) -> dict:
@@ -501,13 +513,24 @@ class Context:
                     None if radial is None else radial.data_ptr(), n, fraction, score.data_ptr(), _stream_ptr(stream))
         return score
 
+    def autotune(self, frames, lib_ids, top_n=5, prefilter=1.0, stream=None) -> int:
+        """Pick the sparse kernel's block size for these libraries by timing; returns it."""
+        if isinstance(lib_ids, int):
+            lib_ids = [lib_ids]
+        n, H, W = frames.shape
+        p = make_params(top_n=top_n, prefilter=prefilter)
+        return tm_autotune(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W, list(lib_ids),
+                           _stream_ptr(stream))
+
     def check(self, stream=None):
         """Synchronise and raise TmError(TM_ERR_TIMEOUT) if a kernel stopped on a bounded wait."""
         tm_check(self.handle, _stream_ptr(stream))
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
-              path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None):
-        """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32."""
+              path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None,
+              graph=False):
+        """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32.
+        graph=True replays repeated identical calls as a CUDA graph (needs a created stream)."""
         import torch
         if isinstance(lib_ids, int):
             lib_ids = [lib_ids]
@@ -515,6 +538,8 @@ class Context:
         if out is None:
             out = torch.empty((len(lib_ids), n, top_n, 5), dtype=torch.int32, device=frames.device)
         p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k)
+        if graph:
+            p.reserved |= TM_INDEX_GRAPH
         self.last_stats = tm_index_patterns(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W, None,
                                             list(lib_ids), out.data_ptr(), _stream_ptr(stream))
         return out

@@ -292,3 +292,38 @@ def test_index_single_phase_full_size_sampled(ctx):
     ref = O.index(scan.frames[pick], lib, N=5)
     compare_hits(h[pick], ref, lib)
     ctx.unload_library(lid)
+
+
+def test_index_graph_replay_equals_direct(ctx, tiny):
+    """With the graph flag on a created stream, the second identical call is captured into a
+    CUDA graph and later calls replay it; every result equals the direct call's."""
+    import torch
+    ts, scan, lib, ref = tiny
+    lid = ctx.load_library(ts, 60, 180)
+    f = _t(scan.frames)
+    direct = _hits(ctx, scan.frames, lid, top_n=5)[0]
+    s = torch.cuda.Stream()
+    out = torch.empty((1, f.shape[0], 5, 5), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(s):
+        for _ in range(4):
+            out.zero_()
+            ctx.index(f, lid, top_n=5, out=out, stream=s, graph=True)
+            s.synchronize()
+            assert np.array_equal(tmgb.hits_to_numpy(out)[0], direct)
+    assert ctx.last_stats["launches"] >= 2
+    ctx.unload_library(lid)
+
+
+def test_autotune_keeps_results(ctx, fcc, tmp_path, monkeypatch):
+    """The autotuner only changes the sparse kernel's block size: results are identical."""
+    ts, scan, lib = fcc
+    monkeypatch.setenv("TMGB_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    c2 = tmgb.Context(0)
+    lid = c2.load_library(ts, 128, 360)
+    before = _hits(c2, scan.frames, lid, top_n=5, prefilter=0.5)
+    best = c2.autotune(_t(scan.frames), lid, top_n=5, prefilter=0.5)
+    assert best in (128, 256, 512)
+    after = _hits(c2, scan.frames, lid, top_n=5, prefilter=0.5)
+    assert np.array_equal(before, after)
+    c2.close()
+    assert (tmp_path / "tune.txt").read_text().split()[1] == str(best)
