@@ -164,18 +164,24 @@ int tm_library_export(tm_ctx* ctx, int lib_id, int64_t* offsets, int32_t* r, int
 /* The host half of tm_load_library without a device: validates the descriptor and puts
  * the templates on the polar grid exactly as tm_load_library does.  Call once with NULL
  * arrays to get the sizes in *info, then again with host buffers as for
- * tm_library_export.  info->device_bytes is 0.  Needs no GPU. */
+ * tm_library_export; packed [n_spots] (nullable) receives each spot's word as the sparse
+ * kernel reads it (bits 0..23: row of the spot's radius among the library's distinct radii
+ * times the row pitch, plus t; bits 24..31: the first shift block that wraps).
+ * info->device_bytes is 0.  Needs no GPU. */
 int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, int64_t* offsets,
-                            int32_t* r, int32_t* t, float* intensity, float* norm, int32_t* order);
+                            int32_t* r, int32_t* t, float* intensity, float* norm, int32_t* order,
+                            int32_t* packed);
 
 /* Stage 1 (Section 2.2, Fig. 2 (a)-(c)): gamma/subtract and bilinear polar resampling.
  * frames_dev [n][H][W] (TM_DTYPE_U16 or TM_DTYPE_F32, row-major, contiguous);
+ * centres_dev [n][2] float (cx, cy) per pattern, finite, or NULL to use params->cx/cy for
+ * every pattern (the direct beam is the origin of the transform, Section 2.2);
  * polar_dev [n][n_r][n_theta] float; norm_dev [n] float = sqrt(sum over the polar image
  * of P^2) (nullable); radial_dev [n][n_r] float = sum over theta (nullable).
  * Uses params->gamma, subtract, cx, cy. */
 int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,
-                       int32_t dtype, int64_t n, int32_t H, int32_t W, int32_t n_r,
-                       int32_t n_theta, double dr, float* polar_dev, float* norm_dev,
+                       int32_t dtype, int64_t n, int32_t H, int32_t W, const float* centres_dev,
+                       int32_t n_r, int32_t n_theta, double dr, float* polar_dev, float* norm_dev,
                        float* radial_dev, void* stream);
 
 /* Stage 2 (Section 2.2, azimuthally integrated pre-filter, Fig. 3): score_k =
@@ -225,8 +231,8 @@ int tm_check(tm_ctx* ctx, void* stream);
  * scores every surviving template exactly in FP32 (Stage 3 with a fused top-N);
  * TM_PATH_BF16_RESCORE takes the rescore_k best by the Stage A7 pre-score (exact radix
  * select, ties to the lower index) and rescores them exactly in FP32 before the top-N.  out_dev [n_libs][n][top_n]
- * tm_hit.  centres_dev must be NULL in this build (per-pattern centres:
- * TM_ERR_UNSUPPORTED).  stats (host, nullable) receives counts for the call. */
+ * tm_hit.  centres_dev [n][2] float per-pattern beam centres (finite) or NULL for
+ * params->cx/cy.  stats (host, nullable) receives counts for the call. */
 int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,
                       int32_t dtype, int64_t n, int32_t H, int32_t W, const float* centres_dev,
                       const int32_t* lib_ids, int32_t n_libs, tm_hit* out_dev,

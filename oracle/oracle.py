@@ -258,9 +258,10 @@ def top_n(q_best: np.ndarray, s_best: np.ndarray, N: int, active: np.ndarray | N
 
 
 def index(frames: np.ndarray, lib: Library, gamma: float = 0.5, subtract: float = 0.0,
-          prefilter_fraction: float = 1.0, N: int = 5, centre=None):
-    """The whole path for a batch of frames; returns a dict of FP64 results."""
-    P = polar(frames, lib.n_r, lib.n_theta, lib.dr, gamma, subtract, centre)
+          prefilter_fraction: float = 1.0, N: int = 5, centre=None, centres: np.ndarray | None = None):
+    """The whole path for a batch of frames; returns a dict of FP64 results.  ``centres``
+    [n][2] gives each pattern's own beam centre."""
+    P = polar(frames, lib.n_r, lib.n_theta, lib.dr, gamma, subtract, centre, centres)
     active = None
     if prefilter_fraction < 1.0:
         active, _ = prefilter(P, lib, prefilter_fraction)

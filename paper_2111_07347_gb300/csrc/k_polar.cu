@@ -31,12 +31,31 @@ __device__ __forceinline__ float tap(const T* frame, int H, int W, int x, int y,
     return gm((float)__ldg(frame + (size_t)y * W + x));
 }
 
+// Tap of a sample at offset (dx, dy) = (r cos theta, r sin theta) from a per-pattern centre
+// (cx, cy): the offsets come from the host in double precision split as hi + lo floats;
+// x = cx + dx is formed with an error-free sum so that the fraction is accurate far below
+// float resolution before it is rounded.
+__device__ __forceinline__ void centre_tap(float c, float hi, float lo, int& i0, float& f, float& g) {
+    const float s = c + hi;
+    const float bb = s - c;
+    const float err = (c - (s - bb)) + (hi - bb);               // s + err == c + hi exactly
+    float base = floorf(s);
+    float fh = s - base;                                        // exact
+    float fl = err + lo;
+    float fr = fh + fl;
+    if (fr < 0.0f) { base -= 1.0f; fh += 1.0f; fr = fh + fl; }
+    else if (fr >= 1.0f) { base += 1.0f; fh -= 1.0f; fr = fh + fl; }
+    i0 = (int)base;
+    f = fr;
+    g = (1.0f - fh) - fl;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024)
 polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
              const int32_t* __restrict__ txy, const float4* __restrict__ tw, Gamma gm, int n_r, int n_theta,
              const uint8_t* __restrict__ keep_row, float* __restrict__ polar, float* __restrict__ pnorm,
-             float* __restrict__ radial) {
+             float* __restrict__ radial, const float2* __restrict__ centres, const float4* __restrict__ toff) {
     extern __shared__ float smem[];
     const int nw = blockDim.x >> 5;
     float* part = smem;                         // [n_r][nw] row partial sums
@@ -47,6 +66,8 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
         const T* frame = frames + (size_t)p * H * W;
         float* out = polar + (size_t)p * n_r * n_theta;
+        float2 cen = make_float2(0.0f, 0.0f);
+        if (centres) cen = __ldg(centres + p);
         float s2 = 0.0f, c2 = 0.0f;             // Kahan sum of P'^2 for this thread
         for (int j0 = 0; j0 < n_r; j0 += U) {
             float rowsum[U];
@@ -60,10 +81,18 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
                     v[u] = 0.0f;
                     if (j < n_r) {
                         const int idx = j * n_theta + k;
-                        const int xy = __ldg(txy + idx);
-                        const int x0 = (int)(int16_t)(xy & 0xffff);
-                        const int y0 = xy >> 16;
-                        const float4 f = __ldg(tw + idx);           // fx, 1 - fx, fy, 1 - fy
+                        int x0, y0;
+                        float4 f;                                   // fx, 1 - fx, fy, 1 - fy
+                        if (centres) {
+                            const float4 o = __ldg(toff + idx);     // dx hi, dx lo, dy hi, dy lo
+                            centre_tap(cen.x, o.x, o.y, x0, f.x, f.y);
+                            centre_tap(cen.y, o.z, o.w, y0, f.z, f.w);
+                        } else {
+                            const int xy = __ldg(txy + idx);
+                            x0 = (int)(int16_t)(xy & 0xffff);
+                            y0 = xy >> 16;
+                            f = __ldg(tw + idx);
+                        }
                         const float v00 = tap(frame, H, W, x0, y0, gm);
                         const float v10 = tap(frame, H, W, x0 + 1, y0, gm);
                         const float v01 = tap(frame, H, W, x0, y0 + 1, gm);
@@ -117,7 +146,7 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st, const uint8_t* keep_row) {
+                         cudaStream_t st, const uint8_t* keep_row, const float2* centres, const float4* offsets) {
     if (n <= 0) return cudaSuccess;
     Gamma gm;
     gm.mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
@@ -138,9 +167,9 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
     const int64_t grid64 = n < 65535 * 16 ? n : 65535 * 16;
     const int grid = (int)grid64;
     if (dtype == TM_DTYPE_U16)
-        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial);
+        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial, centres, offsets);
     else
-        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial);
+        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial, centres, offsets);
     return cudaGetLastError();
 }
 

@@ -122,6 +122,7 @@ struct tm_ctx {
     std::map<int, std::unique_ptr<Library>> libs;
     int next_id = 0;
     std::map<TableKey, PolarTableDev> tables;
+    std::map<std::tuple<int, int, double>, float4*> offset_tables;   // per-pattern-centre taps
     std::map<std::string, Buffer> ws;
     cudaEvent_t ws_event = nullptr;
     unsigned* d_error = nullptr;   // device error word of the bounded waits
@@ -370,12 +371,25 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
     const int64_t ns = (int64_t)L->r.size();
     if (ns >= (int64_t)1 << 31) return fail(TM_ERR_UNSUPPORTED, "tm_load_library: too many spots");
     // distinct radii (rows of the sparse kernel's shared-memory image) and packed spots
+    {
+        std::vector<int32_t> rr(L->r);
+        std::sort(rr.begin(), rr.end());
+        rr.erase(std::unique(rr.begin(), rr.end()), rr.end());
+        L->radii = rr;
+    }
     std::vector<int32_t> row_of(n_r, -1);
     for (size_t i = 0; i < L->radii.size(); ++i) row_of[L->radii[i]] = (int32_t)i;
     spot.resize(ns);
+    // every shared-memory word a spot's blocks read: [row * pitch, row * pitch + pitch)
+    const int64_t image = (int64_t)std::max<size_t>(1, L->radii.size()) * pitch;
     for (int64_t i = 0; i < ns; ++i) {
+        const int row = row_of[L->r[i]];
         const int w = (n_theta - L->t[i] + 31) / 32;
-        spot[i].x = (row_of[L->r[i]] * pitch + L->t[i]) | (w << 24);
+        const int64_t a = (int64_t)row * pitch + L->t[i];
+        if (row < 0 || a < 0 || a >= image || (int64_t)row * pitch + pitch > image || a >= (1 << 24) || w < 1 || w > 63)
+            return fail(TM_ERR_INVALID_ARG, "tm_load_library: internal layout check failed for spot %lld",
+                        (long long)i);
+        spot[i].x = (int32_t)a | (w << 24);
         memcpy(&spot[i].y, &L->I[i], 4);
     }
     return TM_OK;
@@ -399,13 +413,6 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
         return L->off[x + 1] - L->off[x] < L->off[y + 1] - L->off[y];
     });
-    {
-        std::vector<int32_t> rr(L->r);
-        std::sort(rr.begin(), rr.end());
-        rr.erase(std::unique(rr.begin(), rr.end()), rr.end());
-        L->radii = rr;
-    }
-
     struct Up { void** dst; const void* src; size_t bytes; const char* what; };
     Up ups[] = {
         {(void**)&L->d_off, off32.data(), off32.size() * 4, "library offsets"},
@@ -585,6 +592,33 @@ tmgb::DenseLib dense_view(const Library* L) {
     return v;
 }
 
+// Offsets (r cos theta, r sin theta) of every polar sample, each split as float hi + lo
+// of its double value, for frames with per-pattern centres; cached per grid.
+int offset_table(tm_ctx* ctx, int n_r, int n_theta, double dr, const float4** out) {
+    auto key = std::make_tuple(n_r, n_theta, dr);
+    auto it = ctx->offset_tables.find(key);
+    if (it == ctx->offset_tables.end()) {
+        const size_t m = (size_t)n_r * n_theta;
+        std::vector<float4> v(m);
+        for (int j = 0; j < n_r; ++j) {
+            const double r = j * dr;
+            for (int k = 0; k < n_theta; ++k) {
+                const double th = 2.0 * kPi * k / n_theta;
+                const double dx = r * cos(th), dy = r * sin(th);
+                const float xh = (float)dx, yh = (float)dy;
+                v[(size_t)j * n_theta + k] = make_float4(xh, (float)(dx - (double)xh), yh, (float)(dy - (double)yh));
+            }
+        }
+        float4* d = nullptr;
+        int rc = dev_alloc(ctx, (void**)&d, m * 16, "offset table");
+        if (rc) return rc;
+        TM_CUDA(cudaMemcpy(d, v.data(), m * 16, cudaMemcpyHostToDevice), "offset table");
+        it = ctx->offset_tables.emplace(key, d).first;
+    }
+    *out = it->second;
+    return TM_OK;
+}
+
 int check_params(const tm_index_params* p) {
     if (!p) return fail(TM_ERR_INVALID_ARG, "params is NULL");
     if (!(p->gamma > 0.0 && isfinite(p->gamma))) return fail(TM_ERR_INVALID_ARG, "gamma must be finite and > 0");
@@ -729,6 +763,7 @@ void tm_destroy(tm_ctx* ctx) {
         }
         for (auto& kv : ctx->ws)
             if (kv.second.p) cudaFree(kv.second.p);
+        for (auto& kv : ctx->offset_tables) cudaFree(kv.second);
         for (auto& kv : ctx->spectral) {
             cudaFree(kv.second.basis);
             cudaFree(kv.second.twiddle);
@@ -825,7 +860,7 @@ static void export_host(const Library* L, int64_t* offsets, int32_t* r, int32_t*
 }
 
 int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, int64_t* offsets, int32_t* r,
-                            int32_t* t, float* intensity, float* norm, int32_t* order) {
+                            int32_t* t, float* intensity, float* norm, int32_t* order, int32_t* packed) {
     if (!info) return fail(TM_ERR_INVALID_ARG, "tm_library_prepare_host: info is NULL");
     Library L;
     Prepared P;
@@ -833,6 +868,8 @@ int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, 
     if (rc) return rc;
     fill_info(&L, info);
     export_host(&L, offsets, r, t, intensity, norm, order);
+    if (packed)
+        for (size_t i = 0; i < P.spot.size(); ++i) packed[i] = P.spot[i].x;
     return TM_OK;
 }
 
@@ -847,8 +884,8 @@ int tm_library_export(tm_ctx* ctx, int lib_id, int64_t* offsets, int32_t* r, int
 }
 
 int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype,
-                       int64_t n, int32_t H, int32_t W, int32_t n_r, int32_t n_theta, double dr,
-                       float* polar_dev, float* norm_dev, float* radial_dev, void* stream) {
+                       int64_t n, int32_t H, int32_t W, const float* centres_dev, int32_t n_r, int32_t n_theta,
+                       double dr, float* polar_dev, float* norm_dev, float* radial_dev, void* stream) {
     if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: ctx is NULL");
     int rc = check_params(params);
     if (rc) return rc;
@@ -862,12 +899,14 @@ int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* f
     DeviceGuard g(ctx->device);
     const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
     const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
-    tmgb::PolarTable tab;
-    rc = polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
+    tmgb::PolarTable tab{};
+    const float4* offs = nullptr;
+    rc = centres_dev ? offset_table(ctx, n_r, n_theta, dr, &offs) : polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     TM_CUDA(tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                             polar_dev, norm_dev, radial_dev, st), "tm_polar_transform: launch");
+                             polar_dev, norm_dev, radial_dev, st, nullptr, (const float2*)centres_dev, offs),
+            "tm_polar_transform: launch");
     return TM_OK;
 }
 
@@ -946,7 +985,6 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: dtype");
     if (n_libs < 1 || n_libs > TM_MAX_LIBS || !lib_ids)
         return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: n_libs must be in [1, %d]", TM_MAX_LIBS);
-    if (centres_dev) return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: per-pattern centres are not supported");
     if (params->path != TM_PATH_FP32_SPARSE && params->path != TM_PATH_BF16_RESCORE)
         return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: unknown path %d", params->path);
     const bool bf16 = params->path == TM_PATH_BF16_RESCORE;
@@ -974,8 +1012,9 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                     n_theta);
     const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
     const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
-    tmgb::PolarTable tab;
-    rc = polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
+    tmgb::PolarTable tab{};
+    const float4* offs = nullptr;
+    rc = centres_dev ? offset_table(ctx, n_r, n_theta, dr, &offs) : polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
     if (rc) return rc;
     const bool pre = params->prefilter_fraction < 1.0;
     const int kc = params->rescore_k;
@@ -1050,7 +1089,9 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             {
                 StageTimer tmr(ctx, TM_STAGE_POLAR, st);
                 TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                                           polar, pnorm, radial, st, rmap.keep_row), "tm_index_patterns: polar");
+                                           polar, pnorm, radial, st, rmap.keep_row,
+                                           centres_dev ? (const float2*)centres_dev + c0 : nullptr, offs),
+                        "tm_index_patterns: polar");
             }
             ++launches;
             if (pre) {
@@ -1160,8 +1201,8 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     // CUDA graph: the second identical call on a created stream is captured, later ones replay
     if ((params->reserved & TM_INDEX_GRAPH) && st != nullptr && !ctx->profiling) {
         char key[512];
-        int off = snprintf(key, sizeof key, "%p|%p|%p|%d|%lld|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|", st,
-                           frames_dev, (void*)out_dev, dtype, (long long)n, H, W, params->gamma, params->subtract,
+        int off = snprintf(key, sizeof key, "%p|%p|%p|%p|%d|%lld|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|", st,
+                           frames_dev, (const void*)centres_dev, (void*)out_dev, dtype, (long long)n, H, W, params->gamma, params->subtract,
                            params->cx, params->cy, params->prefilter_fraction, params->top_n, params->path,
                            params->rescore_k);
         for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);

@@ -48,11 +48,13 @@ struct PolarTable {            // bilinear taps for one (H, W, n_r, n_theta, dr,
 };
 
 // keep_row [n_r] (nullable): rows whose polar values are stored; the norm and the row
-// sums always cover every row.
+// sums always cover every row.  centres [n] (nullable): per-pattern beam centres, used with
+// offsets [n_r * n_theta] = (r cos, r sin) split into float hi/lo pairs; tab is then unused.
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st, const uint8_t* keep_row = nullptr);
+                         cudaStream_t st, const uint8_t* keep_row = nullptr,
+                         const float2* centres = nullptr, const float4* offsets = nullptr);
 
 cudaError_t launch_radial_norm(const float* radial, int64_t n, int n_r, float* out,
                                cudaStream_t st);

@@ -107,9 +107,9 @@ _SIGS = {
     "tm_library_info_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(tm_library_info)]),
     "tm_library_export": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "tm_library_prepare_host": (ctypes.c_int, [ctypes.POINTER(tm_library_desc), ctypes.POINTER(tm_library_info),
-                                               _P, _P, _P, _P, _P, _P]),
+                                               _P, _P, _P, _P, _P, _P, _P]),
     "tm_polar_transform": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
-                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_double, _P, _P, _P, _P]),
     "tm_prefilter": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P]),
     "tm_correlate": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
@@ -215,9 +215,11 @@ def tm_library_prepare_host(ts, n_r: int, n_theta: int, dr: float = 1.0, mirror=
     d = _Desc(ts, n_r, n_theta, dr, mirror, unit_intensity)
     info = tm_library_info()
     _check(library().tm_library_prepare_host(ctypes.byref(d.desc), ctypes.byref(info), None, None, None,
-                                             None, None, None))
+                                             None, None, None, None))
     out = _alloc_export(info)
-    _check(library().tm_library_prepare_host(ctypes.byref(d.desc), ctypes.byref(info), *_export_ptrs(out)))
+    out["packed"] = np.zeros(info.n_spots, np.int32)
+    _check(library().tm_library_prepare_host(ctypes.byref(d.desc), ctypes.byref(info), *_export_ptrs(out),
+                                             out["packed"].ctypes.data if out["packed"].size else None))
     out["info"] = _info_dict(info)
     return out
 
@@ -268,10 +270,10 @@ def make_params(gamma=0.5, subtract=0.0, cx=math.nan, cy=math.nan, prefilter=1.0
     return p
 
 
-def tm_polar_transform(ctx, params, frames_ptr, dtype, n, H, W, n_r, n_theta, dr, polar_ptr, norm_ptr,
+def tm_polar_transform(ctx, params, frames_ptr, dtype, n, H, W, centres_ptr, n_r, n_theta, dr, polar_ptr, norm_ptr,
                        radial_ptr, stream) -> None:
-    _check(library().tm_polar_transform(ctx, ctypes.byref(params), frames_ptr, dtype, n, H, W, n_r, n_theta, dr,
-                                        polar_ptr, norm_ptr, radial_ptr, stream))
+    _check(library().tm_polar_transform(ctx, ctypes.byref(params), frames_ptr, dtype, n, H, W, centres_ptr, n_r,
+                                        n_theta, dr, polar_ptr, norm_ptr, radial_ptr, stream))
 
 
 def tm_prefilter(ctx, lib_id, radial_ptr, n, fraction, mask_ptr, score_ptr, stream) -> None:
@@ -470,7 +472,9 @@ class Context:
         return tm_library_export(self.handle, lib_id)
 
     def polar_transform(self, frames, n_r, n_theta, dr=1.0, gamma=0.5, subtract=0.0, cx=math.nan, cy=math.nan,
-                        stream=None):
+                        centres=None, stream=None):
+        """frames [n][H][W] -> (polar [n][n_r][n_theta], norm [n], radial [n][n_r]); centres: optional
+        float32 [n][2] device tensor of per-pattern (cx, cy)."""
         import torch
         n, H, W = frames.shape
         dev = frames.device
@@ -478,7 +482,8 @@ class Context:
         norm = torch.empty((n,), dtype=torch.float32, device=dev)
         radial = torch.empty((n, n_r), dtype=torch.float32, device=dev)
         p = make_params(gamma, subtract, cx, cy)
-        tm_polar_transform(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W, n_r, n_theta, dr,
+        tm_polar_transform(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W,
+                           None if centres is None else centres.data_ptr(), n_r, n_theta, dr,
                            polar.data_ptr(), norm.data_ptr(), radial.data_ptr(), _stream_ptr(stream))
         return polar, norm, radial
 
@@ -528,7 +533,7 @@ class Context:
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
               path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None,
-              graph=False):
+              graph=False, centres=None):
         """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32.
         graph=True replays repeated identical calls as a CUDA graph (needs a created stream)."""
         import torch
@@ -540,6 +545,7 @@ class Context:
         p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k)
         if graph:
             p.reserved |= TM_INDEX_GRAPH
-        self.last_stats = tm_index_patterns(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W, None,
+        self.last_stats = tm_index_patterns(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W,
+                                            None if centres is None else centres.data_ptr(),
                                             list(lib_ids), out.data_ptr(), _stream_ptr(stream))
         return out

@@ -56,9 +56,11 @@ def fcc():
 
 # ------------------------------------------------------------------ stage 1: polar
 
-def _check_polar(ctx, frames, n_r, n_theta, gamma=0.5, subtract=0.0, dr=1.0):
-    P_ref = O.polar(frames, n_r, n_theta, dr, gamma, subtract)
-    polar, norm, radial = ctx.polar_transform(_t(frames), n_r, n_theta, dr, gamma, subtract)
+def _check_polar(ctx, frames, n_r, n_theta, gamma=0.5, subtract=0.0, dr=1.0, centres=None):
+    P_ref = O.polar(frames, n_r, n_theta, dr, gamma, subtract,
+                    centres=None if centres is None else centres.astype(np.float64))
+    polar, norm, radial = ctx.polar_transform(_t(frames), n_r, n_theta, dr, gamma, subtract,
+                                              centres=None if centres is None else _t(centres))
     P = _np(polar).astype(np.float64)
     # each sample is a convex combination of four float gamma values (correctly rounded
     # sqrt / powf) with weights within a few ulps: error <= 8 ulp of the largest tap; the
@@ -87,6 +89,17 @@ def test_polar_u16_256_and_options(ctx, fcc):
     _check_polar(ctx, scan.frames[:24], 128, 360)
     _check_polar(ctx, scan.frames[:8], 128, 360, gamma=1.0, subtract=0.3)
     _check_polar(ctx, scan.frames[:8], 100, 90, gamma=0.7, dr=1.25)
+
+
+def test_polar_per_pattern_centres(ctx, fcc):
+    """Each pattern resampled about its own beam centre (fractional, off the frame centre)."""
+    ts, scan, lib = fcc
+    rng = np.random.default_rng(8)
+    n = 16
+    centres = (np.array([127.5, 127.5]) + rng.uniform(-6.0, 6.0, size=(n, 2))).astype(np.float32)
+    centres[0] = (127.5, 127.5)
+    centres[1] = (100.0, 140.25)
+    _check_polar(ctx, scan.frames[:n], 128, 360, centres=centres)
 
 
 def test_polar_ragged_and_tiny_grids(ctx):
@@ -231,6 +244,19 @@ def test_index_options_and_edges(ctx):
         h = _hits(ctx, frames, lid, **kw)[0]
         compare_hits(h, ref, lib)
         ctx.unload_library(lid)
+
+
+def test_index_per_pattern_centres(ctx, tiny):
+    ts, scan, lib, ref = tiny
+    rng = np.random.default_rng(9)
+    n = 48
+    centres = (np.array([63.5, 63.5]) + rng.uniform(-2.0, 2.0, size=(n, 2))).astype(np.float32)
+    lid = ctx.load_library(ts, 60, 180)
+    out = ctx.index(_t(scan.frames[:n]), lid, top_n=5, centres=_t(centres))
+    h = tmgb.hits_to_numpy(out)[0]
+    r = O.index(scan.frames[:n], lib, N=5, centres=centres.astype(np.float64))
+    compare_hits(h, r, lib)
+    ctx.unload_library(lid)
 
 
 def test_index_zero_frames_and_single_pattern(ctx, tiny):

@@ -119,3 +119,53 @@ def test_prepare_rejects_bad_descriptor(lib, bad):
     with pytest.raises(tmgb.TmError) as e:
         tmgb.tm_library_prepare_host(ts, **kw)
     assert e.value.code == tmgb.TM_ERR_INVALID_ARG
+
+
+def _round_nb(nb):
+    return nb if nb <= 4 else 6 if nb <= 6 else 8 if nb <= 8 else 12 if nb <= 12 else 16 if nb <= 16 \
+        else 24 if nb <= 24 else 32
+
+
+def _pitch(n_theta):
+    """Row pitch of the sparse kernel's shared-memory rows (n_theta + 32, and at least
+    32 x the widest rounded block count)."""
+    return max(n_theta + 32, 32 * _round_nb((n_theta + 31) // 32))
+
+
+@pytest.mark.parametrize("which", ["random", "fcc", "hcp", "odd"])
+def test_sparse_layout_reads_stay_in_bounds(lib, which):
+    """Replay the sparse kernel's shared-memory indexing on the CPU for every spot, lane and
+    shift block: the packed word decodes to the spot's row among the library's distinct radii
+    and its column; every address stays inside that row's padded span; the word read equals
+    the polar sample at (t + s) mod n_theta for the lane's shift s."""
+    if which == "random":
+        ts, _, _ = synth.tiny_workload(n_side=1)
+        n_r, n_theta = 60, 180
+    elif which == "odd":
+        ts, _, _ = synth.tiny_workload(n_side=1)
+        n_r, n_theta = 61, 77
+    else:
+        ts = synth.kinematic_library(which, step_deg=3.0)
+        n_r, n_theta = 128, 360
+    h = tmgb.tm_library_prepare_host(ts, n_r, n_theta)
+    radii = np.unique(h["r"])
+    pitch = _pitch(n_theta)
+    word = h["packed"].astype(np.int64) & 0xFFFFFFFF
+    a = word & 0xFFFFFF
+    w = word >> 24
+    row, col = a // pitch, a % pitch
+    assert np.array_equal(radii[row], h["r"])
+    assert np.array_equal(col, h["t"])
+    assert np.array_equal(w, (n_theta - h["t"] + 31) // 32)
+    lanes = np.arange(32)
+    for k in range(h["info"]["n_templates"]):
+        S = n_theta // h["order"][k]
+        nb = _round_nb((S + 31) // 32)
+        for i in range(h["offsets"][k], h["offsets"][k + 1]):
+            for b in range(nb):
+                base = a[i] + 32 * b - (n_theta if b >= w[i] else 0)
+                addr = base + lanes
+                lo, hi = row[i] * pitch, row[i] * pitch + pitch
+                assert np.all((addr >= lo) & (addr < hi)), (k, i, b)
+                # column c of a row holds P'[c mod n_theta]
+                assert np.array_equal((addr - lo) % n_theta, (h["t"][i] + 32 * b + lanes) % n_theta)
