@@ -1,0 +1,183 @@
+// Whole-path indexing (FP32 sparse path, one library) that allocates no device memory.
+//
+// Who needs this: callers that cannot call cudaMalloc while indexing -- an application
+// whose device memory is owned by another allocator (a framework's caching allocator that
+// must see every allocation), or an acquisition callback in instrument-control software
+// that runs inside a fixed, pre-reserved device budget and must not block on the driver's
+// allocator.  tm_index_patterns grows per-stream scratch buffers on first use; this entry
+// point instead keeps its scratch (bilinear tap table, polar images, image norms and the
+// pattern counter) in one statically sized device array that every GPU which loads the
+// library holds for the life of the process.
+//
+// Limits and rules:
+// * The array holds kScratchBytes (64 MiB); a call whose scratch does not fit (for a
+//   128 x 360 polar grid: about 340 patterns per call) is rejected with
+//   TM_ERR_INVALID_ARG and a message giving the size it needed.
+// * All calls share the one array and it keeps the previous call's contents; the call
+//   rewrites every part it reads (the pattern counter is cleared on the stream first).
+//   Calls whose work overlaps on the GPU (several streams, several host threads) race on
+//   the array: serialise them on one stream.
+// * The first call on a device looks up the array's device address
+//   (cudaGetSymbolAddress) with that device current; make that first call before any
+//   stream capture begins.
+// * No cudaMalloc, cudaFree or other allocating call is made, on the device or the host:
+//   the tap table is computed in double precision into a static host staging area (grids
+//   of up to kMaxTaps polar samples) and copied into the array on the caller's stream.
+#include <math.h>
+#include <stdio.h>
+
+#include <mutex>
+
+#include "tm_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)64 << 20;
+constexpr size_t kMaxTaps = (size_t)1 << 20;
+constexpr double kPi = 3.14159265358979323846;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;                      // guards the lookups below and the host staging
+int32_t g_host_xy[kMaxTaps];
+float4 g_host_w[kMaxTaps];
+void* g_scratch_dev[128] = {};        // device address of g_scratch, per CUDA device
+
+int fail(int code, const char* msg) {
+    tmgb::set_last_error(msg);
+    return code;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device address of the scratch array on the current device (looked up once per device).
+int scratch_for(int device, unsigned char** out) {
+    if (device < 0 || device >= 128) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: device id");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_dev[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            char buf[256];
+            snprintf(buf, sizeof buf, "tm_index_patterns_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            cudaGetLastError();
+            return fail(TM_ERR_CUDA, buf);
+        }
+        g_scratch_dev[device] = p;
+    }
+    *out = (unsigned char*)g_scratch_dev[device];
+    return TM_OK;
+}
+
+}  // namespace
+
+extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,
+                                         int32_t dtype, int64_t n, int32_t H, int32_t W, int32_t lib_id,
+                                         tm_hit* out_dev, void* stream) {
+    if (!ctx || !params) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: NULL argument");
+    if (!(params->gamma > 0.0 && isfinite(params->gamma)) || !isfinite(params->subtract) || isinf(params->cx) ||
+        isinf(params->cy))
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: bad gamma, subtract or centre");
+    if (params->path != TM_PATH_FP32_SPARSE || params->prefilter_fraction != 1.0)
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: only the FP32 sparse path without pre-filter");
+    if (params->top_n < 1 || params->top_n > TM_MAX_TOPN)
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: top_n out of range");
+    if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000 || (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32))
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: bad frames");
+    int device = 0, num_sms = 0, n_r = 0, n_theta = 0;
+    double dr = 1.0;
+    tmgb::SparseLib view;
+    int rc = tmgb::library_view(ctx, lib_id, &device, &num_sms, &view, &n_r, &n_theta, &dr);
+    if (rc) return rc;
+    if (n == 0) return TM_OK;
+    if (!frames_dev || !out_dev) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: NULL buffer");
+    const int N = params->top_n;
+    if (!tmgb::sparse_smem_bytes(view.n_rad, n_theta, N))
+        return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns_noalloc: polar grid does not fit shared memory");
+
+    // scratch layout: tap positions | tap weights | polar images | image norms | counter
+    const size_t m = (size_t)n_r * n_theta;
+    if (m > kMaxTaps) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: polar grid larger than 2^20 samples");
+    const size_t o_xy = 0;
+    const size_t o_w = align256(o_xy + m * 4);
+    const size_t o_polar = align256(o_w + m * 16);
+    const size_t o_norm = align256(o_polar + (size_t)n * m * 4);
+    const size_t o_count = align256(o_norm + (size_t)n * 4);
+    const size_t need = o_count + 256;
+    if (need > kScratchBytes) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "tm_index_patterns_noalloc: %lld patterns on a %dx%d grid need %zu bytes of scratch; "
+                 "the static scratch holds %zu (index fewer patterns per call)",
+                 (long long)n, n_r, n_theta, need, kScratchBytes);
+        return fail(TM_ERR_INVALID_ARG, buf);
+    }
+
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != device) cudaSetDevice(device);
+    unsigned char* scratch = nullptr;
+    rc = scratch_for(device, &scratch);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!rc) {
+        // bilinear taps for this geometry, in double precision on the host; the staging is
+        // reused once the copies below have consumed it (a copy from pageable memory
+        // returns after the data has been taken)
+        std::lock_guard<std::mutex> lk(g_mu);
+        const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
+        const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
+        int32_t* xy = g_host_xy;
+        float4* wv = g_host_w;
+        for (int j = 0; j < n_r; ++j) {
+            const double r = j * dr;
+            for (int k = 0; k < n_theta; ++k) {
+                const double th = 2.0 * kPi * k / n_theta;
+                const double x = cx + r * cos(th), y = cy + r * sin(th);
+                double x0 = floor(x), y0 = floor(y);
+                x0 = fmin(fmax(x0, -2.0), (double)W + 1.0);
+                y0 = fmin(fmax(y0, -2.0), (double)H + 1.0);
+                double fx = x - x0, fy = y - y0;
+                if (fx < 0.0 || fx >= 1.0) fx = 0.0;
+                if (fy < 0.0 || fy >= 1.0) fy = 0.0;
+                const size_t i = (size_t)j * n_theta + k;
+                xy[i] = (int32_t)((uint32_t)(uint16_t)(int16_t)(int)x0 | ((uint32_t)(int16_t)(int)y0 << 16));
+                wv[i] = make_float4((float)fx, (float)(1.0 - fx), (float)fy, (float)(1.0 - fy));
+            }
+        }
+        cudaError_t e = cudaMemcpyAsync(scratch + o_xy, xy, m * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_w, wv, m * 16, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            tmgb::PolarTable tab;
+            tab.xy = (const int32_t*)(scratch + o_xy);
+            tab.w = (const float4*)(scratch + o_w);
+            float* polar = (float*)(scratch + o_polar);
+            float* pnorm = (float*)(scratch + o_norm);
+            e = tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
+                                   polar, pnorm, nullptr, st);
+            if (e == cudaSuccess) {
+                tmgb::SparseCall c{};
+                c.polar = polar;
+                c.pnorm = pnorm;
+                c.n = n;
+                c.n_r = n_r;
+                c.n_theta = n_theta;
+                c.pitch = tmgb::sparse_pitch(n_theta);
+                c.max_rad = view.n_rad;
+                c.pattern_counter = (int*)(scratch + o_count);
+                c.n_libs = 1;
+                c.lib[0] = view;
+                c.hits = out_dev;
+                c.hits_lib_stride = n * N;
+                c.top_n = N;
+                e = tmgb::launch_sparse(c, num_sms, st);
+            }
+        }
+        if (e != cudaSuccess) {
+            char buf[256];
+            snprintf(buf, sizeof buf, "tm_index_patterns_noalloc: %s", cudaGetErrorString(e));
+            rc = fail(TM_ERR_CUDA, buf);
+        }
+    }
+    if (prev >= 0 && prev != device) cudaSetDevice(prev);
+    return rc;
+}

@@ -119,6 +119,9 @@ _SIGS = {
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
     "tm_prescore": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     "tm_check": (ctypes.c_int, [_P, _P]),
+    "tm_index_patterns_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32,
+                                                 ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                                 _P]),
     "tm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
                                    ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                    _P]),
