@@ -21,6 +21,25 @@ pytestmark = pytest.mark.gpu
 PRE_TOL = 0.01      # |Q~ - Q| <= PRE_TOL * Q_top1 (BF16 G and basis: ~2^-8 relative per term)
 
 
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    from paper_2111_07347_gb300 import build
+    build.build()
+    c = tmgb.Context(0)
+    yield c
+    c.check()
+    c.close()
+
+
+def _t(a):
+    import torch
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16)).cuda().view(torch.uint16)
+    return torch.from_numpy(a).cuda()
+
+
 def _check_prescore(ctx, ts, frames, n_r, n_theta, kcs=(64, 256), fraction=1.0):
     """Pre-score of every template vs the oracle's exact Q; returns (worst error / Q_top,
     {kc: fraction of patterns whose kc best pre-scores contain a template attaining the
