@@ -7,10 +7,13 @@
 //
 // Design (GB300):
 // * Shared memory holds only the polar rows the library uses (its distinct spot radii --
-//   a few to a few tens of the 128 rows), each padded to sparse_pitch(Nθ) >= Nθ + 32
-//   columns with column c = P'[c mod Nθ]; a warp reading 32 consecutive shifts of one spot
-//   never splits at the wrap and never conflicts on a bank.  The small footprint lets
-//   several CTAs share an SM and leaves L1 to cache the library's spot lists.
+//   a few to a few tens of the 128 rows), column c of a row holding P'[c mod Nθ].  When the
+//   rows fit twice over (pitch Nθ + 32 NB), shift block b of a spot at column t reads
+//   columns t + 32 b + [0, 32) with no wrap test at all (one load and one FMA per block);
+//   otherwise rows are padded by 32 columns and a block past the wrap reads 32 b - Nθ
+//   further (a select per block).  Either way a warp's 32 consecutive shifts never split at
+//   the wrap and never conflict on a bank.  The small footprint lets several CTAs share an
+//   SM and leaves L1 to cache the library's spot lists.
 // * A persistent CTA takes patterns from a global counter; its warps take 32-template
 //   mask words from a shared counter.  One warp scores one template: lane L accumulates
 //   shifts s = 32 b + L of every shift block b in registers; the template's spots arrive
@@ -40,12 +43,14 @@ constexpr int kMaxWarps = kMaxThreads / 32;
 
 }  // namespace
 
-// Row pitch of the polar rows in shared memory.  Block b of a spot at column t reads
-// columns t + 32 b + [0, 32) (or that minus n_theta once it wraps), so the pitch covers
-// n_theta + 32 columns and every column 32 * NB - 1 that the widest rounded block count
-// NB can touch; column c holds P'[c mod n_theta].
-int sparse_pitch(int n_theta) {
+// Row pitch of the polar rows in shared memory, column c holding P'[c mod n_theta].
+// Wrap-free layout: block b of a spot at column t reads t + 32 b + [0, 32) for b < NB (NB the
+// widest rounded block count), so the pitch is n_theta + 32 NB.  Wrapped layout: blocks past
+// the wrap read n_theta columns earlier, so n_theta + 32 columns and every column 32 NB - 1
+// suffice.
+int sparse_pitch(int n_theta, bool wrap_free) {
     const int nb = round_nb((n_theta + 31) / 32);
+    if (wrap_free) return n_theta + 32 * nb;
     const int a = n_theta + 32, b = 32 * nb;
     return a > b ? a : b;
 }
@@ -59,10 +64,10 @@ __device__ __forceinline__ bool better(float qa, int ka, float qb, int kb) {
 // Correlation C(s) of one template for all its shifts (warp-collective).  Returns the
 // warp-wide maximum; when it reaches thr_c, *shift_out is the lowest shift attaining it
 // and `resolved` is set.
-template <int NB>
+template <int NB, bool WF>
 __device__ __forceinline__ float score_template(const float* __restrict__ sP, const SparseLib& L, int beg, int end,
-                                                int S, int n_theta, int lane, float thr_c, int& shift_out,
-                                                bool& resolved) {
+                                                int S, int n_theta, int pitch, int lane, float thr_c,
+                                                int& shift_out, bool& resolved) {
     float acc[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
@@ -73,21 +78,28 @@ __device__ __forceinline__ float score_template(const float* __restrict__ sP, co
         for (int j = 0; j < cnt; ++j) {
             const int px = __shfl_sync(0xffffffffu, mine.x, j);
             const float I = __int_as_float(__shfl_sync(0xffffffffu, mine.y, j));
-            const int a = px & 0xffffff;
-            const int w = (int)((unsigned)px >> 24);
-            const float* p1 = sP + a + lane;                      // blocks b < w: no wrap
-            const float* p2 = p1 - n_theta;                       // blocks b >= w: wrapped
+            const int t = px & 0x7ff;
+            const int row = (px >> 11) & 0x1fff;
+            const float* p1 = sP + row * pitch + t + lane;
+            if (WF) {
 #pragma unroll
-            for (int b = 0; b < NB; ++b) acc[b] = fmaf(I, (b < w ? p1 : p2)[32 * b], acc[b]);
+                for (int b = 0; b < NB; ++b) acc[b] = fmaf(I, p1[32 * b], acc[b]);
+            } else {
+                const int w = (int)((unsigned)px >> 24);
+                const float* p2 = p1 - n_theta;                   // blocks b >= w: wrapped
+#pragma unroll
+                for (int b = 0; b < NB; ++b) acc[b] = fmaf(I, (b < w ? p1 : p2)[32 * b], acc[b]);
+            }
         }
     }
     float best = -FLT_MAX;
 #pragma unroll
     for (int b = 0; b < NB; ++b)
         if (32 * b + lane < S) best = fmaxf(best, acc[b]);
+    resolved = false;
+    if (!__any_sync(0xffffffffu, best >= thr_c)) return best;    // cannot enter the top-N
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-    resolved = false;
     if (best >= thr_c) {
         int s = INT_MAX;
 #pragma unroll
@@ -101,23 +113,23 @@ __device__ __forceinline__ float score_template(const float* __restrict__ sP, co
     return best;
 }
 
-template <int NBMAX>
+template <int NBMAX, bool WF>
 __device__ __forceinline__ float score_dispatch(const float* sP, const SparseLib& L, int beg, int end, int S,
-                                                int n_theta, int lane, float thr_c, int& s, bool& res) {
+                                                int n_theta, int pitch, int lane, float thr_c, int& s, bool& res) {
     const int nb = (S + 31) >> 5;
-    if (nb <= 1) return score_template<1>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (nb <= 2) return score_template<2>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (nb <= 3) return score_template<3>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (nb <= 4) return score_template<4>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (NBMAX >= 6 && nb <= 6) return score_template<(NBMAX >= 6 ? 6 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (NBMAX >= 8 && nb <= 8) return score_template<(NBMAX >= 8 ? 8 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (NBMAX >= 12 && nb <= 12) return score_template<(NBMAX >= 12 ? 12 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (NBMAX >= 16 && nb <= 16) return score_template<(NBMAX >= 16 ? 16 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    if (NBMAX >= 24 && nb <= 24) return score_template<(NBMAX >= 24 ? 24 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
-    return score_template<(NBMAX >= 32 ? 32 : 1)>(sP, L, beg, end, S, n_theta, lane, thr_c, s, res);
+    if (nb <= 1) return score_template<1, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (nb <= 2) return score_template<2, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (nb <= 3) return score_template<3, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (nb <= 4) return score_template<4, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (NBMAX >= 6 && nb <= 6) return score_template<(NBMAX >= 6 ? 6 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (NBMAX >= 8 && nb <= 8) return score_template<(NBMAX >= 8 ? 8 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (NBMAX >= 12 && nb <= 12) return score_template<(NBMAX >= 12 ? 12 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (NBMAX >= 16 && nb <= 16) return score_template<(NBMAX >= 16 ? 16 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    if (NBMAX >= 24 && nb <= 24) return score_template<(NBMAX >= 24 ? 24 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    return score_template<(NBMAX >= 32 ? 32 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
 }
 
-template <int NBMAX>
+template <int NBMAX, bool WF>
 __global__ void __launch_bounds__(kMaxThreads)
 sparse_kernel(const SparseCall c) {
     extern __shared__ __align__(16) float smem[];
@@ -202,7 +214,8 @@ sparse_kernel(const SparseCall c) {
                     }
                     int s = 0;
                     bool resolved = false;
-                    const float best = score_dispatch<NBMAX>(sP, L, beg, end, S, n_theta, lane, thr_c, s, resolved);
+                    const float best = score_dispatch<NBMAX, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s,
+                                                                 resolved);
                     if (!resolved) continue;
                     float q;
                     if (d > 0.0f) q = __fdiv_rn(best, d);
@@ -269,40 +282,63 @@ sparse_kernel(const SparseCall c) {
     }
 }
 
-template <int NBMAX>
+template <int NBMAX, bool WF>
 cudaError_t launch_nb(const SparseCall& c, int num_sms, size_t smem, cudaStream_t st) {
     const int threads = (c.threads == 128 || c.threads == 512) ? c.threads : 256;
-    cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX, WF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX>, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX, WF>, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > c.n) grid = c.n;
     e = cudaMemsetAsync(c.pattern_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    sparse_kernel<NBMAX><<<(int)grid, threads, smem, st>>>(c);
+    sparse_kernel<NBMAX, WF><<<(int)grid, threads, smem, st>>>(c);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n) {
+// Layout for a call: the wrap-free rows when they fit in kWrapFreeBytes (several CTAs per
+// SM), else the wrapped rows; 0 when even those do not fit.
+constexpr size_t kWrapFreeBytes = 100 * 1024;
+
+size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, bool* wrap_free, int* pitch) {
     if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
-    const size_t b = (size_t)max_rad * sparse_pitch(n_theta) * 4 + (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16;
-    return b <= 232448 ? b : 0;
+    const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16;
+    for (int wf = 1; wf >= 0; --wf) {
+        const int pch = sparse_pitch(n_theta, wf != 0);
+        const size_t b = (size_t)max_rad * pch * 4 + lists;
+        if ((wf && b <= kWrapFreeBytes) || (!wf && b <= 232448)) {
+            if (wrap_free) *wrap_free = wf != 0;
+            if (pitch) *pitch = pch;
+            return b;
+        }
+    }
+    return 0;
 }
 
-cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st) {
-    if (c.n <= 0) return cudaSuccess;
-    const size_t smem = sparse_smem_bytes(c.max_rad, c.n_theta, c.top_n);
+cudaError_t launch_sparse(const SparseCall& call, int num_sms, cudaStream_t st) {
+    if (call.n <= 0) return cudaSuccess;
+    bool wf = false;
+    int pitch = 0;
+    const size_t smem = sparse_smem_bytes(call.max_rad, call.n_theta, call.top_n, &wf, &pitch);
     if (!smem) return cudaErrorInvalidValue;
+    SparseCall c = call;
+    c.pitch = pitch;
     const int nbmax = (c.n_theta + 31) / 32;
-    if (nbmax <= 6) return launch_nb<6>(c, num_sms, smem, st);
-    if (nbmax <= 12) return launch_nb<12>(c, num_sms, smem, st);
-    if (nbmax <= 24) return launch_nb<24>(c, num_sms, smem, st);
-    return launch_nb<32>(c, num_sms, smem, st);
+    if (wf) {
+        if (nbmax <= 6) return launch_nb<6, true>(c, num_sms, smem, st);
+        if (nbmax <= 12) return launch_nb<12, true>(c, num_sms, smem, st);
+        if (nbmax <= 24) return launch_nb<24, true>(c, num_sms, smem, st);
+        return launch_nb<32, true>(c, num_sms, smem, st);
+    }
+    if (nbmax <= 6) return launch_nb<6, false>(c, num_sms, smem, st);
+    if (nbmax <= 12) return launch_nb<12, false>(c, num_sms, smem, st);
+    if (nbmax <= 24) return launch_nb<24, false>(c, num_sms, smem, st);
+    return launch_nb<32, false>(c, num_sms, smem, st);
 }
 
 }  // namespace tmgb

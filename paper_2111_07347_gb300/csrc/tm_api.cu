@@ -297,8 +297,7 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
             return fail(TM_ERR_INVALID_ARG, "tm_load_library: spot %lld is not finite", (long long)i);
 
     const int n_r = d->n_r, n_theta = d->n_theta;
-    const int pitch = tmgb::sparse_pitch(n_theta);
-    if ((int64_t)n_r * pitch >= (1 << 24))
+    if (n_r >= 8192 || n_theta >= 2048)
         return fail(TM_ERR_UNSUPPORTED, "tm_load_library: polar grid %dx%d too large for the sparse layout", n_r, n_theta);
     L->K0 = K0;
     L->mirror = (d->flags & TM_LIB_MIRROR) ? 1 : 0;
@@ -380,16 +379,15 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
     std::vector<int32_t> row_of(n_r, -1);
     for (size_t i = 0; i < L->radii.size(); ++i) row_of[L->radii[i]] = (int32_t)i;
     spot.resize(ns);
-    // every shared-memory word a spot's blocks read: [row * pitch, row * pitch + pitch)
-    const int64_t image = (int64_t)std::max<size_t>(1, L->radii.size()) * pitch;
+    const int n_rows = (int)std::max<size_t>(1, L->radii.size());
     for (int64_t i = 0; i < ns; ++i) {
         const int row = row_of[L->r[i]];
-        const int w = (n_theta - L->t[i] + 31) / 32;
-        const int64_t a = (int64_t)row * pitch + L->t[i];
-        if (row < 0 || a < 0 || a >= image || (int64_t)row * pitch + pitch > image || a >= (1 << 24) || w < 1 || w > 63)
+        const int t = L->t[i];
+        const int w = (n_theta - t + 31) / 32;
+        if (row < 0 || row >= n_rows || row >= 8192 || t < 0 || t >= n_theta || t >= 2048 || w < 1 || w > 63)
             return fail(TM_ERR_INVALID_ARG, "tm_load_library: internal layout check failed for spot %lld",
                         (long long)i);
-        spot[i].x = (int32_t)a | (w << 24);
+        spot[i].x = t | (row << 11) | (w << 24);
         memcpy(&spot[i].y, &L->I[i], 4);
     }
     return TM_OK;
@@ -963,7 +961,7 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
     c.n = n;
     c.n_r = L->n_r;
     c.n_theta = L->n_theta;
-    c.pitch = tmgb::sparse_pitch(L->n_theta);
+    c.pitch = 0;
     c.n_libs = 1;
     c.lib[0] = sparse_view(L);
     c.mask[0] = mask_dev;
@@ -1118,7 +1116,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             c.n = m;
             c.n_r = n_r;
             c.n_theta = n_theta;
-            c.pitch = tmgb::sparse_pitch(n_theta);
+            c.pitch = 0;
             c.max_rad = max_rad;
             c.pattern_counter = pcount;
             c.n_libs = n_libs;

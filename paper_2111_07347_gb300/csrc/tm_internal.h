@@ -17,10 +17,9 @@ void set_last_error(const char* msg);
 
 // ------------------------------------------------------------------ device library views
 // Sparse templates in CSR.  The sparse kernel keeps only the library's distinct spot
-// radii (radii[0..n_rad)) as rows of its shared-memory polar image, row pitch
-// sparse_pitch(n_theta).  spot[i].x packs the shared-memory address of the spot: bits
-// 0..23 = rho * pitch + t with rho the spot's row in radii[], bits 24..31 =
-// w = ceil((n_theta - t) / 32), the first 32-wide shift block whose columns wrap past
+// radii (radii[0..n_rad)) as rows of its shared-memory polar image.  spot[i].x packs
+// bits 0..10 = t (angle column), bits 11..23 = rho (the spot's row in radii[]), bits 24..29
+// = w = ceil((n_theta - t) / 32), the first 32-wide shift block whose columns wrap past
 // n_theta.  spot[i].y = float bits of the intensity.
 struct SparseLib {
     const int32_t* off;        // [K + 1]
@@ -71,7 +70,7 @@ struct SparseCall {
     const float* pnorm;        // [n]
     int64_t n;
     int n_r, n_theta;
-    int pitch;                          // sparse_pitch(n_theta)
+    int pitch;                          // set by launch_sparse (layout row pitch)
     int max_rad;                        // largest n_rad of the libraries (shared-memory rows)
     int* pattern_counter;               // device int, zeroed by the launcher
     int n_libs;
@@ -85,9 +84,10 @@ struct SparseCall {
     int threads;                        // block size: 128, 256 or 512 (0 = 256)
 };
 
-// Shared-memory bytes the sparse kernel needs (0 when unsupported).
-size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n);
-int sparse_pitch(int n_theta);
+// Shared-memory bytes the sparse kernel needs (0 when unsupported), the layout it uses
+// (wrap-free rows when they fit comfortably) and its row pitch.
+size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, bool* wrap_free = nullptr, int* pitch = nullptr);
+int sparse_pitch(int n_theta, bool wrap_free);
 cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);
 
 // ------------------------------------------------------------------ BF16 tensor-core path

@@ -161,7 +161,7 @@ extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* par
                 c.n = n;
                 c.n_r = n_r;
                 c.n_theta = n_theta;
-                c.pitch = tmgb::sparse_pitch(n_theta);
+                c.pitch = 0;
                 c.max_rad = view.n_rad;
                 c.pattern_counter = (int*)(scratch + o_count);
                 c.n_libs = 1;

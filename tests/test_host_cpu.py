@@ -126,18 +126,20 @@ def _round_nb(nb):
         else 24 if nb <= 24 else 32
 
 
-def _pitch(n_theta):
-    """Row pitch of the sparse kernel's shared-memory rows (n_theta + 32, and at least
-    32 x the widest rounded block count)."""
-    return max(n_theta + 32, 32 * _round_nb((n_theta + 31) // 32))
+def _pitch(n_theta, wrap_free):
+    """Row pitch of the sparse kernel's shared-memory rows: wrap-free rows hold n_theta + 32 NB
+    columns (NB the widest rounded shift-block count); wrapped rows n_theta + 32 columns and at
+    least 32 NB."""
+    nb = _round_nb((n_theta + 31) // 32)
+    return n_theta + 32 * nb if wrap_free else max(n_theta + 32, 32 * nb)
 
 
 @pytest.mark.parametrize("which", ["random", "fcc", "hcp", "odd"])
 def test_sparse_layout_reads_stay_in_bounds(lib, which):
     """Replay the sparse kernel's shared-memory indexing on the CPU for every spot, lane and
-    shift block: the packed word decodes to the spot's row among the library's distinct radii
-    and its column; every address stays inside that row's padded span; the word read equals
-    the polar sample at (t + s) mod n_theta for the lane's shift s."""
+    shift block, in both row layouts: the packed word decodes to the spot's angle column and
+    its row among the library's distinct radii; every address stays inside that row; the word
+    read equals the polar sample at (t + s) mod n_theta for the lane's shift s."""
     if which == "random":
         ts, _, _ = synth.tiny_workload(n_side=1)
         n_r, n_theta = 60, 180
@@ -149,23 +151,24 @@ def test_sparse_layout_reads_stay_in_bounds(lib, which):
         n_r, n_theta = 128, 360
     h = tmgb.tm_library_prepare_host(ts, n_r, n_theta)
     radii = np.unique(h["r"])
-    pitch = _pitch(n_theta)
     word = h["packed"].astype(np.int64) & 0xFFFFFFFF
-    a = word & 0xFFFFFF
+    t = word & 0x7FF
+    row = (word >> 11) & 0x1FFF
     w = word >> 24
-    row, col = a // pitch, a % pitch
     assert np.array_equal(radii[row], h["r"])
-    assert np.array_equal(col, h["t"])
+    assert np.array_equal(t, h["t"])
     assert np.array_equal(w, (n_theta - h["t"] + 31) // 32)
     lanes = np.arange(32)
-    for k in range(h["info"]["n_templates"]):
-        S = n_theta // h["order"][k]
-        nb = _round_nb((S + 31) // 32)
-        for i in range(h["offsets"][k], h["offsets"][k + 1]):
-            for b in range(nb):
-                base = a[i] + 32 * b - (n_theta if b >= w[i] else 0)
-                addr = base + lanes
-                lo, hi = row[i] * pitch, row[i] * pitch + pitch
-                assert np.all((addr >= lo) & (addr < hi)), (k, i, b)
-                # column c of a row holds P'[c mod n_theta]
-                assert np.array_equal((addr - lo) % n_theta, (h["t"][i] + 32 * b + lanes) % n_theta)
+    for wrap_free in (True, False):
+        pitch = _pitch(n_theta, wrap_free)
+        for k in range(h["info"]["n_templates"]):
+            S = n_theta // h["order"][k]
+            nb = _round_nb((S + 31) // 32)
+            for i in range(h["offsets"][k], h["offsets"][k + 1]):
+                lo = row[i] * pitch
+                for b in range(nb):
+                    col = t[i] + 32 * b - (n_theta if (not wrap_free and b >= w[i]) else 0) + lanes
+                    assert np.all((col >= 0) & (col < pitch)), (wrap_free, k, i, b)
+                    # column c of a row holds P'[c mod n_theta]
+                    assert np.array_equal(col % n_theta, (t[i] + 32 * b + lanes) % n_theta)
+                    assert lo + col.max() < len(radii) * pitch
