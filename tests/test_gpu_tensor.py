@@ -52,18 +52,24 @@ def _check_prescore(ctx, ts, frames, n_r, n_theta, kcs=(64, 256), fraction=1.0):
     pre = pre.cpu().numpy().astype(np.float64)
     P = O.polar(frames, n_r, n_theta)
     act = np.ones((frames.shape[0], lib.K), bool)
+    sc = None
     if fraction < 1.0:
-        act, _ = O.prefilter(P, lib, fraction)
+        act, sc = O.prefilter(P, lib, fraction)
+    keep = O.keep_count(fraction, lib.K)
     q, s = O.scores(P, lib, act)
     worst = 0.0
     rec = {kc: 0 for kc in kcs}
     ks = np.arange(lib.K)
     for p in range(frames.shape[0]):
         scored = ~np.isnan(pre[p])
-        # the GPU's pre-filter may differ from the oracle's only at threshold near-ties
         assert scored.sum() == act[p].sum()
         both = scored & act[p]
-        assert both.sum() >= act[p].sum() - 2
+        if sc is not None:
+            # the GPU's pre-filter may differ from the oracle's only among templates whose
+            # FP64 pre-filter score ties with the keep threshold to 1e-5
+            thr = np.sort(sc[p])[::-1][keep - 1]
+            diff = np.flatnonzero(scored != act[p])
+            assert np.all(np.abs(sc[p, diff] - thr) <= 1e-5 * max(abs(thr), 1e-3)), (p, diff.size)
         q_top = q[p][act[p]].max()
         err = np.abs(pre[p][both] - q[p][both])
         worst = max(worst, float(err.max() / max(abs(q_top), 1e-30)))
