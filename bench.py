@@ -35,6 +35,7 @@ METRIC = "patterns/s indexed, BF16-TC vs FP32 sparse at ≥99.5% top-1 match; p9
 WORKLOAD = ("single-phase scan: 16384 x 256x256 u16 frames, FCC 0.5 deg (+mirrors), polar 128x360, "
             "prefilter 50%, top-5; BF16 tensor-core pre-score + FP32 rescore of the top-256 vs FP32 sparse")
 N_R, N_THETA, TOP_N, PREFILTER, RESCORE_K = 128, 360, 5, 0.5, 256
+E2E_CHUNK = 2048                  # patterns per chunk of the host-buffer entry point (tm_index_patterns_host)
 MATCH_SAMPLE = 512
 # tensor-core work per (pattern, scored template): 2 x 180 shifts x (182 + 180) frequency terms
 DENSE_FLOPS_PER_PAIR = 2 * 180 * (182 + 180)
@@ -136,13 +137,16 @@ def kernel_sha(path: str) -> str:
 
 
 def traffic_from_profiles(kernel_file: str, key: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per full-size launch from the committed ncu summary `profiles/traffic.txt`
+    (lines: kernel, sha256[:16] of its source file, bytes, note), if it was taken on this
+    source; None otherwise."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
-        d = json.load(open(p))[key]
-        if d["source_sha"] == kernel_sha(kernel_file):
-            return d["dram_bytes_per_launch_full"]
-    except Exception:
+        for line in open(p):
+            f = line.split()
+            if len(f) >= 3 and not f[0].startswith("#") and f[0] == key and f[1] == kernel_sha(kernel_file):
+                return float(f[2])
+    except OSError:
         pass
     return None
 
@@ -366,34 +370,31 @@ def run_ours(args):
     ms, prof, clk, launches_per_step = res[head]
     value = world * n / (ms / 1e3)
 
-    # ---- end to end: pinned host frames -> device -> index -> hits back to the host
+    # ---- end to end through the host-buffer entry point (tm_index_patterns_host): pinned host
+    # frames -> device (chunked, copies overlapping the previous chunk's kernels) -> hits back
+    # in pinned host memory; host wall clock around the synchronous call
     host, host_np = pinned_u16(scan.frames)
     host_out = torch.empty((1, n, TOP_N, 5), dtype=torch.int32).pin_memory()
     e2e_steps = max(2, args.steps // 2)
-    buf = torch.empty_like(frames_d)
     kw_head = kw_bf16 if head == "bf16" else kw_fp32
 
     def e2e_step():
-        buf.copy_(host, non_blocking=True)
-        ctx.index(buf, lid, out=outs[head], **kw_head)
-        host_out.copy_(outs[head], non_blocking=True)
+        ctx.index_host(host, lid, out=host_out, chunk=E2E_CHUNK, **kw_head)
 
     e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
-    a1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = a0.elapsed_time(a1) / e2e_steps
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "patterns/s", "ms_per_step": e2e_ms, "path": head,
+           "api": "tm_index_patterns_host", "chunk_patterns": E2E_CHUNK,
            "h2d_bytes_per_step": int(scan.frames.nbytes), "d2h_bytes_per_step": int(host_out.numel() * 4)}
 
     sm = torch.cuda.get_device_properties(local).multi_processor_count

@@ -238,6 +238,20 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                       const int32_t* lib_ids, int32_t n_libs, tm_hit* out_dev,
                       tm_stats* stats, void* stream);
 
+/* The whole path (as tm_index_patterns) for frames and results in HOST memory.  The paper's
+ * GPU implementation moves each image to the device before indexing it (Section 2.2); here
+ * the batch is cut into chunks of `chunk` patterns (0: 4096) that alternate between two
+ * streams owned by the context, so the host->device copy of one chunk overlaps the kernels
+ * of the previous one, and each chunk's hits are copied back as soon as they are ready.
+ * frames_host [n][H][W] (dtype), centres_host [n][2] float or NULL, out_host
+ * [n_libs][n][top_n] tm_hit.  Pass page-locked host memory for the overlap (pageable memory
+ * works, with the copies serialised by the driver).  Synchronous: returns when out_host is
+ * complete.  One host-buffer call at a time per context (later calls wait).  stats (nullable)
+ * receives the totals.  Errors as tm_index_patterns. */
+int tm_index_patterns_host(tm_ctx* ctx, const tm_index_params* params, const void* frames_host, int32_t dtype,
+                           int64_t n, int32_t H, int32_t W, const float* centres_host, const int32_t* lib_ids,
+                           int32_t n_libs, tm_hit* out_host, int64_t chunk, tm_stats* stats);
+
 /* Per-stage device time, measured with CUDA events recorded on the stream each kernel
  * is launched on (around every launch of the stage). */
 enum {

@@ -13,11 +13,13 @@
 // 128 x 192 x 384 BF16 GEMM per 128 templates gives all n shifts (E and O live in TMEM
 // columns [0, 192) and [192, 384)).
 //
-// CTA layout (one per SM, persistent over patterns; 288 threads):
-//   warps 0-3  producers: thread i builds row i (one template) of G, 64 K-elements per
-//              chunk, in BF16, into a 2-slot shared-memory ring (128B-swizzled K-major);
-//   warp  8    TMEM allocation and the single MMA-issuing thread;
-//   warps 4-7  epilogue: tcgen05.ld of E and O, max over all n shifts, one pre-score
+// CTA layout (one per SM, persistent over patterns; 672 threads):
+//   warps 0-15 producers: four threads per row (one template) of G, eight frequencies each
+//              per 64-element chunk, in BF16, into a 2-slot shared-memory ring
+//              (128B-swizzled K-major); four warps per scheduler hide the latency of the
+//              twiddle recurrence;
+//   warp  20   TMEM allocation and the single MMA-issuing thread;
+//   warps 16-19 epilogue: tcgen05.ld of E and O, max over all n shifts, one pre-score
 //              per (pattern, template) written to global memory (the candidates are
 //              then chosen by the exact radix select and rescored in FP32).
 // The basis (w_m / n) cos / -sin for both halves stays resident in shared memory.
@@ -40,7 +42,11 @@ constexpr int kChunk = 64;                 // K per ring slot (one 128-byte swiz
 constexpr int kChunks = kKB / kChunk;      // 6
 constexpr int kSlotBytes = kRows * 128;    // 16 KB
 constexpr int kBasisChunkBytes = kN * 128; // 24 KB
-constexpr int kThreads = 288;
+constexpr int kProdWarps = 16;             // 4 threads per row, 8 frequencies each
+constexpr int kProdThreads = kProdWarps * 32;
+constexpr int kEpiWarp0 = kProdWarps;      // 4 epilogue warps
+constexpr int kMmaWarp = kProdWarps + 4;
+constexpr int kThreads = (kMmaWarp + 1) * 32;
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -58,9 +64,7 @@ __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
-    uint64_t st;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(addr) : "memory");
-    (void)st;
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(addr) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
@@ -147,10 +151,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ bool better(float qa, int ka, float qb, int kb) {
-    return qa > qb || (qa == qb && ka < kb);
-}
-
 struct Smem {
     uint8_t* basis;       // kChunks x [kN rows x 128 B], swizzled
     uint8_t* ring;        // 2 x [kRows x 128 B], swizzled
@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
     for (int i = threadIdx.x; i < n_theta; i += blockDim.x) s.tw[i] = c.twiddle[i];
     for (int i = threadIdx.x; i < c.n_r; i += blockDim.x) s.rmap[i] = (int16_t)c.rmap[i];
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&s.bar[0]), kRows);
-        mbar_init(smem_u32(&s.bar[1]), kRows);
+        mbar_init(smem_u32(&s.bar[0]), kProdThreads);
+        mbar_init(smem_u32(&s.bar[1]), kProdThreads);
         mbar_init(smem_u32(&s.bar[2]), 1);
         mbar_init(smem_u32(&s.bar[3]), 1);
         mbar_init(bar_accf, 1);
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
         *s.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s.tmem_base)),
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -217,16 +217,17 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
     tc_fence_after();
     const uint32_t tmem = *s.tmem_base;
 
-    if (warp < 4) {
+    if (warp < kProdWarps) {
         // ================================================================ producers
-        const int row = threadIdx.x;
+        const int row = threadIdx.x & (kRows - 1);
+        const int quarter = threadIdx.x >> 7;                    // frequencies 8 q .. 8 q + 7 of a chunk
         uint32_t g = 0;                                         // global chunk counter
         bool stop = false;
         for (int64_t p = blockIdx.x; p < c.n && !stop; p += gridDim.x) {
-            named_bar(1, kRows);                                // previous pattern's P^ no longer read
+            named_bar(1, kProdThreads);                         // previous pattern's P^ no longer read
             const __half2* src = (const __half2*)c.phat + (size_t)p * c.n_rad * c.n_freq;
-            for (int i = row; i < c.n_rad * c.n_freq; i += kRows) s.phat[i] = src[i];
-            named_bar(1, kRows);
+            for (int i = threadIdx.x; i < c.n_rad * c.n_freq; i += kProdThreads) s.phat[i] = src[i];
+            named_bar(1, kProdThreads);
             for (int li = 0; li < c.n_libs && !stop; ++li) {
                 const DenseLib& L = c.lib[li];
                 const int tiles = (c.count[li] + kRows - 1) / kRows;
@@ -242,48 +243,51 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
                     }
                     for (int ch = 0; ch < kChunks; ++ch, ++g) {
                         const uint32_t slot = g & 1u, use = g >> 1;
-                        if (row == 0) {
+                        if (threadIdx.x == 0) {
                             if (!mbar_wait(bar_empty0 + 8 * slot, (use & 1u) ^ 1u, abort_flag)) *abort_flag = 1;
                         }
-                        named_bar(1, kRows);
+                        named_bar(1, kProdThreads);
                         if (*abort_flag) { stop = true; break; }
                         const int part = ch / 3;                   // 0: even m, 1: odd m
-                        const int m0 = 2 * ((ch % 3) * 32) + part;
+                        const int m0 = 2 * ((ch % 3) * 32 + quarter * 8) + part;
                         int nvalid = (H - m0) / 2 + 1;             // frequencies m0 + 2 jj <= H
                         if (m0 > H) nvalid = 0;
-                        if (nvalid > 32) nvalid = 32;
-                        float are[32], aim[32];
+                        if (nvalid > 8) nvalid = 8;
+                        float are[8], aim[8];
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) { are[jj] = 0.0f; aim[jj] = 0.0f; }
-                        for (int i = beg; i < end; ++i) {
-                            const int rt = L.rt[i];
-                            const int r = rt & 0xffff, tt = rt >> 16;
-                            const float I = __int_as_float(L.spot[i].y) * inv_norm;
-                            const __half2* ph = s.phat + (size_t)s.rmap[r] * c.n_freq + m0;
-                            float2 w = s.tw[(int)(((int64_t)m0 * tt) % n_theta)];
-                            w.x *= I;
-                            w.y *= I;
-                            const float2 st = s.tw[(2 * tt) % n_theta];
+                        for (int jj = 0; jj < 8; ++jj) { are[jj] = 0.0f; aim[jj] = 0.0f; }
+                        if (nvalid > 0) {
+                            for (int i = beg; i < end; ++i) {
+                                const int rt = L.rt[i];
+                                const int r = rt & 0xffff, tt = rt >> 16;
+                                const float I = __int_as_float(L.spot[i].y) * inv_norm;
+                                const __half2* ph = s.phat + (size_t)s.rmap[r] * c.n_freq + m0;
+                                float2 w = s.tw[(m0 * tt) % n_theta];
+                                w.x *= I;
+                                w.y *= I;
+                                const float2 st = s.tw[(2 * tt) % n_theta];
 #pragma unroll
-                            for (int jj = 0; jj < 32; ++jj) {
-                                if (jj < nvalid) {
-                                    const float2 pv = __half22float2(ph[2 * jj]);
-                                    are[jj] = fmaf(w.x, pv.x, fmaf(-w.y, pv.y, are[jj]));
-                                    aim[jj] = fmaf(w.x, pv.y, fmaf(w.y, pv.x, aim[jj]));
-                                    const float wx = w.x * st.x - w.y * st.y;
-                                    w.y = fmaf(w.x, st.y, w.y * st.x);
-                                    w.x = wx;
+                                for (int jj = 0; jj < 8; ++jj) {
+                                    if (jj < nvalid) {
+                                        const float2 pv = __half22float2(ph[2 * jj]);
+                                        are[jj] = fmaf(w.x, pv.x, fmaf(-w.y, pv.y, are[jj]));
+                                        aim[jj] = fmaf(w.x, pv.y, fmaf(w.y, pv.x, aim[jj]));
+                                        const float wx = w.x * st.x - w.y * st.y;
+                                        w.y = fmaf(w.x, st.y, w.y * st.x);
+                                        w.x = wx;
+                                    }
                                 }
                             }
                         }
                         uint8_t* dst = s.ring + slot * kSlotBytes + row * 128;
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
+                        for (int h = 0; h < 2; ++h) {
+                            const int q = 2 * quarter + h;              // 16-byte chunk of the row
                             uint4 v;
-                            __nv_bfloat162 b0 = __floats2bfloat162_rn(are[4 * q + 0], aim[4 * q + 0]);
-                            __nv_bfloat162 b1 = __floats2bfloat162_rn(are[4 * q + 1], aim[4 * q + 1]);
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(are[4 * q + 2], aim[4 * q + 2]);
-                            __nv_bfloat162 b3 = __floats2bfloat162_rn(are[4 * q + 3], aim[4 * q + 3]);
+                            __nv_bfloat162 b0 = __floats2bfloat162_rn(are[4 * h + 0], aim[4 * h + 0]);
+                            __nv_bfloat162 b1 = __floats2bfloat162_rn(are[4 * h + 1], aim[4 * h + 1]);
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(are[4 * h + 2], aim[4 * h + 2]);
+                            __nv_bfloat162 b3 = __floats2bfloat162_rn(are[4 * h + 3], aim[4 * h + 3]);
                             v.x = *(uint32_t*)&b0;
                             v.y = *(uint32_t*)&b1;
                             v.z = *(uint32_t*)&b2;
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
                 }
             }
         }
-    } else if (warp == 8) {
+    } else if (warp == kMmaWarp) {
         // ================================================================ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(kRows, kN);
@@ -339,8 +343,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
             }
         }
     } else {
-        // ================================================================ epilogue (warps 4-7)
-        const int ew = warp - 4;
+        // ================================================================ epilogue (warps 16-19)
+        const int ew = warp - kEpiWarp0;
         const int row = ew * 32 + lane;
         const uint32_t tbase = tmem + ((uint32_t)(ew * 32) << 16);
         uint32_t tt = 0;
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
     __syncthreads();
     tc_fence_after();
     if (*abort_flag && threadIdx.x == 0) atomicOr(c.error, 1u);
-    if (warp == 8) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }

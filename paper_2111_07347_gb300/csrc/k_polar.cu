@@ -4,38 +4,113 @@
 // the image norm sqrt(sum P'^2) of Eq. 1 and the azimuthal sums R_P[j] used by the
 // pre-filter (Section 2.2, Fig. 3).
 //
-// One CTA per pattern (grid-stride).  Thread k owns polar column k; rows are walked in
-// order, so the writes of a row are coalesced.  Tap positions and the fractions fx, 1-fx,
-// fy, 1-fy come from a table built on the host in double precision for the call's centre
-// (storing 1-fx avoids the cancellation of forming it in float when fx is near 1), so
-// each bilinear weight is within a few float ulps of its exact value.  Reductions run in a fixed order: the result does not
-// depend on the grid size or on other patterns of the batch.
+// One CTA per pattern (grid-stride over patterns).  The CTA's threads form R row groups of
+// `cols` threads (a multiple of 32); thread (g, k0) owns polar columns k0, k0 + cols, ... of
+// rows g, g + R, ..., four rows at a time, so the stores of a row are coalesced and four
+// samples are in flight per thread.
+//
+// Staged form (frame fits in shared memory): the CTA first copies the frame into shared
+// memory with 16-byte global loads; rows are padded to an odd number of 32-bit words, so
+// samples on an arc (same x, different y) fall in different banks.  Otherwise the taps
+// are read from global memory.
+//
+// Tap positions and bilinear fractions come from a table built on the host in double
+// precision for the call's centre.  The fractions are stored as 23-bit fixed point q, so
+// that both weights come out of float arithmetic exactly: with y = 1 + q 2^-23 (formed by
+// bit assembly), fx = y - 1 and 1 - fx = 2 - y, both exact; each weight is then within
+// 2^-24 of the double-precision value.  A sample whose four taps are all inside the
+// frame takes a fast path with one bounds test and the subtraction applied once
+// (the weights sum to exactly 1); edge samples test each tap (zero outside).
+// For u16 frames the gamma of the pixel values below 4096 (all of them at the counts of an
+// electron diffraction pattern) is tabulated once per CTA in shared memory, g(v) - c from
+// the same correctly rounded sqrtf / powf, so a tap is one table read; larger values are
+// computed directly.
+// Reductions run in a fixed order: the result does not depend on the grid size or on
+// other patterns of the batch.
+#include <math.h>
+
+#include <algorithm>
+
 #include "tm_internal.h"
 
 namespace tmgb {
 namespace {
 
-struct Gamma {
-    int mode;            // 0: sqrt (gamma = 0.5), 1: identity, 2: powf
-    float g, sub;
-    __device__ __forceinline__ float operator()(float v) const {
-        v = fmaxf(v, 0.0f);
-        float r = mode == 0 ? sqrtf(v) : (mode == 1 ? v : powf(v, g));
-        return r - sub;
-    }
-};
+constexpr double kPi = 3.14159265358979323846;
 
-template <typename T>
-__device__ __forceinline__ float tap(const T* frame, int H, int W, int x, int y, const Gamma& gm) {
-    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return 0.0f;  // zero outside
-    return gm((float)__ldg(frame + (size_t)y * W + x));
+constexpr int kLut = 4096;                  // u16 values with a tabulated gamma
+
+// Gamma without the subtraction (negative inputs clamp to 0).  MODE 0: v^0.5 (correctly
+// rounded sqrtf), 1: v, 2: v^g (powf).
+template <int MODE>
+__device__ __forceinline__ float gamma_of(float v, float g) {
+    v = fmaxf(v, 0.0f);
+    if (MODE == 1) return v;
+    if (MODE == 0) return sqrtf(v);
+    return powf(v, g);
 }
 
-// The same tap from a frame staged in shared memory.
-template <typename T>
-__device__ __forceinline__ float tap(T* frame, int H, int W, int x, int y, const Gamma& gm) {
-    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return 0.0f;
-    return gm((float)frame[y * W + x]);
+template <bool SMEM, typename T>
+__device__ __forceinline__ T load_px(const T* p) {
+    if (SMEM) return *p;
+    return __ldg(p);
+}
+
+// g(v) - sub of one raw pixel.  u16: from the table lut[v] = g(v) - sub (filled with the same
+// functions), computed directly for v >= kLut.
+template <int MODE>
+__device__ __forceinline__ float tap_value(uint16_t v, const float* lut, float g, float sub) {
+    return v < kLut ? lut[v] : gamma_of<MODE>((float)v, g) - sub;
+}
+template <int MODE>
+__device__ __forceinline__ float tap_value(float v, const float* lut, float g, float sub) {
+    return gamma_of<MODE>(v, g) - sub;
+}
+
+__device__ __forceinline__ bool all_in_lut(uint16_t a, uint16_t b, uint16_t c, uint16_t d) {
+    return ((a | b | c | d) & ~(kLut - 1)) == 0;
+}
+__device__ __forceinline__ bool all_in_lut(float, float, float, float) { return false; }
+
+// Weights (f, 1 - f) from the 23-bit fixed-point fraction q (q < 2^23): both exact.
+__device__ __forceinline__ void fixed_weights(uint32_t q, float& f, float& g) {
+    const float y = __uint_as_float(0x3F800000u | q);       // 1 + q 2^-23
+    f = y - 1.0f;
+    g = 2.0f - y;
+}
+
+// Bilinear sample of the gamma-corrected, subtracted frame at (x0 + fx, y0 + fy); the frame
+// has row pitch `pitch` elements; taps outside [0, W) x [0, H) contribute zero.
+template <typename T, int MODE, bool SMEM>
+__device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int W, int x0, int y0, float fx,
+                                          float gx, float fy, float gy, const float* lut, float g, float sub) {
+    if ((unsigned)x0 < (unsigned)(W - 1) && (unsigned)y0 < (unsigned)(H - 1)) {
+        const T* p = frame + y0 * pitch + x0;
+        const T a = load_px<SMEM>(p), b = load_px<SMEM>(p + 1);
+        const T c = load_px<SMEM>(p + pitch), d = load_px<SMEM>(p + pitch + 1);
+        float v00, v10, v01, v11;
+        if (all_in_lut(a, b, c, d)) {
+            v00 = lut[(int)a];
+            v10 = lut[(int)b];
+            v01 = lut[(int)c];
+            v11 = lut[(int)d];
+        } else {
+            v00 = tap_value<MODE>(a, lut, g, sub);
+            v10 = tap_value<MODE>(b, lut, g, sub);
+            v01 = tap_value<MODE>(c, lut, g, sub);
+            v11 = tap_value<MODE>(d, lut, g, sub);
+        }
+        return gy * (gx * v00 + fx * v10) + fy * (gx * v01 + fx * v11);
+    }
+    float v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int x = x0 + (t & 1), y = y0 + (t >> 1);
+        v[t] = 0.0f;
+        if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H)
+            v[t] = tap_value<MODE>(load_px<SMEM>(frame + y * pitch + x), lut, g, sub);
+    }
+    return gy * (gx * v[0] + fx * v[1]) + fy * (gx * v[2] + fx * v[3]);
 }
 
 // Tap of a sample at offset (dx, dy) = (r cos theta, r sin theta) from a per-pattern centre
@@ -57,169 +132,157 @@ __device__ __forceinline__ void centre_tap(float c, float hi, float lo, int& i0,
     g = (1.0f - fh) - fl;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024)
-polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
-             const int32_t* __restrict__ txy, const float4* __restrict__ tw, Gamma gm, int n_r, int n_theta,
+// Sum of a[u] over the 32 lanes for four rows u at once (6 shuffles instead of 20): after
+// the exchange the lanes 8u hold the total of row u.  Fixed order: deterministic.
+__device__ __forceinline__ float warp_sum4(const float a[4], int lane) {
+    const bool hi = lane & 16;
+    const float b0 = (hi ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, hi ? a[0] : a[2], 16);
+    const float b1 = (hi ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, hi ? a[1] : a[3], 16);
+    const bool h8 = lane & 8;
+    float c = (h8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h8 ? b0 : b1, 8);
+    c += __shfl_xor_sync(0xffffffffu, c, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;                                   // row (lane >> 3) when (lane & 7) == 0
+}
+
+// One polar sample (table entry idx): tap position and weights from the fixed table, or
+// from the per-pattern centre plus the offset table.
+template <typename T, int MODE, bool STAGED, bool CENTRES>
+__device__ __forceinline__ float sample(const T* frame, int pitch, int H, int W, int idx,
+                                       const int32_t* __restrict__ txy, const uint2* __restrict__ tq,
+                                       const float4* __restrict__ toff, float2 cen, const float* lut, float g,
+                                       float sub) {
+    int x0, y0;
+    float fx, gx, fy, gy;
+    if (CENTRES) {
+        const float4 o = __ldg(toff + idx);                      // dx hi, dx lo, dy hi, dy lo
+        centre_tap(cen.x, o.x, o.y, x0, fx, gx);
+        centre_tap(cen.y, o.z, o.w, y0, fy, gy);
+    } else {
+        const int xy = __ldg(txy + idx);
+        const uint2 q = __ldg(tq + idx);
+        x0 = (int)(int16_t)(xy & 0xffff);
+        y0 = xy >> 16;
+        fixed_weights(q.x, fx, gx);
+        fixed_weights(q.y, fy, gy);
+    }
+    return bilinear<T, MODE, STAGED>(frame, pitch, H, W, x0, y0, fx, gx, fy, gy, lut, g, sub);
+}
+
+constexpr int kMaxThreads = 768;            // 80 registers per thread at one CTA per SM
+
+template <typename T, int MODE, bool STAGED, bool CENTRES>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, const int32_t* __restrict__ txy,
+             const uint2* __restrict__ tq, float g, float sub, int n_r, int n_theta, int R,
              const uint8_t* __restrict__ keep_row, float* __restrict__ polar, float* __restrict__ pnorm,
              float* __restrict__ radial, const float2* __restrict__ centres, const float4* __restrict__ toff) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int cols = blockDim.x / R;                     // threads per row group (multiple of 32)
+    const int grp = threadIdx.x / cols, k0 = threadIdx.x - grp * cols;
     const int nw = blockDim.x >> 5;
-    float* part = smem;                         // [n_r][nw] row partial sums
-    float* red = smem + (size_t)n_r * nw;       // [blockDim] norm partials
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int U = 4;                        // rows in flight per thread
+    const size_t fbytes = STAGED ? (size_t)H * pitch * sizeof(T) : 0;
+    constexpr bool kHasLut = sizeof(T) == 2;
+    T* sF = (T*)smem_raw;
+    float* lut = (float*)(smem_raw + ((fbytes + 15) & ~(size_t)15));   // [kLut] for u16 frames
+    float* part = lut + (kHasLut ? kLut : 0);                           // [n_r][nw]
+    float* red = part + (size_t)n_r * nw;                               // [blockDim]
+    if (kHasLut) {
+        for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut[i] = gamma_of<MODE>((float)i, g) - sub;
+        __syncthreads();
+    }
+    const int my_rows = grp < n_r ? (n_r - grp + R - 1) / R : 0;        // rows grp, grp + R, ...
+    const int rstride = R * n_theta;                                    // table step between them
 
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
-        const T* frame = frames + (size_t)p * H * W;
-        float* out = polar + (size_t)p * n_r * n_theta;
-        float2 cen = make_float2(0.0f, 0.0f);
-        if (centres) cen = __ldg(centres + p);
-        float s2 = 0.0f, c2 = 0.0f;             // Kahan sum of P'^2 for this thread
-        for (int j0 = 0; j0 < n_r; j0 += U) {
-            float rowsum[U];
+        const T* gframe = frames + (size_t)p * H * W;
+        const T* frame = gframe;
+        if (STAGED) {
+            __syncthreads();                             // previous pattern's reads are done
+            const bool vec = (((uintptr_t)gframe) & 15) == 0 && (W * sizeof(T)) % 16 == 0;
+            if (vec) {
+                const int vr = (int)(W * sizeof(T) / 16);           // 16-byte vectors per row
+                const int nv = H * vr;
+                const uint4* src = (const uint4*)gframe;
+                constexpr int B = 8;                                // loads in flight per thread
+                for (int i0 = threadIdx.x; i0 < nv; i0 += B * blockDim.x) {
+                    uint4 v[B];
 #pragma unroll
-            for (int u = 0; u < U; ++u) rowsum[u] = 0.0f;
-            for (int k = threadIdx.x; k < n_theta; k += blockDim.x) {
-                float v[U];
+                    for (int b = 0; b < B; ++b) {
+                        const int i = i0 + b * blockDim.x;
+                        if (i < nv) v[b] = __ldg(src + i);
+                    }
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int j = j0 + u;
-                    v[u] = 0.0f;
-                    if (j < n_r) {
-                        const int idx = j * n_theta + k;
-                        int x0, y0;
-                        float4 f;                                   // fx, 1 - fx, fy, 1 - fy
-                        if (centres) {
-                            const float4 o = __ldg(toff + idx);     // dx hi, dx lo, dy hi, dy lo
-                            centre_tap(cen.x, o.x, o.y, x0, f.x, f.y);
-                            centre_tap(cen.y, o.z, o.w, y0, f.z, f.w);
-                        } else {
-                            const int xy = __ldg(txy + idx);
-                            x0 = (int)(int16_t)(xy & 0xffff);
-                            y0 = xy >> 16;
-                            f = __ldg(tw + idx);
+                    for (int b = 0; b < B; ++b) {
+                        const int i = i0 + b * blockDim.x;
+                        if (i < nv) {
+                            const int y = i / vr, xv = i - y * vr;
+                            uint32_t* d = (uint32_t*)(sF + (size_t)y * pitch) + xv * 4;
+                            d[0] = v[b].x;
+                            d[1] = v[b].y;
+                            d[2] = v[b].z;
+                            d[3] = v[b].w;
                         }
-                        const float v00 = tap(frame, H, W, x0, y0, gm);
-                        const float v10 = tap(frame, H, W, x0 + 1, y0, gm);
-                        const float v01 = tap(frame, H, W, x0, y0 + 1, gm);
-                        const float v11 = tap(frame, H, W, x0 + 1, y0 + 1, gm);
-                        v[u] = f.w * (f.y * v00 + f.x * v10) + f.z * (f.y * v01 + f.x * v11);
                     }
                 }
+            } else {
+                for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
+                    const int y = e / W;
+                    sF[(size_t)y * pitch + (e - y * W)] = gframe[e];
+                }
+            }
+            __syncthreads();
+            frame = sF;
+        }
+        float* out = polar + (size_t)p * n_r * n_theta;
+        float2 cen = make_float2(0.0f, 0.0f);
+        if (CENTRES) cen = __ldg(centres + p);
+        const int pf = STAGED ? pitch : W;
+        float s2 = 0.0f, c2 = 0.0f;                      // Kahan sum of P'^2 for this thread
+        for (int b = 0; b < my_rows; b += 4) {           // warp-uniform
+            const int nu = my_rows - b;                  // rows left in this batch (>= 1)
+            const int j0 = grp + R * b;
+            unsigned keep = 0;                           // rows of the batch whose values are stored
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int j = j0 + u;
-                    if (j < n_r) {
-                        if (!keep_row || keep_row[j]) out[j * n_theta + k] = v[u];
+            for (int u = 0; u < 4; ++u)
+                if (u < nu && (!keep_row || keep_row[j0 + R * u])) keep |= 1u << u;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int k = k0; k < n_theta; k += cols) {
+                const int idx0 = j0 * n_theta + k;
+                float v[4];
+                if (nu >= 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = sample<T, MODE, STAGED, CENTRES>(frame, pf, H, W, idx0 + u * rstride, txy, tq, toff,
+                                                                cen, lut, g, sub);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = u < nu ? sample<T, MODE, STAGED, CENTRES>(frame, pf, H, W, idx0 + u * rstride, txy, tq,
+                                                                         toff, cen, lut, g, sub)
+                                      : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u < nu) {
+                        if ((keep >> u) & 1u) out[idx0 + u * rstride] = v[u];
                         const float y = fmaf(v[u], v[u], -c2);
                         const float t = s2 + y;
                         c2 = (t - s2) - y;
                         s2 = t;
-                        rowsum[u] += v[u];
+                        acc[u] += v[u];
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                float r = rowsum[u];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-                if (lane == 0 && j0 + u < n_r) part[(j0 + u) * nw + warp] = r;
-            }
+            const float r = warp_sum4(acc, lane);
+            const int u = lane >> 3;
+            if ((lane & 7) == 0 && u < nu) part[(j0 + R * u) * nw + warp] = r;
         }
         red[threadIdx.x] = s2;
         __syncthreads();
         // fixed-order tree over the block (blockDim is a multiple of 32)
-        for (int w = 1; w < (int)blockDim.x; w <<= 1) {
-            const int i = threadIdx.x;
-            if ((i & (2 * w - 1)) == 0 && i + w < (int)blockDim.x) red[i] += red[i + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0 && pnorm) pnorm[p] = sqrtf(red[0]);
-        if (radial) {
-            for (int j = threadIdx.x; j < n_r; j += blockDim.x) {
-                float s = 0.0f;
-                for (int w = 0; w < nw; ++w) s += part[j * nw + w];
-                radial[(size_t)p * n_r + j] = s;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Staged variant: the CTA first copies the whole frame into shared memory with coalesced
-// 16-byte loads, then every tap is a shared-memory read.  Rows are split over R groups of
-// warps (thread (g, k): rows j = g, g + R, ...), so a CTA has R x 32 ceil(n_theta / 32)
-// threads.  Used when the frame fits in shared memory.
-template <typename T>
-__global__ void __launch_bounds__(1024)
-polar_staged_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
-                    const int32_t* __restrict__ txy, const float4* __restrict__ tw, Gamma gm, int n_r, int n_theta,
-                    int R, const uint8_t* __restrict__ keep_row, float* __restrict__ polar,
-                    float* __restrict__ pnorm, float* __restrict__ radial, const float2* __restrict__ centres,
-                    const float4* __restrict__ toff) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int cols = blockDim.x / R;                     // threads per row group (multiple of 32)
-    const int g = threadIdx.x / cols, k0 = threadIdx.x - g * cols;
-    const int nw = blockDim.x >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t fbytes = (size_t)H * W * sizeof(T);
-    T* sF = (T*)smem_raw;
-    float* part = (float*)(smem_raw + ((fbytes + 15) & ~(size_t)15));   // [n_r][nw]
-    float* red = part + (size_t)n_r * nw;                               // [blockDim]
-
-    for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
-        const T* frame = frames + (size_t)p * H * W;
-        __syncthreads();
-        if ((((uintptr_t)frame) & 15) == 0) {
-            const size_t nv = fbytes / 16;
-            const uint4* src = (const uint4*)frame;
-            uint4* dst = (uint4*)sF;
-            for (size_t i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = __ldg(src + i);
-            for (size_t i = nv * 16 / sizeof(T) + threadIdx.x; i < (size_t)H * W; i += blockDim.x) sF[i] = frame[i];
-        } else {
-            for (size_t i = threadIdx.x; i < (size_t)H * W; i += blockDim.x) sF[i] = frame[i];
-        }
-        __syncthreads();
-        float* out = polar + (size_t)p * n_r * n_theta;
-        float2 cen = make_float2(0.0f, 0.0f);
-        if (centres) cen = __ldg(centres + p);
-        float s2 = 0.0f, c2 = 0.0f;                      // Kahan sum of P'^2 for this thread
-        for (int j = g; j < n_r; j += R) {
-            float rowsum = 0.0f;
-            for (int k = k0; k < n_theta; k += cols) {
-                const int idx = j * n_theta + k;
-                int x0, y0;
-                float4 f;                                // fx, 1 - fx, fy, 1 - fy
-                if (centres) {
-                    const float4 o = __ldg(toff + idx);
-                    centre_tap(cen.x, o.x, o.y, x0, f.x, f.y);
-                    centre_tap(cen.y, o.z, o.w, y0, f.z, f.w);
-                } else {
-                    const int xy = __ldg(txy + idx);
-                    x0 = (int)(int16_t)(xy & 0xffff);
-                    y0 = xy >> 16;
-                    f = __ldg(tw + idx);
-                }
-                const float v00 = tap(sF, H, W, x0, y0, gm);
-                const float v10 = tap(sF, H, W, x0 + 1, y0, gm);
-                const float v01 = tap(sF, H, W, x0, y0 + 1, gm);
-                const float v11 = tap(sF, H, W, x0 + 1, y0 + 1, gm);
-                const float v = f.w * (f.y * v00 + f.x * v10) + f.z * (f.y * v01 + f.x * v11);
-                if (!keep_row || keep_row[j]) out[idx] = v;
-                const float y = fmaf(v, v, -c2);
-                const float t = s2 + y;
-                c2 = (t - s2) - y;
-                s2 = t;
-                rowsum += v;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
-            if (lane == 0) part[j * nw + warp] = rowsum;  // warps of other groups leave theirs for row j
-        }
-        red[threadIdx.x] = s2;
-        __syncthreads();
         for (int w = 1; w < (int)blockDim.x; w <<= 1) {
             const int i = threadIdx.x;
             if ((i & (2 * w - 1)) == 0 && i + w < (int)blockDim.x) red[i] += red[i + w];
@@ -236,76 +299,105 @@ polar_staged_kernel(const T* __restrict__ frames, int64_t n, int H, int W,
                 radial[(size_t)p * n_r + j] = s;
             }
         }
+        if (!STAGED) __syncthreads();                    // part / red reused by the next pattern
     }
 }
 
+template <typename T, int MODE, bool STAGED, bool CENTRES>
+cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab, float g, float sub,
+                       int n_r, int n_theta, int R, int threads, size_t smem, const uint8_t* keep_row, float* polar,
+                       float* pnorm, float* radial, const float2* centres, const float4* offsets, cudaStream_t st) {
+    auto kern = polar_kernel<T, MODE, STAGED, CENTRES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1, dev = 0, sms = 148;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > n) grid = n;
+    kern<<<(int)grid, threads, smem, st>>>(frames, n, H, W, pitch, tab.xy, tab.q, g, sub, n_r, n_theta, R, keep_row,
+                                           polar, pnorm, radial, centres, offsets);
+    return cudaGetLastError();
+}
+
+template <typename T, bool STAGED>
+cudaError_t launch_mode(int mode, const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab,
+                        float g, float sub, int n_r, int n_theta, int R, int threads, size_t smem,
+                        const uint8_t* keep_row, float* polar, float* pnorm, float* radial, const float2* centres,
+                        const float4* offsets, cudaStream_t st) {
+    if (mode == 0)
+        return (centres ? launch_one<T, 0, STAGED, true> : launch_one<T, 0, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
+                                        polar, pnorm, radial, centres, offsets, st);
+    if (mode == 1)
+        return (centres ? launch_one<T, 1, STAGED, true> : launch_one<T, 1, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
+                                        polar, pnorm, radial, centres, offsets, st);
+    return (centres ? launch_one<T, 2, STAGED, true> : launch_one<T, 2, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
+                                    polar, pnorm, radial, centres, offsets, st);
+}
+
+template <typename T>
+cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const PolarTable& tab, int mode, float g,
+                         float sub, int n_r, int n_theta, float* polar, float* pnorm, float* radial, cudaStream_t st,
+                         const uint8_t* keep_row, const float2* centres, const float4* offsets) {
+    const int cols = ((n_theta + 31) / 32) * 32;
+    if (cols <= kMaxThreads) {
+        // staged: rows padded to an odd number of 32-bit words
+        int words = (int)((W * sizeof(T) + 3) / 4);
+        if (words % 2 == 0) ++words;
+        const int pitch = (int)(words * 4 / sizeof(T));
+        const int R = std::max(1, std::min(4, kMaxThreads / cols));
+        const int threads = R * cols;
+        const int nw = threads / 32;
+        const size_t fbytes = ((size_t)H * pitch * sizeof(T) + 15) & ~(size_t)15;
+        const size_t lut = sizeof(T) == 2 ? kLut * sizeof(float) : 0;
+        const size_t smem = fbytes + lut + ((size_t)n_r * nw + threads) * sizeof(float);
+        if (smem <= 200 * 1024)
+            return launch_mode<T, true>(mode, frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem,
+                                        keep_row, polar, pnorm, radial, centres, offsets, st);
+    }
+    const int threads = cols < kMaxThreads ? cols : kMaxThreads;
+    const size_t smem = (sizeof(T) == 2 ? kLut * sizeof(float) : 0) + ((size_t)n_r * (threads / 32) + threads) * sizeof(float);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    return launch_mode<T, false>(mode, frames, n, H, W, W, tab, g, sub, n_r, n_theta, 1, threads, smem, keep_row,
+                                 polar, pnorm, radial, centres, offsets, st);
+}
+
 }  // namespace
+
+void build_polar_taps(int H, int W, int n_r, int n_theta, double dr, double cx, double cy, int32_t* xy, uint2* q) {
+    (void)H;
+    for (int j = 0; j < n_r; ++j) {
+        const double r = j * dr;
+        for (int k = 0; k < n_theta; ++k) {
+            const double th = 2.0 * kPi * k / n_theta;
+            const double x = cx + r * cos(th), y = cy + r * sin(th);
+            double x0 = floor(x), y0 = floor(y);
+            double fx = x - x0, fy = y - y0;
+            int64_t qx = llround(fx * 8388608.0), qy = llround(fy * 8388608.0);
+            if (qx >= 8388608) { qx = 0; x0 += 1.0; }          // fraction rounds up to the next tap
+            if (qy >= 8388608) { qy = 0; y0 += 1.0; }
+            // taps outside [-2, size + 1] contribute zero either way; clamp into int16
+            if (x0 < -2.0 || x0 > (double)W + 1.0) { x0 = std::min(std::max(x0, -2.0), (double)W + 1.0); qx = 0; }
+            if (y0 < -2.0 || y0 > (double)H + 1.0) { y0 = std::min(std::max(y0, -2.0), (double)H + 1.0); qy = 0; }
+            const size_t i = (size_t)j * n_theta + k;
+            xy[i] = (int32_t)((uint32_t)(uint16_t)(int16_t)(int)x0 | ((uint32_t)(int16_t)(int)y0 << 16));
+            q[i] = make_uint2((uint32_t)qx, (uint32_t)qy);
+        }
+    }
+}
 
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
                          cudaStream_t st, const uint8_t* keep_row, const float2* centres, const float4* offsets) {
     if (n <= 0) return cudaSuccess;
-    Gamma gm;
-    gm.mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
-    gm.g = (float)gamma;
-    gm.sub = (float)subtract;
-    const size_t esz = dtype == TM_DTYPE_U16 ? 2 : 4;
-    const size_t fbytes = (size_t)H * W * esz;
-    const int cols = ((n_theta + 31) / 32) * 32;
-    if (cols <= 512) {
-        // staged: frame in shared memory, rows split over R groups of warps
-        const int R = cols <= 256 ? 4 : 2;
-        const int threads = R * cols;
-        const int nw = threads / 32;
-        const size_t smem = ((fbytes + 15) & ~(size_t)15) + ((size_t)n_r * nw + threads) * sizeof(float);
-        if (smem <= 200 * 1024) {
-            cudaError_t e;
-            if (dtype == TM_DTYPE_U16)
-                e = cudaFuncSetAttribute(polar_staged_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            else
-                e = cudaFuncSetAttribute(polar_staged_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            int per_sm = 1;
-            if (dtype == TM_DTYPE_U16)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, polar_staged_kernel<uint16_t>, threads, smem);
-            else
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, polar_staged_kernel<float>, threads, smem);
-            int dev = 0, sms = 148;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-            if (grid > n) grid = n;
-            if (dtype == TM_DTYPE_U16)
-                polar_staged_kernel<uint16_t><<<(int)grid, threads, smem, st>>>(
-                    (const uint16_t*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, R, keep_row, polar, pnorm,
-                    radial, centres, offsets);
-            else
-                polar_staged_kernel<float><<<(int)grid, threads, smem, st>>>(
-                    (const float*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, R, keep_row, polar, pnorm,
-                    radial, centres, offsets);
-            return cudaGetLastError();
-        }
-    }
-    int threads = cols;
-    if (threads > 1024) threads = 1024;
-    const int nw = threads / 32;
-    const size_t smem = ((size_t)n_r * nw + threads) * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t e;
-        if (dtype == TM_DTYPE_U16)
-            e = cudaFuncSetAttribute(polar_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        else
-            e = cudaFuncSetAttribute(polar_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int64_t grid64 = n < 65535 * 16 ? n : 65535 * 16;
-    const int grid = (int)grid64;
+    const int mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
     if (dtype == TM_DTYPE_U16)
-        polar_kernel<uint16_t><<<grid, threads, smem, st>>>((const uint16_t*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial, centres, offsets);
-    else
-        polar_kernel<float><<<grid, threads, smem, st>>>((const float*)frames, n, H, W, tab.xy, tab.w, gm, n_r, n_theta, keep_row, polar, pnorm, radial, centres, offsets);
-    return cudaGetLastError();
+        return launch_typed<uint16_t>((const uint16_t*)frames, n, H, W, tab, mode, (float)gamma, (float)subtract, n_r,
+                                      n_theta, polar, pnorm, radial, st, keep_row, centres, offsets);
+    return launch_typed<float>((const float*)frames, n, H, W, tab, mode, (float)gamma, (float)subtract, n_r, n_theta,
+                               polar, pnorm, radial, st, keep_row, centres, offsets);
 }
 
 }  // namespace tmgb

@@ -61,41 +61,70 @@ __device__ __forceinline__ bool better(float qa, int ka, float qb, int kb) {
     return qa > qb || (qa == qb && ka < kb);
 }
 
+// Adds spot (px, I) to the accumulators: block b of lane L holds shift 32 b + L.  FIRST
+// initialises them instead.  px must be a real spot word: its wrap block w keeps every read
+// inside the spot's row.
+template <int NB, bool WF, bool FIRST>
+__device__ __forceinline__ void add_spot(float (&acc)[NB], const float* __restrict__ sP, int px, float I, int pitch,
+                                         int n_theta, int lane) {
+    const int t = px & 0x7ff;
+    const int row = (px >> 11) & 0x1fff;
+    const float* p1 = sP + row * pitch + t + lane;
+    if (WF) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[b] = FIRST ? I * p1[32 * b] : fmaf(I, p1[32 * b], acc[b]);
+    } else {
+        const int w = (int)((unsigned)px >> 24);
+        const float* p2 = p1 - n_theta;                       // blocks b >= w: wrapped
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float v = (b < w ? p1 : p2)[32 * b];
+            acc[b] = FIRST ? I * v : fmaf(I, v, acc[b]);
+        }
+    }
+}
+
 // Correlation C(s) of one template for all its shifts (warp-collective).  Returns the
 // warp-wide maximum; when it reaches thr_c, *shift_out is the lowest shift attaining it
 // and `resolved` is set.
-template <int NB, bool WF>
+template <int NB, bool WF, bool FULL = false>
 __device__ __forceinline__ float score_template(const float* __restrict__ sP, const SparseLib& L, int beg, int end,
                                                 int S, int n_theta, int pitch, int lane, float thr_c,
                                                 int& shift_out, bool& resolved) {
     float acc[NB];
+    int cnt = min(32, end - beg);
+    if (cnt <= 0) {                                               // no spot on the grid: C = 0, no read
 #pragma unroll
-    for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
-    for (int i0 = beg; i0 < end; i0 += 32) {
-        const int cnt = min(32, end - i0);
-        int2 mine = make_int2(0, 0);
-        if (lane < cnt) mine = __ldg(L.spot + i0 + lane);         // one lane-parallel load
-        for (int j = 0; j < cnt; ++j) {
-            const int px = __shfl_sync(0xffffffffu, mine.x, j);
-            const float I = __int_as_float(__shfl_sync(0xffffffffu, mine.y, j));
-            const int t = px & 0x7ff;
-            const int row = (px >> 11) & 0x1fff;
-            const float* p1 = sP + row * pitch + t + lane;
-            if (WF) {
-#pragma unroll
-                for (int b = 0; b < NB; ++b) acc[b] = fmaf(I, p1[32 * b], acc[b]);
-            } else {
-                const int w = (int)((unsigned)px >> 24);
-                const float* p2 = p1 - n_theta;                   // blocks b >= w: wrapped
-#pragma unroll
-                for (int b = 0; b < NB; ++b) acc[b] = fmaf(I, (b < w ? p1 : p2)[32 * b], acc[b]);
-            }
-        }
+        for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
+        cnt = 0;
     }
+    int2 mine = make_int2(0, 0);
+    if (lane < cnt) mine = __ldg(L.spot + beg + lane);            // one lane-parallel load
+    if (cnt > 0)
+        add_spot<NB, WF, true>(acc, sP, __shfl_sync(0xffffffffu, mine.x, 0),
+                               __int_as_float(__shfl_sync(0xffffffffu, mine.y, 0)), pitch, n_theta, lane);
+    for (int i0 = beg, j = 1;;) {
+        for (; j < cnt; ++j)
+            add_spot<NB, WF, false>(acc, sP, __shfl_sync(0xffffffffu, mine.x, j),
+                                    __int_as_float(__shfl_sync(0xffffffffu, mine.y, j)), pitch, n_theta, lane);
+        i0 += 32;
+        if (i0 >= end) break;
+        cnt = min(32, end - i0);
+        if (lane < cnt) mine = __ldg(L.spot + i0 + lane);
+        j = 0;
+    }
+    // Every lane's block b holds C((32 b + lane) mod Nθ), computed by the same operations as the
+    // shift it repeats (column c of a row holds P'[c mod Nθ]); so for a template slid over all
+    // Nθ shifts (FULL: S == Nθ) the maximum needs no lane mask.  Otherwise shifts >= S are masked.
     float best = -FLT_MAX;
+    if (FULL) {
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
-        if (32 * b + lane < S) best = fmaxf(best, acc[b]);
+        for (int b = 0; b < NB; ++b) best = fmaxf(best, acc[b]);
+    } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (32 * b + lane < S) best = fmaxf(best, acc[b]);
+    }
     resolved = false;
     if (!__any_sync(0xffffffffu, best >= thr_c)) return best;    // cannot enter the top-N
 #pragma unroll
@@ -117,6 +146,8 @@ template <int NBMAX, bool WF>
 __device__ __forceinline__ float score_dispatch(const float* sP, const SparseLib& L, int beg, int end, int S,
                                                 int n_theta, int pitch, int lane, float thr_c, int& s, bool& res) {
     const int nb = (S + 31) >> 5;
+    if (S == n_theta && round_nb(nb) == NBMAX)                 // the common case, tested first
+        return score_template<NBMAX, WF, true>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
     if (nb <= 1) return score_template<1, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
     if (nb <= 2) return score_template<2, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
     if (nb <= 3) return score_template<3, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
@@ -130,7 +161,7 @@ __device__ __forceinline__ float score_dispatch(const float* sP, const SparseLib
 }
 
 template <int NBMAX, bool WF>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(kMaxThreads, NBMAX <= 12 ? 2 : 1)
 sparse_kernel(const SparseCall c) {
     extern __shared__ __align__(16) float smem[];
     const int n_theta = c.n_theta, pitch = c.pitch;
@@ -174,6 +205,8 @@ sparse_kernel(const SparseCall c) {
             float* wq = lq + warp * N;
             int* wk = lk + warp * N;
             int* ws = ls + warp * N;
+            const bool use_thr = !qo && c.hits;
+            float qthr = -INFINITY;                          // the warp's N-th best Q once its list is full
             for (;;) {
                 int wd = 0;
                 if (lane == 0) wd = atomicAdd(counter, 1);
@@ -208,8 +241,8 @@ sparse_kernel(const SparseCall c) {
                     // correlation units, with a margin for the division's rounding) cannot
                     // enter the top-N, so its best shift is not resolved
                     float thr_c = -FLT_MAX;
-                    if (!qo && c.hits && lcnt[warp] >= N && d > 0.0f) {
-                        const float t = wq[N - 1] * d;
+                    if (use_thr && qthr > -INFINITY && d > 0.0f) {
+                        const float t = qthr * d;
                         thr_c = t - fabsf(t) * 1e-6f;
                     }
                     int s = 0;
@@ -236,6 +269,11 @@ sparse_kernel(const SparseCall c) {
                         }
                     }
                     __syncwarp();
+                    if (use_thr) {
+                        float nt = -INFINITY;
+                        if (lane == 0 && lcnt[warp] >= N) nt = wq[N - 1];
+                        qthr = __shfl_sync(0xffffffffu, nt, 0);
+                    }
                 }
             }
             __syncthreads();

@@ -90,7 +90,7 @@ struct Buffer {
 
 struct PolarTableDev {
     int32_t* xy = nullptr;
-    float4* w = nullptr;
+    uint2* q = nullptr;
     size_t bytes = 0;
 };
 
@@ -142,6 +142,9 @@ struct tm_ctx {
     std::map<std::string, int> tuned;
     int tune_override = 0;
     std::string tune_file;
+    // host-buffer entry point: two streams alternate over the chunks of a call
+    cudaStream_t host_streams[2] = {nullptr, nullptr};
+    std::mutex host_mu;            // one host-buffer call at a time per context
     // stage timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -462,35 +465,19 @@ int polar_table(tm_ctx* ctx, int H, int W, int n_r, int n_theta, double dr, doub
     if (it == ctx->tables.end()) {
         const size_t m = (size_t)n_r * n_theta;
         std::vector<int32_t> xy(m);
-        std::vector<float4> wv(m);
-        for (int j = 0; j < n_r; ++j) {
-            const double r = j * dr;
-            for (int k = 0; k < n_theta; ++k) {
-                const double th = 2.0 * kPi * k / n_theta;
-                const double x = cx + r * cos(th), y = cy + r * sin(th);
-                double x0 = floor(x), y0 = floor(y);
-                // taps outside [-2, size] contribute zero either way; clamp to int16
-                x0 = std::min(std::max(x0, -2.0), (double)W + 1.0);
-                y0 = std::min(std::max(y0, -2.0), (double)H + 1.0);
-                double ffx = x - x0, ffy = y - y0;
-                if (ffx < 0.0 || ffx >= 1.0) ffx = 0.0;       // clamped: all taps outside
-                if (ffy < 0.0 || ffy >= 1.0) ffy = 0.0;
-                const int ix = (int)x0, iy = (int)y0;
-                xy[(size_t)j * n_theta + k] = (int32_t)((uint32_t)(uint16_t)(int16_t)ix | ((uint32_t)(int16_t)iy << 16));
-                wv[(size_t)j * n_theta + k] = make_float4((float)ffx, (float)(1.0 - ffx), (float)ffy, (float)(1.0 - ffy));
-            }
-        }
+        std::vector<uint2> q(m);
+        tmgb::build_polar_taps(H, W, n_r, n_theta, dr, cx, cy, xy.data(), q.data());
         PolarTableDev t;
         int rc = dev_alloc(ctx, (void**)&t.xy, m * 4, "polar table");
-        if (!rc) rc = dev_alloc(ctx, (void**)&t.w, m * 16, "polar table");
+        if (!rc) rc = dev_alloc(ctx, (void**)&t.q, m * 8, "polar table");
         if (rc) return rc;
-        t.bytes = m * 20;
+        t.bytes = m * 12;
         TM_CUDA(cudaMemcpy(t.xy, xy.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
-        TM_CUDA(cudaMemcpy(t.w, wv.data(), m * 16, cudaMemcpyHostToDevice), "polar table");
+        TM_CUDA(cudaMemcpy(t.q, q.data(), m * 8, cudaMemcpyHostToDevice), "polar table");
         it = ctx->tables.emplace(key, t).first;
     }
     out->xy = it->second.xy;
-    out->w = it->second.w;
+    out->q = it->second.q;
     return TM_OK;
 }
 
@@ -662,6 +649,88 @@ int library_view(tm_ctx* ctx, int lib_id, int* device, int* num_sms, SparseLib* 
 
 extern "C" {
 
+// Whole path from host buffers: chunks of the batch alternate between two streams, so the
+// host->device copy of one chunk overlaps the kernels of the previous one.
+int tm_index_patterns_host(tm_ctx* ctx, const tm_index_params* params, const void* frames_host, int32_t dtype,
+                           int64_t n, int32_t H, int32_t W, const float* centres_host, const int32_t* lib_ids,
+                           int32_t n_libs, tm_hit* out_host, int64_t chunk, tm_stats* stats) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_host: ctx is NULL");
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000)
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_host: bad shape");
+    if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_host: dtype");
+    if (n_libs < 1 || n_libs > TM_MAX_LIBS || !lib_ids)
+        return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_host: n_libs must be in [1, %d]", TM_MAX_LIBS);
+    if (chunk < 0) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_host: chunk must be >= 0");
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (n == 0) return TM_OK;
+    if (!frames_host || !out_host) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_host: NULL buffer");
+    if (chunk == 0) chunk = 4096;
+    if (chunk > n) chunk = n;
+    std::lock_guard<std::mutex> hl(ctx->host_mu);
+    DeviceGuard g(ctx->device);
+    const size_t esz = dtype == TM_DTYPE_U16 ? 2 : 4;
+    const size_t frame_bytes = (size_t)H * W * esz;
+    const int N = params->top_n;
+    const size_t hit_row = (size_t)N * sizeof(tm_hit);       // one pattern's hits for one library
+    void* dfr[2];
+    void* dcen[2] = {nullptr, nullptr};
+    void* dhit[2];
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (int i = 0; i < 2; ++i) {
+            if (!ctx->host_streams[i])
+                TM_CUDA(cudaStreamCreateWithFlags(&ctx->host_streams[i], cudaStreamNonBlocking), "host streams");
+            cudaStream_t hs = ctx->host_streams[i];
+            rc = workspace(ctx, hs, "host_frames", (size_t)chunk * frame_bytes, &dfr[i]);
+            if (!rc) rc = workspace(ctx, hs, "host_hits", (size_t)n_libs * chunk * hit_row, &dhit[i]);
+            if (!rc && centres_host) rc = workspace(ctx, hs, "host_centres", (size_t)chunk * 8, &dcen[i]);
+            if (rc) return rc;
+        }
+    }
+    int slot = 0;
+    for (int64_t p0 = 0; p0 < n; p0 += chunk, slot ^= 1) {
+        const int64_t m = std::min<int64_t>(chunk, n - p0);
+        cudaStream_t hs = ctx->host_streams[slot];
+        cudaError_t e = cudaMemcpyAsync(dfr[slot], (const char*)frames_host + (size_t)p0 * frame_bytes,
+                                        (size_t)m * frame_bytes, cudaMemcpyHostToDevice, hs);
+        if (e == cudaSuccess && centres_host)
+            e = cudaMemcpyAsync(dcen[slot], centres_host + 2 * p0, (size_t)m * 8, cudaMemcpyHostToDevice, hs);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(TM_ERR_CUDA, "tm_index_patterns_host: copy to the device: %s", cudaGetErrorString(e));
+            break;
+        }
+        tm_stats cs;
+        rc = tm_index_patterns(ctx, params, dfr[slot], dtype, m, H, W, centres_host ? (const float*)dcen[slot] : nullptr,
+                               lib_ids, n_libs, (tm_hit*)dhit[slot], stats ? &cs : nullptr, hs);
+        if (rc) break;
+        // hits [n_libs][m][N] of the chunk -> rows p0.. of out_host [n_libs][n][N]
+        e = cudaMemcpy2DAsync((char*)out_host + (size_t)p0 * hit_row, (size_t)n * hit_row, dhit[slot],
+                              (size_t)m * hit_row, (size_t)m * hit_row, (size_t)n_libs, cudaMemcpyDeviceToHost, hs);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(TM_ERR_CUDA, "tm_index_patterns_host: copy to the host: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (stats) {
+            stats->patterns += cs.patterns;
+            stats->correlations += cs.correlations;
+            stats->templates_scored += cs.templates_scored;
+            stats->launches += cs.launches;
+        }
+    }
+    for (cudaStream_t hs : ctx->host_streams) {
+        cudaError_t e = cudaStreamSynchronize(hs);
+        if (e != cudaSuccess && !rc) {
+            cudaGetLastError();
+            rc = fail(TM_ERR_CUDA, "tm_index_patterns_host: %s", cudaGetErrorString(e));
+        }
+    }
+    return rc;
+}
+
 void tm_index_params_default(tm_index_params* p) {
     if (!p) return;
     p->gamma = 0.5;
@@ -757,7 +826,7 @@ void tm_destroy(tm_ctx* ctx) {
         for (auto& kv : ctx->libs) free_library(ctx, kv.second.get());
         for (auto& kv : ctx->tables) {
             cudaFree(kv.second.xy);
-            cudaFree(kv.second.w);
+            cudaFree(kv.second.q);
         }
         for (auto& kv : ctx->ws)
             if (kv.second.p) cudaFree(kv.second.p);
@@ -772,6 +841,8 @@ void tm_destroy(tm_ctx* ctx) {
             cudaFree(kv.second.keep_row);
         }
         if (ctx->d_error) cudaFree(ctx->d_error);
+        for (cudaStream_t hs : ctx->host_streams)
+            if (hs) cudaStreamDestroy(hs);
         for (auto& kv : ctx->graphs)
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (ctx->ws_event) cudaEventDestroy(ctx->ws_event);

@@ -43,8 +43,11 @@ struct RadialLib {
 // ------------------------------------------------------------------ launchers
 struct PolarTable {            // bilinear taps for one (H, W, n_r, n_theta, dr, cx, cy)
     const int32_t* xy;         // [n_r * n_theta]  x0 | (y0 << 16) as int16 pairs
-    const float4* w;           // [n_r * n_theta]  (fx, 1 - fx, fy, 1 - fy), each rounded from FP64
+    const uint2* q;            // [n_r * n_theta]  (fx, fy) as 23-bit fixed point, < 2^23
 };
+
+// Host: the tap table of PolarTable for centre (cx, cy), in double precision.
+void build_polar_taps(int H, int W, int n_r, int n_theta, double dr, double cx, double cy, int32_t* xy, uint2* q);
 
 // keep_row [n_r] (nullable): rows whose polar values are stored; the norm and the row
 // sums always cover every row.  centres [n] (nullable): per-pattern beam centres, used with

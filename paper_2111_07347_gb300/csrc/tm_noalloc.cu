@@ -34,13 +34,12 @@ namespace {
 
 constexpr size_t kScratchBytes = (size_t)64 << 20;
 constexpr size_t kMaxTaps = (size_t)1 << 20;
-constexpr double kPi = 3.14159265358979323846;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;                      // guards the lookups below and the host staging
 int32_t g_host_xy[kMaxTaps];
-float4 g_host_w[kMaxTaps];
+uint2 g_host_q[kMaxTaps];
 void* g_scratch_dev[128] = {};        // device address of g_scratch, per CUDA device
 
 int fail(int code, const char* msg) {
@@ -100,7 +99,7 @@ extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* par
     if (m > kMaxTaps) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: polar grid larger than 2^20 samples");
     const size_t o_xy = 0;
     const size_t o_w = align256(o_xy + m * 4);
-    const size_t o_polar = align256(o_w + m * 16);
+    const size_t o_polar = align256(o_w + m * 8);
     const size_t o_norm = align256(o_polar + (size_t)n * m * 4);
     const size_t o_count = align256(o_norm + (size_t)n * 4);
     const size_t need = o_count + 256;
@@ -127,29 +126,14 @@ extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* par
         const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
         const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
         int32_t* xy = g_host_xy;
-        float4* wv = g_host_w;
-        for (int j = 0; j < n_r; ++j) {
-            const double r = j * dr;
-            for (int k = 0; k < n_theta; ++k) {
-                const double th = 2.0 * kPi * k / n_theta;
-                const double x = cx + r * cos(th), y = cy + r * sin(th);
-                double x0 = floor(x), y0 = floor(y);
-                x0 = fmin(fmax(x0, -2.0), (double)W + 1.0);
-                y0 = fmin(fmax(y0, -2.0), (double)H + 1.0);
-                double fx = x - x0, fy = y - y0;
-                if (fx < 0.0 || fx >= 1.0) fx = 0.0;
-                if (fy < 0.0 || fy >= 1.0) fy = 0.0;
-                const size_t i = (size_t)j * n_theta + k;
-                xy[i] = (int32_t)((uint32_t)(uint16_t)(int16_t)(int)x0 | ((uint32_t)(int16_t)(int)y0 << 16));
-                wv[i] = make_float4((float)fx, (float)(1.0 - fx), (float)fy, (float)(1.0 - fy));
-            }
-        }
+        uint2* qv = g_host_q;
+        tmgb::build_polar_taps(H, W, n_r, n_theta, dr, cx, cy, xy, qv);
         cudaError_t e = cudaMemcpyAsync(scratch + o_xy, xy, m * 4, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_w, wv, m * 16, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_w, qv, m * 8, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
             tmgb::PolarTable tab;
             tab.xy = (const int32_t*)(scratch + o_xy);
-            tab.w = (const float4*)(scratch + o_w);
+            tab.q = (const uint2*)(scratch + o_w);
             float* polar = (float*)(scratch + o_polar);
             float* pnorm = (float*)(scratch + o_norm);
             e = tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,

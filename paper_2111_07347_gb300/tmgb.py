@@ -116,6 +116,9 @@ _SIGS = {
     "tm_index_patterns": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
                                          ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P,
                                          ctypes.POINTER(tm_stats), _P]),
+    "tm_index_patterns_host": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32,
+                                              ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32,
+                                              _P, ctypes.c_int64, ctypes.POINTER(tm_stats)]),
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
     "tm_prescore": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, _P, _P]),
     "tm_check": (ctypes.c_int, [_P, _P]),
@@ -311,6 +314,15 @@ def tm_index_patterns(ctx, params, frames_ptr, dtype, n, H, W, centres_ptr, lib_
     return {name: getattr(st, name) for name, _ in tm_stats._fields_}
 
 
+def tm_index_patterns_host(ctx, params, frames_ptr, dtype, n, H, W, centres_ptr, lib_ids, out_ptr,
+                           chunk: int = 0) -> dict:
+    ids = (ctypes.c_int32 * len(lib_ids))(*lib_ids)
+    st = tm_stats()
+    _check(library().tm_index_patterns_host(ctx, ctypes.byref(params), frames_ptr, dtype, n, H, W, centres_ptr,
+                                            ids, len(lib_ids), out_ptr, chunk, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in tm_stats._fields_}
+
+
 def tm_profile_enable(ctx, enable: bool) -> None:
     _check(library().tm_profile_enable(ctx, 1 if enable else 0))
 
@@ -432,9 +444,23 @@ def _dtype_code(t):
     raise TypeError("frames must be torch.uint16 or torch.float32")
 
 
+def _host_buffer(a, what):
+    """(address, dtype code or None) of a C-contiguous host numpy array or CPU torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what} must be C-contiguous")
+        code = {np.dtype(np.uint16): TM_DTYPE_U16, np.dtype(np.float32): TM_DTYPE_F32}.get(a.dtype)
+        return a.ctypes.data, code
+    if a.device.type != "cpu" or not a.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous host tensor")
+    import torch
+    code = {torch.uint16: TM_DTYPE_U16, torch.float32: TM_DTYPE_F32}.get(a.dtype)
+    return a.data_ptr(), code
+
+
 def hits_to_numpy(hits) -> np.ndarray:
-    """[..., N, 5] int32 tensor of tm_hit rows -> structured numpy array."""
-    a = hits.detach().cpu().contiguous().numpy()
+    """[..., N, 5] int32 tensor or array of tm_hit rows -> structured numpy array."""
+    a = np.ascontiguousarray(hits) if isinstance(hits, np.ndarray) else hits.detach().cpu().contiguous().numpy()
     return a.view(HIT_DTYPE).reshape(a.shape[:-1])
 
 
@@ -533,6 +559,33 @@ class Context:
     def check(self, stream=None):
         """Synchronise and raise TmError(TM_ERR_TIMEOUT) if a kernel stopped on a bounded wait."""
         tm_check(self.handle, _stream_ptr(stream))
+
+    def index_host(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
+                   path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, chunk=0,
+                   centres=None):
+        """frames [n][H][W] uint16/float32 in host memory (numpy, or a CPU tensor -- pinned for
+        copy/compute overlap) -> hits [n_libs][n][top_n][5] int32 in host memory (`out`, numpy
+        or CPU tensor, else a new numpy array).  Synchronous."""
+        if isinstance(lib_ids, int):
+            lib_ids = [lib_ids]
+        n, H, W = frames.shape
+        fptr, code = _host_buffer(frames, "frames")
+        if code is None:
+            raise TypeError("frames must be uint16 or float32")
+        if out is None:
+            out = np.empty((len(lib_ids), n, top_n, 5), dtype=np.int32)
+        if tuple(out.shape) != (len(lib_ids), n, top_n, 5):
+            raise ValueError("out must have shape [n_libs][n][top_n][5]")
+        optr, _ = _host_buffer(out, "out")
+        cptr = None
+        if centres is not None:
+            cptr, ccode = _host_buffer(centres, "centres")
+            if ccode != TM_DTYPE_F32 or tuple(centres.shape) != (n, 2):
+                raise ValueError("centres must be float32 [n][2]")
+        p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k)
+        self.last_stats = tm_index_patterns_host(self.handle, p, fptr, code, n, H, W, cptr, list(lib_ids), optr,
+                                                 chunk)
+        return out
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
               path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None,
