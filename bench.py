@@ -432,8 +432,21 @@ def run_ours(args):
     stages = {nm: {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                    for k, v in res[nm][1].items()} for nm in res}
     pol_ms = res[head][1].get("polar", (0.0, 1))[0] / args.steps
-    hbm_bytes = n * (256 * 256 * 2 + N_R * N_THETA * 4 + N_R * 4 + 4)
-    stages[head].setdefault("polar", {})["hbm_gbs"] = hbm_bytes / (pol_ms / 1e3) / 1e9 if pol_ms else None
+    # polar stage against HBM: frames read, the library's rows stored (the norm and the
+    # azimuthal sums cover every row but only the used rows are written), sums and norms
+    kept_rows = int(np.unique(ctx.library_export(lid)["r"]).size)
+    hbm_bytes = n * (256 * 256 * 2 + kept_rows * N_THETA * 4 + N_R * 4 + 4)
+    if pol_ms:
+        pol_gbs = hbm_bytes / (pol_ms / 1e3) / 1e9
+        pol_peak = MEASURED.get("hbm_gbs") or 6800.0
+        pol_traffic = traffic_from_profiles(os.path.join(ROOT, "paper_2111_07347_gb300", "csrc", "k_polar.cu"),
+                                            "polar_kernel")
+        stages[head].setdefault("polar", {}).update(
+            {"hbm_gbs": pol_gbs, "roofline": {"bound": "hbm", "kernel": "polar_kernel", "achieved": pol_gbs,
+                                              "peak": pol_peak, "unit": "GB/s", "frac": pol_gbs / pol_peak,
+                                              "algorithmic_bytes_per_launch": hbm_bytes,
+                                              "traffic": pol_traffic * n / 16384 if pol_traffic else None,
+                                              "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"}})
 
     line = {"metric": METRIC, "value": value, "unit": "patterns/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -120,6 +120,13 @@ typedef struct tm_index_params {
  * is on. */
 #define TM_INDEX_GRAPH 1
 
+/* tm_index_params.reserved flag for tests of the failure path: the BF16 tensor-core kernel's
+ * MMA issuer issues nothing, so its producer and epilogue waits run out (about 1 s each);
+ * the kernel records the timeout in the context's device error word, stops its roles,
+ * frees its tensor memory and returns.  tm_check then reports TM_ERR_TIMEOUT; the call's
+ * hits are meaningless; the context stays usable. */
+#define TM_INDEX_TEST_STALL 2
+
 /* One result row.  Rows of a pattern are ordered by (score desc, template asc); when
  * fewer than N templates take part the tail rows have template_index = -1 and
  * score = -inf. */

@@ -17,13 +17,13 @@
 //   warps 0-15 producers: four threads per row (one template) of G, eight frequencies each
 //              per 64-element chunk, in BF16, into a 2-slot shared-memory ring
 //              (128B-swizzled K-major); four warps per scheduler hide the latency of the
-//              twiddle recurrence;
+//              twiddle recurrence; each warp waits for a free slot on its own;
 //   warp  20   TMEM allocation and the single MMA-issuing thread;
 //   warps 16-19 epilogue: tcgen05.ld of E and O, max over all n shifts, one pre-score
 //              per (pattern, template) written to global memory (the candidates are
 //              then chosen by the exact radix select and rescored in FP32).
 // The basis (w_m / n) cos / -sin for both halves stays resident in shared memory.
-// Every mbarrier wait is bounded by the global timer; on timeout the CTA records an error
+// Every mbarrier wait is bounded by the global timer (1 s); on timeout the CTA records an error
 // in a device word, stops its roles uniformly, releases TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -47,7 +47,7 @@ constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kEpiWarp0 = kProdWarps;      // 4 epilogue warps
 constexpr int kMmaWarp = kProdWarps + 4;
 constexpr int kThreads = (kMmaWarp + 1) * 32;
-constexpr unsigned long long kTimeoutNs = 4000000000ull;
+constexpr unsigned long long kTimeoutNs = 1000000000ull;   // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -160,6 +160,8 @@ struct Smem {
     uint64_t* bar;        // full[2], empty[2], acc_full, acc_empty
     uint32_t* tmem_base;
     int* abort_flag;
+    int* prod_stop;       // producers' uniform stop decision, published at pattern boundaries
+    int* epi_stop;        // [2] epilogue's uniform stop decision, by tile parity
 };
 
 // Template row of tile t of (lib, pattern p), or -1 past the survivors.
@@ -181,6 +183,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
     s.bar = (uint64_t*)(((uintptr_t)(s.rmap + c.n_r) + 15) & ~(uintptr_t)15);
     s.tmem_base = (uint32_t*)(s.bar + 6);
     s.abort_flag = (int*)(s.tmem_base + 1);
+    s.prod_stop = s.abort_flag + 1;
+    s.epi_stop = s.prod_stop + 1;
     volatile int* abort_flag = s.abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -223,15 +227,20 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
         const int quarter = threadIdx.x >> 7;                    // frequencies 8 q .. 8 q + 7 of a chunk
         uint32_t g = 0;                                         // global chunk counter
         bool stop = false;
-        for (int64_t p = blockIdx.x; p < c.n && !stop; p += gridDim.x) {
+        for (int64_t p = blockIdx.x; p < c.n; p += gridDim.x) {
+            // all producer warps reach this point (a warp that saw a failed wait skips the rest
+            // of its pattern instead of leaving); thread 0 publishes one stop decision
             named_bar(1, kProdThreads);                         // previous pattern's P^ no longer read
+            if (threadIdx.x == 0) *s.prod_stop = *abort_flag;
+            named_bar(1, kProdThreads);
+            if (*(volatile int*)s.prod_stop) break;
             const __half2* src = (const __half2*)c.phat + (size_t)p * c.n_rad * c.n_freq;
             for (int i = threadIdx.x; i < c.n_rad * c.n_freq; i += kProdThreads) s.phat[i] = src[i];
             named_bar(1, kProdThreads);
-            for (int li = 0; li < c.n_libs && !stop; ++li) {
+            for (int li = 0; li < c.n_libs; ++li) {
                 const DenseLib& L = c.lib[li];
                 const int tiles = (c.count[li] + kRows - 1) / kRows;
-                for (int t = 0; t < tiles && !stop; ++t) {
+                for (int t = 0; t < tiles; ++t) {
                     const int k = row_template(c, li, p, t * kRows + row);
                     int beg = 0, end = 0;
                     float inv_norm = 0.0f;
@@ -243,11 +252,14 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
                     }
                     for (int ch = 0; ch < kChunks; ++ch, ++g) {
                         const uint32_t slot = g & 1u, use = g >> 1;
-                        if (threadIdx.x == 0) {
-                            if (!mbar_wait(bar_empty0 + 8 * slot, (use & 1u) ^ 1u, abort_flag)) *abort_flag = 1;
-                        }
-                        named_bar(1, kProdThreads);
-                        if (*abort_flag) { stop = true; break; }
+                        // each warp waits for the slot on its own (no block-wide barrier per chunk);
+                        // warps drift at most the ring depth apart, since a slot is only freed
+                        // once every producer thread has filled it
+                        if (stop) continue;                      // skipping to the pattern boundary
+                        int ok = 1;
+                        if (lane == 0) ok = mbar_wait(bar_empty0 + 8 * slot, (use & 1u) ^ 1u, abort_flag) ? 1 : 0;
+                        ok = __shfl_sync(0xffffffffu, ok, 0);
+                        if (!ok) { *abort_flag = 1; stop = true; continue; }
                         const int part = ch / 3;                   // 0: even m, 1: odd m
                         const int m0 = 2 * ((ch % 3) * 32 + quarter * 8) + part;
                         int nvalid = (H - m0) / 2 + 1;             // frequencies m0 + 2 jj <= H
@@ -302,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
         }
     } else if (warp == kMmaWarp) {
         // ================================================================ MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && !c.stall) {
             const uint32_t idesc = idesc_bf16(kRows, kN);
             const uint32_t ring0 = smem_u32(s.ring), basis0 = smem_u32(s.basis);
             uint32_t g = 0, tt = 0;
@@ -354,11 +366,15 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
                 const int tiles = (c.count[li] + kRows - 1) / kRows;
                 float* out = c.pre[li] + (size_t)p * c.lib[li].K;
                 for (int t = 0; t < tiles; ++t, ++tt) {
+                    // row 0 waits and publishes one decision (a word per tile parity, so the
+                    // next tile's write cannot overtake a slow reader of this one)
                     if (row == 0) {
-                        if (!mbar_wait(bar_accf, tt & 1u, abort_flag)) *abort_flag = 1;
+                        const bool ok = mbar_wait(bar_accf, tt & 1u, abort_flag);
+                        if (!ok) *abort_flag = 1;
+                        s.epi_stop[tt & 1u] = (!ok || *abort_flag) ? 1 : 0;
                     }
                     named_bar(2, kRows);
-                    if (*abort_flag) { stop = true; break; }
+                    if (*(volatile int*)&s.epi_stop[tt & 1u]) { stop = true; break; }
                     tc_fence_after();
                     float best = -FLT_MAX;
 #pragma unroll 1
@@ -395,7 +411,7 @@ size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq) {
     size_t b = 1024;                                           // alignment slack
     b += (size_t)kChunks * kBasisChunkBytes + 2 * kSlotBytes;
     b += (size_t)n_rad * n_freq * 4 + 16 + (size_t)n_theta * 8 + (size_t)n_r * 2 + 16;
-    b += 6 * 8 + 8 + 16;
+    b += 6 * 8 + 4 * 5 + 16;          // barriers, TMEM base, abort flag, stop words
     return b;
 }
 

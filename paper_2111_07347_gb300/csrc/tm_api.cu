@@ -1225,6 +1225,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                     TM_CUDA(cudaMemsetAsync(score[i], 0xFF, (size_t)m * libs[i]->K * 4, st), "tm_index_patterns: memset");
                 }
                 dc.error = ctx->d_error;
+                dc.stall = (params->reserved & TM_INDEX_TEST_STALL) ? 1 : 0;
                 {
                     StageTimer tmr(ctx, TM_STAGE_DENSE, st);
                     TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_index_patterns: dense");

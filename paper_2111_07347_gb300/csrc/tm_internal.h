@@ -116,6 +116,7 @@ struct DenseCall {
     int count[TM_MAX_LIBS];             // templates scored per pattern
     float* pre[TM_MAX_LIBS];            // [n][K] out: pre-score of every scored template
     unsigned* error;                    // device word: bit 0 = a bounded wait timed out
+    int stall;                          // test hook: the MMA issuer issues nothing
 };
 
 bool dense_supported(int n_theta);

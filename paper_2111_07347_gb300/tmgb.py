@@ -25,6 +25,7 @@ TM_COORDS_POLAR, TM_COORDS_XY = 0, 1
 TM_LIB_MIRROR, TM_LIB_UNIT_INTENSITY = 1, 2
 TM_PATH_FP32_SPARSE, TM_PATH_BF16_RESCORE = 0, 1
 TM_INDEX_GRAPH = 1
+TM_INDEX_TEST_STALL = 2
 
 
 class TmError(RuntimeError):
@@ -589,9 +590,10 @@ class Context:
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
               path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None,
-              graph=False, centres=None):
+              graph=False, centres=None, test_stall=False):
         """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32.
-        graph=True replays repeated identical calls as a CUDA graph (needs a created stream)."""
+        graph=True replays repeated identical calls as a CUDA graph (needs a created stream).
+        test_stall=True sets TM_INDEX_TEST_STALL (failure-path tests of the bounded waits)."""
         import torch
         if isinstance(lib_ids, int):
             lib_ids = [lib_ids]
@@ -601,6 +603,8 @@ class Context:
         p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k)
         if graph:
             p.reserved |= TM_INDEX_GRAPH
+        if test_stall:
+            p.reserved |= TM_INDEX_TEST_STALL
         self.last_stats = tm_index_patterns(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W,
                                             None if centres is None else centres.data_ptr(),
                                             list(lib_ids), out.data_ptr(), _stream_ptr(stream))

@@ -194,3 +194,28 @@ def test_index_bf16_single_phase_full_size_sampled(ctx):
         assert abs(h["score"][p, 0] - q_top) <= max(tol(q_top, q_top), 1e-5 * abs(q_top)) or k0 != ref["template"][i, 0]
     assert same >= 31, same
     ctx.unload_library(lid)
+
+
+def test_bounded_waits_time_out_report_and_recover(ctx):
+    """Failure path of the tensor-core kernel without a GPU fault: with the MMA issuer told to
+    issue nothing, every producer and epilogue wait runs out (about 1 s); the kernel records
+    the timeout, frees its tensor memory and returns; tm_check reports TM_ERR_TIMEOUT; the
+    next call on the same context gives the normal results."""
+    import time
+    ts, scan, prm = synth.tiny_workload(n_side=4)
+    lid = ctx.load_library(ts, 60, 180)
+    frames = _t(scan.frames)
+    kw = dict(top_n=5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=64)
+    ref = tmgb.hits_to_numpy(ctx.index(frames, lid, **kw))
+    ctx.check()
+    t0 = time.perf_counter()
+    ctx.index(frames, lid, test_stall=True, **kw)
+    with pytest.raises(tmgb.TmError) as e:
+        ctx.check()
+    assert e.value.code == tmgb.TM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    ctx.check()                                   # the error word was cleared
+    again = tmgb.hits_to_numpy(ctx.index(frames, lid, **kw))
+    ctx.check()
+    assert np.array_equal(again, ref)
+    ctx.unload_library(lid)
