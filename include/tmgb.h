@@ -171,13 +171,19 @@ int tm_library_export(tm_ctx* ctx, int lib_id, int64_t* offsets, int32_t* r, int
 /* The host half of tm_load_library without a device: validates the descriptor and puts
  * the templates on the polar grid exactly as tm_load_library does.  Call once with NULL
  * arrays to get the sizes in *info, then again with host buffers as for
- * tm_library_export; packed [n_spots] (nullable) receives each spot's word as the sparse
- * kernel reads it (bits 0..23: row of the spot's radius among the library's distinct radii
- * times the row pitch, plus t; bits 24..31: the first shift block that wraps).
- * info->device_bytes is 0.  Needs no GPU. */
+ * tm_library_export.  The sparse kernel's spot words (both nullable, [n_spots]): packed
+ * receives t | rho << 11 | w << 24 (t the angle column, rho the row of the spot's radius
+ * among the library's distinct radii, w = ceil((n_theta - t) / 32) the first 32-wide shift
+ * block that wraps), packed2 the spot's float offset in the kernel's dual-copy row layout
+ * (bits 0..15: (t odd ? n_rad + rho : rho) * pitch_dual + (t & ~1)) and in its wrap-free
+ * layout (bits 16..31: rho * pitch_wf + t), with pitch_dual = n_theta + 64 * NB2 rounded up
+ * to even and pitch_wf = n_theta + 32 * NB, NB2 and NB the 64- and 32-wide block counts
+ * ceil(n_theta / 64) and ceil(n_theta / 32) rounded up to 1, 2, 3, 4, 6, 8, 12, 16, 24 or
+ * 32; a field is 0 when its layout would not fit 16 bits.  info->device_bytes is 0.  Needs
+ * no GPU. */
 int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, int64_t* offsets,
                             int32_t* r, int32_t* t, float* intensity, float* norm, int32_t* order,
-                            int32_t* packed);
+                            int32_t* packed, int32_t* packed2);
 
 /* Stage 1 (Section 2.2, Fig. 2 (a)-(c)): gamma/subtract and bilinear polar resampling.
  * frames_dev [n][H][W] (TM_DTYPE_U16 or TM_DTYPE_F32, row-major, contiguous);

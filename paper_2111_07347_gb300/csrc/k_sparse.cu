@@ -7,19 +7,23 @@
 //
 // Design (GB300):
 // * Shared memory holds only the polar rows the library uses (its distinct spot radii --
-//   a few to a few tens of the 128 rows), column c of a row holding P'[c mod Nθ].  When the
-//   rows fit twice over (pitch Nθ + 32 NB), shift block b of a spot at column t reads
-//   columns t + 32 b + [0, 32) with no wrap test at all (one load and one FMA per block);
-//   otherwise rows are padded by 32 columns and a block past the wrap reads 32 b - Nθ
-//   further (a select per block).  Either way a warp's 32 consecutive shifts never split at
-//   the wrap and never conflict on a bank.  The small footprint lets several CTAs share an
-//   SM and leaves L1 to cache the library's spot lists.
+//   a few to a few tens of the 128 rows); column c of a row holds P'[c mod Nθ], so a warp
+//   reading 32 or 64 consecutive shifts never splits at the wrap.  Three layouts, the
+//   first that fits:
+//   - dual: every row twice, the second copy shifted by one column, pitch Nθ + 64 NB2.  A spot
+//     at column t reads float2 pairs at even columns of the copy (t & 1): lane L of 64-wide
+//     shift block b takes shifts 64 b + 2 L + {0, 1} with ONE 8-byte load and two FMAs;
+//   - wrap-free: one copy, pitch Nθ + 32 NB; block b of lane L reads column t + 32 b + L
+//     (one 4-byte load and one FMA per shift);
+//   - wrapped: one copy padded by 32 columns; a block past the wrap reads Nθ columns earlier
+//     (a select per block).
+//   The library stores, per spot, its shared-memory offset in the dual and wrap-free
+//   layouts, so no address is decoded in the inner loop.
 // * A persistent CTA takes patterns from a global counter; its warps take 32-template
-//   mask words from a shared counter.  One warp scores one template: lane L accumulates
-//   shifts s = 32 b + L of every shift block b in registers; the template's spots arrive
-//   in one lane-parallel load and are broadcast by shuffles; a spot costs, per block, one
-//   shared-memory load and one FMA.  The bound is the shared-memory load path (one 4-byte
-//   operand per multiply-add).
+//   mask words from a shared counter.  One warp scores one template: the lanes hold all its
+//   shifts in registers; the template's spots arrive in one lane-parallel load and are
+//   broadcast by shuffles.  The bound is the shared-memory load path (4 bytes per
+//   multiply-add).
 // * The best shift is only resolved (lowest shift among equal maxima) when the template
 //   can enter the warp's top-N, or when per-template results are requested.
 // Results do not depend on scheduling: a template's sum runs over its spots in CSR order
@@ -43,17 +47,23 @@ constexpr int kMaxWarps = kMaxThreads / 32;
 
 }  // namespace
 
-// Row pitch of the polar rows in shared memory, column c holding P'[c mod n_theta].
-// Wrap-free layout: block b of a spot at column t reads t + 32 b + [0, 32) for b < NB (NB the
-// widest rounded block count), so the pitch is n_theta + 32 NB.  Wrapped layout: blocks past
-// the wrap read n_theta columns earlier, so n_theta + 32 columns and every column 32 NB - 1
-// suffice.
-int sparse_pitch(int n_theta, bool wrap_free) {
+// Row pitch (floats) of a layout, column c holding P'[c mod n_theta] (second dual copy:
+// P'[(c + 1) mod n_theta]).  Dual: pairs at even columns t' + 2 L + 64 b + {0, 1} for
+// t' = t & ~1 and b < NB2, so n_theta + 64 NB2 columns (even, for 8-byte alignment).
+// Wrap-free: t + 32 b + L for b < NB, so n_theta + 32 NB.  Wrapped: blocks past the wrap read
+// n_theta columns earlier, so n_theta + 32 columns and every column below 32 NB suffice.
+int sparse_pitch(int n_theta, int layout) {
+    if (layout == TM_LAYOUT_DUAL) {
+        const int p = n_theta + 64 * round_nb((n_theta + 63) / 64);
+        return p + (p & 1);
+    }
     const int nb = round_nb((n_theta + 31) / 32);
-    if (wrap_free) return n_theta + 32 * nb;
+    if (layout == TM_LAYOUT_WF) return n_theta + 32 * nb;
     const int a = n_theta + 32, b = 32 * nb;
     return a > b ? a : b;
 }
+
+int sparse_rows(int n_rad, int layout) { return layout == TM_LAYOUT_DUAL ? 2 * n_rad : n_rad; }
 
 namespace {
 
@@ -61,69 +71,99 @@ __device__ __forceinline__ bool better(float qa, int ka, float qb, int kb) {
     return qa > qb || (qa == qb && ka < kb);
 }
 
-// Adds spot (px, I) to the accumulators: block b of lane L holds shift 32 b + L.  FIRST
-// initialises them instead.  px must be a real spot word: its wrap block w keeps every read
-// inside the spot's row.
-template <int NB, bool WF, bool FIRST>
-__device__ __forceinline__ void add_spot(float (&acc)[NB], const float* __restrict__ sP, int px, float I, int pitch,
-                                         int n_theta, int lane) {
-    const int t = px & 0x7ff;
-    const int row = (px >> 11) & 0x1fff;
-    const float* p1 = sP + row * pitch + t + lane;
-    if (WF) {
+// ---------------------------------------------------------------- per-layout spot updates
+// acc holds V values per lane (V = 2 NB for the dual layout, NB otherwise); value v of lane L
+// is shift shift_of(v, L).  FIRST initialises instead of accumulating.
+
+template <int LAYOUT>
+__device__ __forceinline__ int shift_of(int v, int lane) {
+    return LAYOUT == TM_LAYOUT_DUAL ? 64 * (v >> 1) + 2 * lane + (v & 1) : 32 * v + lane;
+}
+
+// Dual and wrap-free layouts: px holds the spot's shared-memory offset (bits 0..15 dual,
+// 16..31 wrap-free).
+template <int V, int LAYOUT, bool FIRST>
+__device__ __forceinline__ void add_spot(float (&acc)[V], const float* __restrict__ sP, int px, float I, int lane) {
+    if (LAYOUT == TM_LAYOUT_DUAL) {
+        const float2* p = reinterpret_cast<const float2*>(sP + (px & 0xffff)) + lane;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) acc[b] = FIRST ? I * p1[32 * b] : fmaf(I, p1[32 * b], acc[b]);
-    } else {
-        const int w = (int)((unsigned)px >> 24);
-        const float* p2 = p1 - n_theta;                       // blocks b >= w: wrapped
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const float v = (b < w ? p1 : p2)[32 * b];
-            acc[b] = FIRST ? I * v : fmaf(I, v, acc[b]);
+        for (int b = 0; b < V / 2; ++b) {
+            const float2 v = p[32 * b];
+            acc[2 * b] = FIRST ? I * v.x : fmaf(I, v.x, acc[2 * b]);
+            acc[2 * b + 1] = FIRST ? I * v.y : fmaf(I, v.y, acc[2 * b + 1]);
         }
+    } else {
+        const float* p = sP + ((unsigned)px >> 16) + lane;
+#pragma unroll
+        for (int b = 0; b < V; ++b) acc[b] = FIRST ? I * p[32 * b] : fmaf(I, p[32 * b], acc[b]);
     }
 }
 
-// Correlation C(s) of one template for all its shifts (warp-collective).  Returns the
-// warp-wide maximum; when it reaches thr_c, *shift_out is the lowest shift attaining it
-// and `resolved` is set.
-template <int NB, bool WF, bool FULL = false>
-__device__ __forceinline__ float score_template(const float* __restrict__ sP, const SparseLib& L, int beg, int end,
-                                                int S, int n_theta, int pitch, int lane, float thr_c,
+// Wrapped layout: px = t | row << 11 | w << 24, w the first 32-wide block past the wrap.
+template <int V, bool FIRST>
+__device__ __forceinline__ void add_spot_wrapped(float (&acc)[V], const float* __restrict__ sP, int px, float I,
+                                                 int pitch, int n_theta, int lane) {
+    const int t = px & 0x7ff;
+    const int row = (px >> 11) & 0x1fff;
+    const int w = (int)((unsigned)px >> 24);
+    const float* p1 = sP + row * pitch + t + lane;
+    const float* p2 = p1 - n_theta;                           // blocks b >= w: wrapped
+#pragma unroll
+    for (int b = 0; b < V; ++b) {
+        const float v = (b < w ? p1 : p2)[32 * b];
+        acc[b] = FIRST ? I * v : fmaf(I, v, acc[b]);
+    }
+}
+
+// Correlation C(s) of one template for all its shifts (warp-collective).  NB = shift blocks
+// (64 wide for the dual layout, else 32).  Returns the warp-wide maximum; when it reaches
+// thr_c, shift_out is the lowest shift attaining it and `resolved` is set.  FULL: the
+// template is slid over all n_theta shifts.
+template <int NB, int LAYOUT, bool FULL>
+__device__ __forceinline__ float score_template(const float* __restrict__ sP, const int2* __restrict__ spots, int beg,
+                                                int cnt_all, int S, int n_theta, int pitch, int lane, float thr_c,
                                                 int& shift_out, bool& resolved) {
-    float acc[NB];
-    int cnt = min(32, end - beg);
+    constexpr int V = LAYOUT == TM_LAYOUT_DUAL ? 2 * NB : NB;
+    float acc[V];
+    int cnt = min(32, cnt_all);
     if (cnt <= 0) {                                               // no spot on the grid: C = 0, no read
 #pragma unroll
-        for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
+        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
         cnt = 0;
     }
     int2 mine = make_int2(0, 0);
-    if (lane < cnt) mine = __ldg(L.spot + beg + lane);            // one lane-parallel load
-    if (cnt > 0)
-        add_spot<NB, WF, true>(acc, sP, __shfl_sync(0xffffffffu, mine.x, 0),
-                               __int_as_float(__shfl_sync(0xffffffffu, mine.y, 0)), pitch, n_theta, lane);
+    if (lane < cnt) mine = __ldg(spots + beg + lane);             // one lane-parallel load
+    if (cnt > 0) {
+        const int px = __shfl_sync(0xffffffffu, mine.x, 0);
+        const float I = __int_as_float(__shfl_sync(0xffffffffu, mine.y, 0));
+        if (LAYOUT == TM_LAYOUT_WRAP) add_spot_wrapped<V, true>(acc, sP, px, I, pitch, n_theta, lane);
+        else add_spot<V, LAYOUT, true>(acc, sP, px, I, lane);
+    }
+    const int end = beg + cnt_all;
     for (int i0 = beg, j = 1;;) {
-        for (; j < cnt; ++j)
-            add_spot<NB, WF, false>(acc, sP, __shfl_sync(0xffffffffu, mine.x, j),
-                                    __int_as_float(__shfl_sync(0xffffffffu, mine.y, j)), pitch, n_theta, lane);
+        for (; j < cnt; ++j) {
+            const int px = __shfl_sync(0xffffffffu, mine.x, j);
+            const float I = __int_as_float(__shfl_sync(0xffffffffu, mine.y, j));
+            if (LAYOUT == TM_LAYOUT_WRAP) add_spot_wrapped<V, false>(acc, sP, px, I, pitch, n_theta, lane);
+            else add_spot<V, LAYOUT, false>(acc, sP, px, I, lane);
+        }
         i0 += 32;
         if (i0 >= end) break;
         cnt = min(32, end - i0);
-        if (lane < cnt) mine = __ldg(L.spot + i0 + lane);
+        if (lane < cnt) mine = __ldg(spots + i0 + lane);
         j = 0;
     }
-    // Every lane's block b holds C((32 b + lane) mod Nθ), computed by the same operations as the
-    // shift it repeats (column c of a row holds P'[c mod Nθ]); so for a template slid over all
-    // Nθ shifts (FULL: S == Nθ) the maximum needs no lane mask.  Otherwise shifts >= S are masked.
+    // Every value holds C(shift mod Nθ), computed by the same operations as the shift it
+    // repeats (column c of a row holds P'[c mod Nθ]); so for a template slid over all Nθ
+    // shifts the maximum needs no lane mask.  Otherwise shifts >= S are masked.
     float best = -FLT_MAX;
     if (FULL) {
 #pragma unroll
-        for (int b = 0; b < NB; ++b) best = fmaxf(best, acc[b]);
+        for (int v = 0; v < V; ++v) best = fmaxf(best, acc[v]);
     } else {
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-            if (32 * b + lane < S) best = fmaxf(best, acc[b]);
+        for (int v = 0; v < V; ++v)
+            if (shift_of<LAYOUT>(v, lane) < S) best = fmaxf(best, acc[v]);
     }
     resolved = false;
     if (!__any_sync(0xffffffffu, best >= thr_c)) return best;    // cannot enter the top-N
@@ -132,8 +172,10 @@ __device__ __forceinline__ float score_template(const float* __restrict__ sP, co
     if (best >= thr_c) {
         int s = INT_MAX;
 #pragma unroll
-        for (int b = NB - 1; b >= 0; --b)
-            if (32 * b + lane < S && acc[b] == best) s = 32 * b + lane;
+        for (int v = 0; v < V; ++v) {
+            const int sv = shift_of<LAYOUT>(v, lane);
+            if (sv < S && acc[v] == best) s = min(s, sv);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s = min(s, __shfl_xor_sync(0xffffffffu, s, o));
         shift_out = s;
@@ -142,34 +184,39 @@ __device__ __forceinline__ float score_template(const float* __restrict__ sP, co
     return best;
 }
 
-template <int NBMAX, bool WF>
-__device__ __forceinline__ float score_dispatch(const float* sP, const SparseLib& L, int beg, int end, int S,
+template <int NBMAX, int LAYOUT>
+__device__ __forceinline__ float score_dispatch(const float* sP, const int2* spots, int beg, int cnt, int S,
                                                 int n_theta, int pitch, int lane, float thr_c, int& s, bool& res) {
-    const int nb = (S + 31) >> 5;
-    if (S == n_theta && round_nb(nb) == NBMAX)                 // the common case, tested first
-        return score_template<NBMAX, WF, true>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (nb <= 1) return score_template<1, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (nb <= 2) return score_template<2, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (nb <= 3) return score_template<3, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (nb <= 4) return score_template<4, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (NBMAX >= 6 && nb <= 6) return score_template<(NBMAX >= 6 ? 6 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (NBMAX >= 8 && nb <= 8) return score_template<(NBMAX >= 8 ? 8 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (NBMAX >= 12 && nb <= 12) return score_template<(NBMAX >= 12 ? 12 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (NBMAX >= 16 && nb <= 16) return score_template<(NBMAX >= 16 ? 16 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    if (NBMAX >= 24 && nb <= 24) return score_template<(NBMAX >= 24 ? 24 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
-    return score_template<(NBMAX >= 32 ? 32 : 1), WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s, res);
+    constexpr int W = LAYOUT == TM_LAYOUT_DUAL ? 64 : 32;
+    if (S == n_theta && round_nb((n_theta + W - 1) / W) == NBMAX)   // the common case, tested first
+        return score_template<NBMAX, LAYOUT, true>(sP, spots, beg, cnt, S, n_theta, pitch, lane, thr_c, s, res);
+    const int nb = (S + W - 1) / W;
+#define TMGB_SCORE(NBV)                                                                                          \
+    return score_template<(NBMAX >= NBV ? NBV : 1), LAYOUT, false>(sP, spots, beg, cnt, S, n_theta, pitch, lane, \
+                                                                   thr_c, s, res)
+    if (nb <= 1) TMGB_SCORE(1);
+    if (nb <= 2) TMGB_SCORE(2);
+    if (nb <= 3) TMGB_SCORE(3);
+    if (nb <= 4) TMGB_SCORE(4);
+    if (NBMAX >= 6 && nb <= 6) TMGB_SCORE(6);
+    if (NBMAX >= 8 && nb <= 8) TMGB_SCORE(8);
+    if (NBMAX >= 12 && nb <= 12) TMGB_SCORE(12);
+    if (NBMAX >= 16 && nb <= 16) TMGB_SCORE(16);
+    if (NBMAX >= 24 && nb <= 24) TMGB_SCORE(24);
+    TMGB_SCORE(32);
+#undef TMGB_SCORE
 }
 
-template <int NBMAX, bool WF>
-__global__ void __launch_bounds__(kMaxThreads, NBMAX <= 12 ? 2 : 1)
+template <int NBMAX, int LAYOUT>
+__global__ void __launch_bounds__(kMaxThreads, (LAYOUT == TM_LAYOUT_DUAL ? 2 * NBMAX : NBMAX) <= 12 ? 2 : 1)
 sparse_kernel(const SparseCall c) {
     extern __shared__ __align__(16) float smem[];
     const int n_theta = c.n_theta, pitch = c.pitch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int kWarps = blockDim.x >> 5;
     const int N = c.top_n;
-    float* sP = smem;                                        // [max_rad][pitch]
-    float* lq = sP + (size_t)c.max_rad * pitch;              // [kWarps][N]
+    float* sP = smem;                                        // [rows][pitch]
+    float* lq = sP + (size_t)(LAYOUT == TM_LAYOUT_DUAL ? 2 : 1) * c.max_rad * pitch;   // [kWarps][N]
     int* lk = (int*)(lq + kWarps * N);                       // [kWarps][N]
     int* ls = lk + kWarps * N;                               // [kWarps][N]
     int* lcnt = ls + kWarps * N;                             // [kWarps]
@@ -186,12 +233,15 @@ sparse_kernel(const SparseCall c) {
         const float pn = __ldg(c.pnorm + p);
         for (int li = 0; li < c.n_libs; ++li) {
             const SparseLib L = c.lib[li];
-            // the library's polar rows, padded with wrapped columns
-            for (int rr = warp; rr < L.n_rad; rr += kWarps) {
-                const float* row = src + (size_t)__ldg(L.radii + rr) * n_theta;
+            // the library's polar rows (dual layout: a second copy shifted by one column)
+            const int rows = (LAYOUT == TM_LAYOUT_DUAL ? 2 : 1) * L.n_rad;
+            for (int rr = warp; rr < rows; rr += kWarps) {
+                const int r0 = rr < L.n_rad ? rr : rr - L.n_rad;
+                const int sh = rr < L.n_rad ? 0 : 1;
+                const float* row = src + (size_t)__ldg(L.radii + r0) * n_theta;
                 float* dst = sP + (size_t)rr * pitch;
                 for (int col = lane; col < pitch; col += 32) {
-                    int sc = col;
+                    int sc = col + sh;
                     while (sc >= n_theta) sc -= n_theta;
                     dst[col] = __ldg(row + sc);
                 }
@@ -199,6 +249,7 @@ sparse_kernel(const SparseCall c) {
             if (threadIdx.x == 0) *counter = 0;
             if (threadIdx.x < kWarps) lcnt[threadIdx.x] = 0;
             __syncthreads();
+            const int2* spots = LAYOUT == TM_LAYOUT_WRAP ? L.spot : L.spot2;
             const uint32_t* mrow = c.mask[li] ? c.mask[li] + (size_t)p * L.words : nullptr;
             float* qo = c.q_out[li] ? c.q_out[li] + (size_t)p * L.K : nullptr;
             int32_t* so = c.s_out[li] ? c.s_out[li] + (size_t)p * L.K : nullptr;
@@ -215,15 +266,12 @@ sparse_kernel(const SparseCall c) {
                 uint32_t m = mrow ? __ldg(mrow + wd) : 0xffffffffu;
                 const int rem = L.K - wd * 32;
                 if (rem < 32) m &= (1u << rem) - 1u;
-                // per-lane metadata of the word's 32 templates (one round trip per word)
+                // per-lane metadata of the word's 32 templates: {first spot, spots | shifts << 16,
+                // norm bits} in one load
                 const int kl = wd * 32 + lane;
-                int beg_l = 0, end_l = 0, S_l = 1;
-                float tn_l = 0.0f;
+                int4 meta_l = make_int4(0, 1 << 16, 0, 0);
                 if (lane < rem && ((m >> lane) & 1u)) {
-                    beg_l = __ldg(L.off + kl);
-                    end_l = __ldg(L.off + kl + 1);
-                    S_l = __ldg(L.nshift + kl);
-                    tn_l = __ldg(L.norm + kl);
+                    meta_l = __ldg(L.meta + kl);
                 } else if (qo && lane < rem) {
                     qo[kl] = -INFINITY;
                     so[kl] = -1;
@@ -232,10 +280,10 @@ sparse_kernel(const SparseCall c) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
                     const int k = wd * 32 + bit;
-                    const int beg = __shfl_sync(0xffffffffu, beg_l, bit);
-                    const int end = __shfl_sync(0xffffffffu, end_l, bit);
-                    const int S = __shfl_sync(0xffffffffu, S_l, bit);
-                    const float tn = __shfl_sync(0xffffffffu, tn_l, bit);
+                    const int beg = __shfl_sync(0xffffffffu, meta_l.x, bit);
+                    const int cs = __shfl_sync(0xffffffffu, meta_l.y, bit);
+                    const float tn = __int_as_float(__shfl_sync(0xffffffffu, meta_l.z, bit));
+                    const int cnt = cs & 0xffff, S = (int)((unsigned)cs >> 16);
                     const float d = pn * tn;
                     // a template whose correlation stays below the warp's N-th best (in
                     // correlation units, with a margin for the division's rounding) cannot
@@ -247,8 +295,8 @@ sparse_kernel(const SparseCall c) {
                     }
                     int s = 0;
                     bool resolved = false;
-                    const float best = score_dispatch<NBMAX, WF>(sP, L, beg, end, S, n_theta, pitch, lane, thr_c, s,
-                                                                 resolved);
+                    const float best =
+                        score_dispatch<NBMAX, LAYOUT>(sP, spots, beg, cnt, S, n_theta, pitch, lane, thr_c, s, resolved);
                     if (!resolved) continue;
                     float q;
                     if (d > 0.0f) q = __fdiv_rn(best, d);
@@ -256,15 +304,15 @@ sparse_kernel(const SparseCall c) {
                     if (lane == 0) {
                         if (qo) { qo[k] = q; so[k] = s; }
                         if (c.hits) {
-                            const int cnt = lcnt[warp];
-                            if (cnt < N || better(q, k, wq[N - 1], wk[N - 1])) {
-                                int i = cnt < N ? cnt : N - 1;
+                            const int cnt_l = lcnt[warp];
+                            if (cnt_l < N || better(q, k, wq[N - 1], wk[N - 1])) {
+                                int i = cnt_l < N ? cnt_l : N - 1;
                                 while (i > 0 && better(q, k, wq[i - 1], wk[i - 1])) {
                                     wq[i] = wq[i - 1]; wk[i] = wk[i - 1]; ws[i] = ws[i - 1];
                                     --i;
                                 }
                                 wq[i] = q; wk[i] = k; ws[i] = s;
-                                if (cnt < N) lcnt[warp] = cnt + 1;
+                                if (cnt_l < N) lcnt[warp] = cnt_l + 1;
                             }
                         }
                     }
@@ -320,37 +368,44 @@ sparse_kernel(const SparseCall c) {
     }
 }
 
-template <int NBMAX, bool WF>
+template <int NBMAX, int LAYOUT>
 cudaError_t launch_nb(const SparseCall& c, int num_sms, size_t smem, cudaStream_t st) {
     const int threads = (c.threads == 128 || c.threads == 512) ? c.threads : 256;
-    cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX, WF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX, WF>, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX, LAYOUT>, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > c.n) grid = c.n;
     e = cudaMemsetAsync(c.pattern_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    sparse_kernel<NBMAX, WF><<<(int)grid, threads, smem, st>>>(c);
+    sparse_kernel<NBMAX, LAYOUT><<<(int)grid, threads, smem, st>>>(c);
     return cudaGetLastError();
 }
 
-}  // namespace
-
-// Layout for a call: the wrap-free rows when they fit in kWrapFreeBytes (several CTAs per
-// SM), else the wrapped rows; 0 when even those do not fit.
+// Shared-memory budgets of the layouts: the dual layout only when four CTAs still fit on an
+// SM, the wrap-free one when at least two do.
+constexpr size_t kDualBytes = 54 * 1024;
 constexpr size_t kWrapFreeBytes = 100 * 1024;
 
-size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, bool* wrap_free, int* pitch) {
+}  // namespace
+
+size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout, int* pitch) {
     if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
     const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16;
-    for (int wf = 1; wf >= 0; --wf) {
-        const int pch = sparse_pitch(n_theta, wf != 0);
-        const size_t b = (size_t)max_rad * pch * 4 + lists;
-        if ((wf && b <= kWrapFreeBytes) || (!wf && b <= 232448)) {
-            if (wrap_free) *wrap_free = wf != 0;
+    const int order[3] = {TM_LAYOUT_DUAL, TM_LAYOUT_WF, TM_LAYOUT_WRAP};
+    const size_t limit[3] = {kDualBytes, kWrapFreeBytes, 232448};
+    for (int i = 0; i < 3; ++i) {
+        const int pch = sparse_pitch(n_theta, order[i]);
+        const size_t rows = (size_t)sparse_rows(max_rad, order[i]);
+        // per-spot offsets of the dual and wrap-free layouts are 16-bit
+        if (order[i] != TM_LAYOUT_WRAP && rows * pch > 65535) continue;
+        const size_t b = rows * pch * 4 + lists;
+        if (b <= limit[i]) {
+            if (layout) *layout = order[i];
             if (pitch) *pitch = pch;
             return b;
         }
@@ -360,23 +415,29 @@ size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, bool* wrap_free, i
 
 cudaError_t launch_sparse(const SparseCall& call, int num_sms, cudaStream_t st) {
     if (call.n <= 0) return cudaSuccess;
-    bool wf = false;
-    int pitch = 0;
-    const size_t smem = sparse_smem_bytes(call.max_rad, call.n_theta, call.top_n, &wf, &pitch);
+    int layout = TM_LAYOUT_WRAP, pitch = 0;
+    const size_t smem = sparse_smem_bytes(call.max_rad, call.n_theta, call.top_n, &layout, &pitch);
     if (!smem) return cudaErrorInvalidValue;
     SparseCall c = call;
     c.pitch = pitch;
-    const int nbmax = (c.n_theta + 31) / 32;
-    if (wf) {
-        if (nbmax <= 6) return launch_nb<6, true>(c, num_sms, smem, st);
-        if (nbmax <= 12) return launch_nb<12, true>(c, num_sms, smem, st);
-        if (nbmax <= 24) return launch_nb<24, true>(c, num_sms, smem, st);
-        return launch_nb<32, true>(c, num_sms, smem, st);
+    if (layout == TM_LAYOUT_DUAL) {
+        const int nb2 = (c.n_theta + 63) / 64;
+        if (nb2 <= 3) return launch_nb<3, TM_LAYOUT_DUAL>(c, num_sms, smem, st);
+        if (nb2 <= 6) return launch_nb<6, TM_LAYOUT_DUAL>(c, num_sms, smem, st);
+        if (nb2 <= 12) return launch_nb<12, TM_LAYOUT_DUAL>(c, num_sms, smem, st);
+        return launch_nb<16, TM_LAYOUT_DUAL>(c, num_sms, smem, st);
     }
-    if (nbmax <= 6) return launch_nb<6, false>(c, num_sms, smem, st);
-    if (nbmax <= 12) return launch_nb<12, false>(c, num_sms, smem, st);
-    if (nbmax <= 24) return launch_nb<24, false>(c, num_sms, smem, st);
-    return launch_nb<32, false>(c, num_sms, smem, st);
+    const int nbmax = (c.n_theta + 31) / 32;
+    if (layout == TM_LAYOUT_WF) {
+        if (nbmax <= 6) return launch_nb<6, TM_LAYOUT_WF>(c, num_sms, smem, st);
+        if (nbmax <= 12) return launch_nb<12, TM_LAYOUT_WF>(c, num_sms, smem, st);
+        if (nbmax <= 24) return launch_nb<24, TM_LAYOUT_WF>(c, num_sms, smem, st);
+        return launch_nb<32, TM_LAYOUT_WF>(c, num_sms, smem, st);
+    }
+    if (nbmax <= 6) return launch_nb<6, TM_LAYOUT_WRAP>(c, num_sms, smem, st);
+    if (nbmax <= 12) return launch_nb<12, TM_LAYOUT_WRAP>(c, num_sms, smem, st);
+    if (nbmax <= 24) return launch_nb<24, TM_LAYOUT_WRAP>(c, num_sms, smem, st);
+    return launch_nb<32, TM_LAYOUT_WRAP>(c, num_sms, smem, st);
 }
 
 }  // namespace tmgb

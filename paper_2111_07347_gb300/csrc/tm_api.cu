@@ -72,6 +72,8 @@ struct Library {
     // device
     int32_t* d_off = nullptr;
     int2* d_spot = nullptr;
+    int2* d_spot2 = nullptr;       // per-spot offsets in the dual / wrap-free layouts
+    int4* d_meta = nullptr;        // per template {first spot, spots | shifts << 16, norm bits, 0}
     float* d_norm = nullptr;
     int32_t* d_nshift = nullptr;
     float* d_radial = nullptr;
@@ -267,7 +269,8 @@ int rotational_order(const Merged& m, int n_theta) {
 
 // Host half of library loading: validation, rounding, merging, mirrors, norms, orders.
 struct Prepared {
-    std::vector<int2> spot;
+    std::vector<int2> spot, spot2;
+    std::vector<int4> meta;
     std::vector<int32_t> nshift;
     std::vector<double> radial, rnorm;
 };
@@ -393,6 +396,27 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
         spot[i].x = t | (row << 11) | (w << 24);
         memcpy(&spot[i].y, &L->I[i], 4);
     }
+    // offsets in the dual-copy and wrap-free row layouts (0 where a layout cannot be used)
+    const int64_t pd = tmgb::sparse_pitch(n_theta, tmgb::TM_LAYOUT_DUAL);
+    const int64_t pw = tmgb::sparse_pitch(n_theta, tmgb::TM_LAYOUT_WF);
+    const bool dual_ok = 2 * n_rows * pd <= 65535, wf_ok = n_rows * pw <= 65535;
+    P->spot2.resize(ns);
+    for (int64_t i = 0; i < ns; ++i) {
+        const int64_t row = row_of[L->r[i]], t = L->t[i];
+        const int64_t od = dual_ok ? ((t & 1) ? n_rows + row : row) * pd + (t & ~(int64_t)1) : 0;
+        const int64_t ow = wf_ok ? row * pw + t : 0;
+        P->spot2[i].x = (int32_t)(uint32_t)(od | (ow << 16));
+        P->spot2[i].y = spot[i].y;
+    }
+    P->meta.resize(L->K);
+    for (int64_t k = 0; k < L->K; ++k) {
+        const int64_t cnt = L->off[k + 1] - L->off[k];
+        if (cnt > 65535) return fail(TM_ERR_UNSUPPORTED, "tm_load_library: template %lld has %lld spots (max 65535)",
+                                     (long long)k, (long long)cnt);
+        int32_t nb;
+        memcpy(&nb, &L->norm[k], 4);
+        P->meta[k] = make_int4((int32_t)L->off[k], (int32_t)(cnt | ((int64_t)P->nshift[k] << 16)), nb, 0);
+    }
     return TM_OK;
 }
 
@@ -418,6 +442,8 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
     Up ups[] = {
         {(void**)&L->d_off, off32.data(), off32.size() * 4, "library offsets"},
         {(void**)&L->d_spot, spot.data(), spot.size() * 8, "library spots"},
+        {(void**)&L->d_spot2, P.spot2.data(), P.spot2.size() * 8, "library spot offsets"},
+        {(void**)&L->d_meta, P.meta.data(), P.meta.size() * 16, "library template metadata"},
         {(void**)&L->d_norm, L->norm.data(), L->norm.size() * 4, "library norms"},
         {(void**)&L->d_nshift, nshift.data(), nshift.size() * 4, "library shifts"},
         {(void**)&L->d_radial, radf.data(), radf.size() * 4, "library radial profiles"},
@@ -436,7 +462,8 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
 }
 
 void free_library(tm_ctx* ctx, Library* L) {
-    void* ps[] = {L->d_off, L->d_spot, L->d_norm, L->d_nshift, L->d_radial, L->d_rnorm, L->d_rt, L->d_order, L->d_radii};
+    void* ps[] = {L->d_off,    L->d_spot, L->d_spot2, L->d_meta, L->d_norm, L->d_nshift,
+                  L->d_radial, L->d_rnorm, L->d_rt, L->d_order, L->d_radii};
     for (void* p : ps)
         if (p) cudaFree(p);
     ctx->used -= std::min(ctx->used, L->bytes);
@@ -446,6 +473,8 @@ tmgb::SparseLib sparse_view(const Library* L) {
     tmgb::SparseLib v;
     v.off = L->d_off;
     v.spot = L->d_spot;
+    v.spot2 = L->d_spot2;
+    v.meta = L->d_meta;
     v.norm = L->d_norm;
     v.nshift = L->d_nshift;
     v.radii = L->d_radii;
@@ -929,7 +958,8 @@ static void export_host(const Library* L, int64_t* offsets, int32_t* r, int32_t*
 }
 
 int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, int64_t* offsets, int32_t* r,
-                            int32_t* t, float* intensity, float* norm, int32_t* order, int32_t* packed) {
+                            int32_t* t, float* intensity, float* norm, int32_t* order, int32_t* packed,
+                            int32_t* packed2) {
     if (!info) return fail(TM_ERR_INVALID_ARG, "tm_library_prepare_host: info is NULL");
     Library L;
     Prepared P;
@@ -939,6 +969,8 @@ int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, 
     export_host(&L, offsets, r, t, intensity, norm, order);
     if (packed)
         for (size_t i = 0; i < P.spot.size(); ++i) packed[i] = P.spot[i].x;
+    if (packed2)
+        for (size_t i = 0; i < P.spot2.size(); ++i) packed2[i] = P.spot2[i].x;
     return TM_OK;
 }
 

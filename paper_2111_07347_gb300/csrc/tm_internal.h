@@ -16,14 +16,24 @@ void set_last_error(const char* msg);
 
 
 // ------------------------------------------------------------------ device library views
-// Sparse templates in CSR.  The sparse kernel keeps only the library's distinct spot
-// radii (radii[0..n_rad)) as rows of its shared-memory polar image.  spot[i].x packs
-// bits 0..10 = t (angle column), bits 11..23 = rho (the spot's row in radii[]), bits 24..29
-// = w = ceil((n_theta - t) / 32), the first 32-wide shift block whose columns wrap past
-// n_theta.  spot[i].y = float bits of the intensity.
+// Sparse templates in CSR.  The sparse kernel keeps only the library's distinct spot radii
+// (radii[0..n_rad)) as rows of its shared-memory polar image, in one of three layouts
+// (TM_LAYOUT_*, chosen per call by shared-memory size).
+//   spot[i]  = {t | rho << 11 | w << 24, intensity bits}: t the angle column, rho the spot's row
+//              in radii[], w = ceil((n_theta - t) / 32) the first 32-wide shift block whose
+//              columns wrap past n_theta (wrapped layout);
+//   spot2[i] = {off_dual | off_wf << 16, intensity bits}: the spot's float offset in the dual
+//              layout ((t & 1 ? n_rad + rho : rho) * pitch_dual + (t & ~1)) and in the wrap-free
+//              layout (rho * pitch_wf + t), each 0 when it does not fit 16 bits (the layout is
+//              then never chosen);
+//   meta[k]  = {first spot, spots | shifts << 16, norm bits, 0}.
+enum { TM_LAYOUT_DUAL = 0, TM_LAYOUT_WF = 1, TM_LAYOUT_WRAP = 2 };
+
 struct SparseLib {
     const int32_t* off;        // [K + 1]
     const int2* spot;          // [n_spots]
+    const int2* spot2;         // [n_spots]
+    const int4* meta;          // [K]
     const float* norm;         // [K]  sqrt(sum I^2)
     const int32_t* nshift;     // [K]  shifts to evaluate = n_theta / order_k
     const int32_t* radii;      // [n_rad]  distinct spot radii (polar rows), ascending
@@ -89,8 +99,9 @@ struct SparseCall {
 
 // Shared-memory bytes the sparse kernel needs (0 when unsupported), the layout it uses
 // (wrap-free rows when they fit comfortably) and its row pitch.
-size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, bool* wrap_free = nullptr, int* pitch = nullptr);
-int sparse_pitch(int n_theta, bool wrap_free);
+size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout = nullptr, int* pitch = nullptr);
+int sparse_pitch(int n_theta, int layout);
+int sparse_rows(int n_rad, int layout);
 cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);
 
 // ------------------------------------------------------------------ BF16 tensor-core path

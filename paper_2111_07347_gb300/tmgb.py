@@ -108,7 +108,7 @@ _SIGS = {
     "tm_library_info_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(tm_library_info)]),
     "tm_library_export": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "tm_library_prepare_host": (ctypes.c_int, [ctypes.POINTER(tm_library_desc), ctypes.POINTER(tm_library_info),
-                                               _P, _P, _P, _P, _P, _P, _P]),
+                                               _P, _P, _P, _P, _P, _P, _P, _P]),
     "tm_polar_transform": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_double, _P, _P, _P, _P]),
@@ -222,11 +222,13 @@ def tm_library_prepare_host(ts, n_r: int, n_theta: int, dr: float = 1.0, mirror=
     d = _Desc(ts, n_r, n_theta, dr, mirror, unit_intensity)
     info = tm_library_info()
     _check(library().tm_library_prepare_host(ctypes.byref(d.desc), ctypes.byref(info), None, None, None,
-                                             None, None, None, None))
+                                             None, None, None, None, None))
     out = _alloc_export(info)
     out["packed"] = np.zeros(info.n_spots, np.int32)
+    out["packed2"] = np.zeros(info.n_spots, np.int32)
     _check(library().tm_library_prepare_host(ctypes.byref(d.desc), ctypes.byref(info), *_export_ptrs(out),
-                                             out["packed"].ctypes.data if out["packed"].size else None))
+                                             out["packed"].ctypes.data if out["packed"].size else None,
+                                             out["packed2"].ctypes.data if out["packed2"].size else None))
     out["info"] = _info_dict(info)
     return out
 

@@ -126,20 +126,27 @@ def _round_nb(nb):
         else 24 if nb <= 24 else 32
 
 
-def _pitch(n_theta, wrap_free):
-    """Row pitch of the sparse kernel's shared-memory rows: wrap-free rows hold n_theta + 32 NB
-    columns (NB the widest rounded shift-block count); wrapped rows n_theta + 32 columns and at
-    least 32 NB."""
+def _pitch(n_theta, layout):
+    """Row pitch of the sparse kernel's shared-memory rows.  dual: two copies of each row (the
+    second shifted by one column), n_theta + 64 NB2 columns rounded up to even; wrap-free:
+    n_theta + 32 NB; wrapped: n_theta + 32 and at least 32 NB (NB2, NB the rounded 64- and
+    32-wide block counts)."""
+    if layout == "dual":
+        p = n_theta + 64 * _round_nb((n_theta + 63) // 64)
+        return p + (p & 1)
     nb = _round_nb((n_theta + 31) // 32)
-    return n_theta + 32 * nb if wrap_free else max(n_theta + 32, 32 * nb)
+    return n_theta + 32 * nb if layout == "wf" else max(n_theta + 32, 32 * nb)
 
 
 @pytest.mark.parametrize("which", ["random", "fcc", "hcp", "odd"])
 def test_sparse_layout_reads_stay_in_bounds(lib, which):
     """Replay the sparse kernel's shared-memory indexing on the CPU for every spot, lane and
-    shift block, in both row layouts: the packed word decodes to the spot's angle column and
-    its row among the library's distinct radii; every address stays inside that row; the word
-    read equals the polar sample at (t + s) mod n_theta for the lane's shift s."""
+    shift block, in all three row layouts: the spot words decode to the spot's angle column
+    and its row among the library's distinct radii (wrapped layout) or to its precomputed
+    offsets (dual and wrap-free layouts); every address stays inside the rows; the value read
+    is the polar sample at (t + s) mod n_theta for the lane's shift s, given how each layout
+    fills its rows (column c of a row holds P'[c mod n_theta]; the second dual copy holds
+    P'[(c + 1) mod n_theta])."""
     if which == "random":
         ts, _, _ = synth.tiny_workload(n_side=1)
         n_r, n_theta = 60, 180
@@ -151,6 +158,7 @@ def test_sparse_layout_reads_stay_in_bounds(lib, which):
         n_r, n_theta = 128, 360
     h = tmgb.tm_library_prepare_host(ts, n_r, n_theta)
     radii = np.unique(h["r"])
+    n_rad = max(1, radii.size)
     word = h["packed"].astype(np.int64) & 0xFFFFFFFF
     t = word & 0x7FF
     row = (word >> 11) & 0x1FFF
@@ -158,17 +166,42 @@ def test_sparse_layout_reads_stay_in_bounds(lib, which):
     assert np.array_equal(radii[row], h["r"])
     assert np.array_equal(t, h["t"])
     assert np.array_equal(w, (n_theta - h["t"] + 31) // 32)
+    w2 = h["packed2"].astype(np.int64) & 0xFFFFFFFF
+    off_d, off_w = w2 & 0xFFFF, w2 >> 16
+    pd, pw = _pitch(n_theta, "dual"), _pitch(n_theta, "wf")
+    dual_ok, wf_ok = 2 * n_rad * pd <= 65535, n_rad * pw <= 65535
+    if dual_ok:
+        assert np.array_equal(off_d, np.where(t & 1, n_rad + row, row) * pd + (t & ~1))
+    if wf_ok:
+        assert np.array_equal(off_w, row * pw + t)
     lanes = np.arange(32)
-    for wrap_free in (True, False):
-        pitch = _pitch(n_theta, wrap_free)
+    for layout in ("dual", "wf", "wrap"):
+        if (layout == "dual" and not dual_ok) or (layout == "wf" and not wf_ok):
+            continue
+        pitch = _pitch(n_theta, layout)
+        rows = 2 * n_rad if layout == "dual" else n_rad
+        bw = 64 if layout == "dual" else 32
         for k in range(h["info"]["n_templates"]):
             S = n_theta // h["order"][k]
-            nb = _round_nb((S + 31) // 32)
+            nb = _round_nb((S + bw - 1) // bw)
             for i in range(h["offsets"][k], h["offsets"][k + 1]):
-                lo = row[i] * pitch
                 for b in range(nb):
-                    col = t[i] + 32 * b - (n_theta if (not wrap_free and b >= w[i]) else 0) + lanes
-                    assert np.all((col >= 0) & (col < pitch)), (wrap_free, k, i, b)
-                    # column c of a row holds P'[c mod n_theta]
-                    assert np.array_equal(col % n_theta, (t[i] + 32 * b + lanes) % n_theta)
-                    assert lo + col.max() < len(radii) * pitch
+                    if layout == "dual":
+                        for e in (0, 1):
+                            addr = off_d[i] + 2 * lanes + 64 * b + e          # float index
+                            r_, col = addr // pitch, addr % pitch
+                            assert np.all(addr < rows * pitch) and np.all(r_ < rows), (k, i, b)
+                            assert off_d[i] % 2 == 0 and np.all(r_ == r_[0])
+                            src_row = r_[0] % n_rad
+                            assert src_row == row[i]
+                            val_col = (col + (1 if r_[0] >= n_rad else 0)) % n_theta
+                            assert np.array_equal(val_col, (t[i] + 2 * lanes + 64 * b + e) % n_theta)
+                    else:
+                        if layout == "wf":
+                            col = off_w[i] - row[i] * pitch + 32 * b + lanes
+                        else:
+                            col = t[i] + 32 * b - (n_theta if b >= w[i] else 0) + lanes
+                        assert np.all((col >= 0) & (col < pitch)), (layout, k, i, b)
+                        assert row[i] * pitch + col.max() < rows * pitch
+                        # column c of a row holds P'[c mod n_theta]
+                        assert np.array_equal(col % n_theta, (t[i] + 32 * b + lanes) % n_theta)
