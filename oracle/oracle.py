@@ -21,6 +21,9 @@ Steps, in the paper's order (Section 2.2):
   matrix-vector product; the best fraction kept (Section 2.2, Fig. 3).
 * ``top_n``            -- templates ranked by their best Q (Section 2.2: "sorted and
   the top N best matching templates can be queried").
+* ``frame_sum`` / ``matrix_mask`` / ``apply_mask`` -- the two-stage indexing of Section 4.3:
+  mean of all patterns, thresholded, cleaned by erosions and dilations, and the masked
+  patterns indexed again.
 * ``dense_scores`` / ``dft_scores`` -- Q(k, s) for every shift written as the dense
   circulant contraction and as its angular-DFT factorisation (Section 2.2, the
   complexity discussion naming the FFT cross-correlation alternative), both in FP64.
@@ -307,3 +310,67 @@ def dft_scores(P: np.ndarray, lib: Library) -> np.ndarray:
         d = nP * lib.norm[k]
         out[k] = C / d if d > 0 else 0.0
     return out
+
+
+# ----------------------------------------------------------------------------------
+# Two-stage (masked) indexing, Section 4.3: the matrix reflections are removed with a
+# mask made from the average of all patterns, thresholded, then cleaned by erosions and
+# dilations; the masked patterns are indexed against the precipitate library.
+# ----------------------------------------------------------------------------------
+
+def frame_sum(frames: np.ndarray) -> np.ndarray:
+    """Per-pixel sum over the frames, in FP64, frames added in order p = 0, 1, ... (exact for
+    integer frames; the order is fixed for float frames).  frames [n][H][W] -> [H][W]."""
+    s = np.zeros(frames.shape[1:], dtype=np.float64)
+    for p in range(frames.shape[0]):
+        s += frames[p].astype(np.float64)
+    return s
+
+
+def _shifted(B: np.ndarray, dy: int, dx: int) -> np.ndarray:
+    """B moved so that out[y, x] = B[y + dy, x + dx], False outside the image."""
+    H, W = B.shape
+    out = np.zeros_like(B)
+    ys, ye = max(0, -dy), min(H, H - dy)
+    xs, xe = max(0, -dx), min(W, W - dx)
+    out[ys:ye, xs:xe] = B[ys + dy:ye + dy, xs + dx:xe + dx]
+    return out
+
+
+def erode(B: np.ndarray) -> np.ndarray:
+    """Binary erosion by the 3 x 3 square: a pixel stays set when all nine pixels of its
+    neighbourhood are set (pixels outside the image count as unset)."""
+    out = np.ones_like(B, dtype=bool)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            out &= _shifted(B.astype(bool), dy, dx)
+    return out
+
+
+def dilate(B: np.ndarray) -> np.ndarray:
+    """Binary dilation by the 3 x 3 square: a pixel is set when any pixel of its
+    neighbourhood is set."""
+    out = np.zeros_like(B, dtype=bool)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            out |= _shifted(B.astype(bool), dy, dx)
+    return out
+
+
+def matrix_mask(sums: np.ndarray, n: int, threshold: float, n_open: int, n_dilate: int) -> np.ndarray:
+    """Mask of the pixels to keep (uint8 1 = keep).  Pixels whose mean over the n patterns
+    exceeds ``threshold`` (sum > threshold * n, in FP64) are the intense matrix reflections;
+    ``n_open`` erosions then ``n_open`` dilations remove noise-like features smaller than the
+    structuring element, ``n_dilate`` further dilations cover the tails of the peaks; the
+    kept pixels are the complement."""
+    B = sums > float(threshold) * float(n)
+    for _ in range(n_open):
+        B = erode(B)
+    for _ in range(n_open + n_dilate):
+        B = dilate(B)
+    return (~B).astype(np.uint8)
+
+
+def apply_mask(frames: np.ndarray, mask: np.ndarray) -> np.ndarray:
+    """Masked patterns: pixels outside the mask set to zero (before gamma and subtraction)."""
+    return frames * mask.astype(frames.dtype)[None]

@@ -231,7 +231,7 @@ def render_scan(rng: np.random.Generator, ts: TemplateSet, n_patterns: int, H: i
                 n_theta: int, dtype=np.uint16, electrons: float = 2000.0,
                 shares=(0.4, 0.4, 0.2), spot_sigma: float = 1.5, beam_sigma: float = 2.0,
                 bg_scale: float | None = None, exact_every: int = 8, chunk: int = 1024,
-                templates: np.ndarray | None = None) -> Scan:
+                templates: np.ndarray | None = None, angles: np.ndarray | None = None) -> Scan:
     """Render ``n_patterns`` frames.  Pattern p shows template k_p ~ U{0..K-1} (K counts
     mirror copies when ``ts.mirror``; a mirror copy reflects ky -> -ky) rotated in plane by
     phi_p ~ U[0, 2pi); every ``exact_every``-th pattern uses phi = m 2pi/n_theta exactly.
@@ -242,7 +242,8 @@ def render_scan(rng: np.random.Generator, ts: TemplateSet, n_patterns: int, H: i
     background exp(-rho/rho0), rho0 = W/8.  Counting noise is Poisson: the counts of each
     part are Poisson and each electron lands at a point drawn from its part's density and
     is binned to the pixel whose centre is nearest (pixel (i, j) is centred on x = j,
-    y = i).  Electrons falling outside the frame are lost.
+    y = i).  Electrons falling outside the frame are lost.  ``templates`` / ``angles`` fix the
+    template and in-plane angle of every pattern instead.
     """
     K0 = ts.n_templates
     K = ts.n_expanded
@@ -254,7 +255,9 @@ def render_scan(rng: np.random.Generator, ts: TemplateSet, n_patterns: int, H: i
         tk = np.asarray(templates, dtype=np.int64)
     phi = rng.uniform(0.0, 2.0 * math.pi, size=n_patterns)
     exact = np.zeros(n_patterns, dtype=bool)
-    if exact_every:
+    if angles is not None:                     # given in-plane angles (no exact subset)
+        phi = np.asarray(angles, dtype=np.float64).copy()
+    elif exact_every:
         exact[::exact_every] = True
         m = rng.integers(0, n_theta, size=int(exact.sum()))
         phi[exact] = m * (2.0 * math.pi / n_theta)
@@ -335,3 +338,30 @@ def single_phase_workload(n_patterns: int = 16384, structure: str = "fcc", step_
     ts = kinematic_library(structure, step_deg=step_deg, max_spots=max_spots)
     scan = render_scan(rng, ts, n_patterns, 256, 256, n_theta=360, dtype=np.uint16)
     return ts, scan, dict(n_r=128, n_theta=360, dr=1.0, gamma=0.5, top_n=5, prefilter=0.5)
+
+
+def two_phase_workload(n_patterns: int = 4096, stream: int = 0, matrix_share: float = 0.5,
+                       precipitate_fraction: float = 0.5):
+    """The two-stage (masked) indexing workload shaped after Section 4.3: every pattern shows
+    one matrix orientation (a single grain: FCC, one template and in-plane angle for the whole
+    scan) with 2000 electrons; a fraction of the patterns also shows a precipitate template
+    (HCP, random template and angle per pattern) with 500 electrons in its spots only.  The
+    paper's G-phase precipitate library is not available; the HCP kinematic library stands
+    in for it.  Returns (matrix TemplateSet, precipitate TemplateSet, frames u16 [n][256][256],
+    dict of the truth)."""
+    rng = make_rng(5, stream)
+    fcc = kinematic_library("fcc")
+    hcp = kinematic_library("hcp")
+    k_m = int(rng.integers(0, fcc.n_expanded))
+    phi_m = float(rng.uniform(0.0, 2.0 * math.pi))
+    mat = render_scan(rng, fcc, n_patterns, 256, 256, n_theta=360,
+                      shares=(matrix_share, (1.0 - matrix_share) * 0.7, (1.0 - matrix_share) * 0.3),
+                      templates=np.full(n_patterns, k_m), angles=np.full(n_patterns, phi_m))
+    pre = render_scan(rng, hcp, n_patterns, 256, 256, n_theta=360, electrons=500.0, shares=(1.0, 0.0, 0.0))
+    has = rng.random(n_patterns) < precipitate_fraction
+    frames = mat.frames.astype(np.int64)
+    frames[has] += pre.frames[has]
+    frames = np.minimum(frames, 65535).astype(np.uint16)
+    truth = dict(matrix_template=k_m, matrix_angle=phi_m, has_precipitate=has,
+                 precipitate_template=pre.template, precipitate_angle=pre.angle)
+    return fcc, hcp, frames, truth

@@ -282,3 +282,49 @@ def test_tiny_workload_recovers_truth():
     m = np.round(scan.angle[ex] / (2 * math.pi / 180)).astype(int) % 180
     err = np.abs(((r["shift"][ex, 0] - m) + 90) % 180 - 90)
     assert np.mean(err <= 1) > 0.95
+
+
+# ------------------------------------------------------------------ two-stage indexing (Section 4.3)
+
+def test_frame_sum_closed_forms():
+    n = 37
+    f = np.broadcast_to(np.arange(n, dtype=np.uint16)[:, None, None], (n, 3, 4)).copy()
+    assert np.array_equal(O.frame_sum(f), np.full((3, 4), n * (n - 1) / 2))
+    g = np.full((n, 2, 2), 0.25, dtype=np.float32)
+    g[5] = 1.5
+    assert np.array_equal(O.frame_sum(g), np.full((2, 2), 0.25 * (n - 1) + 1.5))
+
+
+def test_morphology_closed_forms():
+    B = np.zeros((9, 9), bool)
+    B[4, 4] = True
+    D = O.dilate(B)
+    assert D.sum() == 9 and D[3:6, 3:6].all()                    # a point grows to the 3 x 3 square
+    assert np.array_equal(O.erode(D), B)                          # and shrinks back
+    assert not O.erode(B).any()                                   # an isolated point is eroded
+    full = np.ones((5, 5), bool)
+    E = O.erode(full)                                             # outside counts as unset
+    assert E.sum() == 9 and E[1:4, 1:4].all()
+    blk = np.zeros((11, 11), bool)
+    blk[2:7, 3:8] = True
+    assert np.array_equal(O.dilate(O.erode(blk)), blk)            # opening keeps a 5 x 5 block
+
+
+def test_matrix_mask_removes_specks_and_covers_tails():
+    n = 10
+    sums = np.zeros((21, 21))
+    sums[2, 2] = 100.0 * n                                        # one-pixel speck (noise)
+    sums[9:12, 9:12] = 50.0 * n                                   # a 3 x 3 intense reflection
+    sums[15, 15] = 0.5 * n                                        # below the threshold
+    M = O.matrix_mask(sums, n, threshold=1.0, n_open=1, n_dilate=2)
+    assert M.dtype == np.uint8
+    masked = M == 0
+    assert masked.sum() == 49 and masked[7:14, 7:14].all()        # 3 x 3 opened, dilated twice -> 7 x 7
+    assert M[2, 2] == 1 and M[15, 15] == 1
+    # exactly at the threshold: sum > threshold * n is strict
+    s2 = np.zeros((3, 3))
+    s2[1, 1] = 2.0 * n
+    assert O.matrix_mask(s2, n, threshold=2.0, n_open=0, n_dilate=0).all()
+    f = np.full((2, 21, 21), 7, dtype=np.uint16)
+    fm = O.apply_mask(f, M)
+    assert fm.dtype == np.uint16 and fm[:, 10, 10].sum() == 0 and np.all(fm[:, 0, 0] == 7)
