@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", default="fp32,bf16", help="paths to time (fp32, bf16)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
+    ap.add_argument("--no-two-stage", action="store_true", help="skip the two-stage (masked) indexing run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -165,6 +166,56 @@ def cpu_baseline(ts, scan, seconds: float) -> dict:
     dt = time.perf_counter() - t
     return {"value": n / dt, "unit": "patterns/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"first {n} patterns of the scan, whole path (polar, pre-filter, Q, top-5), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ two-stage (masked) indexing
+
+def two_stage_bench(ctx, stream, steps: int, n_total: int = 16384, unique: int = 2048) -> dict:
+    """The masked indexing of Section 4.3 on the two-phase scan (single-grain FCC matrix, HCP
+    precipitates in half of the patterns): per step the per-pixel sums over the scan, the
+    mask (threshold 1 count per pattern, one opening, two dilations) and the FP32 indexing of
+    the masked patterns against the precipitate library (unit intensities, subtraction 0.4).
+    The scan is `unique` rendered frames repeated on the device."""
+    import torch
+    fcc, hcp, frames, truth = synth.two_phase_workload(unique)
+    base = torch.from_numpy(frames.view(np.int16)).cuda()
+    dev = base.repeat(n_total // unique, 1, 1).view(torch.uint16)
+    lh = ctx.load_library(hcp, N_R, N_THETA, unit_intensity=True)
+    out = torch.empty((1, n_total, TOP_N, 5), dtype=torch.int32, device="cuda")
+    sums = torch.empty((256, 256), dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(rec):
+        if rec:
+            ev[0].record(stream)
+        ctx.frame_sum(dev, out=sums)
+        if rec:
+            ev[1].record(stream)
+        mask = ctx.matrix_mask(sums, n_total, 1.0, n_open=1, n_dilate=2)
+        if rec:
+            ev[2].record(stream)
+        ctx.index(dev, lh, top_n=TOP_N, subtract=0.4, mask=mask, out=out)
+        if rec:
+            ev[3].record(stream)
+        return mask
+
+    for _ in range(2):
+        step(False)
+    torch.cuda.synchronize()
+    t = np.zeros(3)
+    for _ in range(steps):
+        mask = step(True)
+        torch.cuda.synchronize()
+        t += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+    t /= steps
+    ms = float(t.sum())
+    masked = int((mask == 0).sum().item())
+    ctx.unload_library(lh)
+    return {"patterns_per_s": n_total / (ms / 1e3), "ms_per_step": ms, "sum_ms": float(t[0]), "mask_ms": float(t[1]),
+            "index_ms": float(t[2]), "sum_gbs": n_total * 256 * 256 * 2 / (t[0] / 1e3) / 1e9,
+            "masked_pixels": masked, "patterns": n_total, "library": f"HCP 0.5 deg, {hcp.n_expanded} templates",
+            "workload": "two-phase scan (FCC single grain + HCP precipitates in half the patterns), "
+                        f"{unique} rendered 256x256 u16 frames repeated to {n_total}"}
 
 
 # ------------------------------------------------------------------ serving loop (scan lines and maps)
@@ -465,6 +516,8 @@ def run_ours(args):
             "macs_per_step_sparse": macs_step, "survivors_per_step": survivors_step,
             "roofline": roofline, "stages": stages, "e2e": e2e,
             "gpu_launches": int(launches_per_step * args.steps), "clocks": clk}
+    if not args.no_two_stage:
+        line["two_stage"] = two_stage_bench(ctx, stream, max(2, args.steps // 2))
     if not args.no_serving:
         hcp = synth.kinematic_library("hcp")
         lid_h = ctx.load_library(hcp, N_R, N_THETA)

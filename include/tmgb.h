@@ -109,6 +109,9 @@ typedef struct tm_index_params {
     int32_t path;                 /* TM_PATH_FP32_SPARSE or TM_PATH_BF16_RESCORE         */
     int32_t rescore_k;            /* BF16 path: candidates rescored exactly (default 256) */
     int32_t reserved;             /* TM_INDEX_* flags                                     */
+    const uint8_t* pixel_mask;    /* device [H][W] bytes, 16-byte aligned, or NULL: pixels
+                                     whose byte is 0 read as 0 before gamma and subtraction
+                                     (masked indexing, Section 4.3; see tm_matrix_mask)   */
 } tm_index_params;
 
 /* tm_index_params.reserved flag: replay the call as a CUDA graph.  The first call with a
@@ -304,8 +307,28 @@ int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* params, const 
                               int32_t dtype, int64_t n, int32_t H, int32_t W, int32_t lib_id,
                               tm_hit* out_dev, void* stream);
 
+/* ---------------------------------------------------------------- two-stage indexing
+ * Section 4.3: the intense matrix reflections are removed from every pattern with a mask
+ * made from the average of all patterns, thresholded, then cleaned by erosions (noise-like
+ * features) and dilations (tails of intense peaks); the masked patterns are indexed against
+ * the precipitate library (tm_index_params.pixel_mask). */
+
+/* Per-pixel sum over frames: sum_dev [H][W] double = (accumulate ? sum_dev : 0) + sum over
+ * p of frames_dev[p] in frame order, in FP64 (exact for u16 frames; the fixed order makes
+ * f32 results reproducible and chunked sums equal one pass).  Asynchronous on stream. */
+int tm_frame_sum(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t n, int32_t H, int32_t W,
+                 int32_t accumulate, double* sum_dev, void* stream);
+
+/* Mask of the pixels to keep: mask_dev [H][W] bytes, 1 = keep.  Set pixels are those with
+ * sum > threshold * n_frames (FP64; the mean exceeds threshold); then n_open erosions, n_open
+ * dilations (an opening: removes features smaller than the 3 x 3 structuring element) and
+ * n_dilate further dilations (cover the tails of the peaks); pixels outside the image count as
+ * unset; the mask is the complement.  Asynchronous on stream. */
+int tm_matrix_mask(tm_ctx* ctx, const double* sum_dev, int64_t n_frames, int32_t H, int32_t W, double threshold,
+                   int32_t n_open, int32_t n_dilate, uint8_t* mask_dev, void* stream);
+
 /* Default parameters: gamma 0.5, subtract 0, centre NaN, prefilter 1, top_n 5,
- * FP32 sparse path, rescore_k 256. */
+ * FP32 sparse path, rescore_k 256, no pixel mask. */
 void tm_index_params_default(tm_index_params* p);
 
 /* ---------------------------------------------------------------- serving loop

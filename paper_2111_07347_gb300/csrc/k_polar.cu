@@ -56,6 +56,35 @@ __device__ __forceinline__ T load_px(const T* p) {
     return __ldg(p);
 }
 
+// Pixel mask (Section 4.3, masked indexing): pixels whose mask byte is 0 read as 0.
+// Global taps: the mask has the frame's layout (row pitch W).
+template <bool SMEM, typename T>
+__device__ __forceinline__ T load_px_masked(const T* p, const T* frame, const uint8_t* pmask) {
+    const T v = load_px<SMEM>(p);
+    if (SMEM || !pmask) return v;
+    return __ldg(pmask + (p - frame)) ? v : T(0);
+}
+
+// A 16-byte vector of pixels starting at pixel 16 i / sizeof(T) of the frame, masked.
+__device__ __forceinline__ uint32_t keep_pair(uint32_t mb) {   // mask bytes at bits 0..7, 8..15
+    return ((mb & 0xffu) ? 0x0000ffffu : 0u) | ((mb & 0xff00u) ? 0xffff0000u : 0u);
+}
+__device__ __forceinline__ void mask_vector(uint4& v, const uint8_t* pmask, int i) {
+    // u16 frames: 8 pixels per vector (the float variant below takes 4)
+    const uint2 m = __ldg(reinterpret_cast<const uint2*>(pmask) + i);
+    v.x &= keep_pair(m.x);
+    v.y &= keep_pair(m.x >> 16);
+    v.z &= keep_pair(m.y);
+    v.w &= keep_pair(m.y >> 16);
+}
+__device__ __forceinline__ void mask_vector4(uint4& v, const uint8_t* pmask, int i) {
+    const uint32_t m = __ldg(reinterpret_cast<const uint32_t*>(pmask) + i);
+    v.x = (m & 0xffu) ? v.x : 0u;
+    v.y = (m & 0xff00u) ? v.y : 0u;
+    v.z = (m & 0xff0000u) ? v.z : 0u;
+    v.w = (m & 0xff000000u) ? v.w : 0u;
+}
+
 // g(v) - sub of one raw pixel.  u16: from the table lut[v] = g(v) - sub (filled with the same
 // functions), computed directly for v >= kLut.
 template <int MODE>
@@ -83,11 +112,12 @@ __device__ __forceinline__ void fixed_weights(uint32_t q, float& f, float& g) {
 // has row pitch `pitch` elements; taps outside [0, W) x [0, H) contribute zero.
 template <typename T, int MODE, bool SMEM>
 __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int W, int x0, int y0, float fx,
-                                          float gx, float fy, float gy, const float* lut, float g, float sub) {
+                                          float gx, float fy, float gy, const float* lut, float g, float sub,
+                                          const uint8_t* pmask) {
     if ((unsigned)x0 < (unsigned)(W - 1) && (unsigned)y0 < (unsigned)(H - 1)) {
         const T* p = frame + y0 * pitch + x0;
-        const T a = load_px<SMEM>(p), b = load_px<SMEM>(p + 1);
-        const T c = load_px<SMEM>(p + pitch), d = load_px<SMEM>(p + pitch + 1);
+        const T a = load_px_masked<SMEM>(p, frame, pmask), b = load_px_masked<SMEM>(p + 1, frame, pmask);
+        const T c = load_px_masked<SMEM>(p + pitch, frame, pmask), d = load_px_masked<SMEM>(p + pitch + 1, frame, pmask);
         float v00, v10, v01, v11;
         if (all_in_lut(a, b, c, d)) {
             v00 = lut[(int)a];
@@ -108,7 +138,7 @@ __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int 
         const int x = x0 + (t & 1), y = y0 + (t >> 1);
         v[t] = 0.0f;
         if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H)
-            v[t] = tap_value<MODE>(load_px<SMEM>(frame + y * pitch + x), lut, g, sub);
+            v[t] = tap_value<MODE>(load_px_masked<SMEM>(frame + y * pitch + x, frame, pmask), lut, g, sub);
     }
     return gy * (gx * v[0] + fx * v[1]) + fy * (gx * v[2] + fx * v[3]);
 }
@@ -152,7 +182,7 @@ template <typename T, int MODE, bool STAGED, bool CENTRES>
 __device__ __forceinline__ float sample(const T* frame, int pitch, int H, int W, int idx,
                                        const int32_t* __restrict__ txy, const uint2* __restrict__ tq,
                                        const float4* __restrict__ toff, float2 cen, const float* lut, float g,
-                                       float sub) {
+                                       float sub, const uint8_t* pmask) {
     int x0, y0;
     float fx, gx, fy, gy;
     if (CENTRES) {
@@ -167,7 +197,7 @@ __device__ __forceinline__ float sample(const T* frame, int pitch, int H, int W,
         fixed_weights(q.x, fx, gx);
         fixed_weights(q.y, fy, gy);
     }
-    return bilinear<T, MODE, STAGED>(frame, pitch, H, W, x0, y0, fx, gx, fy, gy, lut, g, sub);
+    return bilinear<T, MODE, STAGED>(frame, pitch, H, W, x0, y0, fx, gx, fy, gy, lut, g, sub, pmask);
 }
 
 constexpr int kMaxThreads = 768;            // 80 registers per thread at one CTA per SM
@@ -176,7 +206,8 @@ template <typename T, int MODE, bool STAGED, bool CENTRES>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, const int32_t* __restrict__ txy,
              const uint2* __restrict__ tq, float g, float sub, int n_r, int n_theta, int R,
-             const uint8_t* __restrict__ keep_row, float* __restrict__ polar, float* __restrict__ pnorm,
+             const uint8_t* __restrict__ keep_row, const uint8_t* __restrict__ pmask, float* __restrict__ polar,
+             float* __restrict__ pnorm,
              float* __restrict__ radial, const float2* __restrict__ centres, const float4* __restrict__ toff) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int cols = blockDim.x / R;                     // threads per row group (multiple of 32)
@@ -212,7 +243,13 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
 #pragma unroll
                     for (int b = 0; b < B; ++b) {
                         const int i = i0 + b * blockDim.x;
-                        if (i < nv) v[b] = __ldg(src + i);
+                        if (i < nv) {
+                            v[b] = __ldg(src + i);
+                            if (pmask) {
+                                if (sizeof(T) == 2) mask_vector(v[b], pmask, i);
+                                else mask_vector4(v[b], pmask, i);
+                            }
+                        }
                     }
 #pragma unroll
                     for (int b = 0; b < B; ++b) {
@@ -230,7 +267,7 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
             } else {
                 for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
                     const int y = e / W;
-                    sF[(size_t)y * pitch + (e - y * W)] = gframe[e];
+                    sF[(size_t)y * pitch + (e - y * W)] = (!pmask || pmask[e]) ? gframe[e] : T(0);
                 }
             }
             __syncthreads();
@@ -256,12 +293,12 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         v[u] = sample<T, MODE, STAGED, CENTRES>(frame, pf, H, W, idx0 + u * rstride, txy, tq, toff,
-                                                                cen, lut, g, sub);
+                                                                cen, lut, g, sub, pmask);
                 } else {
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         v[u] = u < nu ? sample<T, MODE, STAGED, CENTRES>(frame, pf, H, W, idx0 + u * rstride, txy, tq,
-                                                                         toff, cen, lut, g, sub)
+                                                                         toff, cen, lut, g, sub, pmask)
                                       : 0.0f;
                 }
 #pragma unroll
@@ -305,8 +342,9 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
 
 template <typename T, int MODE, bool STAGED, bool CENTRES>
 cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab, float g, float sub,
-                       int n_r, int n_theta, int R, int threads, size_t smem, const uint8_t* keep_row, float* polar,
-                       float* pnorm, float* radial, const float2* centres, const float4* offsets, cudaStream_t st) {
+                       int n_r, int n_theta, int R, int threads, size_t smem, const uint8_t* keep_row,
+                       const uint8_t* pmask, float* polar, float* pnorm, float* radial, const float2* centres,
+                       const float4* offsets, cudaStream_t st) {
     auto kern = polar_kernel<T, MODE, STAGED, CENTRES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -317,29 +355,29 @@ cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, cons
     int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > n) grid = n;
     kern<<<(int)grid, threads, smem, st>>>(frames, n, H, W, pitch, tab.xy, tab.q, g, sub, n_r, n_theta, R, keep_row,
-                                           polar, pnorm, radial, centres, offsets);
+                                           pmask, polar, pnorm, radial, centres, offsets);
     return cudaGetLastError();
 }
 
 template <typename T, bool STAGED>
 cudaError_t launch_mode(int mode, const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab,
                         float g, float sub, int n_r, int n_theta, int R, int threads, size_t smem,
-                        const uint8_t* keep_row, float* polar, float* pnorm, float* radial, const float2* centres,
-                        const float4* offsets, cudaStream_t st) {
+                        const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm, float* radial,
+                        const float2* centres, const float4* offsets, cudaStream_t st) {
     if (mode == 0)
         return (centres ? launch_one<T, 0, STAGED, true> : launch_one<T, 0, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
-                                        polar, pnorm, radial, centres, offsets, st);
+                                        pmask, polar, pnorm, radial, centres, offsets, st);
     if (mode == 1)
         return (centres ? launch_one<T, 1, STAGED, true> : launch_one<T, 1, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
-                                        polar, pnorm, radial, centres, offsets, st);
+                                        pmask, polar, pnorm, radial, centres, offsets, st);
     return (centres ? launch_one<T, 2, STAGED, true> : launch_one<T, 2, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
-                                    polar, pnorm, radial, centres, offsets, st);
+                                    pmask, polar, pnorm, radial, centres, offsets, st);
 }
 
 template <typename T>
 cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const PolarTable& tab, int mode, float g,
                          float sub, int n_r, int n_theta, float* polar, float* pnorm, float* radial, cudaStream_t st,
-                         const uint8_t* keep_row, const float2* centres, const float4* offsets) {
+                         const uint8_t* keep_row, const float2* centres, const float4* offsets, const uint8_t* pmask) {
     const int cols = ((n_theta + 31) / 32) * 32;
     if (cols <= kMaxThreads) {
         // staged: rows padded to an odd number of 32-bit words
@@ -354,13 +392,13 @@ cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const PolarTa
         const size_t smem = fbytes + lut + ((size_t)n_r * nw + threads) * sizeof(float);
         if (smem <= 200 * 1024)
             return launch_mode<T, true>(mode, frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem,
-                                        keep_row, polar, pnorm, radial, centres, offsets, st);
+                                        keep_row, pmask, polar, pnorm, radial, centres, offsets, st);
     }
     const int threads = cols < kMaxThreads ? cols : kMaxThreads;
     const size_t smem = (sizeof(T) == 2 ? kLut * sizeof(float) : 0) + ((size_t)n_r * (threads / 32) + threads) * sizeof(float);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     return launch_mode<T, false>(mode, frames, n, H, W, W, tab, g, sub, n_r, n_theta, 1, threads, smem, keep_row,
-                                 polar, pnorm, radial, centres, offsets, st);
+                                 pmask, polar, pnorm, radial, centres, offsets, st);
 }
 
 }  // namespace
@@ -390,14 +428,15 @@ void build_polar_taps(int H, int W, int n_r, int n_theta, double dr, double cx, 
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st, const uint8_t* keep_row, const float2* centres, const float4* offsets) {
+                         cudaStream_t st, const uint8_t* keep_row, const float2* centres, const float4* offsets,
+                         const uint8_t* pixel_mask) {
     if (n <= 0) return cudaSuccess;
     const int mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
     if (dtype == TM_DTYPE_U16)
         return launch_typed<uint16_t>((const uint16_t*)frames, n, H, W, tab, mode, (float)gamma, (float)subtract, n_r,
-                                      n_theta, polar, pnorm, radial, st, keep_row, centres, offsets);
+                                      n_theta, polar, pnorm, radial, st, keep_row, centres, offsets, pixel_mask);
     return launch_typed<float>((const float*)frames, n, H, W, tab, mode, (float)gamma, (float)subtract, n_r, n_theta,
-                               polar, pnorm, radial, st, keep_row, centres, offsets);
+                               polar, pnorm, radial, st, keep_row, centres, offsets, pixel_mask);
 }
 
 }  // namespace tmgb

@@ -641,6 +641,7 @@ int check_params(const tm_index_params* p) {
     if (!(p->prefilter_fraction > 0.0 && p->prefilter_fraction <= 1.0))
         return fail(TM_ERR_INVALID_ARG, "prefilter_fraction must be in (0, 1]");
     if (p->top_n < 1 || p->top_n > TM_MAX_TOPN) return fail(TM_ERR_INVALID_ARG, "top_n must be in [1, %d]", TM_MAX_TOPN);
+    if (((uintptr_t)p->pixel_mask & 15) != 0) return fail(TM_ERR_INVALID_ARG, "pixel_mask must be 16-byte aligned");
     return TM_OK;
 }
 
@@ -760,6 +761,46 @@ int tm_index_patterns_host(tm_ctx* ctx, const tm_index_params* params, const voi
     return rc;
 }
 
+int tm_frame_sum(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t n, int32_t H, int32_t W,
+                 int32_t accumulate, double* sum_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_frame_sum: ctx is NULL");
+    if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000) return fail(TM_ERR_INVALID_ARG, "tm_frame_sum: bad shape");
+    if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_frame_sum: dtype");
+    if (!sum_dev || (n > 0 && !frames_dev)) return fail(TM_ERR_INVALID_ARG, "tm_frame_sum: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0 && !accumulate) {
+        TM_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)H * W * sizeof(double), st), "tm_frame_sum: memset");
+        return TM_OK;
+    }
+    TM_CUDA(tmgb::launch_frame_sum(frames_dev, dtype, n, H, W, accumulate ? 1 : 0, sum_dev, ctx->num_sms, st),
+            "tm_frame_sum: launch");
+    return TM_OK;
+}
+
+int tm_matrix_mask(tm_ctx* ctx, const double* sum_dev, int64_t n_frames, int32_t H, int32_t W, double threshold,
+                   int32_t n_open, int32_t n_dilate, uint8_t* mask_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_matrix_mask: ctx is NULL");
+    if (n_frames < 1 || H < 1 || W < 1 || H > 32000 || W > 32000)
+        return fail(TM_ERR_INVALID_ARG, "tm_matrix_mask: bad shape or frame count");
+    if (!isfinite(threshold)) return fail(TM_ERR_INVALID_ARG, "tm_matrix_mask: threshold must be finite");
+    if (n_open < 0 || n_dilate < 0 || n_open > 1000 || n_dilate > 1000)
+        return fail(TM_ERR_INVALID_ARG, "tm_matrix_mask: n_open and n_dilate must be in [0, 1000]");
+    if (!sum_dev || !mask_dev) return fail(TM_ERR_INVALID_ARG, "tm_matrix_mask: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    void* scratch = nullptr;
+    int rc = workspace(ctx, st, "mask_scratch", (size_t)H * W, &scratch);
+    if (rc) return rc;
+    const double thr_n = threshold * (double)n_frames;       // the comparison of the oracle: sum > threshold * n
+    TM_CUDA(tmgb::launch_matrix_mask(sum_dev, H, W, thr_n, n_open, n_dilate, mask_dev, (uint8_t*)scratch,
+                                     ctx->num_sms, st),
+            "tm_matrix_mask: launch");
+    return TM_OK;
+}
+
 void tm_index_params_default(tm_index_params* p) {
     if (!p) return;
     p->gamma = 0.5;
@@ -771,6 +812,7 @@ void tm_index_params_default(tm_index_params* p) {
     p->path = TM_PATH_FP32_SPARSE;
     p->rescore_k = 256;
     p->reserved = 0;
+    p->pixel_mask = nullptr;
 }
 
 const char* tm_last_error(void) { return g_err.c_str(); }
@@ -1006,7 +1048,8 @@ int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* f
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     TM_CUDA(tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                             polar_dev, norm_dev, radial_dev, st, nullptr, (const float2*)centres_dev, offs),
+                             polar_dev, norm_dev, radial_dev, st, nullptr, (const float2*)centres_dev, offs,
+                             params->pixel_mask),
             "tm_polar_transform: launch");
     return TM_OK;
 }
@@ -1191,7 +1234,8 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                 StageTimer tmr(ctx, TM_STAGE_POLAR, st);
                 TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
                                            polar, pnorm, radial, st, rmap.keep_row,
-                                           centres_dev ? (const float2*)centres_dev + c0 : nullptr, offs),
+                                           centres_dev ? (const float2*)centres_dev + c0 : nullptr, offs,
+                                           params->pixel_mask),
                         "tm_index_patterns: polar");
             }
             ++launches;
@@ -1303,10 +1347,10 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     // CUDA graph: the second identical call on a created stream is captured, later ones replay
     if ((params->reserved & TM_INDEX_GRAPH) && st != nullptr && !ctx->profiling) {
         char key[512];
-        int off = snprintf(key, sizeof key, "%p|%p|%p|%p|%d|%lld|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|", st,
-                           frames_dev, (const void*)centres_dev, (void*)out_dev, dtype, (long long)n, H, W, params->gamma, params->subtract,
-                           params->cx, params->cy, params->prefilter_fraction, params->top_n, params->path,
-                           params->rescore_k);
+        int off = snprintf(key, sizeof key, "%p|%p|%p|%p|%p|%d|%lld|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|", st,
+                           frames_dev, (const void*)centres_dev, (void*)out_dev, (const void*)params->pixel_mask, dtype,
+                           (long long)n, H, W, params->gamma, params->subtract, params->cx, params->cy,
+                           params->prefilter_fraction, params->top_n, params->path, params->rescore_k);
         for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);
         tm_ctx::GraphEntry& ge = ctx->graphs[key];
         if (ge.exec && ge.ws_gen == ctx->ws_gen) {
@@ -1380,6 +1424,7 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
     tm_index_params p = *params;
     p.path = TM_PATH_FP32_SPARSE;
     p.reserved = 0;
+    p.pixel_mask = nullptr;
     const int cand[3] = {128, 256, 512};
     int best = 256;
     double best_ms = 1e30;

@@ -66,7 +66,15 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
                          cudaStream_t st, const uint8_t* keep_row = nullptr,
-                         const float2* centres = nullptr, const float4* offsets = nullptr);
+                         const float2* centres = nullptr, const float4* offsets = nullptr,
+                         const uint8_t* pixel_mask = nullptr);
+
+// Two-stage indexing (Section 4.3): per-pixel FP64 sums over frames (accumulate: add onto
+// out), and the mask of kept pixels from the sums (scratch: H * W bytes).
+cudaError_t launch_frame_sum(const void* frames, int dtype, int64_t n, int H, int W, int accumulate, double* out,
+                             int num_sms, cudaStream_t st);
+cudaError_t launch_matrix_mask(const double* sum, int H, int W, double thr_n, int n_open, int n_dilate,
+                               uint8_t* mask, uint8_t* scratch, int num_sms, cudaStream_t st);
 
 cudaError_t launch_radial_norm(const float* radial, int64_t n, int n_r, float* out,
                                cudaStream_t st);
