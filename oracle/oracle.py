@@ -21,6 +21,8 @@ Steps, in the paper's order (Section 2.2):
   matrix-vector product; the best fraction kept (Section 2.2, Fig. 3).
 * ``top_n``            -- templates ranked by their best Q (Section 2.2: "sorted and
   the top N best matching templates can be queried").
+* ``find_centres`` -- the direct beam's centre per pattern (centre of mass in a disc), and
+  ``polar(threshold=...)`` -- low-intensity pixels set to zero (Section 3.1's preprocessing).
 * ``frame_sum`` / ``matrix_mask`` / ``apply_mask`` -- the two-stage indexing of Section 4.3:
   mean of all patterns, thresholded, cleaned by erosions and dilations, and the masked
   patterns indexed again.
@@ -163,10 +165,15 @@ def prepare_library(ts, n_r: int, n_theta: int, dr: float = 1.0, mirror: bool | 
 # ----------------------------------------------------------------------------------
 
 def polar(frames: np.ndarray, n_r: int, n_theta: int, dr: float = 1.0, gamma: float = 0.5,
-          subtract: float = 0.0, centre=None, centres: np.ndarray | None = None) -> np.ndarray:
+          subtract: float = 0.0, centre=None, centres: np.ndarray | None = None,
+          threshold: float = 0.0) -> np.ndarray:
     """Gamma/subtract then bilinear polar resampling: [n][H][W] -> [n][n_r][n_theta] FP64.
-    Default centre ((W-1)/2, (H-1)/2); ``centres`` [n][2] overrides per pattern."""
+    Default centre ((W-1)/2, (H-1)/2); ``centres`` [n][2] overrides per pattern.  A positive
+    ``threshold`` first sets pixels below it to zero (Section 3.1: low-intensity pixels set to
+    zero before the gamma correction)."""
     frames = np.ascontiguousarray(frames)
+    if threshold > 0.0:
+        frames = np.where(frames < threshold, 0, frames).astype(frames.dtype)
     if frames.dtype == np.uint16:
         dt = 0
     elif frames.dtype == np.float32:
@@ -261,10 +268,11 @@ def top_n(q_best: np.ndarray, s_best: np.ndarray, N: int, active: np.ndarray | N
 
 
 def index(frames: np.ndarray, lib: Library, gamma: float = 0.5, subtract: float = 0.0,
-          prefilter_fraction: float = 1.0, N: int = 5, centre=None, centres: np.ndarray | None = None):
+          prefilter_fraction: float = 1.0, N: int = 5, centre=None, centres: np.ndarray | None = None,
+          threshold: float = 0.0):
     """The whole path for a batch of frames; returns a dict of FP64 results.  ``centres``
     [n][2] gives each pattern's own beam centre."""
-    P = polar(frames, lib.n_r, lib.n_theta, lib.dr, gamma, subtract, centre, centres)
+    P = polar(frames, lib.n_r, lib.n_theta, lib.dr, gamma, subtract, centre, centres, threshold)
     active = None
     if prefilter_fraction < 1.0:
         active, _ = prefilter(P, lib, prefilter_fraction)
@@ -374,3 +382,39 @@ def matrix_mask(sums: np.ndarray, n: int, threshold: float, n_open: int, n_dilat
 def apply_mask(frames: np.ndarray, mask: np.ndarray) -> np.ndarray:
     """Masked patterns: pixels outside the mask set to zero (before gamma and subtraction)."""
     return frames * mask.astype(frames.dtype)[None]
+
+
+# ----------------------------------------------------------------------------------
+# Direct-beam centring (Section 3.1: "the direct beam in each image was centered"): the
+# centre used for the polar transform is found per pattern.
+# ----------------------------------------------------------------------------------
+
+def find_centres(frames: np.ndarray, centre, radius: float, iterations: int) -> np.ndarray:
+    """Per pattern, the intensity-weighted centre of mass of the pixels within ``radius`` of
+    the current estimate (starting at ``centre`` = (cx, cy)), repeated ``iterations`` times.
+    FP64, pixels visited row by row (y, then x ascending) over the disc's bounding box,
+    distances compared as (dx*dx) + (dy*dy) <= radius*radius; a disc with zero total
+    intensity keeps the estimate.  Returns [n][2] float32 (the index call's centre type)."""
+    n, H, W = frames.shape
+    out = np.empty((n, 2), dtype=np.float32)
+    r2 = float(radius) * float(radius)
+    for p in range(n):
+        f = frames[p]
+        cx, cy = float(centre[0]), float(centre[1])
+        for _ in range(iterations):
+            y_lo, y_hi = max(0, math.ceil(cy - radius)), min(H - 1, math.floor(cy + radius))
+            x_lo, x_hi = max(0, math.ceil(cx - radius)), min(W - 1, math.floor(cx + radius))
+            s0 = sx = sy = 0.0
+            for y in range(y_lo, y_hi + 1):
+                dy = y - cy
+                for x in range(x_lo, x_hi + 1):
+                    dx = x - cx
+                    if dx * dx + dy * dy <= r2:
+                        v = float(f[y, x])
+                        s0 += v
+                        sx += float(x) * v
+                        sy += float(y) * v
+            if s0 > 0.0:
+                cx, cy = sx / s0, sy / s0
+        out[p] = (cx, cy)
+    return out

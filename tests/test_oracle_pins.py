@@ -328,3 +328,36 @@ def test_matrix_mask_removes_specks_and_covers_tails():
     f = np.full((2, 21, 21), 7, dtype=np.uint16)
     fm = O.apply_mask(f, M)
     assert fm.dtype == np.uint16 and fm[:, 10, 10].sum() == 0 and np.all(fm[:, 0, 0] == 7)
+
+
+# ------------------------------------------------------------------ preprocessing: centring, threshold (Section 3.1)
+
+def test_find_centres_symmetric_blob_and_shift():
+    f = np.zeros((2, 32, 40), dtype=np.uint16)
+    # a blob symmetric about (x, y) = (17, 12): its centre of mass is exactly that point
+    for dy in range(-2, 3):
+        for dx in range(-2, 3):
+            f[0, 12 + dy, 17 + dx] = 10 - 2 * (abs(dx) + abs(dy))
+    f[1] = np.roll(f[0], (3, -4), axis=(0, 1))                      # moved by (dx, dy) = (-4, 3)
+    c = O.find_centres(f, (15.0, 14.0), radius=6.0, iterations=3)
+    assert np.array_equal(c, np.array([[17.0, 12.0], [13.0, 15.0]], dtype=np.float32))
+    z = np.zeros((1, 8, 8), dtype=np.float32)                        # nothing in the disc: estimate kept
+    assert np.array_equal(O.find_centres(z, (3.5, 2.25), 2.0, 4), np.array([[3.5, 2.25]], dtype=np.float32))
+
+
+def test_find_centres_disc_membership():
+    f = np.zeros((1, 9, 9), dtype=np.uint16)
+    f[0, 4, 4] = 1
+    f[0, 4, 7] = 1                                                   # distance 3 from (4, 4)
+    assert np.array_equal(O.find_centres(f, (4.0, 4.0), 2.9, 1)[0], np.float32([4.0, 4.0]))
+    assert np.array_equal(O.find_centres(f, (4.0, 4.0), 3.0, 1)[0], np.float32([5.5, 4.0]))
+
+
+def test_threshold_sets_low_pixels_to_zero():
+    f = np.full((1, 16, 16), 9, dtype=np.uint16)
+    f[0, :, :8] = 3
+    P0 = O.polar(f, 6, 8, gamma=1.0)
+    P1 = O.polar(f, 6, 8, gamma=1.0, threshold=5.0)
+    P2 = O.polar(np.where(f < 5, 0, f).astype(np.uint16), 6, 8, gamma=1.0)
+    assert np.array_equal(P1, P2) and not np.array_equal(P0, P1)
+    assert np.array_equal(O.polar(f, 6, 8, threshold=3.0), O.polar(f, 6, 8))   # strict: 3 < 3 is false
