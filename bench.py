@@ -177,6 +177,7 @@ def two_stage_bench(ctx, stream, steps: int, n_total: int = 16384, unique: int =
     the masked patterns against the precipitate library (unit intensities, subtraction 0.4).
     The scan is `unique` rendered frames repeated on the device."""
     import torch
+    from paper_2111_07347_gb300 import synth
     fcc, hcp, frames, truth = synth.two_phase_workload(unique)
     base = torch.from_numpy(frames.view(np.int16)).cuda()
     dev = base.repeat(n_total // unique, 1, 1).view(torch.uint16)

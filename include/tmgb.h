@@ -112,6 +112,8 @@ typedef struct tm_index_params {
     const uint8_t* pixel_mask;    /* device [H][W] bytes, 16-byte aligned, or NULL: pixels
                                      whose byte is 0 read as 0 before gamma and subtraction
                                      (masked indexing, Section 4.3; see tm_matrix_mask)   */
+    double threshold;             /* > 0: raw pixels below it read as 0 before gamma
+                                     (Section 3.1: low-intensity pixels set to zero); 0 = off */
 } tm_index_params;
 
 /* tm_index_params.reserved flag: replay the call as a CUDA graph.  The first call with a
@@ -327,8 +329,19 @@ int tm_frame_sum(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t n, 
 int tm_matrix_mask(tm_ctx* ctx, const double* sum_dev, int64_t n_frames, int32_t H, int32_t W, double threshold,
                    int32_t n_open, int32_t n_dilate, uint8_t* mask_dev, void* stream);
 
+/* Direct-beam centring (Section 3.1: the beam of every pattern is centred; the polar
+ * transform's origin is the beam's centre, Section 2.2).  centres_dev [n][2] float receives,
+ * per pattern, the intensity-weighted centre of mass (x = column, y = row) of the raw pixels
+ * within `radius` of the current estimate, recomputed `iterations` times starting from
+ * (cx0, cy0) (NaN -> ((W-1)/2, (H-1)/2)); FP64 sums over the disc's bounding box row by row,
+ * distances as dx*dx + dy*dy <= radius*radius; an empty disc keeps the estimate.  Pass the
+ * result as tm_index_patterns' centres_dev.  radius in (0, 1e4], iterations in [1, 100].
+ * Asynchronous on stream. */
+int tm_find_centres(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t n, int32_t H, int32_t W,
+                    double cx0, double cy0, double radius, int32_t iterations, float* centres_dev, void* stream);
+
 /* Default parameters: gamma 0.5, subtract 0, centre NaN, prefilter 1, top_n 5,
- * FP32 sparse path, rescore_k 256, no pixel mask. */
+ * FP32 sparse path, rescore_k 256, no pixel mask, no threshold. */
 void tm_index_params_default(tm_index_params* p);
 
 /* ---------------------------------------------------------------- serving loop

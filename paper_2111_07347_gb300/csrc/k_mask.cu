@@ -5,7 +5,9 @@
 //
 // frame_sum_kernel: one thread per pixel adds the pixel over the frames in frame order, in
 //   FP64 (exact for u16 frames; a fixed order for f32), optionally onto a previous sum, so
-//   a scan may be summed chunk by chunk with the same result.
+//   a scan may be summed chunk by chunk with the same result.  For u16 frames, whose sums
+//   are exact integers in any order, groups of frames are summed in parallel in 64-bit
+//   integers and the partials added, which keeps the whole GPU busy.
 // threshold_kernel / morph_kernel: the binary image (sum > threshold * n) and one 3 x 3
 //   erosion or dilation step (pixels outside the image count as unset); the kept pixels
 //   are the complement of the final image.
@@ -29,6 +31,40 @@ __global__ void frame_sum_kernel(const T* __restrict__ frames, int64_t n, int64_
             for (int u = 0; u < 8; ++u) s += (double)v[u];
         }
         for (; f < n; ++f) s += (double)__ldg(p + f * hw);
+        out[i] = s;
+    }
+}
+
+// u16 frames: the sums are integers below 2^53, exact in any order, so groups of frames are
+// summed in parallel (partial [groups][hw]) and the partials added afterwards.
+__global__ void frame_sum_u16_groups_kernel(const uint16_t* __restrict__ frames, int64_t n, int64_t hw, int groups,
+                                            double* __restrict__ partial) {
+    const int64_t per = (n + groups - 1) / groups;
+    const int64_t total = (int64_t)groups * hw;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int gi = (int)(t / hw);
+        const int64_t i = t - (int64_t)gi * hw;
+        const int64_t f0 = gi * per, f1 = min(n, f0 + per);
+        uint64_t s = 0;                                     // exact: at most 65535 per frame
+        const uint16_t* p = frames + i;
+        int64_t f = f0;
+        for (; f + 16 <= f1; f += 16) {                     // 16 loads in flight per thread
+            uint32_t v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = __ldg(p + (f + u) * hw);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s += v[u];
+        }
+        for (; f < f1; ++f) s += __ldg(p + f * hw);
+        partial[t] = (double)s;
+    }
+}
+
+__global__ void add_partials_kernel(const double* __restrict__ partial, int64_t hw, int groups, int accumulate,
+                                    double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = accumulate ? out[i] : 0.0;
+        for (int gi = 0; gi < groups; ++gi) s += partial[(int64_t)gi * hw + i];
         out[i] = s;
     }
 }
@@ -67,22 +103,46 @@ __global__ void invert_kernel(const uint8_t* __restrict__ in, int64_t hw, uint8_
 
 int grid_for(int64_t items, int threads, int num_sms) {
     const int64_t g = (items + threads - 1) / threads;
-    const int64_t cap = (int64_t)num_sms * 8;
+    const int64_t cap = (int64_t)num_sms * 8;               // 8 CTAs of 256 threads: a full SM
     return (int)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 
 }  // namespace
 
+int frame_sum_groups(int64_t n, int64_t hw, int num_sms) {
+    // enough threads to fill the GPU (2048 resident threads per SM), at least 64 frames per group
+    int64_t g = (int64_t)num_sms * 2048 / (hw > 0 ? hw : 1);
+    if (g > n / 64) g = n / 64;
+    if (g > 64) g = 64;
+    return (int)(g < 1 ? 1 : g);
+}
+
+size_t frame_sum_scratch_bytes(int dtype, int64_t n, int H, int W, int num_sms) {
+    const int64_t hw = (int64_t)H * W;
+    if (dtype != TM_DTYPE_U16) return 0;
+    const int g = frame_sum_groups(n, hw, num_sms);
+    return g > 1 ? (size_t)g * hw * sizeof(double) : 0;
+}
+
 cudaError_t launch_frame_sum(const void* frames, int dtype, int64_t n, int H, int W, int accumulate, double* out,
-                             int num_sms, cudaStream_t st) {
+                             double* scratch, int num_sms, cudaStream_t st) {
     const int64_t hw = (int64_t)H * W;
     if (hw <= 0) return cudaSuccess;
     const int threads = 256;
-    const int grid = grid_for(hw, threads, num_sms);
-    if (dtype == TM_DTYPE_U16)
-        frame_sum_kernel<uint16_t><<<grid, threads, 0, st>>>((const uint16_t*)frames, n, hw, accumulate, out);
-    else
-        frame_sum_kernel<float><<<grid, threads, 0, st>>>((const float*)frames, n, hw, accumulate, out);
+    if (dtype == TM_DTYPE_U16) {
+        const int groups = frame_sum_groups(n, hw, num_sms);
+        if (groups > 1 && scratch) {
+            frame_sum_u16_groups_kernel<<<grid_for((int64_t)groups * hw, threads, num_sms), threads, 0, st>>>(
+                (const uint16_t*)frames, n, hw, groups, scratch);
+            add_partials_kernel<<<grid_for(hw, threads, num_sms), threads, 0, st>>>(scratch, hw, groups, accumulate, out);
+            return cudaGetLastError();
+        }
+        frame_sum_kernel<uint16_t><<<grid_for(hw, threads, num_sms), threads, 0, st>>>((const uint16_t*)frames, n, hw,
+                                                                                       accumulate, out);
+    } else {
+        frame_sum_kernel<float><<<grid_for(hw, threads, num_sms), threads, 0, st>>>((const float*)frames, n, hw,
+                                                                                    accumulate, out);
+    }
     return cudaGetLastError();
 }
 

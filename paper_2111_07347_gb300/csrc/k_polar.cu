@@ -88,12 +88,14 @@ __device__ __forceinline__ void mask_vector4(uint4& v, const uint8_t* pmask, int
 // g(v) - sub of one raw pixel.  u16: from the table lut[v] = g(v) - sub (filled with the same
 // functions), computed directly for v >= kLut.
 template <int MODE>
-__device__ __forceinline__ float tap_value(uint16_t v, const float* lut, float g, float sub) {
-    return v < kLut ? lut[v] : gamma_of<MODE>((float)v, g) - sub;
+__device__ __forceinline__ float tap_value(uint16_t v, const float* lut, float2 g, float sub) {
+    if (v < kLut) return lut[v];
+    const float f = (float)v;
+    return gamma_of<MODE>(f < g.y ? 0.0f : f, g.x) - sub;
 }
 template <int MODE>
-__device__ __forceinline__ float tap_value(float v, const float* lut, float g, float sub) {
-    return gamma_of<MODE>(v, g) - sub;
+__device__ __forceinline__ float tap_value(float v, const float* lut, float2 g, float sub) {
+    return gamma_of<MODE>(v < g.y ? 0.0f : v, g.x) - sub;
 }
 
 __device__ __forceinline__ bool all_in_lut(uint16_t a, uint16_t b, uint16_t c, uint16_t d) {
@@ -112,7 +114,7 @@ __device__ __forceinline__ void fixed_weights(uint32_t q, float& f, float& g) {
 // has row pitch `pitch` elements; taps outside [0, W) x [0, H) contribute zero.
 template <typename T, int MODE, bool SMEM>
 __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int W, int x0, int y0, float fx,
-                                          float gx, float fy, float gy, const float* lut, float g, float sub,
+                                          float gx, float fy, float gy, const float* lut, float2 g, float sub,
                                           const uint8_t* pmask) {
     if ((unsigned)x0 < (unsigned)(W - 1) && (unsigned)y0 < (unsigned)(H - 1)) {
         const T* p = frame + y0 * pitch + x0;
@@ -181,7 +183,7 @@ __device__ __forceinline__ float warp_sum4(const float a[4], int lane) {
 template <typename T, int MODE, bool STAGED, bool CENTRES>
 __device__ __forceinline__ float sample(const T* frame, int pitch, int H, int W, int idx,
                                        const int32_t* __restrict__ txy, const uint2* __restrict__ tq,
-                                       const float4* __restrict__ toff, float2 cen, const float* lut, float g,
+                                       const float4* __restrict__ toff, float2 cen, const float* lut, float2 g,
                                        float sub, const uint8_t* pmask) {
     int x0, y0;
     float fx, gx, fy, gy;
@@ -205,7 +207,7 @@ constexpr int kMaxThreads = 768;            // 80 registers per thread at one CT
 template <typename T, int MODE, bool STAGED, bool CENTRES>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, const int32_t* __restrict__ txy,
-             const uint2* __restrict__ tq, float g, float sub, int n_r, int n_theta, int R,
+             const uint2* __restrict__ tq, float2 g, float sub, int n_r, int n_theta, int R,
              const uint8_t* __restrict__ keep_row, const uint8_t* __restrict__ pmask, float* __restrict__ polar,
              float* __restrict__ pnorm,
              float* __restrict__ radial, const float2* __restrict__ centres, const float4* __restrict__ toff) {
@@ -221,7 +223,10 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
     float* part = lut + (kHasLut ? kLut : 0);                           // [n_r][nw]
     float* red = part + (size_t)n_r * nw;                               // [blockDim]
     if (kHasLut) {
-        for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut[i] = gamma_of<MODE>((float)i, g) - sub;
+        for (int i = threadIdx.x; i < kLut; i += blockDim.x) {
+            const float f = (float)i;
+            lut[i] = gamma_of<MODE>(f < g.y ? 0.0f : f, g.x) - sub;
+        }
         __syncthreads();
     }
     const int my_rows = grp < n_r ? (n_r - grp + R - 1) / R : 0;        // rows grp, grp + R, ...
@@ -341,7 +346,7 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
 }
 
 template <typename T, int MODE, bool STAGED, bool CENTRES>
-cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab, float g, float sub,
+cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab, float2 g, float sub,
                        int n_r, int n_theta, int R, int threads, size_t smem, const uint8_t* keep_row,
                        const uint8_t* pmask, float* polar, float* pnorm, float* radial, const float2* centres,
                        const float4* offsets, cudaStream_t st) {
@@ -361,7 +366,7 @@ cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, cons
 
 template <typename T, bool STAGED>
 cudaError_t launch_mode(int mode, const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab,
-                        float g, float sub, int n_r, int n_theta, int R, int threads, size_t smem,
+                        float2 g, float sub, int n_r, int n_theta, int R, int threads, size_t smem,
                         const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm, float* radial,
                         const float2* centres, const float4* offsets, cudaStream_t st) {
     if (mode == 0)
@@ -375,7 +380,7 @@ cudaError_t launch_mode(int mode, const T* frames, int64_t n, int H, int W, int 
 }
 
 template <typename T>
-cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const PolarTable& tab, int mode, float g,
+cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const PolarTable& tab, int mode, float2 g,
                          float sub, int n_r, int n_theta, float* polar, float* pnorm, float* radial, cudaStream_t st,
                          const uint8_t* keep_row, const float2* centres, const float4* offsets, const uint8_t* pmask) {
     const int cols = ((n_theta + 31) / 32) * 32;
@@ -429,13 +434,21 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          const PolarTable& tab, double gamma, double subtract, int n_r,
                          int n_theta, float* polar, float* pnorm, float* radial,
                          cudaStream_t st, const uint8_t* keep_row, const float2* centres, const float4* offsets,
-                         const uint8_t* pixel_mask) {
+                         const uint8_t* pixel_mask, double threshold) {
     if (n <= 0) return cudaSuccess;
     const int mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
+    // threshold: pixels v < threshold read as 0.  As a float t with v < t exactly when
+    // v < threshold for every float v (t rounded up when the float is below threshold).
+    float thr = -INFINITY;
+    if (threshold > 0.0) {
+        thr = (float)threshold;
+        if ((double)thr < threshold) thr = nextafterf(thr, INFINITY);
+    }
+    const float2 g = make_float2((float)gamma, thr);
     if (dtype == TM_DTYPE_U16)
-        return launch_typed<uint16_t>((const uint16_t*)frames, n, H, W, tab, mode, (float)gamma, (float)subtract, n_r,
+        return launch_typed<uint16_t>((const uint16_t*)frames, n, H, W, tab, mode, g, (float)subtract, n_r,
                                       n_theta, polar, pnorm, radial, st, keep_row, centres, offsets, pixel_mask);
-    return launch_typed<float>((const float*)frames, n, H, W, tab, mode, (float)gamma, (float)subtract, n_r, n_theta,
+    return launch_typed<float>((const float*)frames, n, H, W, tab, mode, g, (float)subtract, n_r, n_theta,
                                polar, pnorm, radial, st, keep_row, centres, offsets, pixel_mask);
 }
 

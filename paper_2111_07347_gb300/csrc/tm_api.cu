@@ -642,6 +642,8 @@ int check_params(const tm_index_params* p) {
         return fail(TM_ERR_INVALID_ARG, "prefilter_fraction must be in (0, 1]");
     if (p->top_n < 1 || p->top_n > TM_MAX_TOPN) return fail(TM_ERR_INVALID_ARG, "top_n must be in [1, %d]", TM_MAX_TOPN);
     if (((uintptr_t)p->pixel_mask & 15) != 0) return fail(TM_ERR_INVALID_ARG, "pixel_mask must be 16-byte aligned");
+    if (!(p->threshold >= 0.0 && isfinite(p->threshold)))
+        return fail(TM_ERR_INVALID_ARG, "threshold must be finite and >= 0");
     return TM_OK;
 }
 
@@ -774,7 +776,14 @@ int tm_frame_sum(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t n, 
         TM_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)H * W * sizeof(double), st), "tm_frame_sum: memset");
         return TM_OK;
     }
-    TM_CUDA(tmgb::launch_frame_sum(frames_dev, dtype, n, H, W, accumulate ? 1 : 0, sum_dev, ctx->num_sms, st),
+    void* scratch = nullptr;
+    const size_t sb = tmgb::frame_sum_scratch_bytes(dtype, n, H, W, ctx->num_sms);
+    if (sb) {
+        int rc = workspace(ctx, st, "frame_sum_partials", sb, &scratch);
+        if (rc) return rc;
+    }
+    TM_CUDA(tmgb::launch_frame_sum(frames_dev, dtype, n, H, W, accumulate ? 1 : 0, sum_dev, (double*)scratch,
+                                   ctx->num_sms, st),
             "tm_frame_sum: launch");
     return TM_OK;
 }
@@ -801,6 +810,26 @@ int tm_matrix_mask(tm_ctx* ctx, const double* sum_dev, int64_t n_frames, int32_t
     return TM_OK;
 }
 
+int tm_find_centres(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t n, int32_t H, int32_t W,
+                    double cx0, double cy0, double radius, int32_t iterations, float* centres_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_find_centres: ctx is NULL");
+    if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000) return fail(TM_ERR_INVALID_ARG, "tm_find_centres: bad shape");
+    if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_find_centres: dtype");
+    if (!(radius > 0.0 && radius <= 1e4)) return fail(TM_ERR_INVALID_ARG, "tm_find_centres: radius must be in (0, 1e4]");
+    if (iterations < 1 || iterations > 100) return fail(TM_ERR_INVALID_ARG, "tm_find_centres: iterations must be in [1, 100]");
+    if (isinf(cx0) || isinf(cy0)) return fail(TM_ERR_INVALID_ARG, "tm_find_centres: centre must be finite or NaN");
+    if (n == 0) return TM_OK;
+    if (!frames_dev || !centres_dev) return fail(TM_ERR_INVALID_ARG, "tm_find_centres: NULL buffer");
+    if (isnan(cx0)) cx0 = (W - 1) / 2.0;
+    if (isnan(cy0)) cy0 = (H - 1) / 2.0;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    TM_CUDA(tmgb::launch_find_centres(frames_dev, dtype, n, H, W, cx0, cy0, radius, iterations, (float2*)centres_dev,
+                                      (cudaStream_t)stream),
+            "tm_find_centres: launch");
+    return TM_OK;
+}
+
 void tm_index_params_default(tm_index_params* p) {
     if (!p) return;
     p->gamma = 0.5;
@@ -813,6 +842,7 @@ void tm_index_params_default(tm_index_params* p) {
     p->rescore_k = 256;
     p->reserved = 0;
     p->pixel_mask = nullptr;
+    p->threshold = 0.0;
 }
 
 const char* tm_last_error(void) { return g_err.c_str(); }
@@ -1049,7 +1079,7 @@ int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* f
     cudaStream_t st = (cudaStream_t)stream;
     TM_CUDA(tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
                              polar_dev, norm_dev, radial_dev, st, nullptr, (const float2*)centres_dev, offs,
-                             params->pixel_mask),
+                             params->pixel_mask, params->threshold),
             "tm_polar_transform: launch");
     return TM_OK;
 }
@@ -1235,7 +1265,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                 TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
                                            polar, pnorm, radial, st, rmap.keep_row,
                                            centres_dev ? (const float2*)centres_dev + c0 : nullptr, offs,
-                                           params->pixel_mask),
+                                           params->pixel_mask, params->threshold),
                         "tm_index_patterns: polar");
             }
             ++launches;
@@ -1347,10 +1377,11 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     // CUDA graph: the second identical call on a created stream is captured, later ones replay
     if ((params->reserved & TM_INDEX_GRAPH) && st != nullptr && !ctx->profiling) {
         char key[512];
-        int off = snprintf(key, sizeof key, "%p|%p|%p|%p|%p|%d|%lld|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|", st,
-                           frames_dev, (const void*)centres_dev, (void*)out_dev, (const void*)params->pixel_mask, dtype,
-                           (long long)n, H, W, params->gamma, params->subtract, params->cx, params->cy,
-                           params->prefilter_fraction, params->top_n, params->path, params->rescore_k);
+        int off = snprintf(key, sizeof key, "%p|%p|%p|%p|%p|%d|%lld|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|",
+                           st, frames_dev, (const void*)centres_dev, (void*)out_dev, (const void*)params->pixel_mask,
+                           dtype, (long long)n, H, W, params->gamma, params->subtract, params->cx, params->cy,
+                           params->prefilter_fraction, params->threshold, params->top_n, params->path,
+                           params->rescore_k);
         for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);
         tm_ctx::GraphEntry& ge = ctx->graphs[key];
         if (ge.exec && ge.ws_gen == ctx->ws_gen) {
@@ -1425,6 +1456,7 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
     p.path = TM_PATH_FP32_SPARSE;
     p.reserved = 0;
     p.pixel_mask = nullptr;
+    p.threshold = 0.0;
     const int cand[3] = {128, 256, 512};
     int best = 256;
     double best_ms = 1e30;

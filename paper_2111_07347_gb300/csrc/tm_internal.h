@@ -67,12 +67,18 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          int n_theta, float* polar, float* pnorm, float* radial,
                          cudaStream_t st, const uint8_t* keep_row = nullptr,
                          const float2* centres = nullptr, const float4* offsets = nullptr,
-                         const uint8_t* pixel_mask = nullptr);
+                         const uint8_t* pixel_mask = nullptr, double threshold = 0.0);
+
+// Direct-beam centres: per pattern the centre of mass within `radius` of the estimate,
+// `iterations` times from (cx0, cy0), FP64 in a fixed order; out [n] (cx, cy) floats.
+cudaError_t launch_find_centres(const void* frames, int dtype, int64_t n, int H, int W, double cx0, double cy0,
+                                double radius, int iterations, float2* out, cudaStream_t st);
 
 // Two-stage indexing (Section 4.3): per-pixel FP64 sums over frames (accumulate: add onto
 // out), and the mask of kept pixels from the sums (scratch: H * W bytes).
+size_t frame_sum_scratch_bytes(int dtype, int64_t n, int H, int W, int num_sms);
 cudaError_t launch_frame_sum(const void* frames, int dtype, int64_t n, int H, int W, int accumulate, double* out,
-                             int num_sms, cudaStream_t st);
+                             double* scratch, int num_sms, cudaStream_t st);
 cudaError_t launch_matrix_mask(const double* sum, int H, int W, double thr_n, int n_open, int n_dilate,
                                uint8_t* mask, uint8_t* scratch, int num_sms, cudaStream_t st);
 

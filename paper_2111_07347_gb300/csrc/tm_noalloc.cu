@@ -137,7 +137,8 @@ extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* par
             float* polar = (float*)(scratch + o_polar);
             float* pnorm = (float*)(scratch + o_norm);
             e = tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                                   polar, pnorm, nullptr, st, nullptr, nullptr, nullptr, params->pixel_mask);
+                                   polar, pnorm, nullptr, st, nullptr, nullptr, nullptr, params->pixel_mask,
+                                   params->threshold);
             if (e == cudaSuccess) {
                 tmgb::SparseCall c{};
                 c.polar = polar;

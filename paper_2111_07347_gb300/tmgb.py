@@ -55,7 +55,7 @@ class tm_index_params(ctypes.Structure):
                 ("cx", ctypes.c_double), ("cy", ctypes.c_double),
                 ("prefilter_fraction", ctypes.c_double), ("top_n", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("rescore_k", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("pixel_mask", ctypes.c_void_p)]
+                ("reserved", ctypes.c_int32), ("pixel_mask", ctypes.c_void_p), ("threshold", ctypes.c_double)]
 
 
 class tm_hit(ctypes.Structure):
@@ -121,6 +121,8 @@ _SIGS = {
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                               _P, ctypes.c_int64, ctypes.POINTER(tm_stats)]),
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
+    "tm_find_centres": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P]),
     "tm_frame_sum": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32, _P, _P]),
     "tm_matrix_mask": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -276,12 +278,14 @@ def tm_library_export(ctx: int, lib_id: int) -> dict:
 
 
 def make_params(gamma=0.5, subtract=0.0, cx=math.nan, cy=math.nan, prefilter=1.0, top_n=5,
-                path=TM_PATH_FP32_SPARSE, rescore_k=256, mask=None) -> tm_index_params:
-    """mask: device uint8 tensor [H][W] (pixels with 0 read as 0) or None."""
+                path=TM_PATH_FP32_SPARSE, rescore_k=256, mask=None, threshold=0.0) -> tm_index_params:
+    """mask: device uint8 tensor [H][W] (pixels with 0 read as 0) or None; threshold > 0: raw
+    pixels below it read as 0."""
     p = tm_index_params_default()
     p.gamma, p.subtract, p.cx, p.cy = gamma, subtract, cx, cy
     p.prefilter_fraction, p.top_n, p.path, p.rescore_k = prefilter, top_n, path, rescore_k
     p.pixel_mask = None if mask is None else mask.data_ptr()
+    p.threshold = threshold
     return p
 
 
@@ -510,7 +514,7 @@ class Context:
         return tm_library_export(self.handle, lib_id)
 
     def polar_transform(self, frames, n_r, n_theta, dr=1.0, gamma=0.5, subtract=0.0, cx=math.nan, cy=math.nan,
-                        centres=None, stream=None, mask=None):
+                        centres=None, stream=None, mask=None, threshold=0.0):
         """frames [n][H][W] -> (polar [n][n_r][n_theta], norm [n], radial [n][n_r]); centres: optional
         float32 [n][2] device tensor of per-pattern (cx, cy)."""
         import torch
@@ -519,7 +523,7 @@ class Context:
         polar = torch.empty((n, n_r, n_theta), dtype=torch.float32, device=dev)
         norm = torch.empty((n,), dtype=torch.float32, device=dev)
         radial = torch.empty((n, n_r), dtype=torch.float32, device=dev)
-        p = make_params(gamma, subtract, cx, cy, mask=mask)
+        p = make_params(gamma, subtract, cx, cy, mask=mask, threshold=threshold)
         tm_polar_transform(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W,
                            None if centres is None else centres.data_ptr(), n_r, n_theta, dr,
                            polar.data_ptr(), norm.data_ptr(), radial.data_ptr(), _stream_ptr(stream))
@@ -565,6 +569,17 @@ class Context:
         return tm_autotune(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W, list(lib_ids),
                            _stream_ptr(stream))
 
+    def find_centres(self, frames, radius=6.0, iterations=3, cx=math.nan, cy=math.nan, out=None, stream=None):
+        """Direct-beam centre per pattern (device frames [n][H][W]) -> float32 [n][2] tensor."""
+        import torch
+        n, H, W = frames.shape
+        if out is None:
+            out = torch.empty((n, 2), dtype=torch.float32, device=frames.device)
+        _check(library().tm_find_centres(self.handle, frames.data_ptr(), _dtype_code(frames), n, H, W, float(cx),
+                                         float(cy), float(radius), int(iterations), out.data_ptr(),
+                                         _stream_ptr(stream)))
+        return out
+
     def frame_sum(self, frames, out=None, accumulate=False, stream=None):
         """Per-pixel FP64 sum over frames [n][H][W] (device) -> [H][W] float64 tensor; with
         accumulate=True the sums are added onto `out`."""
@@ -591,7 +606,7 @@ class Context:
 
     def index_host(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
                    path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, chunk=0,
-                   centres=None, mask=None):
+                   centres=None, mask=None, threshold=0.0):
         """frames [n][H][W] uint16/float32 in host memory (numpy, or a CPU tensor -- pinned for
         copy/compute overlap) -> hits [n_libs][n][top_n][5] int32 in host memory (`out`, numpy
         or CPU tensor, else a new numpy array).  Synchronous."""
@@ -611,14 +626,14 @@ class Context:
             cptr, ccode = _host_buffer(centres, "centres")
             if ccode != TM_DTYPE_F32 or tuple(centres.shape) != (n, 2):
                 raise ValueError("centres must be float32 [n][2]")
-        p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k, mask=mask)
+        p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k, mask=mask, threshold=threshold)
         self.last_stats = tm_index_patterns_host(self.handle, p, fptr, code, n, H, W, cptr, list(lib_ids), optr,
                                                  chunk)
         return out
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
               path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None,
-              graph=False, centres=None, test_stall=False, mask=None):
+              graph=False, centres=None, test_stall=False, mask=None, threshold=0.0):
         """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32.
         graph=True replays repeated identical calls as a CUDA graph (needs a created stream).
         test_stall=True sets TM_INDEX_TEST_STALL (failure-path tests of the bounded waits)."""
@@ -628,7 +643,7 @@ class Context:
         n, H, W = frames.shape
         if out is None:
             out = torch.empty((len(lib_ids), n, top_n, 5), dtype=torch.int32, device=frames.device)
-        p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k, mask=mask)
+        p = make_params(gamma, subtract, cx, cy, prefilter, top_n, path, rescore_k, mask=mask, threshold=threshold)
         if graph:
             p.reserved |= TM_INDEX_GRAPH
         if test_stall:
