@@ -418,3 +418,36 @@ def find_centres(frames: np.ndarray, centre, radius: float, iterations: int) -> 
                 cx, cy = sx / s0, sy / s0
         out[p] = (cx, cy)
     return out
+
+
+# ----------------------------------------------------------------------------------
+# In-plane angle below the polar step (Section 2.2: the resolution of phi_1 is the polar
+# transform's angular step; Section 5 names a better phi_1 optimisation as future work).
+# ----------------------------------------------------------------------------------
+
+def refine_angles(P: np.ndarray, lib: Library, template: np.ndarray, shift: np.ndarray) -> np.ndarray:
+    """Sub-step in-plane angle of top-N hits: Q at the shifts s - 1, s, s + 1 (mod n_theta) of
+    each hit's template, the vertex of the parabola through them, delta = (Q- - Q+) /
+    (2 (Q- - 2 Q0 + Q+)) when the curvature Q- - 2 Q0 + Q+ is negative (else 0), clipped to
+    [-1/2, 1/2]; angle = (s + delta) 360 / n_theta degrees.  P [n][n_r][n_theta];
+    template, shift [n][N] (-1 padding -> NaN)."""
+    n, N = template.shape
+    out = np.full((n, N), np.nan)
+    nt = lib.n_theta
+    for p in range(n):
+        nP = math.sqrt(float(np.sum(P[p] * P[p])))
+        for j in range(N):
+            k, s = int(template[p, j]), int(shift[p, j])
+            if k < 0:
+                continue
+            d = nP * lib.norm[k]
+            q = []
+            for ds in (-1, 0, 1):
+                acc = 0.0
+                for i in range(lib.off[k], lib.off[k + 1]):
+                    acc += lib.I[i] * P[p, lib.ri[i], (lib.ti[i] + s + ds) % nt]
+                q.append(acc / d if d > 0 else 0.0)
+            curv = q[0] - 2.0 * q[1] + q[2]
+            delta = (q[0] - q[2]) / (2.0 * curv) if curv < 0.0 else 0.0
+            out[p, j] = (s + min(0.5, max(-0.5, delta))) * 360.0 / nt
+    return out

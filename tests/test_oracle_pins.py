@@ -361,3 +361,29 @@ def test_threshold_sets_low_pixels_to_zero():
     P2 = O.polar(np.where(f < 5, 0, f).astype(np.uint16), 6, 8, gamma=1.0)
     assert np.array_equal(P1, P2) and not np.array_equal(P0, P1)
     assert np.array_equal(O.polar(f, 6, 8, threshold=3.0), O.polar(f, 6, 8))   # strict: 3 < 3 is false
+
+
+# ------------------------------------------------------------------ sub-step in-plane angle
+
+def test_refine_angles_vertex_of_a_parabola():
+    """A polar image whose single row is a sampled parabola in theta around a non-integer
+    maximum: a one-spot template's Q(s) follows it, so the refined angle is the true vertex."""
+    nt = 36
+    ts = synth.TemplateSet(np.array([0, 1]), np.array([3.0]), np.array([0.0]), np.array([2.0]))
+    lib = O.prepare_library(ts, 5, nt)
+    P = np.zeros((1, 5, nt))
+    x0 = 10.3                                                     # vertex, in columns
+    cols = np.arange(nt)
+    P[0, 3] = 50.0 - (cols - x0) ** 2
+    P[0, 3] = np.maximum(P[0, 3], 1.0)
+    a = O.refine_angles(P, lib, np.array([[0]]), np.array([[10]]))
+    assert abs(a[0, 0] - x0 * 10.0) < 1e-9                         # 360 / 36 = 10 degrees per column
+    # at a flat or inverted neighbourhood the step itself is kept; padding stays NaN
+    P2 = np.ones((1, 5, nt))
+    a2 = O.refine_angles(P2, lib, np.array([[0, -1]]), np.array([[7, -1]]))
+    assert a2[0, 0] == 70.0 and np.isnan(a2[0, 1])
+    # the offset is clipped to half a step
+    P3 = np.zeros((1, 5, nt))
+    P3[0, 3, 9], P3[0, 3, 10], P3[0, 3, 11] = 1.0, 1.0, 0.0        # vertex pulled beyond half a step
+    a3 = O.refine_angles(P3, lib, np.array([[0]]), np.array([[10]]))
+    assert a3[0, 0] == 95.0
