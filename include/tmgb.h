@@ -132,6 +132,14 @@ typedef struct tm_index_params {
  * hits are meaningless; the context stays usable. */
 #define TM_INDEX_TEST_STALL 2
 
+/* tm_index_params.reserved flag: in-plane angle below the polar step (Section 2.2: phi_1 is
+ * resolved to the angular step of the polar grid; Section 5 names a better phi_1 optimisation
+ * as future work).  Each hit's angle_deg becomes (shift + delta) 360 / n_theta, delta the
+ * vertex of the parabola through Q at shift - 1, shift, shift + 1 (mod n_theta):
+ * (Q- - Q+) / (2 (Q- - 2 Q0 + Q+)) for a negative curvature, else 0, clipped to [-1/2, 1/2].
+ * The shift field keeps the integer best shift. */
+#define TM_INDEX_REFINE 4
+
 /* One result row.  Rows of a pattern are ordered by (score desc, template asc); when
  * fewer than N templates take part the tail rows have template_index = -1 and
  * score = -inf. */

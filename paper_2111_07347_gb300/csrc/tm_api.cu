@@ -65,6 +65,7 @@ struct Library {
     double dr = 1.0;
     int64_t n_sym = 0, macs = 0;
     int max_spots = 0;
+    int nonneg = 1;                // every intensity >= 0
     // host copies (exported for tests)
     std::vector<int64_t> off;
     std::vector<int32_t> r, t, order;
@@ -396,6 +397,8 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
         spot[i].x = t | (row << 11) | (w << 24);
         memcpy(&spot[i].y, &L->I[i], 4);
     }
+    for (float I : L->I)
+        if (!(I >= 0.0f)) L->nonneg = 0;
     // offsets in the dual-copy and wrap-free row layouts (0 where a layout cannot be used)
     const int64_t pd = tmgb::sparse_pitch(n_theta, tmgb::TM_LAYOUT_DUAL);
     const int64_t pw = tmgb::sparse_pitch(n_theta, tmgb::TM_LAYOUT_WF);
@@ -483,6 +486,7 @@ tmgb::SparseLib sparse_view(const Library* L) {
     v.K0 = (int32_t)L->K0;
     v.mirror = L->mirror;
     v.words = (int32_t)((L->K + 31) / 32);
+    v.nonneg = L->nonneg;
     return v;
 }
 
@@ -1363,6 +1367,22 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                     scored += m * keep[i];
                 }
             }
+            if (params->reserved & TM_INDEX_REFINE) {
+                tmgb::RefineCall rc{};
+                rc.polar = polar;
+                rc.pnorm = pnorm;
+                rc.n = m;
+                rc.n_r = n_r;
+                rc.n_theta = n_theta;
+                rc.top_n = N;
+                rc.n_libs = n_libs;
+                for (int i = 0; i < n_libs; ++i)
+                    rc.lib[i] = tmgb::RefineLib{libs[i]->d_off, libs[i]->d_rt, libs[i]->d_spot, libs[i]->d_norm};
+                rc.hits = out_dev + (size_t)c0 * N;
+                rc.hits_lib_stride = n * N;
+                TM_CUDA(tmgb::launch_refine(rc, ctx->num_sms, st), "tm_index_patterns: refine");
+                ++launches;
+            }
         }
         return TM_OK;
     };
@@ -1382,6 +1402,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                            dtype, (long long)n, H, W, params->gamma, params->subtract, params->cx, params->cy,
                            params->prefilter_fraction, params->threshold, params->top_n, params->path,
                            params->rescore_k);
+        off += snprintf(key + off, sizeof key - off, "r%d|", params->reserved & ~TM_INDEX_GRAPH);
         for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);
         tm_ctx::GraphEntry& ge = ctx->graphs[key];
         if (ge.exec && ge.ws_gen == ctx->ws_gen) {

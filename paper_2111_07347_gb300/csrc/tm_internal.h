@@ -42,6 +42,7 @@ struct SparseLib {
     int32_t K0;
     int32_t mirror;
     int32_t words;             // ceil(K / 32)
+    int32_t nonneg;            // every intensity >= 0 (the sparse kernel may then prune by bounds)
 };
 
 struct RadialLib {
@@ -68,6 +69,25 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
                          cudaStream_t st, const uint8_t* keep_row = nullptr,
                          const float2* centres = nullptr, const float4* offsets = nullptr,
                          const uint8_t* pixel_mask = nullptr, double threshold = 0.0);
+
+// Sub-step in-plane angle of the top-N hits (parabola through Q at s - 1, s, s + 1).
+struct RefineLib {
+    const int32_t* off;        // [K + 1]
+    const int32_t* rt;         // [n_spots]  r | t << 16
+    const int2* spot;          // [n_spots]  .y = intensity bits
+    const float* norm;         // [K]
+};
+struct RefineCall {
+    const float* polar;        // [n][n_r][n_theta]  (rows of the libraries' radii)
+    const float* pnorm;        // [n]
+    int64_t n;
+    int n_r, n_theta, top_n;
+    int n_libs;
+    RefineLib lib[TM_MAX_LIBS];
+    tm_hit* hits;              // [n_libs][hits_lib_stride]: angle_deg rewritten in place
+    int64_t hits_lib_stride;
+};
+cudaError_t launch_refine(const RefineCall& c, int num_sms, cudaStream_t st);
 
 // Direct-beam centres: per pattern the centre of mass within `radius` of the estimate,
 // `iterations` times from (cx0, cy0), FP64 in a fixed order; out [n] (cx, cy) floats.

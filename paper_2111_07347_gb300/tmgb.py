@@ -26,6 +26,7 @@ TM_LIB_MIRROR, TM_LIB_UNIT_INTENSITY = 1, 2
 TM_PATH_FP32_SPARSE, TM_PATH_BF16_RESCORE = 0, 1
 TM_INDEX_GRAPH = 1
 TM_INDEX_TEST_STALL = 2
+TM_INDEX_REFINE = 4
 
 
 class TmError(RuntimeError):
@@ -633,7 +634,7 @@ class Context:
 
     def index(self, frames, lib_ids, top_n=5, gamma=0.5, subtract=0.0, prefilter=1.0,
               path=TM_PATH_FP32_SPARSE, rescore_k=256, cx=math.nan, cy=math.nan, out=None, stream=None,
-              graph=False, centres=None, test_stall=False, mask=None, threshold=0.0):
+              graph=False, centres=None, test_stall=False, mask=None, threshold=0.0, refine=False):
         """frames [n][H][W] uint16/float32 on the device -> hits [n_libs][n][top_n][5] int32.
         graph=True replays repeated identical calls as a CUDA graph (needs a created stream).
         test_stall=True sets TM_INDEX_TEST_STALL (failure-path tests of the bounded waits)."""
@@ -648,6 +649,8 @@ class Context:
             p.reserved |= TM_INDEX_GRAPH
         if test_stall:
             p.reserved |= TM_INDEX_TEST_STALL
+        if refine:
+            p.reserved |= TM_INDEX_REFINE
         self.last_stats = tm_index_patterns(self.handle, p, frames.data_ptr(), _dtype_code(frames), n, H, W,
                                             None if centres is None else centres.data_ptr(),
                                             list(lib_ids), out.data_ptr(), _stream_ptr(stream))

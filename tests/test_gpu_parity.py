@@ -353,3 +353,37 @@ def test_autotune_keeps_results(ctx, fcc, tmp_path, monkeypatch):
     assert np.array_equal(before, after)
     c2.close()
     assert (tmp_path / "tune.txt").read_text().split()[1] == str(best)
+
+
+def test_refined_angles_match_oracle_and_reduce_error(ctx, tiny):
+    """TM_INDEX_REFINE: templates, shifts and scores unchanged; the sub-step angle equals the
+    oracle's parabola vertex (evaluated at the GPU's own hits) within the propagation of the
+    Q tolerance; on the tiny scan (2 degree polar step, continuous true angles) it lowers the
+    angle error of correctly indexed patterns."""
+    ts, scan, lib, ref = tiny
+    lid = ctx.load_library(ts, 60, 180)
+    plain = _hits(ctx, scan.frames, lid, top_n=5)[0]
+    fine = _hits(ctx, scan.frames, lid, top_n=5, refine=True)[0]
+    for f in ("template_index", "shift", "score", "mirror"):
+        assert np.array_equal(plain[f], fine[f])
+    a_ref = O.refine_angles(ref["polar"], lib, fine["template_index"].astype(np.int64), fine["shift"].astype(np.int64))
+    step = 360.0 / 180
+    nP = np.sqrt((ref["polar"] ** 2).sum(axis=(1, 2)))
+    for p in range(scan.frames.shape[0]):
+        for j in range(5):
+            k, s = int(fine["template_index"][p, j]), int(fine["shift"][p, j])
+            d = nP[p] * lib.norm[k]
+            q = [sum(lib.I[i] * ref["polar"][p, lib.ri[i], (lib.ti[i] + s + ds) % 180]
+                     for i in range(lib.off[k], lib.off[k + 1])) / d for ds in (-1, 0, 1)]
+            curv = abs(q[0] - 2 * q[1] + q[2])
+            tol = step * (min(0.5, 5e-5 * abs(q[1]) / max(curv, 1e-30)) + 1e-5)
+            assert abs(fine["angle_deg"][p, j] - a_ref[p, j]) <= tol, (p, j, fine["angle_deg"][p, j], a_ref[p, j])
+    ok = fine["template_index"][:, 0] == scan.template
+    true_deg = np.degrees(scan.angle) % 360.0
+
+    def err(a):
+        return np.abs((a - true_deg + 180.0) % 360.0 - 180.0)
+
+    e_plain, e_fine = err(plain["angle_deg"][:, 0])[ok], err(fine["angle_deg"][:, 0])[ok]
+    assert e_fine.mean() < e_plain.mean(), (e_fine.mean(), e_plain.mean())
+    ctx.unload_library(lid)
