@@ -71,6 +71,26 @@ __device__ __forceinline__ bool better(float qa, int ka, float qb, int kb) {
     return qa > qb || (qa == qb && ka < kb);
 }
 
+// Order-preserving integer key of a float (for atomicMax on scores).
+__device__ __forceinline__ unsigned score_key(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_score(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Row (among the library's distinct radii) of a spot word.  Dual and wrap-free layouts hold
+// a float offset row * pitch + column (column < pitch); (off + 1/2) / pitch in float is off by
+// far less than 1/(2 pitch), so its floor is the row exactly.
+template <int LAYOUT>
+__device__ __forceinline__ int spot_row(int px, float inv_pitch, int n_rad) {
+    if (LAYOUT == TM_LAYOUT_WRAP) return (px >> 11) & 0x1fff;
+    const unsigned off = LAYOUT == TM_LAYOUT_DUAL ? ((unsigned)px & 0xffffu) : ((unsigned)px >> 16);
+    const int r = (int)(((float)off + 0.5f) * inv_pitch);
+    return (LAYOUT == TM_LAYOUT_DUAL && r >= n_rad) ? r - n_rad : r;
+}
+
 // ---------------------------------------------------------------- per-layout spot updates
 // acc holds V values per lane (V = 2 NB for the dual layout, NB otherwise); value v of lane L
 // is shift shift_of(v, L).  FIRST initialises instead of accumulating.
@@ -124,15 +144,16 @@ __device__ __forceinline__ float score_template(const float* __restrict__ sP, co
                                                 int cnt_all, int S, int n_theta, int pitch, int lane, float thr_c,
                                                 int& shift_out, bool& resolved) {
     constexpr int V = LAYOUT == TM_LAYOUT_DUAL ? 2 * NB : NB;
-    float acc[V];
+    resolved = false;
     int cnt = min(32, cnt_all);
+    int2 mine = make_int2(0, 0);
+    if (lane < cnt) mine = __ldg(spots + beg + lane);             // one lane-parallel load
+    float acc[V];
     if (cnt <= 0) {                                               // no spot on the grid: C = 0, no read
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = 0.0f;
         cnt = 0;
     }
-    int2 mine = make_int2(0, 0);
-    if (lane < cnt) mine = __ldg(spots + beg + lane);             // one lane-parallel load
     if (cnt > 0) {
         const int px = __shfl_sync(0xffffffffu, mine.x, 0);
         const float I = __int_as_float(__shfl_sync(0xffffffffu, mine.y, 0));
@@ -165,7 +186,6 @@ __device__ __forceinline__ float score_template(const float* __restrict__ sP, co
         for (int v = 0; v < V; ++v)
             if (shift_of<LAYOUT>(v, lane) < S) best = fmaxf(best, acc[v]);
     }
-    resolved = false;
     if (!__any_sync(0xffffffffu, best >= thr_c)) return best;    // cannot enter the top-N
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -188,6 +208,7 @@ template <int NBMAX, int LAYOUT>
 __device__ __forceinline__ float score_dispatch(const float* sP, const int2* spots, int beg, int cnt, int S,
                                                 int n_theta, int pitch, int lane, float thr_c, int& s, bool& res) {
     constexpr int W = LAYOUT == TM_LAYOUT_DUAL ? 64 : 32;
+    res = false;
     if (S == n_theta && round_nb((n_theta + W - 1) / W) == NBMAX)   // the common case, tested first
         return score_template<NBMAX, LAYOUT, true>(sP, spots, beg, cnt, S, n_theta, pitch, lane, thr_c, s, res);
     const int nb = (S + W - 1) / W;
@@ -222,6 +243,10 @@ sparse_kernel(const SparseCall c) {
     int* lcnt = ls + kWarps * N;                             // [kWarps]
     int* counter = lcnt + kWarps;                            // [1]
     int* s_pattern = counter + 1;                            // [1]
+    unsigned* s_thr = (unsigned*)(s_pattern + 1);            // [1] best of the warps' N-th scores (key)
+    float* s_rmax = (float*)(s_thr + 1);                     // [max_rad] row maxima of P'
+    float* s_rabs = s_rmax + c.max_rad;                      // [max_rad] row maxima of |P'|
+    const float inv_pitch = 1.0f / (float)pitch;
 
     for (;;) {
         __syncthreads();                                     // previous pattern fully done
@@ -240,16 +265,32 @@ sparse_kernel(const SparseCall c) {
                 const int sh = rr < L.n_rad ? 0 : 1;
                 const float* row = src + (size_t)__ldg(L.radii + r0) * n_theta;
                 float* dst = sP + (size_t)rr * pitch;
+                float mx = -INFINITY, ma = 0.0f;
                 for (int col = lane; col < pitch; col += 32) {
                     int sc = col + sh;
                     while (sc >= n_theta) sc -= n_theta;
-                    dst[col] = __ldg(row + sc);
+                    const float v = __ldg(row + sc);
+                    dst[col] = v;
+                    mx = fmaxf(mx, v);
+                    ma = fmaxf(ma, fabsf(v));
+                }
+                if (rr < L.n_rad) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+                    }
+                    if (lane == 0) { s_rmax[rr] = mx; s_rabs[rr] = ma; }
                 }
             }
-            if (threadIdx.x == 0) *counter = 0;
+            if (threadIdx.x == 0) { *counter = 0; *s_thr = score_key(-INFINITY); }
             if (threadIdx.x < kWarps) lcnt[threadIdx.x] = 0;
             __syncthreads();
             const int2* spots = LAYOUT == TM_LAYOUT_WRAP ? L.spot : L.spot2;
+            float pmax = 0.0f;                               // max |P'| over the library's rows
+            for (int rr = lane; rr < L.n_rad; rr += 32) pmax = fmaxf(pmax, s_rabs[rr]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
             const uint32_t* mrow = c.mask[li] ? c.mask[li] + (size_t)p * L.words : nullptr;
             float* qo = c.q_out[li] ? c.q_out[li] + (size_t)p * L.K : nullptr;
             int32_t* so = c.s_out[li] ? c.s_out[li] + (size_t)p * L.K : nullptr;
@@ -257,6 +298,7 @@ sparse_kernel(const SparseCall c) {
             int* wk = lk + warp * N;
             int* ws = ls + warp * N;
             const bool use_thr = !qo && c.hits;
+            const bool prune = use_thr && L.nonneg;
             float qthr = -INFINITY;                          // the warp's N-th best Q once its list is full
             for (;;) {
                 int wd = 0;
@@ -267,7 +309,7 @@ sparse_kernel(const SparseCall c) {
                 const int rem = L.K - wd * 32;
                 if (rem < 32) m &= (1u << rem) - 1u;
                 // per-lane metadata of the word's 32 templates: {first spot, spots | shifts << 16,
-                // norm bits} in one load
+                // norm bits, intensity-sum bits} in one load
                 const int kl = wd * 32 + lane;
                 int4 meta_l = make_int4(0, 1 << 16, 0, 0);
                 if (lane < rem && ((m >> lane) & 1u)) {
@@ -276,6 +318,19 @@ sparse_kernel(const SparseCall c) {
                     qo[kl] = -INFINITY;
                     so[kl] = -1;
                 }
+                // exact pruning (intensities >= 0): each lane bounds its template's best correlation,
+                // C(s) <= ub = sum_i I_i max_c P'[r_i][c], plus a margin for the rounding of both
+                // sums (2^-24 per operation; sum_i |I_i P'| <= isum * pmax)
+                float ubm_l = INFINITY;
+                if (prune && lane < rem && ((m >> lane) & 1u)) {
+                    const int cnt_l = meta_l.y & 0xffff;
+                    float ub = 0.0f;
+                    for (int i = 0; i < cnt_l; ++i) {
+                        const int2 w = __ldg(spots + meta_l.x + i);
+                        ub = fmaf(__int_as_float(w.y), s_rmax[spot_row<LAYOUT>(w.x, inv_pitch, L.n_rad)], ub);
+                    }
+                    ubm_l = ub + (2.0f * (float)cnt_l + 40.0f) * 5.9604645e-8f * __int_as_float(meta_l.w) * pmax;
+                }
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
@@ -283,14 +338,24 @@ sparse_kernel(const SparseCall c) {
                     const int beg = __shfl_sync(0xffffffffu, meta_l.x, bit);
                     const int cs = __shfl_sync(0xffffffffu, meta_l.y, bit);
                     const float tn = __int_as_float(__shfl_sync(0xffffffffu, meta_l.z, bit));
+                    const float ubm = __shfl_sync(0xffffffffu, ubm_l, bit);
                     const int cnt = cs & 0xffff, S = (int)((unsigned)cs >> 16);
                     const float d = pn * tn;
-                    // a template whose correlation stays below the warp's N-th best (in
-                    // correlation units, with a margin for the division's rounding) cannot
-                    // enter the top-N, so its best shift is not resolved
+                    // Every warp's N-th best score is a lower bound of the pattern's final N-th
+                    // best, and so is the best of them (s_thr).  A template below it cannot
+                    // enter the top-N.
+                    const float thr = use_thr ? fmaxf(qthr, key_score(*(volatile unsigned*)s_thr)) : -INFINITY;
+                    // the template is skipped when its bound stays below thr * d (then Q < thr)
+                    if (thr > -INFINITY && d > 0.0f) {
+                        const float td = thr * d;
+                        if (ubm < td - fabsf(td) * 4.8e-7f) continue;
+                    }
+                    // a template whose correlation stays below the threshold (in correlation
+                    // units, with a margin for the division's rounding) cannot enter the
+                    // top-N, so its best shift is not resolved
                     float thr_c = -FLT_MAX;
-                    if (use_thr && qthr > -INFINITY && d > 0.0f) {
-                        const float t = qthr * d;
+                    if (use_thr && thr > -INFINITY && d > 0.0f) {
+                        const float t = thr * d;
                         thr_c = t - fabsf(t) * 1e-6f;
                     }
                     int s = 0;
@@ -319,7 +384,10 @@ sparse_kernel(const SparseCall c) {
                     __syncwarp();
                     if (use_thr) {
                         float nt = -INFINITY;
-                        if (lane == 0 && lcnt[warp] >= N) nt = wq[N - 1];
+                        if (lane == 0 && lcnt[warp] >= N) {
+                            nt = wq[N - 1];
+                            atomicMax(s_thr, score_key(nt));
+                        }
                         qthr = __shfl_sync(0xffffffffu, nt, 0);
                     }
                 }
@@ -395,7 +463,7 @@ constexpr size_t kWrapFreeBytes = 100 * 1024;
 
 size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout, int* pitch) {
     if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
-    const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16;
+    const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16 + (size_t)max_rad * 8 + 16;
     const int order[3] = {TM_LAYOUT_DUAL, TM_LAYOUT_WF, TM_LAYOUT_WRAP};
     const size_t limit[3] = {kDualBytes, kWrapFreeBytes, 232448};
     for (int i = 0; i < 3; ++i) {

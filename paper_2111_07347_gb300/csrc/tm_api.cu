@@ -416,9 +416,15 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
         const int64_t cnt = L->off[k + 1] - L->off[k];
         if (cnt > 65535) return fail(TM_ERR_UNSUPPORTED, "tm_load_library: template %lld has %lld spots (max 65535)",
                                      (long long)k, (long long)cnt);
-        int32_t nb;
+        int32_t nb, sb;
         memcpy(&nb, &L->norm[k], 4);
-        P->meta[k] = make_int4((int32_t)L->off[k], (int32_t)(cnt | ((int64_t)P->nshift[k] << 16)), nb, 0);
+        // sum of |intensities|, rounded up: bounds the rounding of the sparse kernel's sums
+        double isum = 0.0;
+        for (int64_t i = L->off[k]; i < L->off[k + 1]; ++i) isum += fabs((double)L->I[i]);
+        float fs = (float)isum;
+        if ((double)fs < isum) fs = nextafterf(fs, INFINITY);
+        memcpy(&sb, &fs, 4);
+        P->meta[k] = make_int4((int32_t)L->off[k], (int32_t)(cnt | ((int64_t)P->nshift[k] << 16)), nb, sb);
     }
     return TM_OK;
 }

@@ -26,7 +26,7 @@ void set_last_error(const char* msg);
 //              layout ((t & 1 ? n_rad + rho : rho) * pitch_dual + (t & ~1)) and in the wrap-free
 //              layout (rho * pitch_wf + t), each 0 when it does not fit 16 bits (the layout is
 //              then never chosen);
-//   meta[k]  = {first spot, spots | shifts << 16, norm bits, 0}.
+//   meta[k]  = {first spot, spots | shifts << 16, norm bits, bits of sum_i |I_i| rounded up}.
 enum { TM_LAYOUT_DUAL = 0, TM_LAYOUT_WF = 1, TM_LAYOUT_WRAP = 2 };
 
 struct SparseLib {

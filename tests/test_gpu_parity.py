@@ -387,3 +387,43 @@ def test_refined_angles_match_oracle_and_reduce_error(ctx, tiny):
     e_plain, e_fine = err(plain["angle_deg"][:, 0])[ok], err(fine["angle_deg"][:, 0])[ok]
     assert e_fine.mean() < e_plain.mean(), (e_fine.mean(), e_plain.mean())
     ctx.unload_library(lid)
+
+
+def _topn_from_scores(q, s, active, N):
+    """Top-N by (Q desc, template asc) over the active templates of each pattern."""
+    n, K = q.shape
+    tk = np.full((n, N), -1, np.int64)
+    ts_ = np.full((n, N), -1, np.int64)
+    tq = np.full((n, N), -np.inf, np.float32)
+    for p in range(n):
+        idx = np.flatnonzero(active[p])
+        order = idx[np.lexsort((idx, -q[p, idx].astype(np.float64)))][:N]
+        tk[p, :len(order)], ts_[p, :len(order)], tq[p, :len(order)] = order, s[p, order], q[p, order]
+    return tk, ts_, tq
+
+
+@pytest.mark.parametrize("which,prefilter,subtract", [("fcc", 0.5, 0.0), ("fcc", 1.0, 0.3), ("hcp", 0.5, 0.0)])
+def test_bound_pruning_is_exact(ctx, which, prefilter, subtract):
+    """The fused top-N skips templates whose bound cannot reach the running N-th best; its hits
+    equal, bit for bit, the top-N taken from every template's score computed without skipping
+    (tm_correlate) on the same polar images and the same pre-filter mask."""
+    ts = synth.kinematic_library(which, step_deg=1.0)
+    rng = synth.make_rng(9)
+    scan = synth.render_scan(rng, ts, 48, 256, 256, n_theta=360)
+    lid = ctx.load_library(ts, 128, 360)
+    K = ctx.library_info(lid)["n_templates"]
+    f = _t(scan.frames)
+    hits = tmgb.hits_to_numpy(ctx.index(f, lid, top_n=5, prefilter=prefilter, subtract=subtract))[0]
+    polar, norm, radial = ctx.polar_transform(f, 128, 360, subtract=subtract)
+    mask = None
+    active = np.ones((48, K), bool)
+    if prefilter < 1.0:
+        mask, _ = ctx.prefilter(lid, radial, prefilter)
+        bits = np.unpackbits(mask.cpu().numpy().view(np.uint8), bitorder="little").reshape(48, -1)
+        active = bits[:, :K].astype(bool)
+    q, s = ctx.correlate(lid, polar, norm, mask=mask)
+    tk, tsh, tq = _topn_from_scores(q.cpu().numpy(), s.cpu().numpy(), active, 5)
+    assert np.array_equal(hits["template_index"], tk)
+    assert np.array_equal(hits["shift"], tsh)
+    assert np.array_equal(hits["score"], tq)
+    ctx.unload_library(lid)
