@@ -292,6 +292,9 @@ enum {
 typedef struct tm_profile {
     double ms[TM_STAGE_COUNT];        /* summed launch durations                        */
     int64_t launches[TM_STAGE_COUNT]; /* kernel launches timed                           */
+    int64_t sparse_macs;              /* multiply-adds (spots x shifts of the templates
+                                         scored) the FP32 sparse kernel executed; its bound
+                                         pruning skips templates that cannot enter the top-N */
 } tm_profile;
 
 /* Enable (1) or disable (0) stage timing for later calls on ctx; resets the totals. */

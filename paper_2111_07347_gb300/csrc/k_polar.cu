@@ -14,17 +14,23 @@
 // samples on an arc (same x, different y) fall in different banks.  Otherwise the taps
 // are read from global memory.
 //
-// Tap positions and bilinear fractions come from a table built on the host in double
-// precision for the call's centre.  The fractions are stored as 23-bit fixed point q, so
-// that both weights come out of float arithmetic exactly: with y = 1 + q 2^-23 (formed by
-// bit assembly), fx = y - 1 and 1 - fx = 2 - y, both exact; each weight is then within
-// 2^-24 of the double-precision value.  A sample whose four taps are all inside the
-// frame takes a fast path with one bounds test and the subtraction applied once
-// (the weights sum to exactly 1); edge samples test each tap (zero outside).
+// Tap positions come from fixed-point ray stepping: along the ray of angle theta_k the
+// sample of row j sits at x = cx + j dr cos(theta_k), kept as a signed 32.32 fixed-point
+// integer X = CX + j DX, with DX = round(dr cos(theta_k) 2^32) built on the host in double
+// precision (one pair per angle, 16 B, instead of a table entry per sample).  The integer
+// part of X is the tap column x0; the top 23 bits of the fraction (rounded, the carry
+// going into x0) give the bilinear weight exactly: with y = 1 + q 2^-23 (formed by bit
+// assembly), fx = y - 1 and 1 - fx = 2 - y are both exact.  The position error is at most
+// (j + 1) 2^-33 px before the rounding to 23 bits, each weight within 2^-24 (+ that) of
+// the double-precision value.  A per-pattern centre enters only through CX, converted
+// exactly from its float value.  A sample whose four taps are all inside the frame takes
+// a fast path with one bounds test and the subtraction applied once (the weights sum to
+// exactly 1); edge samples test each tap (zero outside).
 // For u16 frames the gamma of the pixel values below 4096 (all of them at the counts of an
 // electron diffraction pattern) is tabulated once per CTA in shared memory, g(v) - c from
 // the same correctly rounded sqrtf / powf, so a tap is one table read; larger values are
-// computed directly.
+// computed directly.  The staging notes whether any pixel of the frame is that large, and
+// frames without one take a path with no per-tap range test.
 // Reductions run in a fixed order: the result does not depend on the grid size or on
 // other patterns of the batch.
 #include <math.h>
@@ -112,7 +118,7 @@ __device__ __forceinline__ void fixed_weights(uint32_t q, float& f, float& g) {
 
 // Bilinear sample of the gamma-corrected, subtracted frame at (x0 + fx, y0 + fy); the frame
 // has row pitch `pitch` elements; taps outside [0, W) x [0, H) contribute zero.
-template <typename T, int MODE, bool SMEM>
+template <typename T, int MODE, bool SMEM, bool LUT_ONLY>
 __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int W, int x0, int y0, float fx,
                                           float gx, float fy, float gy, const float* lut, float2 g, float sub,
                                           const uint8_t* pmask) {
@@ -121,7 +127,7 @@ __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int 
         const T a = load_px_masked<SMEM>(p, frame, pmask), b = load_px_masked<SMEM>(p + 1, frame, pmask);
         const T c = load_px_masked<SMEM>(p + pitch, frame, pmask), d = load_px_masked<SMEM>(p + pitch + 1, frame, pmask);
         float v00, v10, v01, v11;
-        if (all_in_lut(a, b, c, d)) {
+        if (LUT_ONLY || all_in_lut(a, b, c, d)) {
             v00 = lut[(int)a];
             v10 = lut[(int)b];
             v01 = lut[(int)c];
@@ -145,25 +151,6 @@ __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int 
     return gy * (gx * v[0] + fx * v[1]) + fy * (gx * v[2] + fx * v[3]);
 }
 
-// Tap of a sample at offset (dx, dy) = (r cos theta, r sin theta) from a per-pattern centre
-// (cx, cy): the offsets come from the host in double precision split as hi + lo floats;
-// x = cx + dx is formed with an error-free sum so that the fraction is accurate far below
-// float resolution before it is rounded.
-__device__ __forceinline__ void centre_tap(float c, float hi, float lo, int& i0, float& f, float& g) {
-    const float s = c + hi;
-    const float bb = s - c;
-    const float err = (c - (s - bb)) + (hi - bb);               // s + err == c + hi exactly
-    float base = floorf(s);
-    float fh = s - base;                                        // exact
-    float fl = err + lo;
-    float fr = fh + fl;
-    if (fr < 0.0f) { base -= 1.0f; fh += 1.0f; fr = fh + fl; }
-    else if (fr >= 1.0f) { base += 1.0f; fh -= 1.0f; fr = fh + fl; }
-    i0 = (int)base;
-    f = fr;
-    g = (1.0f - fh) - fl;
-}
-
 // Sum of a[u] over the 32 lanes for four rows u at once (6 shuffles instead of 20): after
 // the exchange the lanes 8u hold the total of row u.  Fixed order: deterministic.
 __device__ __forceinline__ float warp_sum4(const float a[4], int lane) {
@@ -178,39 +165,94 @@ __device__ __forceinline__ float warp_sum4(const float a[4], int lane) {
     return c;                                   // row (lane >> 3) when (lane & 7) == 0
 }
 
-// One polar sample (table entry idx): tap position and weights from the fixed table, or
-// from the per-pattern centre plus the offset table.
-template <typename T, int MODE, bool STAGED, bool CENTRES>
-__device__ __forceinline__ float sample(const T* frame, int pitch, int H, int W, int idx,
-                                       const int32_t* __restrict__ txy, const uint2* __restrict__ tq,
-                                       const float4* __restrict__ toff, float2 cen, const float* lut, float2 g,
-                                       float sub, const uint8_t* pmask) {
-    int x0, y0;
+constexpr long long kRound = 1ll << 8;     // half of the last kept fraction bit (2^-24 of a pixel)
+
+// One polar sample at the fixed-point position (X, Y) (32.32, rounding bias included).
+template <typename T, int MODE, bool STAGED, bool LUT_ONLY>
+__device__ __forceinline__ float sample_at(const T* frame, int pitch, int H, int W, long long X, long long Y,
+                                          const float* lut, float2 g, float sub, const uint8_t* pmask) {
     float fx, gx, fy, gy;
-    if (CENTRES) {
-        const float4 o = __ldg(toff + idx);                      // dx hi, dx lo, dy hi, dy lo
-        centre_tap(cen.x, o.x, o.y, x0, fx, gx);
-        centre_tap(cen.y, o.z, o.w, y0, fy, gy);
-    } else {
-        const int xy = __ldg(txy + idx);
-        const uint2 q = __ldg(tq + idx);
-        x0 = (int)(int16_t)(xy & 0xffff);
-        y0 = xy >> 16;
-        fixed_weights(q.x, fx, gx);
-        fixed_weights(q.y, fy, gy);
-    }
-    return bilinear<T, MODE, STAGED>(frame, pitch, H, W, x0, y0, fx, gx, fy, gy, lut, g, sub, pmask);
+    fixed_weights((uint32_t)X >> 9, fx, gx);
+    fixed_weights((uint32_t)Y >> 9, fy, gy);
+    return bilinear<T, MODE, STAGED, LUT_ONLY>(frame, pitch, H, W, (int)(X >> 32), (int)(Y >> 32), fx, gx, fy, gy, lut,
+                                              g, sub, pmask);
 }
 
 constexpr int kMaxThreads = 768;            // 80 registers per thread at one CTA per SM
 
-template <typename T, int MODE, bool STAGED, bool CENTRES>
+// The polar rows of one pattern: thread (grp, k0) takes columns k0, k0 + cols, ... of rows
+// grp, grp + R, ..., four rows at a time.  Stores the kept rows, adds P'^2 to the thread's
+// Kahan sum and leaves each row's partial sums per warp in part[row][warp].
+template <typename T, int MODE, bool STAGED, bool LUT_ONLY>
+__device__ __forceinline__ void polar_rows(const T* frame, int pf, int H, int W, long long cxb, long long cyb,
+                                           const longlong2* __restrict__ rays, int n_r, int n_theta, int R,
+                                           int cols, int grp, int k0, int lane, int warp, int nw,
+                                           const uint8_t* __restrict__ keep_row, const uint8_t* pmask,
+                                           const float* lut, float2 g, float sub, float* __restrict__ out,
+                                           float* part, float& s2, float& c2) {
+    const int my_rows = grp < n_r ? (n_r - grp + R - 1) / R : 0;        // rows grp, grp + R, ... (warp-uniform)
+    for (int kk = 0; kk < n_theta; kk += cols) {                        // block-uniform
+        const int k = kk + k0;
+        const bool active = k < n_theta;
+        long long X = cxb, Y = cyb, SX = 0, SY = 0;
+        if (active) {
+            const longlong2 d = __ldg(rays + k);
+            X += (long long)grp * d.x;
+            Y += (long long)grp * d.y;
+            SX = (long long)R * d.x;
+            SY = (long long)R * d.y;
+        }
+        for (int b = 0; b < my_rows; b += 4) {                          // warp-uniform
+            const int nu = my_rows - b;                                 // rows left in this batch (>= 1)
+            const int j0 = grp + R * b;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (active) {
+                float v[4];
+                if (nu >= 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v[u] = sample_at<T, MODE, STAGED, LUT_ONLY>(frame, pf, H, W, X, Y, lut, g, sub, pmask);
+                        X += SX;
+                        Y += SY;
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v[u] = u < nu ? sample_at<T, MODE, STAGED, LUT_ONLY>(frame, pf, H, W, X, Y, lut, g, sub, pmask)
+                                      : 0.0f;
+                        X += SX;
+                        Y += SY;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u < nu) {
+                        const int j = j0 + R * u;
+                        if (!keep_row || keep_row[j]) out[(size_t)j * n_theta + k] = v[u];
+                        const float y = fmaf(v[u], v[u], -c2);
+                        const float t = s2 + y;
+                        c2 = (t - s2) - y;
+                        s2 = t;
+                        acc[u] = v[u];
+                    }
+                }
+            }
+            const float r = warp_sum4(acc, lane);
+            const int u = lane >> 3;
+            if ((lane & 7) == 0 && u < nu) {
+                float* dst = part + (j0 + R * u) * nw + warp;
+                *dst = kk ? *dst + r : r;
+            }
+        }
+    }
+}
+
+template <typename T, int MODE, bool STAGED>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, const int32_t* __restrict__ txy,
-             const uint2* __restrict__ tq, float2 g, float sub, int n_r, int n_theta, int R,
+polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, const longlong2* __restrict__ rays,
+             long long cxb, long long cyb, float2 g, float sub, int n_r, int n_theta, int R,
              const uint8_t* __restrict__ keep_row, const uint8_t* __restrict__ pmask, float* __restrict__ polar,
-             float* __restrict__ pnorm,
-             float* __restrict__ radial, const float2* __restrict__ centres, const float4* __restrict__ toff) {
+             float* __restrict__ pnorm, float* __restrict__ radial, const float2* __restrict__ centres) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int cols = blockDim.x / R;                     // threads per row group (multiple of 32)
     const int grp = threadIdx.x / cols, k0 = threadIdx.x - grp * cols;
@@ -229,14 +271,14 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
         }
         __syncthreads();
     }
-    const int my_rows = grp < n_r ? (n_r - grp + R - 1) / R : 0;        // rows grp, grp + R, ...
-    const int rstride = R * n_theta;                                    // table step between them
 
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
         const T* gframe = frames + (size_t)p * H * W;
         const T* frame = gframe;
+        bool big = true;                                 // some pixel may lie beyond the gamma table
         if (STAGED) {
             __syncthreads();                             // previous pattern's reads are done
+            uint32_t hi_bits = 0;                        // OR of the staged u16 words, above the table
             const bool vec = (((uintptr_t)gframe) & 15) == 0 && (W * sizeof(T)) % 16 == 0;
             if (vec) {
                 const int vr = (int)(W * sizeof(T) / 16);           // 16-byte vectors per row
@@ -266,62 +308,37 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
                             d[1] = v[b].y;
                             d[2] = v[b].z;
                             d[3] = v[b].w;
+                            hi_bits |= v[b].x | v[b].y | v[b].z | v[b].w;
                         }
                     }
                 }
             } else {
                 for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
                     const int y = e / W;
-                    sF[(size_t)y * pitch + (e - y * W)] = (!pmask || pmask[e]) ? gframe[e] : T(0);
+                    const T v = (!pmask || pmask[e]) ? gframe[e] : T(0);
+                    sF[(size_t)y * pitch + (e - y * W)] = v;
+                    if (kHasLut) hi_bits |= (uint32_t)v;
                 }
             }
-            __syncthreads();
+            // u16 words: a pixel >= kLut sets a bit of 0xF000 in its half
+            big = __syncthreads_or(kHasLut ? (hi_bits & 0xF000F000u) != 0 : 1) != 0;
             frame = sF;
         }
         float* out = polar + (size_t)p * n_r * n_theta;
-        float2 cen = make_float2(0.0f, 0.0f);
-        if (CENTRES) cen = __ldg(centres + p);
+        long long cx = cxb, cy = cyb;
+        if (centres) {                                   // exact: c 2^32 is an integer-valued float
+            const float2 c = __ldg(centres + p);
+            cx = __float2ll_rn(c.x * 4294967296.0f) + kRound;
+            cy = __float2ll_rn(c.y * 4294967296.0f) + kRound;
+        }
         const int pf = STAGED ? pitch : W;
         float s2 = 0.0f, c2 = 0.0f;                      // Kahan sum of P'^2 for this thread
-        for (int b = 0; b < my_rows; b += 4) {           // warp-uniform
-            const int nu = my_rows - b;                  // rows left in this batch (>= 1)
-            const int j0 = grp + R * b;
-            unsigned keep = 0;                           // rows of the batch whose values are stored
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (u < nu && (!keep_row || keep_row[j0 + R * u])) keep |= 1u << u;
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            for (int k = k0; k < n_theta; k += cols) {
-                const int idx0 = j0 * n_theta + k;
-                float v[4];
-                if (nu >= 4) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        v[u] = sample<T, MODE, STAGED, CENTRES>(frame, pf, H, W, idx0 + u * rstride, txy, tq, toff,
-                                                                cen, lut, g, sub, pmask);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        v[u] = u < nu ? sample<T, MODE, STAGED, CENTRES>(frame, pf, H, W, idx0 + u * rstride, txy, tq,
-                                                                         toff, cen, lut, g, sub, pmask)
-                                      : 0.0f;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (u < nu) {
-                        if ((keep >> u) & 1u) out[idx0 + u * rstride] = v[u];
-                        const float y = fmaf(v[u], v[u], -c2);
-                        const float t = s2 + y;
-                        c2 = (t - s2) - y;
-                        s2 = t;
-                        acc[u] += v[u];
-                    }
-                }
-            }
-            const float r = warp_sum4(acc, lane);
-            const int u = lane >> 3;
-            if ((lane & 7) == 0 && u < nu) part[(j0 + R * u) * nw + warp] = r;
-        }
+        if (kHasLut && STAGED && !big)
+            polar_rows<T, MODE, STAGED, true>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, R, cols, grp, k0, lane,
+                                              warp, nw, keep_row, pmask, lut, g, sub, out, part, s2, c2);
+        else
+            polar_rows<T, MODE, STAGED, false>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, R, cols, grp, k0, lane,
+                                               warp, nw, keep_row, pmask, lut, g, sub, out, part, s2, c2);
         red[threadIdx.x] = s2;
         __syncthreads();
         // fixed-order tree over the block (blockDim is a multiple of 32)
@@ -345,12 +362,12 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
     }
 }
 
-template <typename T, int MODE, bool STAGED, bool CENTRES>
-cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab, float2 g, float sub,
-                       int n_r, int n_theta, int R, int threads, size_t smem, const uint8_t* keep_row,
-                       const uint8_t* pmask, float* polar, float* pnorm, float* radial, const float2* centres,
-                       const float4* offsets, cudaStream_t st) {
-    auto kern = polar_kernel<T, MODE, STAGED, CENTRES>;
+template <typename T, int MODE, bool STAGED>
+cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, const longlong2* rays, long long cxb,
+                       long long cyb, float2 g, float sub, int n_r, int n_theta, int R, int threads, size_t smem,
+                       const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm, float* radial,
+                       const float2* centres, cudaStream_t st) {
+    auto kern = polar_kernel<T, MODE, STAGED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1, dev = 0, sms = 148;
@@ -359,30 +376,25 @@ cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, cons
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > n) grid = n;
-    kern<<<(int)grid, threads, smem, st>>>(frames, n, H, W, pitch, tab.xy, tab.q, g, sub, n_r, n_theta, R, keep_row,
-                                           pmask, polar, pnorm, radial, centres, offsets);
+    kern<<<(int)grid, threads, smem, st>>>(frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, keep_row,
+                                           pmask, polar, pnorm, radial, centres);
     return cudaGetLastError();
 }
 
 template <typename T, bool STAGED>
-cudaError_t launch_mode(int mode, const T* frames, int64_t n, int H, int W, int pitch, const PolarTable& tab,
-                        float2 g, float sub, int n_r, int n_theta, int R, int threads, size_t smem,
-                        const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm, float* radial,
-                        const float2* centres, const float4* offsets, cudaStream_t st) {
-    if (mode == 0)
-        return (centres ? launch_one<T, 0, STAGED, true> : launch_one<T, 0, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
-                                        pmask, polar, pnorm, radial, centres, offsets, st);
-    if (mode == 1)
-        return (centres ? launch_one<T, 1, STAGED, true> : launch_one<T, 1, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
-                                        pmask, polar, pnorm, radial, centres, offsets, st);
-    return (centres ? launch_one<T, 2, STAGED, true> : launch_one<T, 2, STAGED, false>)(frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem, keep_row,
-                                    pmask, polar, pnorm, radial, centres, offsets, st);
+cudaError_t launch_mode(int mode, const T* frames, int64_t n, int H, int W, int pitch, const longlong2* rays,
+                        long long cxb, long long cyb, float2 g, float sub, int n_r, int n_theta, int R, int threads,
+                        size_t smem, const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm,
+                        float* radial, const float2* centres, cudaStream_t st) {
+    auto f = mode == 0 ? launch_one<T, 0, STAGED> : (mode == 1 ? launch_one<T, 1, STAGED> : launch_one<T, 2, STAGED>);
+    return f(frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, threads, smem, keep_row, pmask, polar,
+             pnorm, radial, centres, st);
 }
 
 template <typename T>
-cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const PolarTable& tab, int mode, float2 g,
-                         float sub, int n_r, int n_theta, float* polar, float* pnorm, float* radial, cudaStream_t st,
-                         const uint8_t* keep_row, const float2* centres, const float4* offsets, const uint8_t* pmask) {
+cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const longlong2* rays, long long cxb, long long cyb,
+                         int mode, float2 g, float sub, int n_r, int n_theta, float* polar, float* pnorm, float* radial,
+                         cudaStream_t st, const uint8_t* keep_row, const float2* centres, const uint8_t* pmask) {
     const int cols = ((n_theta + 31) / 32) * 32;
     if (cols <= kMaxThreads) {
         // staged: rows padded to an odd number of 32-bit words
@@ -396,46 +408,33 @@ cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const PolarTa
         const size_t lut = sizeof(T) == 2 ? kLut * sizeof(float) : 0;
         const size_t smem = fbytes + lut + ((size_t)n_r * nw + threads) * sizeof(float);
         if (smem <= 200 * 1024)
-            return launch_mode<T, true>(mode, frames, n, H, W, pitch, tab, g, sub, n_r, n_theta, R, threads, smem,
-                                        keep_row, pmask, polar, pnorm, radial, centres, offsets, st);
+            return launch_mode<T, true>(mode, frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, threads,
+                                        smem, keep_row, pmask, polar, pnorm, radial, centres, st);
     }
     const int threads = cols < kMaxThreads ? cols : kMaxThreads;
     const size_t smem = (sizeof(T) == 2 ? kLut * sizeof(float) : 0) + ((size_t)n_r * (threads / 32) + threads) * sizeof(float);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    return launch_mode<T, false>(mode, frames, n, H, W, W, tab, g, sub, n_r, n_theta, 1, threads, smem, keep_row,
-                                 pmask, polar, pnorm, radial, centres, offsets, st);
+    return launch_mode<T, false>(mode, frames, n, H, W, W, rays, cxb, cyb, g, sub, n_r, n_theta, 1, threads, smem,
+                                 keep_row, pmask, polar, pnorm, radial, centres, st);
 }
 
 }  // namespace
 
-void build_polar_taps(int H, int W, int n_r, int n_theta, double dr, double cx, double cy, int32_t* xy, uint2* q) {
-    (void)H;
-    for (int j = 0; j < n_r; ++j) {
-        const double r = j * dr;
-        for (int k = 0; k < n_theta; ++k) {
-            const double th = 2.0 * kPi * k / n_theta;
-            const double x = cx + r * cos(th), y = cy + r * sin(th);
-            double x0 = floor(x), y0 = floor(y);
-            double fx = x - x0, fy = y - y0;
-            int64_t qx = llround(fx * 8388608.0), qy = llround(fy * 8388608.0);
-            if (qx >= 8388608) { qx = 0; x0 += 1.0; }          // fraction rounds up to the next tap
-            if (qy >= 8388608) { qy = 0; y0 += 1.0; }
-            // taps outside [-2, size + 1] contribute zero either way; clamp into int16
-            if (x0 < -2.0 || x0 > (double)W + 1.0) { x0 = std::min(std::max(x0, -2.0), (double)W + 1.0); qx = 0; }
-            if (y0 < -2.0 || y0 > (double)H + 1.0) { y0 = std::min(std::max(y0, -2.0), (double)H + 1.0); qy = 0; }
-            const size_t i = (size_t)j * n_theta + k;
-            xy[i] = (int32_t)((uint32_t)(uint16_t)(int16_t)(int)x0 | ((uint32_t)(int16_t)(int)y0 << 16));
-            q[i] = make_uint2((uint32_t)qx, (uint32_t)qy);
-        }
+void build_polar_rays(int n_theta, double dr, longlong2* rays) {
+    for (int k = 0; k < n_theta; ++k) {
+        const double th = 2.0 * kPi * k / n_theta;
+        rays[k].x = llround(dr * cos(th) * 4294967296.0);
+        rays[k].y = llround(dr * sin(th) * 4294967296.0);
     }
 }
 
-cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
-                         const PolarTable& tab, double gamma, double subtract, int n_r,
-                         int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st, const uint8_t* keep_row, const float2* centres, const float4* offsets,
+cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W, const longlong2* rays, double cx,
+                         double cy, double gamma, double subtract, int n_r, int n_theta, float* polar, float* pnorm,
+                         float* radial, cudaStream_t st, const uint8_t* keep_row, const float2* centres,
                          const uint8_t* pixel_mask, double threshold) {
     if (n <= 0) return cudaSuccess;
+    // positions stay within 2^31 px in the 32.32 format (the caller bounds n_r dr as well)
+    if (!(fabs(cx) < 1073741824.0 && fabs(cy) < 1073741824.0)) return cudaErrorInvalidValue;
     const int mode = gamma == 0.5 ? 0 : (gamma == 1.0 ? 1 : 2);
     // threshold: pixels v < threshold read as 0.  As a float t with v < t exactly when
     // v < threshold for every float v (t rounded up when the float is below threshold).
@@ -445,11 +444,12 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
         if ((double)thr < threshold) thr = nextafterf(thr, INFINITY);
     }
     const float2 g = make_float2((float)gamma, thr);
+    const long long cxb = llround(cx * 4294967296.0) + kRound, cyb = llround(cy * 4294967296.0) + kRound;
     if (dtype == TM_DTYPE_U16)
-        return launch_typed<uint16_t>((const uint16_t*)frames, n, H, W, tab, mode, g, (float)subtract, n_r,
-                                      n_theta, polar, pnorm, radial, st, keep_row, centres, offsets, pixel_mask);
-    return launch_typed<float>((const float*)frames, n, H, W, tab, mode, g, (float)subtract, n_r, n_theta,
-                               polar, pnorm, radial, st, keep_row, centres, offsets, pixel_mask);
+        return launch_typed<uint16_t>((const uint16_t*)frames, n, H, W, rays, cxb, cyb, mode, g, (float)subtract, n_r,
+                                      n_theta, polar, pnorm, radial, st, keep_row, centres, pixel_mask);
+    return launch_typed<float>((const float*)frames, n, H, W, rays, cxb, cyb, mode, g, (float)subtract, n_r, n_theta,
+                               polar, pnorm, radial, st, keep_row, centres, pixel_mask);
 }
 
 }  // namespace tmgb

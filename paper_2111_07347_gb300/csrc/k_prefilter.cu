@@ -1,15 +1,21 @@
 // Stage 2: the azimuthally integrated pre-filter (arXiv 2111.07347, Section 2.2 and
 // Fig. 3): the polar image and every template are integrated over the azimuth, the
 // integrated image is correlated with the integrated library (one matrix-vector product
-// per pattern; here one matrix-matrix product per batch) and only the best-correlated
-// templates go on to full matching.
+// per pattern) and only the best-correlated templates go on to full matching.
 //
 //   score[p][k] = R_P[p] . R_T[k] / (|R_P[p]| |R_T[k]|)        (0 if a norm is 0)
 //   keep the ceil(f K) largest per pattern, ties to the lower k  -> bit mask [p][K/32]
 //
-// The scores are a tiled FP32 SIMT product (n_r = 128 is far too short a contraction
-// to pay for tensor-core staging); the selection is an exact 4-pass radix select over
-// order-preserving integer keys, one CTA per pattern.
+// R_T[k] is zero outside the library's few distinct spot radii (9 rows of 128 for FCC), so
+// the product runs over those rows only, in ascending order: the same FP32 sums as the
+// full-length product, whose other terms add exact zeros.  One CTA takes PB patterns: it
+// forms their scores in shared memory (the library's rows are read once for PB patterns)
+// and selects from there, so the scores need not reach global memory.  The selection is
+// exact: a radix select over order-preserving integer keys whose 8-bit digits start at the
+// highest bit in which the pattern's keys differ (cosine scores share their sign and most
+// exponent bits), stopping early once every key of the bin that holds the boundary is kept.
+// The keys' range comes with the scores; one warp finds each digit's bin from per-lane bin
+// counts held in registers; in the first pass, lanes that share a bin are counted together.
 #include "tm_internal.h"
 
 namespace tmgb {
@@ -30,125 +36,281 @@ __global__ void radial_norm_kernel(const float* __restrict__ radial, int64_t n, 
     if (lane == 0) out[p] = sqrtf(s);
 }
 
-constexpr int PT = 64, KT = 64, RC = 16;   // tile: 64 patterns x 64 templates, 16-deep chunks
-
-__global__ void __launch_bounds__(256)
-prefilter_scores_kernel(const float* __restrict__ radial, const float* __restrict__ rpn, int64_t n,
-                        int n_r, RadialLib lib, float* __restrict__ score) {
-    __shared__ float sp[RC][PT + 4];
-    __shared__ float st[RC][KT + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;    // 16 x 16 threads, 4 x 4 each
-    const int64_t p0 = (int64_t)blockIdx.y * PT;
-    const int k0 = blockIdx.x * KT;
-    float acc[4][4] = {};
-    for (int r0 = 0; r0 < n_r; r0 += RC) {
-        for (int i = threadIdx.x; i < RC * PT; i += 256) {
-            const int rr = i % RC, pp = i / RC;
-            const int64_t p = p0 + pp;
-            sp[rr][pp] = (p < n && r0 + rr < n_r) ? radial[(size_t)p * n_r + r0 + rr] : 0.0f;
-        }
-        for (int i = threadIdx.x; i < RC * KT; i += 256) {
-            const int rr = i % RC, kk = i / RC;
-            const int k = k0 + kk;
-            st[rr][kk] = (k < lib.K && r0 + rr < n_r) ? lib.radial[(size_t)k * n_r + r0 + rr] : 0.0f;
-        }
-        __syncthreads();
-        #pragma unroll
-        for (int rr = 0; rr < RC; ++rr) {
-            float a[4], b[4];
-            #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sp[rr][ty * 4 + i];
-            #pragma unroll
-            for (int i = 0; i < 4; ++i) b[i] = st[rr][tx * 4 + i];
-            #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(a[i], b[jj], acc[i][jj]);
-        }
-        __syncthreads();
-    }
-    #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t p = p0 + ty * 4 + i;
-        if (p >= n) continue;
-        const float np_ = rpn[p];
-        #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            const int k = k0 + tx * 4 + jj;
-            if (k >= lib.K) continue;
-            const float d = np_ * lib.rnorm[k];
-            score[(size_t)p * lib.K + k] = d > 0.0f ? __fdiv_rn(acc[i][jj], d) : 0.0f;
-        }
-    }
-}
-
 __device__ __forceinline__ uint32_t order_key(float x) {
     const uint32_t u = __float_as_uint(x);
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);     // larger float -> larger key
 }
 
 constexpr int SEL_THREADS = 512;
+constexpr int SEL_BINS = 256;                              // digits of at most 8 bits
+constexpr int MAX_PB = 2;
 
+struct SelShared {
+    uint32_t kmin[MAX_PB], kmax[MAX_PB];                    // range of each pattern's keys
+    uint32_t prefix, remaining, done;
+    uint32_t wsum[SEL_THREADS / 32];
+};
+
+// Running min / max of a thread's keys into sh (lane 0 of each warp after a warp reduce).
+__device__ __forceinline__ void range_publish(uint32_t lo, uint32_t hi, uint32_t* kmin, uint32_t* kmax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(kmin, lo);
+        atomicMax(kmax, hi);
+    }
+}
+
+// Histogram increment; with `gather`, lanes of a warp that share a bin are first counted
+// together (the first digit of cosine scores puts most keys in a few bins).
+__device__ __forceinline__ void hist_add(uint32_t* hist, bool in, uint32_t bin, bool gather) {
+    const int lane = threadIdx.x & 31;
+    unsigned pending = __ballot_sync(0xffffffffu, in);
+    if (gather) {
+#pragma unroll 1
+        for (int it = 0; it < 3 && pending; ++it) {
+            const int leader = __ffs(pending) - 1;
+            const uint32_t b = __shfl_sync(0xffffffffu, bin, leader);
+            const unsigned m = __ballot_sync(0xffffffffu, ((pending >> lane) & 1u) && bin == b);
+            if (lane == leader) atomicAdd(&hist[b], (uint32_t)__popc(m));
+            pending &= ~m;
+        }
+    }
+    if ((pending >> lane) & 1u) atomicAdd(&hist[bin], 1u);
+}
+
+// The `keep` largest of keys[0, K) (ties to the lower index) as bits of mrow[ceil(K/32)].
+// [kmin, kmax] is the keys' range.  Called by the whole block with uniform arguments after a
+// barrier that follows the last write of keys; ends with a barrier.
+__device__ __forceinline__ void select_keep(const uint32_t* keys, int K, int keep, uint32_t kmin, uint32_t kmax, uint32_t* hist,
+                            SelShared& sh, uint32_t* __restrict__ mrow) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int words = (K + 31) >> 5;
+    if (keep <= 0 || keep >= K) {
+        for (int w = tid; w < words; w += blockDim.x) {
+            const int left = K - 32 * w;
+            mrow[w] = keep <= 0 ? 0u : (left >= 32 ? 0xffffffffu : (1u << left) - 1u);
+        }
+        __syncthreads();
+        return;
+    }
+    uint32_t T, need;
+    if (kmin == kmax) {
+        T = kmin;                                           // all equal: the first `keep` indices
+        need = (uint32_t)keep;
+    } else {
+        const int bits = 32 - __clz(kmin ^ kmax);           // the keys differ in bits [0, bits)
+        uint32_t prefix = bits == 32 ? 0u : (kmin >> bits) << bits;
+        uint32_t pmask = bits == 32 ? 0u : 0xffffffffu << bits;
+        uint32_t rem = (uint32_t)keep;                      // still to take among the candidates
+        int left = bits;
+        bool done = false;
+        for (int pass = 0; left > 0; ++pass) {
+            const int d = min(8, left);
+            const int shift = left - d;
+            const uint32_t nb = 1u << d, dm = nb - 1u;
+            for (uint32_t i = tid; i < nb; i += blockDim.x) hist[i] = 0u;
+            __syncthreads();
+            for (int k0 = warp * 32; k0 < K; k0 += blockDim.x) {      // warp-uniform trip count
+                const int k = k0 + lane;
+                const uint32_t x = k < K ? keys[k] : 0u;
+                hist_add(hist, k < K && (x & pmask) == prefix, (x >> shift) & dm, pass == 0);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // lane l holds bins [l c, l c + c) in registers; suffix sums over the lanes
+                // find the bin where the count from the top first reaches rem
+                const uint32_t c = nb >= 32u ? nb >> 5 : 1u;
+                const uint32_t b0 = (uint32_t)lane * c;
+                uint32_t h[8];
+                if (c == 8u) {
+                    const uint4 a = *reinterpret_cast<const uint4*>(hist + b0);
+                    const uint4 e = *reinterpret_cast<const uint4*>(hist + b0 + 4);
+                    h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
+                    h[4] = e.x; h[5] = e.y; h[6] = e.z; h[7] = e.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) h[i] = ((uint32_t)i < c && b0 + i < nb) ? hist[b0 + i] : 0u;
+                }
+                uint32_t t = 0u;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t += h[i];
+                uint32_t sfx = t;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_down_sync(0xffffffffu, sfx, o);
+                    if (lane + o < 32) sfx += v;
+                }
+                const uint32_t above = sfx - t;
+                if (b0 < nb && sfx >= rem && above < rem) {
+                    uint32_t cum = above, cum_at = above, hb = 0u;
+                    int bi = 0;
+                    bool found = false;
+#pragma unroll
+                    for (int i = 7; i >= 0; --i) {
+                        if (!found && (uint32_t)i < c) {
+                            if (cum + h[i] >= rem) {
+                                found = true;
+                                bi = i;
+                                cum_at = cum;
+                                hb = h[i];
+                            } else {
+                                cum += h[i];
+                            }
+                        }
+                    }
+                    sh.done = cum_at + hb == rem ? 1u : 0u;
+                    sh.prefix = prefix | ((b0 + (uint32_t)bi) << shift);
+                    sh.remaining = rem - cum_at;
+                }
+            }
+            __syncthreads();
+            prefix = sh.prefix;
+            rem = sh.remaining;
+            pmask |= dm << shift;
+            left = shift;
+            if (sh.done) { done = true; break; }
+        }
+        // done: every candidate of the last bin is kept, so keep all keys >= the bin's lowest
+        T = prefix;
+        need = done ? 0xffffffffu : rem;
+    }
+    // kept = key > T, or key == T among the first `need` such keys in index order; each warp
+    // writes a contiguous run of words
+    const int per = (words + nw - 1) / nw;
+    const int w0 = warp * per, w1 = min(words, w0 + per);
+    if (need != 0xffffffffu) {
+        uint32_t cnt = 0u;
+        for (int w = w0; w < w1; ++w) {
+            const int k = 32 * w + lane;
+            cnt += __popc(__ballot_sync(0xffffffffu, k < K && keys[k] == T));
+        }
+        if (lane == 0) sh.wsum[warp] = cnt;
+        __syncthreads();
+    }
+    uint32_t before = 0u;
+    if (need != 0xffffffffu)
+        for (int w = 0; w < warp; ++w) before += sh.wsum[w];
+    for (int w = w0; w < w1; ++w) {
+        const int k = 32 * w + lane;
+        const uint32_t key = k < K ? keys[k] : 0u;
+        const bool eq = k < K && key == T;
+        const uint32_t eqb = __ballot_sync(0xffffffffu, eq);
+        const uint32_t rank = before + __popc(eqb & ((1u << lane) - 1u));
+        const bool kept = k < K && (key > T || (eq && rank < need));
+        const uint32_t word = __ballot_sync(0xffffffffu, kept);
+        if (lane == 0) mrow[w] = word;
+        before += __popc(eqb);
+    }
+    __syncthreads();
+}
+
+// PB patterns per CTA: scores into shared memory as keys, then one selection per pattern.
+// The library's radial sums are [K][n_pad] (n_pad = n_rad rounded up to 4, zero-padded), read
+// as float4; the patterns' sums at the radii go to shared memory in the same padded form.
+template <int PB>
+__global__ void __launch_bounds__(SEL_THREADS)
+prefilter_kernel(const float* __restrict__ radial, const float* __restrict__ rpn, int64_t n, int n_r,
+                 RadialLib lib, int keep, uint32_t* __restrict__ mask, float* __restrict__ score) {
+    extern __shared__ __align__(16) uint32_t keys[];        // rp [PB][n_pad], then keys [PB][K]
+    __shared__ __align__(16) uint32_t hist[SEL_BINS];
+    __shared__ SelShared sh;
+    const int K = lib.K, n_rad = lib.n_rad, n_pad = (n_rad + 3) & ~3, words = (K + 31) >> 5;
+    float* rp = (float*)keys;
+    uint32_t* kb = keys + PB * n_pad;
+    for (int64_t p0 = (int64_t)blockIdx.x * PB; p0 < n; p0 += (int64_t)gridDim.x * PB) {
+        if (threadIdx.x < PB) {
+            sh.kmin[threadIdx.x] = 0xffffffffu;
+            sh.kmax[threadIdx.x] = 0u;
+        }
+        for (int i = threadIdx.x; i < PB * n_pad; i += blockDim.x) {
+            const int b = i / n_pad, j = i - b * n_pad;
+            const int64_t p = p0 + b;
+            rp[i] = (p < n && j < n_rad) ? __ldg(radial + (size_t)p * n_r + __ldg(lib.radii + j)) : 0.0f;
+        }
+        float np_[PB];
+#pragma unroll
+        for (int b = 0; b < PB; ++b) np_[b] = p0 + b < n ? __ldg(rpn + p0 + b) : 0.0f;
+        __syncthreads();
+        uint32_t lo[PB], hi[PB];
+#pragma unroll
+        for (int b = 0; b < PB; ++b) { lo[b] = 0xffffffffu; hi[b] = 0u; }
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            float acc[PB];
+#pragma unroll
+            for (int b = 0; b < PB; ++b) acc[b] = 0.0f;
+            const float4* t4 = reinterpret_cast<const float4*>(lib.radc + (size_t)k * n_pad);
+            for (int j4 = 0; j4 < n_pad; j4 += 4) {
+                const float4 t = __ldg(t4 + (j4 >> 2));
+#pragma unroll
+                for (int b = 0; b < PB; ++b) {
+                    const float4 r = *reinterpret_cast<const float4*>(rp + b * n_pad + j4);
+                    // ascending radii; the padding adds exact zeros
+                    acc[b] = fmaf(r.x, t.x, acc[b]);
+                    acc[b] = fmaf(r.y, t.y, acc[b]);
+                    acc[b] = fmaf(r.z, t.z, acc[b]);
+                    acc[b] = fmaf(r.w, t.w, acc[b]);
+                }
+            }
+            const float rk = __ldg(lib.rnorm + k);
+#pragma unroll
+            for (int b = 0; b < PB; ++b) {
+                const float d = np_[b] * rk;
+                const float sc = d > 0.0f ? __fdiv_rn(acc[b], d) : 0.0f;
+                const uint32_t key = order_key(sc);
+                kb[b * K + k] = key;
+                lo[b] = min(lo[b], key);
+                hi[b] = max(hi[b], key);
+                if (score && p0 + b < n) score[(size_t)(p0 + b) * K + k] = sc;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < PB; ++b) range_publish(lo[b], hi[b], &sh.kmin[b], &sh.kmax[b]);
+        __syncthreads();
+#pragma unroll 1
+        for (int b = 0; b < PB; ++b)
+            if (p0 + b < n)
+                select_keep(kb + (size_t)b * K, K, keep, sh.kmin[b], sh.kmax[b], hist, sh,
+                            mask + (size_t)(p0 + b) * words);
+    }
+}
+
+// Selection alone, over scores already in global memory (the BF16 path's candidates).
 __global__ void __launch_bounds__(SEL_THREADS)
 prefilter_select_kernel(const float* __restrict__ score, int64_t n, int K, int keep,
                         uint32_t* __restrict__ mask) {
-    extern __shared__ uint32_t keys[];              // [K]
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t s_prefix, s_remaining, s_wsum[SEL_THREADS / 32];
+    extern __shared__ __align__(16) uint32_t keys[];        // [K]
+    __shared__ __align__(16) uint32_t hist[SEL_BINS];
+    __shared__ SelShared sh;
     const int words = (K + 31) >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
-        for (int k = threadIdx.x; k < K; k += blockDim.x) keys[k] = order_key(score[(size_t)p * K + k]);
-        if (threadIdx.x == 0) { s_prefix = 0; s_remaining = (uint32_t)keep; }
+        if (threadIdx.x == 0) {
+            sh.kmin[0] = 0xffffffffu;
+            sh.kmax[0] = 0u;
+        }
         __syncthreads();
-        uint32_t pmask = 0;
-        for (int pass = 0; pass < 4; ++pass) {
-            const int shift = 24 - 8 * pass;
-            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-            __syncthreads();
-            const uint32_t prefix = s_prefix;
-            for (int k = threadIdx.x; k < K; k += blockDim.x) {
-                const uint32_t key = keys[k];
-                if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t rem = s_remaining, cum = 0;
-                int b = 255;
-                for (; b > 0; --b) {
-                    if (cum + hist[b] >= rem) break;
-                    cum += hist[b];
-                }
-                s_remaining = rem - cum;
-                s_prefix = prefix | ((uint32_t)b << shift);
-            }
-            pmask |= 255u << shift;
-            __syncthreads();
+        uint32_t lo = 0xffffffffu, hi = 0u;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const uint32_t key = order_key(__ldg(score + (size_t)p * K + k));
+            keys[k] = key;
+            lo = min(lo, key);
+            hi = max(hi, key);
         }
-        const uint32_t T = s_prefix;          // key of the keep-th largest score
-        const uint32_t need = s_remaining;    // how many entries equal to T are kept
-        // keep keys > T, and the first `need` keys == T in ascending k
-        uint32_t taken = 0;
-        for (int base = 0; base < words * 32; base += blockDim.x) {
-            const int k = base + threadIdx.x;
-            const uint32_t key = k < K ? keys[k] : 0u;
-            const bool eq = k < K && key == T;
-            const uint32_t ball = __ballot_sync(0xffffffffu, eq);
-            if (lane == 0) s_wsum[warp] = __popc(ball);
-            __syncthreads();
-            uint32_t before = taken;
-            for (int w = 0; w < warp; ++w) before += s_wsum[w];
-            before += __popc(ball & ((1u << lane) - 1u));
-            const bool kept = k < K && (key > T || (eq && before < need));
-            const uint32_t word = __ballot_sync(0xffffffffu, kept);
-            if (lane == 0 && (k >> 5) < words) mask[(size_t)p * words + (k >> 5)] = word;
-            uint32_t tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wsum[w];
-            taken += tot;
-            __syncthreads();
-        }
+        range_publish(lo, hi, &sh.kmin[0], &sh.kmax[0]);
+        __syncthreads();
+        select_keep(keys, K, keep, sh.kmin[0], sh.kmax[0], hist, sh, mask + (size_t)p * words);
     }
 }
+
+cudaError_t allow_smem(const void* fn, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+constexpr size_t kSelSmemMax = 200 * 1024;                  // dynamic part, beside hist and sh
 
 }  // namespace
 
@@ -159,24 +321,36 @@ cudaError_t launch_radial_norm(const float* radial, int64_t n, int n_r, float* o
     return cudaGetLastError();
 }
 
-cudaError_t launch_prefilter_scores(const float* radial, const float* radial_norm, int64_t n, int n_r,
-                                    const RadialLib& lib, float* score, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    dim3 grid((lib.K + KT - 1) / KT, (unsigned)((n + PT - 1) / PT));
-    prefilter_scores_kernel<<<grid, 256, 0, st>>>(radial, radial_norm, n, n_r, lib, score);
+cudaError_t launch_prefilter(const float* radial, const float* radial_norm, int64_t n, int n_r, const RadialLib& lib,
+                             int keep, uint32_t* mask, float* score, cudaStream_t st) {
+    if (n <= 0 || lib.K <= 0) return cudaSuccess;
+    const size_t per = (size_t)lib.K * 4 + (size_t)((lib.n_rad + 3) & ~3) * 4;
+    // two patterns per CTA while their keys stay within 100 KB (three CTAs fit an SM)
+    const int pb = 2 * per <= 100 * 1024 ? 2 : 1;
+    const size_t smem = pb * per;
+    if (smem > kSelSmemMax) return cudaErrorInvalidValue;
+    const int64_t groups = (n + pb - 1) / pb;
+    const unsigned grid = (unsigned)(groups < (1 << 20) ? groups : (1 << 20));
+    cudaError_t e;
+    if (pb == 2) {
+        e = allow_smem((const void*)prefilter_kernel<2>, smem);
+        if (e != cudaSuccess) return e;
+        prefilter_kernel<2><<<grid, SEL_THREADS, smem, st>>>(radial, radial_norm, n, n_r, lib, keep, mask, score);
+    } else {
+        e = allow_smem((const void*)prefilter_kernel<1>, smem);
+        if (e != cudaSuccess) return e;
+        prefilter_kernel<1><<<grid, SEL_THREADS, smem, st>>>(radial, radial_norm, n, n_r, lib, keep, mask, score);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_prefilter_select(const float* score, int64_t n, int K, int keep, uint32_t* mask,
                                     cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+    if (n <= 0 || K <= 0) return cudaSuccess;
     const size_t smem = (size_t)K * sizeof(uint32_t);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(prefilter_select_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    if (smem > kSelSmemMax) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem((const void*)prefilter_select_kernel, smem);
+    if (e != cudaSuccess) return e;
     const int grid = (int)(n < 65536 ? n : 65536);
     prefilter_select_kernel<<<grid, SEL_THREADS, smem, st>>>(score, n, K, keep, mask);
     return cudaGetLastError();

@@ -247,6 +247,7 @@ sparse_kernel(const SparseCall c) {
     float* s_rmax = (float*)(s_thr + 1);                     // [max_rad] row maxima of P'
     float* s_rabs = s_rmax + c.max_rad;                      // [max_rad] row maxima of |P'|
     const float inv_pitch = 1.0f / (float)pitch;
+    unsigned long long work = 0;                             // multiply-adds of this warp (lane 0)
 
     for (;;) {
         __syncthreads();                                     // previous pattern fully done
@@ -362,6 +363,7 @@ sparse_kernel(const SparseCall c) {
                     bool resolved = false;
                     const float best =
                         score_dispatch<NBMAX, LAYOUT>(sP, spots, beg, cnt, S, n_theta, pitch, lane, thr_c, s, resolved);
+                    if (c.work) work += (unsigned long long)cnt * (unsigned long long)S;
                     if (!resolved) continue;
                     float q;
                     if (d > 0.0f) q = __fdiv_rn(best, d);
@@ -434,6 +436,7 @@ sparse_kernel(const SparseCall c) {
             __syncthreads();
         }
     }
+    if (c.work && lane == 0 && work) atomicAdd(c.work, work);
 }
 
 template <int NBMAX, int LAYOUT>

@@ -77,7 +77,7 @@ struct Library {
     int4* d_meta = nullptr;        // per template {first spot, spots | shifts << 16, norm bits, 0}
     float* d_norm = nullptr;
     int32_t* d_nshift = nullptr;
-    float* d_radial = nullptr;
+    float* d_radial = nullptr;     // [K][n_rad rounded up to 4] radial profiles at the distinct radii
     float* d_rnorm = nullptr;
     int32_t* d_rt = nullptr;       // r | (t << 16) per spot (BF16 path)
     int32_t* d_radii = nullptr;    // distinct spot radii (sparse kernel rows)
@@ -91,13 +91,6 @@ struct Buffer {
     size_t bytes = 0;
 };
 
-struct PolarTableDev {
-    int32_t* xy = nullptr;
-    uint2* q = nullptr;
-    size_t bytes = 0;
-};
-
-using TableKey = std::tuple<int, int, int, int, double, double, double>;
 
 struct SpectralTables {            // per n_theta: inverse-DFT basis and twiddles
     void* basis = nullptr;         // bf16 [rows][cols]
@@ -124,11 +117,11 @@ struct tm_ctx {
     std::mutex mu;
     std::map<int, std::unique_ptr<Library>> libs;
     int next_id = 0;
-    std::map<TableKey, PolarTableDev> tables;
-    std::map<std::tuple<int, int, double>, float4*> offset_tables;   // per-pattern-centre taps
+    std::map<std::pair<int, double>, longlong2*> rays;   // polar ray steps per (n_theta, dr)
     std::map<std::string, Buffer> ws;
     cudaEvent_t ws_event = nullptr;
     unsigned* d_error = nullptr;   // device error word of the bounded waits
+    unsigned long long* d_work = nullptr;   // sparse multiply-adds executed while profiling
     std::map<int, SpectralTables> spectral;
     std::map<std::string, RadiusMap> radius_maps;
     // CUDA graphs of whole-path calls (TM_INDEX_GRAPH)
@@ -287,7 +280,8 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
         return fail(TM_ERR_INVALID_ARG, "tm_load_library: px_per_unit must be > 0");
     if (d->n_r < 1 || d->n_r > 4096) return fail(TM_ERR_INVALID_ARG, "tm_load_library: n_r=%d", d->n_r);
     if (d->n_theta < 1 || d->n_theta > 1024) return fail(TM_ERR_INVALID_ARG, "tm_load_library: n_theta=%d", d->n_theta);
-    if (!(d->dr > 0.0 && isfinite(d->dr))) return fail(TM_ERR_INVALID_ARG, "tm_load_library: dr must be > 0");
+    if (!(d->dr > 0.0 && d->n_r * d->dr < 1048576.0))
+        return fail(TM_ERR_INVALID_ARG, "tm_load_library: dr must be > 0 with n_r dr < 2^20");
     if (d->flags & ~(uint32_t)(TM_LIB_MIRROR | TM_LIB_UNIT_INTENSITY))
         return fail(TM_ERR_INVALID_ARG, "tm_load_library: unknown flags 0x%x", d->flags);
     const int64_t K0 = d->n_templates;
@@ -439,7 +433,13 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
     std::vector<double>& rnorm = P.rnorm;
     std::vector<int32_t> off32(L->K + 1);
     for (int64_t k = 0; k <= L->K; ++k) off32[k] = (int32_t)L->off[k];
-    std::vector<float> radf(radial.begin(), radial.end()), rnf(rnorm.begin(), rnorm.end());
+    // radial profiles at the library's distinct radii only (zero elsewhere), [K][n_pad]
+    // with n_pad = n_rad rounded up to 4 and zero padding
+    const size_t n_rad = L->radii.size(), n_pad = (n_rad + 3) & ~(size_t)3;
+    std::vector<float> radf(n_pad * (size_t)L->K, 0.0f), rnf(rnorm.begin(), rnorm.end());
+    for (int64_t k = 0; k < L->K; ++k)
+        for (size_t j = 0; j < n_rad; ++j)
+            radf[(size_t)k * n_pad + j] = (float)radial[(size_t)k * L->n_r + L->radii[j]];
     std::vector<int32_t> rt(L->r.size());
     for (size_t i = 0; i < rt.size(); ++i) rt[i] = L->r[i] | (L->t[i] << 16);
     std::vector<int32_t> order(L->K);
@@ -496,27 +496,20 @@ tmgb::SparseLib sparse_view(const Library* L) {
     return v;
 }
 
-// Bilinear taps for the call's geometry, built in double precision and cached.
-int polar_table(tm_ctx* ctx, int H, int W, int n_r, int n_theta, double dr, double cx, double cy,
-                tmgb::PolarTable* out) {
-    TableKey key(H, W, n_r, n_theta, dr, cx, cy);
-    auto it = ctx->tables.find(key);
-    if (it == ctx->tables.end()) {
-        const size_t m = (size_t)n_r * n_theta;
-        std::vector<int32_t> xy(m);
-        std::vector<uint2> q(m);
-        tmgb::build_polar_taps(H, W, n_r, n_theta, dr, cx, cy, xy.data(), q.data());
-        PolarTableDev t;
-        int rc = dev_alloc(ctx, (void**)&t.xy, m * 4, "polar table");
-        if (!rc) rc = dev_alloc(ctx, (void**)&t.q, m * 8, "polar table");
+// Ray steps of the polar grid (fixed point, built in double precision), cached per grid.
+int polar_rays(tm_ctx* ctx, int n_theta, double dr, const longlong2** out) {
+    const auto key = std::make_pair(n_theta, dr);
+    auto it = ctx->rays.find(key);
+    if (it == ctx->rays.end()) {
+        std::vector<longlong2> v(n_theta);
+        tmgb::build_polar_rays(n_theta, dr, v.data());
+        longlong2* d = nullptr;
+        int rc = dev_alloc(ctx, (void**)&d, v.size() * sizeof(longlong2), "polar rays");
         if (rc) return rc;
-        t.bytes = m * 12;
-        TM_CUDA(cudaMemcpy(t.xy, xy.data(), m * 4, cudaMemcpyHostToDevice), "polar table");
-        TM_CUDA(cudaMemcpy(t.q, q.data(), m * 8, cudaMemcpyHostToDevice), "polar table");
-        it = ctx->tables.emplace(key, t).first;
+        TM_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(longlong2), cudaMemcpyHostToDevice), "polar rays");
+        it = ctx->rays.emplace(key, d).first;
     }
-    out->xy = it->second.xy;
-    out->q = it->second.q;
+    *out = it->second;
     return TM_OK;
 }
 
@@ -616,38 +609,12 @@ tmgb::DenseLib dense_view(const Library* L) {
     return v;
 }
 
-// Offsets (r cos theta, r sin theta) of every polar sample, each split as float hi + lo
-// of its double value, for frames with per-pattern centres; cached per grid.
-int offset_table(tm_ctx* ctx, int n_r, int n_theta, double dr, const float4** out) {
-    auto key = std::make_tuple(n_r, n_theta, dr);
-    auto it = ctx->offset_tables.find(key);
-    if (it == ctx->offset_tables.end()) {
-        const size_t m = (size_t)n_r * n_theta;
-        std::vector<float4> v(m);
-        for (int j = 0; j < n_r; ++j) {
-            const double r = j * dr;
-            for (int k = 0; k < n_theta; ++k) {
-                const double th = 2.0 * kPi * k / n_theta;
-                const double dx = r * cos(th), dy = r * sin(th);
-                const float xh = (float)dx, yh = (float)dy;
-                v[(size_t)j * n_theta + k] = make_float4(xh, (float)(dx - (double)xh), yh, (float)(dy - (double)yh));
-            }
-        }
-        float4* d = nullptr;
-        int rc = dev_alloc(ctx, (void**)&d, m * 16, "offset table");
-        if (rc) return rc;
-        TM_CUDA(cudaMemcpy(d, v.data(), m * 16, cudaMemcpyHostToDevice), "offset table");
-        it = ctx->offset_tables.emplace(key, d).first;
-    }
-    *out = it->second;
-    return TM_OK;
-}
-
 int check_params(const tm_index_params* p) {
     if (!p) return fail(TM_ERR_INVALID_ARG, "params is NULL");
     if (!(p->gamma > 0.0 && isfinite(p->gamma))) return fail(TM_ERR_INVALID_ARG, "gamma must be finite and > 0");
     if (!isfinite(p->subtract)) return fail(TM_ERR_INVALID_ARG, "subtract must be finite");
-    if (isinf(p->cx) || isinf(p->cy)) return fail(TM_ERR_INVALID_ARG, "centre must be finite or NaN");
+    if (isinf(p->cx) || isinf(p->cy) || fabs(p->cx) >= 1048576.0 || fabs(p->cy) >= 1048576.0)
+        return fail(TM_ERR_INVALID_ARG, "centre must be NaN or finite with |c| < 2^20");
     if (!(p->prefilter_fraction > 0.0 && p->prefilter_fraction <= 1.0))
         return fail(TM_ERR_INVALID_ARG, "prefilter_fraction must be in (0, 1]");
     if (p->top_n < 1 || p->top_n > TM_MAX_TOPN) return fail(TM_ERR_INVALID_ARG, "top_n must be in [1, %d]", TM_MAX_TOPN);
@@ -655,6 +622,10 @@ int check_params(const tm_index_params* p) {
     if (!(p->threshold >= 0.0 && isfinite(p->threshold)))
         return fail(TM_ERR_INVALID_ARG, "threshold must be finite and >= 0");
     return TM_OK;
+}
+
+tmgb::RadialLib radial_lib(const Library* L) {
+    return tmgb::RadialLib{L->d_radial, L->d_rnorm, L->d_radii, (int32_t)L->radii.size(), (int32_t)L->K};
 }
 
 int keep_count(double f, int64_t K) {
@@ -875,6 +846,8 @@ int tm_create(int device, size_t hbm_budget_bytes, tm_ctx** out) {
     ctx->num_sms = prop.multiProcessorCount;
     TM_CUDA(cudaEventCreateWithFlags(&ctx->ws_event, cudaEventDisableTiming), "tm_create: cudaEventCreate");
     TM_CUDA(cudaMalloc(&ctx->d_error, sizeof(unsigned)), "tm_create: error word");
+    TM_CUDA(cudaMalloc(&ctx->d_work, sizeof(unsigned long long)), "tm_create: work counter");
+    TM_CUDA(cudaMemset(ctx->d_work, 0, sizeof(unsigned long long)), "tm_create: work counter");
     if (const char* f = getenv("TMGB_TUNE_CACHE")) {
         ctx->tune_file = f;
         if (FILE* fh = fopen(f, "r")) {
@@ -902,6 +875,7 @@ int tm_profile_enable(tm_ctx* ctx, int enable) {
     }
     ctx->ev_marks.clear();
     ctx->profiling = enable != 0;
+    TM_CUDA(cudaMemset(ctx->d_work, 0, sizeof(unsigned long long)), "tm_profile_enable: reset");
     return TM_OK;
 }
 
@@ -921,6 +895,10 @@ int tm_profile_read(tm_ctx* ctx, tm_profile* out) {
         ctx->ev_pool.push_back(std::get<2>(m));
     }
     ctx->ev_marks.clear();
+    unsigned long long w = 0;
+    TM_CUDA(cudaMemcpy(&w, ctx->d_work, sizeof w, cudaMemcpyDeviceToHost), "tm_profile_read: work");
+    TM_CUDA(cudaMemset(ctx->d_work, 0, sizeof w), "tm_profile_read: reset");
+    out->sparse_macs = (int64_t)w;
     return TM_OK;
 }
 
@@ -935,13 +913,9 @@ void tm_destroy(tm_ctx* ctx) {
         }
         for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
         for (auto& kv : ctx->libs) free_library(ctx, kv.second.get());
-        for (auto& kv : ctx->tables) {
-            cudaFree(kv.second.xy);
-            cudaFree(kv.second.q);
-        }
+        for (auto& kv : ctx->rays) cudaFree(kv.second);
         for (auto& kv : ctx->ws)
             if (kv.second.p) cudaFree(kv.second.p);
-        for (auto& kv : ctx->offset_tables) cudaFree(kv.second);
         for (auto& kv : ctx->spectral) {
             cudaFree(kv.second.basis);
             cudaFree(kv.second.twiddle);
@@ -952,6 +926,7 @@ void tm_destroy(tm_ctx* ctx) {
             cudaFree(kv.second.keep_row);
         }
         if (ctx->d_error) cudaFree(ctx->d_error);
+        if (ctx->d_work) cudaFree(ctx->d_work);
         for (cudaStream_t hs : ctx->host_streams)
             if (hs) cudaStreamDestroy(hs);
         for (auto& kv : ctx->graphs)
@@ -1074,7 +1049,7 @@ int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* f
     if (rc) return rc;
     if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: bad shape");
     if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: dtype");
-    if (n_r < 1 || n_r > 4096 || n_theta < 1 || n_theta > 4096 || !(dr > 0.0 && isfinite(dr)))
+    if (n_r < 1 || n_r > 4096 || n_theta < 1 || n_theta > 4096 || !(dr > 0.0 && n_r * dr < 1048576.0))
         return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: bad polar grid");
     if (n == 0) return TM_OK;
     if (!frames_dev || !polar_dev) return fail(TM_ERR_INVALID_ARG, "tm_polar_transform: NULL buffer");
@@ -1082,14 +1057,13 @@ int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* f
     DeviceGuard g(ctx->device);
     const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
     const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
-    tmgb::PolarTable tab{};
-    const float4* offs = nullptr;
-    rc = centres_dev ? offset_table(ctx, n_r, n_theta, dr, &offs) : polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
+    const longlong2* rays = nullptr;
+    rc = polar_rays(ctx, n_theta, dr, &rays);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    TM_CUDA(tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                             polar_dev, norm_dev, radial_dev, st, nullptr, (const float2*)centres_dev, offs,
-                             params->pixel_mask, params->threshold),
+    TM_CUDA(tmgb::launch_polar(frames_dev, dtype, n, H, W, rays, cx, cy, params->gamma, params->subtract, n_r, n_theta,
+                               polar_dev, norm_dev, radial_dev, st, nullptr, (const float2*)centres_dev,
+                               params->pixel_mask, params->threshold),
             "tm_polar_transform: launch");
     return TM_OK;
 }
@@ -1109,16 +1083,10 @@ int tm_prefilter(tm_ctx* ctx, int lib_id, const float* radial_dev, int64_t n, do
     float* rn;
     int rc = workspace(ctx, st, "radial_norm", (size_t)n * 4, (void**)&rn);
     if (rc) return rc;
-    float* sc = score_dev;
-    if (!sc) {
-        rc = workspace(ctx, st, "score", (size_t)n * L->K * 4, (void**)&sc);
-        if (rc) return rc;
-    }
-    tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
     TM_CUDA(tmgb::launch_radial_norm(radial_dev, n, L->n_r, rn, st), "tm_prefilter: radial norm");
-    TM_CUDA(tmgb::launch_prefilter_scores(radial_dev, rn, n, L->n_r, rl, sc, st), "tm_prefilter: scores");
     const int keep = keep_count(fraction, L->K);
-    TM_CUDA(tmgb::launch_prefilter_select(sc, n, (int)L->K, keep, mask_dev, st), "tm_prefilter: select");
+    TM_CUDA(tmgb::launch_prefilter(radial_dev, rn, n, L->n_r, radial_lib(L), keep, mask_dev, score_dev, st),
+            "tm_prefilter: scores and selection");
     return TM_OK;
 }
 
@@ -1196,9 +1164,8 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                     n_theta);
     const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
     const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
-    tmgb::PolarTable tab{};
-    const float4* offs = nullptr;
-    rc = centres_dev ? offset_table(ctx, n_r, n_theta, dr, &offs) : polar_table(ctx, H, W, n_r, n_theta, dr, cx, cy, &tab);
+    const longlong2* rays = nullptr;
+    rc = polar_rays(ctx, n_theta, dr, &rays);
     if (rc) return rc;
     const bool pre = params->prefilter_fraction < 1.0;
     const int kc = params->rescore_k;
@@ -1250,12 +1217,11 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     int32_t* list[TM_MAX_LIBS] = {};
     for (int i = 0; i < n_libs; ++i) {
         const std::string s = std::to_string(i);
-        // score/mask: pre-filter scores and keep-mask; on the BF16 path reused afterwards for
-        // the pre-scores and the mask of the candidates to rescore
-        if (pre || bf16) {
-            rc = workspace(ctx, st, "score" + s, (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
-            if (!rc) rc = workspace(ctx, st, "mask" + s, (size_t)chunk * ((libs[i]->K + 31) / 32) * 4, (void**)&mask[i]);
-        }
+        // mask: the pre-filter's keep-mask, on the BF16 path reused afterwards for the mask of
+        // the candidates to rescore; score: the BF16 pre-scores
+        if (bf16) rc = workspace(ctx, st, "score" + s, (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
+        if (!rc && (pre || bf16))
+            rc = workspace(ctx, st, "mask" + s, (size_t)chunk * ((libs[i]->K + 31) / 32) * 4, (void**)&mask[i]);
         if (!rc && pre && bf16) rc = workspace(ctx, st, "list" + s, (size_t)chunk * keep[i] * 4, (void**)&list[i]);
         if (rc) return rc;
     }
@@ -1272,9 +1238,9 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             const void* fr = (const char*)frames_dev + (size_t)c0 * H * W * esz;
             {
                 StageTimer tmr(ctx, TM_STAGE_POLAR, st);
-                TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                                           polar, pnorm, radial, st, rmap.keep_row,
-                                           centres_dev ? (const float2*)centres_dev + c0 : nullptr, offs,
+                TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, rays, cx, cy, params->gamma, params->subtract, n_r,
+                                           n_theta, polar, pnorm, radial, st, rmap.keep_row,
+                                           centres_dev ? (const float2*)centres_dev + c0 : nullptr,
                                            params->pixel_mask, params->threshold),
                         "tm_index_patterns: polar");
             }
@@ -1285,11 +1251,9 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                 ++launches;
                 for (int i = 0; i < n_libs; ++i) {
                     Library* L = libs[i];
-                    tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
-                    TM_CUDA(tmgb::launch_prefilter_scores(radial, rn, m, n_r, rl, score[i], st), "tm_index_patterns: scores");
-                    TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)L->K, keep[i], mask[i], st),
-                            "tm_index_patterns: select");
-                    launches += 2;
+                    TM_CUDA(tmgb::launch_prefilter(radial, rn, m, n_r, radial_lib(L), keep[i], mask[i], nullptr, st),
+                            "tm_index_patterns: pre-filter");
+                    ++launches;
                     if (bf16) {
                         TM_CUDA(tmgb::launch_compact(mask[i], m, (int)L->K, L->d_order, keep[i], list[i], st),
                                 "tm_index_patterns: compact");
@@ -1314,6 +1278,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             c.hits = out_dev + (size_t)c0 * N;
             c.hits_lib_stride = n * N;
             c.top_n = N;
+            c.work = ctx->profiling ? ctx->d_work : nullptr;
             if (bf16) {
                 {
                     StageTimer tmr(ctx, TM_STAGE_DFT, st);
@@ -1551,22 +1516,19 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
     cudaStream_t st = (cudaStream_t)stream;
     void* phat;
     rc = workspace(ctx, st, "phat", (size_t)n * rm.n_rad * n_freq * 4, &phat);
-    float* sc = nullptr;
     float* rn = nullptr;
     uint32_t* mask = nullptr;
     int32_t* list = nullptr;
     if (!rc && fraction < 1.0) {
-        rc = workspace(ctx, st, "score0", (size_t)n * L->K * 4, (void**)&sc);
-        if (!rc) rc = workspace(ctx, st, "radial_norm", (size_t)n * 4, (void**)&rn);
+        rc = workspace(ctx, st, "radial_norm", (size_t)n * 4, (void**)&rn);
         if (!rc) rc = workspace(ctx, st, "mask0", (size_t)n * ((L->K + 31) / 32) * 4, (void**)&mask);
         if (!rc) rc = workspace(ctx, st, "list0", (size_t)n * keep * 4, (void**)&list);
     }
     if (rc) return rc;
     if (fraction < 1.0) {
-        tmgb::RadialLib rl{L->d_radial, L->d_rnorm, (int32_t)L->K};
         TM_CUDA(tmgb::launch_radial_norm(radial_dev, n, n_r, rn, st), "tm_prescore: radial norm");
-        TM_CUDA(tmgb::launch_prefilter_scores(radial_dev, rn, n, n_r, rl, sc, st), "tm_prescore: scores");
-        TM_CUDA(tmgb::launch_prefilter_select(sc, n, (int)L->K, keep, mask, st), "tm_prescore: select");
+        TM_CUDA(tmgb::launch_prefilter(radial_dev, rn, n, n_r, radial_lib(L), keep, mask, nullptr, st),
+                "tm_prescore: pre-filter");
         TM_CUDA(tmgb::launch_compact(mask, n, (int)L->K, L->d_order, keep, list, st), "tm_prescore: compact");
     }
     TM_CUDA(tmgb::launch_dft(polar_dev, norm_dev, n, n_r, n_theta, rm.radii, rm.n_rad, n_freq, spec.twiddle, phat,

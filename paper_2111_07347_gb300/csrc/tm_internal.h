@@ -46,29 +46,28 @@ struct SparseLib {
 };
 
 struct RadialLib {
-    const float* radial;       // [K][n_r]  azimuthal sums of the templates
-    const float* rnorm;        // [K]       |R_T,k|
+    const float* radc;         // [K][n_pad]  azimuthal sums of the templates at the library's radii
+                               //             (n_pad = n_rad rounded up to 4, zero-padded)
+    const float* rnorm;        // [K]         |R_T,k|
+    const int32_t* radii;      // [n_rad]     ascending polar rows (every other row of R_T is 0)
+    int32_t n_rad;
     int32_t K;
 };
 
 // ------------------------------------------------------------------ launchers
-struct PolarTable {            // bilinear taps for one (H, W, n_r, n_theta, dr, cx, cy)
-    const int32_t* xy;         // [n_r * n_theta]  x0 | (y0 << 16) as int16 pairs
-    const uint2* q;            // [n_r * n_theta]  (fx, fy) as 23-bit fixed point, < 2^23
-};
+// Host: the ray steps of the polar grid, (round(dr cos theta_k 2^32), round(dr sin theta_k
+// 2^32)) for k < n_theta, in double precision: row j of ray k lies at (cx, cy) + j (step).
+void build_polar_rays(int n_theta, double dr, longlong2* rays);
 
-// Host: the tap table of PolarTable for centre (cx, cy), in double precision.
-void build_polar_taps(int H, int W, int n_r, int n_theta, double dr, double cx, double cy, int32_t* xy, uint2* q);
-
+// rays [n_theta] from build_polar_rays; (cx, cy) the centre (|c| < 2^30, n_r dr < 2^30).
 // keep_row [n_r] (nullable): rows whose polar values are stored; the norm and the row
-// sums always cover every row.  centres [n] (nullable): per-pattern beam centres, used with
-// offsets [n_r * n_theta] = (r cos, r sin) split into float hi/lo pairs; tab is then unused.
-cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
-                         const PolarTable& tab, double gamma, double subtract, int n_r,
-                         int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st, const uint8_t* keep_row = nullptr,
-                         const float2* centres = nullptr, const float4* offsets = nullptr,
-                         const uint8_t* pixel_mask = nullptr, double threshold = 0.0);
+// sums always cover every row.  centres [n] (nullable): per-pattern beam centres, used
+// instead of (cx, cy).
+cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W, const longlong2* rays, double cx,
+                         double cy, double gamma, double subtract, int n_r, int n_theta, float* polar, float* pnorm,
+                         float* radial, cudaStream_t st, const uint8_t* keep_row = nullptr,
+                         const float2* centres = nullptr, const uint8_t* pixel_mask = nullptr,
+                         double threshold = 0.0);
 
 // Sub-step in-plane angle of the top-N hits (parabola through Q at s - 1, s, s + 1).
 struct RefineLib {
@@ -105,9 +104,11 @@ cudaError_t launch_matrix_mask(const double* sum, int H, int W, double thr_n, in
 cudaError_t launch_radial_norm(const float* radial, int64_t n, int n_r, float* out,
                                cudaStream_t st);
 
-cudaError_t launch_prefilter_scores(const float* radial, const float* radial_norm, int64_t n,
-                                    int n_r, const RadialLib& lib, float* score,
-                                    cudaStream_t st);
+// Scores and selection in one pass: mask [n][ceil(K/32)] of the keep best-correlated
+// templates per pattern; score [n][K] (nullable) receives the scores.
+cudaError_t launch_prefilter(const float* radial, const float* radial_norm, int64_t n, int n_r,
+                             const RadialLib& lib, int keep, uint32_t* mask, float* score,
+                             cudaStream_t st);
 
 cudaError_t launch_prefilter_select(const float* score, int64_t n, int K, int keep,
                                     uint32_t* mask, cudaStream_t st);
@@ -129,6 +130,7 @@ struct SparseCall {
     int64_t hits_lib_stride;            // elements between libraries (>= n * top_n)
     int top_n;
     int threads;                        // block size: 128, 256 or 512 (0 = 256)
+    unsigned long long* work;           // nullable: += multiply-adds executed (per warp, at exit)
 };
 
 // Shared-memory bytes the sparse kernel needs (0 when unsupported), the layout it uses

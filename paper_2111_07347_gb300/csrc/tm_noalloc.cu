@@ -5,13 +5,13 @@
 // must see every allocation), or an acquisition callback in instrument-control software
 // that runs inside a fixed, pre-reserved device budget and must not block on the driver's
 // allocator.  tm_index_patterns grows per-stream scratch buffers on first use; this entry
-// point instead keeps its scratch (bilinear tap table, polar images, image norms and the
+// point instead keeps its scratch (polar ray steps, polar images, image norms and the
 // pattern counter) in one statically sized device array that every GPU which loads the
 // library holds for the life of the process.
 //
 // Limits and rules:
 // * The array holds kScratchBytes (64 MiB); a call whose scratch does not fit (for a
-//   128 x 360 polar grid: about 340 patterns per call) is rejected with
+//   128 x 360 polar grid: about 360 patterns per call) is rejected with
 //   TM_ERR_INVALID_ARG and a message giving the size it needed.
 // * All calls share the one array and it keeps the previous call's contents; the call
 //   rewrites every part it reads (the pattern counter is cleared on the stream first).
@@ -21,8 +21,8 @@
 //   (cudaGetSymbolAddress) with that device current; make that first call before any
 //   stream capture begins.
 // * No cudaMalloc, cudaFree or other allocating call is made, on the device or the host:
-//   the tap table is computed in double precision into a static host staging area (grids
-//   of up to kMaxTaps polar samples) and copied into the array on the caller's stream.
+//   the ray steps of the polar grid are computed in double precision into a static host
+//   staging area and copied into the array on the caller's stream.
 #include <math.h>
 #include <stdio.h>
 
@@ -33,13 +33,11 @@
 namespace {
 
 constexpr size_t kScratchBytes = (size_t)64 << 20;
-constexpr size_t kMaxTaps = (size_t)1 << 20;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;                      // guards the lookups below and the host staging
-int32_t g_host_xy[kMaxTaps];
-uint2 g_host_q[kMaxTaps];
+longlong2 g_host_rays[4096];          // n_theta <= 4096
 void* g_scratch_dev[128] = {};        // device address of g_scratch, per CUDA device
 
 int fail(int code, const char* msg) {
@@ -75,7 +73,7 @@ extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* par
                                          tm_hit* out_dev, void* stream) {
     if (!ctx || !params) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: NULL argument");
     if (!(params->gamma > 0.0 && isfinite(params->gamma)) || !isfinite(params->subtract) || isinf(params->cx) ||
-        isinf(params->cy))
+        isinf(params->cy) || fabs(params->cx) >= 1048576.0 || fabs(params->cy) >= 1048576.0)
         return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: bad gamma, subtract or centre");
     if (params->path != TM_PATH_FP32_SPARSE || params->prefilter_fraction != 1.0)
         return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: only the FP32 sparse path without pre-filter");
@@ -94,12 +92,11 @@ extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* par
     if (!tmgb::sparse_smem_bytes(view.n_rad, n_theta, N))
         return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns_noalloc: polar grid does not fit shared memory");
 
-    // scratch layout: tap positions | tap weights | polar images | image norms | counter
+    // scratch layout: ray steps | polar images | image norms | counter
     const size_t m = (size_t)n_r * n_theta;
-    if (m > kMaxTaps) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: polar grid larger than 2^20 samples");
-    const size_t o_xy = 0;
-    const size_t o_w = align256(o_xy + m * 4);
-    const size_t o_polar = align256(o_w + m * 8);
+    if (n_theta > 4096) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns_noalloc: n_theta > 4096");
+    const size_t o_rays = 0;
+    const size_t o_polar = align256(o_rays + (size_t)n_theta * sizeof(longlong2));
     const size_t o_norm = align256(o_polar + (size_t)n * m * 4);
     const size_t o_count = align256(o_norm + (size_t)n * 4);
     const size_t need = o_count + 256;
@@ -119,25 +116,21 @@ extern "C" int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* par
     rc = scratch_for(device, &scratch);
     cudaStream_t st = (cudaStream_t)stream;
     if (!rc) {
-        // bilinear taps for this geometry, in double precision on the host; the staging is
-        // reused once the copies below have consumed it (a copy from pageable memory
-        // returns after the data has been taken)
+        // ray steps of this grid, in double precision on the host; the staging is reused
+        // once the copy below has consumed it (a copy from pageable memory returns after
+        // the data has been taken)
         std::lock_guard<std::mutex> lk(g_mu);
         const double cx = isnan(params->cx) ? (W - 1) / 2.0 : params->cx;
         const double cy = isnan(params->cy) ? (H - 1) / 2.0 : params->cy;
-        int32_t* xy = g_host_xy;
-        uint2* qv = g_host_q;
-        tmgb::build_polar_taps(H, W, n_r, n_theta, dr, cx, cy, xy, qv);
-        cudaError_t e = cudaMemcpyAsync(scratch + o_xy, xy, m * 4, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_w, qv, m * 8, cudaMemcpyHostToDevice, st);
+        tmgb::build_polar_rays(n_theta, dr, g_host_rays);
+        cudaError_t e = cudaMemcpyAsync(scratch + o_rays, g_host_rays, (size_t)n_theta * sizeof(longlong2),
+                                        cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
-            tmgb::PolarTable tab;
-            tab.xy = (const int32_t*)(scratch + o_xy);
-            tab.q = (const uint2*)(scratch + o_w);
+            const longlong2* rays = (const longlong2*)(scratch + o_rays);
             float* polar = (float*)(scratch + o_polar);
             float* pnorm = (float*)(scratch + o_norm);
-            e = tmgb::launch_polar(frames_dev, dtype, n, H, W, tab, params->gamma, params->subtract, n_r, n_theta,
-                                   polar, pnorm, nullptr, st, nullptr, nullptr, nullptr, params->pixel_mask,
+            e = tmgb::launch_polar(frames_dev, dtype, n, H, W, rays, cx, cy, params->gamma, params->subtract, n_r,
+                                   n_theta, polar, pnorm, nullptr, st, nullptr, nullptr, params->pixel_mask,
                                    params->threshold);
             if (e == cudaSuccess) {
                 tmgb::SparseCall c{};

@@ -92,7 +92,8 @@ STAGES = ["polar", "prefilter", "sparse", "dft", "dense", "rescore", "stage6", "
 
 
 class tm_profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * TM_STAGE_COUNT), ("launches", ctypes.c_int64 * TM_STAGE_COUNT)]
+    _fields_ = [("ms", ctypes.c_double * TM_STAGE_COUNT), ("launches", ctypes.c_int64 * TM_STAGE_COUNT),
+                ("sparse_macs", ctypes.c_int64)]
 
 
 HIT_DTYPE = np.dtype([("template_index", "<i4"), ("shift", "<i4"), ("score", "<f4"),
@@ -341,10 +342,13 @@ def tm_profile_enable(ctx, enable: bool) -> None:
     _check(library().tm_profile_enable(ctx, 1 if enable else 0))
 
 
-def tm_profile_read(ctx) -> dict:
+def tm_profile_read(ctx, counters: bool = False):
+    """Stage totals {stage: (ms, launches)}; with counters=True also the work counters
+    ({"sparse_macs": multiply-adds the FP32 sparse kernel executed})."""
     p = tm_profile()
     _check(library().tm_profile_read(ctx, ctypes.byref(p)))
-    return {STAGES[i]: (p.ms[i], p.launches[i]) for i in range(TM_STAGE_COUNT) if p.launches[i]}
+    stages = {STAGES[i]: (p.ms[i], p.launches[i]) for i in range(TM_STAGE_COUNT) if p.launches[i]}
+    return (stages, {"sparse_macs": int(p.sparse_macs)}) if counters else stages
 
 
 def tm_server_params_default() -> tm_server_params:
@@ -499,8 +503,8 @@ class Context:
     def profile_enable(self, enable=True):
         tm_profile_enable(self.handle, enable)
 
-    def profile_read(self) -> dict:
-        return tm_profile_read(self.handle)
+    def profile_read(self, counters=False):
+        return tm_profile_read(self.handle, counters)
 
     def load_library(self, ts, n_r, n_theta, dr=1.0, mirror=None, unit_intensity=False) -> int:
         return tm_load_library(self.handle, ts, n_r, n_theta, dr, mirror, unit_intensity)

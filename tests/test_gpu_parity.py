@@ -175,6 +175,52 @@ def test_prefilter_parity(ctx, fcc):
     ctx.unload_library(lid)
 
 
+def _topk_mask(score, keep):
+    """The keep largest FP32 scores of each row, ties to the lower index (values ordered as
+    their bit patterns order them, -0 below +0)."""
+    u = np.ascontiguousarray(score, dtype=np.float32).view(np.uint32).astype(np.int64)
+    key = np.where(u & 0x80000000, 0xFFFFFFFF - u, u | 0x80000000)
+    out = np.zeros(score.shape, bool)
+    idx = np.arange(score.shape[1])
+    for p in range(score.shape[0]):
+        out[p, np.lexsort((idx, -key[p]))[:keep]] = True
+    return out
+
+
+def test_prefilter_selection_is_exact(ctx, fcc):
+    """Keeping a template is an integer decision taken on the kernel's own FP32 scores: the
+    mask is the top-keep of those scores, ties to the lower index, bit for bit; also for a
+    blank frame (every score 0) and for a library whose templates all come in equal pairs."""
+    ts, scan, lib = fcc
+    lid = ctx.load_library(ts, 128, 360)
+    K = ctx.library_info(lid)["n_templates"]
+    frames = scan.frames[:40].copy()
+    frames[5] = 0
+    polar, norm, radial = ctx.polar_transform(_t(frames), 128, 360)
+    for f in (0.5, 0.1, 0.97, 1e-4):
+        mask, score = ctx.prefilter(lid, radial, f)
+        sc = _np(score)
+        assert np.all(sc[5] == 0)
+        assert np.array_equal(_unpack(mask, K), _topk_mask(sc, O.keep_count(f, K))), f
+    ctx.unload_library(lid)
+    rt = synth.random_templates(synth.make_rng(4), 77)
+    cnt = np.diff(rt.offsets)
+    twice = np.repeat(np.arange(rt.n_templates), 2)
+    sl = [np.arange(rt.offsets[k], rt.offsets[k + 1]) for k in twice]
+    dup = synth.TemplateSet(offsets=np.concatenate([[0], np.cumsum(cnt[twice])]).astype(np.int64),
+                            a=np.concatenate([rt.a[i] for i in sl]), b=np.concatenate([rt.b[i] for i in sl]),
+                            intensity=np.concatenate([rt.intensity[i] for i in sl]))
+    lid = ctx.load_library(dup, 60, 180)
+    _, tscan, _ = synth.tiny_workload(n_side=4)
+    polar, norm, radial = ctx.polar_transform(_t(tscan.frames), 60, 180)
+    for f in (0.5, 0.3, 0.02):
+        mask, score = ctx.prefilter(lid, radial, f)
+        sc = _np(score)
+        assert np.array_equal(sc[:, 0::2], sc[:, 1::2])
+        assert np.array_equal(_unpack(mask, 2 * rt.n_templates), _topk_mask(sc, O.keep_count(f, 2 * rt.n_templates)))
+    ctx.unload_library(lid)
+
+
 # ------------------------------------------------------------------ whole path
 
 def _hits(ctx, frames, lids, **kw):
@@ -413,7 +459,10 @@ def test_bound_pruning_is_exact(ctx, which, prefilter, subtract):
     lid = ctx.load_library(ts, 128, 360)
     K = ctx.library_info(lid)["n_templates"]
     f = _t(scan.frames)
+    ctx.profile_enable(True)
     hits = tmgb.hits_to_numpy(ctx.index(f, lid, top_n=5, prefilter=prefilter, subtract=subtract))[0]
+    _, counters = ctx.profile_read(counters=True)
+    ctx.profile_enable(False)
     polar, norm, radial = ctx.polar_transform(f, 128, 360, subtract=subtract)
     mask = None
     active = np.ones((48, K), bool)
@@ -426,4 +475,11 @@ def test_bound_pruning_is_exact(ctx, which, prefilter, subtract):
     assert np.array_equal(hits["template_index"], tk)
     assert np.array_equal(hits["shift"], tsh)
     assert np.array_equal(hits["score"], tq)
+    # the executed multiply-adds: at most every surviving template's spots x shifts, and at
+    # least those of the templates in the top-N (they are always scored)
+    exp = ctx.library_export(lid)
+    work_k = np.diff(exp["offsets"]).astype(np.int64) * (360 // exp["order"].astype(np.int64))
+    full = int((active.astype(np.int64) @ work_k).sum())
+    held = int(work_k[tk[tk >= 0]].sum())
+    assert held <= counters["sparse_macs"] <= full, (held, counters["sparse_macs"], full)
     ctx.unload_library(lid)
