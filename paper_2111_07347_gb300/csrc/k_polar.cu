@@ -118,11 +118,12 @@ __device__ __forceinline__ void fixed_weights(uint32_t q, float& f, float& g) {
 
 // Bilinear sample of the gamma-corrected, subtracted frame at (x0 + fx, y0 + fy); the frame
 // has row pitch `pitch` elements; taps outside [0, W) x [0, H) contribute zero.
-template <typename T, int MODE, bool SMEM, bool LUT_ONLY>
+// CHECK = false: the caller knows that all four taps lie inside the frame.
+template <typename T, int MODE, bool SMEM, bool LUT_ONLY, bool CHECK>
 __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int W, int x0, int y0, float fx,
                                           float gx, float fy, float gy, const float* lut, float2 g, float sub,
                                           const uint8_t* pmask) {
-    if ((unsigned)x0 < (unsigned)(W - 1) && (unsigned)y0 < (unsigned)(H - 1)) {
+    if (!CHECK || ((unsigned)x0 < (unsigned)(W - 1) && (unsigned)y0 < (unsigned)(H - 1))) {
         const T* p = frame + y0 * pitch + x0;
         const T a = load_px_masked<SMEM>(p, frame, pmask), b = load_px_masked<SMEM>(p + 1, frame, pmask);
         const T c = load_px_masked<SMEM>(p + pitch, frame, pmask), d = load_px_masked<SMEM>(p + pitch + 1, frame, pmask);
@@ -168,67 +169,76 @@ __device__ __forceinline__ float warp_sum4(const float a[4], int lane) {
 constexpr long long kRound = 1ll << 8;     // half of the last kept fraction bit (2^-24 of a pixel)
 
 // One polar sample at the fixed-point position (X, Y) (32.32, rounding bias included).
-template <typename T, int MODE, bool STAGED, bool LUT_ONLY>
+template <typename T, int MODE, bool STAGED, bool LUT_ONLY, bool CHECK>
 __device__ __forceinline__ float sample_at(const T* frame, int pitch, int H, int W, long long X, long long Y,
                                           const float* lut, float2 g, float sub, const uint8_t* pmask) {
     float fx, gx, fy, gy;
     fixed_weights((uint32_t)X >> 9, fx, gx);
     fixed_weights((uint32_t)Y >> 9, fy, gy);
-    return bilinear<T, MODE, STAGED, LUT_ONLY>(frame, pitch, H, W, (int)(X >> 32), (int)(Y >> 32), fx, gx, fy, gy, lut,
-                                              g, sub, pmask);
+    return bilinear<T, MODE, STAGED, LUT_ONLY, CHECK>(frame, pitch, H, W, (int)(X >> 32), (int)(Y >> 32), fx, gx, fy,
+                                                     gy, lut, g, sub, pmask);
+}
+
+// Whether the four taps of a sample at fixed-point (X, Y) lie inside the frame.
+__device__ __forceinline__ bool taps_inside(long long X, long long Y, int H, int W) {
+    return (unsigned)(int)(X >> 32) < (unsigned)(W - 1) && (unsigned)(int)(Y >> 32) < (unsigned)(H - 1);
 }
 
 constexpr int kMaxThreads = 768;            // 80 registers per thread at one CTA per SM
 
-// The polar rows of one pattern: thread (grp, k0) takes columns k0, k0 + cols, ... of rows
-// grp, grp + R, ..., four rows at a time.  Stores the kept rows, adds P'^2 to the thread's
-// Kahan sum and leaves each row's partial sums per warp in part[row][warp].
-template <typename T, int MODE, bool STAGED, bool LUT_ONLY>
-__device__ __forceinline__ void polar_rows(const T* frame, int pf, int H, int W, long long cxb, long long cyb,
-                                           const longlong2* __restrict__ rays, int n_r, int n_theta, int R,
-                                           int cols, int grp, int k0, int lane, int warp, int nw,
-                                           const uint8_t* __restrict__ keep_row, const uint8_t* pmask,
-                                           const float* lut, float2 g, float sub, float* __restrict__ out,
-                                           float* part, float& s2, float& c2) {
-    const int my_rows = grp < n_r ? (n_r - grp + R - 1) / R : 0;        // rows grp, grp + R, ... (warp-uniform)
-    for (int kk = 0; kk < n_theta; kk += cols) {                        // block-uniform
-        const int k = kk + k0;
-        const bool active = k < n_theta;
-        long long X = cxb, Y = cyb, SX = 0, SY = 0;
+// One column of the thread's rows (batches of four), from the fixed-point position (X, Y) of
+// its first row and the step (SX, SY) between its rows.  keepm: bit i set when the thread's
+// i-th row is stored (rows past 64 read keep_row).  CHECK = false when the whole column lies
+// inside the frame.
+template <typename T, int MODE, bool STAGED, bool LUT_ONLY, bool CHECK>
+__device__ __forceinline__ void polar_column(const T* frame, int pf, int H, int W, long long X, long long Y,
+                                             long long SX, long long SY, int k, bool active, int my_rows, int grp,
+                                             int R, int n_theta, int lane, int warp, int nw, int kk,
+                                             unsigned long long keepm, const uint8_t* __restrict__ keep_row,
+                                             const uint8_t* pmask, const float* lut, float2 g, float sub,
+                                             float* __restrict__ out, float* part, float& s2, float& c2) {
+    for (int b = 0; b < my_rows; b += 4) {                              // warp-uniform
+        const int nu = my_rows - b;                                     // rows left in this batch (>= 1)
+        const int j0 = grp + R * b;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (active) {
-            const longlong2 d = __ldg(rays + k);
-            X += (long long)grp * d.x;
-            Y += (long long)grp * d.y;
-            SX = (long long)R * d.x;
-            SY = (long long)R * d.y;
-        }
-        for (int b = 0; b < my_rows; b += 4) {                          // warp-uniform
-            const int nu = my_rows - b;                                 // rows left in this batch (>= 1)
-            const int j0 = grp + R * b;
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            if (active) {
-                float v[4];
-                if (nu >= 4) {
+            unsigned kb = (unsigned)(keepm >> b) & 15u;                 // rows of the batch that are stored
+            if (b + 4 > 64) {
+                kb = 0u;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        v[u] = sample_at<T, MODE, STAGED, LUT_ONLY>(frame, pf, H, W, X, Y, lut, g, sub, pmask);
-                        X += SX;
-                        Y += SY;
-                    }
-                } else {
+                for (int u = 0; u < 4; ++u)
+                    if (u < nu && (!keep_row || keep_row[j0 + R * u])) kb |= 1u << u;
+            }
+            float v[4];
+            if (nu >= 4) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        v[u] = u < nu ? sample_at<T, MODE, STAGED, LUT_ONLY>(frame, pf, H, W, X, Y, lut, g, sub, pmask)
-                                      : 0.0f;
-                        X += SX;
-                        Y += SY;
-                    }
+                for (int u = 0; u < 4; ++u) {
+                    v[u] = sample_at<T, MODE, STAGED, LUT_ONLY, CHECK>(frame, pf, H, W, X, Y, lut, g, sub, pmask);
+                    X += SX;
+                    Y += SY;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if ((kb >> u) & 1u) out[(size_t)(j0 + R * u) * n_theta + k] = v[u];
+                    const float y = fmaf(v[u], v[u], -c2);
+                    const float t = s2 + y;
+                    c2 = (t - s2) - y;
+                    s2 = t;
+                    acc[u] = v[u];
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    v[u] = u < nu ? sample_at<T, MODE, STAGED, LUT_ONLY, CHECK>(frame, pf, H, W, X, Y, lut, g, sub,
+                                                                               pmask)
+                                  : 0.0f;
+                    X += SX;
+                    Y += SY;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (u < nu) {
-                        const int j = j0 + R * u;
-                        if (!keep_row || keep_row[j]) out[(size_t)j * n_theta + k] = v[u];
+                        if ((kb >> u) & 1u) out[(size_t)(j0 + R * u) * n_theta + k] = v[u];
                         const float y = fmaf(v[u], v[u], -c2);
                         const float t = s2 + y;
                         c2 = (t - s2) - y;
@@ -237,13 +247,50 @@ __device__ __forceinline__ void polar_rows(const T* frame, int pf, int H, int W,
                     }
                 }
             }
-            const float r = warp_sum4(acc, lane);
-            const int u = lane >> 3;
-            if ((lane & 7) == 0 && u < nu) {
-                float* dst = part + (j0 + R * u) * nw + warp;
-                *dst = kk ? *dst + r : r;
-            }
         }
+        const float r = warp_sum4(acc, lane);
+        const int u = lane >> 3;
+        if ((lane & 7) == 0 && u < nu) {
+            float* dst = part + (j0 + R * u) * nw + warp;
+            *dst = kk ? *dst + r : r;
+        }
+    }
+}
+
+// The polar rows of one pattern: thread (grp, k0) takes columns k0, k0 + cols, ... of rows
+// grp, grp + R, ..., four rows at a time.  Stores the kept rows, adds P'^2 to the thread's
+// Kahan sum and leaves each row's partial sums per warp in part[row][warp].
+template <typename T, int MODE, bool STAGED, bool LUT_ONLY>
+__device__ __forceinline__ void polar_rows(const T* frame, int pf, int H, int W, long long cxb, long long cyb,
+                                           const longlong2* __restrict__ rays, int n_r, int n_theta, int R,
+                                           int cols, int grp, int k0, int lane, int warp, int nw,
+                                           unsigned long long keepm, const uint8_t* __restrict__ keep_row,
+                                           const uint8_t* pmask, const float* lut, float2 g, float sub,
+                                           float* __restrict__ out, float* part, float& s2, float& c2) {
+    const int my_rows = grp < n_r ? (n_r - grp + R - 1) / R : 0;        // rows grp, grp + R, ... (warp-uniform)
+    for (int kk = 0; kk < n_theta; kk += cols) {                        // block-uniform
+        const int k = kk + k0;
+        const bool active = k < n_theta;
+        long long X = cxb, Y = cyb, SX = 0, SY = 0;
+        bool inside = true;
+        if (active) {
+            const longlong2 d = __ldg(rays + k);
+            X += (long long)grp * d.x;
+            Y += (long long)grp * d.y;
+            SX = (long long)R * d.x;
+            SY = (long long)R * d.y;
+            // the column is a segment, so its samples are inside when both ends are
+            const long long last = my_rows > 0 ? (long long)(my_rows - 1) : 0;
+            inside = taps_inside(X, Y, H, W) && taps_inside(X + last * SX, Y + last * SY, H, W);
+        }
+        if (__all_sync(0xffffffffu, inside))
+            polar_column<T, MODE, STAGED, LUT_ONLY, false>(frame, pf, H, W, X, Y, SX, SY, k, active, my_rows, grp, R,
+                                                           n_theta, lane, warp, nw, kk, keepm, keep_row, pmask, lut,
+                                                           g, sub, out, part, s2, c2);
+        else
+            polar_column<T, MODE, STAGED, LUT_ONLY, true>(frame, pf, H, W, X, Y, SX, SY, k, active, my_rows, grp, R,
+                                                          n_theta, lane, warp, nw, kk, keepm, keep_row, pmask, lut, g,
+                                                          sub, out, part, s2, c2);
     }
 }
 
@@ -260,6 +307,13 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t fbytes = STAGED ? (size_t)H * pitch * sizeof(T) : 0;
     constexpr bool kHasLut = sizeof(T) == 2;
+    // rows of this thread that are stored (its first 64 rows; later ones read keep_row)
+    unsigned long long keepm = 0ull;
+    if (grp < n_r) {
+        const int my_rows = (n_r - grp + R - 1) / R;
+        for (int i = 0; i < my_rows && i < 64; ++i)
+            if (!keep_row || keep_row[grp + R * i]) keepm |= 1ull << i;
+    }
     T* sF = (T*)smem_raw;
     float* lut = (float*)(smem_raw + ((fbytes + 15) & ~(size_t)15));   // [kLut] for u16 frames
     float* part = lut + (kHasLut ? kLut : 0);                           // [n_r][nw]
@@ -335,10 +389,10 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
         float s2 = 0.0f, c2 = 0.0f;                      // Kahan sum of P'^2 for this thread
         if (kHasLut && STAGED && !big)
             polar_rows<T, MODE, STAGED, true>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, R, cols, grp, k0, lane,
-                                              warp, nw, keep_row, pmask, lut, g, sub, out, part, s2, c2);
+                                              warp, nw, keepm, keep_row, pmask, lut, g, sub, out, part, s2, c2);
         else
             polar_rows<T, MODE, STAGED, false>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, R, cols, grp, k0, lane,
-                                               warp, nw, keep_row, pmask, lut, g, sub, out, part, s2, c2);
+                                               warp, nw, keepm, keep_row, pmask, lut, g, sub, out, part, s2, c2);
         red[threadIdx.x] = s2;
         __syncthreads();
         // fixed-order tree over the block (blockDim is a multiple of 32)

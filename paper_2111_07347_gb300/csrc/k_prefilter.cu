@@ -42,12 +42,13 @@ __device__ __forceinline__ uint32_t order_key(float x) {
 }
 
 constexpr int SEL_THREADS = 512;
-constexpr int SEL_BINS = 256;                              // digits of at most 8 bits
+constexpr int SEL_BINS = 2048;                             // digits of at most 11 bits
+constexpr int SEL_CAND = 256;                              // candidates finished by one warp
 constexpr int MAX_PB = 2;
 
 struct SelShared {
     uint32_t kmin[MAX_PB], kmax[MAX_PB];                    // range of each pattern's keys
-    uint32_t prefix, remaining, done;
+    uint32_t prefix, remaining, bincount, ncand, T, need, neq;
     uint32_t wsum[SEL_THREADS / 32];
 };
 
@@ -64,29 +65,73 @@ __device__ __forceinline__ void range_publish(uint32_t lo, uint32_t hi, uint32_t
     }
 }
 
-// Histogram increment; with `gather`, lanes of a warp that share a bin are first counted
-// together (the first digit of cosine scores puts most keys in a few bins).
-__device__ __forceinline__ void hist_add(uint32_t* hist, bool in, uint32_t bin, bool gather) {
-    const int lane = threadIdx.x & 31;
-    unsigned pending = __ballot_sync(0xffffffffu, in);
-    if (gather) {
-#pragma unroll 1
-        for (int it = 0; it < 3 && pending; ++it) {
-            const int leader = __ffs(pending) - 1;
-            const uint32_t b = __shfl_sync(0xffffffffu, bin, leader);
-            const unsigned m = __ballot_sync(0xffffffffu, ((pending >> lane) & 1u) && bin == b);
-            if (lane == leader) atomicAdd(&hist[b], (uint32_t)__popc(m));
-            pending &= ~m;
+// Warp 0: the bin of hist[0, nb) (nb a power of two <= 2048) where the count taken from the
+// top bin down first reaches rem (>= 1, <= the total).  Level 1: lane l sums its c = nb / 32
+// bins and a suffix scan over lanes finds the lane whose run holds the bin; level 2: the lanes
+// split that run (two bins each, from the top) and a prefix scan finds the bin.  Writes the
+// bin's prefix bits, what is left to take inside it and its count to sh.
+__device__ __forceinline__ void find_bin(const uint32_t* hist, uint32_t nb, uint32_t rem, uint32_t prefix, int shift,
+                                         SelShared& sh, int lane) {
+    const uint32_t c = nb >= 32u ? nb >> 5 : 1u;
+    const uint32_t b0 = (uint32_t)lane * c;
+    uint32_t t = 0u;
+    if (b0 < nb) {
+        if (c >= 4u) {
+            for (uint32_t i = 0; i < c; i += 4) {
+                const uint4 a = *reinterpret_cast<const uint4*>(hist + b0 + i);
+                t += a.x + a.y + a.z + a.w;
+            }
+        } else {
+            for (uint32_t i = 0; i < c; ++i) t += hist[b0 + i];
         }
     }
-    if ((pending >> lane) & 1u) atomicAdd(&hist[bin], 1u);
+    uint32_t sfx = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_down_sync(0xffffffffu, sfx, o);
+        if (lane + o < 32) sfx += v;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, b0 < nb && sfx >= rem && sfx - t < rem);
+    const int L = hit ? __ffs(hit) - 1 : 0;                 // exactly one lane
+    const uint32_t above = __shfl_sync(0xffffffffu, sfx - t, L);
+    // level 2 over bins [L c, L c + c): lane i takes bins top - 2 i and top - 2 i - 1
+    const int top = L * (int)c + (int)c - 1, bot = L * (int)c;
+    const int hi_b = top - 2 * lane, lo_b = hi_b - 1;
+    const uint32_t hh = hi_b >= bot ? hist[hi_b] : 0u;
+    const uint32_t hl = lo_b >= bot ? hist[lo_b] : 0u;
+    const uint32_t q = hh + hl;
+    uint32_t inc = q;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const uint32_t exc = inc - q;
+    if (hi_b >= bot && above + inc >= rem && above + exc < rem) {
+        uint32_t cum = above + exc;
+        int bin = hi_b;
+        uint32_t cnt = hh;
+        if (cum + hh < rem) {
+            cum += hh;
+            bin = lo_b;
+            cnt = hl;
+        }
+        sh.prefix = prefix | ((uint32_t)bin << shift);
+        sh.remaining = rem - cum;
+        sh.bincount = cnt;
+    }
 }
 
 // The `keep` largest of keys[0, K) (ties to the lower index) as bits of mrow[ceil(K/32)].
 // [kmin, kmax] is the keys' range.  Called by the whole block with uniform arguments after a
 // barrier that follows the last write of keys; ends with a barrier.
-__device__ __forceinline__ void select_keep(const uint32_t* keys, int K, int keep, uint32_t kmin, uint32_t kmax, uint32_t* hist,
-                            SelShared& sh, uint32_t* __restrict__ mrow) {
+//   Block-wide histogram passes of up to 11 bits (starting at the highest bit in which the
+//   keys differ) narrow the boundary to one bin; once that bin holds at most SEL_CAND keys
+//   they are gathered and warp 0 finishes bit by bit with ballots over registers.  The
+//   threshold T and the number `need` of keys equal to T that are kept then give the mask.
+__device__ __forceinline__ void select_keep(const uint32_t* keys, int K, int keep, uint32_t kmin, uint32_t kmax,
+                                            uint32_t* hist, uint32_t* cand, SelShared& sh,
+                                            uint32_t* __restrict__ mrow) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int words = (K + 31) >> 5;
     if (keep <= 0 || keep >= K) {
@@ -97,103 +142,130 @@ __device__ __forceinline__ void select_keep(const uint32_t* keys, int K, int kee
         __syncthreads();
         return;
     }
-    uint32_t T, need;
+    uint32_t T, need, neq;                                  // neq: keys equal to T (0: unknown)
     if (kmin == kmax) {
         T = kmin;                                           // all equal: the first `keep` indices
         need = (uint32_t)keep;
+        neq = (uint32_t)K;
     } else {
         const int bits = 32 - __clz(kmin ^ kmax);           // the keys differ in bits [0, bits)
         uint32_t prefix = bits == 32 ? 0u : (kmin >> bits) << bits;
         uint32_t pmask = bits == 32 ? 0u : 0xffffffffu << bits;
         uint32_t rem = (uint32_t)keep;                      // still to take among the candidates
         int left = bits;
-        bool done = false;
-        for (int pass = 0; left > 0; ++pass) {
-            const int d = min(8, left);
+        uint32_t nbin = 0u;
+        for (;;) {
+            const int d = min(11, left);
             const int shift = left - d;
             const uint32_t nb = 1u << d, dm = nb - 1u;
             for (uint32_t i = tid; i < nb; i += blockDim.x) hist[i] = 0u;
             __syncthreads();
-            for (int k0 = warp * 32; k0 < K; k0 += blockDim.x) {      // warp-uniform trip count
-                const int k = k0 + lane;
-                const uint32_t x = k < K ? keys[k] : 0u;
-                hist_add(hist, k < K && (x & pmask) == prefix, (x >> shift) & dm, pass == 0);
+            for (int k = tid; k < K; k += blockDim.x) {
+                const uint32_t x = keys[k];
+                if ((x & pmask) == prefix) atomicAdd(&hist[(x >> shift) & dm], 1u);
             }
             __syncthreads();
-            if (warp == 0) {
-                // lane l holds bins [l c, l c + c) in registers; suffix sums over the lanes
-                // find the bin where the count from the top first reaches rem
-                const uint32_t c = nb >= 32u ? nb >> 5 : 1u;
-                const uint32_t b0 = (uint32_t)lane * c;
-                uint32_t h[8];
-                if (c == 8u) {
-                    const uint4 a = *reinterpret_cast<const uint4*>(hist + b0);
-                    const uint4 e = *reinterpret_cast<const uint4*>(hist + b0 + 4);
-                    h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
-                    h[4] = e.x; h[5] = e.y; h[6] = e.z; h[7] = e.w;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) h[i] = ((uint32_t)i < c && b0 + i < nb) ? hist[b0 + i] : 0u;
-                }
-                uint32_t t = 0u;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) t += h[i];
-                uint32_t sfx = t;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t v = __shfl_down_sync(0xffffffffu, sfx, o);
-                    if (lane + o < 32) sfx += v;
-                }
-                const uint32_t above = sfx - t;
-                if (b0 < nb && sfx >= rem && above < rem) {
-                    uint32_t cum = above, cum_at = above, hb = 0u;
-                    int bi = 0;
-                    bool found = false;
-#pragma unroll
-                    for (int i = 7; i >= 0; --i) {
-                        if (!found && (uint32_t)i < c) {
-                            if (cum + h[i] >= rem) {
-                                found = true;
-                                bi = i;
-                                cum_at = cum;
-                                hb = h[i];
-                            } else {
-                                cum += h[i];
-                            }
-                        }
-                    }
-                    sh.done = cum_at + hb == rem ? 1u : 0u;
-                    sh.prefix = prefix | ((b0 + (uint32_t)bi) << shift);
-                    sh.remaining = rem - cum_at;
-                }
-            }
+            if (warp == 0) find_bin(hist, nb, rem, prefix, shift, sh, lane);
             __syncthreads();
             prefix = sh.prefix;
             rem = sh.remaining;
+            nbin = sh.bincount;
             pmask |= dm << shift;
             left = shift;
-            if (sh.done) { done = true; break; }
+            if (nbin == rem || left == 0 || nbin <= (uint32_t)SEL_CAND) break;
         }
-        // done: every candidate of the last bin is kept, so keep all keys >= the bin's lowest
-        T = prefix;
-        need = done ? 0xffffffffu : rem;
+        if (nbin == rem) {                                  // every key of the bin is kept
+            T = prefix;
+            need = 0xffffffffu;
+            neq = 0u;
+        } else if (left == 0) {                             // the bin is one key value
+            T = prefix;
+            need = rem;
+            neq = nbin;
+        } else {
+            // gather the bin's keys (order does not matter) and finish in warp 0's registers
+            if (tid == 0) sh.ncand = 0u;
+            __syncthreads();
+            for (int k0 = warp * 32; k0 < K; k0 += blockDim.x) {            // warp-uniform trip count
+                const int k = k0 + lane;
+                const uint32_t x = k < K ? keys[k] : 0u;
+                const bool in = k < K && (x & pmask) == prefix;
+                const unsigned b = __ballot_sync(0xffffffffu, in);
+                if (b) {
+                    uint32_t base = 0u;
+                    if (lane == 0) base = atomicAdd(&sh.ncand, (uint32_t)__popc(b));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const uint32_t at = base + __popc(b & ((1u << lane) - 1u));
+                    if (in && at < (uint32_t)SEL_CAND) cand[at] = x;
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t nc = min(sh.ncand, (uint32_t)SEL_CAND);
+                uint32_t r[SEL_CAND / 32];
+                unsigned play = 0u;                         // bit i: r[i] still a candidate
+#pragma unroll
+                for (int i = 0; i < SEL_CAND / 32; ++i) {
+                    const uint32_t idx = (uint32_t)(lane + 32 * i);
+                    r[i] = idx < nc ? cand[idx] : 0u;
+                    if (idx < nc) play |= 1u << i;
+                }
+                uint32_t tv = prefix, rr = rem;
+                for (int bit = left - 1; bit >= 0; --bit) {
+                    unsigned with = 0u;
+                    uint32_t c1 = 0u;
+#pragma unroll
+                    for (int i = 0; i < SEL_CAND / 32; ++i) {
+                        const bool one = ((play >> i) & 1u) && ((r[i] >> bit) & 1u);
+                        if (one) with |= 1u << i;
+                        c1 += __popc(__ballot_sync(0xffffffffu, one));
+                    }
+                    if (c1 >= rr) {
+                        play = with;
+                        tv |= 1u << bit;
+                    } else {
+                        rr -= c1;
+                        play &= ~with;
+                    }
+                }
+                uint32_t ne = 0u;
+#pragma unroll
+                for (int i = 0; i < SEL_CAND / 32; ++i) ne += __popc(__ballot_sync(0xffffffffu, (play >> i) & 1u));
+                if (lane == 0) {
+                    sh.T = tv;
+                    sh.need = rr;
+                    sh.neq = ne;
+                }
+            }
+            __syncthreads();
+            T = sh.T;
+            need = sh.need;
+            neq = sh.neq;
+        }
+    }
+    const int per = (words + nw - 1) / nw;
+    const int w0 = warp * per, w1 = min(words, w0 + per);
+    if (need == 0xffffffffu || (neq != 0u && need >= neq)) {
+        // every key equal to T is kept: kept = key >= T
+        for (int w = w0; w < w1; ++w) {
+            const int k = 32 * w + lane;
+            const uint32_t word = __ballot_sync(0xffffffffu, k < K && keys[k] >= T);
+            if (lane == 0) mrow[w] = word;
+        }
+        __syncthreads();
+        return;
     }
     // kept = key > T, or key == T among the first `need` such keys in index order; each warp
     // writes a contiguous run of words
-    const int per = (words + nw - 1) / nw;
-    const int w0 = warp * per, w1 = min(words, w0 + per);
-    if (need != 0xffffffffu) {
-        uint32_t cnt = 0u;
-        for (int w = w0; w < w1; ++w) {
-            const int k = 32 * w + lane;
-            cnt += __popc(__ballot_sync(0xffffffffu, k < K && keys[k] == T));
-        }
-        if (lane == 0) sh.wsum[warp] = cnt;
-        __syncthreads();
+    uint32_t cnt = 0u;
+    for (int w = w0; w < w1; ++w) {
+        const int k = 32 * w + lane;
+        cnt += __popc(__ballot_sync(0xffffffffu, k < K && keys[k] == T));
     }
+    if (lane == 0) sh.wsum[warp] = cnt;
+    __syncthreads();
     uint32_t before = 0u;
-    if (need != 0xffffffffu)
-        for (int w = 0; w < warp; ++w) before += sh.wsum[w];
+    for (int w = 0; w < warp; ++w) before += sh.wsum[w];
     for (int w = w0; w < w1; ++w) {
         const int k = 32 * w + lane;
         const uint32_t key = k < K ? keys[k] : 0u;
@@ -217,6 +289,7 @@ prefilter_kernel(const float* __restrict__ radial, const float* __restrict__ rpn
                  RadialLib lib, int keep, uint32_t* __restrict__ mask, float* __restrict__ score) {
     extern __shared__ __align__(16) uint32_t keys[];        // rp [PB][n_pad], then keys [PB][K]
     __shared__ __align__(16) uint32_t hist[SEL_BINS];
+    __shared__ uint32_t cand[SEL_CAND];
     __shared__ SelShared sh;
     const int K = lib.K, n_rad = lib.n_rad, n_pad = (n_rad + 3) & ~3, words = (K + 31) >> 5;
     float* rp = (float*)keys;
@@ -273,7 +346,7 @@ prefilter_kernel(const float* __restrict__ radial, const float* __restrict__ rpn
 #pragma unroll 1
         for (int b = 0; b < PB; ++b)
             if (p0 + b < n)
-                select_keep(kb + (size_t)b * K, K, keep, sh.kmin[b], sh.kmax[b], hist, sh,
+                select_keep(kb + (size_t)b * K, K, keep, sh.kmin[b], sh.kmax[b], hist, cand, sh,
                             mask + (size_t)(p0 + b) * words);
     }
 }
@@ -284,6 +357,7 @@ prefilter_select_kernel(const float* __restrict__ score, int64_t n, int K, int k
                         uint32_t* __restrict__ mask) {
     extern __shared__ __align__(16) uint32_t keys[];        // [K]
     __shared__ __align__(16) uint32_t hist[SEL_BINS];
+    __shared__ uint32_t cand[SEL_CAND];
     __shared__ SelShared sh;
     const int words = (K + 31) >> 5;
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
@@ -301,7 +375,7 @@ prefilter_select_kernel(const float* __restrict__ score, int64_t n, int K, int k
         }
         range_publish(lo, hi, &sh.kmin[0], &sh.kmax[0]);
         __syncthreads();
-        select_keep(keys, K, keep, sh.kmin[0], sh.kmax[0], hist, sh, mask + (size_t)p * words);
+        select_keep(keys, K, keep, sh.kmin[0], sh.kmax[0], hist, cand, sh, mask + (size_t)p * words);
     }
 }
 

@@ -332,6 +332,17 @@ sparse_kernel(const SparseCall c) {
                     }
                     ubm_l = ub + (2.0f * (float)cnt_l + 40.0f) * 5.9604645e-8f * __int_as_float(meta_l.w) * pmax;
                 }
+                // drop, all lanes at once, the templates whose bound is already below the
+                // threshold (the threshold only rises, so the test in the loop would drop them
+                // as well); the loop then visits the others only
+                if (prune) {
+                    const float thr0 = fmaxf(qthr, key_score(*(volatile unsigned*)s_thr));
+                    if (thr0 > -INFINITY) {
+                        const float d_l = pn * __int_as_float(meta_l.z);
+                        const float td = thr0 * d_l;
+                        m &= ~__ballot_sync(0xffffffffu, d_l > 0.0f && ubm_l < td - fabsf(td) * 4.8e-7f);
+                    }
+                }
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
