@@ -28,6 +28,7 @@
 //   can enter the warp's top-N, or when per-template results are requested.
 // Results do not depend on scheduling: a template's sum runs over its spots in CSR order
 // and ranking uses the total order (Q desc, template asc).
+#include <cuda_fp16.h>
 #include <float.h>
 #include <limits.h>
 
@@ -80,16 +81,33 @@ __device__ __forceinline__ float key_score(unsigned k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Row (among the library's distinct radii) of a spot word.  Dual and wrap-free layouts hold
-// a float offset row * pitch + column (column < pitch); (off + 1/2) / pitch in float is off by
-// far less than 1/(2 pitch), so its floor is the row exactly.
+// Row (among the library's distinct radii) and column t of a spot word.  Dual and wrap-free
+// words hold the offset row * pitch + column (column < pitch); (off + 1/2) / pitch in float
+// is off by far less than 1/(2 pitch), so its floor is the row exactly.  Dual: rows n_rad..
+// are the copy shifted by one column, which holds the spots of odd t at column t - 1.
 template <int LAYOUT>
-__device__ __forceinline__ int spot_row(int px, float inv_pitch, int n_rad) {
-    if (LAYOUT == TM_LAYOUT_WRAP) return (px >> 11) & 0x1fff;
-    const unsigned off = LAYOUT == TM_LAYOUT_DUAL ? ((unsigned)px & 0xffffu) : ((unsigned)px >> 16);
-    const int r = (int)(((float)off + 0.5f) * inv_pitch);
-    return (LAYOUT == TM_LAYOUT_DUAL && r >= n_rad) ? r - n_rad : r;
+__device__ __forceinline__ void spot_row_col(int px, float inv_pitch, int pitch, int n_rad, int& row, int& t) {
+    if (LAYOUT == TM_LAYOUT_WRAP) {
+        t = px & 0x7ff;
+        row = (px >> 11) & 0x1fff;
+        return;
+    }
+    const int off = LAYOUT == TM_LAYOUT_DUAL ? (int)((unsigned)px & 0xffffu) : (int)((unsigned)px >> 16);
+    const int rr = (int)(((float)off + 0.5f) * inv_pitch);
+    t = off - rr * pitch;
+    row = rr;
+    if (LAYOUT == TM_LAYOUT_DUAL && rr >= n_rad) {
+        row = rr - n_rad;
+        t += 1;
+    }
 }
+
+// Windows of the shift range for the pruning bound: three windows of ww = ceil(Nθ / 3)
+// shifts; a spot at column t visits, over window h, the columns [t + h ww, t + h ww + ww) of
+// its row, which the ncov 32-column chunks from (t + h ww) / 32 on cover.
+__host__ __device__ inline int prune_ww(int n_theta) { return (n_theta + 2) / 3; }
+__host__ __device__ inline int prune_ncov(int n_theta) { return (prune_ww(n_theta) + 31) / 32 + 1; }
+__host__ __device__ inline int prune_nchw(int n_theta) { return ((n_theta - 1 + 2 * prune_ww(n_theta)) >> 5) + 1; }
 
 // ---------------------------------------------------------------- per-layout spot updates
 // acc holds V values per lane (V = 2 NB for the dual layout, NB otherwise); value v of lane L
@@ -246,6 +264,12 @@ sparse_kernel(const SparseCall c) {
     unsigned* s_thr = (unsigned*)(s_pattern + 1);            // [1] best of the warps' N-th scores (key)
     float* s_rmax = (float*)(s_thr + 1);                     // [max_rad] row maxima of P'
     float* s_rabs = s_rmax + c.max_rad;                      // [max_rad] row maxima of |P'|
+    // window maxima for the pruning bound, rounded up: s_cw[row][j] bounds P' over the columns
+    // [32 j, 32 (j + ncov)) (chunk maxima held one per lane, so at most 32 chunks per row)
+    const int ww = prune_ww(n_theta), ncov = prune_ncov(n_theta), nchw = prune_nchw(n_theta);
+    const int nq = nchw + ncov - 1;
+    const bool windows = nq <= 32;
+    __half* s_cw = reinterpret_cast<__half*>(s_rabs + c.max_rad);   // [max_rad][nchw]
     const float inv_pitch = 1.0f / (float)pitch;
     unsigned long long work = 0;                             // multiply-adds of this warp (lane 0)
 
@@ -267,15 +291,39 @@ sparse_kernel(const SparseCall c) {
                 const float* row = src + (size_t)__ldg(L.radii + r0) * n_theta;
                 float* dst = sP + (size_t)rr * pitch;
                 float mx = -INFINITY, ma = 0.0f;
-                for (int col = lane; col < pitch; col += 32) {
+                // copy-0 rows also take the maxima of the 32-column chunks q < nq of
+                // P'[c mod Nθ] (lane q keeps chunk q); warp-uniform trip count
+                const bool first = rr < L.n_rad;
+                const bool chunks = first && windows;
+                const int ncol = chunks ? max(pitch, 32 * nq) : pitch;
+                float mq = -INFINITY;
+                for (int c0 = 0; c0 < ncol; c0 += 32) {
+                    const int col = c0 + lane;
                     int sc = col + sh;
                     while (sc >= n_theta) sc -= n_theta;
-                    const float v = __ldg(row + sc);
-                    dst[col] = v;
-                    mx = fmaxf(mx, v);
-                    ma = fmaxf(ma, fabsf(v));
+                    const bool valid = col < pitch || chunks;
+                    const float v = valid ? __ldg(row + sc) : -INFINITY;
+                    if (col < pitch) dst[col] = v;
+                    if (valid) {
+                        mx = fmaxf(mx, v);
+                        ma = fmaxf(ma, fabsf(v));
+                    }
+                    if (chunks) {
+                        float m = v;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                        if (lane == (c0 >> 5)) mq = m;
+                    }
                 }
-                if (rr < L.n_rad) {
+                if (chunks) {
+                    float w = -INFINITY;
+                    for (int i = 0; i < ncov; ++i) {
+                        const float o = __shfl_sync(0xffffffffu, mq, (lane + i) & 31);
+                        if (lane + i < nq) w = fmaxf(w, o);
+                    }
+                    if (lane < nchw) s_cw[rr * nchw + lane] = __float2half_ru(w);
+                }
+                if (first) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -319,17 +367,30 @@ sparse_kernel(const SparseCall c) {
                     qo[kl] = -INFINITY;
                     so[kl] = -1;
                 }
-                // exact pruning (intensities >= 0): each lane bounds its template's best correlation,
-                // C(s) <= ub = sum_i I_i max_c P'[r_i][c], plus a margin for the rounding of both
-                // sums (2^-24 per operation; sum_i |I_i P'| <= isum * pmax)
+                // exact pruning (intensities >= 0): each lane bounds its template's best correlation
+                // over each of three windows of shifts, C(s) <= sum_i I_i max P'[r_i][visited
+                // columns] (the window maxima are rounded up), or with windows too wide for the
+                // chunk table over the whole row; plus a margin for the rounding of both sums
+                // (2^-24 per operation; sum_i |I_i P'| <= isum * pmax)
                 float ubm_l = INFINITY;
                 if (prune && lane < rem && ((m >> lane) & 1u)) {
                     const int cnt_l = meta_l.y & 0xffff;
-                    float ub = 0.0f;
+                    float ub = 0.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
                     for (int i = 0; i < cnt_l; ++i) {
                         const int2 w = __ldg(spots + meta_l.x + i);
-                        ub = fmaf(__int_as_float(w.y), s_rmax[spot_row<LAYOUT>(w.x, inv_pitch, L.n_rad)], ub);
+                        const float I = __int_as_float(w.y);
+                        int row, t;
+                        spot_row_col<LAYOUT>(w.x, inv_pitch, pitch, L.n_rad, row, t);
+                        if (windows) {
+                            const __half* cr = s_cw + row * nchw;
+                            u0 = fmaf(I, __half2float(cr[t >> 5]), u0);
+                            u1 = fmaf(I, __half2float(cr[(t + ww) >> 5]), u1);
+                            u2 = fmaf(I, __half2float(cr[(t + 2 * ww) >> 5]), u2);
+                        } else {
+                            ub = fmaf(I, s_rmax[row], ub);
+                        }
                     }
+                    if (windows) ub = fmaxf(fmaxf(u0, u1), u2);
                     ubm_l = ub + (2.0f * (float)cnt_l + 40.0f) * 5.9604645e-8f * __int_as_float(meta_l.w) * pmax;
                 }
                 // drop, all lanes at once, the templates whose bound is already below the
@@ -485,7 +546,8 @@ size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout, int* 
         const size_t rows = (size_t)sparse_rows(max_rad, order[i]);
         // per-spot offsets of the dual and wrap-free layouts are 16-bit
         if (order[i] != TM_LAYOUT_WRAP && rows * pch > 65535) continue;
-        const size_t b = rows * pch * 4 + lists;
+        const size_t windows = (size_t)max_rad * prune_nchw(n_theta) * 2;   // half [max_rad][nchw]
+        const size_t b = rows * pch * 4 + lists + windows;
         if (b <= limit[i]) {
             if (layout) *layout = order[i];
             if (pitch) *pitch = pch;

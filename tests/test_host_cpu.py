@@ -205,3 +205,26 @@ def test_sparse_layout_reads_stay_in_bounds(lib, which):
                         assert row[i] * pitch + col.max() < rows * pitch
                         # column c of a row holds P'[c mod n_theta]
                         assert np.array_equal(col % n_theta, (t[i] + 32 * b + lanes) % n_theta)
+        # pruning windows: the spot word decodes (FP32 row division, as in the kernel) to the
+        # spot's row and column; the window maxima cw[row][j], j = (t + h ww) / 32 for the
+        # three windows h, lie inside [n_rad][nchw] and their ncov chunks cover the window
+        ww = (n_theta + 2) // 3
+        ncov = (ww + 31) // 32 + 1
+        nchw = ((n_theta - 1 + 2 * ww) >> 5) + 1
+        inv = np.float32(1.0) / np.float32(pitch)
+        for i in range(len(word)):
+            if layout == "wrap":
+                r_dec, t_dec = row[i], t[i]
+            else:
+                off = off_d[i] if layout == "dual" else off_w[i]
+                rr = int((np.float32(off) + np.float32(0.5)) * inv)
+                r_dec, t_dec = rr, off - rr * pitch
+                if layout == "dual" and rr >= n_rad:
+                    r_dec, t_dec = rr - n_rad, t_dec + 1
+            assert r_dec == row[i] and t_dec == t[i], (layout, i)
+            for hw in range(3):
+                s0 = t_dec + hw * ww
+                j = s0 >> 5
+                assert 0 <= j < nchw and r_dec * nchw + j < n_rad * nchw, (layout, i, hw)
+                assert 32 * j <= s0 and s0 + ww <= 32 * (j + ncov)
+        assert 3 * ww >= n_theta
