@@ -202,20 +202,34 @@ __device__ __forceinline__ void select_keep(const uint32_t* keys, int K, int kee
             __syncthreads();
             if (warp == 0) {
                 const uint32_t nc = min(sh.ncand, (uint32_t)SEL_CAND);
+                const int slots = (int)((nc + 31u) >> 5);   // registers in use per lane
                 uint32_t r[SEL_CAND / 32];
                 unsigned play = 0u;                         // bit i: r[i] still a candidate
+                uint32_t vor = 0u, vand = 0xffffffffu;
 #pragma unroll
                 for (int i = 0; i < SEL_CAND / 32; ++i) {
                     const uint32_t idx = (uint32_t)(lane + 32 * i);
                     r[i] = idx < nc ? cand[idx] : 0u;
-                    if (idx < nc) play |= 1u << i;
+                    if (idx < nc) {
+                        play |= 1u << i;
+                        vor |= r[i];
+                        vand &= r[i];
+                    }
                 }
-                uint32_t tv = prefix, rr = rem;
-                for (int bit = left - 1; bit >= 0; --bit) {
+                // bits in which every candidate agrees are taken as they are; the others are
+                // decided from the highest down, keeping the side that holds the rem-th key
+                vor = __reduce_or_sync(0xffffffffu, vor);
+                vand = __reduce_and_sync(0xffffffffu, vand);
+                const uint32_t low = (1u << left) - 1u;     // left <= 31 here
+                const uint32_t diff = (vor ^ vand) & low;
+                uint32_t tv = prefix | (vand & low & ~(diff ? (2u << (31 - __clz(diff))) - 1u : 0u));
+                uint32_t rr = rem;
+                for (int bit = diff ? 31 - __clz(diff) : -1; bit >= 0; --bit) {
                     unsigned with = 0u;
                     uint32_t c1 = 0u;
 #pragma unroll
                     for (int i = 0; i < SEL_CAND / 32; ++i) {
+                        if (i >= slots) break;
                         const bool one = ((play >> i) & 1u) && ((r[i] >> bit) & 1u);
                         if (one) with |= 1u << i;
                         c1 += __popc(__ballot_sync(0xffffffffu, one));
@@ -230,7 +244,10 @@ __device__ __forceinline__ void select_keep(const uint32_t* keys, int K, int kee
                 }
                 uint32_t ne = 0u;
 #pragma unroll
-                for (int i = 0; i < SEL_CAND / 32; ++i) ne += __popc(__ballot_sync(0xffffffffu, (play >> i) & 1u));
+                for (int i = 0; i < SEL_CAND / 32; ++i) {
+                    if (i >= slots) break;
+                    ne += __popc(__ballot_sync(0xffffffffu, (play >> i) & 1u));
+                }
                 if (lane == 0) {
                     sh.T = tv;
                     sh.need = rr;

@@ -102,13 +102,6 @@ __device__ __forceinline__ void spot_row_col(int px, float inv_pitch, int pitch,
     }
 }
 
-// Windows of the shift range for the pruning bound: three windows of ww = ceil(Nθ / 3)
-// shifts; a spot at column t visits, over window h, the columns [t + h ww, t + h ww + ww) of
-// its row, which the ncov 32-column chunks from (t + h ww) / 32 on cover.
-__host__ __device__ inline int prune_ww(int n_theta) { return (n_theta + 2) / 3; }
-__host__ __device__ inline int prune_ncov(int n_theta) { return (prune_ww(n_theta) + 31) / 32 + 1; }
-__host__ __device__ inline int prune_nchw(int n_theta) { return ((n_theta - 1 + 2 * prune_ww(n_theta)) >> 5) + 1; }
-
 // ---------------------------------------------------------------- per-layout spot updates
 // acc holds V values per lane (V = 2 NB for the dual layout, NB otherwise); value v of lane L
 // is shift shift_of(v, L).  FIRST initialises instead of accumulating.
@@ -266,9 +259,8 @@ sparse_kernel(const SparseCall c) {
     float* s_rabs = s_rmax + c.max_rad;                      // [max_rad] row maxima of |P'|
     // window maxima for the pruning bound, rounded up: s_cw[row][j] bounds P' over the columns
     // [32 j, 32 (j + ncov)) (chunk maxima held one per lane, so at most 32 chunks per row)
-    const int ww = prune_ww(n_theta), ncov = prune_ncov(n_theta), nchw = prune_nchw(n_theta);
+    const int ncov = prune_ncov(n_theta), nchw = prune_nchw(n_theta);
     const int nq = nchw + ncov - 1;
-    const bool windows = nq <= 32;
     __half* s_cw = reinterpret_cast<__half*>(s_rabs + c.max_rad);   // [max_rad][nchw]
     const float inv_pitch = 1.0f / (float)pitch;
     unsigned long long work = 0;                             // multiply-adds of this warp (lane 0)
@@ -283,6 +275,7 @@ sparse_kernel(const SparseCall c) {
         const float pn = __ldg(c.pnorm + p);
         for (int li = 0; li < c.n_libs; ++li) {
             const SparseLib L = c.lib[li];
+            const bool windows = L.bspot != nullptr;         // window bounds (else whole-row bounds)
             // the library's polar rows (dual layout: a second copy shifted by one column)
             const int rows = (LAYOUT == TM_LAYOUT_DUAL ? 2 : 1) * L.n_rad;
             for (int rr = warp; rr < rows; rr += kWarps) {
@@ -294,7 +287,7 @@ sparse_kernel(const SparseCall c) {
                 // copy-0 rows also take the maxima of the 32-column chunks q < nq of
                 // P'[c mod Nθ] (lane q keeps chunk q); warp-uniform trip count
                 const bool first = rr < L.n_rad;
-                const bool chunks = first && windows;
+                const bool chunks = first && windows;        // (windows imply nq <= 32)
                 const int ncol = chunks ? max(pitch, 32 * nq) : pitch;
                 float mq = -INFINITY;
                 for (int c0 = 0; c0 < ncol; c0 += 32) {
@@ -376,21 +369,25 @@ sparse_kernel(const SparseCall c) {
                 if (prune && lane < rem && ((m >> lane) & 1u)) {
                     const int cnt_l = meta_l.y & 0xffff;
                     float ub = 0.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
-                    for (int i = 0; i < cnt_l; ++i) {
-                        const int2 w = __ldg(spots + meta_l.x + i);
-                        const float I = __int_as_float(w.y);
-                        int row, t;
-                        spot_row_col<LAYOUT>(w.x, inv_pitch, pitch, L.n_rad, row, t);
-                        if (windows) {
-                            const __half* cr = s_cw + row * nchw;
-                            u0 = fmaf(I, __half2float(cr[t >> 5]), u0);
-                            u1 = fmaf(I, __half2float(cr[(t + ww) >> 5]), u1);
-                            u2 = fmaf(I, __half2float(cr[(t + 2 * ww) >> 5]), u2);
-                        } else {
-                            ub = fmaf(I, s_rmax[row], ub);
+                    if (windows) {
+                        // per spot: its intensity and the table entries of its three windows
+                        for (int i = 0; i < cnt_l; ++i) {
+                            const int2 w = __ldg(L.bspot + meta_l.x + i);
+                            const float I = __int_as_float(w.x);
+                            const int j0 = w.y & 0xffff;
+                            u0 = fmaf(I, __half2float(s_cw[j0]), u0);
+                            u1 = fmaf(I, __half2float(s_cw[j0 + ((w.y >> 16) & 0xff)]), u1);
+                            u2 = fmaf(I, __half2float(s_cw[j0 + (int)((unsigned)w.y >> 24)]), u2);
+                        }
+                        ub = fmaxf(fmaxf(u0, u1), u2);
+                    } else {
+                        for (int i = 0; i < cnt_l; ++i) {
+                            const int2 w = __ldg(spots + meta_l.x + i);
+                            int row, t;
+                            spot_row_col<LAYOUT>(w.x, inv_pitch, pitch, L.n_rad, row, t);
+                            ub = fmaf(__int_as_float(w.y), s_rmax[row], ub);
                         }
                     }
-                    if (windows) ub = fmaxf(fmaxf(u0, u1), u2);
                     ubm_l = ub + (2.0f * (float)cnt_l + 40.0f) * 5.9604645e-8f * __int_as_float(meta_l.w) * pmax;
                 }
                 // drop, all lanes at once, the templates whose bound is already below the

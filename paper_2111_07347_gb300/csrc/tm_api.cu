@@ -74,6 +74,7 @@ struct Library {
     int32_t* d_off = nullptr;
     int2* d_spot = nullptr;
     int2* d_spot2 = nullptr;       // per-spot offsets in the dual / wrap-free layouts
+    int2* d_bspot = nullptr;       // per-spot pruning-window entries (null: none)
     int4* d_meta = nullptr;        // per template {first spot, spots | shifts << 16, norm bits, 0}
     float* d_norm = nullptr;
     int32_t* d_nshift = nullptr;
@@ -263,7 +264,7 @@ int rotational_order(const Merged& m, int n_theta) {
 
 // Host half of library loading: validation, rounding, merging, mirrors, norms, orders.
 struct Prepared {
-    std::vector<int2> spot, spot2;
+    std::vector<int2> spot, spot2, bspot;
     std::vector<int4> meta;
     std::vector<int32_t> nshift;
     std::vector<double> radial, rnorm;
@@ -405,6 +406,27 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
         P->spot2[i].x = (int32_t)(uint32_t)(od | (ow << 16));
         P->spot2[i].y = spot[i].y;
     }
+    // per spot, the sparse kernel's window-table entries for its pruning bound: row * nchw +
+    // (t + h ww) / 32 for h = 0, 1, 2, as the first (16 bits) and two increments (8 bits each);
+    // none when the table does not fit (the kernel then bounds by whole rows)
+    {
+        const int ww = tmgb::prune_ww(n_theta), nchw = tmgb::prune_nchw(n_theta);
+        const bool win = nchw + tmgb::prune_ncov(n_theta) - 1 <= 32 && (int64_t)n_rows * nchw <= 65536 &&
+                         (2 * ww) / 32 + 1 <= 255;
+        if (win) {
+            P->bspot.resize(ns);
+            for (int64_t i = 0; i < ns; ++i) {
+                const int64_t row = row_of[L->r[i]], t = L->t[i];
+                const int64_t j0 = row * nchw + (t >> 5);
+                const int64_t d1 = ((t + ww) >> 5) - (t >> 5), d2 = ((t + 2 * ww) >> 5) - (t >> 5);
+                if (j0 > 65535 || d1 < 0 || d2 < d1 || d2 > 255 || j0 + d2 >= (int64_t)n_rows * nchw)
+                    return fail(TM_ERR_INVALID_ARG, "tm_load_library: internal window-table check failed for spot %lld",
+                                (long long)i);
+                P->bspot[i].x = spot[i].y;
+                P->bspot[i].y = (int32_t)(uint32_t)(j0 | (d1 << 16) | (d2 << 24));
+            }
+        }
+    }
     P->meta.resize(L->K);
     for (int64_t k = 0; k < L->K; ++k) {
         const int64_t cnt = L->off[k + 1] - L->off[k];
@@ -467,12 +489,19 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
         L->bytes += u.bytes ? u.bytes : 16;
         if (u.bytes) TM_CUDA(cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice), u.what);
     }
+    if (!P.bspot.empty()) {                        // absent (null) when the window table does not fit
+        const size_t b = P.bspot.size() * 8;
+        rc = dev_alloc(ctx, (void**)&L->d_bspot, b, "library spot bound entries");
+        if (rc) return rc;
+        L->bytes += b;
+        TM_CUDA(cudaMemcpy(L->d_bspot, P.bspot.data(), b, cudaMemcpyHostToDevice), "library spot bound entries");
+    }
     return TM_OK;
 }
 
 void free_library(tm_ctx* ctx, Library* L) {
     void* ps[] = {L->d_off,    L->d_spot, L->d_spot2, L->d_meta, L->d_norm, L->d_nshift,
-                  L->d_radial, L->d_rnorm, L->d_rt, L->d_order, L->d_radii};
+                  L->d_radial, L->d_rnorm, L->d_rt, L->d_order, L->d_radii, L->d_bspot};
     for (void* p : ps)
         if (p) cudaFree(p);
     ctx->used -= std::min(ctx->used, L->bytes);
@@ -483,6 +512,7 @@ tmgb::SparseLib sparse_view(const Library* L) {
     v.off = L->d_off;
     v.spot = L->d_spot;
     v.spot2 = L->d_spot2;
+    v.bspot = L->d_bspot;
     v.meta = L->d_meta;
     v.norm = L->d_norm;
     v.nshift = L->d_nshift;

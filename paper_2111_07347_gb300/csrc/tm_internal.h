@@ -43,7 +43,17 @@ struct SparseLib {
     int32_t mirror;
     int32_t words;             // ceil(K / 32)
     int32_t nonneg;            // every intensity >= 0 (the sparse kernel may then prune by bounds)
+    const int2* bspot;         // [n_spots] {intensity, window-table entries} or null (no window bounds)
 };
+
+// Windows of the shift range for the sparse kernel's pruning bound: three windows of
+// ww = ceil(Nθ / 3) shifts; a spot at column t visits, over window h, the columns
+// [t + h ww, t + h ww + ww) of its row, which the ncov 32-column chunks from chunk
+// (t + h ww) / 32 on cover.  The kernel keeps, per library row, the maxima over the windows
+// starting in each of the nchw chunks; one lane holds one chunk, so nchw + ncov - 1 <= 32.
+__host__ __device__ inline int prune_ww(int n_theta) { return (n_theta + 2) / 3; }
+__host__ __device__ inline int prune_ncov(int n_theta) { return (prune_ww(n_theta) + 31) / 32 + 1; }
+__host__ __device__ inline int prune_nchw(int n_theta) { return ((n_theta - 1 + 2 * prune_ww(n_theta)) >> 5) + 1; }
 
 struct RadialLib {
     const float* radc;         // [K][n_pad]  azimuthal sums of the templates at the library's radii
