@@ -424,7 +424,7 @@ cudaError_t launch_dense(const DenseCall& c, int num_sms, cudaStream_t st) {
     if (c.n <= 0) return cudaSuccess;
     const size_t smem = dense_smem_bytes(c.n_theta, c.n_r, c.n_rad, c.n_freq);
     if (smem > 232448) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = kernel_occupancy((const void*)dense_kernel, kThreads, smem, nullptr);
     if (e != cudaSuccess) return e;
     int64_t grid = num_sms;
     if (grid > c.n) grid = c.n;

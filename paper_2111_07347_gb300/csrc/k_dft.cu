@@ -104,10 +104,9 @@ cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_
     if (n <= 0) return cudaSuccess;
     const size_t smem = (size_t)n_rad * n_theta * 4 + (size_t)n_theta * 8;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_kernel, 256, smem);
+    const cudaError_t e = kernel_occupancy((const void*)dft_kernel, 256, smem, &per_sm);
+    if (e != cudaSuccess) return e;
     int64_t grid = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
     if (grid > n) grid = n;
     dft_kernel<<<(int)grid, 256, smem, st>>>(polar, pnorm, n, n_r, n_theta, radii, n_rad, n_freq, twiddle,

@@ -422,13 +422,10 @@ cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, cons
                        const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm, float* radial,
                        const float2* centres, cudaStream_t st) {
     auto kern = polar_kernel<T, MODE, STAGED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 1;
+    const cudaError_t e = kernel_occupancy((const void*)kern, threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    int per_sm = 1, dev = 0, sms = 148;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    int64_t grid = (int64_t)device_sms() * (per_sm > 0 ? per_sm : 1);
     if (grid > n) grid = n;
     kern<<<(int)grid, threads, smem, st>>>(frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, keep_row,
                                            pmask, polar, pnorm, radial, centres);

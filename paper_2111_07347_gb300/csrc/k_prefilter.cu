@@ -396,10 +396,7 @@ prefilter_select_kernel(const float* __restrict__ score, int64_t n, int K, int k
     }
 }
 
-cudaError_t allow_smem(const void* fn, size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+cudaError_t allow_smem(const void* fn, size_t smem) { return kernel_occupancy(fn, SEL_THREADS, smem, nullptr); }
 
 constexpr size_t kSelSmemMax = 200 * 1024;                  // dynamic part, beside hist and sh
 

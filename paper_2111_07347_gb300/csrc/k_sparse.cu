@@ -511,11 +511,8 @@ sparse_kernel(const SparseCall c) {
 template <int NBMAX, int LAYOUT>
 cudaError_t launch_nb(const SparseCall& c, int num_sms, size_t smem, cudaStream_t st) {
     const int threads = (c.threads == 128 || c.threads == 512) ? c.threads : 256;
-    cudaError_t e = cudaFuncSetAttribute(sparse_kernel<NBMAX, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<NBMAX, LAYOUT>, threads, smem);
+    cudaError_t e = kernel_occupancy((const void*)sparse_kernel<NBMAX, LAYOUT>, threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)num_sms * per_sm;

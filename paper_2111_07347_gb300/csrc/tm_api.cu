@@ -109,6 +109,50 @@ struct RadiusMap {                 // per set of libraries: union of radii
 
 namespace tmgb {
 void set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+std::mutex g_launch_mu;
+std::map<std::tuple<const void*, int, int, size_t>, int> g_occupancy;   // (fn, device, threads, smem)
+std::map<std::pair<const void*, int>, size_t> g_smem_limit;              // (fn, device) -> limit set
+std::map<int, int> g_sms;
+}  // namespace
+
+cudaError_t kernel_occupancy(const void* fn, int threads, size_t smem, int* per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    size_t& lim = g_smem_limit[std::make_pair(fn, dev)];
+    if (smem > 48 * 1024 && smem > lim) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        lim = smem;
+    }
+    if (!per_sm) return cudaSuccess;
+    const auto key = std::make_tuple(fn, dev, threads, smem);
+    auto it = g_occupancy.find(key);
+    if (it == g_occupancy.end()) {
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem);
+        if (e != cudaSuccess) return e;
+        it = g_occupancy.emplace(key, b).first;
+    }
+    *per_sm = it->second;
+    return cudaSuccess;
+}
+
+int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = g_sms.find(dev);
+    if (it == g_sms.end()) {
+        int sms = 1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+        it = g_sms.emplace(dev, sms).first;
+    }
+    return it->second;
+}
 }  // namespace tmgb
 
 struct tm_ctx {

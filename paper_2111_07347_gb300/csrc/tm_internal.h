@@ -64,6 +64,14 @@ struct RadialLib {
     int32_t K;
 };
 
+// ------------------------------------------------------------------ launch configuration
+// Raises fn's dynamic shared-memory limit to smem (once per kernel, device and size) and
+// returns its resident blocks per SM for `threads` threads (per_sm may be null).  Cached, so
+// repeated launches make no driver queries.
+cudaError_t kernel_occupancy(const void* fn, int threads, size_t smem, int* per_sm);
+// Number of SMs of the current device (cached).
+int device_sms();
+
 // ------------------------------------------------------------------ launchers
 // Host: the ray steps of the polar grid, (round(dr cos theta_k 2^32), round(dr sin theta_k
 // 2^32)) for k < n_theta, in double precision: row j of ray k lies at (cx, cy) + j (step).
