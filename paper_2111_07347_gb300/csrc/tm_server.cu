@@ -5,9 +5,12 @@
 // frames and its hits.  Requests are split into tiles; whenever a slot is free the worker
 // takes the next tile of the highest-priority request that still has tiles (ties: the
 // earlier submission), copies its frames to the device, runs tm_index_patterns on the
-// slot's stream and copies the hits back into the request's output, then records an
-// event.  Finished slots are detected by polling their events, so tiles of different
-// requests overlap on the device (copies of one tile with the kernels of another).
+// slot's stream and copies the hits into the slot's pinned host staging, then records an
+// event.  Finished slots are detected by polling their events; the worker then copies the
+// staged hits into the request's output (which may be pageable memory: a device-to-host
+// copy into pageable memory would block the worker until the slot's kernels finish).  So
+// tiles of different requests overlap on the device (copies of one tile with the kernels
+// of another); frames in pinned memory are copied asynchronously as well.
 // Admission: the frame bytes of requests submitted and not finished stay within
 // queue_bytes.  Every wait is bounded by the caller's timeout.
 #include <stdio.h>
@@ -43,6 +46,7 @@ struct Slot {
     cudaEvent_t done = nullptr;
     void* frames = nullptr;      // device staging
     tm_hit* hits = nullptr;      // device [max_libs][tile][max_top_n]
+    tm_hit* hits_host = nullptr; // pinned host staging of the same
     std::shared_ptr<Request> req;
     int64_t p0 = 0, m = 0;
     bool busy = false;
@@ -107,6 +111,12 @@ void worker_main(tm_server* s) {
             if (q == cudaErrorNotReady) { any_busy = true; continue; }
             auto r = sl.req;
             if (q != cudaSuccess && r->status == TM_OK) r->status = TM_ERR_CUDA;
+            if (r->status == TM_OK) {
+                const int N = r->req.params.top_n, L = r->req.n_libs;
+                for (int li = 0; li < L; ++li)
+                    memcpy(r->req.out_host + ((size_t)li * r->req.n + sl.p0) * N, sl.hits_host + (size_t)li * sl.m * N,
+                           (size_t)sl.m * N * sizeof(tm_hit));
+            }
             sl.busy = false;
             sl.req.reset();
             r->tiles_inflight--;
@@ -152,12 +162,9 @@ void worker_main(tm_server* s) {
                 if (rc == TM_OK)
                     rc = tm_index_patterns(s->ctx, &r->req.params, sl.frames, r->req.dtype, m, r->req.H, r->req.W,
                                            nullptr, r->libs.data(), L, sl.hits, nullptr, sl.stream);
-                for (int li = 0; li < L && rc == TM_OK; ++li) {
-                    tm_hit* dst = r->req.out_host + ((size_t)li * r->req.n + sl.p0) * N;
-                    if (cudaMemcpyAsync(dst, sl.hits + (size_t)li * m * N, (size_t)m * N * sizeof(tm_hit),
-                                        cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
-                        rc = TM_ERR_CUDA;
-                }
+                if (rc == TM_OK && cudaMemcpyAsync(sl.hits_host, sl.hits, (size_t)L * m * N * sizeof(tm_hit),
+                                                   cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                    rc = TM_ERR_CUDA;
                 if (rc != TM_OK && r->status == TM_OK) r->status = rc;
                 cudaEventRecord(sl.done, sl.stream);
                 dispatched = true;
@@ -210,11 +217,14 @@ int tm_server_create(tm_ctx* ctx, const tm_server_params* params, tm_server** ou
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc(&sl.frames, (size_t)p.tile_patterns * p.max_H * p.max_W * 4) != cudaSuccess ||
-            cudaMalloc(&sl.hits, (size_t)p.max_libs * p.tile_patterns * p.max_top_n * sizeof(tm_hit)) != cudaSuccess) {
+            cudaMalloc(&sl.hits, (size_t)p.max_libs * p.tile_patterns * p.max_top_n * sizeof(tm_hit)) != cudaSuccess ||
+            cudaMallocHost(&sl.hits_host, (size_t)p.max_libs * p.tile_patterns * p.max_top_n * sizeof(tm_hit)) !=
+                cudaSuccess) {
             cudaGetLastError();
             for (auto& x : s->slots) {
                 if (x.frames) cudaFree(x.frames);
                 if (x.hits) cudaFree(x.hits);
+                if (x.hits_host) cudaFreeHost(x.hits_host);
                 if (x.done) cudaEventDestroy(x.done);
                 if (x.stream) cudaStreamDestroy(x.stream);
             }
@@ -309,6 +319,7 @@ void tm_server_destroy(tm_server* s) {
         cudaStreamSynchronize(sl.stream);
         cudaFree(sl.frames);
         cudaFree(sl.hits);
+        cudaFreeHost(sl.hits_host);
         cudaEventDestroy(sl.done);
         cudaStreamDestroy(sl.stream);
     }
