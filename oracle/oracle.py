@@ -26,6 +26,9 @@ Steps, in the paper's order (Section 2.2):
 * ``frame_sum`` / ``matrix_mask`` / ``apply_mask`` -- the two-stage indexing of Section 4.3:
   mean of all patterns, thresholded, cleaned by erosions and dilations, and the masked
   patterns indexed again.
+* ``gaussian_filter`` / ``dog_background`` / ``preprocess`` -- the diffuse background
+  removed by a difference of Gaussians and the result smoothed by a Gaussian blur
+  (Section 3.1's preprocessing; parameters are the caller's).
 * ``dense_scores`` / ``dft_scores`` -- Q(k, s) for every shift written as the dense
   circulant contraction and as its angular-DFT factorisation (Section 2.2, the
   complexity discussion naming the FFT cross-correlation alternative), both in FP64.
@@ -418,6 +421,59 @@ def find_centres(frames: np.ndarray, centre, radius: float, iterations: int) -> 
                 cx, cy = sx / s0, sy / s0
         out[p] = (cx, cy)
     return out
+
+
+# ----------------------------------------------------------------------------------
+# Background removal and smoothing (the preprocessing of Section 3.1: the diffuse
+# background removed with a difference of Gaussians, the result smoothed by a Gaussian
+# blur).  The paper gives neither the sigmas nor the edge rule; the reading here: a 1-D
+# Gaussian of standard deviation sigma on the integer offsets |i| <= radius, radius =
+# floor(truncate * sigma + 1/2), normalised to sum 1; applied along rows, then along
+# columns, with the edge pixel repeated outside the frame; the difference of Gaussians is
+# G(sigma_min) * x - G(sigma_max) * x with negative values set to 0.
+# ----------------------------------------------------------------------------------
+
+def gaussian_weights(sigma: float, truncate: float = 4.0) -> np.ndarray:
+    """Weights w[i + radius], i = -radius..radius, of the 1-D Gaussian (FP64, sum 1)."""
+    radius = int(math.floor(truncate * sigma + 0.5))
+    w = np.array([math.exp(-0.5 * (i / sigma) ** 2) for i in range(-radius, radius + 1)])
+    return w / w.sum()
+
+
+def _filter_axis(x: np.ndarray, w: np.ndarray, axis: int) -> np.ndarray:
+    """out[.., j, ..] = sum_i w[i] x[.., clamp(j + i - radius), ..] along one axis, the
+    terms added in the order i = 0, 1, ... (plain loops over the offsets)."""
+    radius = (w.shape[0] - 1) // 2
+    n = x.shape[axis]
+    out = np.zeros_like(x, dtype=np.float64)
+    idx = np.arange(n)
+    for i in range(w.shape[0]):
+        src = np.clip(idx + i - radius, 0, n - 1)
+        out += w[i] * np.take(x, src, axis=axis)
+    return out
+
+
+def gaussian_filter(img: np.ndarray, sigma: float, truncate: float = 4.0) -> np.ndarray:
+    """Gaussian smoothing of [..][H][W] images, rows (along W) first, then columns."""
+    w = gaussian_weights(sigma, truncate)
+    x = np.asarray(img, dtype=np.float64)
+    return _filter_axis(_filter_axis(x, w, x.ndim - 1), w, x.ndim - 2)
+
+
+def dog_background(img: np.ndarray, sigma_min: float, sigma_max: float, truncate: float = 4.0) -> np.ndarray:
+    """Difference of Gaussians, G(sigma_min) * x - G(sigma_max) * x, negative values set to 0."""
+    return np.maximum(gaussian_filter(img, sigma_min, truncate) - gaussian_filter(img, sigma_max, truncate), 0.0)
+
+
+def preprocess(frames: np.ndarray, dog=None, blur: float = 0.0, truncate: float = 4.0) -> np.ndarray:
+    """frames [n][H][W] -> float64: the difference of Gaussians (dog = (sigma_min, sigma_max),
+    or None), then a Gaussian blur of standard deviation `blur` (0: none)."""
+    x = np.asarray(frames, dtype=np.float64)
+    if dog is not None:
+        x = dog_background(x, dog[0], dog[1], truncate)
+    if blur > 0.0:
+        x = gaussian_filter(x, blur, truncate)
+    return x
 
 
 # ----------------------------------------------------------------------------------

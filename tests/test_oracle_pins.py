@@ -387,3 +387,56 @@ def test_refine_angles_vertex_of_a_parabola():
     P3[0, 3, 9], P3[0, 3, 10], P3[0, 3, 11] = 1.0, 1.0, 0.0        # vertex pulled beyond half a step
     a3 = O.refine_angles(P3, lib, np.array([[0]]), np.array([[10]]))
     assert a3[0, 0] == 95.0
+
+
+# ------------------------------------------------------------------ background removal and blur
+
+def test_gaussian_filter_matches_scipy():
+    """The separable filter with the edge pixel repeated equals scipy's Gaussian filter in
+    'nearest' mode with the same truncation (radius = floor(4 sigma + 1/2)), including a
+    radius larger than the frame."""
+    nd = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(21)
+    x = rng.random((2, 23, 31)) * 100.0
+    for sigma in (0.6, 1.0, 2.5, 7.0, 12.0):
+        ref = np.stack([nd.gaussian_filter(f, sigma, mode="nearest", truncate=4.0) for f in x])
+        assert np.allclose(O.gaussian_filter(x, sigma), ref, rtol=0, atol=1e-11)
+
+
+def test_gaussian_filter_closed_forms():
+    """A unit impulse far from the edges becomes the outer product of the normalised 1-D
+    Gaussian exp(-i^2 / (2 sigma^2)); a constant image stays constant; a linear ramp stays
+    the ramp where the kernel does not reach the edges."""
+    sigma = 1.7
+    r = int(math.floor(4.0 * sigma + 0.5))
+    g = np.array([math.exp(-i * i / (2.0 * sigma * sigma)) for i in range(-r, r + 1)])
+    g /= g.sum()
+    w = O.gaussian_weights(sigma)
+    assert w.shape == g.shape and np.allclose(w, g, rtol=1e-13, atol=0)
+    img = np.zeros((41, 45))
+    img[20, 22] = 1.0
+    out = O.gaussian_filter(img, sigma)
+    assert np.allclose(out[20 - r:21 + r, 22 - r:23 + r], np.outer(g, g), rtol=0, atol=1e-16)
+    assert abs(out.sum() - 1.0) < 1e-12
+    assert np.allclose(O.gaussian_filter(np.full((9, 12), 3.25), 2.0), 3.25, rtol=0, atol=1e-13)
+    yy, xx = np.mgrid[0:40, 0:44]
+    ramp = 0.5 * xx - 0.25 * yy + 3.0
+    out = O.gaussian_filter(ramp, sigma)
+    assert np.allclose(out[r:-r, r:-r], ramp[r:-r, r:-r], rtol=0, atol=1e-12)
+
+
+def test_difference_of_gaussians_removes_smooth_background():
+    """The difference of Gaussians is 0 on a constant or linear background (away from the
+    edges), never negative, and keeps a sharp spot standing on a broad background."""
+    yy, xx = np.mgrid[0:64, 0:64]
+    back = 50.0 + 0.3 * xx + 0.1 * yy
+    d = O.dog_background(back, 1.0, 4.0)
+    assert np.all(d >= 0.0) and np.max(np.abs(d[16:-16, 16:-16])) < 1e-9
+    spot = back.copy()
+    spot[32, 30] += 200.0
+    d = O.dog_background(spot, 1.0, 4.0)
+    assert d[32, 30] > 10.0 and np.argmax(d) == 32 * 64 + 30
+    f = np.random.default_rng(3).poisson(5.0, size=(2, 20, 24)).astype(np.uint16)
+    assert np.array_equal(O.preprocess(f), f.astype(np.float64))              # nothing asked: the frames
+    assert np.allclose(O.preprocess(f, dog=(1.0, 3.0), blur=1.5),
+                       O.gaussian_filter(O.dog_background(f, 1.0, 3.0), 1.5), rtol=0, atol=1e-12)
