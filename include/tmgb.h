@@ -351,6 +351,26 @@ int tm_matrix_mask(tm_ctx* ctx, const double* sum_dev, int64_t n_frames, int32_t
 int tm_find_centres(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t n, int32_t H, int32_t W,
                     double cx0, double cy0, double radius, int32_t iterations, float* centres_dev, void* stream);
 
+/* Background removal and smoothing (Section 3.1: the diffuse background of every pattern was
+ * removed with a difference of Gaussians and the result smoothed by a Gaussian blur; the
+ * paper gives no parameters).  out_dev [n][H][W] float receives, per frame x (frames_dev
+ * [n][H][W] u16 or f32): d = max(G(dog_sigma_min) * x - G(dog_sigma_max) * x, 0) when
+ * dog_sigma_max > 0 (else d = x), then G(blur_sigma) * d when blur_sigma > 0.  G(s) is the
+ * separable Gaussian of standard deviation s on the integer offsets |i| <= floor(truncate s
+ * + 1/2) (truncate <= 0: 4), normalised to sum 1, applied along rows then along columns with
+ * the edge pixel repeated outside the frame; FP32 sums in ascending offset order, weights
+ * from double precision.  Radii up to 256; sigmas must be 0 or in [0.1, 64].  Index the
+ * result as TM_DTYPE_F32 frames (gamma and the threshold then apply to it).  Uses context
+ * workspace; asynchronous on stream. */
+typedef struct tm_preprocess_params {
+    double dog_sigma_min;    /* inner Gaussian of the difference (< dog_sigma_max)         */
+    double dog_sigma_max;    /* outer Gaussian; <= 0: no background removal               */
+    double blur_sigma;       /* smoothing after it; <= 0: none                            */
+    double truncate;         /* kernel radius in sigmas (<= 0: 4)                         */
+} tm_preprocess_params;
+int tm_preprocess(tm_ctx* ctx, const tm_preprocess_params* params, const void* frames_dev, int32_t dtype, int64_t n,
+                  int32_t H, int32_t W, float* out_dev, void* stream);
+
 /* Default parameters: gamma 0.5, subtract 0, centre NaN, prefilter 1, top_n 5,
  * FP32 sparse path, rescore_k 256, no pixel mask, no threshold. */
 void tm_index_params_default(tm_index_params* p);

@@ -885,6 +885,72 @@ int tm_find_centres(tm_ctx* ctx, const void* frames_dev, int32_t dtype, int64_t 
     return TM_OK;
 }
 
+int tm_preprocess(tm_ctx* ctx, const tm_preprocess_params* pp, const void* frames_dev, int32_t dtype, int64_t n,
+                  int32_t H, int32_t W, float* out_dev, void* stream) {
+    if (!ctx || !pp) return fail(TM_ERR_INVALID_ARG, "tm_preprocess: NULL argument");
+    if (n < 0 || H < 1 || W < 1 || H > 32000 || W > 32000) return fail(TM_ERR_INVALID_ARG, "tm_preprocess: bad shape");
+    if (dtype != TM_DTYPE_U16 && dtype != TM_DTYPE_F32) return fail(TM_ERR_INVALID_ARG, "tm_preprocess: dtype");
+    const bool dog = pp->dog_sigma_max > 0.0, blur = pp->blur_sigma > 0.0;
+    const double tr = pp->truncate > 0.0 ? pp->truncate : 4.0;
+    auto sigma_ok = [](double s) { return s >= 0.1 && s <= 64.0; };
+    if ((dog && !(sigma_ok(pp->dog_sigma_min) && sigma_ok(pp->dog_sigma_max) && pp->dog_sigma_min < pp->dog_sigma_max)) ||
+        (blur && !sigma_ok(pp->blur_sigma)) || !(tr <= 64.0) || isnan(pp->dog_sigma_max) || isnan(pp->blur_sigma))
+        return fail(TM_ERR_INVALID_ARG, "tm_preprocess: sigmas must be in [0.1, 64] (dog_sigma_min < dog_sigma_max)");
+    auto radius = [&](double s) { return (int)floor(tr * s + 0.5); };
+    const int r_min = dog ? radius(pp->dog_sigma_min) : 0, r_max = dog ? radius(pp->dog_sigma_max) : 0;
+    const int r_blur = blur ? radius(pp->blur_sigma) : 0;
+    if (r_min > 256 || r_max > 256 || r_blur > 256) return fail(TM_ERR_INVALID_ARG, "tm_preprocess: radius above 256");
+    if (tmgb::gauss_cols_smem(H, r_min, r_max, 1) > 232448)
+        return fail(TM_ERR_UNSUPPORTED, "tm_preprocess: frames of %d rows do not fit the column pass", H);
+    if (n == 0) return TM_OK;
+    if (!frames_dev || !out_dev) return fail(TM_ERR_INVALID_ARG, "tm_preprocess: NULL buffer");
+    // weights (double precision, normalised, rounded to float): [min | max | blur | identity]
+    std::vector<float> w;
+    auto add = [&](double s, int r) -> size_t {
+        const size_t at = w.size();
+        if (s <= 0.0) {
+            w.push_back(1.0f);
+            return at;
+        }
+        std::vector<double> d(2 * r + 1);
+        double sum = 0.0;
+        for (int i = -r; i <= r; ++i) sum += (d[i + r] = exp(-0.5 * (i / s) * (i / s)));
+        for (double v : d) w.push_back((float)(v / sum));
+        return at;
+    };
+    const size_t o_min = add(dog ? pp->dog_sigma_min : 0.0, r_min), o_max = add(dog ? pp->dog_sigma_max : 0.0, r_max);
+    const size_t o_blur = add(blur ? pp->blur_sigma : 0.0, r_blur);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    float* dw;
+    int rc = workspace(ctx, st, "pre_weights", w.size() * sizeof(float), (void**)&dw);
+    const size_t img = (size_t)n * H * W * sizeof(float);
+    float *t1 = nullptr, *t2 = nullptr;
+    if (!rc) rc = workspace(ctx, st, "pre_t1", img, (void**)&t1);
+    if (!rc && dog) rc = workspace(ctx, st, "pre_t2", img, (void**)&t2);
+    if (rc) return rc;
+    TM_CUDA(cudaMemcpyAsync(dw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, st), "tm_preprocess: weights");
+    const int64_t rows = n * (int64_t)H;
+    if (dog) {
+        TM_CUDA(tmgb::launch_gauss_rows(frames_dev, dtype, rows, W, dw + o_min, r_min, dw + o_max, r_max, t1, t2, st),
+                "tm_preprocess: rows");
+        TM_CUDA(tmgb::launch_gauss_cols(t1, t2, n, H, W, dw + o_min, r_min, dw + o_max, r_max, 1, out_dev, st),
+                "tm_preprocess: columns");
+    }
+    if (blur) {
+        TM_CUDA(tmgb::launch_gauss_rows(dog ? (const void*)out_dev : frames_dev, dog ? TM_DTYPE_F32 : dtype, rows, W,
+                                        dw + o_blur, r_blur, nullptr, 0, t1, nullptr, st),
+                "tm_preprocess: rows");
+        TM_CUDA(tmgb::launch_gauss_cols(t1, nullptr, n, H, W, dw + o_blur, r_blur, nullptr, 0, 0, out_dev, st),
+                "tm_preprocess: columns");
+    }
+    if (!dog && !blur)                                       // identity: the frames as floats
+        TM_CUDA(tmgb::launch_gauss_rows(frames_dev, dtype, rows, W, dw + o_blur, 0, nullptr, 0, out_dev, nullptr, st),
+                "tm_preprocess: copy");
+    return TM_OK;
+}
+
 void tm_index_params_default(tm_index_params* p) {
     if (!p) return;
     p->gamma = 0.5;

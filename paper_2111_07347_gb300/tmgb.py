@@ -91,6 +91,11 @@ TM_STAGE_COUNT = 8
 STAGES = ["polar", "prefilter", "sparse", "dft", "dense", "rescore", "stage6", "stage7"]
 
 
+class tm_preprocess_params(ctypes.Structure):
+    _fields_ = [("dog_sigma_min", ctypes.c_double), ("dog_sigma_max", ctypes.c_double),
+                ("blur_sigma", ctypes.c_double), ("truncate", ctypes.c_double)]
+
+
 class tm_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * TM_STAGE_COUNT), ("launches", ctypes.c_int64 * TM_STAGE_COUNT),
                 ("sparse_macs", ctypes.c_int64)]
@@ -125,6 +130,8 @@ _SIGS = {
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
     "tm_find_centres": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P]),
+    "tm_preprocess": (ctypes.c_int, [_P, ctypes.POINTER(tm_preprocess_params), _P, ctypes.c_int32, ctypes.c_int64,
+                                     ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "tm_frame_sum": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32, _P, _P]),
     "tm_matrix_mask": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -583,6 +590,19 @@ class Context:
         _check(library().tm_find_centres(self.handle, frames.data_ptr(), _dtype_code(frames), n, H, W, float(cx),
                                          float(cy), float(radius), int(iterations), out.data_ptr(),
                                          _stream_ptr(stream)))
+        return out
+
+    def preprocess(self, frames, dog=None, blur=0.0, truncate=4.0, out=None, stream=None):
+        """Background removal (difference of Gaussians, dog = (sigma_min, sigma_max)) and
+        Gaussian blur of device frames [n][H][W] -> float32 [n][H][W] tensor."""
+        import torch
+        n, H, W = frames.shape
+        if out is None:
+            out = torch.empty((n, H, W), dtype=torch.float32, device=frames.device)
+        p = tm_preprocess_params(float(dog[0]) if dog else 0.0, float(dog[1]) if dog else 0.0, float(blur),
+                                 float(truncate))
+        _check(library().tm_preprocess(self.handle, ctypes.byref(p), frames.data_ptr(), _dtype_code(frames), n, H, W,
+                                       out.data_ptr(), _stream_ptr(stream)))
         return out
 
     def frame_sum(self, frames, out=None, accumulate=False, stream=None):

@@ -90,3 +90,60 @@ def test_centred_thresholded_index_matches_oracle(ctx, moved):
                   threshold=1.0)
     compare_hits(h, ref, lib)
     ctx.unload_library(lid)
+
+
+# ------------------------------------------------------------------ background removal and blur
+
+def _noisy_frames(rng, n, H, W, dtype):
+    """Patterns on a broad diffuse background (the case the difference of Gaussians is for)."""
+    yy, xx = np.mgrid[0:H, 0:W]
+    back = 20.0 * np.exp(-((xx - W / 2) ** 2 + (yy - H / 2) ** 2) / (2 * (W / 3) ** 2))
+    f = rng.poisson(back[None] + 1.0, size=(n, H, W)).astype(np.float64)
+    for p in range(n):
+        for _ in range(6):
+            y, x = rng.integers(8, H - 8), rng.integers(8, W - 8)
+            f[p, y - 1:y + 2, x - 1:x + 2] += rng.integers(20, 200)
+    return f.astype(dtype)
+
+
+@pytest.mark.parametrize("dog,blur", [((1.0, 4.0), 0.0), (None, 1.5), ((1.0, 6.0), 1.2), (None, 0.0), ((0.7, 2.3), 9.0)])
+def test_background_removal_and_blur_match_oracle(ctx, dog, blur):
+    """Difference of Gaussians and blur on the GPU (FP32 sums) against the FP64 oracle: within
+    3e-5 of the frames' largest value (two passes of up to 2 * 4 * 9 + 1 terms each, twice,
+    at 2^-24 per term), for u16 and f32 frames, a frame narrower than the blur's radius
+    included."""
+    rng = np.random.default_rng(17)
+    for shape, dtype in (((6, 96, 80), np.uint16), ((4, 64, 64), np.float32), ((2, 40, 24), np.float32)):
+        f = _noisy_frames(rng, *shape, dtype)
+        ref = O.preprocess(f, dog=dog, blur=blur)
+        out = ctx.preprocess(_t(f), dog=dog, blur=blur).cpu().numpy().astype(np.float64)
+        assert out.shape == ref.shape
+        assert np.all(np.abs(out - ref) <= 3e-5 * float(f.max())), (shape, np.abs(out - ref).max())
+        if dog is not None:
+            assert np.all(out >= 0.0)
+
+
+def test_index_after_background_removal(ctx):
+    """The whole path on preprocessed frames: the tiny scan on a diffuse background, the
+    background removed and blurred on the GPU and indexed, against the oracle's own
+    preprocessing and index; the GPU's top-1 template is the oracle's, or within 1e-4 of
+    the oracle's best Q (the two preprocessings differ by FP32 rounding), on >= 98 %."""
+    ts, scan, _ = synth.tiny_workload(n_side=8)
+    rng = np.random.default_rng(5)
+    H, W = scan.frames.shape[1:]
+    yy, xx = np.mgrid[0:H, 0:W]
+    back = 3.0 * np.exp(-((xx - W / 2) ** 2 + (yy - H / 2) ** 2) / (2 * 30.0 ** 2))
+    frames = (scan.frames + back[None] + rng.random(scan.frames.shape) * 0.2).astype(np.float32)
+    lib = O.prepare_library(ts, 60, 180)
+    lid = ctx.load_library(ts, 60, 180)
+    pre = ctx.preprocess(_t(frames), dog=(1.0, 5.0), blur=1.0)
+    h = tmgb.hits_to_numpy(ctx.index(pre, lid, top_n=5))[0]
+    # the oracle indexes float32 frames, as the GPU path does: its preprocessing rounded to them
+    ref = O.index(O.preprocess(frames, dog=(1.0, 5.0), blur=1.0).astype(np.float32), lib, N=5)
+    ok = 0
+    for p in range(frames.shape[0]):
+        k = int(h["template_index"][p, 0])
+        qb = ref["score"][p, 0]
+        ok += int(k == ref["template"][p, 0] or abs(ref["q_best"][p, k] - qb) <= 1e-4 * abs(qb))
+    assert ok >= 0.98 * frames.shape[0], ok
+    ctx.unload_library(lid)
