@@ -910,12 +910,13 @@ int tm_preprocess(tm_ctx* ctx, const tm_preprocess_params* pp, const void* frame
         const size_t at = w.size();
         if (s <= 0.0) {
             w.push_back(1.0f);
-            return at;
+        } else {
+            std::vector<double> d(2 * r + 1);
+            double sum = 0.0;
+            for (int i = -r; i <= r; ++i) sum += (d[i + r] = exp(-0.5 * (i / s) * (i / s)));
+            for (double v : d) w.push_back((float)(v / sum));
         }
-        std::vector<double> d(2 * r + 1);
-        double sum = 0.0;
-        for (int i = -r; i <= r; ++i) sum += (d[i + r] = exp(-0.5 * (i / s) * (i / s)));
-        for (double v : d) w.push_back((float)(v / sum));
+        w.resize(at + tmgb::gauss_padded_taps(r), 0.0f);    // the kernels take taps four at a time
         return at;
     };
     const size_t o_min = add(dog ? pp->dog_sigma_min : 0.0, r_min), o_max = add(dog ? pp->dog_sigma_max : 0.0, r_max);

@@ -112,6 +112,7 @@ cudaError_t launch_refine(const RefineCall& c, int num_sms, cudaStream_t st);
 // float input) filtered by w1 (and w2, nullable) into out1 (out2); columns of n frames H x W
 // filtered by w1 (dog: and in2 by w2, out = max(a - b, 0)).  Weights [2 r + 1] on the device.
 size_t gauss_cols_smem(int H, int r1, int r2, int dog);
+int gauss_padded_taps(int r);               // weights per filter: 2 r + 1 rounded up, zero-padded
 cudaError_t launch_gauss_rows(const void* in, int dtype, int64_t rows, int W, const float* w1, int r1, const float* w2,
                               int r2, float* out1, float* out2, cudaStream_t st);
 cudaError_t launch_gauss_cols(const float* in1, const float* in2, int64_t n, int H, int W, const float* w1, int r1,
