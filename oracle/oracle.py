@@ -29,6 +29,9 @@ Steps, in the paper's order (Section 2.2):
 * ``gaussian_filter`` / ``dog_background`` / ``preprocess`` -- the diffuse background
   removed by a difference of Gaussians and the result smoothed by a Gaussian blur
   (Section 3.1's preprocessing; parameters are the caller's).
+* ``kinematic_spots`` -- templates simulated over an orientation grid (Section 2.1:
+  reflections near the Ewald sphere by their excitation error, a linear relrod shape,
+  |F|^2 for the intensity, the strongest kept), the step before the library.
 * ``dense_scores`` / ``dft_scores`` -- Q(k, s) for every shift written as the dense
   circulant contraction and as its angular-DFT factorisation (Section 2.2, the
   complexity discussion naming the FFT cross-correlation alternative), both in FP64.
@@ -474,6 +477,49 @@ def preprocess(frames: np.ndarray, dog=None, blur: float = 0.0, truncate: float 
     if blur > 0.0:
         x = gaussian_filter(x, blur, truncate)
     return x
+
+
+# ----------------------------------------------------------------------------------
+# Template simulation over an orientation grid (Section 2.1: for each orientation the
+# reciprocal lattice is rotated into the beam frame, reflections whose excitation error is
+# within s_max are kept with the intensity |F|^2 (1 - |s|/s_max) of a linear relrod shape,
+# projected onto the detector plane; Section 4.1 ignores atomic scattering, so |F|^2 comes
+# from unit scattering factors -- any |F|^2 may be given).  The most intense max_spots are
+# kept, ties by the smaller |g|, then the lower point index.
+# ----------------------------------------------------------------------------------
+
+def kinematic_spots(g: np.ndarray, f2: np.ndarray, gnorm: np.ndarray, rot: np.ndarray, wavelength: float,
+                    s_max: float, max_spots: int):
+    """g [G][3] reciprocal lattice points (1/Angstrom, crystal frame), f2 [G] |F|^2, gnorm
+    [G] |g|, rot [D][3][3] orientation matrices (row j = beam-frame axis j in crystal
+    coordinates; z along the beam).  Per orientation and point, in double precision with
+    every operation rounded in this order: the beam-frame components
+    x_j = (R[j][0] g_0 + R[j][1] g_1) + R[j][2] g_2, t = x_2 + k with k = 1 / wavelength,
+    s = k - sqrt((x_0 x_0 + x_1 x_1) + t t); kept when |s| <= s_max and
+    I = f2 (1 - |s| / s_max) > 0.  Returns (counts [D], spots [D][max_spots][3] = (x_0, x_1, I)
+    in the order: I descending, |g| ascending, point index ascending)."""
+    G, D = g.shape[0], rot.shape[0]
+    k = 1.0 / wavelength
+    counts = np.zeros(D, dtype=np.int32)
+    spots = np.zeros((D, max_spots, 3), dtype=np.float64)
+    for d in range(D):
+        R = [[float(rot[d, j, m]) for m in range(3)] for j in range(3)]
+        cand = []
+        for i in range(G):
+            g0, g1, g2 = float(g[i, 0]), float(g[i, 1]), float(g[i, 2])
+            x = [(R[j][0] * g0 + R[j][1] * g1) + R[j][2] * g2 for j in range(3)]
+            t = x[2] + k
+            s = k - math.sqrt((x[0] * x[0] + x[1] * x[1]) + t * t)
+            if abs(s) <= s_max:
+                inten = float(f2[i]) * (1.0 - abs(s) / s_max)
+                if inten > 0.0:
+                    cand.append((-inten, float(gnorm[i]), i, x[0], x[1], inten))
+        cand.sort()
+        cand = cand[:max_spots]
+        counts[d] = len(cand)
+        for r, c in enumerate(cand):
+            spots[d, r] = (c[3], c[4], c[5])
+    return counts, spots
 
 
 # ----------------------------------------------------------------------------------

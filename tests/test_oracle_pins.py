@@ -440,3 +440,75 @@ def test_difference_of_gaussians_removes_smooth_background():
     assert np.array_equal(O.preprocess(f), f.astype(np.float64))              # nothing asked: the frames
     assert np.allclose(O.preprocess(f, dog=(1.0, 3.0), blur=1.5),
                        O.gaussian_filter(O.dog_background(f, 1.0, 3.0), 1.5), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------------ template simulation
+
+def test_kinematic_zone_axis_closed_form():
+    """FCC seen down [001] (identity orientation): the kept reflections are the zero layer's
+    allowed ones (h, k both even, l = 0, |F|^2 = 16 for the four-atom basis) whose excitation
+    error k - sqrt(k^2 + |g|^2) lies within s_max, each with I = 16 (1 - |s| / s_max); no
+    reflection of the layers l = +-1 (|s| ~ 1/a >> s_max) is kept."""
+    st = synth.STRUCTURES["fcc"]
+    g, F2, gn = synth._reciprocal_points(st, 1.2)
+    lam, s_max = synth.WAVELENGTH_200KV, 0.02
+    counts, spots = O.kinematic_spots(g, F2, gn, np.eye(3)[None], lam, s_max, 500)
+    k = 1.0 / lam
+    a = st["a"]
+    exp = []
+    for h in range(-6, 7):
+        for kk in range(-6, 7):
+            if (h, kk) == (0, 0) or h % 2 or kk % 2:
+                continue
+            gx, gy = h / a, kk / a
+            if math.hypot(gx, gy) > 1.2:
+                continue
+            s = k - math.sqrt(k * k + gx * gx + gy * gy)
+            if abs(s) <= s_max:
+                exp.append((gx, gy, 16.0 * (1.0 - abs(s) / s_max)))
+    got = spots[0, :counts[0]]
+    assert counts[0] == len(exp) > 0
+    key = lambda r: (round(r[0], 9), round(r[1], 9))
+    e = sorted(exp, key=key)
+    o = sorted(map(tuple, got), key=key)
+    for (x0, y0, i0), (x1, y1, i1) in zip(e, o):
+        assert abs(x0 - x1) < 1e-12 and abs(y0 - y1) < 1e-12 and abs(i0 - i1) < 1e-9
+    assert np.all(np.diff(got[:, 2]) <= 0)                                   # strongest first
+
+
+def test_kinematic_on_the_ewald_sphere_and_truncation():
+    """A point placed exactly on the Ewald sphere has s = 0 and keeps its full |F|^2; one at
+    s = s_max / 2 keeps half; max_spots keeps the strongest in order."""
+    lam, s_max = synth.WAVELENGTH_200KV, 0.02
+    k = 1.0 / lam
+    pts, f2 = [], []
+    for a_, s_target, w in ((0.5, 0.0, 4.0), (0.7, s_max / 2, 2.0), (0.9, -s_max / 2, 8.0), (0.3, 0.05, 1.0)):
+        # |v + k z| = k - s  ->  v = (a, 0, -k + sqrt((k - s)^2 - a^2))
+        pts.append((a_, 0.0, -k + math.sqrt((k - s_target) ** 2 - a_ * a_)))
+        f2.append(w)
+    g = np.array(pts)
+    f2 = np.array(f2)
+    gn = np.linalg.norm(g, axis=1)
+    counts, spots = O.kinematic_spots(g, f2, gn, np.eye(3)[None], lam, s_max, 10)
+    assert counts[0] == 3                                                    # the s = 0.05 point is out
+    inten = spots[0, :3, 2]
+    assert np.allclose(sorted(inten), sorted([4.0, 1.0, 4.0]), rtol=0, atol=1e-8)
+    c1, s1 = O.kinematic_spots(g, f2, gn, np.eye(3)[None], lam, s_max, 2)
+    assert c1[0] == 2 and np.array_equal(s1[0, :2], spots[0, :2])
+
+
+def test_kinematic_matches_the_scan_generator():
+    """The orientation-grid simulation equals the (independently written, vectorised)
+    generator of the synthetic scans for FCC, HCP and tetragonal lattices."""
+    for name, system in (("fcc", "cubic"), ("hcp", "hexagonal"), ("tetragonal", "tetragonal")):
+        st = synth.STRUCTURES[name]
+        g, F2, gn = synth._reciprocal_points(st, 1.2)
+        dirs = synth.beam_directions(system, 4.0)
+        R = np.stack([synth._orientation_matrix(d) for d in dirs])
+        counts, spots = O.kinematic_spots(g, F2, gn, R, synth.WAVELENGTH_200KV, 0.02, 150)
+        ts = synth.kinematic_library(name, step_deg=4.0)
+        assert np.array_equal(np.diff(ts.offsets), counts)
+        flat = np.concatenate([spots[d, :counts[d]] for d in range(len(counts))])
+        assert np.allclose(flat[:, 0], ts.a, rtol=0, atol=1e-13)
+        assert np.allclose(flat[:, 1], ts.b, rtol=0, atol=1e-13)
+        assert np.allclose(flat[:, 2], ts.intensity, rtol=1e-12, atol=1e-12)
