@@ -171,6 +171,34 @@ def cpu_baseline(ts, scan, seconds: float) -> dict:
 
 # ------------------------------------------------------------------ two-stage (masked) indexing
 
+def simulation_bench(ctx, stream) -> dict:
+    """Template simulation on the device (Section 2.1) over the 0.5 deg orientation grids of
+    the FCC and HCP libraries: orientations per second, inputs resident on the device."""
+    import torch
+    from paper_2111_07347_gb300 import synth
+    out = {}
+    for name, system in (("fcc", "cubic"), ("hcp", "hexagonal")):
+        st = synth.STRUCTURES[name]
+        g, F2, gn = synth._reciprocal_points(st, 1.2)
+        dirs = synth.beam_directions(system, 0.5)
+        R = np.stack([synth._orientation_matrix(d) for d in dirs])
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+        gd, fd, nd, rd = t(g), t(F2), t(gn), t(R)
+        ctx.kinematic_spots(gd, fd, nd, rd, synth.WAVELENGTH_200KV, 0.02, 150, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            counts, _ = ctx.kinematic_spots(gd, fd, nd, rd, synth.WAVELENGTH_200KV, 0.02, 150, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out[name] = {"orientations": int(R.shape[0]), "points": int(g.shape[0]), "ms": ms,
+                     "orientations_per_s": R.shape[0] / (ms / 1e3),
+                     "spots": int(counts.sum().item())}
+    return out
+
+
 def preprocess_bench(ctx, stream, frames_d, steps: int) -> dict:
     """Section 3.1's background removal (difference of Gaussians, sigmas 1 and 4 px) and blur
     (1 px) of the scan's frames, as tm_preprocess runs them before indexing.  HBM bytes: the
@@ -566,6 +594,7 @@ def run_ours(args):
         line["two_stage"] = two_stage_bench(ctx, stream, max(2, args.steps // 2))
     if not args.no_preprocess:
         line["preprocess"] = preprocess_bench(ctx, stream, frames_d, max(2, args.steps // 2))
+        line["template_simulation"] = simulation_bench(ctx, stream)
     if not args.no_serving:
         hcp = synth.kinematic_library("hcp")
         lid_h = ctx.load_library(hcp, N_R, N_THETA)

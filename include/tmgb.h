@@ -371,6 +371,24 @@ typedef struct tm_preprocess_params {
 int tm_preprocess(tm_ctx* ctx, const tm_preprocess_params* params, const void* frames_dev, int32_t dtype, int64_t n,
                   int32_t H, int32_t W, float* out_dev, void* stream);
 
+/* Template simulation over an orientation grid (Section 2.1: for each orientation the
+ * reflections near the Ewald sphere, by their excitation error, weighted by |F|^2 and a
+ * linear relrod shape, projected onto the detector; the strongest kept).  g_dev [G][3] are
+ * reciprocal lattice points (1/Angstrom, crystal frame), f2_dev [G] their |F|^2 (unit
+ * scattering factors or any table), gnorm_dev [G] their |g|; rot_dev [D][3][3] (row-major)
+ * the orientations: row j is the beam-frame axis j in crystal coordinates, z along the beam.
+ * Per orientation and point, in double precision with each operation rounded in this order:
+ * x_j = (R_j0 g_0 + R_j1 g_1) + R_j2 g_2, t = x_2 + k with k = 1 / wavelength,
+ * s = k - sqrt((x_0 x_0 + x_1 x_1) + t t); kept when |s| <= s_max and
+ * I = |F|^2 (1 - |s| / s_max) > 0.  counts_dev [D] receives the number kept (at most
+ * max_spots; -1 when more than 512 reflections of one orientation are within s_max: make
+ * s_max or the point set smaller) and spots_dev [D][max_spots][3] the (x_0, x_1, I) of the
+ * kept ones, I descending, ties by |g| ascending, then by point index.  Feed them to
+ * tm_load_library as TM_COORDS_XY templates.  Asynchronous on stream. */
+int tm_kinematic_spots(tm_ctx* ctx, const double* g_dev, const double* f2_dev, const double* gnorm_dev, int64_t G,
+                       const double* rot_dev, int64_t D, double wavelength, double s_max, int32_t max_spots,
+                       int32_t* counts_dev, double* spots_dev, void* stream);
+
 /* Default parameters: gamma 0.5, subtract 0, centre NaN, prefilter 1, top_n 5,
  * FP32 sparse path, rescore_k 256, no pixel mask, no threshold. */
 void tm_index_params_default(tm_index_params* p);

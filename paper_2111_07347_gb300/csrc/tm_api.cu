@@ -952,6 +952,25 @@ int tm_preprocess(tm_ctx* ctx, const tm_preprocess_params* pp, const void* frame
     return TM_OK;
 }
 
+int tm_kinematic_spots(tm_ctx* ctx, const double* g_dev, const double* f2_dev, const double* gnorm_dev, int64_t G,
+                       const double* rot_dev, int64_t D, double wavelength, double s_max, int32_t max_spots,
+                       int32_t* counts_dev, double* spots_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_kinematic_spots: ctx is NULL");
+    if (G < 0 || G > (1 << 24) || D < 0 || max_spots < 1 || max_spots > 65535)
+        return fail(TM_ERR_INVALID_ARG, "tm_kinematic_spots: sizes out of range");
+    if (!(wavelength > 0.0 && isfinite(wavelength)) || !(s_max > 0.0 && isfinite(s_max)))
+        return fail(TM_ERR_INVALID_ARG, "tm_kinematic_spots: wavelength and s_max must be finite and > 0");
+    if (D == 0) return TM_OK;
+    if ((G > 0 && (!g_dev || !f2_dev || !gnorm_dev)) || !rot_dev || !counts_dev || !spots_dev)
+        return fail(TM_ERR_INVALID_ARG, "tm_kinematic_spots: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    TM_CUDA(tmgb::launch_kinematic(g_dev, f2_dev, gnorm_dev, G, rot_dev, D, wavelength, s_max, max_spots, counts_dev,
+                                   spots_dev, (cudaStream_t)stream),
+            "tm_kinematic_spots: launch");
+    return TM_OK;
+}
+
 void tm_index_params_default(tm_index_params* p) {
     if (!p) return;
     p->gamma = 0.5;

@@ -118,6 +118,12 @@ cudaError_t launch_gauss_rows(const void* in, int dtype, int64_t rows, int W, co
 cudaError_t launch_gauss_cols(const float* in1, const float* in2, int64_t n, int H, int W, const float* w1, int r1,
                               const float* w2, int r2, int dog, float* out, cudaStream_t st);
 
+// Template simulation (k_kinematic.cu): counts [D], spots [D][max_spots][3].
+int kinematic_cand_max();
+cudaError_t launch_kinematic(const double* g, const double* f2, const double* gnorm, int64_t G, const double* rot,
+                             int64_t D, double wavelength, double s_max, int max_spots, int32_t* counts, double* spots,
+                             cudaStream_t st);
+
 cudaError_t launch_find_centres(const void* frames, int dtype, int64_t n, int H, int W, double cx0, double cy0,
                                 double radius, int iterations, float2* out, cudaStream_t st);
 

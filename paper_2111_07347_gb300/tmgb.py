@@ -130,6 +130,8 @@ _SIGS = {
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
     "tm_find_centres": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P]),
+    "tm_kinematic_spots": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
     "tm_preprocess": (ctypes.c_int, [_P, ctypes.POINTER(tm_preprocess_params), _P, ctypes.c_int32, ctypes.c_int64,
                                      ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "tm_frame_sum": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
@@ -591,6 +593,35 @@ class Context:
                                          float(cy), float(radius), int(iterations), out.data_ptr(),
                                          _stream_ptr(stream)))
         return out
+
+    def kinematic_spots(self, g, f2, gnorm, rot, wavelength, s_max, max_spots, stream=None):
+        """Reflections kept per orientation (device tensors: g [G][3], f2 [G], gnorm [G], rot
+        [D][3][3], float64) -> (counts int32 [D], spots float64 [D][max_spots][3] = kx, ky, I)."""
+        import torch
+        D = rot.shape[0]
+        counts = torch.empty((D,), dtype=torch.int32, device=rot.device)
+        spots = torch.zeros((D, max_spots, 3), dtype=torch.float64, device=rot.device)
+        _check(library().tm_kinematic_spots(self.handle, g.data_ptr(), f2.data_ptr(), gnorm.data_ptr(), g.shape[0],
+                                            rot.data_ptr(), D, float(wavelength), float(s_max), int(max_spots),
+                                            counts.data_ptr(), spots.data_ptr(), _stream_ptr(stream)))
+        return counts, spots
+
+    def kinematic_templates(self, g, f2, gnorm, rot, wavelength, s_max, max_spots=150, px_per_unit=100.0,
+                            mirror=True):
+        """The simulated templates (numpy inputs as for kinematic_spots) as a TemplateSet in
+        (kx, ky) coordinates, ready for load_library."""
+        import torch
+        from . import synth
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+        counts, spots = self.kinematic_spots(t(g), t(f2), t(gnorm), t(rot), wavelength, s_max, max_spots)
+        counts, spots = counts.cpu().numpy(), spots.cpu().numpy()
+        if np.any(counts < 0):
+            raise TmError(TM_ERR_UNSUPPORTED, "more than %d reflections within s_max for an orientation" % 512)
+        offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        flat = np.concatenate([spots[d, :counts[d]] for d in range(len(counts))]) if len(counts) else np.zeros((0, 3))
+        return synth.TemplateSet(offsets, flat[:, 0].copy(), flat[:, 1].copy(), flat[:, 2].copy(), coords="xy",
+                                 px_per_unit=px_per_unit, mirror=mirror, meta={"kind": "kinematic (device)"})
 
     def preprocess(self, frames, dog=None, blur=0.0, truncate=4.0, out=None, stream=None):
         """Background removal (difference of Gaussians, dog = (sigma_min, sigma_max)) and
