@@ -32,6 +32,9 @@ Steps, in the paper's order (Section 2.2):
 * ``kinematic_spots`` -- templates simulated over an orientation grid (Section 2.1:
   reflections near the Ewald sphere by their excitation error, a linear relrod shape,
   |F|^2 for the intensity, the strongest kept), the step before the library.
+* ``orientation_vectors`` / ``angular_deviation`` -- the crystal direction along a sample
+  axis for each pattern's best template and in-plane angle (the vectors of inverse pole
+  figure maps) and the angle between two maps' vectors (Eq. 2).
 * ``dense_scores`` / ``dft_scores`` -- Q(k, s) for every shift written as the dense
   circulant contraction and as its angular-DFT factorisation (Section 2.2, the
   complexity discussion naming the FFT cross-correlation alternative), both in FP64.
@@ -520,6 +523,61 @@ def kinematic_spots(g: np.ndarray, f2: np.ndarray, gnorm: np.ndarray, rot: np.nd
         for r, c in enumerate(cand):
             spots[d, r] = (c[3], c[4], c[5])
     return counts, spots
+
+
+# ----------------------------------------------------------------------------------
+# Orientation maps and their angular deviation (Section 4.1: inverse pole figure maps along
+# the sample axes; Eq. 2: the angle between the vectors two maps hold in a pixel).  Reading:
+# template b has the orientation matrix R_b (rows: the beam-frame axes in crystal
+# coordinates, as its simulation used); its mirror copy reflects the beam-frame y axis
+# (M = diag(1, -1, 1)); a hit at in-plane angle phi shows the template rotated by phi about
+# the beam, so the pattern's orientation is O = Rz(phi) M R_b, and the crystal direction along
+# the sample axis e is v = O^T e.
+# ----------------------------------------------------------------------------------
+
+def orientation_vectors(template: np.ndarray, angle_deg: np.ndarray, rot: np.ndarray, K0: int, axis) -> np.ndarray:
+    """template [n] expanded indices (mirror copies at >= K0; < 0: no hit -> NaN), angle_deg
+    [n] (float32 values, used as doubles), rot [K0][3][3], axis e [3] -> v [n][3] float64.
+    Per pattern, with each operation rounded in this order: c = cos(phi), s = sin(phi) with
+    phi = angle * (pi / 180); u = Rz(phi)^T e = (c e0 + s e1, -s e0 + c e1, e2); u1 negated for a
+    mirror copy; v_j = (R[0][j] u0 + R[1][j] u1) + R[2][j] u2."""
+    n = template.shape[0]
+    out = np.full((n, 3), np.nan)
+    e0, e1, e2 = float(axis[0]), float(axis[1]), float(axis[2])
+    for p in range(n):
+        k = int(template[p])
+        if k < 0:
+            continue
+        mirror = k >= K0
+        b = k - K0 if mirror else k
+        phi = float(angle_deg[p]) * (math.pi / 180.0)
+        c, s = math.cos(phi), math.sin(phi)
+        u0 = c * e0 + s * e1
+        u1 = -s * e0 + c * e1
+        u2 = e2
+        if mirror:
+            u1 = -u1
+        R = rot[b]
+        for j in range(3):
+            out[p, j] = (float(R[0, j]) * u0 + float(R[1, j]) * u1) + float(R[2, j]) * u2
+    return out
+
+
+def angular_deviation(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
+    """Eq. 2 per pattern, in degrees: |acos(va . vb / (|va| |vb|))| (the cosine clipped to
+    [-1, 1]); NaN where either vector is missing."""
+    n = va.shape[0]
+    out = np.full(n, np.nan)
+    for p in range(n):
+        a, b = va[p], vb[p]
+        if np.any(np.isnan(a)) or np.any(np.isnan(b)):
+            continue
+        dot = (float(a[0]) * float(b[0]) + float(a[1]) * float(b[1])) + float(a[2]) * float(b[2])
+        na = math.sqrt((float(a[0]) ** 2 + float(a[1]) ** 2) + float(a[2]) ** 2)
+        nb = math.sqrt((float(b[0]) ** 2 + float(b[1]) ** 2) + float(b[2]) ** 2)
+        cosv = max(-1.0, min(1.0, dot / (na * nb)))
+        out[p] = abs(math.degrees(math.acos(cosv)))
+    return out
 
 
 # ----------------------------------------------------------------------------------

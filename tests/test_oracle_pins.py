@@ -512,3 +512,34 @@ def test_kinematic_matches_the_scan_generator():
         assert np.allclose(flat[:, 0], ts.a, rtol=0, atol=1e-13)
         assert np.allclose(flat[:, 1], ts.b, rtol=0, atol=1e-13)
         assert np.allclose(flat[:, 2], ts.intensity, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ orientation maps (Eq. 2)
+
+def test_orientation_vectors_special_cases():
+    """Identity orientation at phi = 0 gives the sample axis itself; a rotation about the
+    beam leaves the beam axis's vector unchanged and turns X into the direction at -phi;
+    a mirror copy flips the y component; a 90 deg tilt about x maps the beam axis to the
+    crystal's -y ... all against the matrices written out by hand."""
+    I = np.eye(3)[None]
+    z = O.orientation_vectors(np.array([0]), np.array([0.0]), I, 1, (0, 0, 1))
+    assert np.array_equal(z[0], [0.0, 0.0, 1.0])
+    v = O.orientation_vectors(np.array([0, 0]), np.array([37.0, 90.0]), I, 1, (0, 0, 1))
+    assert np.allclose(v, [[0, 0, 1], [0, 0, 1]], atol=1e-15)
+    x = O.orientation_vectors(np.array([0]), np.array([90.0]), I, 1, (1, 0, 0))
+    assert np.allclose(x[0], [0.0, -1.0, 0.0], atol=1e-15)                     # Rz(90)^T X
+    y = O.orientation_vectors(np.array([1]), np.array([0.0]), I, 1, (0, 1, 0))   # mirror copy of 0
+    assert np.allclose(y[0], [0.0, -1.0, 0.0], atol=0)
+    c, s = math.cos(math.radians(90)), math.sin(math.radians(90))
+    Rx = np.array([[1, 0, 0], [0, c, -s], [0, s, c]])[None]                     # rows: beam axes in crystal coords
+    w = O.orientation_vectors(np.array([0, -1]), np.array([0.0, 0.0]), Rx, 1, (0, 0, 1))
+    assert np.allclose(w[0], Rx[0].T @ np.array([0, 0, 1.0]), atol=1e-15) and np.all(np.isnan(w[1]))
+
+
+def test_angular_deviation_eq2():
+    """Eq. 2: parallel 0, orthogonal 90, antiparallel 180 degrees, independent of length;
+    a known angle between two unit vectors; missing vectors give NaN."""
+    va = np.array([[1.0, 0, 0], [0, 2.0, 0], [1.0, 1.0, 0], [0, 0, 3.0], [math.cos(0.3), math.sin(0.3), 0], [np.nan] * 3])
+    vb = np.array([[5.0, 0, 0], [0, 0, 1.0], [-1.0, -1.0, 0], [0, 0, 1.0], [1.0, 0, 0], [1.0, 0, 0]])
+    d = O.angular_deviation(va, vb)
+    assert np.allclose(d[:5], [0.0, 90.0, 180.0, 0.0, math.degrees(0.3)], atol=1e-9) and np.isnan(d[5])
