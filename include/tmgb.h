@@ -389,6 +389,21 @@ int tm_kinematic_spots(tm_ctx* ctx, const double* g_dev, const double* f2_dev, c
                        const double* rot_dev, int64_t D, double wavelength, double s_max, int32_t max_spots,
                        int32_t* counts_dev, double* spots_dev, void* stream);
 
+/* Orientation maps (Section 4.1: inverse pole figure maps along the sample axes).  For each
+ * pattern p, hit hits_dev[p * stride] (its best template b, mirror copies at b >= K0, and
+ * in-plane angle phi = angle_deg) gives the orientation O = Rz(phi) M R_b, with rot_dev
+ * [K0][3][3] the templates' orientation matrices (row-major; rows: the beam-frame axes in
+ * crystal coordinates, as tm_kinematic_spots takes them) and M = diag(1, -1, 1) for a mirror
+ * copy, else 1; v_dev [n][3] double receives v = O^T e, the crystal direction along the
+ * sample axis e = (ex, ey, ez).  FP64, each operation rounded in a fixed order (cos and sin
+ * from the math library); NaN for a missing hit (template index < 0).  Asynchronous. */
+int tm_orientation_vectors(tm_ctx* ctx, const tm_hit* hits_dev, int64_t n, int32_t stride, const double* rot_dev,
+                           int64_t K0, double ex, double ey, double ez, double* v_dev, void* stream);
+/* Eq. 2: deg_dev [n] receives |acos(va . vb / (|va| |vb|))| in degrees (the cosine clipped to
+ * [-1, 1]) for the vectors va_dev, vb_dev [n][3] of two maps; NaN where either is missing. */
+int tm_angular_deviation(tm_ctx* ctx, const double* va_dev, const double* vb_dev, int64_t n, double* deg_dev,
+                         void* stream);
+
 /* Default parameters: gamma 0.5, subtract 0, centre NaN, prefilter 1, top_n 5,
  * FP32 sparse path, rescore_k 256, no pixel mask, no threshold. */
 void tm_index_params_default(tm_index_params* p);

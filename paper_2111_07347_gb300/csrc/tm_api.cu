@@ -971,6 +971,33 @@ int tm_kinematic_spots(tm_ctx* ctx, const double* g_dev, const double* f2_dev, c
     return TM_OK;
 }
 
+int tm_orientation_vectors(tm_ctx* ctx, const tm_hit* hits_dev, int64_t n, int32_t stride, const double* rot_dev,
+                           int64_t K0, double ex, double ey, double ez, double* v_dev, void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_orientation_vectors: ctx is NULL");
+    if (n < 0 || stride < 1 || K0 < 1) return fail(TM_ERR_INVALID_ARG, "tm_orientation_vectors: bad sizes");
+    if (!isfinite(ex) || !isfinite(ey) || !isfinite(ez)) return fail(TM_ERR_INVALID_ARG, "tm_orientation_vectors: axis");
+    if (n == 0) return TM_OK;
+    if (!hits_dev || !rot_dev || !v_dev) return fail(TM_ERR_INVALID_ARG, "tm_orientation_vectors: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    TM_CUDA(tmgb::launch_orientation_vectors(hits_dev, n, stride, rot_dev, K0, ex, ey, ez, v_dev, (cudaStream_t)stream),
+            "tm_orientation_vectors: launch");
+    return TM_OK;
+}
+
+int tm_angular_deviation(tm_ctx* ctx, const double* va_dev, const double* vb_dev, int64_t n, double* deg_dev,
+                         void* stream) {
+    if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_angular_deviation: ctx is NULL");
+    if (n < 0) return fail(TM_ERR_INVALID_ARG, "tm_angular_deviation: n < 0");
+    if (n == 0) return TM_OK;
+    if (!va_dev || !vb_dev || !deg_dev) return fail(TM_ERR_INVALID_ARG, "tm_angular_deviation: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    TM_CUDA(tmgb::launch_angular_deviation(va_dev, vb_dev, n, deg_dev, (cudaStream_t)stream),
+            "tm_angular_deviation: launch");
+    return TM_OK;
+}
+
 void tm_index_params_default(tm_index_params* p) {
     if (!p) return;
     p->gamma = 0.5;

@@ -118,6 +118,11 @@ cudaError_t launch_gauss_rows(const void* in, int dtype, int64_t rows, int W, co
 cudaError_t launch_gauss_cols(const float* in1, const float* in2, int64_t n, int H, int W, const float* w1, int r1,
                               const float* w2, int r2, int dog, float* out, cudaStream_t st);
 
+// Orientation maps and Eq. 2 (k_orient.cu).
+cudaError_t launch_orientation_vectors(const tm_hit* hits, int64_t n, int stride, const double* rot, int64_t K0,
+                                       double e0, double e1, double e2, double* v, cudaStream_t st);
+cudaError_t launch_angular_deviation(const double* va, const double* vb, int64_t n, double* deg, cudaStream_t st);
+
 // Template simulation (k_kinematic.cu): counts [D], spots [D][max_spots][3].
 int kinematic_cand_max();
 cudaError_t launch_kinematic(const double* g, const double* f2, const double* gnorm, int64_t G, const double* rot,

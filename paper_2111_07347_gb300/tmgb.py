@@ -130,6 +130,9 @@ _SIGS = {
     "tm_index_params_default": (None, [ctypes.POINTER(tm_index_params)]),
     "tm_find_centres": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P]),
+    "tm_orientation_vectors": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int64,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P]),
+    "tm_angular_deviation": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     "tm_kinematic_spots": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
     "tm_preprocess": (ctypes.c_int, [_P, ctypes.POINTER(tm_preprocess_params), _P, ctypes.c_int32, ctypes.c_int64,
@@ -593,6 +596,27 @@ class Context:
                                          float(cy), float(radius), int(iterations), out.data_ptr(),
                                          _stream_ptr(stream)))
         return out
+
+    def orientation_vectors(self, hits, rot, K0, axis=(0.0, 0.0, 1.0), stream=None):
+        """Crystal direction along the sample axis for each pattern's best hit: hits the
+        [n][top_n][5] int32 device tensor of index(), rot [K0][3][3] float64 device tensor
+        -> float64 [n][3] (NaN where no hit)."""
+        import torch
+        n, top_n = hits.shape[-3], hits.shape[-2]
+        v = torch.empty((n, 3), dtype=torch.float64, device=hits.device)
+        _check(library().tm_orientation_vectors(self.handle, hits.data_ptr(), n, top_n, rot.data_ptr(), int(K0),
+                                                float(axis[0]), float(axis[1]), float(axis[2]), v.data_ptr(),
+                                                _stream_ptr(stream)))
+        return v
+
+    def angular_deviation(self, va, vb, stream=None):
+        """Eq. 2 per pattern in degrees (float64 device tensors [n][3] -> [n])."""
+        import torch
+        n = va.shape[0]
+        d = torch.empty((n,), dtype=torch.float64, device=va.device)
+        _check(library().tm_angular_deviation(self.handle, va.data_ptr(), vb.data_ptr(), n, d.data_ptr(),
+                                              _stream_ptr(stream)))
+        return d
 
     def kinematic_spots(self, g, f2, gnorm, rot, wavelength, s_max, max_spots, stream=None):
         """Reflections kept per orientation (device tensors: g [G][3], f2 [G], gnorm [G], rot

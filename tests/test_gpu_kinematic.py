@@ -82,3 +82,41 @@ def test_kinematic_overflow_is_reported(ctx):
     assert np.all(counts.cpu().numpy() == -1)
     with pytest.raises(tmgb.TmError):
         ctx.kinematic_templates(g, F2, gn, R[:3], synth.WAVELENGTH_200KV, 50.0, 20)
+
+
+def test_orientation_vectors_and_deviation_match_oracle(ctx):
+    """Orientation-map vectors and Eq. 2 on the GPU against the oracle (FP64 with the same
+    operation order; cos, sin and acos from the math libraries, so within 1e-12), for random
+    hits over the FCC grid's orientations, mirror copies and missing hits included."""
+    import torch
+    g, F2, gn, R = _inputs("fcc", "cubic", 3.0)
+    K0 = R.shape[0]
+    rng = np.random.default_rng(8)
+    n, top_n = 500, 3
+    tmpl = rng.integers(0, 2 * K0, size=n)
+    tmpl[::37] = -1
+    ang = (rng.integers(0, 360, size=n) * 1.0 + rng.random(n)).astype(np.float32)
+    hits = np.zeros((n, top_n, 5), dtype=np.int32)
+    hits[:, 0, 0] = tmpl
+    hits[:, 0, 1] = ang.astype(np.int32)
+    hits[:, 0, 3] = ang.view(np.int32)
+    hits[:, 0, 4] = (tmpl >= K0).astype(np.int32)
+    hits[:, 1:, 0] = 5                                                   # rows 1.. are ignored
+    hd = torch.from_numpy(hits).cuda()
+    rd = _dev(R)
+    for axis in ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.0, 0.6, 0.8)):
+        v = ctx.orientation_vectors(hd, rd, K0, axis).cpu().numpy()
+        ref = O.orientation_vectors(tmpl, ang, R, K0, axis)
+        assert np.array_equal(np.isnan(v), np.isnan(ref))
+        ok = ~np.isnan(ref)
+        assert np.allclose(v[ok], ref[ok], rtol=0, atol=1e-12)
+    va = rng.standard_normal((n, 3))
+    vb = va + 0.3 * rng.standard_normal((n, 3))
+    vb[::11] = va[::11] * 2.5                                            # parallel
+    vb[::13] = -va[::13]                                                 # antiparallel
+    va[::17] = np.nan
+    d = ctx.angular_deviation(_dev(va), _dev(vb)).cpu().numpy()
+    dref = O.angular_deviation(va, vb)
+    assert np.array_equal(np.isnan(d), np.isnan(dref))
+    ok = ~np.isnan(dref)
+    assert np.allclose(d[ok], dref[ok], rtol=0, atol=1e-9)
