@@ -288,7 +288,7 @@ def serve_bench(ctx, lib_ids, pool: np.ndarray, path_kw: dict, seconds: float = 
     from paper_2111_07347_gb300 import tmgb
     rng = np.random.default_rng(seed)
     n_pool = pool.shape[0]
-    srv = tmgb.Server(ctx, slots=3, tile_patterns=512, max_libs=len(lib_ids), max_top_n=TOP_N)
+    srv = tmgb.Server(ctx, slots=4, tile_patterns=512, max_libs=len(lib_ids), max_top_n=TOP_N, priority_slots=1)
 
     def submit(n, prio):
         a = int(rng.integers(0, n_pool - n + 1))
@@ -302,7 +302,7 @@ def serve_bench(ctx, lib_ids, pool: np.ndarray, path_kw: dict, seconds: float = 
     cap = 6 * 16384 / (time.perf_counter() - t0)
     mean_line, mean_map = (64 + 512) / 2, (64 * 64 + 128 * 128) / 2
     mean_req = 0.8 * mean_line + 0.2 * mean_map
-    out = {"capacity_patterns_per_s": cap, "slots": 3, "tile_patterns": 512,
+    out = {"capacity_patterns_per_s": cap, "slots": 4, "priority_slots": 1, "tile_patterns": 512,
            "maps": "64^2 and 128^2 only (frame pool of 16384)"}
     for load in (0.25, 0.5, 0.8):
         lam = load * cap / mean_req
@@ -590,11 +590,6 @@ def run_ours(args):
             "macs_per_step_sparse": macs_step, "survivors_per_step": survivors_step,
             "roofline": roofline, "stages": stages, "e2e": e2e,
             "gpu_launches": int(launches_per_step * args.steps), "clocks": clk}
-    if not args.no_two_stage:
-        line["two_stage"] = two_stage_bench(ctx, stream, max(2, args.steps // 2))
-    if not args.no_preprocess:
-        line["preprocess"] = preprocess_bench(ctx, stream, frames_d, max(2, args.steps // 2))
-        line["template_simulation"] = simulation_bench(ctx, stream)
     if not args.no_serving:
         hcp = synth.kinematic_library("hcp")
         lid_h = ctx.load_library(hcp, N_R, N_THETA)
@@ -603,6 +598,11 @@ def run_ours(args):
         line["serving"] = serving
         line["p99_line_ms"] = serving["load_50"].get("line_p99_ms")
         line["serving_workload"] = "FCC + HCP resident, Poisson arrivals, 80 % lines 64-512 / 20 % maps"
+    if not args.no_two_stage:
+        line["two_stage"] = two_stage_bench(ctx, stream, max(2, args.steps // 2))
+    if not args.no_preprocess:
+        line["preprocess"] = preprocess_bench(ctx, stream, frames_d, max(2, args.steps // 2))
+        line["template_simulation"] = simulation_bench(ctx, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ts, scan, args.cpu_seconds)
     if rank == 0:

@@ -429,7 +429,10 @@ typedef struct tm_server_params {
     size_t queue_bytes;           /* admission budget: frame bytes of requests submitted
                                      and not finished; 0 = no limit                       */
     int32_t blocking_submit;      /* 1: submit waits for budget; 0: TM_ERR_BUSY           */
-    int32_t reserved;
+    int32_t priority_slots;       /* of the slots, how many take only requests of priority
+                                     > 0 (scan lines), so that they never wait behind map
+                                     tiles; such tiles also run on high-priority streams;
+                                     default 1 (0 when slots == 1)                         */
 } tm_server_params;
 
 typedef struct tm_request {

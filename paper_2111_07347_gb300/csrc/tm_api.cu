@@ -1413,11 +1413,15 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
         if (rc) return rc;
     }
     const size_t esz = dtype == TM_DTYPE_U16 ? 2 : 4;
+    // the sparse kernel's block size: forced (autotuning), tuned for these libraries, or by
+    // default 256 -- but 512 when the chunk has at most two patterns per SM, so that each
+    // pattern is shared by twice the warps (the latency of small batches such as scan lines)
     int sparse_threads = ctx->tune_override;
     if (!sparse_threads) {
         auto tt = ctx->tuned.find(tune_key(libs, n_libs, N));
         if (tt != ctx->tuned.end()) sparse_threads = tt->second;
     }
+    if (!sparse_threads && std::min(chunk, n) <= 2 * (int64_t)ctx->num_sms) sparse_threads = 512;
     int64_t launches = 0, corr = 0, scored = 0;
     auto enqueue = [&]() -> int {
         for (int64_t c0 = 0; c0 < n; c0 += chunk) {
@@ -1465,6 +1469,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             c.hits = out_dev + (size_t)c0 * N;
             c.hits_lib_stride = n * N;
             c.top_n = N;
+            c.threads = sparse_threads;
             c.work = ctx->profiling ? ctx->d_work : nullptr;
             if (bf16) {
                 {
@@ -1560,7 +1565,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                            dtype, (long long)n, H, W, params->gamma, params->subtract, params->cx, params->cy,
                            params->prefilter_fraction, params->threshold, params->top_n, params->path,
                            params->rescore_k);
-        off += snprintf(key + off, sizeof key - off, "r%d|", params->reserved & ~TM_INDEX_GRAPH);
+        off += snprintf(key + off, sizeof key - off, "r%d|t%d|", params->reserved & ~TM_INDEX_GRAPH, sparse_threads);
         for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);
         tm_ctx::GraphEntry& ge = ctx->graphs[key];
         if (ge.exec && ge.ws_gen == ctx->ws_gen) {

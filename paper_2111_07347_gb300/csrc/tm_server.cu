@@ -10,7 +10,10 @@
 // staged hits into the request's output (which may be pageable memory: a device-to-host
 // copy into pageable memory would block the worker until the slot's kernels finish).  So
 // tiles of different requests overlap on the device (copies of one tile with the kernels
-// of another); frames in pinned memory are copied asynchronously as well.
+// of another); frames in pinned memory are copied asynchronously as well.  The last
+// `priority_slots` slots take only requests of priority > 0 (scan lines), which therefore
+// never wait for a slot held by a map's tile, and tiles of such requests run on the slot's
+// high-priority stream, so their thread blocks are scheduled ahead of a map's as SMs free.
 // Admission: the frame bytes of requests submitted and not finished stay within
 // queue_bytes.  Every wait is bounded by the caller's timeout.
 #include <stdio.h>
@@ -43,6 +46,8 @@ struct Request {
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaStream_t stream_hi = nullptr;   // high-priority stream for tiles of priority > 0
+    bool lines_only = false;            // takes only requests of priority > 0
     cudaEvent_t done = nullptr;
     void* frames = nullptr;      // device staging
     tm_hit* hits = nullptr;      // device [max_libs][tile][max_top_n]
@@ -89,11 +94,12 @@ void finish_locked(tm_server* s, const std::shared_ptr<Request>& r) {
     s->cv_room.notify_all();
 }
 
-// Pick the next tile: highest priority, then submission order.
-std::shared_ptr<Request> pick_locked(tm_server* s) {
+// Pick the next tile: highest priority, then submission order; a slot reserved for scan
+// lines takes only requests of priority > 0.
+std::shared_ptr<Request> pick_locked(tm_server* s, bool lines_only) {
     std::shared_ptr<Request> best;
     for (auto& r : s->pending) {
-        if (r->cancelled || r->next >= r->req.n) continue;
+        if (r->cancelled || r->next >= r->req.n || (lines_only && r->req.priority <= 0)) continue;
         if (!best || r->req.priority > best->req.priority) best = r;
     }
     return best;
@@ -143,8 +149,8 @@ void worker_main(tm_server* s) {
         if (!s->stop && !s->paused) {
             for (auto& sl : s->slots) {
                 if (sl.busy) continue;
-                auto r = pick_locked(s);
-                if (!r) break;
+                auto r = pick_locked(s, sl.lines_only);
+                if (!r) continue;
                 const int64_t m = std::min<int64_t>(s->prm.tile_patterns, r->req.n - r->next);
                 const size_t esz = r->req.dtype == TM_DTYPE_U16 ? 2 : 4;
                 const size_t fb = (size_t)m * r->req.H * r->req.W * esz;
@@ -157,16 +163,17 @@ void worker_main(tm_server* s) {
                 r->tiles_inflight++;
                 if (r->t_first < 0) r->t_first = s->now_ms();
                 int rc = TM_OK;
-                if (cudaMemcpyAsync(sl.frames, src, fb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) rc = TM_ERR_CUDA;
+                const cudaStream_t st = r->req.priority > 0 ? sl.stream_hi : sl.stream;
+                if (cudaMemcpyAsync(sl.frames, src, fb, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = TM_ERR_CUDA;
                 const int N = r->req.params.top_n, L = r->req.n_libs;
                 if (rc == TM_OK)
                     rc = tm_index_patterns(s->ctx, &r->req.params, sl.frames, r->req.dtype, m, r->req.H, r->req.W,
-                                           nullptr, r->libs.data(), L, sl.hits, nullptr, sl.stream);
+                                           nullptr, r->libs.data(), L, sl.hits, nullptr, st);
                 if (rc == TM_OK && cudaMemcpyAsync(sl.hits_host, sl.hits, (size_t)L * m * N * sizeof(tm_hit),
-                                                   cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                                                   cudaMemcpyDeviceToHost, st) != cudaSuccess)
                     rc = TM_ERR_CUDA;
                 if (rc != TM_OK && r->status == TM_OK) r->status = rc;
-                cudaEventRecord(sl.done, sl.stream);
+                cudaEventRecord(sl.done, st);
                 dispatched = true;
             }
         }
@@ -197,6 +204,7 @@ void tm_server_params_default(tm_server_params* p) {
     p->max_top_n = 5;
     p->queue_bytes = 0;
     p->blocking_submit = 1;
+    p->priority_slots = 1;
 }
 
 int tm_server_create(tm_ctx* ctx, const tm_server_params* params, tm_server** out) {
@@ -205,7 +213,8 @@ int tm_server_create(tm_ctx* ctx, const tm_server_params* params, tm_server** ou
     if (params) p = *params;
     else tm_server_params_default(&p);
     if (p.slots < 1 || p.slots > 16 || p.tile_patterns < 1 || p.max_H < 1 || p.max_W < 1 || p.max_libs < 1 ||
-        p.max_libs > TM_MAX_LIBS || p.max_top_n < 1 || p.max_top_n > TM_MAX_TOPN)
+        p.max_libs > TM_MAX_LIBS || p.max_top_n < 1 || p.max_top_n > TM_MAX_TOPN || p.priority_slots < 0 ||
+        (p.priority_slots >= p.slots && p.slots > 1) || (p.slots == 1 && p.priority_slots > 0))
         return sfail(TM_ERR_INVALID_ARG, "tm_server_create: bad parameters");
     auto s = std::make_unique<tm_server>();
     s->ctx = ctx;
@@ -213,8 +222,12 @@ int tm_server_create(tm_ctx* ctx, const tm_server_params* params, tm_server** ou
     s->t0 = std::chrono::steady_clock::now();
     if (cudaGetDevice(&s->device) != cudaSuccess) return sfail(TM_ERR_CUDA, "tm_server_create: no device");
     s->slots.resize(p.slots);
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    for (int i = 0; i < p.slots; ++i) s->slots[i].lines_only = i >= p.slots - p.priority_slots;
     for (auto& sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc(&sl.frames, (size_t)p.tile_patterns * p.max_H * p.max_W * 4) != cudaSuccess ||
             cudaMalloc(&sl.hits, (size_t)p.max_libs * p.tile_patterns * p.max_top_n * sizeof(tm_hit)) != cudaSuccess ||
@@ -227,6 +240,7 @@ int tm_server_create(tm_ctx* ctx, const tm_server_params* params, tm_server** ou
                 if (x.hits_host) cudaFreeHost(x.hits_host);
                 if (x.done) cudaEventDestroy(x.done);
                 if (x.stream) cudaStreamDestroy(x.stream);
+                if (x.stream_hi) cudaStreamDestroy(x.stream_hi);
             }
             return sfail(TM_ERR_OOM, "tm_server_create: staging allocation failed");
         }
@@ -317,11 +331,13 @@ void tm_server_destroy(tm_server* s) {
     if (s->worker.joinable()) s->worker.join();
     for (auto& sl : s->slots) {
         cudaStreamSynchronize(sl.stream);
+        cudaStreamSynchronize(sl.stream_hi);
         cudaFree(sl.frames);
         cudaFree(sl.hits);
         cudaFreeHost(sl.hits_host);
         cudaEventDestroy(sl.done);
         cudaStreamDestroy(sl.stream);
+        cudaStreamDestroy(sl.stream_hi);
     }
     delete s;
 }

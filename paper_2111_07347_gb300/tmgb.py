@@ -72,7 +72,8 @@ class tm_stats(ctypes.Structure):
 class tm_server_params(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("tile_patterns", ctypes.c_int32), ("max_H", ctypes.c_int32),
                 ("max_W", ctypes.c_int32), ("max_libs", ctypes.c_int32), ("max_top_n", ctypes.c_int32),
-                ("queue_bytes", ctypes.c_size_t), ("blocking_submit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("queue_bytes", ctypes.c_size_t), ("blocking_submit", ctypes.c_int32),
+                ("priority_slots", ctypes.c_int32)]
 
 
 class tm_request(ctypes.Structure):
@@ -403,10 +404,11 @@ class Server:
     """Serving loop over a Context: host frames in, host hits out (see tm_server_* in tmgb.h)."""
 
     def __init__(self, ctx: "Context", slots=3, tile_patterns=512, max_H=256, max_W=256, max_libs=2, max_top_n=5,
-                 queue_bytes=0, blocking_submit=True):
+                 queue_bytes=0, blocking_submit=True, priority_slots=None):
         p = tm_server_params_default()
         p.slots, p.tile_patterns, p.max_H, p.max_W = slots, tile_patterns, max_H, max_W
         p.max_libs, p.max_top_n, p.queue_bytes, p.blocking_submit = max_libs, max_top_n, queue_bytes, int(blocking_submit)
+        p.priority_slots = (1 if slots > 1 else 0) if priority_slots is None else priority_slots
         self.ctx = ctx
         self.handle = tm_server_create(ctx.handle, p)
         self._keep = {}

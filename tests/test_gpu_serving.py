@@ -128,3 +128,20 @@ def test_rejects_requests_beyond_limits(env):
         srv.submit(np.ascontiguousarray(frames[:4]), [la], top_n=3)
     assert e.value.code == tmgb.TM_ERR_INVALID_ARG
     srv.close()
+
+
+def test_scan_lines_do_not_wait_for_map_tiles(env):
+    """With a slot reserved for requests of priority > 0, a scan line submitted behind two
+    maps (whose tiles fill the other slot) finishes before them, with the same hits as a
+    direct call."""
+    ctx, la, lb, frames = env
+    srv = tmgb.Server(ctx, slots=2, tile_patterns=128, max_libs=2, priority_slots=1)
+    maps = [srv.submit(np.ascontiguousarray(frames[:1500]), [la, lb], top_n=5, priority=0) for _ in range(2)]
+    line = np.ascontiguousarray(frames[10:138])
+    t = srv.submit(line, [la, lb], top_n=5, priority=1)
+    out, st_line = srv.wait(t, timeout_ms=60000)
+    st_maps = [srv.wait(m, timeout_ms=120000)[1] for m in maps]
+    assert st_line["status"] == tmgb.TM_OK and all(s["status"] == tmgb.TM_OK for s in st_maps)
+    assert st_line["done_ms"] < min(s["done_ms"] for s in st_maps)
+    assert np.array_equal(out, _direct(ctx, line, [la, lb], top_n=5))
+    srv.close()
