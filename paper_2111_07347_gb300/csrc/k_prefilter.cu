@@ -11,11 +11,12 @@
 // full-length product, whose other terms add exact zeros.  One CTA takes PB patterns: it
 // forms their scores in shared memory (the library's rows are read once for PB patterns)
 // and selects from there, so the scores need not reach global memory.  The selection is
-// exact: a radix select over order-preserving integer keys whose 8-bit digits start at the
-// highest bit in which the pattern's keys differ (cosine scores share their sign and most
-// exponent bits), stopping early once every key of the bin that holds the boundary is kept.
-// The keys' range comes with the scores; one warp finds each digit's bin from per-lane bin
-// counts held in registers; in the first pass, lanes that share a bin are counted together.
+// exact: a radix select over order-preserving integer keys whose digits (up to 11 bits)
+// start at the highest bit in which the pattern's keys differ (cosine scores share their sign
+// and most exponent bits; the keys' range comes with the scores).  One warp finds each digit's
+// bin by a two-level scan of the histogram; the passes stop once every key of the boundary's
+// bin is kept or the bin holds at most 256 keys, which one warp then finishes bit by bit in
+// registers over the bits in which they differ.
 #include "tm_internal.h"
 
 namespace tmgb {
