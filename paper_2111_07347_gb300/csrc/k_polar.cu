@@ -5,14 +5,17 @@
 // pre-filter (Section 2.2, Fig. 3).
 //
 // One CTA per pattern (grid-stride over patterns).  The CTA's threads form R row groups of
-// `cols` threads (a multiple of 32); thread (g, k0) owns polar columns k0, k0 + cols, ... of
-// rows g, g + R, ..., four rows at a time, so the stores of a row are coalesced and four
-// samples are in flight per thread.
+// `cols` threads (a multiple of 32).  A warp samples a patch of 8 consecutive angles by 4
+// consecutive rows (lane = 8 sub + kl): the warp-in-group wg, lane (sub, kl) of group g owns
+// columns 8 wg + kl, 8 wg + kl + cols / 4, ... of rows sub + 4 g, sub + 4 (g + R), ..., four
+// rows at a time, so four samples are in flight per thread and a store writes 32-byte runs.
 //
 // Staged form (frame fits in shared memory): the CTA first copies the frame into shared
-// memory with 16-byte global loads; rows are padded to an odd number of 32-bit words, so
-// samples on an arc (same x, different y) fall in different banks.  Otherwise the taps
-// are read from global memory.
+// memory with 16-byte global loads.  The taps of a warp's patch cover a small 2-D region of
+// the frame; rows are padded to 9 (mod 32) 32-bit words, which puts such regions' words in
+// distinct banks more often than a plain odd pitch (whose banks repeat every two pixels along
+// one diagonal direction): 1.5 instead of 2.7 shared-memory wavefronts per tap load on a
+// 256 x 256 frame.  Otherwise the taps are read from global memory.
 //
 // Tap positions come from fixed-point ray stepping: along the ray of angle theta_k the
 // sample of row j sits at x = cx + j dr cos(theta_k), kept as a signed 32.32 fixed-point
@@ -20,17 +23,19 @@
 // precision (one pair per angle, 16 B, instead of a table entry per sample).  The integer
 // part of X is the tap column x0; the top 23 bits of the fraction (rounded, the carry
 // going into x0) give the bilinear weight exactly: with y = 1 + q 2^-23 (formed by bit
-// assembly), fx = y - 1 and 1 - fx = 2 - y are both exact.  The position error is at most
-// (j + 1) 2^-33 px before the rounding to 23 bits, each weight within 2^-24 (+ that) of
-// the double-precision value.  A per-pattern centre enters only through CX, converted
-// exactly from its float value.  A sample whose four taps are all inside the frame takes
-// a fast path with one bounds test and the subtraction applied once (the weights sum to
-// exactly 1); edge samples test each tap (zero outside).
+// assembly), fx = y - 1 is exact, and the sample is formed as interpolations a + fx (b - a).
+// The position error is at most (j + 1) 2^-33 px before the rounding to 23 bits, each weight
+// within 2^-24 (+ that) of the double-precision value.  A per-pattern centre enters only
+// through CX, converted exactly from its float value.  A sample whose four taps are all
+// inside the frame takes a fast path with one bounds test; edge samples test each tap (zero
+// outside).
 // For u16 frames the gamma of the pixel values below 4096 (all of them at the counts of an
 // electron diffraction pattern) is tabulated once per CTA in shared memory, g(v) - c from
 // the same correctly rounded sqrtf / powf, so a tap is one table read; larger values are
 // computed directly.  The staging notes whether any pixel of the frame is that large, and
 // frames without one take a path with no per-tap range test.
+// The norm's squares are added four at a time (one sample per row of a batch), then into the
+// thread's compensated (Kahan) sum.
 // Reductions run in a fixed order: the result does not depend on the grid size or on
 // other patterns of the batch.
 #include <math.h>
@@ -109,20 +114,21 @@ __device__ __forceinline__ bool all_in_lut(uint16_t a, uint16_t b, uint16_t c, u
 }
 __device__ __forceinline__ bool all_in_lut(float, float, float, float) { return false; }
 
-// Weights (f, 1 - f) from the 23-bit fixed-point fraction q (q < 2^23): both exact.
-__device__ __forceinline__ void fixed_weights(uint32_t q, float& f, float& g) {
-    const float y = __uint_as_float(0x3F800000u | q);       // 1 + q 2^-23
-    f = y - 1.0f;
-    g = 2.0f - y;
+// Weight f = q 2^-23 from the 23-bit fixed-point fraction q (q < 2^23), exact.
+__device__ __forceinline__ float fixed_weight(uint32_t q) {
+    return __uint_as_float(0x3F800000u | q) - 1.0f;          // (1 + q 2^-23) - 1
 }
+
+// a + f (b - a): the interpolation between two taps.
+__device__ __forceinline__ float lerp(float a, float b, float f) { return fmaf(f, b - a, a); }
 
 // Bilinear sample of the gamma-corrected, subtracted frame at (x0 + fx, y0 + fy); the frame
 // has row pitch `pitch` elements; taps outside [0, W) x [0, H) contribute zero.
-// CHECK = false: the caller knows that all four taps lie inside the frame.
+// CHECK = false: the caller knows that all four taps lie inside the frame.  LUT_ONLY: every
+// pixel of the frame is below the gamma table's end.
 template <typename T, int MODE, bool SMEM, bool LUT_ONLY, bool CHECK>
 __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int W, int x0, int y0, float fx,
-                                          float gx, float fy, float gy, const float* lut, float2 g, float sub,
-                                          const uint8_t* pmask) {
+                                          float fy, const float* lut, float2 g, float sub, const uint8_t* pmask) {
     if (!CHECK || ((unsigned)x0 < (unsigned)(W - 1) && (unsigned)y0 < (unsigned)(H - 1))) {
         const T* p = frame + y0 * pitch + x0;
         const T a = load_px_masked<SMEM>(p, frame, pmask), b = load_px_masked<SMEM>(p + 1, frame, pmask);
@@ -139,31 +145,32 @@ __device__ __forceinline__ float bilinear(const T* frame, int pitch, int H, int 
             v01 = tap_value<MODE>(c, lut, g, sub);
             v11 = tap_value<MODE>(d, lut, g, sub);
         }
-        return gy * (gx * v00 + fx * v10) + fy * (gx * v01 + fx * v11);
+        return lerp(lerp(v00, v10, fx), lerp(v01, v11, fx), fy);
     }
     float v[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         const int x = x0 + (t & 1), y = y0 + (t >> 1);
         v[t] = 0.0f;
-        if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H)
-            v[t] = tap_value<MODE>(load_px_masked<SMEM>(frame + y * pitch + x, frame, pmask), lut, g, sub);
+        if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H) {
+            const T raw = load_px_masked<SMEM>(frame + y * pitch + x, frame, pmask);
+            v[t] = LUT_ONLY ? lut[(int)raw] : tap_value<MODE>(raw, lut, g, sub);
+        }
     }
-    return gy * (gx * v[0] + fx * v[1]) + fy * (gx * v[2] + fx * v[3]);
+    return lerp(lerp(v[0], v[1], fx), lerp(v[2], v[3], fx), fy);
 }
 
-// Sum of a[u] over the 32 lanes for four rows u at once (6 shuffles instead of 20): after
-// the exchange the lanes 8u hold the total of row u.  Fixed order: deterministic.
-__device__ __forceinline__ float warp_sum4(const float a[4], int lane) {
-    const bool hi = lane & 16;
-    const float b0 = (hi ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, hi ? a[0] : a[2], 16);
-    const float b1 = (hi ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, hi ? a[1] : a[3], 16);
-    const bool h8 = lane & 8;
-    float c = (h8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h8 ? b0 : b1, 8);
-    c += __shfl_xor_sync(0xffffffffu, c, 4);
-    c += __shfl_xor_sync(0xffffffffu, c, 2);
+// Sum of a[u] over the 8 lanes of each group of eight (lanes 8 sub .. 8 sub + 7) for four
+// values u at once (4 shuffles instead of 12): afterwards the even lanes kl of a group hold
+// the total of u = 2 ((kl >> 2) & 1) + ((kl >> 1) & 1).  Fixed order: deterministic.
+__device__ __forceinline__ float group8_sum4(const float a[4], int lane) {
+    const bool h4 = lane & 4;
+    const float b0 = (h4 ? a[2] : a[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a[0] : a[2], 4);
+    const float b1 = (h4 ? a[3] : a[1]) + __shfl_xor_sync(0xffffffffu, h4 ? a[1] : a[3], 4);
+    const bool h2 = lane & 2;
+    float c = (h2 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h2 ? b0 : b1, 2);
     c += __shfl_xor_sync(0xffffffffu, c, 1);
-    return c;                                   // row (lane >> 3) when (lane & 7) == 0
+    return c;
 }
 
 constexpr long long kRound = 1ll << 8;     // half of the last kept fraction bit (2^-24 of a pixel)
@@ -172,11 +179,9 @@ constexpr long long kRound = 1ll << 8;     // half of the last kept fraction bit
 template <typename T, int MODE, bool STAGED, bool LUT_ONLY, bool CHECK>
 __device__ __forceinline__ float sample_at(const T* frame, int pitch, int H, int W, long long X, long long Y,
                                           const float* lut, float2 g, float sub, const uint8_t* pmask) {
-    float fx, gx, fy, gy;
-    fixed_weights((uint32_t)X >> 9, fx, gx);
-    fixed_weights((uint32_t)Y >> 9, fy, gy);
-    return bilinear<T, MODE, STAGED, LUT_ONLY, CHECK>(frame, pitch, H, W, (int)(X >> 32), (int)(Y >> 32), fx, gx, fy,
-                                                     gy, lut, g, sub, pmask);
+    return bilinear<T, MODE, STAGED, LUT_ONLY, CHECK>(frame, pitch, H, W, (int)(X >> 32), (int)(Y >> 32),
+                                                     fixed_weight((uint32_t)X >> 9), fixed_weight((uint32_t)Y >> 9),
+                                                     lut, g, sub, pmask);
 }
 
 // Whether the four taps of a sample at fixed-point (X, Y) lie inside the frame.
@@ -187,29 +192,46 @@ __device__ __forceinline__ bool taps_inside(long long X, long long Y, int H, int
 constexpr int kMaxThreads = 768;            // 80 registers per thread at one CTA per SM
 
 // One column of the thread's rows (batches of four), from the fixed-point position (X, Y) of
-// its first row and the step (SX, SY) between its rows.  keepm: bit i set when the thread's
-// i-th row is stored (rows past 64 read keep_row).  CHECK = false when the whole column lies
-// inside the frame.
+// its first row row0 and the step (SX, SY) to its next row (rows row0, row0 + rstep, ...).
+// my_rows: the lane's rows; wrows: the most rows of a lane of the warp (the loop bound, so
+// the loop is warp-uniform).  keepm: bit i set when the lane's i-th row is stored (rows past
+// 64 read keep_row).  CHECK = false when the whole column lies inside the frame.
 template <typename T, int MODE, bool STAGED, bool LUT_ONLY, bool CHECK>
 __device__ __forceinline__ void polar_column(const T* frame, int pf, int H, int W, long long X, long long Y,
-                                             long long SX, long long SY, int k, bool active, int my_rows, int grp,
-                                             int R, int n_theta, int lane, int warp, int nw, int kk,
+                                             long long SX, long long SY, int k, bool active, int my_rows, int wrows,
+                                             int row0, int rstep, int n_theta, int lane, int warp, int nw, int kk,
                                              unsigned long long keepm, const uint8_t* __restrict__ keep_row,
                                              const uint8_t* pmask, const float* lut, float2 g, float sub,
                                              float* __restrict__ out, float* part, float& s2, float& c2) {
-    for (int b = 0; b < my_rows; b += 4) {                              // warp-uniform
-        const int nu = my_rows - b;                                     // rows left in this batch (>= 1)
-        const int j0 = grp + R * b;
+    for (int b = 0; b < wrows; b += 4) {                                // warp-uniform
+        const int nu = my_rows - b;                                     // this lane's rows left (may be <= 0)
+        const int j0 = row0 + rstep * b;
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (active) {
-            unsigned kb = (unsigned)(keepm >> b) & 15u;                 // rows of the batch that are stored
-            if (b + 4 > 64) {
+        if (active && nu > 0) {
+            unsigned kb;                                                // rows of the batch that are stored
+            if (b + 4 <= 64) {
+                kb = (unsigned)(keepm >> b) & 15u;
+            } else {
                 kb = 0u;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (u < nu && (!keep_row || keep_row[j0 + R * u])) kb |= 1u << u;
+                    if (u < nu && (!keep_row || keep_row[j0 + rstep * u])) kb |= 1u << u;
             }
             float v[4];
+            // stores of the kept rows, the row sums' inputs, and the batch's squares (zeros past
+            // the lane's rows) added to the norm in one compensated step
+            auto tail = [&]() {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if ((kb >> u) & 1u) out[(size_t)(j0 + rstep * u) * n_theta + k] = v[u];
+                    acc[u] = v[u];
+                }
+                const float q = fmaf(v[3], v[3], fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0])));
+                const float y = q - c2;
+                const float t = s2 + y;
+                c2 = (t - s2) - y;
+                s2 = t;
+            };
             if (nu >= 4) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -217,15 +239,7 @@ __device__ __forceinline__ void polar_column(const T* frame, int pf, int H, int 
                     X += SX;
                     Y += SY;
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if ((kb >> u) & 1u) out[(size_t)(j0 + R * u) * n_theta + k] = v[u];
-                    const float y = fmaf(v[u], v[u], -c2);
-                    const float t = s2 + y;
-                    c2 = (t - s2) - y;
-                    s2 = t;
-                    acc[u] = v[u];
-                }
+                tail();
             } else {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -235,63 +249,105 @@ __device__ __forceinline__ void polar_column(const T* frame, int pf, int H, int 
                     X += SX;
                     Y += SY;
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (u < nu) {
-                        if ((kb >> u) & 1u) out[(size_t)(j0 + R * u) * n_theta + k] = v[u];
-                        const float y = fmaf(v[u], v[u], -c2);
-                        const float t = s2 + y;
-                        c2 = (t - s2) - y;
-                        s2 = t;
-                        acc[u] = v[u];
-                    }
-                }
+                tail();
             }
         }
-        const float r = warp_sum4(acc, lane);
-        const int u = lane >> 3;
-        if ((lane & 7) == 0 && u < nu) {
-            float* dst = part + (j0 + R * u) * nw + warp;
+        const float r = group8_sum4(acc, lane);
+        const int kl = lane & 7;
+        const int u = ((kl >> 2) & 1) * 2 + ((kl >> 1) & 1);          // the value this lane's sum is of
+        if ((kl & 1) == 0 && u < nu) {
+            float* dst = part + (j0 + rstep * u) * nw + warp;
             *dst = kk ? *dst + r : r;
         }
     }
 }
 
-// The polar rows of one pattern: thread (grp, k0) takes columns k0, k0 + cols, ... of rows
-// grp, grp + R, ..., four rows at a time.  Stores the kept rows, adds P'^2 to the thread's
+// The polar rows of one pattern: the lane takes columns k0, k0 + kstep, ... of rows row0,
+// row0 + rstep, ..., four rows at a time.  Stores the kept rows, adds P'^2 to the thread's
 // Kahan sum and leaves each row's partial sums per warp in part[row][warp].
 template <typename T, int MODE, bool STAGED, bool LUT_ONLY>
 __device__ __forceinline__ void polar_rows(const T* frame, int pf, int H, int W, long long cxb, long long cyb,
-                                           const longlong2* __restrict__ rays, int n_r, int n_theta, int R,
-                                           int cols, int grp, int k0, int lane, int warp, int nw,
+                                           const longlong2* __restrict__ rays, int n_r, int n_theta, int row0,
+                                           int rstep, int wrows, int kstep, int k0, int lane, int warp, int nw,
                                            unsigned long long keepm, const uint8_t* __restrict__ keep_row,
                                            const uint8_t* pmask, const float* lut, float2 g, float sub,
                                            float* __restrict__ out, float* part, float& s2, float& c2) {
-    const int my_rows = grp < n_r ? (n_r - grp + R - 1) / R : 0;        // rows grp, grp + R, ... (warp-uniform)
-    for (int kk = 0; kk < n_theta; kk += cols) {                        // block-uniform
+    const int my_rows = row0 < n_r ? (n_r - row0 + rstep - 1) / rstep : 0;
+    for (int kk = 0; kk < n_theta; kk += kstep) {                       // block-uniform
         const int k = kk + k0;
         const bool active = k < n_theta;
         long long X = cxb, Y = cyb, SX = 0, SY = 0;
         bool inside = true;
         if (active) {
             const longlong2 d = __ldg(rays + k);
-            X += (long long)grp * d.x;
-            Y += (long long)grp * d.y;
-            SX = (long long)R * d.x;
-            SY = (long long)R * d.y;
+            X += (long long)row0 * d.x;
+            Y += (long long)row0 * d.y;
+            SX = (long long)rstep * d.x;
+            SY = (long long)rstep * d.y;
             // the column is a segment, so its samples are inside when both ends are
             const long long last = my_rows > 0 ? (long long)(my_rows - 1) : 0;
             inside = taps_inside(X, Y, H, W) && taps_inside(X + last * SX, Y + last * SY, H, W);
         }
         if (__all_sync(0xffffffffu, inside))
-            polar_column<T, MODE, STAGED, LUT_ONLY, false>(frame, pf, H, W, X, Y, SX, SY, k, active, my_rows, grp, R,
-                                                           n_theta, lane, warp, nw, kk, keepm, keep_row, pmask, lut,
-                                                           g, sub, out, part, s2, c2);
+            polar_column<T, MODE, STAGED, LUT_ONLY, false>(frame, pf, H, W, X, Y, SX, SY, k, active, my_rows, wrows,
+                                                           row0, rstep, n_theta, lane, warp, nw, kk, keepm, keep_row,
+                                                           pmask, lut, g, sub, out, part, s2, c2);
         else
-            polar_column<T, MODE, STAGED, LUT_ONLY, true>(frame, pf, H, W, X, Y, SX, SY, k, active, my_rows, grp, R,
-                                                          n_theta, lane, warp, nw, kk, keepm, keep_row, pmask, lut, g,
-                                                          sub, out, part, s2, c2);
+            polar_column<T, MODE, STAGED, LUT_ONLY, true>(frame, pf, H, W, X, Y, SX, SY, k, active, my_rows, wrows,
+                                                          row0, rstep, n_theta, lane, warp, nw, kk, keepm, keep_row,
+                                                          pmask, lut, g, sub, out, part, s2, c2);
     }
+}
+
+// Copies one frame into shared memory (row pitch `pitch` elements), masked pixels as 0, and
+// returns the OR of the staged 32-bit words (u16: whether a pixel reaches the gamma table's
+// end).
+template <typename T>
+__device__ __forceinline__ uint32_t stage_frame(const T* __restrict__ gframe, T* sF, int H, int W, int pitch,
+                                                const uint8_t* __restrict__ pmask) {
+    uint32_t hi_bits = 0;
+    const bool vec = (((uintptr_t)gframe) & 15) == 0 && (W * sizeof(T)) % 16 == 0;
+    if (vec) {
+        const int vr = (int)(W * sizeof(T) / 16);           // 16-byte vectors per row
+        const int nv = H * vr;
+        const uint4* src = (const uint4*)gframe;
+        constexpr int B = 8;                                // loads in flight per thread
+        for (int i0 = threadIdx.x; i0 < nv; i0 += B * blockDim.x) {
+            uint4 v[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = i0 + b * blockDim.x;
+                if (i < nv) {
+                    v[b] = __ldg(src + i);
+                    if (pmask) {
+                        if (sizeof(T) == 2) mask_vector(v[b], pmask, i);
+                        else mask_vector4(v[b], pmask, i);
+                    }
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int i = i0 + b * blockDim.x;
+                if (i < nv) {
+                    const int y = i / vr, xv = i - y * vr;
+                    uint32_t* d = (uint32_t*)(sF + (size_t)y * pitch) + xv * 4;
+                    d[0] = v[b].x;
+                    d[1] = v[b].y;
+                    d[2] = v[b].z;
+                    d[3] = v[b].w;
+                    hi_bits |= v[b].x | v[b].y | v[b].z | v[b].w;
+                }
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
+            const int y = e / W;
+            const T v = (!pmask || pmask[e]) ? gframe[e] : T(0);
+            sF[(size_t)y * pitch + (e - y * W)] = v;
+            if (sizeof(T) == 2) hi_bits |= (uint32_t)v;
+        }
+    }
+    return hi_bits;
 }
 
 template <typename T, int MODE, bool STAGED>
@@ -302,18 +358,23 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
              float* __restrict__ pnorm, float* __restrict__ radial, const float2* __restrict__ centres) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int cols = blockDim.x / R;                     // threads per row group (multiple of 32)
-    const int grp = threadIdx.x / cols, k0 = threadIdx.x - grp * cols;
+    const int grp = threadIdx.x / cols, t_in = threadIdx.x - grp * cols;
     const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the warp's patch: 8 angles (lane & 7) by 4 rows (lane >> 3)
+    const int k0 = 8 * (t_in >> 5) + (lane & 7), kstep = cols >> 2;
+    const int row0 = (lane >> 3) + 4 * grp, rstep = 4 * R;
+    const int wrows = 4 * grp < n_r ? (n_r - 4 * grp + rstep - 1) / rstep : 0;   // lane sub = 0: the most
     const size_t fbytes = STAGED ? (size_t)H * pitch * sizeof(T) : 0;
     constexpr bool kHasLut = sizeof(T) == 2;
     // rows of this thread that are stored (its first 64 rows; later ones read keep_row)
     unsigned long long keepm = 0ull;
-    if (grp < n_r) {
-        const int my_rows = (n_r - grp + R - 1) / R;
+    if (row0 < n_r) {
+        const int my_rows = (n_r - row0 + rstep - 1) / rstep;
         for (int i = 0; i < my_rows && i < 64; ++i)
-            if (!keep_row || keep_row[grp + R * i]) keepm |= 1ull << i;
+            if (!keep_row || keep_row[row0 + rstep * i]) keepm |= 1ull << i;
     }
+    // the gamma table first (offset 0), so that a staged table offset addresses it directly
     T* sF = (T*)smem_raw;
     float* lut = (float*)(smem_raw + ((fbytes + 15) & ~(size_t)15));   // [kLut] for u16 frames
     float* part = lut + (kHasLut ? kLut : 0);                           // [n_r][nw]
@@ -332,48 +393,7 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
         bool big = true;                                 // some pixel may lie beyond the gamma table
         if (STAGED) {
             __syncthreads();                             // previous pattern's reads are done
-            uint32_t hi_bits = 0;                        // OR of the staged u16 words, above the table
-            const bool vec = (((uintptr_t)gframe) & 15) == 0 && (W * sizeof(T)) % 16 == 0;
-            if (vec) {
-                const int vr = (int)(W * sizeof(T) / 16);           // 16-byte vectors per row
-                const int nv = H * vr;
-                const uint4* src = (const uint4*)gframe;
-                constexpr int B = 8;                                // loads in flight per thread
-                for (int i0 = threadIdx.x; i0 < nv; i0 += B * blockDim.x) {
-                    uint4 v[B];
-#pragma unroll
-                    for (int b = 0; b < B; ++b) {
-                        const int i = i0 + b * blockDim.x;
-                        if (i < nv) {
-                            v[b] = __ldg(src + i);
-                            if (pmask) {
-                                if (sizeof(T) == 2) mask_vector(v[b], pmask, i);
-                                else mask_vector4(v[b], pmask, i);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int b = 0; b < B; ++b) {
-                        const int i = i0 + b * blockDim.x;
-                        if (i < nv) {
-                            const int y = i / vr, xv = i - y * vr;
-                            uint32_t* d = (uint32_t*)(sF + (size_t)y * pitch) + xv * 4;
-                            d[0] = v[b].x;
-                            d[1] = v[b].y;
-                            d[2] = v[b].z;
-                            d[3] = v[b].w;
-                            hi_bits |= v[b].x | v[b].y | v[b].z | v[b].w;
-                        }
-                    }
-                }
-            } else {
-                for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
-                    const int y = e / W;
-                    const T v = (!pmask || pmask[e]) ? gframe[e] : T(0);
-                    sF[(size_t)y * pitch + (e - y * W)] = v;
-                    if (kHasLut) hi_bits |= (uint32_t)v;
-                }
-            }
+            const uint32_t hi_bits = stage_frame<T>(gframe, sF, H, W, pitch, pmask);
             // u16 words: a pixel >= kLut sets a bit of 0xF000 in its half
             big = __syncthreads_or(kHasLut ? (hi_bits & 0xF000F000u) != 0 : 1) != 0;
             frame = sF;
@@ -388,11 +408,13 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
         const int pf = STAGED ? pitch : W;
         float s2 = 0.0f, c2 = 0.0f;                      // Kahan sum of P'^2 for this thread
         if (kHasLut && STAGED && !big)
-            polar_rows<T, MODE, STAGED, true>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, R, cols, grp, k0, lane,
-                                              warp, nw, keepm, keep_row, pmask, lut, g, sub, out, part, s2, c2);
+            polar_rows<T, MODE, STAGED, true>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, row0, rstep, wrows, kstep,
+                                              k0, lane, warp, nw, keepm, keep_row, pmask, lut, g, sub, out, part, s2,
+                                              c2);
         else
-            polar_rows<T, MODE, STAGED, false>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, R, cols, grp, k0, lane,
-                                               warp, nw, keepm, keep_row, pmask, lut, g, sub, out, part, s2, c2);
+            polar_rows<T, MODE, STAGED, false>(frame, pf, H, W, cx, cy, rays, n_r, n_theta, row0, rstep, wrows,
+                                               kstep, k0, lane, warp, nw, keepm, keep_row, pmask, lut, g, sub, out,
+                                               part, s2, c2);
         red[threadIdx.x] = s2;
         __syncthreads();
         // fixed-order tree over the block (blockDim is a multiple of 32)
@@ -403,10 +425,10 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
         }
         if (threadIdx.x == 0 && pnorm) pnorm[p] = sqrtf(red[0]);
         if (radial) {
-            // row j's partials come from the warps of group j % R only
+            // row j's partials come from the warps of group (j / 4) % R only
             const int wpg = cols >> 5;
             for (int j = threadIdx.x; j < n_r; j += blockDim.x) {
-                const int g0 = j % R;
+                const int g0 = (j >> 2) % R;
                 float s = 0.0f;
                 for (int w = 0; w < wpg; ++w) s += part[j * nw + g0 * wpg + w];
                 radial[(size_t)p * n_r + j] = s;
@@ -448,16 +470,20 @@ cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const longlon
                          cudaStream_t st, const uint8_t* keep_row, const float2* centres, const uint8_t* pmask) {
     const int cols = ((n_theta + 31) / 32) * 32;
     if (cols <= kMaxThreads) {
-        // staged: rows padded to an odd number of 32-bit words
-        int words = (int)((W * sizeof(T) + 3) / 4);
-        if (words % 2 == 0) ++words;
-        const int pitch = (int)(words * 4 / sizeof(T));
+        // staged: rows padded to 9 (mod 32) 32-bit words, else (if that does not fit) to an
+        // odd number
+        const int words = (int)((W * sizeof(T) + 3) / 4);
         const int R = std::max(1, std::min(4, kMaxThreads / cols));
         const int threads = R * cols;
         const int nw = threads / 32;
-        const size_t fbytes = ((size_t)H * pitch * sizeof(T) + 15) & ~(size_t)15;
         const size_t lut = sizeof(T) == 2 ? kLut * sizeof(float) : 0;
-        const size_t smem = fbytes + lut + ((size_t)n_r * nw + threads) * sizeof(float);
+        auto smem_of = [&](int pw) {
+            return (((size_t)H * pw * 4 + 15) & ~(size_t)15) + lut + ((size_t)n_r * nw + threads) * sizeof(float);
+        };
+        int pw = words + ((9 - words % 32) + 32) % 32;
+        if (smem_of(pw) > 200 * 1024) pw = words | 1;
+        const int pitch = (int)(pw * 4 / sizeof(T));
+        const size_t smem = smem_of(pw);
         if (smem <= 200 * 1024)
             return launch_mode<T, true>(mode, frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, threads,
                                         smem, keep_row, pmask, polar, pnorm, radial, centres, st);
