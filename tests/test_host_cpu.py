@@ -228,3 +228,58 @@ def test_sparse_layout_reads_stay_in_bounds(lib, which):
                 assert 0 <= j < nchw and r_dec * nchw + j < n_rad * nchw, (layout, i, hw)
                 assert 32 * j <= s0 and s0 + ww <= 32 * (j + ncov)
         assert 3 * ww >= n_theta
+
+
+def _polar_launch(n_theta, staged=True, max_threads=768):
+    """Thread shape of the polar kernel: row groups of cols = 32 ceil(n_theta / 32) threads,
+    R = min(4, 768 / cols) groups when the frame is staged, else one group of at most 768."""
+    cols = (n_theta + 31) // 32 * 32
+    if staged and cols <= max_threads:
+        R = max(1, min(4, max_threads // cols))
+        return cols, R
+    return min(cols, max_threads), 1
+
+
+@pytest.mark.parametrize("n_r,n_theta,staged", [(128, 360, True), (60, 180, True), (30, 7, True), (1, 1, True),
+                                                (61, 77, True), (26, 1000, False), (128, 360, False),
+                                                (130, 361, True)])
+def test_polar_thread_mapping_covers_grid(n_r, n_theta, staged):
+    """Replay the polar kernel's work split on the CPU: a warp samples 8 angles (lane & 7) by
+    4 rows (lane >> 3); thread (group g, warp-in-group wg, lane) takes columns
+    8 wg + (lane & 7) + i cols / 4 and rows (lane >> 3) + 4 g + m 4 R.  Every sample of the
+    n_r x n_theta grid is taken exactly once; in each pass over the columns every warp of a
+    row's group (g = (j / 4) mod R) writes that row's partial sum exactly once, from an even
+    lane of the row's group of eight, which the radial sums then add over the group's warps."""
+    cols, R = _polar_launch(n_theta, staged)
+    threads = cols * R
+    seen = np.zeros((n_r, n_theta), dtype=np.int64)
+    part = {}
+    for tid in range(threads):
+        lane, warp = tid & 31, tid >> 5
+        g, t_in = tid // cols, tid % cols
+        k0, kstep = 8 * (t_in >> 5) + (lane & 7), cols >> 2
+        row0, rstep = (lane >> 3) + 4 * g, 4 * R
+        wrows = -(-(n_r - 4 * g) // rstep) if 4 * g < n_r else 0
+        mine = -(-(n_r - row0) // rstep) if row0 < n_r else 0
+        assert mine <= wrows
+        for kk in range(0, n_theta, kstep):
+            k = kk + k0
+            for b in range(0, wrows, 4):
+                nu = mine - b
+                j0 = row0 + rstep * b
+                if k < n_theta and nu > 0:
+                    for u in range(min(4, nu)):
+                        seen[j0 + rstep * u, k] += 1
+                kl = lane & 7
+                u = ((kl >> 2) & 1) * 2 + ((kl >> 1) & 1)
+                if kl % 2 == 0 and u < nu:
+                    key = (kk, j0 + rstep * u, warp)
+                    assert key not in part and j0 + rstep * u < n_r
+                    part[key] = True
+    assert np.all(seen == 1)
+    wpg = cols // 32
+    for j in range(n_r):
+        g0 = (j >> 2) % R
+        for w in range(g0 * wpg, (g0 + 1) * wpg):
+            for kk in range(0, n_theta, cols >> 2):
+                assert (kk, j, w) in part, (j, w, kk)
