@@ -11,7 +11,8 @@
 // rows at a time, so four samples are in flight per thread and a store writes 32-byte runs.
 //
 // Staged form (frame fits in shared memory): the CTA first copies the frame into shared
-// memory with 16-byte global loads.  The taps of a warp's patch cover a small 2-D region of
+// memory with 16-byte global loads (its next frame having been prefetched into L2 while the
+// previous one was sampled).  The taps of a warp's patch cover a small 2-D region of
 // the frame; rows are padded to 9 (mod 32) 32-bit words, which puts such regions' words in
 // distinct banks more often than a plain odd pitch (whose banks repeat every two pixels along
 // one diagonal direction): 1.5 instead of 2.7 shared-memory wavefronts per tap load on a
@@ -397,6 +398,15 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
             // u16 words: a pixel >= kLut sets a bit of 0xF000 in its half
             big = __syncthreads_or(kHasLut ? (hi_bits & 0xF000F000u) != 0 : 1) != 0;
             frame = sF;
+            // bring the CTA's next frame into L2 while this one is sampled, so that its staging
+            // reads L2 rather than HBM (one 128-byte line per thread and step)
+            const int64_t pnext = p + gridDim.x;
+            if (pnext < n) {
+                const char* nf = reinterpret_cast<const char*>(frames + (size_t)pnext * H * W);
+                const size_t nbytes = (size_t)H * W * sizeof(T);
+                for (size_t off = (size_t)threadIdx.x * 128; off < nbytes; off += (size_t)blockDim.x * 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(nf + off));
+            }
         }
         float* out = polar + (size_t)p * n_r * n_theta;
         long long cx = cxb, cy = cyb;
