@@ -19,7 +19,8 @@
 //     (a select per block).
 //   The library stores, per spot, its shared-memory offset in the dual and wrap-free
 //   layouts, so no address is decoded in the inner loop.
-// * A persistent CTA takes patterns from a global counter; its warps take 32-template
+// * A persistent CTA takes patterns from a global counter (and prefetches into L2 the rows of
+//   the pattern gridDim.x further on, which some CTA takes soon); its warps take 32-template
 //   mask words from a shared counter.  One warp scores one template: the lanes hold all its
 //   shifts in registers; the template's spots arrive in one lane-parallel load and are
 //   broadcast by shuffles.  The bound is the shared-memory load path (4 bytes per
@@ -276,6 +277,17 @@ sparse_kernel(const SparseCall c) {
         for (int li = 0; li < c.n_libs; ++li) {
             const SparseLib L = c.lib[li];
             const bool windows = L.bspot != nullptr;         // window bounds (else whole-row bounds)
+            // bring the same rows of pattern p + gridDim.x into L2: patterns are taken in order,
+            // so the CTA that takes it soon finds them there (one 128-byte line per thread)
+            if (p + gridDim.x < c.n) {
+                const int lines = (n_theta * (int)sizeof(float) + 127) >> 7;
+                const float* nsrc = c.polar + (size_t)(p + gridDim.x) * c.n_r * n_theta;
+                for (int i = threadIdx.x; i < L.n_rad * lines; i += blockDim.x) {
+                    const int r0 = i / lines, l = i - r0 * lines;
+                    const char* a = reinterpret_cast<const char*>(nsrc + (size_t)__ldg(L.radii + r0) * n_theta) + 128 * l;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                }
+            }
             // the library's polar rows (dual layout: a second copy shifted by one column)
             const int rows = (LAYOUT == TM_LAYOUT_DUAL ? 2 : 1) * L.n_rad;
             for (int rr = warp; rr < rows; rr += kWarps) {
