@@ -312,7 +312,7 @@ __device__ __forceinline__ uint32_t stage_frame(const T* __restrict__ gframe, T*
         const int vr = (int)(W * sizeof(T) / 16);           // 16-byte vectors per row
         const int nv = H * vr;
         const uint4* src = (const uint4*)gframe;
-        constexpr int B = 8;                                // loads in flight per thread
+        constexpr int B = 4;                                // loads in flight per thread (the frame is in L2)
         for (int i0 = threadIdx.x; i0 < nv; i0 += B * blockDim.x) {
             uint4 v[B];
 #pragma unroll
