@@ -45,6 +45,7 @@ __host__ __device__ constexpr int round_nb(int nb) {
 }
 
 constexpr int kMaxThreads = 512;            // block sizes: 128, 256 (default) or 512
+constexpr int kStageUnroll = 4;             // row-staging chunks unrolled (their loads overlap)
 constexpr int kMaxWarps = kMaxThreads / 32;
 
 }  // namespace
@@ -302,6 +303,7 @@ sparse_kernel(const SparseCall c) {
                 const bool chunks = first && windows;        // (windows imply nq <= 32)
                 const int ncol = chunks ? max(pitch, 32 * nq) : pitch;
                 float mq = -INFINITY;
+#pragma unroll kStageUnroll
                 for (int c0 = 0; c0 < ncol; c0 += 32) {
                     const int col = c0 + lane;
                     int sc = col + sh;
