@@ -46,6 +46,7 @@ __host__ __device__ constexpr int round_nb(int nb) {
 
 constexpr int kMaxThreads = 512;            // block sizes: 128, 256 (default) or 512
 constexpr int kStageUnroll = 4;             // row-staging chunks unrolled (their loads overlap)
+constexpr int kBoundUnroll = 4;             // bound loop over a template's spots unrolled
 constexpr int kMaxWarps = kMaxThreads / 32;
 
 }  // namespace
@@ -385,6 +386,7 @@ sparse_kernel(const SparseCall c) {
                     float ub = 0.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
                     if (windows) {
                         // per spot: its intensity and the table entries of its three windows
+#pragma unroll kBoundUnroll
                         for (int i = 0; i < cnt_l; ++i) {
                             const int2 w = __ldg(L.bspot + meta_l.x + i);
                             const float I = __int_as_float(w.x);
