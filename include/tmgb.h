@@ -307,15 +307,20 @@ int tm_profile_read(tm_ctx* ctx, tm_profile* out);
  * an application whose device memory belongs to another allocator (a framework's caching
  * allocator that must see every allocation), or an acquisition callback that runs inside
  * a fixed, pre-reserved device budget and must not wait on the driver's allocator.
- * Scratch (tap table, polar images, norms, counter) lives in one static 64 MiB device
- * array that every GPU loading this library keeps for the life of the process; a call
- * whose scratch would not fit (about 340 frames on a 128 x 360 grid) fails with
- * TM_ERR_INVALID_ARG and says how much it needed.  All calls share the array and find the
- * previous call's data in it (each call rewrites what it reads); calls that overlap on the
- * GPU race, so issue them on one stream.  The first call on a device looks the array's
- * address up (cudaGetSymbolAddress) with that device current: make it before any stream
- * capture.  frames_dev [n][H][W], out_dev [n][top_n] tm_hit; params->path must be
- * TM_PATH_FP32_SPARSE and params->prefilter_fraction 1.  Results equal tm_index_patterns'. */
+ * Scratch (polar ray steps, polar images, norms, counter) lives in one static 64 MiB device
+ * array that every GPU loading this library keeps for the life of the process: 512 KiB hold
+ * the ray steps of up to 8 polar grids, and a call needs n_r * n_theta * 4 + 4 bytes per
+ * pattern plus 512 bytes of the rest (361 patterns per call on a 128 x 360 grid); a call
+ * whose scratch would not fit fails with TM_ERR_INVALID_ARG and says how much it needed.
+ * All calls share the array and find the previous call's data in it (each call rewrites
+ * what it reads); calls that overlap on the GPU race, so issue them on one stream.  Set-up:
+ * the first call on a device looks the array's address up (cudaGetSymbolAddress) with that
+ * device current, and the first call for each polar grid (n_theta, dr) on a device writes
+ * the grid's ray steps into the array with a synchronous copy; make those first calls
+ * before any stream capture.  params are checked as for tm_index_patterns (pixel_mask
+ * 16-byte aligned, threshold finite and >= 0, ...); params->path must be
+ * TM_PATH_FP32_SPARSE and params->prefilter_fraction 1.  frames_dev [n][H][W], out_dev
+ * [n][top_n] tm_hit.  Results equal tm_index_patterns'. */
 int tm_index_patterns_noalloc(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev,
                               int32_t dtype, int64_t n, int32_t H, int32_t W, int32_t lib_id,
                               tm_hit* out_dev, void* stream);

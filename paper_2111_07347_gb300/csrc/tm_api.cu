@@ -698,6 +698,14 @@ int check_params(const tm_index_params* p) {
     return TM_OK;
 }
 
+}  // namespace
+
+namespace tmgb {
+int check_index_params(const tm_index_params* p) { return check_params(p); }
+}  // namespace tmgb
+
+namespace {
+
 tmgb::RadialLib radial_lib(const Library* L) {
     return tmgb::RadialLib{L->d_radial, L->d_rnorm, L->d_radii, (int32_t)L->radii.size(), (int32_t)L->K};
 }

@@ -216,6 +216,11 @@ cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_
 cudaError_t launch_compact(const uint32_t* mask, int64_t n, int K, const int32_t* order, int keep,
                            int32_t* list, cudaStream_t st);
 
+// Validation of tm_index_params shared by every whole-path entry point (finite gamma,
+// subtraction and centre; pre-filter fraction; top_n; 16-byte aligned pixel mask; threshold).
+// Returns a TM_* status and sets the thread's last error.
+int check_index_params(const tm_index_params* p);
+
 // Read-only view of a loaded library for entry points defined outside the host API file:
 // device, SM count, the sparse view and the library's polar grid.  Returns a TM_* status.
 int library_view(tm_ctx* ctx, int lib_id, int* device, int* num_sms, SparseLib* view, int* n_r,

@@ -283,3 +283,20 @@ def test_polar_thread_mapping_covers_grid(n_r, n_theta, staged):
         for w in range(g0 * wpg, (g0 + 1) * wpg):
             for kk in range(0, n_theta, cols >> 2):
                 assert (kk, j, w) in part, (j, w, kk)
+
+
+@pytest.mark.parametrize("field,value,needle", [("pixel_mask", 0x1001, "pixel_mask"),
+                                                 ("threshold", -1.0, "threshold"),
+                                                 ("path", tmgb.TM_PATH_BF16_RESCORE, "FP32 sparse"),
+                                                 ("prefilter_fraction", 0.5, "FP32 sparse")])
+def test_noalloc_rejects_bad_params_before_launch(lib, field, value, needle):
+    """The allocation-free entry point validates its parameters on the host, before any
+    device work (here with no context and no GPU): a misaligned mask, a negative threshold,
+    the BF16 path and a pre-filter are refused with TM_ERR_INVALID_ARG."""
+    import ctypes
+    f = lib.tm_index_patterns_noalloc
+    p = tmgb.make_params(top_n=5)
+    setattr(p, field, value)
+    rc = f(None, ctypes.byref(p), None, tmgb.TM_DTYPE_U16, 4, 256, 256, 0, None, None)
+    assert rc == tmgb.TM_ERR_INVALID_ARG
+    assert needle in tmgb.tm_last_error()
