@@ -365,3 +365,68 @@ def two_phase_workload(n_patterns: int = 4096, stream: int = 0, matrix_share: fl
     truth = dict(matrix_template=k_m, matrix_angle=phi_m, has_precipitate=has,
                  precipitate_template=pre.template, precipitate_angle=pre.angle)
     return fcc, hcp, frames, truth
+
+
+#: Kinematic settings of the batched three-phase workload.  Its spot counts must span
+#: 20-250 per template; at the single-phase settings (|g| <= 1.2 1/A, |s| <= 0.02 1/A,
+#: 0.01 1/A per pixel) the three phases give 2.8 / 6.7 / 12 spots on average, because the
+#: reciprocal lattice within 1.2 1/A holds few points and the thin relrod against the Ewald
+#: curvature keeps few of them.  Here the detector calibration is 0.02 1/A per pixel, so the
+#: 128-pixel polar grid reaches |g| = 2.54 1/A, every template keeps the reflections up to
+#: that radius, and the relrod reaches 0.05 1/A (a thinner specimen): FCC 24-77, HCP
+#: 51-160, tetragonal 110-244 spots, the most intense 250 kept; no template falls below 20,
+#: so none is dropped.
+MULTIPHASE_KINEMATICS = dict(g_max=2.54, s_max=0.05, max_spots=250, px_per_unit=50.0)
+MULTIPHASE_STRUCTURES = ("fcc", "hcp", "tetragonal")
+
+
+def multiphase_libraries(step_deg: float = 0.5, min_spots: int = 20):
+    """The three phase libraries of the batched workload (FCC a = 4.05 A, HCP a = 3.21 A
+    c = 5.21 A, tetragonal a = 3.6 A c = 5.1 A at 200 kV over their fundamental triangles at
+    ``step_deg``), with MULTIPHASE_KINEMATICS.  Templates with fewer than ``min_spots`` spots
+    are dropped (their count is in ``meta["dropped"]``)."""
+    out = []
+    for s in MULTIPHASE_STRUCTURES:
+        ts = kinematic_library(s, step_deg=step_deg, **MULTIPHASE_KINEMATICS)
+        cnt = ts.spot_counts()
+        keep = np.nonzero(cnt >= min_spots)[0]
+        dropped = int(cnt.shape[0] - keep.shape[0])
+        if dropped:
+            sel = np.concatenate([np.arange(ts.offsets[k], ts.offsets[k + 1]) for k in keep])
+            offs = np.zeros(keep.shape[0] + 1, dtype=np.int64)
+            np.cumsum(cnt[keep], out=offs[1:])
+            ts = TemplateSet(offs, ts.a[sel], ts.b[sel], ts.intensity[sel], coords=ts.coords,
+                             px_per_unit=ts.px_per_unit, mirror=ts.mirror, meta=dict(ts.meta))
+        ts.meta.update(dropped=dropped, min_spots=min_spots)
+        out.append(ts)
+    return out
+
+
+def multiphase_workload(n_unique: int = 8192, stream: int = 0, step_deg: float = 0.5):
+    """Frames of the batched three-phase scan (256 x 256 u16, polar 128 x 360): pattern p
+    shows a random template of phase truth[p] (phases drawn uniformly), rendered as
+    ``render_scan`` does with the libraries' own calibration.  Every pattern is indexed
+    against all three libraries (top-5 per phase).  Returns (libraries, frames, truth phase,
+    truth template, parameters)."""
+    libs = multiphase_libraries(step_deg)
+    rng = make_rng(2, stream)
+    phase = rng.integers(0, len(libs), size=n_unique)
+    frames = np.zeros((n_unique, 256, 256), dtype=np.uint16)
+    tmpl = np.zeros(n_unique, dtype=np.int64)
+    for i, ts in enumerate(libs):
+        idx = np.nonzero(phase == i)[0]
+        if idx.shape[0]:
+            sc = render_scan(rng, ts, idx.shape[0], 256, 256, n_theta=360)
+            frames[idx] = sc.frames
+            tmpl[idx] = sc.template
+    return libs, frames, phase, tmpl, dict(n_r=128, n_theta=360, dr=1.0, gamma=0.5, top_n=5, prefilter=1.0)
+
+
+def large_map_workload(n_unique: int = 16384, stream: int = 0, step_deg: float = 0.5):
+    """Distinct frames of the large single map (512 x 512 scan of 256 x 256 u16 frames, HCP
+    a = 3.21 A c = 5.21 A at 0.5 deg with mirrors, at most 250 spots, polar 128 x 360, top-5);
+    the full map repeats these ``n_unique`` frames.  Returns (library, scan, parameters)."""
+    rng = make_rng(4, stream)
+    ts = kinematic_library("hcp", step_deg=step_deg, max_spots=250)
+    scan = render_scan(rng, ts, n_unique, 256, 256, n_theta=360, dtype=np.uint16)
+    return ts, scan, dict(n_r=128, n_theta=360, dr=1.0, gamma=0.5, top_n=5, prefilter=1.0)
