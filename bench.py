@@ -40,13 +40,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "patterns/s indexed, BF16-TC vs FP32 sparse at ≥99.5% top-1 match; p99 line ms"
 N_R, N_THETA, TOP_N = 128, 360, 5
-RESCORE_K = 256
 E2E_CHUNK = 2048                  # patterns per chunk of the host-buffer entry point (tm_index_patterns_host)
 # tensor-core work per (pattern, scored template): 2 x 180 shifts x (182 + 180) frequency terms
 DENSE_FLOPS_PER_PAIR = 2 * 180 * (182 + 180)
-LARGE_MAP = dict(total=262144, unique=16384)
-MULTIPHASE = dict(total=65536, unique=8192)
-SINGLE_PHASE = dict(total=16384, prefilter=0.5)
+# rescore_k: candidates of the BF16 pre-score rescored exactly; the configured 64 where it meets the
+# top-1 bar, 256 on the FCC library, whose 2-spot templates have hundreds of near-ties
+LARGE_MAP = dict(total=262144, unique=16384, rescore_k=64)
+MULTIPHASE = dict(total=65536, unique=8192, rescore_k=64)
+SINGLE_PHASE = dict(total=16384, prefilter=0.5, rescore_k=256)
 WORKLOAD = ("large single map: 262144 x 256x256 u16 frames (16384 distinct, repeated), HCP 0.5 deg (+mirrors, "
             "<= 250 spots), polar 128x360, top-5; BF16 tensor-core pre-score + FP32 rescore vs FP32 sparse")
 try:
@@ -610,7 +611,7 @@ def sparse_work(ctx, lids, frames_d, prefilter):
 
 
 def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_unique, sample_idx, prefilter,
-                   oracle_n, local, dev, world, want_paths, rank):
+                   oracle_n, local, dev, world, want_paths, rank, rescore_k):
     """Both paths on one workload: device-timed patterns/s, stages, rooflines, and top-1 against
     the FP64 oracle on sampled distinct frames."""
     import torch
@@ -619,7 +620,7 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
     L = len(lids)
     sm = torch.cuda.get_device_properties(local).multi_processor_count
     kws = {"fp32": dict(top_n=TOP_N, prefilter=prefilter, path=tmgb.TM_PATH_FP32_SPARSE),
-           "bf16": dict(top_n=TOP_N, prefilter=prefilter, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=RESCORE_K)}
+           "bf16": dict(top_n=TOP_N, prefilter=prefilter, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=rescore_k)}
     out = torch.empty((L, n, TOP_N, 5), dtype=torch.int32, device=dev)
     macs_step, pairs_step = sparse_work(ctx, lids, frames_d, prefilter)
     res, hits = {}, {}
@@ -643,7 +644,8 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
     rec = {"patterns": n, "libraries": [ctx.library_info(l)["n_templates"] for l in lids],
            "spots_per_template": [round(ctx.library_info(l)["n_spots"] / ctx.library_info(l)["n_templates"], 2)
                                   for l in lids],
-           "prefilter": prefilter, "macs_per_step_sparse": macs_step, "pairs_per_step": pairs_step, "paths": {}}
+           "prefilter": prefilter, "rescore_k": rescore_k, "macs_per_step_sparse": macs_step,
+           "pairs_per_step": pairs_step, "paths": {}}
     match, recall, oracle_info = {}, {}, None
     if rank == 0 and oracle_n and hits:
         sub = frames_np_unique[sample_idx % frames_np_unique.shape[0]]
@@ -655,7 +657,7 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
             allok = np.concatenate([top1_agrees(h[li], refs[li]) for li in range(L)])
             match[nm] = {"all": match_record(allok), "per_library": per}
         if "bf16" in hits and L == 1:
-            recall = recall_record(ctx, lids[0], sub, refs[0], dev, ks=(64, RESCORE_K))
+            recall = recall_record(ctx, lids[0], sub, refs[0], dev, ks=(64, 256))
     for nm, r in res.items():
         if "unsupported" in r:
             rec["paths"][nm] = r
@@ -708,11 +710,13 @@ def run_ours(args):
             total = LARGE_MAP["total"]
             prefilter = 1.0
             oracle_n = args.oracle_patterns
+            rk = LARGE_MAP["rescore_k"]
         elif wl == "multiphase":
             libs_ts, uniq, phase, _, _ = synth.multiphase_workload(n_unique=MULTIPHASE["unique"], stream=rank)
             total = MULTIPHASE["total"]
             prefilter = 1.0
             oracle_n = args.oracle_multiphase
+            rk = MULTIPHASE["rescore_k"]
         elif wl == "single_phase":
             ts, scan, _ = synth.single_phase_workload(n_patterns=SINGLE_PHASE["total"], stream=rank)
             uniq = scan.frames
@@ -720,6 +724,7 @@ def run_ours(args):
             total = SINGLE_PHASE["total"]
             prefilter = SINGLE_PHASE["prefilter"]
             oracle_n = 512
+            rk = SINGLE_PHASE["rescore_k"]
         else:
             raise SystemExit(f"unknown workload {wl}")
         base = to_device_u16(uniq, dev)
@@ -732,7 +737,7 @@ def run_ours(args):
         reps = total // uniq.shape[0]
         sample_idx = pick + uniq.shape[0] * np.random.default_rng(6).integers(0, reps, size=pick.shape[0])
         rec, res = bench_workload(args, ctx, timer, wl, libs_ts, lids, frames_d, uniq, sample_idx, prefilter,
-                                  oracle_n, local, dev, world, want_paths, rank)
+                                  oracle_n, local, dev, world, want_paths, rank, rk)
         if wl == "multiphase" and rank == 0 and rec.get("paths"):
             rec["phase_share"] = [float((phase == i).mean()) for i in range(3)]
             rec["dropped_templates"] = [t.meta.get("dropped", 0) for t in libs_ts]
@@ -753,7 +758,7 @@ def run_ours(args):
                                     "distinct_frames": int(uniq.shape[0]), "frame": "256x256 u16",
                                     "templates": rec["libraries"], "spots_per_template": rec["spots_per_template"],
                                     "polar": f"{N_R}x{N_THETA}", "prefilter": prefilter, "top_n": TOP_N,
-                                    "path": head, "rescore_k": RESCORE_K,
+                                    "path": head, "rescore_k": rk,
                                     "top1_rule": "headline path: Wilson 95 % lower bound of top-1 agreement with "
                                                  "the FP64 oracle >= 99.5 %",
                                     "l2": "distinct frames (2.1 GB) and each step's 34 GB larger than L2; no flush"}})
@@ -772,7 +777,7 @@ def run_ours(args):
             host_out = torch.empty((len(lids), uniq.shape[0], TOP_N, 5), dtype=torch.int32).pin_memory()
             kw = dict(top_n=TOP_N, prefilter=prefilter,
                       path=tmgb.TM_PATH_BF16_RESCORE if head == "bf16" else tmgb.TM_PATH_FP32_SPARSE,
-                      rescore_k=RESCORE_K)
+                      rescore_k=rk)
 
             def e2e_step():
                 for _ in range(reps):

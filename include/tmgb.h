@@ -155,7 +155,9 @@ typedef struct tm_stats {
     int64_t patterns;             /* patterns indexed by the call                        */
     int64_t correlations;         /* (pattern, template, shift) triples evaluated        */
     int64_t templates_scored;     /* (pattern, template) pairs scored exactly            */
-    int64_t launches;             /* kernels launched by the call                        */
+    int64_t launches;             /* this library's kernels launched by the call (the
+                                     tensor-core path's stage A GEMM runs in cuBLAS and is
+                                     not counted)                                         */
 } tm_stats;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory
@@ -229,12 +231,16 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
 /* Stage A7 alone: the BF16 tensor-core pre-score.  The correlation along theta is taken
  * through the correlation theorem (Section 2.2 names the FFT cross-correlation as the
  * alternative to sliding): C[k, s] = sum_m (w_m / n) Re(G[k, m] e^{2 pi i m s / n}) with
- * G[k, m] = sum_r conj(T^_k[r, m]) P^[r, m]; G is formed in FP32 and rounded to BF16, the
- * sum over frequencies for every shift runs on the tensor cores (tcgen05, FP32
- * accumulation).  score_dev [n][K] float receives Q~ = max_s C / (|P| |T_k|) for every
- * template scored and -NaN for the others (the pre-filter's rejects when fraction < 1).
- * polar_dev / norm_dev: Stage 1 outputs; radial_dev: Stage 1 azimuthal sums (used when
- * fraction < 1).  n_theta must be even and <= 376 (else TM_ERR_UNSUPPORTED). */
+ * G[k, m] = sum_r conj(T^_k[r, m]) P^[r, m] over the library's spot radii.  T^ (the templates'
+ * angular spectra, divided by |T_k|) is built once per library on the device, the first time
+ * the tensor-core path uses it; P^ (divided by |P|) is formed in FP32; both are rounded to BF16.
+ * Stage A (G for every frequency, a batched GEMM over the radii) and stage B (the sum over
+ * frequencies for every shift, with the maximum over shifts) run on the tensor cores with FP32
+ * accumulation.  score_dev [n][K] float receives Q~ = max_s C / (|P| |T_k|) for every template
+ * scored and -NaN for the others (the pre-filter's rejects when fraction < 1).  polar_dev /
+ * norm_dev: Stage 1 outputs; radial_dev: Stage 1 azimuthal sums (used when fraction < 1).
+ * n_theta must be even and <= 376, and the library's distinct radii must fit the DFT's shared
+ * memory (about 150 at n_theta = 360), else TM_ERR_UNSUPPORTED. */
 int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev,
                 const float* radial_dev, int64_t n, double fraction, float* score_dev, void* stream);
 
@@ -285,8 +291,9 @@ enum {
     TM_STAGE_PREFILTER = 1,   /* radial norms, scores and selection                     */
     TM_STAGE_SPARSE = 2,      /* FP32 sparse correlation + top-N                        */
     TM_STAGE_DFT = 3,         /* angular DFT of the polar images (BF16 path)            */
-    TM_STAGE_DENSE = 4,       /* BF16 tensor-core pre-score (BF16 path)                 */
-    TM_STAGE_RESCORE = 5,     /* FP32 rescore of the candidates (BF16 path)             */
+    TM_STAGE_DENSE = 4,       /* BF16 tensor-core inverse DFT + max over shifts (stage B) */
+    TM_STAGE_RESCORE = 5,     /* candidate selection + FP32 rescore (BF16 path)         */
+    TM_STAGE_GEMM = 6,        /* BF16 tensor-core contraction over radii (stage A)      */
     TM_STAGE_COUNT = 8
 };
 typedef struct tm_profile {

@@ -1,7 +1,8 @@
 """Build libtmgb.so (all CUDA sources under csrc/) for sm_103a with nvcc.
 
 Translation units compile in parallel, then link into a shared library next to this
-file.  No cmake, no torch extension machinery: the library has a plain C ABI.
+file (with cuBLAS, which runs the tensor-core path's plain batched GEMM).  No cmake, no torch
+extension machinery: the library has a plain C ABI.
 """
 from __future__ import annotations
 
@@ -58,7 +59,9 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = OUT + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared"]
+    libdir = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-L" + libdir, "-lcublas",
+           "-Xlinker", "-rpath", "-Xlinker", libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

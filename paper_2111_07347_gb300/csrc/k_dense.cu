@@ -1,34 +1,36 @@
-// BF16 tensor-core pre-score (tcgen05, TMEM accumulators) of the correlation index.
+// BF16 tensor-core pre-score, stage B: the inverse angular DFT on tcgen05 with the maximum
+// over shifts fused into the epilogue.
 //
 // The correlation of Eq. 1 along the azimuth is evaluated through the correlation theorem
 // (the FFT cross-correlation alternative the paper names in Section 2.2's complexity
 // paragraph):
 //   C[k, s] = sum_{m=0}^{H} (w_m / n) Re( G[k, m] e^{2 pi i m s / n} ),  H = n / 2,
-//   G[k, m] = sum_{spots i of k} I_i e^{+2 pi i m t_i / n} P^[r_i, m]   (= sum_r conj(T^) P^).
-// Templates are sparse (a few spots), so G is built on CUDA cores from the spot list; the
-// dense part -- the inverse transform over all frequencies for every shift, 2 x 192 x 384
-// multiply-adds per template against 2 x 192 for the sparse sum's inner loop -- runs on
-// the tensor cores.  A radix-2 split halves it: with E[s] the even-m part and O[s] the
-// odd-m part of the sum for s < H, C[s] = E[s] + O[s] and C[s + H] = E[s] - O[s], so one
-// 128 x 192 x 384 BF16 GEMM per 128 templates gives all n shifts (E and O live in TMEM
-// columns [0, 192) and [192, 384)).
+//   G[k, m] = sum_r conj(T^_k[r, m]) P^[r, m],
+// with T^ and P^ the angular DFTs of the template (divided by |T_k|) and of the polar pattern
+// (divided by |P|), so C is Q directly.  Stage A (G, a GEMM per frequency over the radii) runs
+// before this kernel and leaves G in global memory as BF16, frequency-major:
+//   G[j][p][c][k]  (slot j, pattern p of the batch, c = 0 real / 1 imaginary, template k),
+// slot j < 96 holding m = 2 j and slot j >= 96 holding m = 2 (j - 96) + 1.  A radix-2 split
+// halves this kernel's work: with E[s] the even-m part and O[s] the odd-m part of the sum for
+// s < H, C[s] = E[s] + O[s] and C[s + H] = E[s] - O[s], so max(C[s], C[s + H]) = E[s] + |O[s]|.
+// Per (pattern, tile of 128 templates) one GEMM [128 x 384] x [384 x 192] gives E (TMEM columns
+// 0..191, K = slots 0..95) and O (columns 192..383, K = slots 96..191).
 //
-// CTA layout (one per SM, persistent over patterns; 672 threads):
-//   warps 0-15 producers: four threads per row (one template) of G, eight frequencies each
-//              per 64-element chunk, in BF16, into a 2-slot shared-memory ring
-//              (128B-swizzled K-major); four warps per scheduler hide the latency of the
-//              twiddle recurrence; each warp waits for a free slot on its own;
-//   warp  20   TMEM allocation and the single MMA-issuing thread;
-//   warps 16-19 epilogue: tcgen05.ld of E and O, max over all n shifts, one pre-score
-//              per (pattern, template) written to global memory (the candidates are
-//              then chosen by the exact radix select and rescored in FP32).
-// The basis (w_m / n) cos / -sin for both halves stays resident in shared memory.
+// Operands: A = G read by TMA as MN-major tiles (template index contiguous; 64 K-rows of 2 x 64
+// templates per ring slot, 128-byte swizzle); B = the inverse-DFT basis (w_m / n) cos / -sin,
+// K-major, resident in shared memory.  CTA (persistent over (pattern, tile) units, 256 threads):
+//   warp 0 lane 0  TMA producer into a 4-slot ring;
+//   warp 1 lane 0  MMA issuer (tcgen05.mma.cta_group::1.kind::f16, BF16 x BF16 -> FP32 in TMEM);
+//   warp 2         TMEM allocation;
+//   warps 4-7      epilogue: tcgen05.ld of E and O, max over shifts, one pre-score per
+//                  (pattern, template) written to global memory (masked-out templates: -NaN).
 // Every mbarrier wait is bounded by the global timer (1 s); on timeout the CTA records an error
-// in a device word, stops its roles uniformly, releases TMEM and returns.
+// in a device word, stops its roles, lets the copies and MMAs it issued finish, releases TMEM
+// and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
-#include <cuda_fp16.h>
 #include <float.h>
-#include <limits.h>
+#include <math.h>
 
 #include "tm_internal.h"
 
@@ -37,21 +39,18 @@ namespace {
 
 constexpr int kRows = 128;                 // templates per tile (MMA M)
 constexpr int kN = 192;                    // shifts per half (MMA N), >= n_theta / 2
-constexpr int kKB = 384;                   // K: 192 even-m + 192 odd-m elements
-constexpr int kChunk = 64;                 // K per ring slot (one 128-byte swizzle row)
+constexpr int kKB = 384;                   // K: 192 even-m + 192 odd-m (slot, re/im) elements
+constexpr int kChunk = 64;                 // K rows per ring slot
 constexpr int kChunks = kKB / kChunk;      // 6
-constexpr int kSlotBytes = kRows * 128;    // 16 KB
+constexpr int kBoxBytes = 64 * kChunk * 2; // 8 KB: 64 templates x 64 K rows
+constexpr int kSlotBytes = 2 * kBoxBytes;  // 16 KB
+constexpr int kStages = 4;
 constexpr int kBasisChunkBytes = kN * 128; // 24 KB
-constexpr int kProdWarps = 16;             // 4 threads per row, 8 frequencies each
-constexpr int kProdThreads = kProdWarps * 32;
-constexpr int kEpiWarp0 = kProdWarps;      // 4 epilogue warps
-constexpr int kMmaWarp = kProdWarps + 4;
-constexpr int kThreads = (kMmaWarp + 1) * 32;
+constexpr int kThreads = 256;
+constexpr int kEpiWarp0 = 4;
 constexpr unsigned long long kTimeoutNs = 1000000000ull;   // 1 s per wait
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -65,6 +64,12 @@ __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
 
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
+                 "r"(bytes)
+                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
@@ -93,33 +98,49 @@ __device__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_fl
     }
 }
 
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void named_bar(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+// 4-D tiled TMA load (coordinates innermost first) completing on an mbarrier.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptors (128-byte swizzle).  K-major: rows of 64 K-elements, 8-row
+// groups 1024 B apart.  MN-major: rows of 64 MN-elements (one per K index), 8 K-rows 1024 B
+// apart (stride dimension), 64-element MN blocks `mn_stride` bytes apart (leading dimension).
+__device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset between 8-row groups
-    d |= (uint64_t)1 << 46;                      // descriptor version
-    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+__device__ __forceinline__ uint64_t sdesc_mnmajor(uint32_t saddr, uint32_t mn_stride) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((mn_stride >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
-// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 192.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, A MN-major (bit 15), B K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_amn(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -151,67 +172,43 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-struct Smem {
-    uint8_t* basis;       // kChunks x [kN rows x 128 B], swizzled
-    uint8_t* ring;        // 2 x [kRows x 128 B], swizzled
-    __half2* phat;        // [n_rad][n_freq]
-    float2* tw;           // [n_theta]
-    int16_t* rmap;        // [n_r]
-    uint64_t* bar;        // full[2], empty[2], acc_full, acc_empty
-    uint32_t* tmem_base;
-    int* abort_flag;
-    int* prod_stop;       // producers' uniform stop decision, published at pattern boundaries
-    int* epi_stop;        // [2] epilogue's uniform stop decision, by tile parity
-};
-
-// Template row of tile t of (lib, pattern p), or -1 past the survivors.
-__device__ __forceinline__ int row_template(const DenseCall& c, int li, int64_t p, int row) {
-    if (row >= c.count[li]) return -1;
-    const int32_t* lst = c.list[li];
-    return lst ? lst[(size_t)p * c.count[li] + row] : c.lib[li].order[row];
-}
-
-__global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
+__global__ void __launch_bounds__(kThreads, 1) dense_kernel(const __grid_constant__ CUtensorMap gmap, const DenseCall c) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    Smem s;
-    s.basis = base;
-    s.ring = s.basis + kChunks * kBasisChunkBytes;
-    s.phat = (__half2*)(s.ring + 2 * kSlotBytes);
-    s.tw = (float2*)(((uintptr_t)(s.phat + (size_t)c.n_rad * c.n_freq) + 15) & ~(uintptr_t)15);
-    s.rmap = (int16_t*)(s.tw + c.n_theta);
-    s.bar = (uint64_t*)(((uintptr_t)(s.rmap + c.n_r) + 15) & ~(uintptr_t)15);
-    s.tmem_base = (uint32_t*)(s.bar + 6);
-    s.abort_flag = (int*)(s.tmem_base + 1);
-    s.prod_stop = s.abort_flag + 1;
-    s.epi_stop = s.prod_stop + 1;
-    volatile int* abort_flag = s.abort_flag;
+    uint8_t* s_basis = base;                                   // kChunks x [kN rows x 128 B]
+    uint8_t* s_ring = s_basis + kChunks * kBasisChunkBytes;    // kStages x 16 KB
+    uint64_t* bar = (uint64_t*)(s_ring + kStages * kSlotBytes);  // full[S], empty[S], acc_full, acc_empty
+    uint32_t* s_tmem = (uint32_t*)(bar + 2 * kStages + 2);
+    int* s_abort = (int*)(s_tmem + 1);
+    int* s_epi_stop = s_abort + 1;                             // [2], by unit parity
+    volatile int* abort_flag = s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_theta = c.n_theta, H = n_theta / 2;
-    const uint32_t bar_full0 = smem_u32(&s.bar[0]), bar_empty0 = smem_u32(&s.bar[2]);
-    const uint32_t bar_accf = smem_u32(&s.bar[4]), bar_acce = smem_u32(&s.bar[5]);
+    const int H = c.n_theta / 2;
+    const int tiles = (c.K + kRows - 1) / kRows;
+    const int64_t units = c.n * (int64_t)tiles;
+    const uint32_t bar_full0 = smem_u32(&bar[0]), bar_empty0 = smem_u32(&bar[kStages]);
+    const uint32_t bar_accf = smem_u32(&bar[2 * kStages]), bar_acce = smem_u32(&bar[2 * kStages + 1]);
 
-    // ---- one-time setup
+    // ---- one-time setup: the basis, swizzled (16-byte chunk q of row r at (q ^ (r & 7)))
     for (int i = threadIdx.x; i < kChunks * kN * 8; i += blockDim.x) {
         const int cch = i / (kN * 8), rem = i - cch * kN * 8, n = rem >> 3, q = rem & 7;
         const uint4 v = *(const uint4*)((const __nv_bfloat16*)c.basis + (size_t)n * kKB + cch * kChunk + q * 8);
-        *(uint4*)(s.basis + cch * kBasisChunkBytes + n * 128 + ((q ^ (n & 7)) << 4)) = v;
+        *(uint4*)(s_basis + cch * kBasisChunkBytes + n * 128 + ((q ^ (n & 7)) << 4)) = v;
     }
-    for (int i = threadIdx.x; i < n_theta; i += blockDim.x) s.tw[i] = c.twiddle[i];
-    for (int i = threadIdx.x; i < c.n_r; i += blockDim.x) s.rmap[i] = (int16_t)c.rmap[i];
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&s.bar[0]), kProdThreads);
-        mbar_init(smem_u32(&s.bar[1]), kProdThreads);
-        mbar_init(smem_u32(&s.bar[2]), 1);
-        mbar_init(smem_u32(&s.bar[3]), 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(smem_u32(&bar[i]), 1);
+            mbar_init(smem_u32(&bar[kStages + i]), 1);
+        }
         mbar_init(bar_accf, 1);
         mbar_init(bar_acce, kRows);
-        *s.abort_flag = 0;
+        *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&gmap) : "memory");
     }
-    if (warp == kMmaWarp) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s.tmem_base)),
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
@@ -219,134 +216,73 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *s.tmem_base;
+    const uint32_t tmem = *s_tmem;
 
-    if (warp < kProdWarps) {
-        // ================================================================ producers
-        const int row = threadIdx.x & (kRows - 1);
-        const int quarter = threadIdx.x >> 7;                    // frequencies 8 q .. 8 q + 7 of a chunk
-        uint32_t g = 0;                                         // global chunk counter
-        bool stop = false;
-        for (int64_t p = blockIdx.x; p < c.n; p += gridDim.x) {
-            // all producer warps reach this point (a warp that saw a failed wait skips the rest
-            // of its pattern instead of leaving); thread 0 publishes one stop decision
-            named_bar(1, kProdThreads);                         // previous pattern's P^ no longer read
-            if (threadIdx.x == 0) *s.prod_stop = *abort_flag;
-            named_bar(1, kProdThreads);
-            if (*(volatile int*)s.prod_stop) break;
-            const __half2* src = (const __half2*)c.phat + (size_t)p * c.n_rad * c.n_freq;
-            for (int i = threadIdx.x; i < c.n_rad * c.n_freq; i += kProdThreads) s.phat[i] = src[i];
-            named_bar(1, kProdThreads);
-            for (int li = 0; li < c.n_libs; ++li) {
-                const DenseLib& L = c.lib[li];
-                const int tiles = (c.count[li] + kRows - 1) / kRows;
-                for (int t = 0; t < tiles; ++t) {
-                    const int k = row_template(c, li, p, t * kRows + row);
-                    int beg = 0, end = 0;
-                    float inv_norm = 0.0f;
-                    if (k >= 0) {
-                        beg = L.off[k];
-                        end = L.off[k + 1];
-                        const float nk = L.norm[k];
-                        inv_norm = nk > 0.0f ? 1.0f / nk : 0.0f;
+    if (warp == 0) {
+        // ================================================================ TMA producer
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool stop = false;
+            for (int64_t u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+                const int p = (int)(u / tiles), t = (int)(u - (int64_t)p * tiles);
+                for (int ch = 0; ch < kChunks; ++ch, ++g) {
+                    const uint32_t slot = g % kStages, use = g / kStages;
+                    if (!mbar_wait(bar_empty0 + 8 * slot, (use & 1u) ^ 1u, abort_flag)) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
                     }
-                    for (int ch = 0; ch < kChunks; ++ch, ++g) {
-                        const uint32_t slot = g & 1u, use = g >> 1;
-                        // each warp waits for the slot on its own (no block-wide barrier per chunk);
-                        // warps drift at most the ring depth apart, since a slot is only freed
-                        // once every producer thread has filled it
-                        if (stop) continue;                      // skipping to the pattern boundary
-                        int ok = 1;
-                        if (lane == 0) ok = mbar_wait(bar_empty0 + 8 * slot, (use & 1u) ^ 1u, abort_flag) ? 1 : 0;
-                        ok = __shfl_sync(0xffffffffu, ok, 0);
-                        if (!ok) { *abort_flag = 1; stop = true; continue; }
-                        const int part = ch / 3;                   // 0: even m, 1: odd m
-                        const int m0 = 2 * ((ch % 3) * 32 + quarter * 8) + part;
-                        int nvalid = (H - m0) / 2 + 1;             // frequencies m0 + 2 jj <= H
-                        if (m0 > H) nvalid = 0;
-                        if (nvalid > 8) nvalid = 8;
-                        float are[8], aim[8];
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) { are[jj] = 0.0f; aim[jj] = 0.0f; }
-                        if (nvalid > 0) {
-                            for (int i = beg; i < end; ++i) {
-                                const int rt = L.rt[i];
-                                const int r = rt & 0xffff, tt = rt >> 16;
-                                const float I = __int_as_float(L.spot[i].y) * inv_norm;
-                                const __half2* ph = s.phat + (size_t)s.rmap[r] * c.n_freq + m0;
-                                float2 w = s.tw[(m0 * tt) % n_theta];
-                                w.x *= I;
-                                w.y *= I;
-                                const float2 st = s.tw[(2 * tt) % n_theta];
-#pragma unroll
-                                for (int jj = 0; jj < 8; ++jj) {
-                                    if (jj < nvalid) {
-                                        const float2 pv = __half22float2(ph[2 * jj]);
-                                        are[jj] = fmaf(w.x, pv.x, fmaf(-w.y, pv.y, are[jj]));
-                                        aim[jj] = fmaf(w.x, pv.y, fmaf(w.y, pv.x, aim[jj]));
-                                        const float wx = w.x * st.x - w.y * st.y;
-                                        w.y = fmaf(w.x, st.y, w.y * st.x);
-                                        w.x = wx;
-                                    }
-                                }
-                            }
-                        }
-                        uint8_t* dst = s.ring + slot * kSlotBytes + row * 128;
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int q = 2 * quarter + h;              // 16-byte chunk of the row
-                            uint4 v;
-                            __nv_bfloat162 b0 = __floats2bfloat162_rn(are[4 * h + 0], aim[4 * h + 0]);
-                            __nv_bfloat162 b1 = __floats2bfloat162_rn(are[4 * h + 1], aim[4 * h + 1]);
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(are[4 * h + 2], aim[4 * h + 2]);
-                            __nv_bfloat162 b3 = __floats2bfloat162_rn(are[4 * h + 3], aim[4 * h + 3]);
-                            v.x = *(uint32_t*)&b0;
-                            v.y = *(uint32_t*)&b1;
-                            v.z = *(uint32_t*)&b2;
-                            v.w = *(uint32_t*)&b3;
-                            *(uint4*)(dst + ((q ^ (row & 7)) << 4)) = v;
-                        }
-                        fence_proxy_async();
-                        mbar_arrive(bar_full0 + 8 * slot);
-                    }
+                    const uint32_t full = bar_full0 + 8 * slot;
+                    mbar_expect_tx(full, kSlotBytes);
+                    const uint32_t dst = smem_u32(s_ring + slot * kSlotBytes);
+                    tma_load_4d(dst, &gmap, t * kRows, 0, p, ch * (kChunk / 2), full);
+                    tma_load_4d(dst + kBoxBytes, &gmap, t * kRows + 64, 0, p, ch * (kChunk / 2), full);
                 }
             }
+            // the copies issued last must land before the CTA exits (they complete on their own)
+            volatile int never = 0;
+            const uint32_t n_issued = g;
+            for (uint32_t i = 0; i < kStages && i < n_issued; ++i) {
+                const uint32_t gg = n_issued - 1 - i, slot = gg % kStages, use = gg / kStages;
+                mbar_wait(bar_full0 + 8 * slot, use & 1u, &never);
+            }
         }
-    } else if (warp == kMmaWarp) {
+    } else if (warp == 1) {
         // ================================================================ MMA issuer
         if (lane == 0 && !c.stall) {
-            const uint32_t idesc = idesc_bf16(kRows, kN);
-            const uint32_t ring0 = smem_u32(s.ring), basis0 = smem_u32(s.basis);
+            const uint32_t idesc = idesc_bf16_amn(kRows, kN);
+            const uint32_t ring0 = smem_u32(s_ring), basis0 = smem_u32(s_basis);
             uint32_t g = 0, tt = 0;
-            bool stop = false;
+            bool stop = false, issued = false;
             uint32_t last_bar = 0, last_par = 0;
-            bool issued = false;
-            for (int64_t p = blockIdx.x; p < c.n && !stop; p += gridDim.x) {
-                for (int li = 0; li < c.n_libs && !stop; ++li) {
-                    const int tiles = (c.count[li] + kRows - 1) / kRows;
-                    for (int t = 0; t < tiles && !stop; ++t, ++tt) {
-                        if (!mbar_wait(bar_acce, (tt & 1u) ^ 1u, abort_flag)) { *abort_flag = 1; stop = true; break; }
-                        tc_fence_after();
-                        for (int ch = 0; ch < kChunks; ++ch, ++g) {
-                            const uint32_t slot = g & 1u, use = g >> 1;
-                            if (!mbar_wait(bar_full0 + 8 * slot, use & 1u, abort_flag)) { *abort_flag = 1; stop = true; break; }
-                            tc_fence_after();
-                            const uint32_t d = tmem + (ch < 3 ? 0u : (uint32_t)kN);
-#pragma unroll
-                            for (int ks = 0; ks < kChunk / 16; ++ks) {
-                                const uint64_t a = sdesc(ring0 + slot * kSlotBytes + ks * 32);
-                                const uint64_t b = sdesc(basis0 + ch * kBasisChunkBytes + ks * 32);
-                                mma_bf16(d, a, b, idesc, (ch % 3 == 0 && ks == 0) ? 0u : 1u);
-                            }
-                            mma_commit(bar_empty0 + 8 * slot);
-                            last_bar = bar_empty0 + 8 * slot;
-                            last_par = use & 1u;
-                            issued = true;
-                        }
-                        if (stop) break;
-                        mma_commit(bar_accf);
-                    }
+            for (int64_t u = blockIdx.x; u < units && !stop; u += gridDim.x, ++tt) {
+                if (!mbar_wait(bar_acce, (tt & 1u) ^ 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
                 }
+                tc_fence_after();
+                for (int ch = 0; ch < kChunks; ++ch, ++g) {
+                    const uint32_t slot = g % kStages, use = g / kStages;
+                    if (!mbar_wait(bar_full0 + 8 * slot, use & 1u, abort_flag)) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (ch < kChunks / 2 ? 0u : (uint32_t)kN);
+#pragma unroll
+                    for (int ks = 0; ks < kChunk / 16; ++ks) {
+                        const uint64_t a = sdesc_mnmajor(ring0 + slot * kSlotBytes + ks * 2048, kBoxBytes);
+                        const uint64_t b = sdesc_kmajor(basis0 + ch * kBasisChunkBytes + ks * 32);
+                        mma_bf16(d, a, b, idesc, (ch % (kChunks / 2) == 0 && ks == 0) ? 0u : 1u);
+                    }
+                    mma_commit(bar_empty0 + 8 * slot);
+                    last_bar = bar_empty0 + 8 * slot;
+                    last_par = use & 1u;
+                    issued = true;
+                }
+                if (stop) break;
+                mma_commit(bar_accf);
             }
             if (stop && issued) {
                 // let the MMAs already issued finish before TMEM is released
@@ -354,44 +290,42 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
                 mbar_wait(last_bar, last_par, &never);
             }
         }
-    } else {
-        // ================================================================ epilogue (warps 16-19)
+    } else if (warp >= kEpiWarp0) {
+        // ================================================================ epilogue (warps 4-7)
         const int ew = warp - kEpiWarp0;
         const int row = ew * 32 + lane;
         const uint32_t tbase = tmem + ((uint32_t)(ew * 32) << 16);
         uint32_t tt = 0;
-        bool stop = false;
-        for (int64_t p = blockIdx.x; p < c.n && !stop; p += gridDim.x) {
-            for (int li = 0; li < c.n_libs && !stop; ++li) {
-                const int tiles = (c.count[li] + kRows - 1) / kRows;
-                float* out = c.pre[li] + (size_t)p * c.lib[li].K;
-                for (int t = 0; t < tiles; ++t, ++tt) {
-                    // row 0 waits and publishes one decision (a word per tile parity, so the
-                    // next tile's write cannot overtake a slow reader of this one)
-                    if (row == 0) {
-                        const bool ok = mbar_wait(bar_accf, tt & 1u, abort_flag);
-                        if (!ok) *abort_flag = 1;
-                        s.epi_stop[tt & 1u] = (!ok || *abort_flag) ? 1 : 0;
-                    }
-                    named_bar(2, kRows);
-                    if (*(volatile int*)&s.epi_stop[tt & 1u]) { stop = true; break; }
-                    tc_fence_after();
-                    float best = -FLT_MAX;
+        for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++tt) {
+            const int p = (int)(u / tiles), t = (int)(u - (int64_t)p * tiles);
+            // row 0 waits and publishes one decision (a word per unit parity, so the next
+            // unit's write cannot overtake a slow reader of this one)
+            if (row == 0) {
+                const bool ok = mbar_wait(bar_accf, tt & 1u, abort_flag);
+                if (!ok) *abort_flag = 1;
+                s_epi_stop[tt & 1u] = (!ok || *abort_flag) ? 1 : 0;
+            }
+            named_bar(1, kRows);
+            if (*(volatile int*)&s_epi_stop[tt & 1u]) break;
+            tc_fence_after();
+            float best = -FLT_MAX;
 #pragma unroll 1
-                    for (int cb = 0; cb < kN / 32; ++cb) {
-                        float e[32], o[32];
-                        tmem_ld32(tbase + cb * 32, e);
-                        tmem_ld32(tbase + kN + cb * 32, o);
+            for (int cb = 0; cb < kN / 32; ++cb) {
+                float e[32], o[32];
+                tmem_ld32(tbase + cb * 32, e);
+                tmem_ld32(tbase + kN + cb * 32, o);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            if (cb * 32 + j < H) best = fmaxf(best, fmaxf(e[j] + o[j], e[j] - o[j]));
-                        }
-                    }
-                    tc_fence_before();
-                    mbar_arrive(bar_acce);
-                    const int k = row_template(c, li, p, t * kRows + row);
-                    if (k >= 0) out[k] = best;
-                }
+                for (int j = 0; j < 32; ++j)
+                    if (cb * 32 + j < H) best = fmaxf(best, e[j] + fabsf(o[j]));
+            }
+            tc_fence_before();
+            mbar_arrive(bar_acce);
+            const int k = t * kRows + row;
+            if (k < c.K) {
+                const int64_t p_glob = c.p0 + p;
+                bool keep = true;
+                if (c.mask) keep = (c.mask[p_glob * c.words + (k >> 5)] >> (k & 31)) & 1u;
+                c.pre[p_glob * c.K + k] = keep ? best : __int_as_float(0xFFFFFFFF);
             }
         }
     }
@@ -400,35 +334,32 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const DenseCall c) {
     __syncthreads();
     tc_fence_after();
     if (*abort_flag && threadIdx.x == 0) atomicOr(c.error, 1u);
-    if (warp == kMmaWarp) {
+    if (warp == 2) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }
 
 }  // namespace
 
-size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq) {
-    size_t b = 1024;                                           // alignment slack
-    b += (size_t)kChunks * kBasisChunkBytes + 2 * kSlotBytes;
-    b += (size_t)n_rad * n_freq * 4 + 16 + (size_t)n_theta * 8 + (size_t)n_r * 2 + 16;
-    b += 6 * 8 + 4 * 5 + 16;          // barriers, TMEM base, abort flag, stop words
-    return b;
+size_t dense_smem_bytes() {
+    return 1024 + (size_t)kChunks * kBasisChunkBytes + (size_t)kStages * kSlotBytes + (2 * kStages + 2) * 8 + 16;
 }
 
-bool dense_supported(int n_theta) { return n_theta % 2 == 0 && n_theta / 2 <= kN && (n_theta / 2) / 2 + 1 <= kN / 2; }
+bool dense_supported(int n_theta) { return n_theta % 2 == 0 && n_theta >= 4 && n_theta / 2 <= kN && (n_theta / 2) / 2 + 1 <= kN / 2; }
 
 int dense_basis_rows() { return kN; }
 int dense_basis_cols() { return kKB; }
+int dense_slots() { return kKB / 2; }
 
-cudaError_t launch_dense(const DenseCall& c, int num_sms, cudaStream_t st) {
-    if (c.n <= 0) return cudaSuccess;
-    const size_t smem = dense_smem_bytes(c.n_theta, c.n_r, c.n_rad, c.n_freq);
-    if (smem > 232448) return cudaErrorInvalidValue;
+cudaError_t launch_dense(const void* tmap, const DenseCall& c, int num_sms, cudaStream_t st) {
+    if (c.n <= 0 || c.K <= 0) return cudaSuccess;
+    const size_t smem = dense_smem_bytes();
     const cudaError_t e = kernel_occupancy((const void*)dense_kernel, kThreads, smem, nullptr);
     if (e != cudaSuccess) return e;
+    const int64_t units = c.n * (int64_t)((c.K + kRows - 1) / kRows);
     int64_t grid = num_sms;
-    if (grid > c.n) grid = c.n;
-    dense_kernel<<<(int)grid, kThreads, smem, st>>>(c);
+    if (grid > units) grid = units;
+    dense_kernel<<<(int)grid, kThreads, smem, st>>>(*(const CUtensorMap*)tmap, c);
     return cudaGetLastError();
 }
 

@@ -1,124 +1,147 @@
-// Angular DFT of the polar images and survivor compaction for the BF16 tensor-core path.
+// Angular DFT of the polar images for the BF16 tensor-core path.
 //
 // The paper notes (Section 2.2, complexity paragraph) that the azimuthal cross-correlation
-// can be computed through an FFT along phi instead of sliding the template.  The BF16 path
-// uses the correlation theorem along theta: with X^[r, m] = sum_theta X[r, theta]
+// can be computed through an FFT along phi instead of sliding the template.  The tensor-core
+// path uses the correlation theorem along theta: with X^[r, m] = sum_theta X[r, theta]
 // e^{-2 pi i m theta / n}, the correlation of template k with pattern P at shift s is
 //   C[k, s] = sum_{m=0}^{n/2} (w_m / n) Re( G[k, m] e^{2 pi i m s / n} ),
 //   G[k, m] = sum_r conj(T^_k[r, m]) P^[r, m]                (w = 1 at m = 0, n/2; else 2).
-// This file computes P^ (divided by |P|) for the radii the libraries use, in FP32, stored
-// as half precision (values are bounded by sqrt(n_theta)), one CTA per pattern.
-#include <cuda_fp16.h>
+// This file computes P^ / |P| for the radii one library uses, in FP32, and stores it as BF16
+// in the layout of stage A's GEMM (G = T^ x P^ per frequency slot, real arithmetic):
+//   out[j][p][0][2 a + {0, 1}] = ( Re P^[r_a, m],  Im P^[r_a, m])   -> Re G column,
+//   out[j][p][1][2 a + {0, 1}] = ( Im P^[r_a, m], -Re P^[r_a, m])   -> Im G column,
+// for slot j (m = 2 j for j < 96, m = 2 (j - 96) + 1 for j >= 96; slots with m > n/2 and the
+// rows a >= n_rad up to the padded count R are zero), so that with T^ stored as
+// (Re T^, Im T^) pairs, Re G = sum_a (Re T^ Re P^ + Im T^ Im P^) and
+// Im G = sum_a (Re T^ Im P^ - Im T^ Re P^).
+#include <cuda_bf16.h>
 
 #include "tm_internal.h"
 
 namespace tmgb {
 namespace {
 
-// grid-stride over patterns; thread handles (radius slot, frequency m)
+constexpr int kSlots = 192;
+
+__device__ __forceinline__ int slot_freq(int j) { return j < kSlots / 2 ? 2 * j : 2 * (j - kSlots / 2) + 1; }
+
+// grid-stride over patterns; a thread handles (slot j, radius row a), rows fastest
 __global__ void __launch_bounds__(256)
 dft_kernel(const float* __restrict__ polar, const float* __restrict__ pnorm, int64_t n, int n_r, int n_theta,
-           const int32_t* __restrict__ radii, int n_rad, int n_freq, const float2* __restrict__ twiddle,
-           __half2* __restrict__ out) {
+           const int32_t* __restrict__ radii, int n_rad, int R, const float2* __restrict__ twiddle,
+           __nv_bfloat162* __restrict__ out) {
     extern __shared__ float sm[];
-    float* rows = sm;                                  // [n_rad][n_theta]
-    float2* tw = (float2*)(rows + (size_t)n_rad * n_theta);  // [n_theta]: (cos, sin) of 2 pi j / n
+    const int pitch = n_theta + 1;                     // odd pitch: rows a and a + 1 fall in other banks
+    float* rows = sm;                                  // [n_rad][pitch]
+    float2* tw = (float2*)(rows + (((size_t)n_rad * pitch + 1) & ~(size_t)1));  // (cos, sin) of 2 pi j / n
     for (int i = threadIdx.x; i < n_theta; i += blockDim.x) tw[i] = twiddle[i];
+    const int H = n_theta / 2;
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
         __syncthreads();
         const float* src = polar + (size_t)p * n_r * n_theta;
         for (int i = threadIdx.x; i < n_rad * n_theta; i += blockDim.x) {
             const int a = i / n_theta, th = i - a * n_theta;
-            rows[i] = src[(size_t)radii[a] * n_theta + th];
+            rows[a * pitch + th] = src[(size_t)radii[a] * n_theta + th];
         }
         __syncthreads();
         const float pn = pnorm[p];
         const float inv = pn > 0.0f ? 1.0f / pn : 0.0f;
-        __half2* o = out + (size_t)p * n_rad * n_freq;
-        for (int idx = threadIdx.x; idx < n_rad * n_freq; idx += blockDim.x) {
-            const int a = idx / n_freq, m = idx - a * n_freq;
-            const float* row = rows + (size_t)a * n_theta;
+        for (int idx = threadIdx.x; idx < kSlots * R; idx += blockDim.x) {
+            const int j = idx / R, a = idx - j * R;
+            const int m = slot_freq(j);
             float re = 0.0f, im = 0.0f;
-            const float2 step = tw[m];                 // e^{2 pi i m / n}
-            int j = 0;                                 // (m * theta) mod n_theta at block starts
-            for (int th0 = 0; th0 < n_theta; th0 += 32) {
-                float2 w = tw[j];                      // exact restart every 32 angles
-                const int th1 = min(th0 + 32, n_theta);
-                for (int th = th0; th < th1; ++th) {
-                    const float v = row[th];           // same address across the warp: broadcast
-                    re = fmaf(v, w.x, re);
-                    im = fmaf(-v, w.y, im);
-                    const float wx = w.x * step.x - w.y * step.y;
-                    w.y = fmaf(w.x, step.y, w.y * step.x);
-                    w.x = wx;
+            if (a < n_rad && m <= H) {
+                const float* row = rows + (size_t)a * pitch;
+                const float2 step = tw[m];                 // e^{2 pi i m / n}
+                int jj = 0;                                // (m * theta) mod n_theta at block starts
+                for (int th0 = 0; th0 < n_theta; th0 += 32) {
+                    float2 w = tw[jj];                     // exact restart every 32 angles
+                    const int th1 = min(th0 + 32, n_theta);
+                    for (int th = th0; th < th1; ++th) {
+                        const float v = row[th];
+                        re = fmaf(v, w.x, re);
+                        im = fmaf(-v, w.y, im);
+                        const float wx = w.x * step.x - w.y * step.y;
+                        w.y = fmaf(w.x, step.y, w.y * step.x);
+                        w.x = wx;
+                    }
+                    jj = (int)(((int64_t)m * th1) % n_theta);
                 }
-                j = (int)(((int64_t)m * th1) % n_theta);
+                re *= inv;
+                im *= inv;
             }
-            o[idx] = __floats2half2_rn(re * inv, im * inv);
+            __nv_bfloat162* o = out + ((size_t)j * n + p) * 2 * R;
+            o[a] = __floats2bfloat162_rn(re, im);
+            o[R + a] = __floats2bfloat162_rn(im, -re);
         }
     }
 }
 
-// Survivors of the pre-filter mask in the library's dense order (templates sorted by spot
-// count, so a warp of the tensor-core kernel holds templates of similar cost).
-__global__ void __launch_bounds__(512)
-compact_kernel(const uint32_t* __restrict__ mask, int64_t n, int K, int words, const int32_t* __restrict__ order,
-               int keep, int32_t* __restrict__ list) {
-    __shared__ int wsum[16];
-    __shared__ int base_s;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
-        const uint32_t* mrow = mask + (size_t)p * words;
-        if (threadIdx.x == 0) base_s = 0;
-        __syncthreads();
-        for (int d0 = 0; d0 < K; d0 += blockDim.x) {
-            const int d = d0 + threadIdx.x;
-            int k = -1;
-            bool on = false;
-            if (d < K) {
-                k = order[d];
-                on = (mrow[k >> 5] >> (k & 31)) & 1u;
-            }
-            const unsigned b = __ballot_sync(0xffffffffu, on);
-            if (lane == 0) wsum[warp] = __popc(b);
-            __syncthreads();
-            int before = base_s;
-            for (int w = 0; w < warp; ++w) before += wsum[w];
-            before += __popc(b & ((1u << lane) - 1u));
-            if (on && before < keep) list[(size_t)p * keep + before] = k;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int t = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-                base_s += t;
-            }
-            __syncthreads();
+// Template spectra for stage A (built once per library): out[j][2 a + {0, 1}][k] =
+// (Re, Im) of T^_k[r_a, m] / |T_k| = sum over the spots i of k at radius r_a of
+// (I_i / |T_k|) e^{-2 pi i m t_i / n}, BF16, rows a >= n_rad and slots with m > n/2 zero.
+// A block takes 128 templates of one slot j; each thread adds its template's spots into its own
+// column of a shared [2 R][128] FP32 image, which the block then writes row by row.
+__global__ void __launch_bounds__(128)
+spectra_kernel(const int32_t* __restrict__ off, const int32_t* __restrict__ rt, const int2* __restrict__ spot,
+               const float* __restrict__ norm, const int32_t* __restrict__ rowmap, int K, int K_pad, int R,
+               int n_theta, const float2* __restrict__ twiddle, __nv_bfloat16* __restrict__ out) {
+    extern __shared__ float acc[];                     // [2 R][128]
+    const int j = blockIdx.y, k0 = blockIdx.x * 128, k = k0 + threadIdx.x;
+    const int m = slot_freq(j), H = n_theta / 2;
+    for (int i = threadIdx.x; i < 2 * R * 128; i += 128) acc[i] = 0.0f;
+    __syncthreads();
+    if (k < K && m <= H) {
+        const float nk = norm[k];
+        const float inv = nk > 0.0f ? 1.0f / nk : 0.0f;
+        for (int i = off[k]; i < off[k + 1]; ++i) {
+            const int v = rt[i];
+            const int r = v & 0xffff, t = v >> 16;
+            const int a = rowmap[r];
+            const float I = __int_as_float(spot[i].y) * inv;
+            const float2 w = twiddle[(int)(((int64_t)m * t) % n_theta)];
+            acc[(2 * a) * 128 + threadIdx.x] += I * w.x;
+            acc[(2 * a + 1) * 128 + threadIdx.x] -= I * w.y;
         }
     }
+    __syncthreads();
+    if (k < K_pad)
+        for (int row = 0; row < 2 * R; ++row)
+            out[((size_t)j * 2 * R + row) * K_pad + k] = __float2bfloat16_rn(acc[row * 128 + threadIdx.x]);
 }
 
 }  // namespace
 
+cudaError_t launch_spectra(const int32_t* off, const int32_t* rt, const int2* spot, const float* norm,
+                           const int32_t* rowmap, int K, int K_pad, int R, int n_theta, const float2* twiddle,
+                           void* out, cudaStream_t st) {
+    if (K <= 0) return cudaSuccess;
+    const size_t smem = (size_t)2 * R * 128 * 4;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const cudaError_t e = kernel_occupancy((const void*)spectra_kernel, 128, smem, nullptr);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((K_pad + 127) / 128), (unsigned)kSlots);
+    spectra_kernel<<<grid, 128, smem, st>>>(off, rt, spot, norm, rowmap, K, K_pad, R, n_theta, twiddle,
+                                            (__nv_bfloat16*)out);
+    return cudaGetLastError();
+}
+
+size_t dft_smem_bytes(int n_rad, int n_theta) {
+    return ((((size_t)n_rad * (n_theta + 1) + 1) & ~(size_t)1)) * 4 + (size_t)n_theta * 8;
+}
+
 cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_r, int n_theta, const int32_t* radii,
-                       int n_rad, int n_freq, const float2* twiddle, void* out, int num_sms, cudaStream_t st) {
+                       int n_rad, int R, const float2* twiddle, void* out, int num_sms, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const size_t smem = (size_t)n_rad * n_theta * 4 + (size_t)n_theta * 8;
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const size_t smem = dft_smem_bytes(n_rad, n_theta);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     int per_sm = 1;
     const cudaError_t e = kernel_occupancy((const void*)dft_kernel, 256, smem, &per_sm);
     if (e != cudaSuccess) return e;
     int64_t grid = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
     if (grid > n) grid = n;
-    dft_kernel<<<(int)grid, 256, smem, st>>>(polar, pnorm, n, n_r, n_theta, radii, n_rad, n_freq, twiddle,
-                                             (__half2*)out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_compact(const uint32_t* mask, int64_t n, int K, const int32_t* order, int keep, int32_t* list,
-                           cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int grid = (int)(n < 65536 ? n : 65536);
-    compact_kernel<<<grid, 512, 0, st>>>(mask, n, K, (K + 31) / 32, order, keep, list);
+    dft_kernel<<<(int)grid, 256, smem, st>>>(polar, pnorm, n, n_r, n_theta, radii, n_rad, R, twiddle,
+                                             (__nv_bfloat162*)out);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,10 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cublas_v2.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "tm_internal.h"
 
 namespace {
@@ -80,11 +84,16 @@ struct Library {
     int32_t* d_nshift = nullptr;
     float* d_radial = nullptr;     // [K][n_rad rounded up to 4] radial profiles at the distinct radii
     float* d_rnorm = nullptr;
-    int32_t* d_rt = nullptr;       // r | (t << 16) per spot (BF16 path)
+    int32_t* d_rt = nullptr;       // r | (t << 16) per spot (BF16 path, refinement)
     int32_t* d_radii = nullptr;    // distinct spot radii (sparse kernel rows)
-    int32_t* d_order = nullptr;    // templates sorted by spot count (BF16 tile order)
     std::vector<int32_t> radii;    // distinct radii with spots
     size_t bytes = 0;
+    // angular spectra of the templates for the tensor-core path, built on first use:
+    // [192 slots][2 R][K_pad] BF16 (R = distinct radii rounded up to 8, K_pad = K rounded up to 64)
+    void* d_that = nullptr;
+    int32_t* d_rowmap = nullptr;   // [n_r] radius -> row among the distinct radii (-1: none)
+    int R = 0, K_pad = 0;
+    size_t that_bytes = 0;
 };
 
 struct Buffer {
@@ -168,6 +177,8 @@ struct tm_ctx {
     unsigned* d_error = nullptr;   // device error word of the bounded waits
     unsigned long long* d_work = nullptr;   // sparse multiply-adds executed while profiling
     std::map<int, SpectralTables> spectral;
+    cublasHandle_t cublas = nullptr;                     // stage A of the tensor-core path
+    PFN_cuTensorMapEncodeTiled_v12000 encode_tiled = nullptr;
     std::map<std::string, RadiusMap> radius_maps;
     // CUDA graphs of whole-path calls (TM_INDEX_GRAPH)
     struct GraphEntry {
@@ -508,11 +519,6 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
             radf[(size_t)k * n_pad + j] = (float)radial[(size_t)k * L->n_r + L->radii[j]];
     std::vector<int32_t> rt(L->r.size());
     for (size_t i = 0; i < rt.size(); ++i) rt[i] = L->r[i] | (L->t[i] << 16);
-    std::vector<int32_t> order(L->K);
-    for (int64_t k = 0; k < L->K; ++k) order[k] = (int32_t)k;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        return L->off[x + 1] - L->off[x] < L->off[y + 1] - L->off[y];
-    });
     struct Up { void** dst; const void* src; size_t bytes; const char* what; };
     Up ups[] = {
         {(void**)&L->d_off, off32.data(), off32.size() * 4, "library offsets"},
@@ -524,7 +530,6 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
         {(void**)&L->d_radial, radf.data(), radf.size() * 4, "library radial profiles"},
         {(void**)&L->d_rnorm, rnf.data(), rnf.size() * 4, "library radial norms"},
         {(void**)&L->d_rt, rt.data(), rt.size() * 4, "library spot positions"},
-        {(void**)&L->d_order, order.data(), order.size() * 4, "library tile order"},
         {(void**)&L->d_radii, L->radii.data(), L->radii.size() * 4, "library radii"},
     };
     for (auto& u : ups) {
@@ -544,11 +549,11 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
 }
 
 void free_library(tm_ctx* ctx, Library* L) {
-    void* ps[] = {L->d_off,    L->d_spot, L->d_spot2, L->d_meta, L->d_norm, L->d_nshift,
-                  L->d_radial, L->d_rnorm, L->d_rt, L->d_order, L->d_radii, L->d_bspot};
+    void* ps[] = {L->d_off,    L->d_spot,  L->d_spot2, L->d_meta,  L->d_norm,   L->d_nshift, L->d_radial,
+                  L->d_rnorm,  L->d_rt,    L->d_radii, L->d_bspot, L->d_that,   L->d_rowmap};
     for (void* p : ps)
         if (p) cudaFree(p);
-    ctx->used -= std::min(ctx->used, L->bytes);
+    ctx->used -= std::min(ctx->used, L->bytes + L->that_bytes);
 }
 
 tmgb::SparseLib sparse_view(const Library* L) {
@@ -661,6 +666,184 @@ int radius_map(tm_ctx* ctx, Library* const* libs, const int32_t* ids, int n_libs
     return TM_OK;
 }
 
+// ---------------------------------------------------------------- tensor-core path (A7)
+
+// Batch of the tensor-core stages: patterns whose spectra P^ and products G are resident at
+// once, sized so that G (768 B per pattern and padded template) stays within 4 GiB (or a
+// quarter of the context's free budget).
+struct TensorPlan {
+    int64_t nb = 0;
+    size_t phat_per = 0, g_per = 0;        // bytes per pattern
+    size_t bytes(int64_t m) const { return (size_t)m * (phat_per + g_per) + ((size_t)32 << 20); }
+};
+struct TensorBuffers {
+    int64_t nb = 0;
+    void* phat = nullptr;
+    void* g = nullptr;
+    void* cublas_ws = nullptr;
+    size_t cublas_ws_bytes = 0;
+};
+
+inline int lib_R(const Library* L) { return ((int)std::max<size_t>(1, L->radii.size()) + 7) & ~7; }
+inline int lib_K_pad(const Library* L) { return (int)((L->K + 63) & ~(int64_t)63); }
+
+int tensor_plan(tm_ctx* ctx, Library* const* libs, int n_libs, int n_theta, TensorPlan* tp) {
+    int R = 8, K_pad = 64;
+    for (int i = 0; i < n_libs; ++i) {
+        R = std::max(R, lib_R(libs[i]));
+        K_pad = std::max(K_pad, lib_K_pad(libs[i]));
+        const int n_rad = (int)std::max<size_t>(1, libs[i]->radii.size());
+        if (tmgb::dft_smem_bytes(n_rad, n_theta) > 227 * 1024)
+            return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: %d distinct radii exceed the DFT kernel's shared memory",
+                        n_rad);
+    }
+    const size_t slots = (size_t)tmgb::dense_slots();
+    tp->phat_per = slots * 2 * 2 * R * 2;
+    tp->g_per = slots * 2 * K_pad * 2;
+    size_t cap = (size_t)4 << 30;
+    if (ctx->budget) {
+        const size_t freeb = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
+        cap = std::min(cap, freeb / 4);
+    }
+    tp->nb = (int64_t)std::max<size_t>(1, cap / (tp->phat_per + tp->g_per));
+    return TM_OK;
+}
+
+int tensor_buffers(tm_ctx* ctx, cudaStream_t st, const TensorPlan& tp, int64_t nb, TensorBuffers* tb) {
+    tb->nb = nb;
+    tb->cublas_ws_bytes = (size_t)32 << 20;
+    int rc = workspace(ctx, st, "phat", (size_t)nb * tp.phat_per, &tb->phat);
+    if (!rc) rc = workspace(ctx, st, "gmat", (size_t)nb * tp.g_per, &tb->g);
+    if (!rc) rc = workspace(ctx, st, "cublas_ws", tb->cublas_ws_bytes, &tb->cublas_ws);
+    return rc;
+}
+
+// Angular spectra T^ of a library's templates (stage A's left operand), built on the device the
+// first time the tensor-core path uses the library; the call waits for the build, so that work
+// on other streams can use the spectra as soon as it returns.
+int ensure_spectra(tm_ctx* ctx, Library* L, const SpectralTables& spec, cudaStream_t st) {
+    if (L->d_that) return TM_OK;
+    if (ctx->capturing) return fail(TM_ERR_CUDA, "library spectra built during graph capture");
+    const int R = lib_R(L), K_pad = lib_K_pad(L);
+    std::vector<int32_t> rowmap(L->n_r, -1);
+    for (size_t i = 0; i < L->radii.size(); ++i) rowmap[L->radii[i]] = (int32_t)i;
+    const size_t tb = (size_t)tmgb::dense_slots() * 2 * R * K_pad * 2;
+    void* that = nullptr;
+    void* rows = nullptr;
+    int rc = dev_alloc(ctx, &that, tb, "library spectra");
+    if (rc) return rc;
+    rc = dev_alloc(ctx, &rows, rowmap.size() * 4, "library radius rows");
+    if (rc) {
+        dev_free(ctx, that, tb);
+        return rc;
+    }
+    L->d_that = that;
+    L->d_rowmap = (int32_t*)rows;
+    L->R = R;
+    L->K_pad = K_pad;
+    L->that_bytes = tb + rowmap.size() * 4;
+    TM_CUDA(cudaMemcpy(L->d_rowmap, rowmap.data(), rowmap.size() * 4, cudaMemcpyHostToDevice), "library radius rows");
+    TM_CUDA(tmgb::launch_spectra(L->d_off, L->d_rt, L->d_spot, L->d_norm, L->d_rowmap, (int)L->K, K_pad, R, L->n_theta,
+                                 spec.twiddle, L->d_that, st),
+            "library spectra");
+    TM_CUDA(cudaStreamSynchronize(st), "library spectra");
+    return TM_OK;
+}
+
+// Tensor map of G [192][nb][2][K_pad] BF16 for stage B: 4-D (k, c, p, j), boxes of
+// 64 templates x 2 x 1 pattern x 32 slots, 128-byte swizzle, zero fill past K.
+int g_tensor_map(tm_ctx* ctx, void* g, int K, int K_pad, int64_t nb, CUtensorMap* out) {
+    if (!ctx->encode_tiled) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return fail(TM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        }
+        ctx->encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)K, 2, (cuuint64_t)nb, (cuuint64_t)tmgb::dense_slots()};
+    const cuuint64_t strides[3] = {(cuuint64_t)K_pad * 2, (cuuint64_t)K_pad * 4, (cuuint64_t)nb * K_pad * 4};
+    const cuuint32_t box[4] = {64, 2, 1, 32};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = ctx->encode_tiled(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, g, dims, strides, box, es,
+                                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(TM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TM_OK;
+}
+
+// Stage A: for every frequency slot j, G_j [K_pad x 2 nb] = T^_j [K_pad x 2 R] x P^_j [2 R x 2 nb]
+// (column-major, BF16 in and out, FP32 accumulation): one strided batched GEMM on the tensor
+// cores through cuBLAS (a plain library GEMM).
+int stage_a(tm_ctx* ctx, cudaStream_t st, const Library* L, const TensorBuffers& tb, int64_t nb) {
+    cublasStatus_t s = CUBLAS_STATUS_SUCCESS;
+    if (!ctx->cublas) {
+        if (ctx->capturing) return fail(TM_ERR_CUDA, "cuBLAS handle created during graph capture");
+        s = cublasCreate(&ctx->cublas);
+        if (s != CUBLAS_STATUS_SUCCESS) {
+            ctx->cublas = nullptr;
+            return fail(TM_ERR_CUDA, "cublasCreate failed (%d)", (int)s);
+        }
+    }
+    s = cublasSetStream(ctx->cublas, st);
+    if (s == CUBLAS_STATUS_SUCCESS) s = cublasSetWorkspace(ctx->cublas, tb.cublas_ws, tb.cublas_ws_bytes);
+    if (s != CUBLAS_STATUS_SUCCESS) return fail(TM_ERR_CUDA, "cuBLAS set-up failed (%d)", (int)s);
+    const float one = 1.0f, zero = 0.0f;
+    const int R2 = 2 * L->R;
+    s = cublasGemmStridedBatchedEx(ctx->cublas, CUBLAS_OP_N, CUBLAS_OP_N, L->K_pad, (int)(2 * nb), R2, &one,
+                                   L->d_that, CUDA_R_16BF, L->K_pad, (long long)R2 * L->K_pad, tb.phat, CUDA_R_16BF,
+                                   R2, (long long)nb * 2 * R2, &zero, tb.g, CUDA_R_16BF, L->K_pad,
+                                   (long long)2 * nb * L->K_pad, tmgb::dense_slots(), CUBLAS_COMPUTE_32F,
+                                   CUBLAS_GEMM_DEFAULT);
+    if (s != CUBLAS_STATUS_SUCCESS) return fail(TM_ERR_CUDA, "stage A GEMM failed (cuBLAS status %d)", (int)s);
+    return TM_OK;
+}
+
+// Pre-scores of library L for the call's rows [0, m): angular DFT of the polar rows (P^), stage A
+// (G), stage B (inverse DFT and maximum over shifts on tcgen05), in batches of tb.nb patterns.
+// mask (nullable): templates to score per row; out [m][K] (-NaN where not scored).
+int prescore_rows(tm_ctx* ctx, cudaStream_t st, const Library* L, const SpectralTables& spec, const TensorBuffers& tb,
+                  const float* polar, const float* pnorm, int64_t m, const uint32_t* mask, float* out, int stall,
+                  int64_t* launches) {
+    const int n_rad = (int)std::max<size_t>(1, L->radii.size());
+    for (int64_t b0 = 0; b0 < m; b0 += tb.nb) {
+        const int64_t nb = std::min(tb.nb, m - b0);
+        {
+            StageTimer tmr(ctx, TM_STAGE_DFT, st);
+            TM_CUDA(tmgb::launch_dft(polar + (size_t)b0 * L->n_r * L->n_theta, pnorm + b0, nb, L->n_r, L->n_theta,
+                                     L->d_radii, n_rad, L->R, spec.twiddle, tb.phat, ctx->num_sms, st),
+                    "tensor path: dft");
+        }
+        {
+            StageTimer tmr(ctx, TM_STAGE_GEMM, st);
+            const int rc = stage_a(ctx, st, L, tb, nb);
+            if (rc) return rc;
+        }
+        CUtensorMap map;
+        const int rc = g_tensor_map(ctx, tb.g, (int)L->K, L->K_pad, nb, &map);
+        if (rc) return rc;
+        tmgb::DenseCall dc{};
+        dc.n = nb;
+        dc.p0 = b0;
+        dc.n_theta = L->n_theta;
+        dc.K = (int)L->K;
+        dc.basis = spec.basis;
+        dc.mask = mask;
+        dc.words = (int)((L->K + 31) / 32);
+        dc.pre = out;
+        dc.error = ctx->d_error;
+        dc.stall = stall;
+        {
+            StageTimer tmr(ctx, TM_STAGE_DENSE, st);
+            TM_CUDA(tmgb::launch_dense(&map, dc, ctx->num_sms, st), "tensor path: stage B");
+        }
+        *launches += 2;                  // this library's kernels (the GEMM is cuBLAS's)
+    }
+    return TM_OK;
+}
+
 // Signature of a set of libraries for the autotuner: shapes, not ids, so that a tuning
 // cache written by one process applies in the next.
 std::string tune_key(Library* const* libs, int n_libs, int top_n) {
@@ -670,17 +853,6 @@ std::string tune_key(Library* const* libs, int n_libs, int top_n) {
              std::to_string(libs[i]->radii.size()) + "/" + std::to_string(libs[i]->n_theta);
     }
     return k + "|N" + std::to_string(top_n);
-}
-
-tmgb::DenseLib dense_view(const Library* L) {
-    tmgb::DenseLib v;
-    v.off = L->d_off;
-    v.rt = L->d_rt;
-    v.spot = L->d_spot;
-    v.norm = L->d_norm;
-    v.order = L->d_order;
-    v.K = (int32_t)L->K;
-    return v;
 }
 
 int check_params(const tm_index_params* p) {
@@ -1120,6 +1292,7 @@ void tm_destroy(tm_ctx* ctx) {
             cudaFree(kv.second.rmap);
             cudaFree(kv.second.keep_row);
         }
+        if (ctx->cublas) cublasDestroy(ctx->cublas);
         if (ctx->d_error) cudaFree(ctx->d_error);
         if (ctx->d_work) cudaFree(ctx->d_work);
         for (cudaStream_t hs : ctx->host_streams)
@@ -1364,52 +1537,46 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     if (rc) return rc;
     const bool pre = params->prefilter_fraction < 1.0;
     const int kc = params->rescore_k;
-    const int n_freq = n_theta / 2 + 1;
     SpectralTables spec;
     RadiusMap rmap;
     rc = radius_map(ctx, libs, lib_ids, n_libs, n_r, &rmap);
     if (rc) return rc;
+    TensorPlan tp;
     if (bf16) {
         if (!tmgb::dense_supported(n_theta))
             return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: the BF16 path needs an even n_theta <= 376 (got %d)",
                         n_theta);
         rc = spectral_tables(ctx, n_theta, &spec);
+        if (!rc) rc = tensor_plan(ctx, libs, n_libs, n_theta, &tp);
         if (rc) return rc;
-        if (tmgb::dense_smem_bytes(n_theta, n_r, rmap.n_rad, n_freq) > 232448)
-            return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: %d distinct radii exceed the BF16 kernel's shared memory",
-                        rmap.n_rad);
     }
     int keep[TM_MAX_LIBS];
     for (int i = 0; i < n_libs; ++i) keep[i] = keep_count(params->prefilter_fraction, libs[i]->K);
 
     // chunk size from a per-pattern workspace estimate (<= 4 GiB of workspace)
     size_t per = (size_t)n_r * n_theta * 4 + 4 + (size_t)n_r * 4 + 4;
-    for (int i = 0; i < n_libs; ++i) {
+    for (int i = 0; i < n_libs; ++i)
         if (pre || bf16) per += (size_t)libs[i]->K * 4 + ((libs[i]->K + 31) / 32) * 4;
-        if (pre && bf16) per += (size_t)keep[i] * 4;
-    }
-    if (bf16) per += (size_t)rmap.n_rad * n_freq * 4;
     size_t cap = (size_t)4 << 30;
     if (ctx->budget) {
         const size_t freeb = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
-        cap = std::min(cap, freeb / 2);
+        cap = std::min(cap, (freeb - std::min(freeb, tp.bytes(tp.nb))) / 2);
     }
     int64_t chunk = (int64_t)std::max<size_t>(1, cap / per);
     chunk = std::min<int64_t>(chunk, n);
 
     float *polar, *pnorm, *radial, *rn = nullptr;
-    void* phat = nullptr;
     int* pcount = nullptr;
     rc = workspace(ctx, st, "pattern_counter", sizeof(int), (void**)&pcount);
     if (!rc) rc = workspace(ctx, st, "polar", (size_t)chunk * n_r * n_theta * 4, (void**)&polar);
     if (!rc) rc = workspace(ctx, st, "pnorm", (size_t)chunk * 4, (void**)&pnorm);
     if (!rc) rc = workspace(ctx, st, "radial", (size_t)chunk * n_r * 4, (void**)&radial);
     if (!rc && pre) rc = workspace(ctx, st, "radial_norm", (size_t)chunk * 4, (void**)&rn);
-    if (!rc && bf16) rc = workspace(ctx, st, "phat", (size_t)chunk * rmap.n_rad * n_freq * 4, &phat);
+    TensorBuffers tb;
+    if (!rc && bf16) rc = tensor_buffers(ctx, st, tp, std::min<int64_t>(tp.nb, chunk), &tb);
     if (rc) return rc;
     float* score[TM_MAX_LIBS] = {};
     uint32_t* mask[TM_MAX_LIBS] = {};
-    int32_t* list[TM_MAX_LIBS] = {};
     for (int i = 0; i < n_libs; ++i) {
         const std::string s = std::to_string(i);
         // mask: the pre-filter's keep-mask, on the BF16 path reused afterwards for the mask of
@@ -1417,9 +1584,13 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
         if (bf16) rc = workspace(ctx, st, "score" + s, (size_t)chunk * libs[i]->K * 4, (void**)&score[i]);
         if (!rc && (pre || bf16))
             rc = workspace(ctx, st, "mask" + s, (size_t)chunk * ((libs[i]->K + 31) / 32) * 4, (void**)&mask[i]);
-        if (!rc && pre && bf16) rc = workspace(ctx, st, "list" + s, (size_t)chunk * keep[i] * 4, (void**)&list[i]);
         if (rc) return rc;
     }
+    if (bf16)
+        for (int i = 0; i < n_libs; ++i) {
+            rc = ensure_spectra(ctx, libs[i], spec, st);
+            if (rc) return rc;
+        }
     const size_t esz = dtype == TM_DTYPE_U16 ? 2 : 4;
     // the sparse kernel's block size: forced (autotuning), tuned for these libraries, or by
     // default 256 -- but 512 when the chunk has at most two patterns per SM, so that each
@@ -1449,15 +1620,10 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                 TM_CUDA(tmgb::launch_radial_norm(radial, m, n_r, rn, st), "tm_index_patterns: radial norm");
                 ++launches;
                 for (int i = 0; i < n_libs; ++i) {
-                    Library* L = libs[i];
-                    TM_CUDA(tmgb::launch_prefilter(radial, rn, m, n_r, radial_lib(L), keep[i], mask[i], nullptr, st),
+                    TM_CUDA(tmgb::launch_prefilter(radial, rn, m, n_r, radial_lib(libs[i]), keep[i], mask[i], nullptr,
+                                                   st),
                             "tm_index_patterns: pre-filter");
                     ++launches;
-                    if (bf16) {
-                        TM_CUDA(tmgb::launch_compact(mask[i], m, (int)L->K, L->d_order, keep[i], list[i], st),
-                                "tm_index_patterns: compact");
-                        ++launches;
-                    }
                 }
             }
             tmgb::SparseCall c{};
@@ -1480,38 +1646,13 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             c.threads = sparse_threads;
             c.work = ctx->profiling ? ctx->d_work : nullptr;
             if (bf16) {
-                {
-                    StageTimer tmr(ctx, TM_STAGE_DFT, st);
-                    TM_CUDA(tmgb::launch_dft(polar, pnorm, m, n_r, n_theta, rmap.radii, rmap.n_rad, n_freq, spec.twiddle,
-                                             phat, ctx->num_sms, st), "tm_index_patterns: dft");
-                }
-                ++launches;
-                tmgb::DenseCall dc{};
-                dc.phat = phat;
-                dc.n = m;
-                dc.n_theta = n_theta;
-                dc.n_r = n_r;
-                dc.n_rad = rmap.n_rad;
-                dc.n_freq = n_freq;
-                dc.rmap = rmap.rmap;
-                dc.basis = spec.basis;
-                dc.twiddle = spec.twiddle;
-                dc.n_libs = n_libs;
                 for (int i = 0; i < n_libs; ++i) {
-                    dc.lib[i] = dense_view(libs[i]);
-                    dc.list[i] = pre ? list[i] : nullptr;
-                    dc.count[i] = keep[i];
-                    dc.pre[i] = score[i];
-                    // templates not scored read as -NaN, the smallest key of the select
-                    TM_CUDA(cudaMemsetAsync(score[i], 0xFF, (size_t)m * libs[i]->K * 4, st), "tm_index_patterns: memset");
+                    int64_t nl = 0;
+                    const int rc2 = prescore_rows(ctx, st, libs[i], spec, tb, polar, pnorm, m, pre ? mask[i] : nullptr,
+                                                  score[i], (params->reserved & TM_INDEX_TEST_STALL) ? 1 : 0, &nl);
+                    if (rc2) return rc2;
+                    launches += nl;
                 }
-                dc.error = ctx->d_error;
-                dc.stall = (params->reserved & TM_INDEX_TEST_STALL) ? 1 : 0;
-                {
-                    StageTimer tmr(ctx, TM_STAGE_DENSE, st);
-                    TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_index_patterns: dense");
-                }
-                ++launches;
                 {
                     StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
                     for (int i = 0; i < n_libs; ++i) {
@@ -1700,58 +1841,34 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
     DeviceGuard g(ctx->device);
     Library* L = find_lib(ctx, lib_id);
     if (!L) return fail(TM_ERR_NOT_FOUND, "tm_prescore: no library %d", lib_id);
-    const int n_r = L->n_r, n_theta = L->n_theta, n_freq = n_theta / 2 + 1;
+    const int n_r = L->n_r, n_theta = L->n_theta;
     if (!tmgb::dense_supported(n_theta))
         return fail(TM_ERR_UNSUPPORTED, "tm_prescore: needs an even n_theta <= 376 (got %d)", n_theta);
     SpectralTables spec;
-    RadiusMap rm;
+    TensorPlan tp;
     Library* libs[1] = {L};
-    int32_t ids[1] = {lib_id};
     int rc = spectral_tables(ctx, n_theta, &spec);
-    if (!rc) rc = radius_map(ctx, libs, ids, 1, n_r, &rm);
+    if (!rc) rc = tensor_plan(ctx, libs, 1, n_theta, &tp);
     if (rc) return rc;
-    if (tmgb::dense_smem_bytes(n_theta, n_r, rm.n_rad, n_freq) > 232448)
-        return fail(TM_ERR_UNSUPPORTED, "tm_prescore: %d distinct radii exceed shared memory", rm.n_rad);
     const int keep = keep_count(fraction, L->K);
     cudaStream_t st = (cudaStream_t)stream;
-    void* phat;
-    rc = workspace(ctx, st, "phat", (size_t)n * rm.n_rad * n_freq * 4, &phat);
+    TensorBuffers tb;
+    rc = tensor_buffers(ctx, st, tp, std::min<int64_t>(tp.nb, n), &tb);
     float* rn = nullptr;
     uint32_t* mask = nullptr;
-    int32_t* list = nullptr;
     if (!rc && fraction < 1.0) {
         rc = workspace(ctx, st, "radial_norm", (size_t)n * 4, (void**)&rn);
         if (!rc) rc = workspace(ctx, st, "mask0", (size_t)n * ((L->K + 31) / 32) * 4, (void**)&mask);
-        if (!rc) rc = workspace(ctx, st, "list0", (size_t)n * keep * 4, (void**)&list);
     }
+    if (!rc) rc = ensure_spectra(ctx, L, spec, st);
     if (rc) return rc;
     if (fraction < 1.0) {
         TM_CUDA(tmgb::launch_radial_norm(radial_dev, n, n_r, rn, st), "tm_prescore: radial norm");
         TM_CUDA(tmgb::launch_prefilter(radial_dev, rn, n, n_r, radial_lib(L), keep, mask, nullptr, st),
                 "tm_prescore: pre-filter");
-        TM_CUDA(tmgb::launch_compact(mask, n, (int)L->K, L->d_order, keep, list, st), "tm_prescore: compact");
     }
-    TM_CUDA(tmgb::launch_dft(polar_dev, norm_dev, n, n_r, n_theta, rm.radii, rm.n_rad, n_freq, spec.twiddle, phat,
-                             ctx->num_sms, st), "tm_prescore: dft");
-    TM_CUDA(cudaMemsetAsync(score_dev, 0xFF, (size_t)n * L->K * 4, st), "tm_prescore: memset");
-    tmgb::DenseCall dc{};
-    dc.phat = phat;
-    dc.n = n;
-    dc.n_theta = n_theta;
-    dc.n_r = n_r;
-    dc.n_rad = rm.n_rad;
-    dc.n_freq = n_freq;
-    dc.rmap = rm.rmap;
-    dc.basis = spec.basis;
-    dc.twiddle = spec.twiddle;
-    dc.n_libs = 1;
-    dc.lib[0] = dense_view(L);
-    dc.list[0] = list;
-    dc.count[0] = keep;
-    dc.pre[0] = score_dev;
-    dc.error = ctx->d_error;
-    TM_CUDA(tmgb::launch_dense(dc, ctx->num_sms, st), "tm_prescore: dense");
-    return TM_OK;
+    int64_t nl = 0;
+    return prescore_rows(ctx, st, L, spec, tb, polar_dev, norm_dev, n, mask, score_dev, 0, &nl);
 }
 
 }  // extern "C"

@@ -180,41 +180,40 @@ int sparse_rows(int n_rad, int layout);
 cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);
 
 // ------------------------------------------------------------------ BF16 tensor-core path
-struct DenseLib {
-    const int32_t* off;        // [K + 1]
-    const int32_t* rt;         // [n_spots]  r | (t << 16)
-    const int2* spot;          // [n_spots]  .y = float bits of the intensity
-    const float* norm;         // [K]
-    const int32_t* order;      // [K]  templates sorted by spot count (tile order)
-    int32_t K;
-};
-
+// Frequency slots of the angular spectra: slot j < 96 holds m = 2 j, slot j >= 96 holds
+// m = 2 (j - 96) + 1 (even frequencies first, for the radix-2 split of stage B); slots whose
+// frequency exceeds n_theta / 2 are zero.
+//   T^ (per library, built once):  [192][2 R][K_pad] BF16, rows (Re, Im) of T^_k[r_a, m] / |T_k|
+//   P^ (per call, per library):    [192][n][2][2 R]  BF16, (Re, Im) and (Im, -Re) of P^[r_a, m] / |P|
+//   G  (stage A: G_j = T^_j P^_j): [192][n][2][K_pad] BF16, (Re, Im) of G[k, m]
+// with R the library's distinct radii rounded up to 8 and K_pad its templates rounded up to 64.
 struct DenseCall {
-    const void* phat;          // [n][n_rad][n_freq] half2: DFT of the polar rows / |P|
-    int64_t n;
-    int n_theta, n_r, n_rad, n_freq;
-    const int32_t* rmap;       // [n_r]  radius -> row of phat (-1 if unused)
+    int64_t n;                 // patterns of the G batch
+    int64_t p0;                // first pattern of the batch in the call's rows (pre, mask)
+    int n_theta;
+    int K;                     // templates of the library
     const void* basis;         // [192][384] bf16, K-major (dense_basis_rows x dense_basis_cols)
-    const float2* twiddle;     // [n_theta]  (cos, sin) of 2 pi j / n_theta
-    int n_libs;
-    DenseLib lib[TM_MAX_LIBS];
-    const int32_t* list[TM_MAX_LIBS];   // [n][count] survivors or null (all, in tile order)
-    int count[TM_MAX_LIBS];             // templates scored per pattern
-    float* pre[TM_MAX_LIBS];            // [n][K] out: pre-score of every scored template
-    unsigned* error;                    // device word: bit 0 = a bounded wait timed out
-    int stall;                          // test hook: the MMA issuer issues nothing
+    const uint32_t* mask;      // [rows][words] templates to score (pre-filter) or null (all)
+    int words;
+    float* pre;                // [rows][K] out: pre-score, -NaN where masked out
+    unsigned* error;           // device word: bit 0 = a bounded wait timed out
+    int stall;                 // test hook: the MMA issuer issues nothing
 };
 
 bool dense_supported(int n_theta);
 int dense_basis_rows();
 int dense_basis_cols();
-size_t dense_smem_bytes(int n_theta, int n_r, int n_rad, int n_freq);
-cudaError_t launch_dense(const DenseCall& c, int num_sms, cudaStream_t st);
+int dense_slots();
+size_t dense_smem_bytes();
+// tmap: the CUtensorMap of G for this batch (4-D: k, c, p, j; box 64 x 2 x 1 x 32; 128-byte swizzle).
+cudaError_t launch_dense(const void* tmap, const DenseCall& c, int num_sms, cudaStream_t st);
+size_t dft_smem_bytes(int n_rad, int n_theta);
 cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_r, int n_theta,
-                       const int32_t* radii, int n_rad, int n_freq, const float2* twiddle, void* out,
+                       const int32_t* radii, int n_rad, int R, const float2* twiddle, void* out,
                        int num_sms, cudaStream_t st);
-cudaError_t launch_compact(const uint32_t* mask, int64_t n, int K, const int32_t* order, int keep,
-                           int32_t* list, cudaStream_t st);
+cudaError_t launch_spectra(const int32_t* off, const int32_t* rt, const int2* spot, const float* norm,
+                           const int32_t* rowmap, int K, int K_pad, int R, int n_theta, const float2* twiddle,
+                           void* out, cudaStream_t st);
 
 // Validation of tm_index_params shared by every whole-path entry point (finite gamma,
 // subtraction and centre; pre-filter fraction; top_n; 16-byte aligned pixel mask; threshold).
