@@ -6,7 +6,8 @@
 // e^{-2 pi i m theta / n}, the correlation of template k with pattern P at shift s is
 //   C[k, s] = sum_{m=0}^{n/2} (w_m / n) Re( G[k, m] e^{2 pi i m s / n} ),
 //   G[k, m] = sum_r conj(T^_k[r, m]) P^[r, m]                (w = 1 at m = 0, n/2; else 2).
-// This file computes P^ / |P| for the radii one library uses, in FP32, and stores it as BF16
+// The DFT itself is a TF32 GEMM of the polar images with the DFT matrix (cuBLAS, a plain
+// library GEMM); this file packs its result, P^ / |P| for the radii one library uses, as BF16
 // in the layout of stage A's GEMM (G = T^ x P^ per frequency slot, real arithmetic):
 //   out[j][p][0][2 a + {0, 1}] = ( Re P^[r_a, m],  Im P^[r_a, m])   -> Re G column,
 //   out[j][p][1][2 a + {0, 1}] = ( Im P^[r_a, m], -Re P^[r_a, m])   -> Im G column,
@@ -25,55 +26,32 @@ constexpr int kSlots = 192;
 
 __device__ __forceinline__ int slot_freq(int j) { return j < kSlots / 2 ? 2 * j : 2 * (j - kSlots / 2) + 1; }
 
-// grid-stride over patterns; a thread handles (slot j, radius row a), rows fastest
+// Packs the angular DFT of a batch into stage A's operand layout.  dftc [192][2][nb][n_r] FP32
+// holds, for slot j, sum_theta P[p, r, theta] (cos, -sin)(2 pi m_j theta / n) for every polar row
+// (a TF32 GEMM of the polar images with the DFT matrix, columns past n/2 zero); this kernel keeps
+// the library's radii, divides by |P| and writes out[j][p][c][2 a + {0, 1}] as BF16.  A thread
+// takes one (slot, pattern, row a); rows are fastest, so the writes of a warp are contiguous.
 __global__ void __launch_bounds__(256)
-dft_kernel(const float* __restrict__ polar, const float* __restrict__ pnorm, int64_t n, int n_r, int n_theta,
-           const int32_t* __restrict__ radii, int n_rad, int R, const float2* __restrict__ twiddle,
-           __nv_bfloat162* __restrict__ out) {
-    extern __shared__ float sm[];
-    const int pitch = n_theta + 1;                     // odd pitch: rows a and a + 1 fall in other banks
-    float* rows = sm;                                  // [n_rad][pitch]
-    float2* tw = (float2*)(rows + (((size_t)n_rad * pitch + 1) & ~(size_t)1));  // (cos, sin) of 2 pi j / n
-    for (int i = threadIdx.x; i < n_theta; i += blockDim.x) tw[i] = twiddle[i];
-    const int H = n_theta / 2;
-    for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
-        __syncthreads();
-        const float* src = polar + (size_t)p * n_r * n_theta;
-        for (int i = threadIdx.x; i < n_rad * n_theta; i += blockDim.x) {
-            const int a = i / n_theta, th = i - a * n_theta;
-            rows[a * pitch + th] = src[(size_t)radii[a] * n_theta + th];
+pack_kernel(const float* __restrict__ dftc, const float* __restrict__ pnorm, int64_t nb, int n_r,
+            const int32_t* __restrict__ radii, int n_rad, int R, __nv_bfloat162* __restrict__ out) {
+    const int64_t total = (int64_t)kSlots * nb * R;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(idx % R);
+        const int64_t jp = idx / R;
+        const int64_t p = jp % nb;
+        const int j = (int)(jp / nb);
+        float re = 0.0f, im = 0.0f;
+        if (a < n_rad) {
+            const float pn = __ldg(pnorm + p);
+            const float inv = pn > 0.0f ? 1.0f / pn : 0.0f;
+            const int r = __ldg(radii + a);
+            re = __ldg(dftc + ((size_t)(2 * j) * nb + p) * n_r + r) * inv;
+            im = __ldg(dftc + ((size_t)(2 * j + 1) * nb + p) * n_r + r) * inv;
         }
-        __syncthreads();
-        const float pn = pnorm[p];
-        const float inv = pn > 0.0f ? 1.0f / pn : 0.0f;
-        for (int idx = threadIdx.x; idx < kSlots * R; idx += blockDim.x) {
-            const int j = idx / R, a = idx - j * R;
-            const int m = slot_freq(j);
-            float re = 0.0f, im = 0.0f;
-            if (a < n_rad && m <= H) {
-                const float* row = rows + (size_t)a * pitch;
-                const float2 step = tw[m];                 // e^{2 pi i m / n}
-                int jj = 0;                                // (m * theta) mod n_theta at block starts
-                for (int th0 = 0; th0 < n_theta; th0 += 32) {
-                    float2 w = tw[jj];                     // exact restart every 32 angles
-                    const int th1 = min(th0 + 32, n_theta);
-                    for (int th = th0; th < th1; ++th) {
-                        const float v = row[th];
-                        re = fmaf(v, w.x, re);
-                        im = fmaf(-v, w.y, im);
-                        const float wx = w.x * step.x - w.y * step.y;
-                        w.y = fmaf(w.x, step.y, w.y * step.x);
-                        w.x = wx;
-                    }
-                    jj = (int)(((int64_t)m * th1) % n_theta);
-                }
-                re *= inv;
-                im *= inv;
-            }
-            __nv_bfloat162* o = out + ((size_t)j * n + p) * 2 * R;
-            o[a] = __floats2bfloat162_rn(re, im);
-            o[R + a] = __floats2bfloat162_rn(im, -re);
-        }
+        __nv_bfloat162* o = out + ((size_t)j * nb + p) * 2 * R;
+        o[a] = __floats2bfloat162_rn(re, im);
+        o[R + a] = __floats2bfloat162_rn(im, -re);
     }
 }
 
@@ -126,22 +104,13 @@ cudaError_t launch_spectra(const int32_t* off, const int32_t* rt, const int2* sp
     return cudaGetLastError();
 }
 
-size_t dft_smem_bytes(int n_rad, int n_theta) {
-    return ((((size_t)n_rad * (n_theta + 1) + 1) & ~(size_t)1)) * 4 + (size_t)n_theta * 8;
-}
-
-cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_r, int n_theta, const int32_t* radii,
-                       int n_rad, int R, const float2* twiddle, void* out, int num_sms, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const size_t smem = dft_smem_bytes(n_rad, n_theta);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    int per_sm = 1;
-    const cudaError_t e = kernel_occupancy((const void*)dft_kernel, 256, smem, &per_sm);
-    if (e != cudaSuccess) return e;
-    int64_t grid = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > n) grid = n;
-    dft_kernel<<<(int)grid, 256, smem, st>>>(polar, pnorm, n, n_r, n_theta, radii, n_rad, R, twiddle,
-                                             (__nv_bfloat162*)out);
+cudaError_t launch_pack(const float* dftc, const float* pnorm, int64_t nb, int n_r, const int32_t* radii, int n_rad,
+                        int R, void* out, int num_sms, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    const int64_t total = (int64_t)kSlots * nb * R;
+    int64_t grid = (total + 255) / 256;
+    if (grid > (int64_t)num_sms * 16) grid = (int64_t)num_sms * 16;
+    pack_kernel<<<(int)grid, 256, 0, st>>>(dftc, pnorm, nb, n_r, radii, n_rad, R, (__nv_bfloat162*)out);
     return cudaGetLastError();
 }
 

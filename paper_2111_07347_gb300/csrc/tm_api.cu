@@ -102,9 +102,10 @@ struct Buffer {
 };
 
 
-struct SpectralTables {            // per n_theta: inverse-DFT basis and twiddles
+struct SpectralTables {            // per n_theta: DFT matrix, inverse-DFT basis and twiddles
     void* basis = nullptr;         // bf16 [rows][cols]
     float2* twiddle = nullptr;     // [n_theta]
+    float* dftmat = nullptr;       // [2 x 192 columns][n_theta]: (cos, -sin)(2 pi m_j theta / n), 0 for m_j > n/2
 };
 
 struct RadiusMap {                 // per set of libraries: union of radii
@@ -624,12 +625,27 @@ int spectral_tables(tm_ctx* ctx, int n_theta, SpectralTables* out) {
             const double ang = 2.0 * kPi * j / n_theta;
             tw[j] = make_float2((float)cos(ang), (float)sin(ang));
         }
+        // forward DFT matrix, column-major [n_theta][2 x 192]: column 2 j + comp of slot j
+        // (m = 2 j for j < 96, else 2 (j - 96) + 1)
+        const int slots = tmgb::dense_slots();
+        std::vector<float> dm((size_t)n_theta * 2 * slots, 0.0f);
+        for (int j = 0; j < slots; ++j) {
+            const int m = j < slots / 2 ? 2 * j : 2 * (j - slots / 2) + 1;
+            if (m > H) continue;
+            for (int th = 0; th < n_theta; ++th) {
+                const double ang = 2.0 * kPi * (double)(((int64_t)m * th) % n_theta) / n_theta;
+                dm[(size_t)(2 * j) * n_theta + th] = (float)cos(ang);
+                dm[(size_t)(2 * j + 1) * n_theta + th] = (float)-sin(ang);
+            }
+        }
         SpectralTables t;
         int rc = dev_alloc(ctx, &t.basis, basis.size() * 2, "dft basis");
         if (!rc) rc = dev_alloc(ctx, (void**)&t.twiddle, tw.size() * 8, "twiddles");
+        if (!rc) rc = dev_alloc(ctx, (void**)&t.dftmat, dm.size() * 4, "dft matrix");
         if (rc) return rc;
         TM_CUDA(cudaMemcpy(t.basis, basis.data(), basis.size() * 2, cudaMemcpyHostToDevice), "dft basis");
         TM_CUDA(cudaMemcpy(t.twiddle, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice), "twiddles");
+        TM_CUDA(cudaMemcpy(t.dftmat, dm.data(), dm.size() * 4, cudaMemcpyHostToDevice), "dft matrix");
         it = ctx->spectral.emplace(n_theta, t).first;
     }
     *out = it->second;
@@ -673,11 +689,12 @@ int radius_map(tm_ctx* ctx, Library* const* libs, const int32_t* ids, int n_libs
 // quarter of the context's free budget).
 struct TensorPlan {
     int64_t nb = 0;
-    size_t phat_per = 0, g_per = 0;        // bytes per pattern
-    size_t bytes(int64_t m) const { return (size_t)m * (phat_per + g_per) + ((size_t)32 << 20); }
+    size_t dftc_per = 0, phat_per = 0, g_per = 0;   // bytes per pattern
+    size_t bytes(int64_t m) const { return (size_t)m * (dftc_per + phat_per + g_per) + ((size_t)32 << 20); }
 };
 struct TensorBuffers {
     int64_t nb = 0;
+    float* dftc = nullptr;
     void* phat = nullptr;
     void* g = nullptr;
     void* cublas_ws = nullptr;
@@ -692,12 +709,9 @@ int tensor_plan(tm_ctx* ctx, Library* const* libs, int n_libs, int n_theta, Tens
     for (int i = 0; i < n_libs; ++i) {
         R = std::max(R, lib_R(libs[i]));
         K_pad = std::max(K_pad, lib_K_pad(libs[i]));
-        const int n_rad = (int)std::max<size_t>(1, libs[i]->radii.size());
-        if (tmgb::dft_smem_bytes(n_rad, n_theta) > 227 * 1024)
-            return fail(TM_ERR_UNSUPPORTED, "tm_index_patterns: %d distinct radii exceed the DFT kernel's shared memory",
-                        n_rad);
     }
     const size_t slots = (size_t)tmgb::dense_slots();
+    tp->dftc_per = slots * 2 * (size_t)libs[0]->n_r * 4;
     tp->phat_per = slots * 2 * 2 * R * 2;
     tp->g_per = slots * 2 * K_pad * 2;
     size_t cap = (size_t)4 << 30;
@@ -705,14 +719,15 @@ int tensor_plan(tm_ctx* ctx, Library* const* libs, int n_libs, int n_theta, Tens
         const size_t freeb = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
         cap = std::min(cap, freeb / 4);
     }
-    tp->nb = (int64_t)std::max<size_t>(1, cap / (tp->phat_per + tp->g_per));
+    tp->nb = (int64_t)std::max<size_t>(1, cap / (tp->dftc_per + tp->phat_per + tp->g_per));
     return TM_OK;
 }
 
 int tensor_buffers(tm_ctx* ctx, cudaStream_t st, const TensorPlan& tp, int64_t nb, TensorBuffers* tb) {
     tb->nb = nb;
     tb->cublas_ws_bytes = (size_t)32 << 20;
-    int rc = workspace(ctx, st, "phat", (size_t)nb * tp.phat_per, &tb->phat);
+    int rc = workspace(ctx, st, "dftc", (size_t)nb * tp.dftc_per, (void**)&tb->dftc);
+    if (!rc) rc = workspace(ctx, st, "phat", (size_t)nb * tp.phat_per, &tb->phat);
     if (!rc) rc = workspace(ctx, st, "gmat", (size_t)nb * tp.g_per, &tb->g);
     if (!rc) rc = workspace(ctx, st, "cublas_ws", tb->cublas_ws_bytes, &tb->cublas_ws);
     return rc;
@@ -777,7 +792,7 @@ int g_tensor_map(tm_ctx* ctx, void* g, int K, int K_pad, int64_t nb, CUtensorMap
 // Stage A: for every frequency slot j, G_j [K_pad x 2 nb] = T^_j [K_pad x 2 R] x P^_j [2 R x 2 nb]
 // (column-major, BF16 in and out, FP32 accumulation): one strided batched GEMM on the tensor
 // cores through cuBLAS (a plain library GEMM).
-int stage_a(tm_ctx* ctx, cudaStream_t st, const Library* L, const TensorBuffers& tb, int64_t nb) {
+int cublas_on(tm_ctx* ctx, cudaStream_t st, const TensorBuffers& tb) {
     cublasStatus_t s = CUBLAS_STATUS_SUCCESS;
     if (!ctx->cublas) {
         if (ctx->capturing) return fail(TM_ERR_CUDA, "cuBLAS handle created during graph capture");
@@ -790,6 +805,30 @@ int stage_a(tm_ctx* ctx, cudaStream_t st, const Library* L, const TensorBuffers&
     s = cublasSetStream(ctx->cublas, st);
     if (s == CUBLAS_STATUS_SUCCESS) s = cublasSetWorkspace(ctx->cublas, tb.cublas_ws, tb.cublas_ws_bytes);
     if (s != CUBLAS_STATUS_SUCCESS) return fail(TM_ERR_CUDA, "cuBLAS set-up failed (%d)", (int)s);
+    return TM_OK;
+}
+
+// Angular DFT of a batch of polar images: dftc [2 x 192][nb n_r] = polar^T-rows x DFT matrix, i.e.
+// for every pattern and polar row the (Re, Im) of P^ at each frequency slot, in TF32 with FP32
+// accumulation (cuBLAS, a plain library GEMM).  Rows the polar stage did not store give values
+// no later stage reads.
+int dft_gemm(tm_ctx* ctx, cudaStream_t st, const SpectralTables& spec, const float* polar, int64_t nb, int n_r,
+             int n_theta, const TensorBuffers& tb) {
+    int rc = cublas_on(ctx, st, tb);
+    if (rc) return rc;
+    const float one = 1.0f, zero = 0.0f;
+    const cublasStatus_t s = cublasGemmEx(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, (int)(nb * n_r),
+                                          2 * tmgb::dense_slots(), n_theta, &one, polar, CUDA_R_32F, n_theta,
+                                          spec.dftmat, CUDA_R_32F, n_theta, &zero, tb.dftc, CUDA_R_32F,
+                                          (int)(nb * n_r), CUBLAS_COMPUTE_32F_FAST_TF32, CUBLAS_GEMM_DEFAULT);
+    if (s != CUBLAS_STATUS_SUCCESS) return fail(TM_ERR_CUDA, "angular DFT GEMM failed (cuBLAS status %d)", (int)s);
+    return TM_OK;
+}
+
+int stage_a(tm_ctx* ctx, cudaStream_t st, const Library* L, const TensorBuffers& tb, int64_t nb) {
+    int rc = cublas_on(ctx, st, tb);
+    if (rc) return rc;
+    cublasStatus_t s = CUBLAS_STATUS_SUCCESS;
     const float one = 1.0f, zero = 0.0f;
     const int R2 = 2 * L->R;
     s = cublasGemmStridedBatchedEx(ctx->cublas, CUBLAS_OP_N, CUBLAS_OP_N, L->K_pad, (int)(2 * nb), R2, &one,
@@ -801,45 +840,55 @@ int stage_a(tm_ctx* ctx, cudaStream_t st, const Library* L, const TensorBuffers&
     return TM_OK;
 }
 
-// Pre-scores of library L for the call's rows [0, m): angular DFT of the polar rows (P^), stage A
-// (G), stage B (inverse DFT and maximum over shifts on tcgen05), in batches of tb.nb patterns.
-// mask (nullable): templates to score per row; out [m][K] (-NaN where not scored).
-int prescore_rows(tm_ctx* ctx, cudaStream_t st, const Library* L, const SpectralTables& spec, const TensorBuffers& tb,
-                  const float* polar, const float* pnorm, int64_t m, const uint32_t* mask, float* out, int stall,
-                  int64_t* launches) {
-    const int n_rad = (int)std::max<size_t>(1, L->radii.size());
+// Pre-scores of libraries libs[0..n_libs) for the call's rows [0, m): per batch of tb.nb patterns
+// the angular DFT of the polar rows (once), then per library its P^ (packed), stage A (G) and
+// stage B (inverse DFT and maximum over shifts on tcgen05).  masks[i] (nullable): templates to
+// score per row; outs[i] [m][K_i] (-NaN where not scored).
+int prescore_rows(tm_ctx* ctx, cudaStream_t st, Library* const* libs, int n_libs, const SpectralTables& spec,
+                  const TensorBuffers& tb, const float* polar, const float* pnorm, int64_t m,
+                  uint32_t* const* masks, float* const* outs, int stall, int64_t* launches) {
+    const int n_r = libs[0]->n_r, n_theta = libs[0]->n_theta;
     for (int64_t b0 = 0; b0 < m; b0 += tb.nb) {
         const int64_t nb = std::min(tb.nb, m - b0);
         {
             StageTimer tmr(ctx, TM_STAGE_DFT, st);
-            TM_CUDA(tmgb::launch_dft(polar + (size_t)b0 * L->n_r * L->n_theta, pnorm + b0, nb, L->n_r, L->n_theta,
-                                     L->d_radii, n_rad, L->R, spec.twiddle, tb.phat, ctx->num_sms, st),
-                    "tensor path: dft");
-        }
-        {
-            StageTimer tmr(ctx, TM_STAGE_GEMM, st);
-            const int rc = stage_a(ctx, st, L, tb, nb);
+            const int rc = dft_gemm(ctx, st, spec, polar + (size_t)b0 * n_r * n_theta, nb, n_r, n_theta, tb);
             if (rc) return rc;
         }
-        CUtensorMap map;
-        const int rc = g_tensor_map(ctx, tb.g, (int)L->K, L->K_pad, nb, &map);
-        if (rc) return rc;
-        tmgb::DenseCall dc{};
-        dc.n = nb;
-        dc.p0 = b0;
-        dc.n_theta = L->n_theta;
-        dc.K = (int)L->K;
-        dc.basis = spec.basis;
-        dc.mask = mask;
-        dc.words = (int)((L->K + 31) / 32);
-        dc.pre = out;
-        dc.error = ctx->d_error;
-        dc.stall = stall;
-        {
-            StageTimer tmr(ctx, TM_STAGE_DENSE, st);
-            TM_CUDA(tmgb::launch_dense(&map, dc, ctx->num_sms, st), "tensor path: stage B");
+        for (int i = 0; i < n_libs; ++i) {
+            const Library* L = libs[i];
+            const int n_rad = (int)std::max<size_t>(1, L->radii.size());
+            {
+                StageTimer tmr(ctx, TM_STAGE_DFT, st);
+                TM_CUDA(tmgb::launch_pack(tb.dftc, pnorm + b0, nb, n_r, L->d_radii, n_rad, L->R, tb.phat, ctx->num_sms,
+                                          st),
+                        "tensor path: pack");
+            }
+            {
+                StageTimer tmr(ctx, TM_STAGE_GEMM, st);
+                const int rc = stage_a(ctx, st, L, tb, nb);
+                if (rc) return rc;
+            }
+            CUtensorMap map;
+            const int rc = g_tensor_map(ctx, tb.g, (int)L->K, L->K_pad, nb, &map);
+            if (rc) return rc;
+            tmgb::DenseCall dc{};
+            dc.n = nb;
+            dc.p0 = b0;
+            dc.n_theta = n_theta;
+            dc.K = (int)L->K;
+            dc.basis = spec.basis;
+            dc.mask = masks ? masks[i] : nullptr;
+            dc.words = (int)((L->K + 31) / 32);
+            dc.pre = outs[i];
+            dc.error = ctx->d_error;
+            dc.stall = stall;
+            {
+                StageTimer tmr(ctx, TM_STAGE_DENSE, st);
+                TM_CUDA(tmgb::launch_dense(&map, dc, ctx->num_sms, st), "tensor path: stage B");
+            }
+            *launches += 2;              // this library's kernels (the GEMMs are cuBLAS's)
         }
-        *launches += 2;                  // this library's kernels (the GEMM is cuBLAS's)
     }
     return TM_OK;
 }
@@ -1286,6 +1335,7 @@ void tm_destroy(tm_ctx* ctx) {
         for (auto& kv : ctx->spectral) {
             cudaFree(kv.second.basis);
             cudaFree(kv.second.twiddle);
+            cudaFree(kv.second.dftmat);
         }
         for (auto& kv : ctx->radius_maps) {
             cudaFree(kv.second.radii);
@@ -1646,13 +1696,11 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             c.threads = sparse_threads;
             c.work = ctx->profiling ? ctx->d_work : nullptr;
             if (bf16) {
-                for (int i = 0; i < n_libs; ++i) {
-                    int64_t nl = 0;
-                    const int rc2 = prescore_rows(ctx, st, libs[i], spec, tb, polar, pnorm, m, pre ? mask[i] : nullptr,
-                                                  score[i], (params->reserved & TM_INDEX_TEST_STALL) ? 1 : 0, &nl);
-                    if (rc2) return rc2;
-                    launches += nl;
-                }
+                int64_t nl = 0;
+                const int rc2 = prescore_rows(ctx, st, libs, n_libs, spec, tb, polar, pnorm, m, pre ? mask : nullptr,
+                                              score, (params->reserved & TM_INDEX_TEST_STALL) ? 1 : 0, &nl);
+                if (rc2) return rc2;
+                launches += nl;
                 {
                     StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
                     for (int i = 0; i < n_libs; ++i) {
@@ -1868,7 +1916,10 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
                 "tm_prescore: pre-filter");
     }
     int64_t nl = 0;
-    return prescore_rows(ctx, st, L, spec, tb, polar_dev, norm_dev, n, mask, score_dev, 0, &nl);
+    uint32_t* masks[1] = {mask};
+    float* outs[1] = {score_dev};
+    return prescore_rows(ctx, st, libs, 1, spec, tb, polar_dev, norm_dev, n, fraction < 1.0 ? masks : nullptr, outs, 0,
+                         &nl);
 }
 
 }  // extern "C"

@@ -184,6 +184,7 @@ cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);
 // m = 2 (j - 96) + 1 (even frequencies first, for the radix-2 split of stage B); slots whose
 // frequency exceeds n_theta / 2 are zero.
 //   T^ (per library, built once):  [192][2 R][K_pad] BF16, rows (Re, Im) of T^_k[r_a, m] / |T_k|
+//   DFT of the polar rows:          [192][2][n][n_r]  FP32, (Re, Im) of P^[r, m] (a TF32 GEMM)
 //   P^ (per call, per library):    [192][n][2][2 R]  BF16, (Re, Im) and (Im, -Re) of P^[r_a, m] / |P|
 //   G  (stage A: G_j = T^_j P^_j): [192][n][2][K_pad] BF16, (Re, Im) of G[k, m]
 // with R the library's distinct radii rounded up to 8 and K_pad its templates rounded up to 64.
@@ -207,10 +208,10 @@ int dense_slots();
 size_t dense_smem_bytes();
 // tmap: the CUtensorMap of G for this batch (4-D: k, c, p, j; box 64 x 2 x 1 x 32; 128-byte swizzle).
 cudaError_t launch_dense(const void* tmap, const DenseCall& c, int num_sms, cudaStream_t st);
-size_t dft_smem_bytes(int n_rad, int n_theta);
-cudaError_t launch_dft(const float* polar, const float* pnorm, int64_t n, int n_r, int n_theta,
-                       const int32_t* radii, int n_rad, int R, const float2* twiddle, void* out,
-                       int num_sms, cudaStream_t st);
+// dftc [192][2][nb][n_r] FP32 (the DFT GEMM's output for every polar row) -> P^ of one library
+// [192][nb][2][2 R] BF16, divided by |P|.
+cudaError_t launch_pack(const float* dftc, const float* pnorm, int64_t nb, int n_r, const int32_t* radii, int n_rad,
+                        int R, void* out, int num_sms, cudaStream_t st);
 cudaError_t launch_spectra(const int32_t* off, const int32_t* rt, const int2* spot, const float* norm,
                            const int32_t* rowmap, int K, int K_pad, int R, int n_theta, const float2* twiddle,
                            void* out, cudaStream_t st);

@@ -9,8 +9,9 @@ time), with a sample large enough that a top-1 agreement of 99.0 % or less fails
   checked against the oracle.
 - Batched three-phase scan: 65536 frames (8192 distinct) drawn from FCC, HCP and tetragonal
   libraries of 20-250 spots per template, each indexed against all three libraries in one call
-  (top-5 per phase), with the sparse kernel's block size autotuned and the call replayed as a
-  CUDA graph; 384 patterns (1152 per-library top-1 rows) checked against the oracle.
+  (top-5 per phase): the FP32 path with the sparse kernel's block size autotuned and the call
+  replayed as a CUDA graph, and the tensor-core path with the exact rescore of the top 64;
+  384 patterns (1152 per-library top-1 rows) checked against the oracle for each.
 
 Sampled positions span the whole scan (position p holds distinct frame p mod the distinct count).
 """
@@ -89,7 +90,7 @@ def test_large_map_full_size_both_paths(ctx):
     dev = _dev_tiled(scan.frames, total)
     lid = ctx.load_library(ts, N_R, N_THETA)
     h32 = tmgb.hits_to_numpy(ctx.index(dev, lid, top_n=5))[0]
-    h16 = tmgb.hits_to_numpy(ctx.index(dev, lid, top_n=5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=256))[0]
+    h16 = tmgb.hits_to_numpy(ctx.index(dev, lid, top_n=5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=64))[0]
     ctx.check()
     del dev
     torch.cuda.empty_cache()
@@ -132,20 +133,28 @@ def test_batched_multiphase_full_size_graph_autotuned(ctx):
     ctx.check(st)
     assert np.array_equal(h32[0], h32[1]) and np.array_equal(h32[0], h32[2])
     h32 = h32[0]
+    # the tensor-core path with the configured rescore of the top 64, one call for the three libraries
+    h16 = tmgb.hits_to_numpy(ctx.index(dev, lids, top_n=5, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=64))
+    ctx.check()
     del dev
     torch.cuda.empty_cache()
     assert np.array_equal(h32[:, :uniq], h32[:, total - uniq:])
+    assert np.array_equal(h16[:, :uniq], h16[:, total - uniq:])
     pick = np.sort(np.random.default_rng(5).choice(uniq, 384, replace=False))
     pos = pick + uniq * np.random.default_rng(8).integers(0, total // uniq, size=pick.shape[0])
-    oks = []
+    oks32, oks16 = [], []
     for li, ts in enumerate(libs):
         lib = O.prepare_library(ts, N_R, N_THETA)
         ref = O.index(frames[pick], lib, N=5)
-        compare_hits(h32[li][pos[:48]], {k: v[:48] for k, v in ref.items() if hasattr(v, "shape")}, lib)
-        ok = _top1_vs_oracle(h32[li][pos], ref)
+        head = {k: v[:48] for k, v in ref.items() if hasattr(v, "shape")}
+        compare_hits(h32[li][pos[:48]], head, lib)
+        _rescored_rows_exact(h16[li][pos[:48]], head)
         own = phase[pick] == li
-        assert ok[own].mean() >= 0.995, (li, ok[own].mean())
-        oks.append(ok)
-    _assert_bar(np.concatenate(oks), "FP32 sparse path, three-phase scan (all per-library rows)")
+        for h, oks in ((h32, oks32), (h16, oks16)):
+            ok = _top1_vs_oracle(h[li][pos], ref)
+            assert ok[own].mean() >= 0.995, (li, ok[own].mean())
+            oks.append(ok)
+    _assert_bar(np.concatenate(oks32), "FP32 sparse path, three-phase scan (all per-library rows)")
+    _assert_bar(np.concatenate(oks16), "BF16 pre-score + FP32 rescore of 64, three-phase scan (all per-library rows)")
     for lid in lids:
         ctx.unload_library(lid)
