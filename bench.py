@@ -354,62 +354,91 @@ def two_stage_bench(ctx, stream, steps: int, n_total: int = 16384, unique: int =
 
 # ------------------------------------------------------------------ serving loop (scan lines and maps)
 
-def serve_bench(ctx, lib_ids, pool: np.ndarray, path_kw: dict, seconds: float = 2.5, seed: int = 2111_07347 + 103):
-    """Poisson arrivals against device-resident libraries: 80 % scan lines of 64-512
-    patterns (frame rate 1-10 kHz: a line arrives when its last frame is acquired), 20 %
-    maps of 64^2 or 128^2 patterns (the frame pool holds 16384 frames, so the 256^2 and
-    512^2 maps of the workload are left out).  Capacity is measured first with a saturating
-    burst; offered load is then 25 / 50 / 80 % of it.  Latency = completion - arrival."""
+def serve_bench(ctx, lib_ids, line_pool: np.ndarray, map_pool, path_kw: dict, seconds: float = 30.0,
+                line_rate: float = 40.0, seed: int = 2111_07347 + 103):
+    """The serving workload: FCC + HCP libraries resident; two Poisson streams.  Scan lines
+    (64-512 patterns from a pinned host pool, as a detector delivers them) arrive at
+    `line_rate` per second; whole maps (side uniform in {64, 128, 256, 512}, frames already on the
+    device) arrive at the rate that brings the offered load to 25 / 50 / 80 % of the capacity,
+    which is measured first with a saturating burst of maps.  Each level runs `seconds`.  Latency
+    = result ready - arrival (a late submission counts from its intended arrival); the admission
+    wait and the device time of copies and kernels come from the server's per-request timeline."""
     from paper_2111_07347_gb300 import tmgb
     rng = np.random.default_rng(seed)
-    n_pool = pool.shape[0]
-    srv = tmgb.Server(ctx, slots=4, tile_patterns=512, max_libs=len(lib_ids), max_top_n=TOP_N, priority_slots=1)
+    srv = tmgb.Server(ctx, slots=4, tile_patterns=512, max_libs=len(lib_ids), max_top_n=TOP_N, priority_slots=1,
+                      hbm_budget_bytes=1 << 30)
+    n_line, n_map = line_pool.shape[0], map_pool.shape[0]
+    sides = [64, 128, 256, 512]
 
-    def submit(n, prio):
-        a = int(rng.integers(0, n_pool - n + 1))
-        return srv.submit(pool[a:a + n], lib_ids, top_n=TOP_N, priority=prio, **path_kw)
+    def submit_line(n):
+        a = int(rng.integers(0, n_line - n + 1))
+        return srv.submit(line_pool[a:a + n], lib_ids, top_n=TOP_N, priority=1, **path_kw)
 
-    # capacity: a saturating burst of six requests of 16384 patterns
+    def submit_map(side):
+        n = side * side
+        a = int(rng.integers(0, n_map - n + 1))
+        return srv.submit(map_pool[a:a + n], lib_ids, top_n=TOP_N, priority=0, **path_kw)
+
+    # capacity: a saturating burst of maps
     t0 = time.perf_counter()
-    ts = [submit(16384, 0) for _ in range(6)]
-    for t in ts:
+    burst = [submit_map(256) for _ in range(8)]
+    for t in burst:
         srv.wait(t, timeout_ms=600000)
-    cap = 6 * 16384 / (time.perf_counter() - t0)
-    mean_line, mean_map = (64 + 512) / 2, (64 * 64 + 128 * 128) / 2
-    mean_req = 0.8 * mean_line + 0.2 * mean_map
+    cap = 8 * 65536 / (time.perf_counter() - t0)
+    mean_line = (64 + 512) / 2
+    mean_map = float(np.mean([s_ * s_ for s_ in sides]))
     out = {"capacity_patterns_per_s": cap, "slots": 4, "priority_slots": 1, "tile_patterns": 512,
-           "maps": "64^2 and 128^2 only (frame pool of 16384)"}
+           "line_rate_per_s": line_rate, "seconds_per_level": seconds,
+           "maps": "sides 64, 128, 256, 512 (device-resident frames)", "lines": "64-512 patterns, pinned host frames"}
     for load in (0.25, 0.5, 0.8):
-        lam = load * cap / mean_req
-        t_next = time.perf_counter()
-        end = t_next + seconds
+        map_rate = max(0.0, (load * cap - line_rate * mean_line) / mean_map)
+        arrivals = []
+        t = 0.0
+        while True:
+            t += rng.exponential(1.0 / line_rate)
+            if t >= seconds:
+                break
+            arrivals.append((t, "line", int(rng.integers(64, 513))))
+        t = 0.0
+        while map_rate > 0:
+            t += rng.exponential(1.0 / map_rate)
+            if t >= seconds:
+                break
+            arrivals.append((t, "map", int(rng.choice(sides))))
+        arrivals.sort()
+        start = time.perf_counter()
         tickets = []
-        while t_next < end:
-            now = time.perf_counter()
-            if now < t_next:
-                time.sleep(min(t_next - now, 0.002))
-                continue
-            if rng.random() < 0.8:
-                n = int(rng.integers(64, 513))
-                tickets.append(("line", n, submit(n, 1)))
-            else:
-                side = int(rng.choice([64, 128]))
-                tickets.append(("map", side * side, submit(side * side, 0)))
-            t_next += rng.exponential(1.0 / lam)
+        for at, kind, size in arrivals:
+            now = time.perf_counter() - start
+            if now < at:
+                time.sleep(at - now)
+            lag_ms = max(0.0, (time.perf_counter() - start - at) * 1e3)
+            tk = submit_line(size) if kind == "line" else submit_map(size)
+            tickets.append((kind, size if kind == "line" else size * size, tk, lag_ms))
         lat = {"line": [], "map": []}
-        pats = 0
-        first, last = None, None
-        for kind, n, t in tickets:
-            res, st = srv.wait(t, timeout_ms=600000)
-            lat[kind].append(st["done_ms"] - st["submit_ms"])
+        tl = {"admit": [], "queue": [], "h2d": [], "kernels": [], "d2h": []}
+        pats, first, last = 0, None, None
+        for kind, n, tk, lag in tickets:
+            res, st = srv.wait(tk, timeout_ms=600000)
+            lat[kind].append(lag + st["done_ms"] - st["submit_ms"])
+            if kind == "line":
+                tl["admit"].append(lag + st["admit_ms"] - st["submit_ms"])
+                tl["queue"].append(st["first_dispatch_ms"] - st["admit_ms"])
+                tl["h2d"].append(st["h2d_ms"])
+                tl["kernels"].append(st["kernels_ms"])
+                tl["d2h"].append(st["d2h_ms"])
             pats += n
             first = st["submit_ms"] if first is None else min(first, st["submit_ms"])
             last = st["done_ms"] if last is None else max(last, st["done_ms"])
-        rec = {"requests": len(tickets), "throughput_patterns_per_s": pats / max(1e-9, (last - first) / 1e3)}
+        rec = {"offered_load": load, "lines": len(lat["line"]), "maps": len(lat["map"]),
+               "throughput_patterns_per_s": pats / max(1e-9, (last - first) / 1e3)}
         for kind in ("line", "map"):
             if lat[kind]:
                 rec[f"{kind}_p50_ms"] = float(np.percentile(lat[kind], 50))
                 rec[f"{kind}_p99_ms"] = float(np.percentile(lat[kind], 99))
+        if lat["line"]:
+            rec["line_p999_ms"] = float(np.percentile(lat["line"], 99.9))
+            rec["line_timeline_mean_ms"] = {k: float(np.mean(v)) for k, v in tl.items()}
         out[f"load_{int(load * 100)}"] = rec
     srv.close()
     return out
@@ -829,19 +858,23 @@ def run_ours(args):
     pool = line.pop("pool_frames", None)
     if not args.no_serving:
         if pool is None:
-            _, scan, _ = synth.single_phase_workload(n_patterns=16384)
+            _, scan, _ = synth.large_map_workload(n_unique=16384)
             pool = scan.frames
         fcc = synth.kinematic_library("fcc")
         hcp = synth.kinematic_library("hcp")
         lf, lh = ctx.load_library(fcc, N_R, N_THETA), ctx.load_library(hcp, N_R, N_THETA)
         host, host_np = pinned_u16(pool)
-        serving = serve_bench(ctx, [lf, lh], host_np, {"path": tmgb.TM_PATH_FP32_SPARSE})
+        map_pool = to_device_u16(pool, dev).repeat(LARGE_MAP["total"] // pool.shape[0], 1, 1)
+        serving = serve_bench(ctx, [lf, lh], host_np, map_pool, {"path": tmgb.TM_PATH_FP32_SPARSE},
+                              seconds=args.serving_seconds)
         line["serving"] = serving
         line["p99_line_ms"] = serving["load_50"].get("line_p99_ms")
-        line["serving_workload"] = "FCC + HCP resident, Poisson arrivals, 80 % lines 64-512 / 20 % maps"
+        line["serving_workload"] = ("FCC + HCP resident; Poisson scan lines (64-512 patterns, 40/s, host frames) and "
+                                    "Poisson maps (64^2-512^2, device frames) at 25/50/80 % of capacity")
         ctx.unload_library(lf)
         ctx.unload_library(lh)
-        del host, host_np
+        del host, host_np, map_pool
+        torch.cuda.empty_cache()
     if not args.no_two_stage:
         line["two_stage"] = two_stage_bench(ctx, stream, max(2, args.steps // 2))
     if not args.no_preprocess:

@@ -427,8 +427,12 @@ void tm_index_params_default(tm_index_params* p);
  * with device staging for one tile.  Requests (a scan line or a whole map) are split into
  * tiles of `tile_patterns`; tiles of different requests interleave on the device as
  * slots free up, higher-priority requests (scan lines) first, then submission order.
- * The libraries stay resident in the context.  Results of a pattern do not depend on
- * the other patterns of its tile, so a request's result is the same alone and in a mix.
+ * The libraries stay resident in the context, and every admitted request keeps its hits
+ * ([n_libs][n][top_n] tm_hit, the partial top-N state as its tiles complete) in a device
+ * arena of hbm_budget_bytes: a request is admitted when that arena has room for it (and
+ * its frame bytes fit queue_bytes).  Tiles of maps leave reserve_sms SMs free, so a scan
+ * line's kernels start without waiting for a map's.  Results of a pattern do not depend
+ * on the other patterns of its tile, so a request's result is the same alone and in a mix.
  */
 typedef struct tm_server tm_server;
 
@@ -445,11 +449,17 @@ typedef struct tm_server_params {
                                      > 0 (scan lines), so that they never wait behind map
                                      tiles; such tiles also run on high-priority streams;
                                      default 1 (0 when slots == 1)                         */
+    size_t hbm_budget_bytes;      /* device arena for the admitted requests' hits; 0: 256 MiB.
+                                     A request needing more than the whole arena is refused
+                                     (TM_ERR_INVALID_ARG)                                  */
+    int32_t reserve_sms;          /* SMs the persistent kernels of map tiles leave free
+                                     (< 0: a quarter of the SMs when priority_slots > 0,
+                                     else none; default -1)                                */
 } tm_server_params;
 
 typedef struct tm_request {
     const void* frames_host;      /* [n][H][W] host memory (pinned for overlap), read until
-                                     the request finishes                                  */
+                                     the request finishes; NULL when frames_dev is given   */
     int32_t dtype;                /* TM_DTYPE_U16 or TM_DTYPE_F32                          */
     int32_t H, W;
     int64_t n;                    /* patterns, >= 1                                        */
@@ -459,12 +469,18 @@ typedef struct tm_request {
     tm_index_params params;
     tm_hit* out_host;             /* [n_libs][n][top_n] host memory, complete when the
                                      request finishes                                      */
+    const void* frames_dev;       /* [n][H][W] device memory of the context's device instead
+                                     of frames_host (a map already resident on the GPU), or
+                                     NULL; read until the request finishes                 */
 } tm_request;
 
 typedef struct tm_request_status {
     int32_t status;               /* TM_OK, TM_ERR_CANCELLED, or the error of a tile       */
     int32_t tiles;
     double submit_ms, first_dispatch_ms, done_ms;   /* server clock, ms since creation    */
+    double admit_ms;              /* when its hits were given room in the device arena    */
+    double h2d_ms, kernels_ms, d2h_ms;  /* device time of its tiles' frame copies, kernels
+                                     and hit copies, summed over its tiles (CUDA events)   */
 } tm_request_status;
 
 void tm_server_params_default(tm_server_params* p);

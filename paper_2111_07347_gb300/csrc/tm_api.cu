@@ -151,6 +151,12 @@ cudaError_t kernel_occupancy(const void* fn, int threads, size_t smem, int* per_
     return cudaSuccess;
 }
 
+namespace {
+thread_local int t_sm_cap = 0;      // persistent grids of this thread's calls use at most this many SMs
+}
+
+void set_sm_cap(int cap) { t_sm_cap = cap > 0 ? cap : 0; }
+
 int device_sms() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -161,7 +167,7 @@ int device_sms() {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
         it = g_sms.emplace(dev, sms).first;
     }
-    return it->second;
+    return t_sm_cap ? std::min(t_sm_cap, it->second) : it->second;
 }
 }  // namespace tmgb
 
@@ -860,8 +866,8 @@ int prescore_rows(tm_ctx* ctx, cudaStream_t st, Library* const* libs, int n_libs
             const int n_rad = (int)std::max<size_t>(1, L->radii.size());
             {
                 StageTimer tmr(ctx, TM_STAGE_DFT, st);
-                TM_CUDA(tmgb::launch_pack(tb.dftc, pnorm + b0, nb, n_r, L->d_radii, n_rad, L->R, tb.phat, ctx->num_sms,
-                                          st),
+                TM_CUDA(tmgb::launch_pack(tb.dftc, pnorm + b0, nb, n_r, L->d_radii, n_rad, L->R, tb.phat,
+                                          tmgb::device_sms(), st),
                         "tensor path: pack");
             }
             {
@@ -885,7 +891,7 @@ int prescore_rows(tm_ctx* ctx, cudaStream_t st, Library* const* libs, int n_libs
             dc.stall = stall;
             {
                 StageTimer tmr(ctx, TM_STAGE_DENSE, st);
-                TM_CUDA(tmgb::launch_dense(&map, dc, ctx->num_sms, st), "tensor path: stage B");
+                TM_CUDA(tmgb::launch_dense(&map, dc, tmgb::device_sms(), st), "tensor path: stage B");
             }
             *launches += 2;              // this library's kernels (the GEMMs are cuBLAS's)
         }
@@ -1548,6 +1554,15 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
 int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype, int64_t n,
                       int32_t H, int32_t W, const float* centres_dev, const int32_t* lib_ids, int32_t n_libs,
                       tm_hit* out_dev, tm_stats* stats, void* stream) {
+    return tmgb::index_patterns_ex(ctx, params, frames_dev, dtype, n, H, W, centres_dev, lib_ids, n_libs, out_dev, 0,
+                                   stats, stream);
+}
+
+}  // extern "C"
+
+int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype,
+                            int64_t n, int32_t H, int32_t W, const float* centres_dev, const int32_t* lib_ids,
+                            int32_t n_libs, tm_hit* out_dev, int64_t lib_stride, tm_stats* stats, void* stream) {
     if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: ctx is NULL");
     int rc = check_params(params);
     if (rc) return rc;
@@ -1574,6 +1589,9 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     if (n == 0) return TM_OK;
     if (!frames_dev || !out_dev) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: NULL buffer");
     const int n_r = libs[0]->n_r, n_theta = libs[0]->n_theta, N = params->top_n;
+    if (lib_stride == 0) lib_stride = n * N;
+    if (lib_stride < n * N) return fail(TM_ERR_INVALID_ARG, "tm_index_patterns: hits stride below n * top_n");
+    const int sms = tmgb::device_sms();
     const double dr = libs[0]->dr;
     int max_rad = 1;
     for (int i = 0; i < n_libs; ++i) max_rad = std::max<int>(max_rad, (int)libs[i]->radii.size());
@@ -1650,7 +1668,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
         auto tt = ctx->tuned.find(tune_key(libs, n_libs, N));
         if (tt != ctx->tuned.end()) sparse_threads = tt->second;
     }
-    if (!sparse_threads && std::min(chunk, n) <= 2 * (int64_t)ctx->num_sms) sparse_threads = 512;
+    if (!sparse_threads && std::min(chunk, n) <= 2 * (int64_t)sms) sparse_threads = 512;
     int64_t launches = 0, corr = 0, scored = 0;
     auto enqueue = [&]() -> int {
         for (int64_t c0 = 0; c0 < n; c0 += chunk) {
@@ -1691,7 +1709,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                 if (pre || bf16) c.mask[i] = mask[i];
             }
             c.hits = out_dev + (size_t)c0 * N;
-            c.hits_lib_stride = n * N;
+            c.hits_lib_stride = lib_stride;
             c.top_n = N;
             c.threads = sparse_threads;
             c.work = ctx->profiling ? ctx->d_work : nullptr;
@@ -1709,7 +1727,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                                 "tm_index_patterns: candidates");
                         ++launches;
                     }
-                    TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: rescore");
+                    TM_CUDA(tmgb::launch_sparse(c, sms, st), "tm_index_patterns: rescore");
                 }
                 ++launches;
                 for (int i = 0; i < n_libs; ++i) {
@@ -1719,7 +1737,7 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
             } else {
                 {
                     StageTimer tmr(ctx, TM_STAGE_SPARSE, st);
-                    TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_index_patterns: sparse");
+                    TM_CUDA(tmgb::launch_sparse(c, sms, st), "tm_index_patterns: sparse");
                 }
                 ++launches;
                 for (int i = 0; i < n_libs; ++i) {
@@ -1739,8 +1757,8 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                 for (int i = 0; i < n_libs; ++i)
                     rc.lib[i] = tmgb::RefineLib{libs[i]->d_off, libs[i]->d_rt, libs[i]->d_spot, libs[i]->d_norm};
                 rc.hits = out_dev + (size_t)c0 * N;
-                rc.hits_lib_stride = n * N;
-                TM_CUDA(tmgb::launch_refine(rc, ctx->num_sms, st), "tm_index_patterns: refine");
+                rc.hits_lib_stride = lib_stride;
+                TM_CUDA(tmgb::launch_refine(rc, sms, st), "tm_index_patterns: refine");
                 ++launches;
             }
         }
@@ -1762,7 +1780,8 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
                            dtype, (long long)n, H, W, params->gamma, params->subtract, params->cx, params->cy,
                            params->prefilter_fraction, params->threshold, params->top_n, params->path,
                            params->rescore_k);
-        off += snprintf(key + off, sizeof key - off, "r%d|t%d|", params->reserved & ~TM_INDEX_GRAPH, sparse_threads);
+        off += snprintf(key + off, sizeof key - off, "r%d|t%d|s%lld|m%d|", params->reserved & ~TM_INDEX_GRAPH,
+                        sparse_threads, (long long)lib_stride, sms);
         for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);
         tm_ctx::GraphEntry& ge = ctx->graphs[key];
         if (ge.exec && ge.ws_gen == ctx->ws_gen) {
@@ -1809,6 +1828,8 @@ int tm_index_patterns(tm_ctx* ctx, const tm_index_params* params, const void* fr
     report();
     return TM_OK;
 }
+
+extern "C" {
 
 int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype, int64_t n,
                 int32_t H, int32_t W, const int32_t* lib_ids, int32_t n_libs, int32_t* best_threads, void* stream) {

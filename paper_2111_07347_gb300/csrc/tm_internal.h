@@ -69,8 +69,11 @@ struct RadialLib {
 // returns its resident blocks per SM for `threads` threads (per_sm may be null).  Cached, so
 // repeated launches make no driver queries.
 cudaError_t kernel_occupancy(const void* fn, int threads, size_t smem, int* per_sm);
-// Number of SMs of the current device (cached).
+// Number of SMs of the current device (cached), or the calling thread's cap when one is set.
 int device_sms();
+// Caps the persistent grids of this thread's later calls at `cap` SMs (0 = no cap), so that work
+// on other streams finds SMs free (the serving loop leaves SMs to scan lines this way).
+void set_sm_cap(int cap);
 
 // ------------------------------------------------------------------ launchers
 // Host: the ray steps of the polar grid, (round(dr cos theta_k 2^32), round(dr sin theta_k
@@ -215,6 +218,11 @@ cudaError_t launch_pack(const float* dftc, const float* pnorm, int64_t nb, int n
 cudaError_t launch_spectra(const int32_t* off, const int32_t* rt, const int2* spot, const float* norm,
                            const int32_t* rowmap, int K, int K_pad, int R, int n_theta, const float2* twiddle,
                            void* out, cudaStream_t st);
+
+// tm_index_patterns with the hits of library i written at out_dev + i * lib_stride (0: n * top_n).
+int index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype, int64_t n,
+                      int32_t H, int32_t W, const float* centres_dev, const int32_t* lib_ids, int32_t n_libs,
+                      tm_hit* out_dev, int64_t lib_stride, tm_stats* stats, void* stream);
 
 // Validation of tm_index_params shared by every whole-path entry point (finite gamma,
 // subtraction and centre; pre-filter fraction; top_n; 16-byte aligned pixel mask; threshold).

@@ -73,19 +73,21 @@ class tm_server_params(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("tile_patterns", ctypes.c_int32), ("max_H", ctypes.c_int32),
                 ("max_W", ctypes.c_int32), ("max_libs", ctypes.c_int32), ("max_top_n", ctypes.c_int32),
                 ("queue_bytes", ctypes.c_size_t), ("blocking_submit", ctypes.c_int32),
-                ("priority_slots", ctypes.c_int32)]
+                ("priority_slots", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("reserve_sms", ctypes.c_int32)]
 
 
 class tm_request(ctypes.Structure):
     _fields_ = [("frames_host", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("H", ctypes.c_int32),
                 ("W", ctypes.c_int32), ("n", ctypes.c_int64), ("lib_ids", ctypes.c_void_p),
                 ("n_libs", ctypes.c_int32), ("priority", ctypes.c_int32), ("params", tm_index_params),
-                ("out_host", ctypes.c_void_p)]
+                ("out_host", ctypes.c_void_p), ("frames_dev", ctypes.c_void_p)]
 
 
 class tm_request_status(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("tiles", ctypes.c_int32), ("submit_ms", ctypes.c_double),
-                ("first_dispatch_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+                ("first_dispatch_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("h2d_ms", ctypes.c_double), ("kernels_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double)]
 
 
 TM_STAGE_COUNT = 8
@@ -404,18 +406,20 @@ class Server:
     """Serving loop over a Context: host frames in, host hits out (see tm_server_* in tmgb.h)."""
 
     def __init__(self, ctx: "Context", slots=3, tile_patterns=512, max_H=256, max_W=256, max_libs=2, max_top_n=5,
-                 queue_bytes=0, blocking_submit=True, priority_slots=None):
+                 queue_bytes=0, blocking_submit=True, priority_slots=None, hbm_budget_bytes=0, reserve_sms=-1):
         p = tm_server_params_default()
         p.slots, p.tile_patterns, p.max_H, p.max_W = slots, tile_patterns, max_H, max_W
         p.max_libs, p.max_top_n, p.queue_bytes, p.blocking_submit = max_libs, max_top_n, queue_bytes, int(blocking_submit)
         p.priority_slots = (1 if slots > 1 else 0) if priority_slots is None else priority_slots
+        p.hbm_budget_bytes, p.reserve_sms = hbm_budget_bytes, reserve_sms
         self.ctx = ctx
         self.handle = tm_server_create(ctx.handle, p)
         self._keep = {}
 
-    def submit(self, frames: np.ndarray, lib_ids, top_n=5, priority=0, out: np.ndarray | None = None, **kw) -> int:
-        """frames: C-contiguous uint16/float32 [n][H][W] host array (pinned memory gives overlap);
-        returns the ticket.  The result array is returned by wait()."""
+    def submit(self, frames, lib_ids, top_n=5, priority=0, out: np.ndarray | None = None, **kw) -> int:
+        """frames: C-contiguous uint16/float32 [n][H][W] host array (pinned memory gives overlap),
+        or a contiguous CUDA tensor on the context's device (frames already resident); returns
+        the ticket.  The result array is returned by wait()."""
         if isinstance(lib_ids, int):
             lib_ids = [lib_ids]
         n, H, W = frames.shape
@@ -423,8 +427,14 @@ class Server:
             out = np.empty((len(lib_ids), n, top_n), dtype=HIT_DTYPE)
         ids = np.ascontiguousarray(lib_ids, dtype=np.int32)
         r = tm_request()
-        r.frames_host = frames.ctypes.data
-        r.dtype = TM_DTYPE_U16 if frames.dtype == np.uint16 else TM_DTYPE_F32
+        if isinstance(frames, np.ndarray):
+            r.frames_host = frames.ctypes.data
+            r.dtype = TM_DTYPE_U16 if frames.dtype == np.uint16 else TM_DTYPE_F32
+        else:
+            if not frames.is_cuda or not frames.is_contiguous():
+                raise ValueError("device frames must be a contiguous CUDA tensor")
+            r.frames_dev = frames.data_ptr()
+            r.dtype = _dtype_code(frames)
         r.H, r.W, r.n = H, W, n
         r.lib_ids = ids.ctypes.data
         r.n_libs = len(lib_ids)

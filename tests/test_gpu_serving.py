@@ -145,3 +145,38 @@ def test_scan_lines_do_not_wait_for_map_tiles(env):
     assert st_line["done_ms"] < min(s["done_ms"] for s in st_maps)
     assert np.array_equal(out, _direct(ctx, line, [la, lb], top_n=5))
     srv.close()
+
+
+def test_hbm_budget_admission_and_device_frames(env):
+    """Admission by the device budget: every admitted request holds its hits in the server's
+    arena; a non-blocking submit that finds no room gets TM_ERR_BUSY, a request larger than the
+    whole arena is refused, and room returns once a request finishes.  A map whose frames are
+    already on the device (frames_dev) gives the same hits as a direct call, with no frame copy
+    in its timeline; a scan line from host memory records copy and kernel time."""
+    import torch
+    ctx, la, lb, frames = env
+    x = np.ascontiguousarray(frames[:200])
+    hits_bytes = 2 * 200 * 5 * 20                      # [n_libs][n][top_n] tm_hit
+    srv = tmgb.Server(ctx, slots=2, tile_patterns=64, max_libs=2, blocking_submit=False,
+                      hbm_budget_bytes=hits_bytes + 512, priority_slots=1)
+    srv.pause(True)
+    t1 = srv.submit(x, [la, lb], top_n=5, priority=1)
+    with pytest.raises(tmgb.TmError) as e:
+        srv.submit(x, [la, lb], top_n=5, priority=1)
+    assert e.value.code == tmgb.TM_ERR_BUSY
+    with pytest.raises(tmgb.TmError) as e:
+        srv.submit(np.ascontiguousarray(frames[:1000]), [la, lb], top_n=5)
+    assert e.value.code == tmgb.TM_ERR_INVALID_ARG
+    srv.pause(False)
+    out1, st1 = srv.wait(t1, timeout_ms=60000)
+    assert st1["status"] == tmgb.TM_OK
+    assert st1["h2d_ms"] > 0 and st1["kernels_ms"] > 0 and st1["d2h_ms"] > 0
+    assert st1["submit_ms"] <= st1["admit_ms"] <= st1["first_dispatch_ms"] <= st1["done_ms"]
+    assert np.array_equal(out1, _direct(ctx, x, [la, lb], top_n=5))
+    dev = torch.from_numpy(x.view(np.int16)).cuda().view(torch.uint16)
+    t2 = srv.submit(dev, [la, lb], top_n=5, priority=0)
+    out2, st2 = srv.wait(t2, timeout_ms=60000)
+    assert st2["status"] == tmgb.TM_OK and st2["kernels_ms"] > 0
+    assert st2["h2d_ms"] < 0.05
+    assert np.array_equal(out2, out1)
+    srv.close()
