@@ -654,6 +654,12 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
            "bf16": dict(top_n=TOP_N, prefilter=prefilter, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=rescore_k)}
     out = torch.empty((L, n, TOP_N, 5), dtype=torch.int32, device=dev)
     macs_step, pairs_step = sparse_work(ctx, lids, frames_d, prefilter)
+    # the sparse kernel's shape (block size x seeds per warp) chosen by the library's autotuner
+    # for these libraries, on the first frames of the scan (outside every timed region)
+    tune_n = 256 if name == "multiphase" else 2048
+    t0 = time.perf_counter()
+    tuned_threads = ctx.autotune(frames_d[:tune_n], lids, top_n=TOP_N, prefilter=prefilter)
+    tune_s = time.perf_counter() - t0
     res, hits = {}, {}
     for nm in want_paths:
         kw = kws[nm]
@@ -685,6 +691,7 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
     rec = {"patterns": n, "libraries": [ctx.library_info(l)["n_templates"] for l in lids],
            "spots_per_template": [round(ctx.library_info(l)["n_spots"] / ctx.library_info(l)["n_templates"], 2)
                                   for l in lids],
+           "autotune": {"frames": tune_n, "block_threads": tuned_threads, "seconds": tune_s},
            "prefilter": prefilter, "rescore_k": rescore_k, "macs_per_step_sparse": macs_step,
            "pairs_per_step": pairs_step, "paths": {}}
     match, recall, oracle_info = {}, {}, None

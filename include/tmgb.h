@@ -244,12 +244,14 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
 int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* norm_dev,
                 const float* radial_dev, int64_t n, double fraction, float* score_dev, void* stream);
 
-/* Autotune the FP32 sparse kernel for a set of libraries: time its block sizes (128,
- * 256, 512 threads; 256 is the default) on the first min(n, 2048) frames with these
+/* Autotune the FP32 sparse kernel for a set of libraries: time its shapes -- block size (128,
+ * 256, 512 threads; default 256) x templates seeded per warp for the pruned top-N (4, 8, 16;
+ * default 8: the templates of highest bound are scored first, so that the top-N threshold
+ * the others are pruned against starts high) -- on the first min(n, 2048) frames with these
  * parameters, keep the fastest for later calls on libraries of the same shapes (template
  * count, spot count, radii, n_theta) and top_n, and, when the environment variable
- * TMGB_TUNE_CACHE names a file, append "key threads ms" to it; contexts created later read
- * that file back.  Synchronous.  *best_threads (nullable) receives the choice. */
+ * TMGB_TUNE_CACHE names a file, append "key threads seeds ms" to it; contexts created later
+ * read that file back.  Synchronous.  *best_threads (nullable) receives the block size. */
 int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype,
                 int64_t n, int32_t H, int32_t W, const int32_t* lib_ids, int32_t n_libs,
                 int32_t* best_threads, void* stream);
@@ -292,8 +294,9 @@ enum {
     TM_STAGE_SPARSE = 2,      /* FP32 sparse correlation + top-N                        */
     TM_STAGE_DFT = 3,         /* angular DFT of the polar images (BF16 path)            */
     TM_STAGE_DENSE = 4,       /* BF16 tensor-core inverse DFT + max over shifts (stage B) */
-    TM_STAGE_RESCORE = 5,     /* candidate selection + FP32 rescore (BF16 path)         */
+    TM_STAGE_RESCORE = 5,     /* FP32 rescore of the candidates (BF16 path)             */
     TM_STAGE_GEMM = 6,        /* BF16 tensor-core contraction over radii (stage A)      */
+    TM_STAGE_SELECT = 7,      /* exact selection of the candidates (BF16 path)          */
     TM_STAGE_COUNT = 8
 };
 typedef struct tm_profile {

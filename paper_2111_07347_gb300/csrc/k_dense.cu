@@ -18,12 +18,14 @@
 //
 // Operands: A = G read by TMA as MN-major tiles (template index contiguous; 64 K-rows of 2 x 64
 // templates per ring slot, 128-byte swizzle); B = the inverse-DFT basis (w_m / n) cos / -sin,
-// K-major, resident in shared memory.  CTA (persistent over (pattern, tile) units, 256 threads):
+// K-major, resident in shared memory.  CTA (persistent over (pattern, tile) units, 384 threads):
 //   warp 0 lane 0  TMA producer into a 4-slot ring;
 //   warp 1 lane 0  MMA issuer (tcgen05.mma.cta_group::1.kind::f16, BF16 x BF16 -> FP32 in TMEM);
 //   warp 2         TMEM allocation;
-//   warps 4-7      epilogue: tcgen05.ld of E and O, max over shifts, one pre-score per
-//                  (pattern, template) written to global memory (masked-out templates: -NaN).
+//   warps 4-11     epilogue: two warps per TMEM lane quadrant (32 templates), each reading half
+//                  of the shift columns of E and O (tcgen05.ld) and taking their maximum; the
+//                  halves are combined in shared memory and one pre-score per (pattern, template)
+//                  is written to global memory (masked-out templates: -NaN).
 // Every mbarrier wait is bounded by the global timer (1 s); on timeout the CTA records an error
 // in a device word, stops its roles, lets the copies and MMAs it issued finish, releases TMEM
 // and returns.
@@ -46,8 +48,10 @@ constexpr int kBoxBytes = 64 * kChunk * 2; // 8 KB: 64 templates x 64 K rows
 constexpr int kSlotBytes = 2 * kBoxBytes;  // 16 KB
 constexpr int kStages = 4;
 constexpr int kBasisChunkBytes = kN * 128; // 24 KB
-constexpr int kThreads = 256;
 constexpr int kEpiWarp0 = 4;
+constexpr int kEpiWarps = 8;               // two per TMEM lane quadrant, each half of the shift columns
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = (kEpiWarp0 + kEpiWarps) * 32;
 constexpr unsigned long long kTimeoutNs = 1000000000ull;   // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const __grid_constan
     uint32_t* s_tmem = (uint32_t*)(bar + 2 * kStages + 2);
     int* s_abort = (int*)(s_tmem + 1);
     int* s_epi_stop = s_abort + 1;                             // [2], by unit parity
+    float* s_part = (float*)(s_epi_stop + 2);                  // [2 halves][kRows] partial maxima
     volatile int* abort_flag = s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const __grid_constan
             mbar_init(smem_u32(&bar[kStages + i]), 1);
         }
         mbar_init(bar_accf, 1);
-        mbar_init(bar_acce, kRows);
+        mbar_init(bar_acce, kEpiThreads);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&gmap) : "memory");
@@ -291,26 +296,30 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const __grid_constan
             }
         }
     } else if (warp >= kEpiWarp0) {
-        // ================================================================ epilogue (warps 4-7)
+        // ================================================================ epilogue (warps 4-11)
         const int ew = warp - kEpiWarp0;
-        const int row = ew * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(ew * 32) << 16);
+        const int quad = warp & 3, half = ew >> 2;            // TMEM lanes 32 quad.., shift columns by half
+        const int row = quad * 32 + lane;
+        const int et = ew * 32 + lane;                         // epilogue thread index
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
+        constexpr int kBlocks = kN / 32 / 2;                   // 32-column blocks per half
         uint32_t tt = 0;
         for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++tt) {
             const int p = (int)(u / tiles), t = (int)(u - (int64_t)p * tiles);
-            // row 0 waits and publishes one decision (a word per unit parity, so the next
+            // one thread waits and publishes one decision (a word per unit parity, so the next
             // unit's write cannot overtake a slow reader of this one)
-            if (row == 0) {
+            if (et == 0) {
                 const bool ok = mbar_wait(bar_accf, tt & 1u, abort_flag);
                 if (!ok) *abort_flag = 1;
                 s_epi_stop[tt & 1u] = (!ok || *abort_flag) ? 1 : 0;
             }
-            named_bar(1, kRows);
+            named_bar(1, kEpiThreads);
             if (*(volatile int*)&s_epi_stop[tt & 1u]) break;
             tc_fence_after();
             float best = -FLT_MAX;
 #pragma unroll 1
-            for (int cb = 0; cb < kN / 32; ++cb) {
+            for (int b = 0; b < kBlocks; ++b) {
+                const int cb = half * kBlocks + b;
                 float e[32], o[32];
                 tmem_ld32(tbase + cb * 32, e);
                 tmem_ld32(tbase + kN + cb * 32, o);
@@ -320,8 +329,11 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const __grid_constan
             }
             tc_fence_before();
             mbar_arrive(bar_acce);
+            s_part[half * kRows + row] = best;
+            named_bar(2, kEpiThreads);
             const int k = t * kRows + row;
-            if (k < c.K) {
+            if (half == 0 && k < c.K) {
+                best = fmaxf(best, s_part[kRows + row]);
                 const int64_t p_glob = c.p0 + p;
                 bool keep = true;
                 if (c.mask) keep = (c.mask[p_glob * c.words + (k >> 5)] >> (k & 31)) & 1u;
@@ -342,7 +354,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_kernel(const __grid_constan
 }  // namespace
 
 size_t dense_smem_bytes() {
-    return 1024 + (size_t)kChunks * kBasisChunkBytes + (size_t)kStages * kSlotBytes + (2 * kStages + 2) * 8 + 16;
+    return 1024 + (size_t)kChunks * kBasisChunkBytes + (size_t)kStages * kSlotBytes + (2 * kStages + 2) * 8 + 16 +
+           2 * kRows * 4;
 }
 
 bool dense_supported(int n_theta) { return n_theta % 2 == 0 && n_theta >= 4 && n_theta / 2 <= kN && (n_theta / 2) / 2 + 1 <= kN / 2; }

@@ -48,6 +48,7 @@ constexpr int kMaxThreads = 512;            // block sizes: 128, 256 (default) o
 constexpr int kStageUnroll = 4;             // row-staging chunks unrolled (their loads overlap)
 constexpr int kBoundUnroll = 4;             // bound loop over a template's spots unrolled
 constexpr int kMaxWarps = kMaxThreads / 32;
+constexpr int kSeedsMax = 16;              // templates of highest bound scored first, per warp (at most)
 
 }  // namespace
 
@@ -265,6 +266,10 @@ sparse_kernel(const SparseCall c) {
     const int ncov = prune_ncov(n_theta), nchw = prune_nchw(n_theta);
     const int nq = nchw + ncov - 1;
     __half* s_cw = reinterpret_cast<__half*>(s_rabs + c.max_rad);   // [max_rad][nchw]
+    // per-warp seed lists (bound / (|P| |T|) descending, template ids)
+    float* s_seedq = reinterpret_cast<float*>(((uintptr_t)(s_cw + (size_t)c.max_rad * nchw) + 3) & ~(uintptr_t)3);
+    int* s_seedk = reinterpret_cast<int*>(s_seedq + kWarps * kSeedsMax);
+    const int kSeeds = c.seeds_per_warp > 0 ? min(c.seeds_per_warp, kSeedsMax) : 8;
     const float inv_pitch = 1.0f / (float)pitch;
     unsigned long long work = 0;                             // multiply-adds of this warp (lane 0)
 
@@ -357,55 +362,220 @@ sparse_kernel(const SparseCall c) {
             const bool use_thr = !qo && c.hits;
             const bool prune = use_thr && L.nonneg;
             float qthr = -INFINITY;                          // the warp's N-th best Q once its list is full
+            // per-lane metadata of word wd's templates {first spot, spots | shifts << 16, norm bits,
+            // intensity-sum bits} (one load) and the mask of the word's templates to score
+            auto word_meta = [&](int wd, uint32_t& m, int4& meta_l, int& rem) {
+                m = mrow ? __ldg(mrow + wd) : 0xffffffffu;
+                rem = L.K - wd * 32;
+                if (rem < 32) m &= (1u << rem) - 1u;
+                meta_l = make_int4(0, 1 << 16, 0, 0);
+                if (lane < rem && ((m >> lane) & 1u)) meta_l = __ldg(L.meta + wd * 32 + lane);
+            };
+            // exact pruning (intensities >= 0): each lane bounds its template's best correlation
+            // over each of three windows of shifts, C(s) <= sum_i I_i max P'[r_i][visited
+            // columns] (the window maxima are rounded up), or with windows too wide for the
+            // chunk table over the whole row; plus a margin for the rounding of both sums
+            // (2^-24 per operation; sum_i |I_i P'| <= isum * pmax)
+            auto lane_bound = [&](const int4& meta_l) -> float {
+                const int cnt_l = meta_l.y & 0xffff;
+                float ub = 0.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+                if (windows) {
+                    // per spot: its intensity and the table entries of its three windows
+#pragma unroll kBoundUnroll
+                    for (int i = 0; i < cnt_l; ++i) {
+                        const int2 w = __ldg(L.bspot + meta_l.x + i);
+                        const float I = __int_as_float(w.x);
+                        const int j0 = w.y & 0xffff;
+                        u0 = fmaf(I, __half2float(s_cw[j0]), u0);
+                        u1 = fmaf(I, __half2float(s_cw[j0 + ((w.y >> 16) & 0xff)]), u1);
+                        u2 = fmaf(I, __half2float(s_cw[j0 + (int)((unsigned)w.y >> 24)]), u2);
+                    }
+                    ub = fmaxf(fmaxf(u0, u1), u2);
+                } else {
+                    for (int i = 0; i < cnt_l; ++i) {
+                        const int2 w = __ldg(spots + meta_l.x + i);
+                        int row, t;
+                        spot_row_col<LAYOUT>(w.x, inv_pitch, pitch, L.n_rad, row, t);
+                        ub = fmaf(__int_as_float(w.y), s_rmax[row], ub);
+                    }
+                }
+                return ub + (2.0f * (float)cnt_l + 40.0f) * 5.9604645e-8f * __int_as_float(meta_l.w) * pmax;
+            };
+            // score template k (warp-collective) and keep it in the warp's top-N when it enters
+            auto score_one = [&](int k, int beg, int cs, float tn, float ubm) {
+                const int cnt = cs & 0xffff, S = (int)((unsigned)cs >> 16);
+                const float d = pn * tn;
+                // Every warp's N-th best score is a lower bound of the pattern's final N-th
+                // best, and so is the best of them (s_thr).  A template below it cannot
+                // enter the top-N.
+                const float thr = use_thr ? fmaxf(qthr, key_score(*(volatile unsigned*)s_thr)) : -INFINITY;
+                // the template is skipped when its bound stays below thr * d (then Q < thr)
+                if (thr > -INFINITY && d > 0.0f) {
+                    const float td = thr * d;
+                    if (ubm < td - fabsf(td) * 4.8e-7f) return;
+                }
+                // a template whose correlation stays below the threshold (in correlation
+                // units, with a margin for the division's rounding) cannot enter the
+                // top-N, so its best shift is not resolved
+                float thr_c = -FLT_MAX;
+                if (use_thr && thr > -INFINITY && d > 0.0f) {
+                    const float t = thr * d;
+                    thr_c = t - fabsf(t) * 1e-6f;
+                }
+                int s = 0;
+                bool resolved = false;
+                const float best =
+                    score_dispatch<NBMAX, LAYOUT>(sP, spots, beg, cnt, S, n_theta, pitch, lane, thr_c, s, resolved);
+                if (c.work) work += (unsigned long long)cnt * (unsigned long long)S;
+                if (!resolved) return;
+                float q;
+                if (d > 0.0f) q = __fdiv_rn(best, d);
+                else { q = 0.0f; s = 0; }
+                if (lane == 0) {
+                    if (qo) { qo[k] = q; so[k] = s; }
+                    if (c.hits) {
+                        const int cnt_l = lcnt[warp];
+                        if (cnt_l < N || better(q, k, wq[N - 1], wk[N - 1])) {
+                            int i = cnt_l < N ? cnt_l : N - 1;
+                            while (i > 0 && better(q, k, wq[i - 1], wk[i - 1])) {
+                                wq[i] = wq[i - 1]; wk[i] = wk[i - 1]; ws[i] = ws[i - 1];
+                                --i;
+                            }
+                            wq[i] = q; wk[i] = k; ws[i] = s;
+                            if (cnt_l < N) lcnt[warp] = cnt_l + 1;
+                        }
+                    }
+                }
+                __syncwarp();
+                if (use_thr) {
+                    float nt = -INFINITY;
+                    if (lane == 0 && lcnt[warp] >= N) {
+                        nt = wq[N - 1];
+                        atomicMax(s_thr, score_key(nt));
+                    }
+                    qthr = __shfl_sync(0xffffffffu, nt, 0);
+                }
+            };
+            // Seeding (pruned top-N only): a first pass bounds every template and keeps, per warp,
+            // the seeds_per_warp templates of highest bound / (|P| |T|) (an upper bound of their Q; each
+            // 32-template word offers its best).  They are scored first, so the top-N threshold
+            // starts near its final value and the main pass skips almost every other template by
+            // its bound.  Seeded templates are marked and not scored again.
+            // (not with a template mask -- the pre-filter's survivors or the rescore candidates --,
+            // where too few templates remain for the extra pass to pay)
+            const bool seeding = prune && c.seed_bits && !mrow;
+            uint32_t* seedbits = c.seed_bits ? c.seed_bits + (size_t)blockIdx.x * c.seed_words : nullptr;
+            // every template's bound / (|P| |T|) from the seeding pass, rounded up to FP16, so the
+            // main pass compares it with the threshold instead of bounding the template again
+            __half* qbound = c.seed_bits ? c.seed_qub + (size_t)blockIdx.x * c.seed_words * 32 : nullptr;
+            if (seeding) {
+                float* sq = s_seedq + warp * kSeedsMax;
+                int* sk = s_seedk + warp * kSeedsMax;
+                if (lane < kSeeds) { sq[lane] = -INFINITY; sk[lane] = -1; }
+                for (int i = threadIdx.x; i < L.words; i += blockDim.x) seedbits[i] = 0u;
+                __syncwarp();
+                for (;;) {
+                    int wd = 0;
+                    if (lane == 0) wd = atomicAdd(counter, 1);
+                    wd = __shfl_sync(0xffffffffu, wd, 0);
+                    if (wd >= L.words) break;
+                    uint32_t m;
+                    int4 meta_l;
+                    int rem;
+                    word_meta(wd, m, meta_l, rem);
+                    float qb = -INFINITY;
+                    if (lane < rem && ((m >> lane) & 1u)) {
+                        const float d_l = pn * __int_as_float(meta_l.z);
+                        if (d_l > 0.0f) {
+                            qb = lane_bound(meta_l) / d_l;
+                            qbound[wd * 32 + lane] = __float2half_ru(qb);
+                        } else {
+                            qbound[wd * 32 + lane] = __ushort_as_half((unsigned short)0x7c00);   // +inf: never skipped
+                        }
+                    }
+                    float mq = qb;
+                    int ml = lane;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float oq = __shfl_xor_sync(0xffffffffu, mq, o);
+                        const int ol = __shfl_xor_sync(0xffffffffu, ml, o);
+                        if (oq > mq || (oq == mq && ol < ml)) { mq = oq; ml = ol; }
+                    }
+                    if (lane == 0 && mq > sq[kSeeds - 1]) {
+                        int i = kSeeds - 1;
+                        while (i > 0 && mq > sq[i - 1]) { sq[i] = sq[i - 1]; sk[i] = sk[i - 1]; --i; }
+                        sq[i] = mq;
+                        sk[i] = wd * 32 + ml;
+                    }
+                    __syncwarp();
+                }
+                __syncthreads();                             // the bit words are zero; every warp's seeds known
+                for (int i = 0; i < kSeeds; ++i) {
+                    const int k = sk[i];
+                    if (k < 0) break;
+                    if (lane == 0) atomicOr(seedbits + (k >> 5), 1u << (k & 31));
+                    const int4 mk = __ldg(L.meta + k);
+                    score_one(k, mk.x, mk.y, __int_as_float(mk.z), INFINITY);
+                }
+                __syncthreads();
+                // the N-th best of all warps' lists (distinct templates) bounds the final N-th
+                // best from below: it becomes the shared threshold
+                if (warp == 0) {
+                    const int total = kWarps * N;
+                    unsigned long long taken = 0;            // entries taken by this lane (bit per slot)
+                    float nth = -INFINITY;
+                    int got = 0;
+                    for (int j = 0; j < N; ++j) {
+                        float bq = -INFINITY;
+                        int bk = INT_MAX, bi = -1;
+                        for (int ci = lane, slot = 0; ci < total; ci += 32, ++slot) {
+                            const int w = ci / N, i = ci - w * N;
+                            if (i >= lcnt[w] || ((taken >> slot) & 1ull)) continue;
+                            if (bi < 0 || better(lq[ci], lk[ci], bq, bk)) { bq = lq[ci]; bk = lk[ci]; bi = ci; }
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float oq = __shfl_xor_sync(0xffffffffu, bq, o);
+                            const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                            if (oi >= 0 && (bi < 0 || better(oq, ok, bq, bk))) { bq = oq; bk = ok; bi = oi; }
+                        }
+                        if (bi < 0) break;
+                        if ((bi & 31) == lane) taken |= 1ull << (bi >> 5);
+                        nth = bq;
+                        ++got;
+                    }
+                    if (lane == 0 && got == N) atomicMax(s_thr, score_key(nth));
+                }
+                if (threadIdx.x == 0) *counter = 0;
+                __syncthreads();
+            }
             for (;;) {
                 int wd = 0;
                 if (lane == 0) wd = atomicAdd(counter, 1);
                 wd = __shfl_sync(0xffffffffu, wd, 0);
                 if (wd >= L.words) break;
-                uint32_t m = mrow ? __ldg(mrow + wd) : 0xffffffffu;
-                const int rem = L.K - wd * 32;
-                if (rem < 32) m &= (1u << rem) - 1u;
-                // per-lane metadata of the word's 32 templates: {first spot, spots | shifts << 16,
-                // norm bits, intensity-sum bits} in one load
-                const int kl = wd * 32 + lane;
-                int4 meta_l = make_int4(0, 1 << 16, 0, 0);
-                if (lane < rem && ((m >> lane) & 1u)) {
-                    meta_l = __ldg(L.meta + kl);
-                } else if (qo && lane < rem) {
-                    qo[kl] = -INFINITY;
-                    so[kl] = -1;
+                uint32_t m;
+                int4 meta_l;
+                int rem;
+                word_meta(wd, m, meta_l, rem);
+                if (qo && lane < rem && !((m >> lane) & 1u)) {
+                    qo[wd * 32 + lane] = -INFINITY;
+                    so[wd * 32 + lane] = -1;
                 }
-                // exact pruning (intensities >= 0): each lane bounds its template's best correlation
-                // over each of three windows of shifts, C(s) <= sum_i I_i max P'[r_i][visited
-                // columns] (the window maxima are rounded up), or with windows too wide for the
-                // chunk table over the whole row; plus a margin for the rounding of both sums
-                // (2^-24 per operation; sum_i |I_i P'| <= isum * pmax)
                 float ubm_l = INFINITY;
-                if (prune && lane < rem && ((m >> lane) & 1u)) {
-                    const int cnt_l = meta_l.y & 0xffff;
-                    float ub = 0.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
-                    if (windows) {
-                        // per spot: its intensity and the table entries of its three windows
-#pragma unroll kBoundUnroll
-                        for (int i = 0; i < cnt_l; ++i) {
-                            const int2 w = __ldg(L.bspot + meta_l.x + i);
-                            const float I = __int_as_float(w.x);
-                            const int j0 = w.y & 0xffff;
-                            u0 = fmaf(I, __half2float(s_cw[j0]), u0);
-                            u1 = fmaf(I, __half2float(s_cw[j0 + ((w.y >> 16) & 0xff)]), u1);
-                            u2 = fmaf(I, __half2float(s_cw[j0 + (int)((unsigned)w.y >> 24)]), u2);
-                        }
-                        ub = fmaxf(fmaxf(u0, u1), u2);
-                    } else {
-                        for (int i = 0; i < cnt_l; ++i) {
-                            const int2 w = __ldg(spots + meta_l.x + i);
-                            int row, t;
-                            spot_row_col<LAYOUT>(w.x, inv_pitch, pitch, L.n_rad, row, t);
-                            ub = fmaf(__int_as_float(w.y), s_rmax[row], ub);
-                        }
-                    }
-                    ubm_l = ub + (2.0f * (float)cnt_l + 40.0f) * 5.9604645e-8f * __int_as_float(meta_l.w) * pmax;
+                if (seeding) {
+                    // the seeding pass's bounds: drop, all lanes at once, the templates whose bound
+                    // (rounded up) is below the threshold, with a margin far above the rounding of the
+                    // division; a kept template is bounded again, exactly, before it is scored
+                    m &= ~seedbits[wd];
+                    const float thr0 = fmaxf(qthr, key_score(*(volatile unsigned*)s_thr));
+                    bool drop = false;
+                    if (thr0 > -INFINITY && lane < rem && ((m >> lane) & 1u))
+                        drop = __half2float(qbound[wd * 32 + lane]) < thr0 - fabsf(thr0) * 1e-5f;
+                    m &= ~__ballot_sync(0xffffffffu, drop);
                 }
+                if (prune && lane < rem && ((m >> lane) & 1u)) ubm_l = lane_bound(meta_l);
                 // drop, all lanes at once, the templates whose bound is already below the
                 // threshold (the threshold only rises, so the test in the loop would drop them
                 // as well); the loop then visits the others only
@@ -421,62 +591,9 @@ sparse_kernel(const SparseCall c) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1;
                     const int k = wd * 32 + bit;
-                    const int beg = __shfl_sync(0xffffffffu, meta_l.x, bit);
-                    const int cs = __shfl_sync(0xffffffffu, meta_l.y, bit);
-                    const float tn = __int_as_float(__shfl_sync(0xffffffffu, meta_l.z, bit));
-                    const float ubm = __shfl_sync(0xffffffffu, ubm_l, bit);
-                    const int cnt = cs & 0xffff, S = (int)((unsigned)cs >> 16);
-                    const float d = pn * tn;
-                    // Every warp's N-th best score is a lower bound of the pattern's final N-th
-                    // best, and so is the best of them (s_thr).  A template below it cannot
-                    // enter the top-N.
-                    const float thr = use_thr ? fmaxf(qthr, key_score(*(volatile unsigned*)s_thr)) : -INFINITY;
-                    // the template is skipped when its bound stays below thr * d (then Q < thr)
-                    if (thr > -INFINITY && d > 0.0f) {
-                        const float td = thr * d;
-                        if (ubm < td - fabsf(td) * 4.8e-7f) continue;
-                    }
-                    // a template whose correlation stays below the threshold (in correlation
-                    // units, with a margin for the division's rounding) cannot enter the
-                    // top-N, so its best shift is not resolved
-                    float thr_c = -FLT_MAX;
-                    if (use_thr && thr > -INFINITY && d > 0.0f) {
-                        const float t = thr * d;
-                        thr_c = t - fabsf(t) * 1e-6f;
-                    }
-                    int s = 0;
-                    bool resolved = false;
-                    const float best =
-                        score_dispatch<NBMAX, LAYOUT>(sP, spots, beg, cnt, S, n_theta, pitch, lane, thr_c, s, resolved);
-                    if (c.work) work += (unsigned long long)cnt * (unsigned long long)S;
-                    if (!resolved) continue;
-                    float q;
-                    if (d > 0.0f) q = __fdiv_rn(best, d);
-                    else { q = 0.0f; s = 0; }
-                    if (lane == 0) {
-                        if (qo) { qo[k] = q; so[k] = s; }
-                        if (c.hits) {
-                            const int cnt_l = lcnt[warp];
-                            if (cnt_l < N || better(q, k, wq[N - 1], wk[N - 1])) {
-                                int i = cnt_l < N ? cnt_l : N - 1;
-                                while (i > 0 && better(q, k, wq[i - 1], wk[i - 1])) {
-                                    wq[i] = wq[i - 1]; wk[i] = wk[i - 1]; ws[i] = ws[i - 1];
-                                    --i;
-                                }
-                                wq[i] = q; wk[i] = k; ws[i] = s;
-                                if (cnt_l < N) lcnt[warp] = cnt_l + 1;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    if (use_thr) {
-                        float nt = -INFINITY;
-                        if (lane == 0 && lcnt[warp] >= N) {
-                            nt = wq[N - 1];
-                            atomicMax(s_thr, score_key(nt));
-                        }
-                        qthr = __shfl_sync(0xffffffffu, nt, 0);
-                    }
+                    score_one(k, __shfl_sync(0xffffffffu, meta_l.x, bit), __shfl_sync(0xffffffffu, meta_l.y, bit),
+                              __int_as_float(__shfl_sync(0xffffffffu, meta_l.z, bit)),
+                              __shfl_sync(0xffffffffu, ubm_l, bit));
                 }
             }
             __syncthreads();
@@ -533,9 +650,11 @@ cudaError_t launch_nb(const SparseCall& c, int num_sms, size_t smem, cudaStream_
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > c.n) grid = c.n;
+    SparseCall cc = c;
+    if (cc.seed_bits && grid > cc.seed_ctas) cc.seed_bits = nullptr;   // per-CTA bit words not provided: no seeding
     e = cudaMemsetAsync(c.pattern_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    sparse_kernel<NBMAX, LAYOUT><<<(int)grid, threads, smem, st>>>(c);
+    sparse_kernel<NBMAX, LAYOUT><<<(int)grid, threads, smem, st>>>(cc);
     return cudaGetLastError();
 }
 
@@ -546,9 +665,12 @@ constexpr size_t kWrapFreeBytes = 100 * 1024;
 
 }  // namespace
 
+int sparse_max_ctas(int num_sms) { return num_sms * 8; }
+
 size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout, int* pitch) {
     if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
-    const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16 + (size_t)max_rad * 8 + 16;
+    const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16 + (size_t)max_rad * 8 + 16 +
+                         (size_t)kMaxWarps * kSeedsMax * 8 + 4;
     const int order[3] = {TM_LAYOUT_DUAL, TM_LAYOUT_WF, TM_LAYOUT_WRAP};
     const size_t limit[3] = {kDualBytes, kWrapFreeBytes, 232448};
     for (int i = 0; i < 3; ++i) {

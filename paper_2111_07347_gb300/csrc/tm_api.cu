@@ -197,9 +197,11 @@ struct tm_ctx {
     std::map<std::string, GraphEntry> graphs;
     uint64_t ws_gen = 1;           // bumped whenever a workspace buffer is reallocated
     bool capturing = false;
-    // autotuned sparse-kernel block size per library signature (tm_autotune)
-    std::map<std::string, int> tuned;
-    int tune_override = 0;
+    // autotuned sparse-kernel shape per library signature (tm_autotune): block size and
+    // seeds per warp of its pruned top-N
+    struct Tune { int threads = 0, seeds = 0; };
+    std::map<std::string, Tune> tuned;
+    Tune tune_override;
     std::string tune_file;
     // host-buffer entry point: two streams alternate over the chunks of a call
     cudaStream_t host_streams[2] = {nullptr, nullptr};
@@ -1274,9 +1276,9 @@ int tm_create(int device, size_t hbm_budget_bytes, tm_ctx** out) {
         ctx->tune_file = f;
         if (FILE* fh = fopen(f, "r")) {
             char key[512];
-            int threads = 0;
+            int threads = 0, seeds = 0;
             double ms = 0;
-            while (fscanf(fh, "%511s %d %lf", key, &threads, &ms) == 3) ctx->tuned[key] = threads;
+            while (fscanf(fh, "%511s %d %d %lf", key, &threads, &seeds, &ms) == 4) ctx->tuned[key] = {threads, seeds};
             fclose(fh);
         }
     }
@@ -1640,6 +1642,14 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
     if (!rc) rc = workspace(ctx, st, "pnorm", (size_t)chunk * 4, (void**)&pnorm);
     if (!rc) rc = workspace(ctx, st, "radial", (size_t)chunk * n_r * 4, (void**)&radial);
     if (!rc && pre) rc = workspace(ctx, st, "radial_norm", (size_t)chunk * 4, (void**)&rn);
+    // per-CTA words of the sparse kernel's seeded templates (pruned top-N)
+    int max_words = 1;
+    for (int i = 0; i < n_libs; ++i) max_words = std::max<int>(max_words, (int)((libs[i]->K + 31) / 32));
+    uint32_t* seed_bits = nullptr;
+    __half* seed_qub = nullptr;
+    const int seed_ctas = tmgb::sparse_max_ctas(sms);
+    if (!rc) rc = workspace(ctx, st, "seed_bits", (size_t)seed_ctas * max_words * 4, (void**)&seed_bits);
+    if (!rc) rc = workspace(ctx, st, "seed_qub", (size_t)seed_ctas * max_words * 32 * 2, (void**)&seed_qub);
     TensorBuffers tb;
     if (!rc && bf16) rc = tensor_buffers(ctx, st, tp, std::min<int64_t>(tp.nb, chunk), &tb);
     if (rc) return rc;
@@ -1663,10 +1673,13 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
     // the sparse kernel's block size: forced (autotuning), tuned for these libraries, or by
     // default 256 -- but 512 when the chunk has at most two patterns per SM, so that each
     // pattern is shared by twice the warps (the latency of small batches such as scan lines)
-    int sparse_threads = ctx->tune_override;
+    int sparse_threads = ctx->tune_override.threads, sparse_seeds = ctx->tune_override.seeds;
     if (!sparse_threads) {
         auto tt = ctx->tuned.find(tune_key(libs, n_libs, N));
-        if (tt != ctx->tuned.end()) sparse_threads = tt->second;
+        if (tt != ctx->tuned.end()) {
+            sparse_threads = tt->second.threads;
+            sparse_seeds = tt->second.seeds;
+        }
     }
     if (!sparse_threads && std::min(chunk, n) <= 2 * (int64_t)sms) sparse_threads = 512;
     int64_t launches = 0, corr = 0, scored = 0;
@@ -1713,6 +1726,11 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
             c.top_n = N;
             c.threads = sparse_threads;
             c.work = ctx->profiling ? ctx->d_work : nullptr;
+            c.seed_bits = seed_bits;
+            c.seed_qub = seed_qub;
+            c.seed_words = max_words;
+            c.seed_ctas = seed_ctas;
+            c.seeds_per_warp = sparse_seeds;
             if (bf16) {
                 int64_t nl = 0;
                 const int rc2 = prescore_rows(ctx, st, libs, n_libs, spec, tb, polar, pnorm, m, pre ? mask : nullptr,
@@ -1720,13 +1738,16 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
                 if (rc2) return rc2;
                 launches += nl;
                 {
-                    StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
+                    StageTimer tmr(ctx, TM_STAGE_SELECT, st);
                     for (int i = 0; i < n_libs; ++i) {
                         const int kci = std::min(kc, keep[i]);
                         TM_CUDA(tmgb::launch_prefilter_select(score[i], m, (int)libs[i]->K, kci, mask[i], st),
                                 "tm_index_patterns: candidates");
                         ++launches;
                     }
+                }
+                {
+                    StageTimer tmr(ctx, TM_STAGE_RESCORE, st);
                     TM_CUDA(tmgb::launch_sparse(c, sms, st), "tm_index_patterns: rescore");
                 }
                 ++launches;
@@ -1780,8 +1801,8 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
                            dtype, (long long)n, H, W, params->gamma, params->subtract, params->cx, params->cy,
                            params->prefilter_fraction, params->threshold, params->top_n, params->path,
                            params->rescore_k);
-        off += snprintf(key + off, sizeof key - off, "r%d|t%d|s%lld|m%d|", params->reserved & ~TM_INDEX_GRAPH,
-                        sparse_threads, (long long)lib_stride, sms);
+        off += snprintf(key + off, sizeof key - off, "r%d|t%d.%d|s%lld|m%d|", params->reserved & ~TM_INDEX_GRAPH,
+                        sparse_threads, sparse_seeds, (long long)lib_stride, sms);
         for (int i = 0; i < n_libs && off < (int)sizeof key - 12; ++i) off += snprintf(key + off, sizeof key - off, "%d,", lib_ids[i]);
         tm_ctx::GraphEntry& ge = ctx->graphs[key];
         if (ge.exec && ge.ws_gen == ctx->ws_gen) {
@@ -1859,13 +1880,16 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
     p.reserved = 0;
     p.pixel_mask = nullptr;
     p.threshold = 0.0;
-    const int cand[3] = {128, 256, 512};
-    int best = 256;
+    // block sizes x seeds per warp (the templates of highest bound scored first, whose scores
+    // set the top-N threshold the rest is pruned against)
+    const int cand_t[3] = {128, 256, 512}, cand_s[3] = {4, 8, 16};
+    tm_ctx::Tune best{256, 8};
     double best_ms = 1e30;
-    for (int t : cand) {
+    for (int ci = 0; ci < 9; ++ci) {
+        const tm_ctx::Tune tc{cand_t[ci / 3], cand_s[ci % 3]};
         {
             std::lock_guard<std::mutex> lk(ctx->mu);
-            ctx->tune_override = t;
+            ctx->tune_override = tc;
         }
         int rc = tm_index_patterns(ctx, &p, frames_dev, dtype, m, H, W, nullptr, lib_ids, n_libs, out, nullptr, stream);
         if (!rc) rc = tm_profile_enable(ctx, 1);
@@ -1876,13 +1900,13 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
         tm_profile_enable(ctx, 0);
         {
             std::lock_guard<std::mutex> lk(ctx->mu);
-            ctx->tune_override = 0;
+            ctx->tune_override = tm_ctx::Tune{};
         }
         if (rc) return rc;
         const double ms = prof.ms[TM_STAGE_SPARSE];
         if (ms < best_ms) {
             best_ms = ms;
-            best = t;
+            best = tc;
         }
     }
     {
@@ -1890,12 +1914,12 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
         ctx->tuned[key] = best;
         if (!ctx->tune_file.empty()) {
             if (FILE* fh = fopen(ctx->tune_file.c_str(), "a")) {
-                fprintf(fh, "%s %d %.6f\n", key.c_str(), best, best_ms / 3.0);
+                fprintf(fh, "%s %d %d %.6f\n", key.c_str(), best.threads, best.seeds, best_ms / 3.0);
                 fclose(fh);
             }
         }
     }
-    if (best_threads) *best_threads = best;
+    if (best_threads) *best_threads = best.threads;
     return TM_OK;
 }
 

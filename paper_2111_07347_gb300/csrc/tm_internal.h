@@ -1,6 +1,7 @@
 // Internal declarations shared by the host API and the kernels of libtmgb.so.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -173,7 +174,16 @@ struct SparseCall {
     int top_n;
     int threads;                        // block size: 128, 256 or 512 (0 = 256)
     unsigned long long* work;           // nullable: += multiply-adds executed (per warp, at exit)
+    // pruned top-N: per-CTA words marking the templates scored first (seeds), [seed_ctas][seed_words];
+    // null (or a grid larger than seed_ctas) disables seeding
+    uint32_t* seed_bits;
+    __half* seed_qub;                   // [seed_ctas][32 seed_words] bounds of the seeding pass
+    int seed_words;                     // >= the libraries' largest word count
+    int seed_ctas;
+    int seeds_per_warp;                 // 1..16 (0 = 8)
 };
+// Largest grid of the sparse kernel on a device with num_sms SMs (the seed words are per CTA).
+int sparse_max_ctas(int num_sms);
 
 // Shared-memory bytes the sparse kernel needs (0 when unsupported), the layout it uses
 // (wrap-free rows when they fit comfortably) and its row pitch.

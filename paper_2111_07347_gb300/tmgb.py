@@ -91,7 +91,7 @@ class tm_request_status(ctypes.Structure):
 
 
 TM_STAGE_COUNT = 8
-STAGES = ["polar", "prefilter", "sparse", "dft", "dense", "rescore", "gemm", "stage7"]
+STAGES = ["polar", "prefilter", "sparse", "dft", "dense", "rescore", "gemm", "select"]
 
 
 class tm_preprocess_params(ctypes.Structure):
