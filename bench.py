@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "patterns/s indexed, BF16-TC vs FP32 sparse at ≥99.5% top-1 match; p99 line ms"
 N_R, N_THETA, TOP_N = 128, 360, 5
-E2E_CHUNK = 2048                  # patterns per chunk of the host-buffer entry point (tm_index_patterns_host)
+E2E_CHUNK = 4096                  # patterns per chunk of the host-buffer entry point (tm_index_patterns_host)
 # tensor-core work per (pattern, scored template): 2 x 180 shifts x (182 + 180) frequency terms
 DENSE_FLOPS_PER_PAIR = 2 * 180 * (182 + 180)
 # rescore_k: candidates of the BF16 pre-score rescored exactly; the configured 64 where it meets the
