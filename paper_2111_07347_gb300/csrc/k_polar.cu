@@ -351,12 +351,73 @@ __device__ __forceinline__ uint32_t stage_frame(const T* __restrict__ gframe, T*
     return hi_bits;
 }
 
+// ---------------------------------------------------------------- bulk (TMA) staging
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bar_try(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase (1 s of the global timer); false on timeout.
+__device__ bool bar_wait(uint32_t addr, uint32_t parity) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (bar_try(addr, parity)) return true;
+        if ((it & 255u) == 255u) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 1000000000ull) return false;
+        }
+    }
+}
+
+// Copies one frame into shared memory with the bulk-copy engine (one cp.async.bulk per row,
+// rows `pitch` elements apart, every row start and length a multiple of 16 bytes), completing
+// on the mbarrier `bar` (phase `parity`), then returns the OR of the staged words as
+// stage_frame does.  False (uniformly over the CTA) when the wait ran out.
+template <typename T>
+__device__ __forceinline__ bool stage_frame_bulk(const T* __restrict__ gframe, T* sF, int H, int W, int pitch,
+                                                 uint64_t* bar, uint32_t parity, uint32_t& hi_bits) {
+    const uint32_t b = smem_u32(bar);
+    const uint32_t row_bytes = (uint32_t)(W * sizeof(T));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of sF before the copies' writes
+    if (threadIdx.x == 0)
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
+                     "r"(row_bytes * (uint32_t)H)
+                     : "memory");
+    for (int y = threadIdx.x; y < H; y += blockDim.x)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(sF + (size_t)y * pitch)),
+                     "l"(gframe + (size_t)y * W), "r"(row_bytes), "r"(b)
+                     : "memory");
+    const bool ok = bar_wait(b, parity);
+    if (__syncthreads_or(!ok)) return false;
+    hi_bits = 0;
+    const int vr = (int)(row_bytes / 16);
+    for (int i = threadIdx.x; i < H * vr; i += blockDim.x) {
+        const int y = i / vr, xv = i - y * vr;
+        const uint4 v = *(const uint4*)((const char*)(sF + (size_t)y * pitch) + 16 * xv);
+        hi_bits |= v.x | v.y | v.z | v.w;
+    }
+    return true;
+}
+
 template <typename T, int MODE, bool STAGED>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, const longlong2* __restrict__ rays,
              long long cxb, long long cyb, float2 g, float sub, int n_r, int n_theta, int R,
              const uint8_t* __restrict__ keep_row, const uint8_t* __restrict__ pmask, float* __restrict__ polar,
-             float* __restrict__ pnorm, float* __restrict__ radial, const float2* __restrict__ centres) {
+             float* __restrict__ pnorm, float* __restrict__ radial, const float2* __restrict__ centres, int bulk,
+             unsigned* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int cols = blockDim.x / R;                     // threads per row group (multiple of 32)
     const int grp = threadIdx.x / cols, t_in = threadIdx.x - grp * cols;
@@ -380,6 +441,12 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
     float* lut = (float*)(smem_raw + ((fbytes + 15) & ~(size_t)15));   // [kLut] for u16 frames
     float* part = lut + (kHasLut ? kLut : 0);                           // [n_r][nw]
     float* red = part + (size_t)n_r * nw;                               // [blockDim]
+    uint64_t* bar = (uint64_t*)(((uintptr_t)(red + blockDim.x) + 7) & ~(uintptr_t)7);   // bulk staging
+    if (STAGED && bulk && threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t staged = 0;                                                // frames staged by bulk copies
     if (kHasLut) {
         for (int i = threadIdx.x; i < kLut; i += blockDim.x) {
             const float f = (float)i;
@@ -394,7 +461,21 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
         bool big = true;                                 // some pixel may lie beyond the gamma table
         if (STAGED) {
             __syncthreads();                             // previous pattern's reads are done
-            const uint32_t hi_bits = stage_frame<T>(gframe, sF, H, W, pitch, pmask);
+            uint32_t hi_bits = 0;
+            if (bulk) {
+                if (!stage_frame_bulk<T>(gframe, sF, H, W, pitch, bar, staged & 1u, hi_bits)) {
+                    // the copy did not land in time: report it, let it finish (bounded), stop
+                    if (threadIdx.x == 0) {
+                        atomicOr(err, 2u);
+                        bar_wait(smem_u32(bar), staged & 1u);
+                    }
+                    __syncthreads();
+                    return;
+                }
+                ++staged;
+            } else {
+                hi_bits = stage_frame<T>(gframe, sF, H, W, pitch, pmask);
+            }
             // u16 words: a pixel >= kLut sets a bit of 0xF000 in its half
             big = __syncthreads_or(kHasLut ? (hi_bits & 0xF000F000u) != 0 : 1) != 0;
             frame = sF;
@@ -452,7 +533,7 @@ template <typename T, int MODE, bool STAGED>
 cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, const longlong2* rays, long long cxb,
                        long long cyb, float2 g, float sub, int n_r, int n_theta, int R, int threads, size_t smem,
                        const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm, float* radial,
-                       const float2* centres, cudaStream_t st) {
+                       const float2* centres, int bulk, unsigned* err, cudaStream_t st) {
     auto kern = polar_kernel<T, MODE, STAGED>;
     int per_sm = 1;
     const cudaError_t e = kernel_occupancy((const void*)kern, threads, smem, &per_sm);
@@ -460,7 +541,7 @@ cudaError_t launch_one(const T* frames, int64_t n, int H, int W, int pitch, cons
     int64_t grid = (int64_t)device_sms() * (per_sm > 0 ? per_sm : 1);
     if (grid > n) grid = n;
     kern<<<(int)grid, threads, smem, st>>>(frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, keep_row,
-                                           pmask, polar, pnorm, radial, centres);
+                                           pmask, polar, pnorm, radial, centres, bulk, err);
     return cudaGetLastError();
 }
 
@@ -468,41 +549,47 @@ template <typename T, bool STAGED>
 cudaError_t launch_mode(int mode, const T* frames, int64_t n, int H, int W, int pitch, const longlong2* rays,
                         long long cxb, long long cyb, float2 g, float sub, int n_r, int n_theta, int R, int threads,
                         size_t smem, const uint8_t* keep_row, const uint8_t* pmask, float* polar, float* pnorm,
-                        float* radial, const float2* centres, cudaStream_t st) {
+                        float* radial, const float2* centres, int bulk, unsigned* err, cudaStream_t st) {
     auto f = mode == 0 ? launch_one<T, 0, STAGED> : (mode == 1 ? launch_one<T, 1, STAGED> : launch_one<T, 2, STAGED>);
     return f(frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, threads, smem, keep_row, pmask, polar,
-             pnorm, radial, centres, st);
+             pnorm, radial, centres, bulk, err, st);
 }
 
 template <typename T>
 cudaError_t launch_typed(const T* frames, int64_t n, int H, int W, const longlong2* rays, long long cxb, long long cyb,
                          int mode, float2 g, float sub, int n_r, int n_theta, float* polar, float* pnorm, float* radial,
-                         cudaStream_t st, const uint8_t* keep_row, const float2* centres, const uint8_t* pmask) {
+                         cudaStream_t st, const uint8_t* keep_row, const float2* centres, const uint8_t* pmask,
+                         unsigned* err) {
     const int cols = ((n_theta + 31) / 32) * 32;
     if (cols <= kMaxThreads) {
-        // staged: rows padded to 9 (mod 32) 32-bit words, else (if that does not fit) to an
-        // odd number
+        // staged: rows padded to 4 (mod 32) 32-bit words when the frame's rows are whole
+        // 16-byte units (then the rows are copied by the bulk-copy engine), else to 9 (mod 32);
+        // both spread a warp's taps over the banks alike (1.5 shared-memory wavefronts per tap
+        // load on a 256 x 256 frame, replayed on the CPU over every warp's patch); an odd pitch
+        // if neither fits
         const int words = (int)((W * sizeof(T) + 3) / 4);
         const int R = std::max(1, std::min(4, kMaxThreads / cols));
         const int threads = R * cols;
         const int nw = threads / 32;
         const size_t lut = sizeof(T) == 2 ? kLut * sizeof(float) : 0;
         auto smem_of = [&](int pw) {
-            return (((size_t)H * pw * 4 + 15) & ~(size_t)15) + lut + ((size_t)n_r * nw + threads) * sizeof(float);
+            return (((size_t)H * pw * 4 + 15) & ~(size_t)15) + lut + ((size_t)n_r * nw + threads) * sizeof(float) + 16;
         };
-        int pw = words + ((9 - words % 32) + 32) % 32;
+        const bool rows16 = (W * sizeof(T)) % 16 == 0 && ((uintptr_t)frames & 15) == 0;
+        int pw = words + (((rows16 ? 4 : 9) - words % 32) + 32) % 32;
         if (smem_of(pw) > 200 * 1024) pw = words | 1;
         const int pitch = (int)(pw * 4 / sizeof(T));
         const size_t smem = smem_of(pw);
+        const int bulk = rows16 && (pw % 4) == 0 && !pmask && err != nullptr;
         if (smem <= 200 * 1024)
             return launch_mode<T, true>(mode, frames, n, H, W, pitch, rays, cxb, cyb, g, sub, n_r, n_theta, R, threads,
-                                        smem, keep_row, pmask, polar, pnorm, radial, centres, st);
+                                        smem, keep_row, pmask, polar, pnorm, radial, centres, bulk, err, st);
     }
     const int threads = cols < kMaxThreads ? cols : kMaxThreads;
     const size_t smem = (sizeof(T) == 2 ? kLut * sizeof(float) : 0) + ((size_t)n_r * (threads / 32) + threads) * sizeof(float);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     return launch_mode<T, false>(mode, frames, n, H, W, W, rays, cxb, cyb, g, sub, n_r, n_theta, 1, threads, smem,
-                                 keep_row, pmask, polar, pnorm, radial, centres, st);
+                                 keep_row, pmask, polar, pnorm, radial, centres, 0, err, st);
 }
 
 }  // namespace
@@ -518,7 +605,7 @@ void build_polar_rays(int n_theta, double dr, longlong2* rays) {
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W, const longlong2* rays, double cx,
                          double cy, double gamma, double subtract, int n_r, int n_theta, float* polar, float* pnorm,
                          float* radial, cudaStream_t st, const uint8_t* keep_row, const float2* centres,
-                         const uint8_t* pixel_mask, double threshold) {
+                         const uint8_t* pixel_mask, double threshold, unsigned* err) {
     if (n <= 0) return cudaSuccess;
     // positions stay within 2^31 px in the 32.32 format (the caller bounds n_r dr as well)
     if (!(fabs(cx) < 1073741824.0 && fabs(cy) < 1073741824.0)) return cudaErrorInvalidValue;
@@ -534,9 +621,9 @@ cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W,
     const long long cxb = llround(cx * 4294967296.0) + kRound, cyb = llround(cy * 4294967296.0) + kRound;
     if (dtype == TM_DTYPE_U16)
         return launch_typed<uint16_t>((const uint16_t*)frames, n, H, W, rays, cxb, cyb, mode, g, (float)subtract, n_r,
-                                      n_theta, polar, pnorm, radial, st, keep_row, centres, pixel_mask);
+                                      n_theta, polar, pnorm, radial, st, keep_row, centres, pixel_mask, err);
     return launch_typed<float>((const float*)frames, n, H, W, rays, cxb, cyb, mode, g, (float)subtract, n_r, n_theta,
-                               polar, pnorm, radial, st, keep_row, centres, pixel_mask);
+                               polar, pnorm, radial, st, keep_row, centres, pixel_mask, err);
 }
 
 }  // namespace tmgb

@@ -556,25 +556,32 @@ sparse_kernel(const SparseCall c) {
                 wd = __shfl_sync(0xffffffffu, wd, 0);
                 if (wd >= L.words) break;
                 uint32_t m;
-                int4 meta_l;
+                int4 meta_l = make_int4(0, 1 << 16, 0, 0);
                 int rem;
-                word_meta(wd, m, meta_l, rem);
-                if (qo && lane < rem && !((m >> lane) & 1u)) {
-                    qo[wd * 32 + lane] = -INFINITY;
-                    so[wd * 32 + lane] = -1;
-                }
-                float ubm_l = INFINITY;
                 if (seeding) {
                     // the seeding pass's bounds: drop, all lanes at once, the templates whose bound
                     // (rounded up) is below the threshold, with a margin far above the rounding of the
-                    // division; a kept template is bounded again, exactly, before it is scored
+                    // division; a kept template is bounded again, exactly, before it is scored.  The
+                    // metadata of a word is loaded only when some template of it is kept.
+                    rem = L.K - wd * 32;
+                    m = 0xffffffffu;
+                    if (rem < 32) m &= (1u << rem) - 1u;
                     m &= ~seedbits[wd];
                     const float thr0 = fmaxf(qthr, key_score(*(volatile unsigned*)s_thr));
                     bool drop = false;
                     if (thr0 > -INFINITY && lane < rem && ((m >> lane) & 1u))
                         drop = __half2float(qbound[wd * 32 + lane]) < thr0 - fabsf(thr0) * 1e-5f;
                     m &= ~__ballot_sync(0xffffffffu, drop);
+                    if (!m) continue;
+                    if ((m >> lane) & 1u) meta_l = __ldg(L.meta + wd * 32 + lane);
+                } else {
+                    word_meta(wd, m, meta_l, rem);
+                    if (qo && lane < rem && !((m >> lane) & 1u)) {
+                        qo[wd * 32 + lane] = -INFINITY;
+                        so[wd * 32 + lane] = -1;
+                    }
                 }
+                float ubm_l = INFINITY;
                 if (prune && lane < rem && ((m >> lane) & 1u)) ubm_l = lane_bound(meta_l);
                 // drop, all lanes at once, the templates whose bound is already below the
                 // threshold (the threshold only rises, so the test in the loop would drop them

@@ -1489,7 +1489,7 @@ int tm_polar_transform(tm_ctx* ctx, const tm_index_params* params, const void* f
     cudaStream_t st = (cudaStream_t)stream;
     TM_CUDA(tmgb::launch_polar(frames_dev, dtype, n, H, W, rays, cx, cy, params->gamma, params->subtract, n_r, n_theta,
                                polar_dev, norm_dev, radial_dev, st, nullptr, (const float2*)centres_dev,
-                               params->pixel_mask, params->threshold),
+                               params->pixel_mask, params->threshold, ctx->d_error),
             "tm_polar_transform: launch");
     return TM_OK;
 }
@@ -1692,7 +1692,7 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
                 TM_CUDA(tmgb::launch_polar(fr, dtype, m, H, W, rays, cx, cy, params->gamma, params->subtract, n_r,
                                            n_theta, polar, pnorm, radial, st, rmap.keep_row,
                                            centres_dev ? (const float2*)centres_dev + c0 : nullptr,
-                                           params->pixel_mask, params->threshold),
+                                           params->pixel_mask, params->threshold, ctx->d_error),
                         "tm_index_patterns: polar");
             }
             ++launches;

@@ -84,12 +84,14 @@ void build_polar_rays(int n_theta, double dr, longlong2* rays);
 // rays [n_theta] from build_polar_rays; (cx, cy) the centre (|c| < 2^30, n_r dr < 2^30).
 // keep_row [n_r] (nullable): rows whose polar values are stored; the norm and the row
 // sums always cover every row.  centres [n] (nullable): per-pattern beam centres, used
-// instead of (cx, cy).
+// instead of (cx, cy).  err (nullable): device error word; when given, frames whose rows are
+// whole 16-byte units (and no pixel mask) are staged by bulk copies, whose bounded wait sets
+// bit 1 of err if it runs out.
 cudaError_t launch_polar(const void* frames, int dtype, int64_t n, int H, int W, const longlong2* rays, double cx,
                          double cy, double gamma, double subtract, int n_r, int n_theta, float* polar, float* pnorm,
                          float* radial, cudaStream_t st, const uint8_t* keep_row = nullptr,
                          const float2* centres = nullptr, const uint8_t* pixel_mask = nullptr,
-                         double threshold = 0.0);
+                         double threshold = 0.0, unsigned* err = nullptr);
 
 // Sub-step in-plane angle of the top-N hits (parabola through Q at s - 1, s, s + 1).
 struct RefineLib {
