@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=30.0, help="seconds per offered-load level")
     ap.add_argument("--no-two-stage", action="store_true", help="skip the two-stage (masked) indexing run")
     ap.add_argument("--no-preprocess", action="store_true", help="skip the background-removal and blur timing")
+    ap.add_argument("--total", type=int, default=0, help="patterns per step (0: the workload's; smaller for profiling)")
+    ap.add_argument("--distinct", type=int, default=0, help="distinct rendered frames (0: the workload's)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the sparse kernel's default shape")
     return ap.parse_args()
 
 
@@ -658,7 +661,7 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
     # for these libraries, on the first frames of the scan (outside every timed region)
     tune_n = 256 if name == "multiphase" else 2048
     t0 = time.perf_counter()
-    tuned_threads = ctx.autotune(frames_d[:tune_n], lids, top_n=TOP_N, prefilter=prefilter)
+    tuned_threads = None if args.no_autotune else ctx.autotune(frames_d[:tune_n], lids, top_n=TOP_N, prefilter=prefilter)
     tune_s = time.perf_counter() - t0
     res, hits = {}, {}
     for nm in want_paths:
@@ -755,29 +758,34 @@ def run_ours(args):
     head_done = False
     for wi, wl in enumerate(wls):
         if wl == "large_map":
-            ts, scan, _ = synth.large_map_workload(n_unique=LARGE_MAP["unique"], stream=rank)
+            ts, scan, _ = synth.large_map_workload(n_unique=args.distinct or LARGE_MAP["unique"], stream=rank)
             uniq = scan.frames
             libs_ts = [ts]
-            total = LARGE_MAP["total"]
+            total = args.total or LARGE_MAP["total"]
             prefilter = 1.0
             oracle_n = args.oracle_patterns
             rk = LARGE_MAP["rescore_k"]
         elif wl == "multiphase":
-            libs_ts, uniq, phase, _, _ = synth.multiphase_workload(n_unique=MULTIPHASE["unique"], stream=rank)
-            total = MULTIPHASE["total"]
+            libs_ts, uniq, phase, _, _ = synth.multiphase_workload(n_unique=args.distinct or MULTIPHASE["unique"],
+                                                                   stream=rank)
+            total = args.total or MULTIPHASE["total"]
             prefilter = 1.0
             oracle_n = args.oracle_multiphase
             rk = MULTIPHASE["rescore_k"]
         elif wl == "single_phase":
-            ts, scan, _ = synth.single_phase_workload(n_patterns=SINGLE_PHASE["total"], stream=rank)
+            ts, scan, _ = synth.single_phase_workload(n_patterns=args.distinct or SINGLE_PHASE["total"], stream=rank)
             uniq = scan.frames
             libs_ts = [ts]
-            total = SINGLE_PHASE["total"]
+            total = args.total or SINGLE_PHASE["total"]
             prefilter = SINGLE_PHASE["prefilter"]
             oracle_n = 512
             rk = SINGLE_PHASE["rescore_k"]
         else:
             raise SystemExit(f"unknown workload {wl}")
+        if total < uniq.shape[0]:                            # a smaller scan (profiling)
+            uniq = np.ascontiguousarray(uniq[:total])
+            if wl == "multiphase":
+                phase = phase[:total]
         base = to_device_u16(uniq, dev)
         frames_d = base.repeat(total // uniq.shape[0], 1, 1) if total > uniq.shape[0] else base
         del base
@@ -789,7 +797,7 @@ def run_ours(args):
         sample_idx = pick + uniq.shape[0] * np.random.default_rng(6).integers(0, reps, size=pick.shape[0])
         # the FP32 sparse path on the three-phase scan takes tens of seconds per step: it is timed
         # on 4096 of the distinct frames
-        subsets = {"fp32": 4096} if wl == "multiphase" else {}
+        subsets = {"fp32": min(4096, total)} if wl == "multiphase" else {}
         rec, res = bench_workload(args, ctx, timer, wl, libs_ts, lids, frames_d, uniq, sample_idx, prefilter,
                                   oracle_n, local, dev, world, want_paths, rank, rk, subsets, headline=not head_done)
         if wl == "multiphase" and rank == 0 and rec.get("paths"):
