@@ -169,16 +169,16 @@ def kernel_sha(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel_file: str, key: str):
-    """DRAM bytes per full-size launch from the committed ncu summary `profiles/traffic.txt`
-    (lines: kernel, sha256[:16] of its source file, bytes, note), if it was taken on this
-    source; None otherwise."""
+def traffic_from_profiles(kernel_file: str, key: str, units: float):
+    """DRAM bytes of one launch that processes `units` units of work, from the committed ncu
+    summary `profiles/traffic.txt` (lines: kernel, sha256[:16] of its source file, bytes per unit,
+    unit, capture), if it was taken on this source; None otherwise."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         for line in open(p):
             f = line.split()
-            if len(f) >= 3 and not f[0].startswith("#") and f[0] == key and f[1] == kernel_sha(kernel_file):
-                return float(f[2])
+            if len(f) >= 4 and not f[0].startswith("#") and f[0] == key and f[1] == kernel_sha(kernel_file):
+                return float(f[2]) * units
     except OSError:
         pass
     return None
@@ -553,7 +553,7 @@ class Timer:
         return prof, counters, steps
 
 
-def sparse_roofline(prof, counters, prof_steps, macs_step, clk, sm):
+def sparse_roofline(prof, counters, prof_steps, macs_step, clk, sm, patterns_step):
     """Shared-memory roofline of sparse_kernel: one 4-byte operand per FP32 multiply-add.  frac is
     the executed work (the multiply-adds the kernel ran, counted while profiling) over the peak;
     the algorithmic fraction counts every template the definition scores, including those the
@@ -571,7 +571,8 @@ def sparse_roofline(prof, counters, prof_steps, macs_step, clk, sm):
     alg_gbs = 4.0 * alg / (per_launch_ms / 1e3) / 1e9
     return {"bound": "smem", "kernel": "sparse_kernel", "achieved": ex_gbs, "peak": peak, "unit": "GB/s",
             "frac": ex_gbs / peak, "traffic": traffic_from_profiles(
-                os.path.join(ROOT, "paper_2111_07347_gb300", "csrc", "k_sparse.cu"), "sparse_kernel"),
+                os.path.join(ROOT, "paper_2111_07347_gb300", "csrc", "k_sparse.cu"), "sparse_kernel",
+                patterns_step / lps),
             "work": "4 B of shared memory per FP32 multiply-add executed (one polar sample per spot x shift "
                     "of every template the kernel scores)",
             "macs_executed_per_launch": ex, "macs_algorithmic_per_launch": alg,
@@ -592,25 +593,29 @@ def dense_roofline(prof, prof_steps, pairs_step):
     peak = MEASURED.get("bf16_tflops_sustained") or 1700.0
     return {"bound": "tensor", "kernel": "dense_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic_from_profiles(
-                os.path.join(ROOT, "paper_2111_07347_gb300", "csrc", "k_dense.cu"), "dense_kernel"),
+                os.path.join(ROOT, "paper_2111_07347_gb300", "csrc", "k_dense.cu"), "dense_kernel", pairs_step / lps),
             "work": f"{DENSE_FLOPS_PER_PAIR} flop per (pattern, scored template): inverse DFT over "
                     "182 even + 180 odd frequency terms for 180 shifts",
             "peak_basis": "measured sustained cuBLAS bf16 (MEASURED_PEAKS.json)", "launch_ms": per_launch_ms}
 
 
 def polar_roofline(prof, prof_steps, n, kept_rows):
+    """HBM roofline of polar_kernel per launch: the frame read once, the kept rows written, the
+    azimuthal sums and the norm."""
     pol_ms, pol_l = prof.get("polar", (0.0, 0))
     if not pol_l:
         return None
-    ms = pol_ms / prof_steps
-    hbm_bytes = n * (256 * 256 * 2 + kept_rows * N_THETA * 4 + N_R * 4 + 4)
+    ms = pol_ms / pol_l
+    per_launch = n * prof_steps / pol_l
+    hbm_bytes = per_launch * (256 * 256 * 2 + kept_rows * N_THETA * 4 + N_R * 4 + 4)
     gbs = hbm_bytes / (ms / 1e3) / 1e9
     peak = MEASURED.get("hbm_gbs") or 6800.0
-    tr = traffic_from_profiles(os.path.join(ROOT, "paper_2111_07347_gb300", "csrc", "k_polar.cu"), "polar_kernel")
+    tr = traffic_from_profiles(os.path.join(ROOT, "paper_2111_07347_gb300", "csrc", "k_polar.cu"), "polar_kernel",
+                               per_launch)
     return {"bound": "hbm", "kernel": "polar_kernel", "achieved": gbs, "peak": peak, "unit": "GB/s",
-            "frac": gbs / peak, "algorithmic_bytes_per_step": hbm_bytes,
-            "traffic": tr * n / 16384 if tr else None,
-            "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)", "ms_per_step": ms}
+            "frac": gbs / peak, "algorithmic_bytes_per_launch": hbm_bytes, "traffic": tr,
+            "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)", "launch_ms": ms,
+            "ms_per_step": pol_ms / prof_steps}
 
 
 def sparse_work(ctx, lids, frames_d, prefilter):
@@ -715,7 +720,8 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
             continue
         frac_sub = r["patterns_timed"] / n
         roof = (dense_roofline(r["prof"], r["prof_steps"], pairs_step * frac_sub) if nm == "bf16"
-                else sparse_roofline(r["prof"], r["counters"], r["prof_steps"], macs_step * frac_sub, r["clocks"], sm))
+                else sparse_roofline(r["prof"], r["counters"], r["prof_steps"], macs_step * frac_sub, r["clocks"], sm,
+                                     r["patterns_timed"]))
         rec["paths"][nm] = {"patterns_per_s": r["patterns_per_s"], "ms_per_step": r["ms"], "steps": r["steps"],
                             "patterns_timed": r["patterns_timed"], "ms_per_timed_step": r["ms_timed"],
                             "warmup": r["warmup"], "clocks": r["clocks"], "stages": r["stages"],
