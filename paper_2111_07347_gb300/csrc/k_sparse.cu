@@ -27,6 +27,14 @@
 //   multiply-add).
 // * The best shift is only resolved (lowest shift among equal maxima) when the template
 //   can enter the warp's top-N, or when per-template results are requested.
+// * Unmasked top-N (the common case), exact branch and bound: a first pass bounds every
+//   template over three windows of shifts (from per-row window maxima of the pattern) and
+//   stores the bound / (|P| |T|) rounded up to FP16; the templates are visited in spot-count
+//   order (largest first) with each word's bound entries lane-adjacent, so the pass neither
+//   diverges much nor scatters its loads.  Each warp scores first the templates of highest
+//   bound among those it bounded (the seeds); the N-th best Q over all warps' lists is a lower
+//   bound of the final N-th best, and every template whose stored bound is below it is dropped
+//   without a look at its spots.  The others are gathered into one list and scored.
 // Results do not depend on scheduling: a template's sum runs over its spots in CSR order
 // and ranking uses the total order (Q desc, template asc).
 #include <cuda_fp16.h>
@@ -269,6 +277,7 @@ sparse_kernel(const SparseCall c) {
     // per-warp seed lists (bound / (|P| |T|) descending, template ids)
     float* s_seedq = reinterpret_cast<float*>(((uintptr_t)(s_cw + (size_t)c.max_rad * nchw) + 3) & ~(uintptr_t)3);
     int* s_seedk = reinterpret_cast<int*>(s_seedq + kWarps * kSeedsMax);
+    int* s_ncand = s_seedk + kWarps * kSeedsMax;            // [1] candidates after the seeds
     const int kSeeds = c.seeds_per_warp > 0 ? min(c.seeds_per_warp, kSeedsMax) : 8;
     const float inv_pitch = 1.0f / (float)pitch;
     unsigned long long work = 0;                             // multiply-adds of this warp (lane 0)
@@ -375,15 +384,16 @@ sparse_kernel(const SparseCall c) {
             // over each of three windows of shifts, C(s) <= sum_i I_i max P'[r_i][visited
             // columns] (the window maxima are rounded up), or with windows too wide for the
             // chunk table over the whole row; plus a margin for the rounding of both sums
-            // (2^-24 per operation; sum_i |I_i P'| <= isum * pmax)
-            auto lane_bound = [&](const int4& meta_l) -> float {
+            // (2^-24 per operation; sum_i |I_i P'| <= isum * pmax).  bs[i * bstride] holds the
+            // window entries of the template's spot i.
+            auto lane_bound = [&](const int4& meta_l, const int2* bs, int bstride) -> float {
                 const int cnt_l = meta_l.y & 0xffff;
                 float ub = 0.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
                 if (windows) {
                     // per spot: its intensity and the table entries of its three windows
 #pragma unroll kBoundUnroll
                     for (int i = 0; i < cnt_l; ++i) {
-                        const int2 w = __ldg(L.bspot + meta_l.x + i);
+                        const int2 w = __ldg(bs + i * bstride);
                         const float I = __int_as_float(w.x);
                         const int j0 = w.y & 0xffff;
                         u0 = fmaf(I, __half2float(s_cw[j0]), u0);
@@ -463,7 +473,12 @@ sparse_kernel(const SparseCall c) {
             // its bound.  Seeded templates are marked and not scored again.
             // (not with a template mask -- the pre-filter's survivors or the rescore candidates --,
             // where too few templates remain for the extra pass to pay)
-            const bool seeding = prune && c.seed_bits && !mrow;
+            const bool seeding = prune && c.seed_bits && c.seed_cand && !mrow;
+            // Both passes of the seeded search visit the templates in spot-count order (window
+            // bounds only): bit words, stored bounds and seeds then refer to sorted positions,
+            // results to library indices.
+            const bool sorted = seeding && windows && L.ell != nullptr;
+            const int4* smeta = sorted ? L.smeta : L.meta;
             uint32_t* seedbits = c.seed_bits ? c.seed_bits + (size_t)blockIdx.x * c.seed_words : nullptr;
             // every template's bound / (|P| |T|) from the seeding pass, rounded up to FP16, so the
             // main pass compares it with the threshold instead of bounding the template again
@@ -482,12 +497,24 @@ sparse_kernel(const SparseCall c) {
                     uint32_t m;
                     int4 meta_l;
                     int rem;
-                    word_meta(wd, m, meta_l, rem);
+                    const int2* bs = nullptr;
+                    int bstride = 1;
+                    if (sorted) {
+                        rem = L.K - wd * 32;
+                        m = rem < 32 ? (1u << rem) - 1u : 0xffffffffu;
+                        meta_l = make_int4(0, 1 << 16, 0, 0);
+                        if (lane < rem) meta_l = __ldg(smeta + wd * 32 + lane);
+                        bs = L.ell + __ldg(L.ellw + wd) + lane;
+                        bstride = 32;
+                    } else {
+                        word_meta(wd, m, meta_l, rem);
+                        if (windows) bs = L.bspot + meta_l.x;
+                    }
                     float qb = -INFINITY;
                     if (lane < rem && ((m >> lane) & 1u)) {
                         const float d_l = pn * __int_as_float(meta_l.z);
                         if (d_l > 0.0f) {
-                            qb = lane_bound(meta_l) / d_l;
+                            qb = lane_bound(meta_l, bs, bstride) / d_l;
                             qbound[wd * 32 + lane] = __float2half_ru(qb);
                         } else {
                             qbound[wd * 32 + lane] = __ushort_as_half((unsigned short)0x7c00);   // +inf: never skipped
@@ -511,11 +538,11 @@ sparse_kernel(const SparseCall c) {
                 }
                 __syncthreads();                             // the bit words are zero; every warp's seeds known
                 for (int i = 0; i < kSeeds; ++i) {
-                    const int k = sk[i];
-                    if (k < 0) break;
-                    if (lane == 0) atomicOr(seedbits + (k >> 5), 1u << (k & 31));
-                    const int4 mk = __ldg(L.meta + k);
-                    score_one(k, mk.x, mk.y, __int_as_float(mk.z), INFINITY);
+                    const int j = sk[i];
+                    if (j < 0) break;
+                    if (lane == 0) atomicOr(seedbits + (j >> 5), 1u << (j & 31));
+                    const int4 mk = __ldg(smeta + j);
+                    score_one(sorted ? __ldg(L.sperm + j) : j, mk.x, mk.y, __int_as_float(mk.z), INFINITY);
                 }
                 __syncthreads();
                 // the N-th best of all warps' lists (distinct templates) bounds the final N-th
@@ -547,42 +574,96 @@ sparse_kernel(const SparseCall c) {
                     }
                     if (lane == 0 && got == N) atomicMax(s_thr, score_key(nth));
                 }
-                if (threadIdx.x == 0) *counter = 0;
+                if (threadIdx.x == 0) *s_ncand = 0;
                 __syncthreads();
+                // Candidates: the templates not seeded whose stored bound (rounded up) reaches the
+                // threshold, with a margin far above the rounding of the division (the threshold
+                // only rises, so a template dropped here would be dropped later as well).  Each
+                // thread tests 8 consecutive positions; a warp reserves its entries at once.
+                int* cand = c.seed_cand + (size_t)blockIdx.x * c.seed_words * 32;
+                {
+                    const float thr0 = key_score(*(volatile unsigned*)s_thr);
+                    const float cut = thr0 - fabsf(thr0) * 1e-5f;
+                    // warp-uniform trip count (the scan below is warp-collective); lanes past the
+                    // end keep nothing
+                    for (int jw = 256 * warp; jw < 32 * L.words; jw += 8 * blockDim.x) {
+                        const int j0 = jw + 8 * lane;
+                        const bool in = j0 < 32 * L.words;
+                        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                        uint32_t sb = 0xffu;
+                        if (in) {
+                            v = *reinterpret_cast<const uint4*>(qbound + j0);
+                            sb = (seedbits[j0 >> 5] >> (j0 & 31)) & 0xffu;
+                        }
+                        const uint32_t h[4] = {v.x, v.y, v.z, v.w};
+                        uint32_t keep = 0;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float qb = __half2float(__ushort_as_half((unsigned short)(h[u >> 1] >> (16 * (u & 1)))));
+                            const bool k_ok = j0 + u < L.K && !((sb >> u) & 1u) && !(thr0 > -INFINITY && qb < cut);
+                            keep |= (uint32_t)k_ok << u;
+                        }
+                        const int cnt = __popc(keep);
+                        int incl = cnt;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        int base = 0;
+                        if (lane == 31 && incl) base = atomicAdd(s_ncand, incl);
+                        base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+                        while (keep) {
+                            const int u = __ffs(keep) - 1;
+                            keep &= keep - 1;
+                            cand[base++] = j0 + u;
+                        }
+                    }
+                }
+                __syncthreads();
+                const int ncand = *s_ncand;
+                // Warp w takes candidates w, w + kWarps, ...: one lane-parallel load of 32 of them, then
+                // each is tested against the current threshold by its stored bound and scored.
+                for (int b0 = warp; b0 < ncand; b0 += 32 * kWarps) {
+                    const int ci = b0 + lane * kWarps;
+                    int j_l = 0, k_l = 0;
+                    int4 mk_l = make_int4(0, 0, 0, 0);
+                    float qb_l = 0.0f;
+                    if (ci < ncand) {
+                        j_l = cand[ci];
+                        mk_l = __ldg(smeta + j_l);
+                        k_l = sorted ? __ldg(L.sperm + j_l) : j_l;
+                        qb_l = __half2float(qbound[j_l]);
+                    }
+                    uint32_t mm = __ballot_sync(0xffffffffu, ci < ncand);
+                    while (mm) {
+                        const int bit = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const float qb = __shfl_sync(0xffffffffu, qb_l, bit);
+                        const float thr = fmaxf(qthr, key_score(*(volatile unsigned*)s_thr));
+                        if (thr > -INFINITY && qb < thr - fabsf(thr) * 1e-5f) continue;
+                        score_one(__shfl_sync(0xffffffffu, k_l, bit), __shfl_sync(0xffffffffu, mk_l.x, bit),
+                                  __shfl_sync(0xffffffffu, mk_l.y, bit),
+                                  __int_as_float(__shfl_sync(0xffffffffu, mk_l.z, bit)), INFINITY);
+                    }
+                }
             }
-            for (;;) {
+            for (; !seeding;) {
                 int wd = 0;
                 if (lane == 0) wd = atomicAdd(counter, 1);
                 wd = __shfl_sync(0xffffffffu, wd, 0);
                 if (wd >= L.words) break;
                 uint32_t m;
-                int4 meta_l = make_int4(0, 1 << 16, 0, 0);
+                int4 meta_l;
                 int rem;
-                if (seeding) {
-                    // the seeding pass's bounds: drop, all lanes at once, the templates whose bound
-                    // (rounded up) is below the threshold, with a margin far above the rounding of the
-                    // division; a kept template is bounded again, exactly, before it is scored.  The
-                    // metadata of a word is loaded only when some template of it is kept.
-                    rem = L.K - wd * 32;
-                    m = 0xffffffffu;
-                    if (rem < 32) m &= (1u << rem) - 1u;
-                    m &= ~seedbits[wd];
-                    const float thr0 = fmaxf(qthr, key_score(*(volatile unsigned*)s_thr));
-                    bool drop = false;
-                    if (thr0 > -INFINITY && lane < rem && ((m >> lane) & 1u))
-                        drop = __half2float(qbound[wd * 32 + lane]) < thr0 - fabsf(thr0) * 1e-5f;
-                    m &= ~__ballot_sync(0xffffffffu, drop);
-                    if (!m) continue;
-                    if ((m >> lane) & 1u) meta_l = __ldg(L.meta + wd * 32 + lane);
-                } else {
-                    word_meta(wd, m, meta_l, rem);
-                    if (qo && lane < rem && !((m >> lane) & 1u)) {
-                        qo[wd * 32 + lane] = -INFINITY;
-                        so[wd * 32 + lane] = -1;
-                    }
+                word_meta(wd, m, meta_l, rem);
+                if (qo && lane < rem && !((m >> lane) & 1u)) {
+                    qo[wd * 32 + lane] = -INFINITY;
+                    so[wd * 32 + lane] = -1;
                 }
                 float ubm_l = INFINITY;
-                if (prune && lane < rem && ((m >> lane) & 1u)) ubm_l = lane_bound(meta_l);
+                if (prune && lane < rem && ((m >> lane) & 1u))
+                    ubm_l = lane_bound(meta_l, windows ? L.bspot + meta_l.x : nullptr, 1);
                 // drop, all lanes at once, the templates whose bound is already below the
                 // threshold (the threshold only rises, so the test in the loop would drop them
                 // as well); the loop then visits the others only
@@ -677,7 +758,7 @@ int sparse_max_ctas(int num_sms) { return num_sms * 8; }
 size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout, int* pitch) {
     if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
     const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16 + (size_t)max_rad * 8 + 16 +
-                         (size_t)kMaxWarps * kSeedsMax * 8 + 4;
+                         (size_t)kMaxWarps * kSeedsMax * 8 + 8;
     const int order[3] = {TM_LAYOUT_DUAL, TM_LAYOUT_WF, TM_LAYOUT_WRAP};
     const size_t limit[3] = {kDualBytes, kWrapFreeBytes, 232448};
     for (int i = 0; i < 3; ++i) {

@@ -80,6 +80,10 @@ struct Library {
     int2* d_spot2 = nullptr;       // per-spot offsets in the dual / wrap-free layouts
     int2* d_bspot = nullptr;       // per-spot pruning-window entries (null: none)
     int4* d_meta = nullptr;        // per template {first spot, spots | shifts << 16, norm bits, 0}
+    int4* d_smeta = nullptr;       // d_meta in spot-count order, with the order and the bound entries
+    int32_t* d_sperm = nullptr;    //   by word (sliced ELL, lanes adjacent): see tmgb::SparseLib
+    int32_t* d_ellw = nullptr;
+    int2* d_ell = nullptr;
     float* d_norm = nullptr;
     int32_t* d_nshift = nullptr;
     float* d_radial = nullptr;     // [K][n_rad rounded up to 4] radial profiles at the distinct radii
@@ -328,8 +332,9 @@ int rotational_order(const Merged& m, int n_theta) {
 
 // Host half of library loading: validation, rounding, merging, mirrors, norms, orders.
 struct Prepared {
-    std::vector<int2> spot, spot2, bspot;
-    std::vector<int4> meta;
+    std::vector<int2> spot, spot2, bspot, ell;
+    std::vector<int4> meta, smeta;
+    std::vector<int32_t> sperm, ellw;
     std::vector<int32_t> nshift;
     std::vector<double> radial, rnorm;
 };
@@ -506,6 +511,40 @@ int prepare_library(const tm_library_desc* d, Library* L, Prepared* P) {
         memcpy(&sb, &fs, 4);
         P->meta[k] = make_int4((int32_t)L->off[k], (int32_t)(cnt | ((int64_t)P->nshift[k] << 16)), nb, sb);
     }
+    // the bound entries again, templates ordered by spot count (descending, stable: the words
+    // taken last are the cheapest) and each word's entries stored spot-major with its 32 lanes
+    // adjacent, so the bound loop of a warp neither diverges much nor scatters its loads;
+    // padding positions hold empty templates
+    if (!P->bspot.empty()) {
+        const int64_t words = (L->K + 31) / 32;
+        std::vector<int32_t> perm(L->K);
+        for (int64_t k = 0; k < L->K; ++k) perm[k] = (int32_t)k;
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+            return L->off[a + 1] - L->off[a] > L->off[b + 1] - L->off[b];
+        });
+        P->smeta.assign(words * 32, make_int4(0, 0, 0, 0));
+        P->sperm.assign(words * 32, 0);
+        P->ellw.resize(words);
+        int64_t n_ell = 0;
+        for (int64_t w = 0; w < words; ++w) {
+            int64_t mc = 0;
+            for (int64_t j = 32 * w; j < std::min<int64_t>(32 * w + 32, L->K); ++j)
+                mc = std::max<int64_t>(mc, L->off[perm[j] + 1] - L->off[perm[j]]);
+            if (n_ell > INT32_MAX - 32 * mc)
+                return fail(TM_ERR_UNSUPPORTED, "tm_load_library: too many spots for the sorted bound entries");
+            P->ellw[w] = (int32_t)n_ell;
+            n_ell += 32 * mc;
+        }
+        P->ell.assign(n_ell, make_int2(0, 0));
+        for (int64_t j = 0; j < L->K; ++j) {
+            const int32_t k = perm[j];
+            P->sperm[j] = k;
+            P->smeta[j] = P->meta[k];
+            const int64_t w = j >> 5, l = j & 31;
+            for (int64_t i = 0; i < L->off[k + 1] - L->off[k]; ++i)
+                P->ell[P->ellw[w] + 32 * i + l] = P->bspot[L->off[k] + i];
+        }
+    }
     return TM_OK;
 }
 
@@ -553,13 +592,26 @@ int build_library(tm_ctx* ctx, const tm_library_desc* d, Library* L) {
         if (rc) return rc;
         L->bytes += b;
         TM_CUDA(cudaMemcpy(L->d_bspot, P.bspot.data(), b, cudaMemcpyHostToDevice), "library spot bound entries");
+        Up sorted[] = {
+            {(void**)&L->d_smeta, P.smeta.data(), P.smeta.size() * 16, "library sorted template metadata"},
+            {(void**)&L->d_sperm, P.sperm.data(), P.sperm.size() * 4, "library sorted template order"},
+            {(void**)&L->d_ellw, P.ellw.data(), P.ellw.size() * 4, "library sorted bound words"},
+            {(void**)&L->d_ell, P.ell.data(), P.ell.size() * 8, "library sorted bound entries"},
+        };
+        for (auto& u : sorted) {
+            rc = dev_alloc(ctx, u.dst, u.bytes ? u.bytes : 16, u.what);
+            if (rc) return rc;
+            L->bytes += u.bytes ? u.bytes : 16;
+            if (u.bytes) TM_CUDA(cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice), u.what);
+        }
     }
     return TM_OK;
 }
 
 void free_library(tm_ctx* ctx, Library* L) {
     void* ps[] = {L->d_off,    L->d_spot,  L->d_spot2, L->d_meta,  L->d_norm,   L->d_nshift, L->d_radial,
-                  L->d_rnorm,  L->d_rt,    L->d_radii, L->d_bspot, L->d_that,   L->d_rowmap};
+                  L->d_rnorm,  L->d_rt,    L->d_radii, L->d_bspot, L->d_that,   L->d_rowmap,
+                  L->d_smeta,  L->d_sperm, L->d_ellw,  L->d_ell};
     for (void* p : ps)
         if (p) cudaFree(p);
     ctx->used -= std::min(ctx->used, L->bytes + L->that_bytes);
@@ -572,6 +624,10 @@ tmgb::SparseLib sparse_view(const Library* L) {
     v.spot2 = L->d_spot2;
     v.bspot = L->d_bspot;
     v.meta = L->d_meta;
+    v.smeta = L->d_smeta;
+    v.sperm = L->d_sperm;
+    v.ellw = L->d_ellw;
+    v.ell = L->d_ell;
     v.norm = L->d_norm;
     v.nshift = L->d_nshift;
     v.radii = L->d_radii;
@@ -1650,6 +1706,8 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
     const int seed_ctas = tmgb::sparse_max_ctas(sms);
     if (!rc) rc = workspace(ctx, st, "seed_bits", (size_t)seed_ctas * max_words * 4, (void**)&seed_bits);
     if (!rc) rc = workspace(ctx, st, "seed_qub", (size_t)seed_ctas * max_words * 32 * 2, (void**)&seed_qub);
+    int32_t* seed_cand = nullptr;
+    if (!rc) rc = workspace(ctx, st, "seed_cand", (size_t)seed_ctas * max_words * 32 * 4, (void**)&seed_cand);
     TensorBuffers tb;
     if (!rc && bf16) rc = tensor_buffers(ctx, st, tp, std::min<int64_t>(tp.nb, chunk), &tb);
     if (rc) return rc;
@@ -1728,6 +1786,7 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
             c.work = ctx->profiling ? ctx->d_work : nullptr;
             c.seed_bits = seed_bits;
             c.seed_qub = seed_qub;
+            c.seed_cand = seed_cand;
             c.seed_words = max_words;
             c.seed_ctas = seed_ctas;
             c.seeds_per_warp = sparse_seeds;

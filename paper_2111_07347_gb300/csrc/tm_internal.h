@@ -45,6 +45,13 @@ struct SparseLib {
     int32_t words;             // ceil(K / 32)
     int32_t nonneg;            // every intensity >= 0 (the sparse kernel may then prune by bounds)
     const int2* bspot;         // [n_spots] {intensity, window-table entries} or null (no window bounds)
+    // The same templates ordered by spot count, largest first (so the 32 templates of a word have
+    // nearly equal counts), for the unmasked top-N pass that bounds every template; present with
+    // bspot:
+    const int4* smeta;         // [words * 32] meta of the template at each sorted position
+    const int32_t* sperm;      // [words * 32] its library index
+    const int32_t* ellw;       // [words] first entry of each sorted word in ell
+    const int2* ell;           // bspot entries of sorted word w: spot i of lane l at ellw[w] + 32 i + l
 };
 
 // Windows of the shift range for the sparse kernel's pruning bound: three windows of
@@ -180,6 +187,7 @@ struct SparseCall {
     // null (or a grid larger than seed_ctas) disables seeding
     uint32_t* seed_bits;
     __half* seed_qub;                   // [seed_ctas][32 seed_words] bounds of the seeding pass
+    int32_t* seed_cand;                 // [seed_ctas][32 seed_words] templates left after the seeds
     int seed_words;                     // >= the libraries' largest word count
     int seed_ctas;
     int seeds_per_warp;                 // 1..16 (0 = 8)

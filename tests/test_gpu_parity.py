@@ -448,7 +448,8 @@ def _topn_from_scores(q, s, active, N):
     return tk, ts_, tq
 
 
-@pytest.mark.parametrize("which,prefilter,subtract", [("fcc", 0.5, 0.0), ("fcc", 1.0, 0.3), ("hcp", 0.5, 0.0)])
+@pytest.mark.parametrize("which,prefilter,subtract", [("fcc", 0.5, 0.0), ("fcc", 1.0, 0.3), ("hcp", 0.5, 0.0),
+                                                    ("hcp", 1.0, 0.0), ("hcp", 1.0, 0.3)])
 def test_bound_pruning_is_exact(ctx, which, prefilter, subtract):
     """The fused top-N skips templates whose bound cannot reach the running N-th best; its hits
     equal, bit for bit, the top-N taken from every template's score computed without skipping
