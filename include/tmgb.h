@@ -247,11 +247,12 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
 /* Autotune the FP32 sparse kernel for a set of libraries: time its shapes -- block size (128,
  * 256, 512 threads; default 256) x templates seeded per warp for the pruned top-N (4, 8, 16;
  * default 8: the templates of highest bound are scored first, so that the top-N threshold
- * the others are pruned against starts high) -- on the first min(n, 2048) frames with these
+ * the others are pruned against starts high), then the best of these with 2 and 4 patterns
+ * per CTA bounded together (default 1) -- on the first min(n, 2048) frames with these
  * parameters, keep the fastest for later calls on libraries of the same shapes (template
  * count, spot count, radii, n_theta) and top_n, and, when the environment variable
- * TMGB_TUNE_CACHE names a file, append "key threads seeds ms" to it; contexts created later
- * read that file back.  Synchronous.  *best_threads (nullable) receives the block size. */
+ * TMGB_TUNE_CACHE names a file, append "key threads seeds tile ms" to it; contexts created
+ * later read that file back (lines without the tile: 1).  Synchronous.  *best_threads (nullable) receives the block size. */
 int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype,
                 int64_t n, int32_t H, int32_t W, const int32_t* lib_ids, int32_t n_libs,
                 int32_t* best_threads, void* stream);

@@ -203,7 +203,7 @@ struct tm_ctx {
     bool capturing = false;
     // autotuned sparse-kernel shape per library signature (tm_autotune): block size and
     // seeds per warp of its pruned top-N
-    struct Tune { int threads = 0, seeds = 0; };
+    struct Tune { int threads = 0, seeds = 0, tile = 0; };
     std::map<std::string, Tune> tuned;
     Tune tune_override;
     std::string tune_file;
@@ -1331,10 +1331,15 @@ int tm_create(int device, size_t hbm_budget_bytes, tm_ctx** out) {
     if (const char* f = getenv("TMGB_TUNE_CACHE")) {
         ctx->tune_file = f;
         if (FILE* fh = fopen(f, "r")) {
-            char key[512];
-            int threads = 0, seeds = 0;
-            double ms = 0;
-            while (fscanf(fh, "%511s %d %d %lf", key, &threads, &seeds, &ms) == 4) ctx->tuned[key] = {threads, seeds};
+            // lines "key threads seeds tile ms" (older lines without the tile: 1)
+            char line[1024], key[512];
+            while (fgets(line, sizeof line, fh)) {
+                int threads = 0, seeds = 0, tile = 1;
+                double ms = 0;
+                const int got = sscanf(line, "%511s %d %d %d %lf", key, &threads, &seeds, &tile, &ms);
+                if (got == 5) ctx->tuned[key] = {threads, seeds, tile};
+                else if (got == 4) ctx->tuned[key] = {threads, seeds, 1};
+            }
             fclose(fh);
         }
     }
@@ -1704,8 +1709,9 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
     uint32_t* seed_bits = nullptr;
     __half* seed_qub = nullptr;
     const int seed_ctas = tmgb::sparse_max_ctas(sms);
-    if (!rc) rc = workspace(ctx, st, "seed_bits", (size_t)seed_ctas * max_words * 4, (void**)&seed_bits);
-    if (!rc) rc = workspace(ctx, st, "seed_qub", (size_t)seed_ctas * max_words * 32 * 2, (void**)&seed_qub);
+    const size_t seed_slots = (size_t)seed_ctas * tmgb::kSparseTile;   // one per pattern of a CTA's tile
+    if (!rc) rc = workspace(ctx, st, "seed_bits", seed_slots * max_words * 4, (void**)&seed_bits);
+    if (!rc) rc = workspace(ctx, st, "seed_qub", seed_slots * max_words * 32 * 2, (void**)&seed_qub);
     int32_t* seed_cand = nullptr;
     if (!rc) rc = workspace(ctx, st, "seed_cand", (size_t)seed_ctas * max_words * 32 * 4, (void**)&seed_cand);
     TensorBuffers tb;
@@ -1732,11 +1738,13 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
     // default 256 -- but 512 when the chunk has at most two patterns per SM, so that each
     // pattern is shared by twice the warps (the latency of small batches such as scan lines)
     int sparse_threads = ctx->tune_override.threads, sparse_seeds = ctx->tune_override.seeds;
+    int sparse_tile = ctx->tune_override.tile;
     if (!sparse_threads) {
         auto tt = ctx->tuned.find(tune_key(libs, n_libs, N));
         if (tt != ctx->tuned.end()) {
             sparse_threads = tt->second.threads;
             sparse_seeds = tt->second.seeds;
+            sparse_tile = tt->second.tile;
         }
     }
     if (!sparse_threads && std::min(chunk, n) <= 2 * (int64_t)sms) sparse_threads = 512;
@@ -1790,6 +1798,7 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
             c.seed_words = max_words;
             c.seed_ctas = seed_ctas;
             c.seeds_per_warp = sparse_seeds;
+            c.tile = sparse_tile;
             if (bf16) {
                 int64_t nl = 0;
                 const int rc2 = prescore_rows(ctx, st, libs, n_libs, spec, tb, polar, pnorm, m, pre ? mask : nullptr,
@@ -1941,11 +1950,14 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
     p.threshold = 0.0;
     // block sizes x seeds per warp (the templates of highest bound scored first, whose scores
     // set the top-N threshold the rest is pruned against)
+    // (then the best of those with tiles of 2 and 4 patterns bounded together)
     const int cand_t[3] = {128, 256, 512}, cand_s[3] = {4, 8, 16};
-    tm_ctx::Tune best{256, 8};
+    tm_ctx::Tune best{256, 8, 1};
     double best_ms = 1e30;
-    for (int ci = 0; ci < 9; ++ci) {
-        const tm_ctx::Tune tc{cand_t[ci / 3], cand_s[ci % 3]};
+    for (int ci = 0; ci < 11; ++ci) {
+        const tm_ctx::Tune tc =
+            ci < 9 ? tm_ctx::Tune{cand_t[ci / 3], cand_s[ci % 3], 1}
+                   : tm_ctx::Tune{best.threads, best.seeds, ci == 9 ? 2 : 4};
         {
             std::lock_guard<std::mutex> lk(ctx->mu);
             ctx->tune_override = tc;
@@ -1973,7 +1985,7 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
         ctx->tuned[key] = best;
         if (!ctx->tune_file.empty()) {
             if (FILE* fh = fopen(ctx->tune_file.c_str(), "a")) {
-                fprintf(fh, "%s %d %d %.6f\n", key.c_str(), best.threads, best.seeds, best_ms / 3.0);
+                fprintf(fh, "%s %d %d %d %.6f\n", key.c_str(), best.threads, best.seeds, best.tile, best_ms / 3.0);
                 fclose(fh);
             }
         }

@@ -183,21 +183,26 @@ struct SparseCall {
     int top_n;
     int threads;                        // block size: 128, 256 or 512 (0 = 256)
     unsigned long long* work;           // nullable: += multiply-adds executed (per warp, at exit)
-    // pruned top-N: per-CTA words marking the templates scored first (seeds), [seed_ctas][seed_words];
-    // null (or a grid larger than seed_ctas) disables seeding
+    // pruned top-N: per-CTA words marking the templates scored first (seeds),
+    // [seed_ctas][kSparseTile][seed_words]; null (or a grid larger than seed_ctas) disables seeding
     uint32_t* seed_bits;
-    __half* seed_qub;                   // [seed_ctas][32 seed_words] bounds of the seeding pass
+    __half* seed_qub;                   // [seed_ctas][kSparseTile][32 seed_words] bounds of the seeding pass
     int32_t* seed_cand;                 // [seed_ctas][32 seed_words] templates left after the seeds
     int seed_words;                     // >= the libraries' largest word count
     int seed_ctas;
     int seeds_per_warp;                 // 1..16 (0 = 8)
+    int tile;                           // patterns bounded together by the unmasked top-N pass:
+                                        // 1 (0) or up to kSparseTile
 };
-// Largest grid of the sparse kernel on a device with num_sms SMs (the seed words are per CTA).
+// Largest grid of the sparse kernel on a device with num_sms SMs (the seed words are per CTA),
+// and the most patterns a CTA bounds together (seed words and stored bounds per pattern).
+constexpr int kSparseTile = 4;
 int sparse_max_ctas(int num_sms);
 
 // Shared-memory bytes the sparse kernel needs (0 when unsupported), the layout it uses
 // (wrap-free rows when they fit comfortably) and its row pitch.
-size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout = nullptr, int* pitch = nullptr);
+size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout = nullptr, int* pitch = nullptr,
+                         int tile = 1);
 int sparse_pitch(int n_theta, int layout);
 int sparse_rows(int n_rad, int layout);
 cudaError_t launch_sparse(const SparseCall& c, int num_sms, cudaStream_t st);

@@ -484,3 +484,42 @@ def test_bound_pruning_is_exact(ctx, which, prefilter, subtract):
     held = int(work_k[tk[tk >= 0]].sum())
     assert held <= counters["sparse_macs"] <= full, (held, counters["sparse_macs"], full)
     ctx.unload_library(lid)
+
+
+@pytest.mark.parametrize("tile", [2, 4])
+def test_tiled_bound_pass_is_exact(ctx, tile, tmp_path, monkeypatch):
+    """Patterns bounded together in tiles (the unmasked pruned top-N; the tile forced through the
+    tuning cache a new context reads back) give, bit for bit, the top-N taken from every
+    template's score computed without skipping, for one library and for two in one call, with
+    a partial last tile."""
+    import torch
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TMGB_TUNE_CACHE", str(cache))
+    libs = [synth.kinematic_library("hcp", step_deg=1.0), synth.kinematic_library("fcc", step_deg=1.0)]
+    rng = synth.make_rng(21)
+    scan = synth.render_scan(rng, libs[0], 50, 256, 256, n_theta=360)
+    f = _t(scan.frames)
+    for sets in ([0], [0, 1]):
+        c1 = tmgb.Context(0)
+        ids = [c1.load_library(libs[i], 128, 360) for i in sets]
+        c1.autotune(f, ids, top_n=5)
+        c1.close()
+        # force the tile on the cached shape (key threads seeds tile ms)
+        lines = [ln.split() for ln in cache.read_text().splitlines() if ln.strip()]
+        key, threads, seeds = lines[-1][0], lines[-1][1], lines[-1][2]
+        cache.write_text(f"{key} {threads} {seeds} {tile} 0.0\n")
+        c2 = tmgb.Context(0)
+        ids = [c2.load_library(libs[i], 128, 360) for i in sets]
+        hits = tmgb.hits_to_numpy(c2.index(f, ids, top_n=5))
+        c2.check()
+        polar, norm, _ = c2.polar_transform(f, 128, 360)
+        for li, lid in enumerate(ids):
+            K = c2.library_info(lid)["n_templates"]
+            q, s_ = c2.correlate(lid, polar, norm)
+            tk, tsh, tq = _topn_from_scores(q.cpu().numpy(), s_.cpu().numpy(), np.ones((50, K), bool), 5)
+            assert np.array_equal(hits[li]["template_index"], tk), (sets, li)
+            assert np.array_equal(hits[li]["shift"], tsh), (sets, li)
+            assert np.array_equal(hits[li]["score"], tq), (sets, li)
+        c2.close()
+        cache.unlink()
+    torch.cuda.synchronize()
