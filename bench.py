@@ -664,9 +664,10 @@ def bench_workload(args, ctx, timer, name, libs_ts, lids, frames_d, frames_np_un
            "bf16": dict(top_n=TOP_N, prefilter=prefilter, path=tmgb.TM_PATH_BF16_RESCORE, rescore_k=rescore_k)}
     out = torch.empty((L, n, TOP_N, 5), dtype=torch.int32, device=dev)
     macs_step, pairs_step = sparse_work(ctx, lids, frames_d, prefilter)
-    # the sparse kernel's shape (block size x seeds per warp) chosen by the library's autotuner
-    # for these libraries, on the first frames of the scan (outside every timed region)
-    tune_n = 256 if name == "multiphase" else 2048
+    # the sparse kernel's shape (block size x seeds per warp on 2048 frames, then the patterns
+    # bounded together on up to 16384) chosen by the library's autotuner for these libraries, on
+    # the first frames of the scan (outside every timed region)
+    tune_n = 256 if name == "multiphase" else 16384
     t0 = time.perf_counter()
     tuned_threads = None if args.no_autotune else ctx.autotune(frames_d[:tune_n], lids, top_n=TOP_N, prefilter=prefilter)
     tune_s = time.perf_counter() - t0

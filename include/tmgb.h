@@ -128,8 +128,11 @@ typedef struct tm_index_params {
 /* tm_index_params.reserved flag for tests of the failure path: the BF16 tensor-core kernel's
  * MMA issuer issues nothing, so its producer and epilogue waits run out (about 1 s each);
  * the kernel records the timeout in the context's device error word, stops its roles,
- * frees its tensor memory and returns.  tm_check then reports TM_ERR_TIMEOUT; the call's
- * hits are meaningless; the context stays usable. */
+ * frees its tensor memory and returns.  The FP32 sparse kernel's row staging (bulk copies,
+ * for n_theta a multiple of 4 outside the dual row layout) expects 16 bytes more than its
+ * copies bring, so its wait runs out (about 1 s, then 1 s more for the copies); it records
+ * the timeout and returns.  tm_check then reports TM_ERR_TIMEOUT; the call's hits are
+ * meaningless; the context stays usable. */
 #define TM_INDEX_TEST_STALL 2
 
 /* tm_index_params.reserved flag: in-plane angle below the polar step (Section 2.2: phi_1 is
@@ -247,12 +250,13 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
 /* Autotune the FP32 sparse kernel for a set of libraries: time its shapes -- block size (128,
  * 256, 512 threads; default 256) x templates seeded per warp for the pruned top-N (4, 8, 16;
  * default 8: the templates of highest bound are scored first, so that the top-N threshold
- * the others are pruned against starts high), then the best of these with 2 and 4 patterns
- * per CTA bounded together (default 1) -- on the first min(n, 2048) frames with these
- * parameters, keep the fastest for later calls on libraries of the same shapes (template
- * count, spot count, radii, n_theta) and top_n, and, when the environment variable
- * TMGB_TUNE_CACHE names a file, append "key threads seeds tile ms" to it; contexts created
- * later read that file back (lines without the tile: 1).  Synchronous.  *best_threads (nullable) receives the block size. */
+ * the others are pruned against starts high) on the first min(n, 2048) frames, then the best
+ * of these with 1 and 4 patterns per CTA bounded together (default 1) on the first
+ * min(n, 16384) -- with these parameters, keep the fastest for later calls on libraries of
+ * the same shapes (template count, spot count, radii, n_theta) and top_n, and, when the
+ * environment variable TMGB_TUNE_CACHE names a file, append "key threads seeds tile ms" to
+ * it (ms per 2048 frames); contexts created later read that file back (lines without the
+ * tile: 1).  Synchronous.  *best_threads (nullable) receives the block size. */
 int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_dev, int32_t dtype,
                 int64_t n, int32_t H, int32_t W, const int32_t* lib_ids, int32_t n_libs,
                 int32_t* best_threads, void* stream);

@@ -43,6 +43,7 @@
 
 #include <algorithm>
 
+#include "tm_device.h"
 #include "tm_internal.h"
 
 namespace tmgb {
@@ -352,34 +353,6 @@ __device__ __forceinline__ uint32_t stage_frame(const T* __restrict__ gframe, T*
 }
 
 // ---------------------------------------------------------------- bulk (TMA) staging
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool bar_try(uint32_t addr, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase (1 s of the global timer); false on timeout.
-__device__ bool bar_wait(uint32_t addr, uint32_t parity) {
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        if (bar_try(addr, parity)) return true;
-        if ((it & 255u) == 255u) {
-            uint64_t t;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > 1000000000ull) return false;
-        }
-    }
-}
-
 // Copies one frame into shared memory with the bulk-copy engine (one cp.async.bulk per row,
 // rows `pitch` elements apart, every row start and length a multiple of 16 bytes), completing
 // on the mbarrier `bar` (phase `parity`), then returns the OR of the staged words as
@@ -387,19 +360,12 @@ __device__ bool bar_wait(uint32_t addr, uint32_t parity) {
 template <typename T>
 __device__ __forceinline__ bool stage_frame_bulk(const T* __restrict__ gframe, T* sF, int H, int W, int pitch,
                                                  uint64_t* bar, uint32_t parity, uint32_t& hi_bits) {
-    const uint32_t b = smem_u32(bar);
     const uint32_t row_bytes = (uint32_t)(W * sizeof(T));
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of sF before the copies' writes
-    if (threadIdx.x == 0)
-        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
-                     "r"(row_bytes * (uint32_t)H)
-                     : "memory");
+    fence_proxy_async_smem();                            // earlier reads of sF before the copies' writes
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, row_bytes * (uint32_t)H);
     for (int y = threadIdx.x; y < H; y += blockDim.x)
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         smem_u32(sF + (size_t)y * pitch)),
-                     "l"(gframe + (size_t)y * W), "r"(row_bytes), "r"(b)
-                     : "memory");
-    const bool ok = bar_wait(b, parity);
+        bulk_g2s(sF + (size_t)y * pitch, gframe + (size_t)y * W, row_bytes, bar);
+    const bool ok = mbar_wait_bounded(bar, parity);
     if (__syncthreads_or(!ok)) return false;
     hi_bits = 0;
     const int vr = (int)(row_bytes / 16);
@@ -442,10 +408,7 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
     float* part = lut + (kHasLut ? kLut : 0);                           // [n_r][nw]
     float* red = part + (size_t)n_r * nw;                               // [blockDim]
     uint64_t* bar = (uint64_t*)(((uintptr_t)(red + blockDim.x) + 7) & ~(uintptr_t)7);   // bulk staging
-    if (STAGED && bulk && threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (STAGED && bulk && threadIdx.x == 0) mbar_init1(bar);
     uint32_t staged = 0;                                                // frames staged by bulk copies
     if (kHasLut) {
         for (int i = threadIdx.x; i < kLut; i += blockDim.x) {
@@ -467,7 +430,7 @@ polar_kernel(const T* __restrict__ frames, int64_t n, int H, int W, int pitch, c
                     // the copy did not land in time: report it, let it finish (bounded), stop
                     if (threadIdx.x == 0) {
                         atomicOr(err, 2u);
-                        bar_wait(smem_u32(bar), staged & 1u);
+                        mbar_wait_bounded(bar, staged & 1u);
                     }
                     __syncthreads();
                     return;

@@ -41,6 +41,7 @@
 #include <float.h>
 #include <limits.h>
 
+#include "tm_device.h"
 #include "tm_internal.h"
 
 namespace tmgb {
@@ -79,6 +80,11 @@ int sparse_pitch(int n_theta, int layout) {
 int sparse_rows(int n_rad, int layout) { return layout == TM_LAYOUT_DUAL ? 2 * n_rad : n_rad; }
 
 namespace {
+
+__device__ __forceinline__ float max4(const float4& a) { return fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)); }
+__device__ __forceinline__ float4 abs4(const float4& a) {
+    return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w));
+}
 
 __device__ __forceinline__ bool better(float qa, int ka, float qb, int kb) {
     return qa > qb || (qa == qb && ka < kb);
@@ -269,7 +275,7 @@ sparse_kernel(const SparseCall c) {
     unsigned* s_thr = (unsigned*)(s_pattern + 1);            // [1] best of the warps' N-th scores (key)
     float* s_rmax = (float*)(s_thr + 1);                     // [max_rad] row maxima of P'
     float* s_rabs = s_rmax + c.max_rad;                      // [max_rad] row maxima of |P'|
-    // window maxima for the pruning bound, rounded up: s_cw[row][j] bounds P' over the columns
+    // window maxima for the pruning bound: s_cw[row][j] is the maximum of P' over the columns
     // [32 j, 32 (j + ncov)) (chunk maxima held one per lane, so at most 32 chunks per row)
     const int ncov = prune_ncov(n_theta), nchw = prune_nchw(n_theta);
     const int nq = nchw + ncov - 1;
@@ -278,13 +284,18 @@ sparse_kernel(const SparseCall c) {
     const int T = c.tile > 1 ? min(c.tile, kSparseTile) : 1;
     const int TS = T > 1 ? kSparseTile : 1;
     const int tstride = c.max_rad * nchw;
-    __half* s_cw = reinterpret_cast<__half*>(s_rabs + c.max_rad);   // [TS][max_rad][nchw]
+    float* s_cw = s_rabs + c.max_rad;                        // [TS][max_rad][nchw]
     // per-warp seed lists (bound / (|P| |T|) descending, template ids), [TS][kWarps][kSeedsMax]
-    float* s_seedq = reinterpret_cast<float*>(((uintptr_t)(s_cw + (size_t)TS * tstride) + 3) & ~(uintptr_t)3);
+    float* s_seedq = s_cw + (size_t)TS * tstride;
     int* s_seedk = reinterpret_cast<int*>(s_seedq + TS * kWarps * kSeedsMax);
     int* s_ncand = s_seedk + TS * kWarps * kSeedsMax;       // [1] candidates after the seeds
     float* s_tpn = reinterpret_cast<float*>(s_ncand + 1);    // [TS] |P| of the tile's patterns
     unsigned* s_tpmax = reinterpret_cast<unsigned*>(s_tpn + TS);   // [TS] max |P'| (float bits)
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(((uintptr_t)(s_tpmax + TS) + 7) & ~(uintptr_t)7);   // row copies
+    // polar rows staged by bulk copies (single-copy layouts; every segment 16-byte aligned)
+    const bool bulk = c.bulk && LAYOUT != TM_LAYOUT_DUAL && (pitch & 3) == 0 && (n_theta & 3) == 0;
+    uint32_t n_bulk = 0;                                     // bulk stagings so far (mbarrier phase)
+    if (bulk && threadIdx.x == 0) mbar_init1(s_bar);
     const int kSeeds = c.seeds_per_warp > 0 ? min(c.seeds_per_warp, kSeedsMax) : 8;
     const float inv_pitch = 1.0f / (float)pitch;
     unsigned long long work = 0;                             // multiply-adds of this warp (lane 0)
@@ -322,14 +333,37 @@ sparse_kernel(const SparseCall c) {
                 __syncthreads();
                 // window tables: per library row of each pattern, the maxima of the 32-column chunks
                 // q < nq of P'[c mod Nθ] (lane q keeps chunk q; warp-uniform trip count), then of the
-                // chunks each window start covers, rounded up; and the pattern's max |P'|
+                // chunks each window start covers; and the pattern's max |P'|.  With Nθ a multiple
+                // of 8 (at most 512) and 16-byte aligned rows, a chunk is four 8-column pieces
+                // (mod Nθ), whose maxima the lanes take with 16-byte loads.
+                const int npc = n_theta >> 3;
+                const bool pieces = bulk && (n_theta & 7) == 0 && npc <= 64;
                 for (int it = warp; it < nt * L.n_rad; it += kWarps) {
                     const int tl = it / L.n_rad, rr = it - tl * L.n_rad;
                     const float* row =
                         c.polar + (size_t)(p0 + tl) * c.n_r * n_theta + (size_t)__ldg(L.radii + rr) * n_theta;
                     float ma = 0.0f, mq = -INFINITY;
+                    if (pieces) {
+                        float pm[2] = {-INFINITY, -INFINITY};        // pieces lane and lane + 32
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (lane + 32 * h < npc) {
+                                const float4* q4 = reinterpret_cast<const float4*>(row) + 2 * (lane + 32 * h);
+                                const float4 a = __ldg(q4), b = __ldg(q4 + 1);
+                                pm[h] = fmaxf(max4(a), max4(b));
+                                ma = fmaxf(ma, fmaxf(max4(abs4(a)), max4(abs4(b))));
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int pc = (4 * lane + i) % npc;
+                            const float v0 = __shfl_sync(0xffffffffu, pm[0], pc & 31);
+                            const float v1 = __shfl_sync(0xffffffffu, pm[1], pc & 31);
+                            mq = fmaxf(mq, pc >= 32 ? v1 : v0);
+                        }
+                    }
 #pragma unroll kStageUnroll
-                    for (int c0 = 0; c0 < 32 * nq; c0 += 32) {
+                    for (int c0 = 0; c0 < (pieces ? 0 : 32 * nq); c0 += 32) {
                         int sc = c0 + lane;
                         while (sc >= n_theta) sc -= n_theta;
                         const float v = __ldg(row + sc);
@@ -344,16 +378,16 @@ sparse_kernel(const SparseCall c) {
                         const float o = __shfl_sync(0xffffffffu, mq, (lane + i) & 31);
                         if (lane + i < nq) w = fmaxf(w, o);
                     }
-                    if (lane < nchw) s_cw[tl * tstride + rr * nchw + lane] = __float2half_ru(w);
+                    if (lane < nchw) s_cw[tl * tstride + rr * nchw + lane] = w;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
                     if (lane == 0) atomicMax(s_tpmax + tl, __float_as_uint(ma));   // (ma >= 0)
                 }
                 __syncthreads();
-                float tpn[kSparseTile], tpm[kSparseTile];
+                float rpn[kSparseTile], tpm[kSparseTile];     // 1 / |P| (0: |P| = 0) and max |P'|
 #pragma unroll
                 for (int tl = 0; tl < kSparseTile; ++tl) {
-                    tpn[tl] = s_tpn[tl];
+                    rpn[tl] = s_tpn[tl] > 0.0f ? 1.0f / s_tpn[tl] : 0.0f;
                     tpm[tl] = __uint_as_float(s_tpmax[tl]);
                 }
                 // the bound pass of every pattern of the tile (tables of patterns past nt are left
@@ -379,44 +413,48 @@ sparse_kernel(const SparseCall c) {
                         const int j1 = j0 + ((e.y >> 16) & 0xff), j2 = j0 + (int)((unsigned)e.y >> 24);
 #pragma unroll
                         for (int tl = 0; tl < kSparseTile; ++tl) {
-                            const __half* tb = s_cw + tl * tstride;
-                            u[tl][0] = fmaf(I, __half2float(tb[j0]), u[tl][0]);
-                            u[tl][1] = fmaf(I, __half2float(tb[j1]), u[tl][1]);
-                            u[tl][2] = fmaf(I, __half2float(tb[j2]), u[tl][2]);
+                            const float* tb = s_cw + tl * tstride;
+                            u[tl][0] = fmaf(I, tb[j0], u[tl][0]);
+                            u[tl][1] = fmaf(I, tb[j1], u[tl][1]);
+                            u[tl][2] = fmaf(I, tb[j2], u[tl][2]);
                         }
                     }
-                    // the rounding margin of the bound as in the single-pattern pass
+                    // the rounding margin of the bound as in the single-pattern pass; bound / (|P| |T|)
+                    // as a product with the reciprocals (one division per template for the tile),
+                    // whose few roundings stay far inside the 1e-5 relative margin the stored bounds
+                    // are compared with
                     const float tn = __int_as_float(meta_l.z);
                     const float mrg = (2.0f * (float)cnt_l + 40.0f) * 5.9604645e-8f * __int_as_float(meta_l.w);
+                    const float rtn = tn > 0.0f ? 1.0f / tn : 0.0f;
 #pragma unroll
                     for (int tl = 0; tl < kSparseTile; ++tl) {
                         if (tl >= nt) break;                 // uniform
                         __half* qbt = c.seed_qub + ((size_t)blockIdx.x * kSparseTile + tl) * c.seed_words * 32;
                         float qb = -INFINITY;
                         if (lane < rem) {
-                            const float d_l = tpn[tl] * tn;
-                            if (d_l > 0.0f) {
-                                qb = (fmaxf(fmaxf(u[tl][0], u[tl][1]), u[tl][2]) + mrg * tpm[tl]) / d_l;
+                            if (rtn > 0.0f && rpn[tl] > 0.0f) {
+                                qb = (fmaxf(fmaxf(u[tl][0], u[tl][1]), u[tl][2]) + mrg * tpm[tl]) * rtn * rpn[tl];
                                 qbt[wd * 32 + lane] = __float2half_ru(qb);
                             } else {
                                 qbt[wd * 32 + lane] = __ushort_as_half((unsigned short)0x7c00);   // +inf
                             }
                         }
+                        // the word's best bound enters the warp's seed list (lowest lane on ties)
+                        // only when it beats the list's last entry
                         float mq = qb;
-                        int ml = lane;
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            const float oq = __shfl_xor_sync(0xffffffffu, mq, o);
-                            const int ol = __shfl_xor_sync(0xffffffffu, ml, o);
-                            if (oq > mq || (oq == mq && ol < ml)) { mq = oq; ml = ol; }
-                        }
+                        for (int o = 16; o > 0; o >>= 1) mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
                         float* sq = s_seedq + (tl * kWarps + warp) * kSeedsMax;
                         int* sk = s_seedk + (tl * kWarps + warp) * kSeedsMax;
-                        if (lane == 0 && mq > sq[kSeeds - 1]) {
-                            int i = kSeeds - 1;
-                            while (i > 0 && mq > sq[i - 1]) { sq[i] = sq[i - 1]; sk[i] = sk[i - 1]; --i; }
-                            sq[i] = mq;
-                            sk[i] = wd * 32 + ml;
+                        if (mq > sq[kSeeds - 1]) {           // uniform (the list is the warp's own)
+                            const int ml = __ffs(__ballot_sync(0xffffffffu, qb == mq)) - 1;
+                            if (lane == 0) {
+                                int i = kSeeds - 1;
+                                while (i > 0 && mq > sq[i - 1]) { sq[i] = sq[i - 1]; sk[i] = sk[i - 1]; --i; }
+                                sq[i] = mq;
+                                sk[i] = wd * 32 + ml;
+                            }
+                            __syncwarp();
                         }
                     }
                     __syncwarp();
@@ -439,9 +477,33 @@ sparse_kernel(const SparseCall c) {
                         asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
                     }
                 }
-                // the library's polar rows (dual layout: a second copy shifted by one column)
+                // the library's polar rows (dual layout: a second copy shifted by one column); column c of
+                // a row holds P'[c mod Nθ]: with bulk copies, segments of at most Nθ columns
                 const int rows = (LAYOUT == TM_LAYOUT_DUAL ? 2 : 1) * L.n_rad;
-                for (int rr = warp; rr < rows; rr += kWarps) {
+                if (bulk) {
+                    const int nseg = (pitch + n_theta - 1) / n_theta;
+                    fence_proxy_async_smem();                    // earlier reads of sP before the copies
+                    if (threadIdx.x == 0)
+                        mbar_arrive_expect_tx(s_bar, (uint32_t)(L.n_rad * pitch * 4) + (c.test_stall ? 16u : 0u));
+                    for (int it = threadIdx.x; it < L.n_rad * nseg; it += blockDim.x) {
+                        const int rr = it / nseg, c0 = (it - rr * nseg) * n_theta;
+                        bulk_g2s(sP + (size_t)rr * pitch + c0, src + (size_t)__ldg(L.radii + rr) * n_theta,
+                                 (uint32_t)(min(n_theta, pitch - c0) * 4), s_bar);
+                    }
+                    const bool ok = mbar_wait_bounded(s_bar, n_bulk & 1u);
+                    if (__syncthreads_or(!ok)) {
+                        // the copies did not land in time: report it, let them finish (bounded), stop
+                        if (threadIdx.x == 0) {
+                            atomicOr(c.error, 4u);
+                            mbar_wait_bounded(s_bar, n_bulk & 1u);
+                        }
+                        __syncthreads();
+                        return;
+                    }
+                    ++n_bulk;
+                }
+                // row maxima (and window tables) from the staged rows; a tile's patterns need neither
+                for (int rr = warp; rr < ((bulk && tiled) ? 0 : rows); rr += kWarps) {
                     const int r0 = rr < L.n_rad ? rr : rr - L.n_rad;
                     const int sh = rr < L.n_rad ? 0 : 1;
                     const float* row = src + (size_t)__ldg(L.radii + r0) * n_theta;
@@ -451,16 +513,21 @@ sparse_kernel(const SparseCall c) {
                     // P'[c mod Nθ] (lane q keeps chunk q); warp-uniform trip count
                     const bool first = rr < L.n_rad;
                     const bool chunks = first && windows && !tiled;   // (windows imply nq <= 32)
-                    const int ncol = chunks ? max(pitch, 32 * nq) : pitch;
+                    const int ncol = bulk ? (chunks ? 32 * nq : n_theta) : (chunks ? max(pitch, 32 * nq) : pitch);
                     float mq = -INFINITY;
 #pragma unroll kStageUnroll
                     for (int c0 = 0; c0 < ncol; c0 += 32) {
                         const int col = c0 + lane;
                         int sc = col + sh;
                         while (sc >= n_theta) sc -= n_theta;
-                        const bool valid = col < pitch || chunks;
-                        const float v = valid ? __ldg(row + sc) : -INFINITY;
-                        if (col < pitch) dst[col] = v;
+                        const bool valid = bulk || col < pitch || chunks;
+                        float v;
+                        if (bulk) {
+                            v = dst[sc];                         // (staged: column sc < Nθ holds P'[sc])
+                        } else {
+                            v = valid ? __ldg(row + sc) : -INFINITY;
+                            if (col < pitch) dst[col] = v;
+                        }
                         if (valid) {
                             mx = fmaxf(mx, v);
                             ma = fmaxf(ma, fabsf(v));
@@ -478,7 +545,7 @@ sparse_kernel(const SparseCall c) {
                             const float o = __shfl_sync(0xffffffffu, mq, (lane + i) & 31);
                             if (lane + i < nq) w = fmaxf(w, o);
                         }
-                        if (lane < nchw) s_cw[rr * nchw + lane] = __float2half_ru(w);
+                        if (lane < nchw) s_cw[rr * nchw + lane] = w;
                     }
                     if (first) {
 #pragma unroll
@@ -517,8 +584,9 @@ sparse_kernel(const SparseCall c) {
                 };
                 // exact pruning (intensities >= 0): each lane bounds its template's best correlation
                 // over each of three windows of shifts, C(s) <= sum_i I_i max P'[r_i][visited
-                // columns] (the window maxima are rounded up), or with windows too wide for the
-                // chunk table over the whole row; plus a margin for the rounding of both sums
+                // columns] (a superset of the visited columns: whole 32-column chunks), or with
+                // windows too wide for the chunk table over the whole row; plus a margin for the
+                // rounding of both sums
                 // (2^-24 per operation; sum_i |I_i P'| <= isum * pmax).  bs[i * bstride] holds the
                 // window entries of the template's spot i.
                 auto lane_bound = [&](const int4& meta_l, const int2* bs, int bstride) -> float {
@@ -531,9 +599,9 @@ sparse_kernel(const SparseCall c) {
                             const int2 w = __ldg(bs + i * bstride);
                             const float I = __int_as_float(w.x);
                             const int j0 = w.y & 0xffff;
-                            u0 = fmaf(I, __half2float(s_cw[j0]), u0);
-                            u1 = fmaf(I, __half2float(s_cw[j0 + ((w.y >> 16) & 0xff)]), u1);
-                            u2 = fmaf(I, __half2float(s_cw[j0 + (int)((unsigned)w.y >> 24)]), u2);
+                            u0 = fmaf(I, s_cw[j0], u0);
+                            u1 = fmaf(I, s_cw[j0 + ((w.y >> 16) & 0xff)], u1);
+                            u2 = fmaf(I, s_cw[j0 + (int)((unsigned)w.y >> 24)], u2);
                         }
                         ub = fmaxf(fmaxf(u0, u1), u2);
                     } else {
@@ -903,7 +971,7 @@ size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout, int* 
     if (n_theta < 1 || n_theta > 1024 || top_n < 1 || top_n > TM_MAX_TOPN || max_rad < 1) return 0;
     const size_t ts = tile > 1 ? kSparseTile : 1;          // window tables and seed lists per pattern
     const size_t lists = (size_t)kMaxWarps * top_n * 12 + kMaxWarps * 4 + 16 + (size_t)max_rad * 8 + 16 +
-                         ts * kMaxWarps * kSeedsMax * 8 + 8 + ts * 8 + 4;
+                         ts * kMaxWarps * kSeedsMax * 8 + 8 + ts * 8 + 4 + 16;
     const int order[3] = {TM_LAYOUT_DUAL, TM_LAYOUT_WF, TM_LAYOUT_WRAP};
     const size_t limit[3] = {kDualBytes, kWrapFreeBytes, 232448};
     for (int i = 0; i < 3; ++i) {
@@ -911,7 +979,7 @@ size_t sparse_smem_bytes(int max_rad, int n_theta, int top_n, int* layout, int* 
         const size_t rows = (size_t)sparse_rows(max_rad, order[i]);
         // per-spot offsets of the dual and wrap-free layouts are 16-bit
         if (order[i] != TM_LAYOUT_WRAP && rows * pch > 65535) continue;
-        const size_t windows = ts * max_rad * prune_nchw(n_theta) * 2;   // half [ts][max_rad][nchw]
+        const size_t windows = ts * max_rad * prune_nchw(n_theta) * 4;   // float [ts][max_rad][nchw]
         const size_t b = rows * pch * 4 + lists + windows;
         if (b <= limit[i]) {
             if (layout) *layout = order[i];

@@ -1608,6 +1608,8 @@ int tm_correlate(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* n
     c.mask[0] = mask_dev;
     c.q_out[0] = q_dev;
     c.s_out[0] = s_dev;
+    c.bulk = L->n_theta % 4 == 0 && ((uintptr_t)polar_dev & 15) == 0;
+    c.error = ctx->d_error;
     c.hits = nullptr;
     c.top_n = 1;
     TM_CUDA(tmgb::launch_sparse(c, ctx->num_sms, st), "tm_correlate: launch");
@@ -1799,6 +1801,9 @@ int tmgb::index_patterns_ex(tm_ctx* ctx, const tm_index_params* params, const vo
             c.seed_ctas = seed_ctas;
             c.seeds_per_warp = sparse_seeds;
             c.tile = sparse_tile;
+            c.bulk = n_theta % 4 == 0 && ((uintptr_t)polar & 15) == 0;
+            c.error = ctx->d_error;
+            c.test_stall = (params->reserved & TM_INDEX_TEST_STALL) ? 1 : 0;
             if (bf16) {
                 int64_t nl = 0;
                 const int rc2 = prescore_rows(ctx, st, libs, n_libs, spec, tb, polar, pnorm, m, pre ? mask : nullptr,
@@ -1934,13 +1939,15 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
         }
         key = tune_key(libs, n_libs, params->top_n);
     }
-    const int64_t m = std::min<int64_t>(n, 2048);
+    // shapes on the first m frames; the tile (patterns bounded together) on up to m2, enough
+    // tiles per CTA that the last ones do not decide the time
+    const int64_t m = std::min<int64_t>(n, 2048), m2 = std::min<int64_t>(n, 16384);
     const int64_t N = params->top_n;
     tm_hit* out = nullptr;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         DeviceGuard g(ctx->device);
-        int rc = workspace(ctx, (cudaStream_t)stream, "tune_out", (size_t)n_libs * m * N * sizeof(tm_hit), (void**)&out);
+        int rc = workspace(ctx, (cudaStream_t)stream, "tune_out", (size_t)n_libs * m2 * N * sizeof(tm_hit), (void**)&out);
         if (rc) return rc;
     }
     tm_index_params p = *params;
@@ -1948,24 +1955,16 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
     p.reserved = 0;
     p.pixel_mask = nullptr;
     p.threshold = 0.0;
-    // block sizes x seeds per warp (the templates of highest bound scored first, whose scores
-    // set the top-N threshold the rest is pruned against)
-    // (then the best of those with tiles of 2 and 4 patterns bounded together)
-    const int cand_t[3] = {128, 256, 512}, cand_s[3] = {4, 8, 16};
-    tm_ctx::Tune best{256, 8, 1};
-    double best_ms = 1e30;
-    for (int ci = 0; ci < 11; ++ci) {
-        const tm_ctx::Tune tc =
-            ci < 9 ? tm_ctx::Tune{cand_t[ci / 3], cand_s[ci % 3], 1}
-                   : tm_ctx::Tune{best.threads, best.seeds, ci == 9 ? 2 : 4};
+    // milliseconds of the sparse kernel per call of shape tc on the first mm frames (3 timed calls)
+    auto time_shape = [&](const tm_ctx::Tune& tc, int64_t mm, double* ms) -> int {
         {
             std::lock_guard<std::mutex> lk(ctx->mu);
             ctx->tune_override = tc;
         }
-        int rc = tm_index_patterns(ctx, &p, frames_dev, dtype, m, H, W, nullptr, lib_ids, n_libs, out, nullptr, stream);
+        int rc = tm_index_patterns(ctx, &p, frames_dev, dtype, mm, H, W, nullptr, lib_ids, n_libs, out, nullptr, stream);
         if (!rc) rc = tm_profile_enable(ctx, 1);
         for (int r = 0; r < 3 && !rc; ++r)
-            rc = tm_index_patterns(ctx, &p, frames_dev, dtype, m, H, W, nullptr, lib_ids, n_libs, out, nullptr, stream);
+            rc = tm_index_patterns(ctx, &p, frames_dev, dtype, mm, H, W, nullptr, lib_ids, n_libs, out, nullptr, stream);
         tm_profile prof;
         if (!rc) rc = tm_profile_read(ctx, &prof);
         tm_profile_enable(ctx, 0);
@@ -1973,11 +1972,35 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
             std::lock_guard<std::mutex> lk(ctx->mu);
             ctx->tune_override = tm_ctx::Tune{};
         }
+        *ms = prof.ms[TM_STAGE_SPARSE] / 3.0;
+        return rc;
+    };
+    // block sizes x seeds per warp (the templates of highest bound scored first, whose scores
+    // set the top-N threshold the rest is pruned against), then the best of those with tiles
+    // of 4 patterns bounded together
+    const int cand_t[3] = {128, 256, 512}, cand_s[3] = {4, 8, 16};
+    tm_ctx::Tune best{256, 8, 1};
+    double best_ms = 1e30;
+    for (int ci = 0; ci < 9; ++ci) {
+        const tm_ctx::Tune tc{cand_t[ci / 3], cand_s[ci % 3], 1};
+        double ms = 0.0;
+        const int rc = time_shape(tc, m, &ms);
         if (rc) return rc;
-        const double ms = prof.ms[TM_STAGE_SPARSE];
         if (ms < best_ms) {
             best_ms = ms;
             best = tc;
+        }
+    }
+    {
+        double ms1 = 0.0, ms4 = 0.0;
+        const tm_ctx::Tune t4{best.threads, best.seeds, tmgb::kSparseTile};
+        int rc = time_shape(best, m2, &ms1);
+        if (!rc) rc = time_shape(t4, m2, &ms4);
+        if (rc) return rc;
+        best_ms = ms1 * (double)m / (double)m2;
+        if (ms4 < ms1) {
+            best = t4;
+            best_ms = ms4 * (double)m / (double)m2;
         }
     }
     {
@@ -1985,7 +2008,7 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
         ctx->tuned[key] = best;
         if (!ctx->tune_file.empty()) {
             if (FILE* fh = fopen(ctx->tune_file.c_str(), "a")) {
-                fprintf(fh, "%s %d %d %d %.6f\n", key.c_str(), best.threads, best.seeds, best.tile, best_ms / 3.0);
+                fprintf(fh, "%s %d %d %d %.6f\n", key.c_str(), best.threads, best.seeds, best.tile, best_ms);
                 fclose(fh);
             }
         }

@@ -193,6 +193,11 @@ struct SparseCall {
     int seeds_per_warp;                 // 1..16 (0 = 8)
     int tile;                           // patterns bounded together by the unmasked top-N pass:
                                         // 1 (0) or up to kSparseTile
+    int bulk;                           // stage the polar rows with bulk copies (n_theta a multiple
+                                        // of 4, polar 16-byte aligned; not for the dual layout)
+    unsigned* error;                    // device error word: bit 4 when a staging wait ran out
+    int test_stall;                     // failure-path tests: the row staging expects 16 bytes more
+                                        // than its copies bring, so its wait runs out
 };
 // Largest grid of the sparse kernel on a device with num_sms SMs (the seed words are per CTA),
 // and the most patterns a CTA bounds together (seed words and stored bounds per pattern).

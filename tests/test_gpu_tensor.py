@@ -219,3 +219,28 @@ def test_bounded_waits_time_out_report_and_recover(ctx):
     ctx.check()
     assert np.array_equal(again, ref)
     ctx.unload_library(lid)
+
+
+def test_sparse_staging_wait_times_out_report_and_recover(ctx):
+    """Failure path of the FP32 sparse kernel's bulk row staging, without a GPU fault: with the
+    staging told to expect 16 bytes more than its copies bring, its bounded wait runs out; the
+    kernel records the timeout and returns; tm_check reports TM_ERR_TIMEOUT; the next call on
+    the same context gives the normal results (HCP: 25 radii, single-copy row layout)."""
+    import time
+    ts = synth.kinematic_library("hcp", step_deg=3.0)
+    scan = synth.render_scan(synth.make_rng(31), ts, 8, 256, 256, n_theta=360)
+    lid = ctx.load_library(ts, 128, 360)
+    frames = _t(scan.frames)
+    ref = tmgb.hits_to_numpy(ctx.index(frames, lid, top_n=5))
+    ctx.check()
+    t0 = time.perf_counter()
+    ctx.index(frames, lid, top_n=5, test_stall=True)
+    with pytest.raises(tmgb.TmError) as e:
+        ctx.check()
+    assert e.value.code == tmgb.TM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    ctx.check()
+    again = tmgb.hits_to_numpy(ctx.index(frames, lid, top_n=5))
+    ctx.check()
+    assert np.array_equal(again, ref)
+    ctx.unload_library(lid)
