@@ -251,9 +251,10 @@ int tm_prescore(tm_ctx* ctx, int lib_id, const float* polar_dev, const float* no
  * 256, 512 threads; default 256) x templates seeded per warp for the pruned top-N (4, 8, 16;
  * default 8: the templates of highest bound are scored first, so that the top-N threshold
  * the others are pruned against starts high) on the first min(n, 2048) frames, then the best
- * of these with 1 and 4 patterns per CTA bounded together (default 1) on the first
- * min(n, 16384) -- with these parameters, keep the fastest for later calls on libraries of
- * the same shapes (template count, spot count, radii, n_theta) and top_n, and, when the
+ * of these against its block size with 4 patterns per CTA bounded together (default 1) and
+ * each seed count on the first min(n, 16384) -- with these parameters, keep the fastest for
+ * later calls on libraries of the same shapes (template count, spot count, radii, n_theta)
+ * and top_n, and, when the
  * environment variable TMGB_TUNE_CACHE names a file, append "key threads seeds tile ms" to
  * it (ms per 2048 frames); contexts created later read that file back (lines without the
  * tile: 1).  Synchronous.  *best_threads (nullable) receives the block size. */

@@ -1976,8 +1976,8 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
         return rc;
     };
     // block sizes x seeds per warp (the templates of highest bound scored first, whose scores
-    // set the top-N threshold the rest is pruned against), then the best of those with tiles
-    // of 4 patterns bounded together
+    // set the top-N threshold the rest is pruned against), then the best block size with tiles
+    // of 4 patterns bounded together and each seed count
     const int cand_t[3] = {128, 256, 512}, cand_s[3] = {4, 8, 16};
     tm_ctx::Tune best{256, 8, 1};
     double best_ms = 1e30;
@@ -1992,16 +1992,21 @@ int tm_autotune(tm_ctx* ctx, const tm_index_params* params, const void* frames_d
         }
     }
     {
-        double ms1 = 0.0, ms4 = 0.0;
-        const tm_ctx::Tune t4{best.threads, best.seeds, tmgb::kSparseTile};
-        int rc = time_shape(best, m2, &ms1);
-        if (!rc) rc = time_shape(t4, m2, &ms4);
+        // on the larger sample: that shape, and tiles of 4 with each seed count
+        double ms = 0.0;
+        int rc = time_shape(best, m2, &ms);
         if (rc) return rc;
-        best_ms = ms1 * (double)m / (double)m2;
-        if (ms4 < ms1) {
-            best = t4;
-            best_ms = ms4 * (double)m / (double)m2;
+        double best2 = ms;
+        for (int si = 0; si < 3; ++si) {
+            const tm_ctx::Tune t4{best.threads, cand_s[si], tmgb::kSparseTile};
+            rc = time_shape(t4, m2, &ms);
+            if (rc) return rc;
+            if (ms < best2) {
+                best2 = ms;
+                best = t4;
+            }
         }
+        best_ms = best2 * (double)m / (double)m2;
     }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
