@@ -77,7 +77,8 @@ def parse():
     ap.add_argument("--no-preprocess", action="store_true", help="skip the background-removal and blur timing")
     ap.add_argument("--total", type=int, default=0, help="patterns per step (0: the workload's; smaller for profiling)")
     ap.add_argument("--distinct", type=int, default=0, help="distinct rendered frames (0: the workload's)")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the sparse kernel's default shape")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner: the default shape, or the one a TMGB_TUNE_CACHE file holds")
     return ap.parse_args()
 
 
