@@ -832,15 +832,18 @@ sparse_kernel(const SparseCall c) {
                     }
                     __syncthreads();
                     const int ncand = *s_ncand;
-                    // Warp w takes candidates w, w + kWarps, ...: one lane-parallel load of 32 of them, then
-                    // each is tested against the current threshold by its stored bound and scored.
+                    // Warp w takes candidates w, w + kWarps, ... counted from the end of the list, which
+                    // follows the bound pass's order (most spots first), so the templates with the fewest
+                    // spots come first: over a subtracted background they reach a high Q most often, and
+                    // the threshold rises sooner.  One lane-parallel load of 32 of them, then each is tested
+                    // against the current threshold by its stored bound and scored.
                     for (int b0 = warp; b0 < ncand; b0 += 32 * kWarps) {
                         const int ci = b0 + lane * kWarps;
                         int j_l = 0, k_l = 0;
                         int4 mk_l = make_int4(0, 0, 0, 0);
                         float qb_l = 0.0f;
                         if (ci < ncand) {
-                            j_l = cand[ci];
+                            j_l = cand[ncand - 1 - ci];
                             mk_l = __ldg(smeta + j_l);
                             k_l = sorted ? __ldg(L.sperm + j_l) : j_l;
                             qb_l = __half2float(qbound[j_l]);
