@@ -19,9 +19,10 @@
 //     (a select per block).
 //   The library stores, per spot, its shared-memory offset in the dual and wrap-free
 //   layouts, so no address is decoded in the inner loop.
-// * A persistent CTA takes patterns from a global counter (and prefetches into L2 the rows of
-//   the pattern gridDim.x further on, which some CTA takes soon); its warps take 32-template
-//   mask words from a shared counter.  One warp scores one template: the lanes hold all its
+// * A persistent CTA takes patterns (or tiles of up to 4 patterns) from a global counter and
+//   stages their rows (with bulk copies on an mbarrier when the layout allows), prefetching
+//   into L2 the rows of the patterns one tile per CTA further on, which some CTA takes soon;
+//   its warps take 32-template mask words from a shared counter.  One warp scores one template: the lanes hold all its
 //   shifts in registers; the template's spots arrive in one lane-parallel load and are
 //   broadcast by shuffles.  The bound is the shared-memory load path (4 bytes per
 //   multiply-add).
@@ -31,10 +32,12 @@
 //   template over three windows of shifts (from per-row window maxima of the pattern) and
 //   stores the bound / (|P| |T|) rounded up to FP16; the templates are visited in spot-count
 //   order (largest first) with each word's bound entries lane-adjacent, so the pass neither
-//   diverges much nor scatters its loads.  Each warp scores first the templates of highest
-//   bound among those it bounded (the seeds); the N-th best Q over all warps' lists is a lower
-//   bound of the final N-th best, and every template whose stored bound is below it is dropped
-//   without a look at its spots.  The others are gathered into one list and scored.
+//   diverges much nor scatters its loads.  A tile's patterns share this pass: each bound entry
+//   is loaded once and applied to the tile's window tables.  Each warp scores first the
+//   templates of highest bound among those it bounded (the seeds); the N-th best Q over all
+//   warps' lists is a lower bound of the final N-th best, and every template whose stored
+//   bound is below it is dropped without a look at its spots.  The others are gathered into
+//   one list and scored, fewest spots first.
 // Results do not depend on scheduling: a template's sum runs over its spots in CSR order
 // and ranking uses the total order (Q desc, template asc).
 #include <cuda_fp16.h>
