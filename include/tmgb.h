@@ -203,6 +203,22 @@ int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, 
                             int32_t* r, int32_t* t, float* intensity, float* norm, int32_t* order,
                             int32_t* packed, int32_t* packed2);
 
+/* The host half of tm_load_library, continued (no GPU): the sparse kernel's second copy of
+ * its pruning-window entries, used by the unmasked top-N pass that bounds every template
+ * (Eq. 1's numerator bounded over three windows of shifts, Section 2.2).  The templates are
+ * in the order that pass visits them, by spot count, most first, ties by library index;
+ * each 32-template word's entries are stored spot-major with its 32 lanes adjacent.
+ * Call with NULL arrays to get *n_words (ceil(K / 32)) and *n_entries, then with host
+ * buffers: order [n_words * 32] the library index at each position (padding 0);
+ * word_start [n_words] the first entry of each word; entries [n_entries][2] int32 pairs,
+ * entry word_start[w] + 32 i + l holding, for the template at position 32 w + l, its spot
+ * i's {intensity (float bits), window entries j0 | d1 << 16 | d2 << 24} (j0 = rho * nchw +
+ * t / 32 and the chunk increments of the second and third windows), zero where the
+ * template has fewer spots.  TM_ERR_UNSUPPORTED when the library gets no window table
+ * (the kernel then bounds by whole rows and keeps no second copy). */
+int tm_library_bound_entries_host(const tm_library_desc* desc, int32_t* n_words, int64_t* n_entries,
+                                  int32_t* order, int32_t* word_start, int32_t* entries);
+
 /* Stage 1 (Section 2.2, Fig. 2 (a)-(c)): gamma/subtract and bilinear polar resampling.
  * frames_dev [n][H][W] (TM_DTYPE_U16 or TM_DTYPE_F32, row-major, contiguous);
  * centres_dev [n][2] float (cx, cy) per pattern, finite, or NULL to use params->cx/cy for

@@ -1518,6 +1518,23 @@ int tm_library_prepare_host(const tm_library_desc* desc, tm_library_info* info, 
     return TM_OK;
 }
 
+int tm_library_bound_entries_host(const tm_library_desc* desc, int32_t* n_words, int64_t* n_entries,
+                                  int32_t* order, int32_t* word_start, int32_t* entries) {
+    if (!n_words || !n_entries) return fail(TM_ERR_INVALID_ARG, "tm_library_bound_entries_host: NULL size");
+    Library L;
+    Prepared P;
+    int rc = prepare_library(desc, &L, &P);
+    if (rc) return rc;
+    if (P.ell.empty() && P.ellw.empty())
+        return fail(TM_ERR_UNSUPPORTED, "tm_library_bound_entries_host: the library has no window table");
+    *n_words = (int32_t)P.ellw.size();
+    *n_entries = (int64_t)P.ell.size();
+    if (order) memcpy(order, P.sperm.data(), P.sperm.size() * 4);
+    if (word_start) memcpy(word_start, P.ellw.data(), P.ellw.size() * 4);
+    if (entries) memcpy(entries, P.ell.data(), P.ell.size() * 8);
+    return TM_OK;
+}
+
 int tm_library_export(tm_ctx* ctx, int lib_id, int64_t* offsets, int32_t* r, int32_t* t, float* intensity,
                       float* norm, int32_t* order) {
     if (!ctx) return fail(TM_ERR_INVALID_ARG, "tm_library_export: ctx is NULL");

@@ -119,6 +119,8 @@ _SIGS = {
     "tm_library_export": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "tm_library_prepare_host": (ctypes.c_int, [ctypes.POINTER(tm_library_desc), ctypes.POINTER(tm_library_info),
                                                _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tm_library_bound_entries_host": (ctypes.c_int, [ctypes.POINTER(tm_library_desc), ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.POINTER(ctypes.c_int64), _P, _P, _P]),
     "tm_polar_transform": (ctypes.c_int, [_P, ctypes.POINTER(tm_index_params), _P, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_double, _P, _P, _P, _P]),
@@ -253,6 +255,22 @@ def tm_library_prepare_host(ts, n_r: int, n_theta: int, dr: float = 1.0, mirror=
                                              out["packed"].ctypes.data if out["packed"].size else None,
                                              out["packed2"].ctypes.data if out["packed2"].size else None))
     out["info"] = _info_dict(info)
+    return out
+
+
+def tm_library_bound_entries_host(ts, n_r: int, n_theta: int, dr: float = 1.0, mirror=None,
+                                  unit_intensity: bool = False) -> dict:
+    """The sparse kernel's spot-count-ordered bound entries (no GPU): order, word_start,
+    entries [n][2] int32."""
+    d = _Desc(ts, n_r, n_theta, dr, mirror, unit_intensity)
+    nw, ne = ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(library().tm_library_bound_entries_host(ctypes.byref(d.desc), ctypes.byref(nw), ctypes.byref(ne),
+                                                   None, None, None))
+    out = dict(order=np.zeros(nw.value * 32, np.int32), word_start=np.zeros(nw.value, np.int32),
+               entries=np.zeros((ne.value, 2), np.int32))
+    _check(library().tm_library_bound_entries_host(ctypes.byref(d.desc), ctypes.byref(nw), ctypes.byref(ne),
+                                                   out["order"].ctypes.data, out["word_start"].ctypes.data,
+                                                   out["entries"].ctypes.data if ne.value else None))
     return out
 
 

@@ -300,3 +300,52 @@ def test_noalloc_rejects_bad_params_before_launch(lib, field, value, needle):
     rc = f(None, ctypes.byref(p), None, tmgb.TM_DTYPE_U16, 4, 256, 256, 0, None, None)
     assert rc == tmgb.TM_ERR_INVALID_ARG
     assert needle in tmgb.tm_last_error()
+
+
+@pytest.mark.parametrize("which", ["random", "fcc", "hcp"])
+def test_sorted_bound_entries_cover_every_spot(which):
+    """The second copy of the pruning-window entries that the unmasked top-N pass reads. The
+    order must be a permutation of the templates by spot count, most first, ties by library
+    index. For spot i of the template at position 32 w + l the kernel reads entry
+    word_start[w] + 32 i + l. That entry must stay below the next word's start and hold the
+    spot's intensity bits and window-table entries, recomputed here from the spot's radius row
+    and angle column. Every table index must lie inside the rows x chunks table, and every
+    other entry must be zero."""
+    if which == "random":
+        ts, _, _ = synth.tiny_workload(n_side=1)
+        n_r, n_theta = 60, 180
+    else:
+        ts = synth.kinematic_library(which, step_deg=3.0)
+        n_r, n_theta = 128, 360
+    h = tmgb.tm_library_prepare_host(ts, n_r, n_theta)
+    e = tmgb.tm_library_bound_entries_host(ts, n_r, n_theta)
+    off = h["offsets"]
+    K = off.size - 1
+    cnt = np.diff(off)
+    nw = (K + 31) // 32
+    order, ws, ent = e["order"], e["word_start"], e["entries"]
+    assert order.size == 32 * nw and ws.size == nw
+    perm = order[:K]
+    assert np.array_equal(perm, np.lexsort((np.arange(K), -cnt)))
+    radii = np.unique(h["r"])
+    rows = np.searchsorted(radii, h["r"]).astype(np.int64)
+    t = h["t"].astype(np.int64)
+    ww = (n_theta + 2) // 3
+    nchw = ((n_theta - 1 + 2 * ww) >> 5) + 1
+    j0 = rows * nchw + (t >> 5)
+    d1 = ((t + ww) >> 5) - (t >> 5)
+    d2 = ((t + 2 * ww) >> 5) - (t >> 5)
+    assert (j0 + d2 < radii.size * nchw).all()
+    word = j0 | (d1 << 16) | (d2 << 24)
+    ibits = h["intensity"].view(np.int32)
+    ends = np.append(ws[1:], ent.shape[0])
+    seen = np.zeros(ent.shape[0], bool)
+    for pos in range(K):
+        w, lane = divmod(pos, 32)
+        k = perm[pos]
+        idx = ws[w] + 32 * np.arange(cnt[k]) + lane
+        assert (idx < ends[w]).all()
+        assert np.array_equal(ent[idx, 0], ibits[off[k]:off[k + 1]])
+        assert np.array_equal(ent[idx, 1].astype(np.int64) & 0xFFFFFFFF, word[off[k]:off[k + 1]])
+        seen[idx] = True
+    assert not ent[~seen].any()
